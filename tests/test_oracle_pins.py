@@ -1,0 +1,324 @@
+"""Pins of the oracle against facts fixed by mathematics, not by the oracle itself.
+
+Each test names what it pins and why a plausible slip in the oracle would fail it.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spl
+
+from fixtures import hex_cube, p1_jittered, q1_square, rhs_uniform, lognormal_coefficients
+from oracle import dense_mf, gmres, hodlr, hodlr_mf, nd, symbolic
+from oracle.philox import philox4x32_10, rademacher
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------- fixtures
+@pytest.mark.parametrize("m", [5, 6, 9])
+def test_q1_closed_form_eigenvalues(m):
+    """Constant-coefficient Q1 stiffness: lambda_jk = 2/3 (4 - c_j - c_k - 2 c_j c_k),
+    c_j = cos(j pi h) -- a wrong element matrix or a dropped entry moves them."""
+    p = q1_square(m)
+    h = 1.0 / m
+    c = np.cos(np.arange(1, m) * np.pi * h)
+    lam = (2.0 / 3.0) * (4 - c[:, None] - c[None, :] - 2 * c[:, None] * c[None, :])
+    ev = np.linalg.eigvalsh(p.scipy().toarray())
+    np.testing.assert_allclose(np.sort(ev), np.sort(lam.ravel()), atol=1e-13)
+    assert p.nnz == (3 * (m - 1) - 2) ** 2
+
+
+@pytest.mark.parametrize("m", [4, 6])
+def test_hex_closed_form_eigenvalues(m):
+    """Trilinear hex: lambda = 2h/9 [(1-c_j)(2+c_k)(2+c_l) + perms]."""
+    p = hex_cube(m)
+    h = 1.0 / m
+    c = np.cos(np.arange(1, m) * np.pi * h)
+    cj, ck, cl = c[:, None, None], c[None, :, None], c[None, None, :]
+    lam = (2 * h / 9) * ((1 - cj) * (2 + ck) * (2 + cl) + (2 + cj) * (1 - ck) * (2 + cl)
+                         + (2 + cj) * (2 + ck) * (1 - cl))
+    ev = np.linalg.eigvalsh(p.scipy().toarray())
+    np.testing.assert_allclose(np.sort(ev), np.sort(lam.ravel()), atol=1e-13)
+    assert p.nnz == (3 * (m - 1) - 2) ** 3
+
+
+def test_p1_mesh_spd_and_consistent():
+    """P1 element matrices annihilate constants: interior rows away from the boundary
+    sum to zero; the reduced matrix is symmetric positive definite."""
+    p = p1_jittered(12, seed=5)
+    A = p.scipy()
+    assert abs(A - A.T).max() < 1e-14
+    assert np.linalg.eigvalsh(A.toarray()).min() > 0
+    ii, jj = p.coords[:, 0], p.coords[:, 1]
+    deep = (ii > 0) & (ii < p.extents[0] - 1) & (jj > 0) & (jj < p.extents[1] - 1)
+    rs = np.asarray(A.sum(axis=1)).ravel()
+    assert np.abs(rs[deep]).max() < 1e-12
+    assert np.abs(rs[~deep]).min() > 0  # boundary-adjacent rows keep a positive sum
+
+
+def test_lognormal_and_rhs_are_seeded():
+    a = lognormal_coefficients(100, 1.0, seed=1)
+    b = lognormal_coefficients(100, 1.0, seed=1)
+    assert np.array_equal(a, b) and np.all(a > 0)
+    r = rhs_uniform(50, 3, 2)
+    assert r.shape == (50, 3) and r.flags.f_contiguous and np.abs(r).max() <= 1
+
+
+# ----------------------------------------------------------------------------- philox
+def test_philox_known_answer_vectors():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox4x32_10(*v[:6])
+        assert [int(o) for o in out] == v[6:]
+
+
+def test_rademacher_is_balanced_and_keyed():
+    a = rademacher(200, 50, 7, 11)
+    assert set(np.unique(a)) == {-1.0, 1.0}
+    assert abs(a.mean()) < 0.05
+    assert not np.array_equal(a, rademacher(200, 50, 8, 11))
+    assert np.array_equal(a[:10, :5], rademacher(10, 5, 7, 11))
+
+
+# ----------------------------------------------------------------------------- ND + symbolic
+def _dense_symbolic_cholesky(Ap):
+    """Structure of the Cholesky factor by boolean elimination (brute force)."""
+    M = (Ap.toarray() != 0) | np.eye(Ap.shape[0], dtype=bool)
+    # structural pattern: use the CSR pattern, not values
+    M = np.zeros(Ap.shape, dtype=bool)
+    coo = Ap.tocoo()
+    M[coo.row, coo.col] = True
+    n = M.shape[0]
+    for j in range(n):
+        rows = np.nonzero(M[j + 1:, j])[0] + j + 1
+        if rows.size:
+            M[np.ix_(rows, rows)] = True
+    return np.tril(M)
+
+
+@pytest.mark.parametrize("maker", [lambda: q1_square(10), lambda: q1_square(13),
+                                   lambda: hex_cube(6), lambda: p1_jittered(11, 9)])
+def test_nd_and_front_sets_match_brute_force_fill(maker):
+    """I_p^f equals the rows (after I_p) of the Cholesky fill of P A P^T in the
+    columns of I_p; the permutation is one; the tree is a postorder; the two halves
+    below a separator are not adjacent."""
+    p = maker()
+    et = nd.nested_dissection(p.coords, leaf_size=8)
+    assert np.array_equal(np.sort(et.perm), np.arange(p.n))
+    assert np.array_equal(et.iperm[et.perm], np.arange(p.n))
+    nf = et.nfronts
+    assert et.parent[-1] == -1 and np.all(et.parent[:-1] > np.arange(nf - 1))
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    L = _dense_symbolic_cholesky(Ap)
+    owner = np.searchsorted(et.first, np.arange(p.n), side="right") - 1
+    for q in range(nf):
+        b, e = et.first[q], et.first[q + 1]
+        rows = np.nonzero(L[e:, b:e].any(axis=1))[0] + e
+        assert np.array_equal(rows, sym.If[q]), q
+        # relmap places the child's update inside the parent front
+        if et.parent[q] >= 0:
+            par = et.parent[q]
+            front = dense_mf.front_indices(et, sym, par)
+            assert np.array_equal(front[sym.relmap[q]], sym.If[q])
+    # separators separate: no edge between distinct subtrees of a separator
+    A = Ap.tocoo()
+    for q in range(nf):
+        ch = sym.children[q]
+        if len(ch) == 2:
+            def subtree(c):
+                s = {c}
+                for k in range(c, -1, -1):
+                    if et.parent[k] in s:
+                        s.add(k)
+                return s
+            s0, s1 = subtree(ch[0]), subtree(ch[1])
+            o_r, o_c = owner[A.row], owner[A.col]
+            bad = np.isin(o_r, list(s0)) & np.isin(o_c, list(s1))
+            assert not bad.any()
+
+
+def test_nd_rule_on_a_hand_checked_grid():
+    """7x7 interior grid, leaf 4, worked by hand from the stated rule: the root splits
+    x at 3 (tie -> x); each 3x7 half splits y at 3; each 3x3 quarter splits x at 1 into
+    two 1x3 leaves.  Postorder: leaf, leaf, separator, ..., root."""
+    p = q1_square(8)  # 7x7 interior
+    et = nd.nested_dissection(p.coords, leaf_size=4)
+    parent = [2, 2, 6, 5, 5, 6, 14, 9, 9, 13, 12, 12, 13, 14, -1]
+    assert et.parent.tolist() == parent
+    assert et.first.tolist() == [0, 3, 6, 9, 12, 15, 18, 21, 24, 27, 30, 33, 36, 39, 42, 49]
+    y3 = np.arange(3)
+    expect = {
+        0: [(0, y) for y in y3], 1: [(2, y) for y in y3], 2: [(1, y) for y in y3],
+        3: [(0, y + 4) for y in y3], 4: [(2, y + 4) for y in y3], 5: [(1, y + 4) for y in y3],
+        6: [(x, 3) for x in y3],
+        7: [(4, y) for y in y3], 8: [(6, y) for y in y3], 9: [(5, y) for y in y3],
+        10: [(4, y + 4) for y in y3], 11: [(6, y + 4) for y in y3], 12: [(5, y + 4) for y in y3],
+        13: [(x + 4, 3) for x in y3], 14: [(3, y) for y in range(7)],
+    }
+    for q, pts in expect.items():
+        got = p.coords[et.perm[et.first[q]:et.first[q + 1]]]
+        assert [tuple(v) for v in got.tolist()] == pts, q
+    assert et.level.tolist() == [3, 3, 2, 3, 3, 2, 1, 3, 3, 2, 3, 3, 2, 1, 0]
+
+
+# ----------------------------------------------------------------------------- dense MF
+@pytest.mark.parametrize("maker", [lambda: q1_square(12), lambda: hex_cube(5),
+                                   lambda: p1_jittered(10, 3)])
+def test_dense_mf_equals_global_cholesky(maker):
+    """Front factors are the blocks of numpy's Cholesky of P A P^T (Eq. update is the
+    Schur complement), and the solve inverts A."""
+    p = maker()
+    et = nd.nested_dissection(p.coords, leaf_size=8)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    Lg = np.linalg.cholesky(Ap.toarray())
+    fronts, _ = dense_mf.factor(Ap, et, sym)
+    for q, fr in enumerate(fronts):
+        b, e = et.first[q], et.first[q + 1]
+        Lpp = np.tril(fr.cho[0])
+        np.testing.assert_allclose(Lpp, Lg[b:e, b:e], atol=1e-12)
+        Lfp = sla.solve_triangular(Lpp, fr.Ffp.T, lower=True).T
+        np.testing.assert_allclose(Lfp, Lg[sym.If[q]][:, b:e], atol=1e-12)
+    rng = np.random.default_rng(0)
+    xs = rng.standard_normal(p.n)
+    A = p.scipy()
+    x = dense_mf.direct_solve(p.rowptr, p.colidx, p.values, p.coords, A @ xs, leaf_size=8)
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-10 * np.abs(xs).max())
+
+
+# ----------------------------------------------------------------------------- HODLR
+def _random_spd_hodlr(n, leaf, r, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, n)) / np.sqrt(n)
+    K = X @ X.T + np.eye(n)
+    return K
+
+
+def test_truncated_svd_eckart_young():
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((60, 40)) @ np.diag(0.5 ** np.arange(40)) @ rng.standard_normal((40, 40))
+    for tol in [1e-2, 1e-6]:
+        U, V = hodlr.truncated_svd(B, tol)
+        s = np.linalg.svd(B, compute_uv=False)
+        r = U.shape[1]
+        assert s[r - 1] > tol * s[0] >= s[r]
+        err = np.linalg.norm(B - U @ V.T, 2)
+        assert abs(err - s[r]) <= 1e-10 * s[0]
+
+
+def test_rrf_exact_on_low_rank_and_bounded():
+    rng = np.random.default_rng(2)
+    B = rng.standard_normal((80, 7)) @ rng.standard_normal((7, 90))
+    Om = rademacher(90, 17, 1, 3)
+    U, V = hodlr.randomized_range_finder(B, 1e-12, Om)
+    assert U.shape[1] == 7
+    np.testing.assert_allclose(U @ V.T, B, atol=1e-10 * np.abs(B).max())
+    # decaying spectrum: error within a small multiple of tol * sigma_1
+    C = rng.standard_normal((100, 60)) @ np.diag(0.6 ** np.arange(60)) @ rng.standard_normal((60, 70))
+    s1 = np.linalg.norm(C, 2)
+    U, V = hodlr.randomized_range_finder(C, 1e-4, rademacher(70, 40, 2, 3))
+    assert np.linalg.norm(C - U @ V.T, 2) <= 10 * 1e-4 * s1
+
+
+@pytest.mark.parametrize("n,leaf", [(256, 32), (200, 16), (64, 64), (130, 20)])
+def test_woodbury_solve_matches_dense(n, leaf):
+    """Recursive Woodbury inverse of a HODLR matrix equals the dense inverse of the
+    matrix it represents (tol 0: the representation is exact, so also of K)."""
+    K = _random_spd_hodlr(n, leaf, 5, n)
+    H = hodlr.build(K, leaf, 0.0)
+    np.testing.assert_allclose(hodlr.to_dense(H), K, atol=1e-12)
+    hodlr.factor(H)
+    X = np.random.default_rng(3).standard_normal((n, 3))
+    np.testing.assert_allclose(hodlr.solve(H, X), np.linalg.solve(K, X), rtol=1e-9, atol=1e-10)
+    # compressed: equals the inverse of the represented (approximate) matrix
+    H2 = hodlr.build(K, leaf, 1e-2)
+    Kd = hodlr.to_dense(H2)
+    hodlr.factor(H2)
+    np.testing.assert_allclose(hodlr.solve(H2, X), np.linalg.solve(Kd, X), rtol=1e-8, atol=1e-9)
+
+
+def test_hodlr_partition_depth():
+    assert hodlr.hodlr_depth(64, 64) == 0
+    assert hodlr.hodlr_depth(65, 64) == 1
+    assert hodlr.hodlr_depth(1023, 64) == 4
+    H = hodlr.build(np.eye(1023), 64, 0.0)
+    leaves = [nd_ for nd_ in hodlr.iter_nodes(H) if not nd_.children]
+    assert len(leaves) == 16 and max(l.hi - l.lo for l in leaves) <= 64
+    assert {l.level for l in leaves} == {4}
+
+
+# ----------------------------------------------------------------------------- HODLR-MF
+def _setup(p, leaf_nd=64):
+    et = nd.nested_dissection(p.coords, leaf_nd)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    return et, sym, Ap
+
+
+def test_hodlr_mf_tol0_is_exact_direct_solve():
+    """tol 0 keeps every nonzero singular value: the preconditioner is A^{-1} and GMRES
+    converges in one iteration."""
+    p = q1_square(48, lognormal_coefficients(48 * 48, 1.0, seed=1))
+    et, sym, Ap = _setup(p, 16)
+    prm = hodlr_mf.Params(tol=0.0, n_c=8, leaf=8)
+    fr, _ = hodlr_mf.factor(Ap, et, sym, prm)
+    assert any(f.kind == "hodlr" for f in fr)
+    r = np.random.default_rng(0).standard_normal((p.n, 2))
+    x = hodlr_mf.apply(fr, et, sym, r)
+    np.testing.assert_allclose(Ap @ x, r, atol=1e-9)
+    xg, info = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), r[:, 0])
+    assert info["iters"] == 1 and info["relres"] < 1e-10
+
+
+def test_hodlr_mf_preconditioner_is_symmetric_and_close():
+    """M^{-1} built from symmetric HODLR pieces is symmetric; with tol 1e-3 it is a
+    good approximation (||I - M^{-1}A|| < 1) and GMRES reaches 1e-10."""
+    p = q1_square(32, lognormal_coefficients(32 * 32, 1.0, seed=4))
+    et, sym, Ap = _setup(p, 16)
+    prm = hodlr_mf.Params(tol=1e-3, n_c=8, leaf=8)
+    fr, _ = hodlr_mf.factor(Ap, et, sym, prm)
+    Minv = hodlr_mf.apply(fr, et, sym, np.eye(p.n))
+    np.testing.assert_allclose(Minv, Minv.T, atol=1e-10 * np.abs(Minv).max())
+    E = np.eye(p.n) - Minv @ Ap.toarray()
+    assert np.linalg.norm(E, 2) < 0.5
+    b = rhs_uniform(p.n, 1, 0)[:, 0]
+    x, info = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), b)
+    assert info["converged"]
+    xs = spl.spsolve(Ap.tocsc(), b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8
+
+
+def test_hodlr_mf_rrf_matches_svd_iterations():
+    p = q1_square(64)
+    et, sym, Ap = _setup(p)
+    b = rhs_uniform(p.n, 1, 0)[:, 0][et.perm]
+    its = []
+    for comp in ["svd", "rrf"]:
+        prm = hodlr_mf.Params(tol=1e-6, n_c=16, leaf=16, compressor=comp, samples=40)
+        fr, _ = hodlr_mf.factor(Ap, et, sym, prm)
+        x, info = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), b)
+        assert info["converged"]
+        its.append(info["iters"])
+    assert abs(its[0] - its[1]) <= 1
+
+
+# ----------------------------------------------------------------------------- GMRES
+def test_gmres_unpreconditioned_matches_solve():
+    p = q1_square(12)
+    A = p.scipy()
+    b = rhs_uniform(p.n, 1, 3)[:, 0]
+    x, info = gmres.gmres(lambda v: A @ v, lambda v: v, b, rtol=1e-12, restart=10)
+    assert info["converged"]
+    np.testing.assert_allclose(x, np.linalg.solve(A.toarray(), b), rtol=1e-9)
+    h = np.array(info["history"])
+    # within one cycle the rotated residual estimate never increases
+    for c in range(0, len(h), 10):
+        seg = h[c:c + 10]
+        assert np.all(np.diff(seg) <= 1e-15)
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-12
