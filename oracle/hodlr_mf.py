@@ -35,7 +35,7 @@ import scipy.sparse as sp
 from . import hodlr
 from .dense_mf import assemble_fbar, extend_add
 from .nd import ETree
-from .philox import block_id, rademacher
+from .philox import block_id, sketch
 from .symbolic import Symbolic
 
 
@@ -66,7 +66,7 @@ def _compressor(prm: Params, front: int, kind: int):
         if prm.compressor == "svd":
             return hodlr.truncated_svd(B, prm.tol)
         k = min(prm.samples, B.shape[0], B.shape[1])
-        Om = rademacher(B.shape[1], k, block_id(front, kind, level, index), prm.seed)
+        Om = sketch(B.shape[1], k, block_id(front, kind, level, index), prm.seed)
         return hodlr.randomized_range_finder(B, prm.tol, Om)
     return comp
 

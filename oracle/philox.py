@@ -1,4 +1,4 @@
-"""Philox4x32-10 counter-based generator and the Rademacher test matrix drawn from it.
+"""Philox4x32-10 counter-based generator and the sketch matrix drawn from it.
 
 ORACLE / TEST INFRASTRUCTURE ONLY.
 
@@ -13,7 +13,11 @@ bit-identical sketches.
 
 Sketch entry convention: for a block with 64-bit id ``blk`` and seed ``seed``, entry
 ``Omega[i, c]`` uses counter ``(i, c, blk_lo, blk_hi)`` and key ``(seed_lo, seed_hi)``;
-its value is ``+1`` if bit 0 of output word 0 is set, else ``-1``.
+with ``w`` the output word 0, its value is ``((w >> 8) - 2^23) / 2^23``: uniform on a grid
+of 2^24 points in [-1, 1), exactly representable in FP32 and FP64 (no rounding, so both
+sides see identical sketches).  A continuous-like distribution keeps square sketches
+invertible with overwhelming probability (a +-1 sketch is singular with noticeable
+probability at small sizes).
 """
 from __future__ import annotations
 
@@ -55,8 +59,8 @@ def block_id(front: int, kind: int, level: int, node: int) -> int:
     return (int(front) << 24) | (int(kind) << 20) | (int(level) << 16) | int(node)
 
 
-def rademacher(rows: int, cols: int, blk: int, seed: int) -> np.ndarray:
-    """``rows x cols`` matrix of +-1 entries from Philox4x32-10 (convention above)."""
+def sketch(rows: int, cols: int, blk: int, seed: int) -> np.ndarray:
+    """``rows x cols`` sketch matrix from Philox4x32-10 (convention above)."""
     i = np.arange(rows, dtype=np.uint32)[:, None]
     c = np.arange(cols, dtype=np.uint32)[None, :]
     blo = np.uint32(blk & 0xFFFFFFFF)
@@ -64,4 +68,4 @@ def rademacher(rows: int, cols: int, blk: int, seed: int) -> np.ndarray:
     slo = np.uint32(seed & 0xFFFFFFFF)
     shi = np.uint32((seed >> 32) & 0xFFFFFFFF)
     w0, _, _, _ = philox4x32_10(i, c, blo, bhi, slo, shi)
-    return np.where((w0 & np.uint32(1)) != 0, 1.0, -1.0)
+    return ((w0 >> np.uint32(8)).astype(np.float64) - 8388608.0) / 8388608.0

@@ -11,7 +11,7 @@ import scipy.sparse.linalg as spl
 
 from fixtures import hex_cube, p1_jittered, q1_square, rhs_uniform, lognormal_coefficients
 from oracle import dense_mf, gmres, hodlr, hodlr_mf, nd, symbolic
-from oracle.philox import philox4x32_10, rademacher
+from oracle.philox import philox4x32_10, sketch
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -77,12 +77,14 @@ def test_philox_known_answer_vectors():
         assert [int(o) for o in out] == v[6:]
 
 
-def test_rademacher_is_balanced_and_keyed():
-    a = rademacher(200, 50, 7, 11)
-    assert set(np.unique(a)) == {-1.0, 1.0}
-    assert abs(a.mean()) < 0.05
-    assert not np.array_equal(a, rademacher(200, 50, 8, 11))
-    assert np.array_equal(a[:10, :5], rademacher(10, 5, 7, 11))
+def test_sketch_is_uniform_grid_and_keyed():
+    a = sketch(200, 50, 7, 11)
+    assert a.min() >= -1.0 and a.max() < 1.0
+    assert np.all(a * 8388608.0 == np.round(a * 8388608.0))           # 24-bit grid
+    assert np.array_equal(a, a.astype(np.float32).astype(np.float64))  # exact in FP32
+    assert abs(a.mean()) < 0.05 and abs(a.var() - 1.0 / 3.0) < 0.02
+    assert not np.array_equal(a, sketch(200, 50, 8, 11))
+    assert np.array_equal(a[:10, :5], sketch(10, 5, 7, 11))
 
 
 # ----------------------------------------------------------------------------- ND + symbolic
@@ -215,14 +217,14 @@ def test_truncated_svd_eckart_young():
 def test_rrf_exact_on_low_rank_and_bounded():
     rng = np.random.default_rng(2)
     B = rng.standard_normal((80, 7)) @ rng.standard_normal((7, 90))
-    Om = rademacher(90, 17, 1, 3)
+    Om = sketch(90, 17, 1, 3)
     U, V = hodlr.randomized_range_finder(B, 1e-12, Om)
     assert U.shape[1] == 7
     np.testing.assert_allclose(U @ V.T, B, atol=1e-10 * np.abs(B).max())
     # decaying spectrum: error within a small multiple of tol * sigma_1
     C = rng.standard_normal((100, 60)) @ np.diag(0.6 ** np.arange(60)) @ rng.standard_normal((60, 70))
     s1 = np.linalg.norm(C, 2)
-    U, V = hodlr.randomized_range_finder(C, 1e-4, rademacher(70, 40, 2, 3))
+    U, V = hodlr.randomized_range_finder(C, 1e-4, sketch(70, 40, 2, 3))
     assert np.linalg.norm(C - U @ V.T, 2) <= 10 * 1e-4 * s1
 
 
