@@ -1,0 +1,190 @@
+/*
+ * hodlr_mf.h -- C ABI of the GB300 (sm_103a) HODLR-accelerated multifrontal solver.
+ *
+ * The library solves A x = b for a sparse symmetric positive definite finite-element
+ * matrix A (Aminfar & Darve, "A Fast and Memory Efficient Sparse Solver with
+ * Applications to Finite-Element Matrices", arXiv 1410.2697, Section 1) with GMRES
+ * preconditioned by an approximate (HODLR-accelerated) multifrontal factorization
+ * (Sections 3 and 4).  Every numerical step runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Return value: an hm_status code (0 = HM_OK).  No call aborts, traps or throws;
+ *     hm_status_str() gives a message, hm_last_error() the detail of the last failure
+ *     on the calling thread.
+ *   - Array arguments may be host or device (CUDA) pointers; the library detects which
+ *     and copies what it needs.  The caller keeps ownership of every array it passes;
+ *     nothing is retained after a call returns.
+ *   - Sparse matrices are CSR with 64-bit row pointers and 32-bit column indices, the
+ *     FULL symmetric pattern (both triangles), columns sorted within each row, no
+ *     duplicates, indices 0-based.  Dirichlet rows are removed (not replaced by identity).
+ *   - Dense right-hand sides and solutions are column-major n x nrhs (ld = n), FP64.
+ *   - Handles are not thread-safe: one thread (one CUDA stream) per hm_sys_t at a time.
+ */
+#ifndef HODLR_MF_H
+#define HODLR_MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_ctx_s* hm_ctx_t;
+typedef struct hm_sys_s* hm_sys_t;
+
+enum hm_status {
+  HM_OK = 0,
+  HM_ERR_INVALID_ARG = 1,    /* bad size, null pointer, malformed CSR or lattice       */
+  HM_ERR_NOT_SPD = 2,        /* a pivot block was not positive definite (Cholesky)     */
+  HM_ERR_NO_CONVERGENCE = 3, /* GMRES hit max_iters above rtol (x holds the iterate)   */
+  HM_ERR_OUT_OF_MEMORY = 4,  /* device allocation failed or HBM budget exceeded         */
+  HM_ERR_CUDA = 5,           /* a CUDA runtime call failed (see hm_last_error)          */
+  HM_ERR_CAPACITY = 6,       /* a fixed on-chip capacity was exceeded (front too large) */
+  HM_ERR_DEVICE_TIMEOUT = 7, /* a bounded device-side wait gave up                      */
+  HM_ERR_STATE = 8,          /* call out of order (e.g. solve before factor)           */
+  HM_ERR_BREAKDOWN = 9       /* singular Woodbury core / zero pivot in LU               */
+};
+
+enum hm_precision {
+  HM_PREC_FP64 = 0, /* factorization, compression and preconditioner apply in FP64     */
+  HM_PREC_MIXED = 1 /* factorization, compression and apply in FP32; GMRES in FP64     */
+};
+
+typedef struct hm_opts {
+  int device;            /* CUDA device ordinal                                          */
+  int precision;         /* enum hm_precision                                            */
+  int nd_leaf;           /* nested dissection stops at boxes of <= nd_leaf unknowns (64) */
+  int hodlr_leaf;        /* HODLR leaves hold <= hodlr_leaf rows (64)                    */
+  int n_c;               /* fronts whose pivot block has > n_c unknowns become HODLR
+                            fronts; smaller ones stay dense (the paper's n_c)            */
+  int samples;           /* randomized range finder sketch width cap k (>= 1)            */
+  uint64_t seed;         /* seed of the Philox4x32-10 sketch                             */
+  int restart;           /* GMRES restart length m (30)                                  */
+  size_t hbm_budget;     /* bytes the context may allocate on the device; 0 = no limit  */
+  void* stream;          /* cudaStream_t to run on; NULL = a stream the context owns     */
+} hm_opts;
+
+typedef struct hm_solve_info {
+  int32_t iters;         /* GMRES iterations (max over right-hand sides)                 */
+  int32_t restarts;      /* completed restart cycles                                     */
+  double relres;         /* max over right-hand sides of ||b - A x|| / ||b|| (FP64)      */
+  int32_t converged;     /* 1 if every right-hand side reached rtol                      */
+} hm_solve_info;
+
+typedef struct hm_factor_info {
+  int32_t nfronts;       /* elimination-tree nodes                                       */
+  int32_t nlevels;       /* tree depth + 1                                               */
+  int32_t n_hodlr;       /* fronts factored as HODLR fronts                              */
+  int32_t max_rank;      /* largest off-diagonal rank found                              */
+  int32_t rank_capped;   /* blocks whose rank reached their sketch width                 */
+  double factor_bytes;   /* bytes of factor data read by one preconditioner apply        */
+  double front_bytes;    /* bytes of dense front storage                                 */
+} hm_factor_info;
+
+/* Fill *opts with defaults (device 0, mixed precision, nd_leaf 64, hodlr_leaf 64,
+   n_c 64, samples 48, restart 30).  Never fails for a non-null pointer.              */
+int hm_default_opts(hm_opts* opts);
+
+/* Create a context on opts->device.  The context owns a CUDA stream (unless one is
+   given) and the device memory of every system created from it.                     */
+int hm_create(hm_ctx_t* ctx, const hm_opts* opts);
+int hm_ctx_destroy(hm_ctx_t ctx);
+
+/*
+ * Symbolic analysis (Section 4.1.1): nested-dissection ordering, elimination tree,
+ * coupling sets S_p (Eq. couplingSet), frontal index sets I_p^f and the child-to-parent
+ * relative index maps of the extend-add.
+ *
+ *   n, rowptr[n+1], colidx[nnz]   CSR pattern of A (values are given to hm_factor).
+ *   dim, grid_coords[n*dim]       integer lattice coordinates of each unknown (row-major
+ *                                 n x dim, dim 2 or 3); the unknowns must fill their
+ *                                 bounding box.  The ordering is computed on the GPU:
+ *                                 boxes are split along the longest axis (lowest axis on
+ *                                 ties) by the plane (lo+hi)/2, halves first, separator
+ *                                 last, points lexicographic x-fastest, stop at nd_leaf.
+ *   perm_in, nfronts_in, first_in, parent_in
+ *                                 optional user ordering instead of grid_coords: perm_in[n]
+ *                                 maps new -> original index; tree node p (postorder,
+ *                                 children before parents) owns new indices
+ *                                 [first_in[p], first_in[p+1]); parent_in[root] = -1.
+ *                                 Pass NULL / 0 to use grid_coords.
+ *   out                           receives the system handle.
+ * Errors: HM_ERR_INVALID_ARG for a malformed CSR / lattice / tree, HM_ERR_CAPACITY if a
+ * front's candidate index set exceeds the on-chip sort capacity (32768 indices).
+ */
+int hm_analyze(hm_ctx_t ctx, int32_t n, const int64_t* rowptr, const int32_t* colidx,
+               int32_t dim, const int32_t* grid_coords, const int32_t* perm_in,
+               int32_t nfronts_in, const int32_t* first_in, const int32_t* parent_in,
+               hm_sys_t* out);
+
+/* Number of tree nodes and unknowns (either pointer may be NULL).                     */
+int hm_get_sizes(hm_sys_t sys, int32_t* n, int32_t* nfronts);
+
+/* Ordering and tree: perm[n] (new -> original), first[nfronts+1], parent[nfronts],
+   level[nfronts] (depth, root 0).  Host pointers; any may be NULL.                     */
+int hm_get_ordering(hm_sys_t sys, int32_t* perm, int32_t* first, int32_t* parent,
+                    int32_t* level);
+
+/* Symbolic result: nupd[p] = |I_p^f|; if_off[nfronts+1] prefix offsets; if_list[] the
+   sorted new indices of every I_p^f (front p at if_off[p]); relmap[] the position of each
+   entry of I_p^f inside the parent's front [I_parent, I_parent^f] (same offsets; -1
+   at the root).  Host pointers; query total = if_off[nfronts] first with if_list NULL. */
+int hm_get_symbolic(hm_sys_t sys, int32_t* nupd, int64_t* if_off, int32_t* if_list,
+                    int32_t* relmap);
+
+/*
+ * Numerical factorization (Sections 4.1.1 and 4.2.1) of A with the pattern given to
+ * hm_analyze.  values[nnz] are the CSR values (FP64).  tol is the relative truncation
+ * tolerance of the low-rank compression (singular values <= tol * sigma_1 of a block
+ * are dropped); tol <= 0 keeps every sampled direction.  May be called repeatedly with
+ * new values (refactorization).  Errors: HM_ERR_NOT_SPD, HM_ERR_BREAKDOWN, CUDA errors.
+ */
+int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* info);
+
+/*
+ * Solve A X = B by GMRES(restart) preconditioned with the factorization (Section 3):
+ * right preconditioning, flexible form (the preconditioned vectors are stored), FP64
+ * residuals, Arnoldi by classical Gram-Schmidt applied twice, Givens least squares.
+ * b and x are n x nrhs column-major FP64 in the ORIGINAL numbering; x0 = 0.  Stops when
+ * every column reaches ||b - A x|| / ||b|| <= rtol (true residual) or after max_iters.
+ * nrhs <= 64.  Returns HM_ERR_NO_CONVERGENCE (x holds the last iterate) if the cap is hit.
+ */
+int hm_solve(hm_sys_t sys, int32_t nrhs, const double* b, double rtol, int32_t max_iters,
+             double* x, hm_solve_info* info);
+
+/* One preconditioner application z = M^{-1} r (Eqs. upward / downward with the HODLR
+   pivot solves of Section 4.2.2); r, z n x nrhs FP64, original numbering.             */
+int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
+
+/* Inspection for tests: the dense Schur-complement update U_p = F_ff - F_fp F_pp^-1 F_pf
+   of front p as computed by the last hm_factor (nupd[p]^2 entries, column-major, lower
+   triangle valid, FP64).  Host pointer.                                                */
+int hm_get_update(hm_sys_t sys, int32_t front, double* U);
+
+/* Inspection: front kind (0 dense, 1 HODLR) and ranks of the last hm_factor.  ranks
+   receives, for a HODLR front, the rank of F_fp followed by the ranks of the pivot
+   block's off-diagonal blocks level by level (node order); returns the count in *nr. */
+int hm_get_front_ranks(hm_sys_t sys, int32_t front, int32_t* kind, int32_t* ranks,
+                       int32_t* nr);
+
+/* Inspection: the low-rank factors of one compressed block of HODLR front `front` from
+   the last hm_factor.  level = -1 selects the coupling block F_fp ~ W Vf^T (U = W is
+   nupd x k, V = Vf is npiv x k); level >= 0 selects the off-diagonal block of node
+   (level, node) of the pivot block's HODLR tree, F_pp[a, b] ~ U V^T with a / b the rows
+   of its first / second child (U is |a| x k, V is |b| x k).  k is the column capacity;
+   columns at or beyond *rank are zero.  Pass U = V = NULL to query m, n, k, rank.
+   U, V: host, column-major FP64.                                                     */
+int hm_get_hodlr_block(hm_sys_t sys, int32_t front, int32_t level, int32_t node, int32_t* m,
+                       int32_t* n, int32_t* k, int32_t* rank, double* U, double* V);
+
+int hm_destroy(hm_sys_t sys);
+
+const char* hm_status_str(int status);
+const char* hm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HODLR_MF_H */

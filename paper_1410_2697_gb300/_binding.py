@@ -1,0 +1,242 @@
+"""ctypes binding of ``include/hodlr_mf.h`` -- argument marshalling only.
+
+Every function here forwards to the C entry point of the same name in the in-tree
+``libhodlr_mf.so``; all computation happens in its CUDA kernels.  Arrays may be numpy
+arrays (host) or torch CUDA tensors (device); the library detects which.  There is no
+fallback: if the library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhodlr_mf.so")
+
+HM_OK = 0
+HM_ERR_INVALID_ARG = 1
+HM_ERR_NOT_SPD = 2
+HM_ERR_NO_CONVERGENCE = 3
+HM_ERR_OUT_OF_MEMORY = 4
+HM_ERR_CUDA = 5
+HM_ERR_CAPACITY = 6
+HM_ERR_DEVICE_TIMEOUT = 7
+HM_ERR_STATE = 8
+HM_ERR_BREAKDOWN = 9
+HM_PREC_FP64 = 0
+HM_PREC_MIXED = 1
+
+EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_get_sizes",
+            "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_solve", "hm_precond_apply",
+            "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_destroy", "hm_status_str", "hm_last_error"]
+
+
+class HmOpts(C.Structure):
+    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("nd_leaf", C.c_int),
+                ("hodlr_leaf", C.c_int), ("n_c", C.c_int), ("samples", C.c_int),
+                ("seed", C.c_uint64), ("restart", C.c_int), ("hbm_budget", C.c_size_t),
+                ("stream", C.c_void_p)]
+
+
+class HmSolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("relres", C.c_double),
+                ("converged", C.c_int32)]
+
+
+class HmFactorInfo(C.Structure):
+    _fields_ = [("nfronts", C.c_int32), ("nlevels", C.c_int32), ("n_hodlr", C.c_int32),
+                ("max_rank", C.c_int32), ("rank_capped", C.c_int32), ("factor_bytes", C.c_double),
+                ("front_bytes", C.c_double)]
+
+
+class HmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.hm_status_str(status).decode()
+        detail = _lib.hm_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}): {detail}")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1410_2697_gb300.build`"
+                          " (no CPU fallback exists)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.hm_default_opts.argtypes = [C.POINTER(HmOpts)]
+    lib.hm_create.argtypes = [C.POINTER(vp), C.POINTER(HmOpts)]
+    lib.hm_ctx_destroy.argtypes = [vp]
+    lib.hm_analyze.argtypes = [vp, i32, vp, vp, i32, vp, vp, i32, vp, vp, C.POINTER(vp)]
+    lib.hm_get_sizes.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    lib.hm_get_ordering.argtypes = [vp, vp, vp, vp, vp]
+    lib.hm_get_symbolic.argtypes = [vp, vp, vp, vp, vp]
+    lib.hm_factor.argtypes = [vp, vp, dbl, C.POINTER(HmFactorInfo)]
+    lib.hm_solve.argtypes = [vp, i32, vp, dbl, i32, vp, C.POINTER(HmSolveInfo)]
+    lib.hm_precond_apply.argtypes = [vp, i32, vp, vp]
+    lib.hm_get_update.argtypes = [vp, i32, vp]
+    lib.hm_get_front_ranks.argtypes = [vp, i32, C.POINTER(i32), vp, C.POINTER(i32)]
+    lib.hm_get_hodlr_block.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(i32), C.POINTER(i32), vp, vp]
+    lib.hm_destroy.argtypes = [vp]
+    lib.hm_status_str.argtypes = [C.c_int]
+    lib.hm_status_str.restype = C.c_char_p
+    lib.hm_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("hm_status_str", "hm_last_error"):
+            getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int, where: str, ok=(HM_OK,)):
+    if status not in ok:
+        raise HmError(status, where)
+    return status
+
+
+def _ptr(a, dtype, name: str, count: int | None = None):
+    """Pointer of a contiguous numpy array / torch tensor of the given numpy dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype):
+            raise TypeError(f"{name}: expected {np.dtype(dtype)}, got {a.dtype}")
+        if not (a.flags.c_contiguous or a.flags.f_contiguous):
+            raise TypeError(f"{name}: array must be contiguous")
+        if count is not None and a.size < count:
+            raise ValueError(f"{name}: needs {count} elements, has {a.size}")
+        return C.c_void_p(a.ctypes.data)
+    # torch tensor (device or host)
+    tname = {np.float64: "float64", np.int32: "int32", np.int64: "int64"}[np.dtype(dtype).type]
+    if str(a.dtype) != f"torch.{tname}":
+        raise TypeError(f"{name}: expected torch.{tname}, got {a.dtype}")
+    if not a.is_contiguous():
+        raise TypeError(f"{name}: tensor must be contiguous")
+    if count is not None and a.numel() < count:
+        raise ValueError(f"{name}: needs {count} elements, has {a.numel()}")
+    return C.c_void_p(a.data_ptr())
+
+
+def hm_default_opts() -> HmOpts:
+    o = HmOpts()
+    _check(_lib.hm_default_opts(C.byref(o)), "hm_default_opts")
+    return o
+
+
+def hm_create(opts: HmOpts | None = None) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _check(_lib.hm_create(C.byref(ctx), C.byref(opts) if opts is not None else None), "hm_create")
+    return ctx
+
+
+def hm_ctx_destroy(ctx) -> None:
+    _check(_lib.hm_ctx_destroy(ctx), "hm_ctx_destroy")
+
+
+def hm_analyze(ctx, n, rowptr, colidx, dim=0, grid_coords=None, perm_in=None, nfronts_in=0,
+               first_in=None, parent_in=None) -> C.c_void_p:
+    sys_ = C.c_void_p()
+    _check(_lib.hm_analyze(ctx, int(n), _ptr(rowptr, np.int64, "rowptr", n + 1),
+                           _ptr(colidx, np.int32, "colidx"), int(dim),
+                           _ptr(grid_coords, np.int32, "grid_coords"), _ptr(perm_in, np.int32, "perm_in"),
+                           int(nfronts_in), _ptr(first_in, np.int32, "first_in"),
+                           _ptr(parent_in, np.int32, "parent_in"), C.byref(sys_)), "hm_analyze")
+    return sys_
+
+
+def hm_get_sizes(sys_) -> tuple[int, int]:
+    n, nf = C.c_int32(), C.c_int32()
+    _check(_lib.hm_get_sizes(sys_, C.byref(n), C.byref(nf)), "hm_get_sizes")
+    return n.value, nf.value
+
+
+def hm_get_ordering(sys_):
+    n, nf = hm_get_sizes(sys_)
+    perm = np.empty(n, np.int32)
+    first = np.empty(nf + 1, np.int32)
+    parent = np.empty(nf, np.int32)
+    level = np.empty(nf, np.int32)
+    _check(_lib.hm_get_ordering(sys_, _ptr(perm, np.int32, "perm"), _ptr(first, np.int32, "first"),
+                                _ptr(parent, np.int32, "parent"), _ptr(level, np.int32, "level")),
+           "hm_get_ordering")
+    return perm, first, parent, level
+
+
+def hm_get_symbolic(sys_):
+    _, nf = hm_get_sizes(sys_)
+    nupd = np.empty(nf, np.int32)
+    off = np.empty(nf + 1, np.int64)
+    _check(_lib.hm_get_symbolic(sys_, _ptr(nupd, np.int32, "nupd"), _ptr(off, np.int64, "if_off"),
+                                None, None), "hm_get_symbolic")
+    total = int(off[-1])
+    lst = np.empty(max(total, 1), np.int32)
+    rel = np.empty(max(total, 1), np.int32)
+    _check(_lib.hm_get_symbolic(sys_, None, None, _ptr(lst, np.int32, "if_list"),
+                                _ptr(rel, np.int32, "relmap")), "hm_get_symbolic")
+    return nupd, off, lst[:total], rel[:total]
+
+
+def hm_factor(sys_, values, tol: float) -> dict:
+    info = HmFactorInfo()
+    _check(_lib.hm_factor(sys_, _ptr(values, np.float64, "values"), float(tol), C.byref(info)),
+           "hm_factor")
+    return {f: getattr(info, f) for f, _ in HmFactorInfo._fields_}
+
+
+def hm_solve(sys_, nrhs: int, b, rtol: float, max_iters: int, x, raise_on_no_convergence=True) -> dict:
+    info = HmSolveInfo()
+    st = _lib.hm_solve(sys_, int(nrhs), _ptr(b, np.float64, "b"), float(rtol), int(max_iters),
+                       _ptr(x, np.float64, "x"), C.byref(info))
+    ok = (HM_OK,) if raise_on_no_convergence else (HM_OK, HM_ERR_NO_CONVERGENCE)
+    _check(st, "hm_solve", ok)
+    return {f: getattr(info, f) for f, _ in HmSolveInfo._fields_}
+
+
+def hm_precond_apply(sys_, nrhs: int, r, z) -> None:
+    _check(_lib.hm_precond_apply(sys_, int(nrhs), _ptr(r, np.float64, "r"), _ptr(z, np.float64, "z")),
+           "hm_precond_apply")
+
+
+def hm_get_update(sys_, front: int, nupd: int) -> np.ndarray:
+    U = np.zeros((nupd, nupd), dtype=np.float64, order="F")
+    _check(_lib.hm_get_update(sys_, int(front), _ptr(U, np.float64, "U")), "hm_get_update")
+    return U
+
+
+def hm_get_front_ranks(sys_, front: int):
+    kind, nr = C.c_int32(), C.c_int32()
+    _check(_lib.hm_get_front_ranks(sys_, int(front), C.byref(kind), None, C.byref(nr)),
+           "hm_get_front_ranks")
+    r = np.zeros(max(nr.value, 1), np.int32)
+    _check(_lib.hm_get_front_ranks(sys_, int(front), C.byref(kind), _ptr(r, np.int32, "ranks"),
+                                   C.byref(nr)), "hm_get_front_ranks")
+    return kind.value, r[:nr.value]
+
+
+def hm_get_hodlr_block(sys_, front: int, level: int, node: int = 0):
+    """Returns ``(U, V, rank)`` of a compressed block (level -1: F_fp ~ W Vf^T)."""
+    m, n, k, r = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib.hm_get_hodlr_block(sys_, int(front), int(level), int(node), C.byref(m), C.byref(n),
+                                   C.byref(k), C.byref(r), None, None), "hm_get_hodlr_block")
+    U = np.zeros((m.value, k.value), np.float64, order="F")
+    V = np.zeros((n.value, k.value), np.float64, order="F")
+    _check(_lib.hm_get_hodlr_block(sys_, int(front), int(level), int(node), C.byref(m), C.byref(n),
+                                   C.byref(k), C.byref(r), _ptr(U, np.float64, "U"),
+                                   _ptr(V, np.float64, "V")), "hm_get_hodlr_block")
+    return U, V, r.value
+
+
+def hm_destroy(sys_) -> None:
+    _check(_lib.hm_destroy(sys_), "hm_destroy")
+
+
+def hm_status_str(status: int) -> str:
+    return _lib.hm_status_str(int(status)).decode()
+
+
+def hm_last_error() -> str:
+    return _lib.hm_last_error().decode()

@@ -1,0 +1,760 @@
+// hm_analyze.cu -- symbolic analysis on the GPU (Section 4.1.1 of the paper):
+// nested-dissection ordering and elimination tree, coupling sets S_p (Eq. couplingSet),
+// frontal index sets I_p^f and the child-to-parent relative index maps.
+#include <algorithm>
+#include <climits>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+// ------------------------------------------------------------------------------------
+// Validation of the CSR pattern: monotone row pointers, columns in range, strictly
+// increasing within a row.
+// ------------------------------------------------------------------------------------
+__global__ void k_csr_check(const int64_t* rowptr, const int32_t* colidx, int n, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = rowptr[i], e = rowptr[i + 1];
+  if (e < b) { raise_error(err, HM_ERR_INVALID_ARG, 1, i); return; }
+  int prev = -1;
+  for (int64_t k = b; k < e; ++k) {
+    const int c = colidx[k];
+    if (c < 0 || c >= n || c <= prev) { raise_error(err, HM_ERR_INVALID_ARG, 2, i); return; }
+    prev = c;
+  }
+}
+
+__global__ void k_bbox(const int32_t* coords, int n, int dim, int* bb) {
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int d = 0; d < dim; ++d) {
+      const int v = coords[(size_t)i * dim + d];
+      lo[d] = min(lo[d], v);
+      hi[d] = max(hi[d], v);
+    }
+  for (int d = 0; d < dim; ++d) {
+    lo[d] = -warp_max(-lo[d]);
+    hi[d] = warp_max(hi[d]);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&bb[d], lo[d]);
+      atomicMax(&bb[3 + d], hi[d]);
+    }
+  }
+}
+
+// Every lattice point of the bounding box must hold exactly one unknown.
+__global__ void k_lattice_mark(const int32_t* coords, int n, int dim, int3 lo, int3 ext,
+                               unsigned* bitmap, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int x = coords[(size_t)i * dim] - lo.x;
+  const int y = dim > 1 ? coords[(size_t)i * dim + 1] - lo.y : 0;
+  const int z = dim > 2 ? coords[(size_t)i * dim + 2] - lo.z : 0;
+  const int64_t lin = (int64_t)x + (int64_t)ext.x * ((int64_t)y + (int64_t)ext.y * z);
+  const unsigned bit = 1u << (lin & 31);
+  if (atomicOr(&bitmap[lin >> 5], bit) & bit) raise_error(err, HM_ERR_INVALID_ARG, 3, i);
+}
+
+// ------------------------------------------------------------------------------------
+// Nested-dissection box tree, built by one CTA level by level (breadth first).
+// Rule: leaf if the box holds <= leaf points or its longest extent is < 3; otherwise
+// split the longest axis (lowest axis on ties) at mid = (lo + hi) / 2; the lower half,
+// the upper half and then the separator plane are numbered; points within a box or a
+// separator lexicographically (x fastest); tree nodes in postorder.
+// ------------------------------------------------------------------------------------
+struct NdTree {
+  int* lo;      // 3 per node
+  int* hi;      // 3 per node
+  int* axis;    // -1 for a leaf
+  int* mid;
+  int* left;
+  int* right;
+  int* par;
+  int* depth;
+  int* sub;     // nodes in subtree
+  int* post;    // postorder id
+  int* own;     // first new index of the node's own unknowns
+  int* pts;     // first new index of the subtree's unknowns
+  int* lvl_ptr; // BFS level boundaries (<= 64 levels)
+  int* count;   // [0] nodes, [1] levels
+};
+
+__device__ __forceinline__ int64_t box_count(const int* lo, const int* hi, int dim) {
+  int64_t c = 1;
+  for (int d = 0; d < dim; ++d) c *= (int64_t)(hi[d] - lo[d] + 1);
+  return c;
+}
+
+__device__ int block_excl_scan(int v, int* total, int* sh) {
+  // sh: >= 33 ints; blockDim.x multiple of 32, <= 1024
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sh[lane] = s;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = wid > 0 ? sh[wid - 1] : 0;
+  *total = sh[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_nd_tree(NdTree t, int dim, int3 ext, int leaf, int cap,
+                                                  int* first, int* parent, int* level, int* err) {
+  __shared__ int sh[40];
+  __shared__ int s_nodes, s_lb, s_le, s_nlev;
+  if (threadIdx.x == 0) {
+    const int e[3] = {ext.x, ext.y, ext.z};
+    for (int d = 0; d < 3; ++d) { t.lo[d] = 0; t.hi[d] = d < dim ? e[d] - 1 : 0; }
+    t.par[0] = -1;
+    t.depth[0] = 0;
+    s_nodes = 1; s_lb = 0; s_le = 1; s_nlev = 0;
+    t.lvl_ptr[0] = 0;
+  }
+  __syncthreads();
+  // breadth-first expansion
+  while (true) {
+    const int lb = s_lb, le = s_le;
+    if (lb >= le) break;
+    for (int base = lb; base < le; base += blockDim.x) {
+      const int v = base + threadIdx.x;
+      int split = 0, ax = -1;
+      if (v < le) {
+        const int* lo = t.lo + 3 * v;
+        const int* hi = t.hi + 3 * v;
+        int longest = 0;
+        for (int d = 0; d < dim; ++d) {
+          const int e = hi[d] - lo[d] + 1;
+          if (e > longest) { longest = e; ax = d; }
+        }
+        const int64_t cnt = box_count(lo, hi, dim);
+        split = (cnt > leaf && longest >= 3) ? 1 : 0;
+        if (!split) ax = -1;
+      }
+      int total;
+      const int pre = block_excl_scan(split, &total, sh);
+      const int nodes0 = s_nodes;
+      if (v < le) {
+        t.axis[v] = ax;
+        if (split) {
+          const int l = nodes0 + 2 * pre, r = l + 1;
+          if (r >= cap) { raise_error(err, HM_ERR_CAPACITY, 10, v); }
+          else {
+            const int* lo = t.lo + 3 * v;
+            const int* hi = t.hi + 3 * v;
+            const int m = (lo[ax] + hi[ax]) / 2;
+            t.mid[v] = m;
+            for (int d = 0; d < 3; ++d) {
+              t.lo[3 * l + d] = lo[d]; t.hi[3 * l + d] = hi[d];
+              t.lo[3 * r + d] = lo[d]; t.hi[3 * r + d] = hi[d];
+            }
+            t.hi[3 * l + ax] = m - 1;
+            t.lo[3 * r + ax] = m + 1;
+            t.par[l] = v; t.par[r] = v;
+            t.depth[l] = t.depth[v] + 1; t.depth[r] = t.depth[v] + 1;
+            t.left[v] = l; t.right[v] = r;
+          }
+        } else {
+          t.left[v] = -1; t.right[v] = -1; t.mid[v] = 0;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_nodes = nodes0 + 2 * total;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      s_nlev += 1;
+      t.lvl_ptr[s_nlev] = le;
+      s_lb = le;
+      s_le = s_nodes;
+      if (s_nlev >= 63 && s_le > s_lb) { raise_error(err, HM_ERR_CAPACITY, 11, 0); s_le = s_lb; }
+    }
+    __syncthreads();
+  }
+  const int nnodes = s_nodes, nlev = s_nlev;
+  // bottom-up subtree sizes
+  for (int L = nlev - 1; L >= 0; --L) {
+    for (int v = t.lvl_ptr[L] + threadIdx.x; v < t.lvl_ptr[L + 1]; v += blockDim.x)
+      t.sub[v] = t.axis[v] < 0 ? 1 : 1 + t.sub[t.left[v]] + t.sub[t.right[v]];
+    __syncthreads();
+  }
+  // top-down postorder ids and unknown offsets: post[] temporarily holds post_start
+  if (threadIdx.x == 0) { t.post[0] = 0; t.pts[0] = 0; }
+  __syncthreads();
+  for (int L = 0; L < nlev; ++L) {
+    for (int v = t.lvl_ptr[L] + threadIdx.x; v < t.lvl_ptr[L + 1]; v += blockDim.x) {
+      const int ps = t.post[v], pt = t.pts[v];
+      if (t.axis[v] >= 0) {
+        const int l = t.left[v], r = t.right[v];
+        t.post[l] = ps;
+        t.post[r] = ps + t.sub[l];
+        t.pts[l] = pt;
+        const int64_t cl = box_count(t.lo + 3 * l, t.hi + 3 * l, dim);
+        const int64_t cr = box_count(t.lo + 3 * r, t.hi + 3 * r, dim);
+        t.pts[r] = pt + (int)cl;
+        t.own[v] = pt + (int)(cl + cr);
+      } else {
+        t.own[v] = pt;
+      }
+    }
+    __syncthreads();
+  }
+  for (int v = threadIdx.x; v < nnodes; v += blockDim.x) t.post[v] = t.post[v] + t.sub[v] - 1;
+  __syncthreads();
+  for (int v = threadIdx.x; v < nnodes; v += blockDim.x) {
+    const int q = t.post[v];
+    first[q] = t.own[v];
+    parent[q] = t.par[v] >= 0 ? t.post[t.par[v]] : -1;
+    level[q] = t.depth[v];
+  }
+  if (threadIdx.x == 0) {
+    t.count[0] = nnodes;
+    t.count[1] = nlev;
+  }
+}
+
+// New index of every unknown: descend the box tree to the node that owns it.
+__global__ void k_nd_perm(const int32_t* coords, int n, int dim, int3 lo0, NdTree t,
+                          int32_t* perm, int32_t* iperm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3] = {0, 0, 0};
+  c[0] = coords[(size_t)i * dim] - lo0.x;
+  if (dim > 1) c[1] = coords[(size_t)i * dim + 1] - lo0.y;
+  if (dim > 2) c[2] = coords[(size_t)i * dim + 2] - lo0.z;
+  int v = 0;
+  for (int guard = 0; guard < 64; ++guard) {
+    const int ax = t.axis[v];
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) { blo[d] = t.lo[3 * v + d]; bhi[d] = t.hi[3 * v + d]; }
+    bool here = ax < 0;
+    if (!here) {
+      const int m = t.mid[v];
+      if (c[ax] < m) { v = t.left[v]; continue; }
+      if (c[ax] > m) { v = t.right[v]; continue; }
+      blo[ax] = m; bhi[ax] = m;
+      here = true;
+    }
+    const int e0 = bhi[0] - blo[0] + 1, e1 = bhi[1] - blo[1] + 1;
+    const int rank = (c[0] - blo[0]) + e0 * ((c[1] - blo[1]) + e1 * (c[2] - blo[2]));
+    const int nw = t.own[v] + rank;
+    perm[nw] = i;
+    iperm[i] = nw;
+    return;
+  }
+}
+
+__global__ void k_iperm(const int32_t* perm, int n, int32_t* iperm, unsigned* bitmap, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = perm[i];
+  if (o < 0 || o >= n) { raise_error(err, HM_ERR_INVALID_ARG, 4, i); return; }
+  const unsigned bit = 1u << (o & 31);
+  if (atomicOr(&bitmap[o >> 5], bit) & bit) { raise_error(err, HM_ERR_INVALID_ARG, 5, i); return; }
+  iperm[o] = i;
+}
+
+__global__ void k_node_of(const int32_t* first, int nf, int n, int32_t* node_of) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = nf;  // largest q with first[q] <= i
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (first[m] <= i) lo = m; else hi = m;
+  }
+  node_of[i] = lo;
+}
+
+// ------------------------------------------------------------------------------------
+// Permuted CSR (new numbering), rows sorted; psrc keeps the original entry index.
+// ------------------------------------------------------------------------------------
+__global__ void k_prow_len(const int64_t* rowptr, const int32_t* perm, int n, int64_t* len) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = perm[i];
+  len[i] = rowptr[o + 1] - rowptr[o];
+}
+
+__global__ void k_scan_local(const int64_t* in, int64_t* out, int64_t* bsum, int n) {
+  // 256 threads x 4 items, exclusive scan within the block
+  __shared__ int64_t sh[256];
+  const int base = blockIdx.x * 1024;
+  int64_t v[4], s = 0;
+  for (int q = 0; q < 4; ++q) {
+    const int i = base + threadIdx.x * 4 + q;
+    v[q] = i < n ? in[i] : 0;
+    s += v[q];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int64_t y = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += y;
+    __syncthreads();
+  }
+  int64_t run = sh[threadIdx.x] - s;
+  for (int q = 0; q < 4; ++q) {
+    const int i = base + threadIdx.x * 4 + q;
+    if (i < n) out[i] = run;
+    run += v[q];
+  }
+  if (threadIdx.x == 255) bsum[blockIdx.x] = sh[255];
+}
+
+__global__ void k_scan_sums(int64_t* bsum, int nb, int64_t* total) {
+  if (threadIdx.x != 0) return;
+  int64_t run = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int64_t v = bsum[b];
+    bsum[b] = run;
+    run += v;
+  }
+  *total = run;
+}
+
+__global__ void k_scan_add(int64_t* out, const int64_t* bsum, int n) {
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  for (int q = 0; q < 4; ++q) {
+    const int j = i + q * 256;
+    if (j < n) out[j] += bsum[blockIdx.x];
+  }
+}
+
+// out[0..n] exclusive scan of in[0..n-1]; out[n] = total.  tmp holds ceil(n/1024) entries.
+static void exclusive_scan(const int64_t* in, int64_t* out, int64_t* tmp, int n, cudaStream_t s) {
+  const int nb = (n + 1023) / 1024;
+  k_scan_local<<<nb, 256, 0, s>>>(in, out, tmp, n);
+  k_scan_sums<<<1, 32, 0, s>>>(tmp, nb, out + n);
+  k_scan_add<<<nb, 256, 0, s>>>(out, tmp, n);
+}
+
+__global__ void k_prow_fill(const int64_t* rowptr, const int32_t* colidx, const int32_t* perm,
+                            const int32_t* iperm, const int64_t* prowptr, int n, int32_t* pcol,
+                            int64_t* psrc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = perm[i];
+  const int64_t b = rowptr[o], e = rowptr[o + 1], pb = prowptr[i];
+  for (int64_t k = b; k < e; ++k) {
+    const int j = iperm[colidx[k]];
+    int64_t pos = pb + (k - b);
+    // insertion into the sorted prefix
+    while (pos > pb && pcol[pos - 1] > j) {
+      pcol[pos] = pcol[pos - 1];
+      psrc[pos] = psrc[pos - 1];
+      --pos;
+    }
+    pcol[pos] = j;
+    psrc[pos] = k;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Frontal index sets of the fronts of one tree level (one CTA per front):
+// I_p^f = sorted unique( S_p  U  (U_c I_c^f) ) restricted to indices after I_p, where
+// S_p are the graph neighbours of I_p numbered after I_p (Eq. couplingSet).
+// Candidates are gathered in shared memory, bitonic-sorted and de-duplicated; the list
+// is appended to the I^f arena at an atomically claimed offset.
+// ------------------------------------------------------------------------------------
+constexpr int kSymCap = 32768;
+
+__global__ void __launch_bounds__(1024) k_symbolic_level(
+    const int* fronts, const int32_t* first, const int32_t* child_ptr, const int32_t* child_list,
+    const int64_t* prowptr, const int32_t* pcol, int32_t* nupd, int64_t* ifoff, int32_t* iflist,
+    unsigned long long* cursor, int64_t capacity, int* err) {
+  extern __shared__ int buf[];
+  __shared__ int cnt;
+  __shared__ int sh[40];
+  __shared__ long long s_off;
+  const int q = fronts[blockIdx.x];
+  const int b = first[q], e = first[q + 1];
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  // S_p candidates
+  for (int r = b + (threadIdx.x >> 5); r < e; r += (blockDim.x >> 5)) {
+    const int64_t rb = prowptr[r], re = prowptr[r + 1];
+    for (int64_t k = rb + (threadIdx.x & 31); k < re; k += 32) {
+      const int j = pcol[k];
+      if (j >= e) {
+        const int pos = atomicAdd(&cnt, 1);
+        if (pos < kSymCap) buf[pos] = j;
+      }
+    }
+  }
+  // children's update index sets
+  for (int c = child_ptr[q]; c < child_ptr[q + 1]; ++c) {
+    const int ch = child_list[c];
+    const int64_t o = ifoff[ch];
+    const int nc = nupd[ch];
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+      const int j = iflist[o + t];
+      if (j >= e) {
+        const int pos = atomicAdd(&cnt, 1);
+        if (pos < kSymCap) buf[pos] = j;
+      }
+    }
+  }
+  __syncthreads();
+  const int total = cnt;
+  if (total > kSymCap) {
+    if (threadIdx.x == 0) raise_error(err, HM_ERR_CAPACITY, q, total);
+    return;
+  }
+  int n2 = 1;
+  while (n2 < total) n2 <<= 1;
+  for (int t = total + threadIdx.x; t < n2; t += blockDim.x) buf[t] = INT_MAX;
+  __syncthreads();
+  // bitonic sort ascending
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
+        const int lo = 2 * stride * (t / stride) + (t % stride);
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const int a = buf[lo], c = buf[hi];
+        if ((a > c) == up) { buf[lo] = c; buf[hi] = a; }
+      }
+      __syncthreads();
+    }
+  }
+  // unique: each thread handles a contiguous chunk
+  const int per = (n2 + blockDim.x - 1) / blockDim.x;
+  const int t0 = threadIdx.x * per;
+  int mine = 0;
+  for (int t = t0; t < min(t0 + per, n2); ++t) {
+    const int v = buf[t];
+    if (v != INT_MAX && (t == 0 || buf[t - 1] != v)) ++mine;
+  }
+  int uniq;
+  const int pre = block_excl_scan(mine, &uniq, sh);
+  if (threadIdx.x == 0) {
+    const unsigned long long off = atomicAdd(cursor, (unsigned long long)uniq);
+    if ((int64_t)(off + uniq) > capacity) {
+      raise_error(err, HM_ERR_CAPACITY, -1, q);
+      s_off = -1;
+    } else {
+      s_off = (long long)off;
+    }
+    nupd[q] = uniq;
+    ifoff[q] = (int64_t)off;
+  }
+  __syncthreads();
+  if (s_off < 0) return;
+  int w = pre;
+  for (int t = t0; t < min(t0 + per, n2); ++t) {
+    const int v = buf[t];
+    if (v != INT_MAX && (t == 0 || buf[t - 1] != v)) iflist[s_off + w++] = v;
+  }
+}
+
+// Position of each entry of I_c^f inside the parent's front [I_p ; I_p^f].
+__global__ void k_relmap(const int32_t* parent, const int32_t* first, const int32_t* nupd,
+                         const int64_t* ifoff, const int32_t* iflist, int nf, int32_t* relmap,
+                         int* err) {
+  const int c = blockIdx.x;
+  if (c >= nf) return;
+  const int p = parent[c];
+  const int64_t oc = ifoff[c];
+  const int nc = nupd[c];
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    const int v = iflist[oc + t];
+    if (p < 0) { relmap[oc + t] = -1; continue; }
+    const int b = first[p], e = first[p + 1];
+    int pos;
+    if (v < e) {
+      pos = v - b;
+      if (v < b) raise_error(err, HM_ERR_INVALID_ARG, 20, c);
+    } else {
+      const int32_t* L = iflist + ifoff[p];
+      int lo = 0, hi = nupd[p];
+      while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (L[m] < v) lo = m + 1; else hi = m;
+      }
+      if (lo >= nupd[p] || L[lo] != v) raise_error(err, HM_ERR_INVALID_ARG, 21, c);
+      pos = (e - b) + lo;
+    }
+    relmap[oc + t] = pos;
+  }
+}
+
+// Destination (element offset in the front arena) of every lower-triangle entry of the
+// permuted matrix: entry (i, j), i >= j, belongs to the front owning column j (Eq. fbar);
+// -1 for upper-triangle entries.
+__global__ void k_amap(const int64_t* prowptr, const int32_t* pcol, const int32_t* node_of,
+                       const int32_t* first, const int32_t* nupd, const int64_t* ifoff,
+                       const int32_t* iflist, const int64_t* front_off, const int* nhat, int n,
+                       int64_t* amap, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t k = prowptr[i]; k < prowptr[i + 1]; ++k) {
+    const int j = pcol[k];
+    if (j > i) { amap[k] = -1; continue; }
+    const int q = node_of[j];
+    const int b = first[q], e = first[q + 1];
+    const int lc = j - b;
+    int lr;
+    if (i < e) {
+      lr = i - b;
+    } else {
+      const int32_t* L = iflist + ifoff[q];
+      int lo = 0, hi = nupd[q];
+      while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (L[m] < i) lo = m + 1; else hi = m;
+      }
+      if (lo >= nupd[q] || L[lo] != i) { raise_error(err, HM_ERR_INVALID_ARG, 30, i); amap[k] = -1; continue; }
+      lr = (e - b) + lo;
+    }
+    amap[k] = front_off[q] + (int64_t)lr + (int64_t)lc * nhat[q];
+  }
+}
+
+void launch_amap(hm_sys_s* sys) {
+  const int n = sys->n;
+  k_amap<<<(n + 255) / 256, 256, 0, sys->ctx->stream>>>(
+      sys->d_prowptr, sys->d_pcol, sys->d_node_of, sys->d_first, sys->d_nupd, sys->d_ifoff,
+      sys->d_iflist, sys->plan.d_front_off, sys->plan.d_nhat, n, sys->d_amap, sys->d_err);
+}
+
+// ------------------------------------------------------------------------------------
+// Host driver of the symbolic analysis.
+// ------------------------------------------------------------------------------------
+static int tmp_alloc(hm_sys_s* sys, std::vector<void*>* tmp, void** p, size_t bytes) {
+  return dev_alloc_ctx(sys->ctx, tmp, p, bytes);
+}
+
+int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, int dim,
+                 const int32_t* coords, const int32_t* perm_in, int nfronts_in,
+                 const int32_t* first_in, const int32_t* parent_in) {
+  cudaStream_t s = sys->ctx->stream;
+  const int n = sys->n;
+  std::vector<void*> tmp;
+  struct Guard {
+    hm_ctx_s* ctx;
+    std::vector<void*>* t;
+    ~Guard() { dev_free_all(ctx, t); }
+  } guard{sys->ctx, &tmp};
+
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_err, 4 * sizeof(int)));
+  HM_CUDA(cudaMemsetAsync(sys->d_err, 0, 4 * sizeof(int), s));
+  // pattern
+  int64_t ends[2];
+  HM_TRY(copy_in(sys, ends, rowptr, sizeof(int64_t)));
+  HM_TRY(copy_in(sys, ends + 1, rowptr + n, sizeof(int64_t)));
+  if (ends[0] != 0 || ends[1] < n) { set_last_error("rowptr[0] must be 0 and nnz >= n"); return HM_ERR_INVALID_ARG; }
+  sys->nnz = ends[1];
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_rowptr, sizeof(int64_t) * (n + 1)));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_colidx, sizeof(int32_t) * sys->nnz));
+  HM_CUDA(cudaMemcpyAsync(sys->d_rowptr, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, s));
+  HM_CUDA(cudaMemcpyAsync(sys->d_colidx, colidx, sizeof(int32_t) * sys->nnz, cudaMemcpyDefault, s));
+  k_csr_check<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_colidx, n, sys->d_err);
+  HM_TRY(check_device_error(sys, "analyze: CSR check"));
+
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_perm, sizeof(int32_t) * n));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_iperm, sizeof(int32_t) * n));
+  unsigned* bitmap = nullptr;
+  HM_TRY(tmp_alloc(sys, &tmp, (void**)&bitmap, sizeof(unsigned) * ((size_t)n / 32 + 1)));
+  HM_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(unsigned) * ((size_t)n / 32 + 1), s));
+  int nf = 0;
+  if (perm_in == nullptr) {
+    if (coords == nullptr || dim < 2 || dim > 3) {
+      set_last_error("grid_coords (dim 2 or 3) or a user ordering is required");
+      return HM_ERR_INVALID_ARG;
+    }
+    sys->dim = dim;
+    int32_t* d_coords = nullptr;
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_coords, sizeof(int32_t) * (size_t)n * dim));
+    HM_CUDA(cudaMemcpyAsync(d_coords, coords, sizeof(int32_t) * (size_t)n * dim, cudaMemcpyDefault, s));
+    int* d_bb = nullptr;
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_bb, 6 * sizeof(int)));
+    int hbb[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    HM_CUDA(cudaMemcpyAsync(d_bb, hbb, sizeof(hbb), cudaMemcpyHostToDevice, s));
+    k_bbox<<<std::min((n + 255) / 256, 1024), 256, 0, s>>>(d_coords, n, dim, d_bb);
+    HM_CUDA(cudaMemcpyAsync(hbb, d_bb, sizeof(hbb), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    int ext[3] = {1, 1, 1};
+    int64_t cnt = 1;
+    for (int d = 0; d < dim; ++d) { ext[d] = hbb[3 + d] - hbb[d] + 1; cnt *= ext[d]; }
+    if (cnt != n) { set_last_error("grid_coords must fill their bounding box exactly"); return HM_ERR_INVALID_ARG; }
+    const int3 lo0 = make_int3(hbb[0], dim > 1 ? hbb[1] : 0, dim > 2 ? hbb[2] : 0);
+    const int3 e3 = make_int3(ext[0], ext[1], ext[2]);
+    k_lattice_mark<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, lo0, e3, bitmap, sys->d_err);
+    HM_TRY(check_device_error(sys, "analyze: lattice check"));
+    // tree
+    const int cap = n + 1;
+    NdTree t;
+    int* tree = nullptr;
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&tree, sizeof(int) * ((size_t)cap * 16 + 80)));
+    t.lo = tree;
+    t.hi = tree + 3 * (size_t)cap;
+    t.axis = tree + 6 * (size_t)cap;
+    t.mid = tree + 7 * (size_t)cap;
+    t.left = tree + 8 * (size_t)cap;
+    t.right = tree + 9 * (size_t)cap;
+    t.par = tree + 10 * (size_t)cap;
+    t.depth = tree + 11 * (size_t)cap;
+    t.sub = tree + 12 * (size_t)cap;
+    t.post = tree + 13 * (size_t)cap;
+    t.own = tree + 14 * (size_t)cap;
+    t.pts = tree + 15 * (size_t)cap;
+    t.lvl_ptr = tree + 16 * (size_t)cap;
+    t.count = tree + 16 * (size_t)cap + 70;
+    int *d_first_t = nullptr, *d_parent_t = nullptr, *d_level_t = nullptr;
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_first_t, sizeof(int) * (cap + 1)));
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_parent_t, sizeof(int) * cap));
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_level_t, sizeof(int) * cap));
+    k_nd_tree<<<1, 1024, 0, s>>>(t, dim, e3, sys->ctx->opts.nd_leaf, cap, d_first_t, d_parent_t,
+                                 d_level_t, sys->d_err);
+    int cnts[2];
+    HM_CUDA(cudaMemcpyAsync(cnts, t.count, sizeof(cnts), cudaMemcpyDeviceToHost, s));
+    HM_TRY(check_device_error(sys, "analyze: nested dissection"));
+    nf = cnts[0];
+    k_nd_perm<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, lo0, t, sys->d_perm, sys->d_iperm);
+    sys->h_first.resize(nf + 1);
+    sys->h_parent.resize(nf);
+    sys->h_level.resize(nf);
+    HM_CUDA(cudaMemcpyAsync(sys->h_first.data(), d_first_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(sys->h_parent.data(), d_parent_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(sys->h_level.data(), d_level_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
+    HM_TRY(check_device_error(sys, "analyze: permutation"));
+    sys->h_first[nf] = n;
+  } else {
+    nf = nfronts_in;
+    if (nf <= 0 || first_in == nullptr || parent_in == nullptr) {
+      set_last_error("user ordering needs nfronts, first and parent");
+      return HM_ERR_INVALID_ARG;
+    }
+    HM_CUDA(cudaMemcpyAsync(sys->d_perm, perm_in, sizeof(int32_t) * n, cudaMemcpyDefault, s));
+    k_iperm<<<(n + 255) / 256, 256, 0, s>>>(sys->d_perm, n, sys->d_iperm, bitmap, sys->d_err);
+    sys->h_first.resize(nf + 1);
+    sys->h_parent.resize(nf);
+    HM_TRY(copy_in(sys, sys->h_first.data(), first_in, sizeof(int32_t) * (nf + 1)));
+    HM_TRY(copy_in(sys, sys->h_parent.data(), parent_in, sizeof(int32_t) * nf));
+    HM_TRY(check_device_error(sys, "analyze: user permutation"));
+    if (sys->h_first[0] != 0 || sys->h_first[nf] != n) { set_last_error("first[0] = 0, first[nf] = n required"); return HM_ERR_INVALID_ARG; }
+    for (int q = 0; q < nf; ++q) {
+      if (sys->h_first[q + 1] <= sys->h_first[q]) { set_last_error("every tree node needs >= 1 unknown"); return HM_ERR_INVALID_ARG; }
+      const int p = sys->h_parent[q];
+      if ((q == nf - 1) != (p < 0) || (p >= 0 && (p <= q || p >= nf))) {
+        set_last_error("parent[] must be a postorder tree with the root last");
+        return HM_ERR_INVALID_ARG;
+      }
+    }
+    sys->h_level.assign(nf, 0);
+    for (int q = nf - 2; q >= 0; --q) sys->h_level[q] = sys->h_level[sys->h_parent[q]] + 1;
+  }
+  sys->nf = nf;
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_first, sizeof(int32_t) * (nf + 1)));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_parent, sizeof(int32_t) * nf));
+  HM_CUDA(cudaMemcpyAsync(sys->d_first, sys->h_first.data(), sizeof(int32_t) * (nf + 1), cudaMemcpyHostToDevice, s));
+  HM_CUDA(cudaMemcpyAsync(sys->d_parent, sys->h_parent.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, s));
+  // children (ascending) on host and device
+  sys->h_children.assign(nf, {});
+  for (int q = 0; q < nf; ++q)
+    if (sys->h_parent[q] >= 0) sys->h_children[sys->h_parent[q]].push_back(q);
+  std::vector<int32_t> cptr(nf + 1, 0), clist;
+  for (int q = 0; q < nf; ++q) {
+    cptr[q + 1] = cptr[q] + (int)sys->h_children[q].size();
+    for (int c : sys->h_children[q]) clist.push_back(c);
+  }
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_child_ptr, sizeof(int32_t) * (nf + 1)));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_child_list, sizeof(int32_t) * std::max<size_t>(clist.size(), 1)));
+  HM_CUDA(cudaMemcpyAsync(sys->d_child_ptr, cptr.data(), sizeof(int32_t) * (nf + 1), cudaMemcpyHostToDevice, s));
+  if (!clist.empty())
+    HM_CUDA(cudaMemcpyAsync(sys->d_child_list, clist.data(), sizeof(int32_t) * clist.size(), cudaMemcpyHostToDevice, s));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_node_of, sizeof(int32_t) * n));
+  k_node_of<<<(n + 255) / 256, 256, 0, s>>>(sys->d_first, nf, n, sys->d_node_of);
+  // permuted CSR
+  int64_t* len = nullptr;
+  int64_t* bs = nullptr;
+  HM_TRY(tmp_alloc(sys, &tmp, (void**)&len, sizeof(int64_t) * n));
+  HM_TRY(tmp_alloc(sys, &tmp, (void**)&bs, sizeof(int64_t) * ((size_t)n / 1024 + 2)));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_prowptr, sizeof(int64_t) * (n + 1)));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_pcol, sizeof(int32_t) * sys->nnz));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_psrc, sizeof(int64_t) * sys->nnz));
+  k_prow_len<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_perm, n, len);
+  exclusive_scan(len, sys->d_prowptr, bs, n, s);
+  k_prow_fill<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_colidx, sys->d_perm, sys->d_iperm,
+                                              sys->d_prowptr, n, sys->d_pcol, sys->d_psrc);
+  // symbolic, level by level (deepest first)
+  int maxlev = 0;
+  for (int q = 0; q < nf; ++q) maxlev = std::max(maxlev, sys->h_level[q]);
+  std::vector<int> order;
+  std::vector<int> lvl_begin(maxlev + 2, 0);
+  {
+    std::vector<std::vector<int>> by(maxlev + 1);
+    for (int q = 0; q < nf; ++q) by[sys->h_level[q]].push_back(q);
+    for (int l = maxlev; l >= 0; --l) {
+      lvl_begin[maxlev - l] = (int)order.size();
+      for (int q : by[l]) order.push_back(q);
+    }
+    lvl_begin[maxlev + 1] = (int)order.size();
+  }
+  int* d_order = nullptr;
+  HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_order, sizeof(int) * order.size()));
+  HM_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_nupd, sizeof(int32_t) * nf));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_ifoff, sizeof(int64_t) * (nf + 1)));
+  unsigned long long* cursor = nullptr;
+  HM_TRY(tmp_alloc(sys, &tmp, (void**)&cursor, sizeof(unsigned long long)));
+  HM_CUDA(cudaFuncSetAttribute(k_symbolic_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSymCap * (int)sizeof(int)));  // 128 KB + < 1 KB static
+  int64_t capacity = (int64_t)32 * n + 65536;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    HM_TRY(dev_alloc(sys, (void**)&sys->d_iflist, sizeof(int32_t) * capacity));
+    HM_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
+    HM_CUDA(cudaMemsetAsync(sys->d_err, 0, 4 * sizeof(int), s));
+    for (int L = 0; L <= maxlev; ++L) {
+      const int cntL = lvl_begin[L + 1] - lvl_begin[L];
+      if (cntL == 0) continue;
+      k_symbolic_level<<<cntL, 1024, kSymCap * sizeof(int), s>>>(
+          d_order + lvl_begin[L], sys->d_first, sys->d_child_ptr, sys->d_child_list, sys->d_prowptr,
+          sys->d_pcol, sys->d_nupd, sys->d_ifoff, sys->d_iflist, cursor, capacity, sys->d_err);
+    }
+    int herr[4];
+    HM_CUDA(cudaMemcpyAsync(herr, sys->d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    HM_CUDA(cudaGetLastError());
+    if (herr[0] == HM_ERR_CAPACITY && herr[1] == -1) {  // arena too small: grow and retry
+      capacity *= 4;
+      continue;
+    }
+    if (herr[0] != 0) return check_device_error(sys, "analyze: symbolic");
+    break;
+  }
+  unsigned long long total = 0;
+  HM_CUDA(cudaMemcpyAsync(&total, cursor, sizeof(total), cudaMemcpyDeviceToHost, s));
+  sys->h_nupd.resize(nf);
+  sys->h_ifoff.resize(nf + 1);
+  HM_CUDA(cudaMemcpyAsync(sys->h_nupd.data(), sys->d_nupd, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaMemcpyAsync(sys->h_ifoff.data(), sys->d_ifoff, sizeof(int64_t) * nf, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  sys->if_total = (int64_t)total;
+  sys->h_ifoff[nf] = (int64_t)total;
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_relmap, sizeof(int32_t) * std::max<int64_t>(total, 1)));
+  k_relmap<<<nf, 256, 0, s>>>(sys->d_parent, sys->d_first, sys->d_nupd, sys->d_ifoff, sys->d_iflist, nf,
+                              sys->d_relmap, sys->d_err);
+  HM_TRY(check_device_error(sys, "analyze: relative maps"));
+  HM_TRY(build_plan(sys));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_amap, sizeof(int64_t) * sys->nnz));
+  launch_amap(sys);
+  return check_device_error(sys, "analyze: assembly map");
+}
+
+}  // namespace hm

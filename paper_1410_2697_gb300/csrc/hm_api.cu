@@ -1,0 +1,478 @@
+// hm_api.cu -- the extern "C" boundary (include/hodlr_mf.h) and host utilities.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t bytes) {
+  *p = nullptr;
+  bytes = std::max<size_t>(bytes, 16);
+  if (ctx->opts.hbm_budget && ctx->allocated + bytes > ctx->opts.hbm_budget) {
+    set_last_error("HBM budget exceeded: " + std::to_string(ctx->allocated + bytes) + " > " +
+                   std::to_string(ctx->opts.hbm_budget));
+    return HM_ERR_OUT_OF_MEMORY;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_last_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return HM_ERR_OUT_OF_MEMORY;
+  }
+  ctx->allocated += bytes;
+  owner->push_back(*p);
+  // remember the size for the budget through a side table
+  ctx->allocs.push_back((void*)(uintptr_t)bytes);
+  ctx->allocs.push_back(*p);
+  return HM_OK;
+}
+
+void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner) {
+  for (void* p : *owner) {
+    for (size_t i = 0; i + 1 < ctx->allocs.size(); i += 2) {
+      if (ctx->allocs[i + 1] == p) {
+        ctx->allocated -= (size_t)(uintptr_t)ctx->allocs[i];
+        ctx->allocs.erase(ctx->allocs.begin() + i, ctx->allocs.begin() + i + 2);
+        break;
+      }
+    }
+    cudaFree(p);
+  }
+  owner->clear();
+}
+
+int dev_alloc(hm_sys_s* sys, void** p, size_t bytes) { return dev_alloc_ctx(sys->ctx, &sys->allocs, p, bytes); }
+
+int copy_in(hm_sys_s* sys, void* dst, const void* src, size_t bytes) {
+  HM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, sys->ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
+  return HM_OK;
+}
+
+int check_device_error(hm_sys_s* sys, const char* where) {
+  int h[4] = {0, 0, 0, 0};
+  HM_CUDA(cudaMemcpyAsync(h, sys->d_err, sizeof(h), cudaMemcpyDeviceToHost, sys->ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
+  HM_CUDA(cudaGetLastError());
+  if (h[0] != 0) {
+    set_last_error(std::string(where) + ": device status " + std::to_string(h[0]) + " (" +
+                   std::to_string(h[1]) + ", " + std::to_string(h[2]) + ")");
+    return h[0];
+  }
+  return HM_OK;
+}
+
+static void destroy_sys(hm_sys_s* sys) {
+  if (!sys) return;
+  cudaStreamSynchronize(sys->ctx->stream);
+  for (auto& kv : sys->solve_plans) (void)kv;
+  sys->solve_plans.clear();
+  dev_free_all(sys->ctx, &sys->gm.allocs);
+  if (sys->gm.h_res) cudaFreeHost(sys->gm.h_res);
+  dev_free_all(sys->ctx, &sys->allocs);
+  delete sys;
+}
+
+}  // namespace hm
+
+namespace hm {
+
+static int with_device_io(hm_sys_t sys, int nrhs, const double* in, double* out,
+                          int (*fn)(hm_sys_t, int, const double*, double*, void*), void* arg) {
+  const size_t bytes = sizeof(double) * (size_t)sys->n * nrhs;
+  std::vector<void*> tmp;
+  const double* din = in;
+  double* dout = out;
+  const bool out_host = !is_device_ptr(out);
+  if (!is_device_ptr(in)) {
+    void* p;
+    HM_TRY(dev_alloc_ctx(sys->ctx, &tmp, &p, bytes));
+    HM_CUDA(cudaMemcpyAsync(p, in, bytes, cudaMemcpyHostToDevice, sys->ctx->stream));
+    din = (const double*)p;
+  }
+  if (out_host) {
+    void* p;
+    int s = dev_alloc_ctx(sys->ctx, &tmp, &p, bytes);
+    if (s != HM_OK) { dev_free_all(sys->ctx, &tmp); return s; }
+    dout = (double*)p;
+  }
+  int st = fn(sys, nrhs, din, dout, arg);
+  if (out_host && (st == HM_OK || st == HM_ERR_NO_CONVERGENCE)) {
+    cudaError_t e = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, sys->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sys->ctx->stream);
+    if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); st = HM_ERR_CUDA; }
+  }
+  cudaStreamSynchronize(sys->ctx->stream);
+  dev_free_all(sys->ctx, &tmp);
+  return st;
+}
+
+struct SolveArgs {
+  double rtol;
+  int max_iters;
+  hm_solve_info* info;
+};
+
+static int solve_fn(hm_sys_t sys, int nrhs, const double* b, double* x, void* arg) {
+  SolveArgs* a = (SolveArgs*)arg;
+  return gmres_impl(sys, nrhs, b, a->rtol, a->max_iters, x, a->info);
+}
+
+template <typename T>
+static int apply_fn_t(hm_sys_t sys, int nrhs, const double* r, double* z) {
+  cudaStream_t s = sys->ctx->stream;
+  const int n = sys->n;
+  const int64_t nn = (int64_t)n * nrhs;
+  std::vector<void*> tmp;
+  void *rp, *rT, *zT;
+  HM_TRY(dev_alloc_ctx(sys->ctx, &tmp, &rp, sizeof(double) * nn));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &tmp, &rT, sizeof(T) * nn));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &tmp, &zT, sizeof(T) * nn));
+  launch_permute_in(r, (double*)rp, sys->d_perm, n, nrhs, s);
+  launch_cast_to<T>((const double*)rp, (T*)rT, nn, s);
+  int st = apply_impl(sys, nrhs, rT, zT);
+  if (st == HM_OK) {
+    launch_cast_from<T>((const T*)zT, (double*)rp, nn, s);
+    launch_permute_out((const double*)rp, z, sys->d_perm, n, nrhs, s);
+    cudaStreamSynchronize(s);
+    st = check_device_error(sys, "apply");
+  }
+  cudaStreamSynchronize(s);
+  dev_free_all(sys->ctx, &tmp);
+  return st;
+}
+
+static int apply_fn(hm_sys_t sys, int nrhs, const double* r, double* z, void*) {
+  return sys->precision == HM_PREC_FP64 ? apply_fn_t<double>(sys, nrhs, r, z)
+                                        : apply_fn_t<float>(sys, nrhs, r, z);
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+int hm_default_opts(hm_opts* o) {
+  if (!o) return HM_ERR_INVALID_ARG;
+  memset(o, 0, sizeof(*o));
+  o->device = 0;
+  o->precision = HM_PREC_MIXED;
+  o->nd_leaf = 64;
+  o->hodlr_leaf = 64;
+  o->n_c = 64;
+  o->samples = 48;
+  o->seed = 0x5EEDull;
+  o->restart = 30;
+  o->hbm_budget = 0;
+  o->stream = nullptr;
+  return HM_OK;
+}
+
+int hm_create(hm_ctx_t* out, const hm_opts* opts) {
+  if (!out) return HM_ERR_INVALID_ARG;
+  *out = nullptr;
+  hm_opts o;
+  if (opts) o = *opts; else hm_default_opts(&o);
+  if (o.precision != HM_PREC_FP64 && o.precision != HM_PREC_MIXED) {
+    set_last_error("precision must be HM_PREC_FP64 or HM_PREC_MIXED");
+    return HM_ERR_INVALID_ARG;
+  }
+  const int kmax = o.precision == HM_PREC_FP64 ? 112 : 128;
+  if (o.nd_leaf < 1 || o.hodlr_leaf < 2 || o.hodlr_leaf > 64 || o.n_c < 0 || o.n_c > 128 ||
+      o.samples < 1 || o.samples > kmax || o.restart < 1 || o.restart > 200) {
+    set_last_error("option out of range: nd_leaf>=1, 2<=hodlr_leaf<=64, 0<=n_c<=128, "
+                   "1<=samples<=" + std::to_string(kmax) + ", 1<=restart<=200");
+    return HM_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  HM_CUDA(cudaGetDeviceCount(&ndev));
+  if (o.device < 0 || o.device >= ndev) {
+    set_last_error("no such CUDA device");
+    return HM_ERR_INVALID_ARG;
+  }
+  HM_CUDA(cudaSetDevice(o.device));
+  hm_ctx_s* ctx = new hm_ctx_s();
+  ctx->opts = o;
+  if (o.stream) {
+    ctx->stream = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      set_last_error("cudaStreamCreate failed");
+      return HM_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  cudaDeviceProp prop;
+  HM_CUDA(cudaGetDeviceProperties(&prop, o.device));
+  ctx->max_smem = (int)prop.sharedMemPerBlockOptin;
+  ctx->num_sms = prop.multiProcessorCount;
+  int st = dense_fact_setup(ctx->max_smem);
+  if (st == HM_OK) st = dense_comp_setup(ctx->max_smem);
+  if (st != HM_OK) {
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return HM_OK;
+}
+
+int hm_ctx_destroy(hm_ctx_t ctx) {
+  if (!ctx) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->opts.device);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return HM_OK;
+}
+
+int hm_analyze(hm_ctx_t ctx, int32_t n, const int64_t* rowptr, const int32_t* colidx, int32_t dim,
+               const int32_t* grid_coords, const int32_t* perm_in, int32_t nfronts_in,
+               const int32_t* first_in, const int32_t* parent_in, hm_sys_t* out) {
+  if (!ctx || !out || n <= 0 || !rowptr || !colidx) {
+    set_last_error("hm_analyze: null argument or n <= 0");
+    return HM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  cudaSetDevice(ctx->opts.device);
+  hm_sys_s* sys = new hm_sys_s();
+  sys->ctx = ctx;
+  sys->n = n;
+  sys->precision = ctx->opts.precision;
+  int st = analyze_impl(sys, rowptr, colidx, dim, grid_coords, perm_in, nfronts_in, first_in, parent_in);
+  if (st != HM_OK) {
+    destroy_sys(sys);
+    return st;
+  }
+  *out = sys;
+  return HM_OK;
+}
+
+int hm_get_sizes(hm_sys_t sys, int32_t* n, int32_t* nfronts) {
+  if (!sys) return HM_ERR_INVALID_ARG;
+  if (n) *n = sys->n;
+  if (nfronts) *nfronts = sys->nf;
+  return HM_OK;
+}
+
+int hm_get_ordering(hm_sys_t sys, int32_t* perm, int32_t* first, int32_t* parent, int32_t* level) {
+  if (!sys) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(sys->ctx->opts.device);
+  if (perm) HM_TRY(copy_in(sys, perm, sys->d_perm, sizeof(int32_t) * sys->n));
+  if (first) memcpy(first, sys->h_first.data(), sizeof(int32_t) * (sys->nf + 1));
+  if (parent) memcpy(parent, sys->h_parent.data(), sizeof(int32_t) * sys->nf);
+  if (level) memcpy(level, sys->h_level.data(), sizeof(int32_t) * sys->nf);
+  return HM_OK;
+}
+
+int hm_get_symbolic(hm_sys_t sys, int32_t* nupd, int64_t* if_off, int32_t* if_list, int32_t* relmap) {
+  if (!sys) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(sys->ctx->opts.device);
+  const int nf = sys->nf;
+  std::vector<int64_t> off(nf + 1, 0);
+  for (int q = 0; q < nf; ++q) off[q + 1] = off[q] + sys->h_nupd[q];
+  if (nupd) memcpy(nupd, sys->h_nupd.data(), sizeof(int32_t) * nf);
+  if (if_off) memcpy(if_off, off.data(), sizeof(int64_t) * (nf + 1));
+  if (if_list || relmap) {
+    std::vector<int32_t> L(std::max<int64_t>(sys->if_total, 1)), R(std::max<int64_t>(sys->if_total, 1));
+    HM_TRY(copy_in(sys, L.data(), sys->d_iflist, sizeof(int32_t) * sys->if_total));
+    HM_TRY(copy_in(sys, R.data(), sys->d_relmap, sizeof(int32_t) * sys->if_total));
+    for (int q = 0; q < nf; ++q) {
+      const int64_t src = sys->h_ifoff[q];
+      if (if_list) memcpy(if_list + off[q], L.data() + src, sizeof(int32_t) * sys->h_nupd[q]);
+      if (relmap) memcpy(relmap + off[q], R.data() + src, sizeof(int32_t) * sys->h_nupd[q]);
+    }
+  }
+  return HM_OK;
+}
+
+int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* info) {
+  if (!sys || !values) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(sys->ctx->opts.device);
+  sys->factored = false;
+  const double* d_vals = values;
+  void* tmpv = nullptr;
+  std::vector<void*> tmp;
+  if (!is_device_ptr(values)) {
+    HM_TRY(dev_alloc_ctx(sys->ctx, &tmp, &tmpv, sizeof(double) * sys->nnz));
+    HM_CUDA(cudaMemcpyAsync(tmpv, values, sizeof(double) * sys->nnz, cudaMemcpyHostToDevice,
+                            sys->ctx->stream));
+    d_vals = (const double*)tmpv;
+  }
+  int st = factor_impl(sys, d_vals, tol);
+  cudaStreamSynchronize(sys->ctx->stream);
+  dev_free_all(sys->ctx, &tmp);
+  if (st != HM_OK) return st;
+  sys->factored = true;
+  sys->tol = tol;
+  if (info) {
+    const Plan& P = sys->plan;
+    info->nfronts = sys->nf;
+    info->nlevels = P.nlevels;
+    info->n_hodlr = (int)P.hf.size();
+    std::vector<int> r(std::max(P.nrank, 1));
+    if (P.nrank) HM_TRY(copy_in(sys, r.data(), sys->d_ranks, sizeof(int) * P.nrank));
+    int mx = 0, capped = 0;
+    for (const auto& h : P.hf) {
+      if (h.kf > 0) {
+        mx = std::max(mx, r[h.rank_slot_f]);
+        capped += r[h.rank_slot_f] >= h.kf && h.kf < std::min(h.nu, h.np);
+      }
+      for (const auto& nd : h.nodes) {
+        mx = std::max(mx, r[nd.rank_slot]);
+        capped += r[nd.rank_slot] >= nd.kb && nd.kb < std::min(nd.mid - nd.lo, nd.hi - nd.mid);
+      }
+    }
+    info->max_rank = mx;
+    info->rank_capped = capped;
+    info->factor_bytes = P.factor_bytes;
+    info->front_bytes = (double)P.front_total * (sys->precision == HM_PREC_FP64 ? 8 : 4);
+  }
+  return HM_OK;
+}
+
+int hm_solve(hm_sys_t sys, int32_t nrhs, const double* b, double rtol, int32_t max_iters, double* x,
+             hm_solve_info* info) {
+  if (!sys || !b || !x || nrhs < 1 || nrhs > 64 || max_iters < 0) return HM_ERR_INVALID_ARG;
+  if (!sys->factored) { set_last_error("hm_solve before hm_factor"); return HM_ERR_STATE; }
+  cudaSetDevice(sys->ctx->opts.device);
+  SolveArgs a{rtol, max_iters, info};
+  return with_device_io(sys, nrhs, b, x, solve_fn, &a);
+}
+
+int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z) {
+  if (!sys || !r || !z || nrhs < 1 || nrhs > 64) return HM_ERR_INVALID_ARG;
+  if (!sys->factored) { set_last_error("hm_precond_apply before hm_factor"); return HM_ERR_STATE; }
+  cudaSetDevice(sys->ctx->opts.device);
+  return with_device_io(sys, nrhs, r, z, apply_fn, nullptr);
+}
+
+int hm_get_update(hm_sys_t sys, int32_t front, double* U) {
+  if (!sys || !U || front < 0 || front >= sys->nf) return HM_ERR_INVALID_ARG;
+  if (!sys->factored) return HM_ERR_STATE;
+  cudaSetDevice(sys->ctx->opts.device);
+  const FrontGeom& g = sys->plan.fg[front];
+  const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
+  std::vector<unsigned char> buf((size_t)g.nhat * g.nhat * es + 8);
+  HM_TRY(copy_in(sys, buf.data(), (char*)sys->d_front + g.off * es, (size_t)g.nhat * g.nhat * es));
+  for (int c = 0; c < g.nu; ++c)
+    for (int r = 0; r < g.nu; ++r) {
+      const size_t idx = (size_t)(g.np + r) + (size_t)(g.np + c) * g.nhat;
+      U[r + (size_t)c * g.nu] = es == 8 ? ((double*)buf.data())[idx] : (double)((float*)buf.data())[idx];
+    }
+  return HM_OK;
+}
+
+int hm_get_front_ranks(hm_sys_t sys, int32_t front, int32_t* kind, int32_t* ranks, int32_t* nr) {
+  if (!sys || front < 0 || front >= sys->nf) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(sys->ctx->opts.device);
+  const FrontGeom& g = sys->plan.fg[front];
+  if (kind) *kind = g.hodlr >= 0 ? 1 : 0;
+  if (g.hodlr < 0) { if (nr) *nr = 0; return HM_OK; }
+  const HFront& h = sys->plan.hf[g.hodlr];
+  std::vector<int> r(std::max(sys->plan.nrank, 1));
+  HM_TRY(copy_in(sys, r.data(), sys->d_ranks, sizeof(int) * sys->plan.nrank));
+  int k = 0;
+  if (ranks) ranks[k] = h.kf > 0 ? r[h.rank_slot_f] : 0;
+  ++k;
+  for (const auto& nd : h.nodes) {
+    if (ranks) ranks[k] = r[nd.rank_slot];
+    ++k;
+  }
+  if (nr) *nr = k;
+  return HM_OK;
+}
+
+int hm_get_hodlr_block(hm_sys_t sys, int32_t front, int32_t level, int32_t node, int32_t* m,
+                       int32_t* n, int32_t* k, int32_t* rank, double* U, double* V) {
+  if (!sys || front < 0 || front >= sys->nf) return HM_ERR_INVALID_ARG;
+  if (!sys->factored) return HM_ERR_STATE;
+  cudaSetDevice(sys->ctx->opts.device);
+  const FrontGeom& g = sys->plan.fg[front];
+  if (g.hodlr < 0) { set_last_error("not a HODLR front"); return HM_ERR_INVALID_ARG; }
+  const HFront& h = sys->plan.hf[g.hodlr];
+  const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
+  int rows_u, rows_v, cols, slot;
+  int64_t u_off, v_off, ldu, ldv;
+  const void* ubase;
+  if (level < 0) {
+    rows_u = h.nu; rows_v = h.np; cols = h.kf; slot = h.rank_slot_f;
+    ubase = sys->d_w; u_off = h.w_off; ldu = h.nu;
+    v_off = h.bo_off; ldv = h.np;
+  } else {
+    const HNodeGeom* nd = nullptr;
+    for (const auto& x : h.nodes)
+      if (x.level == level && x.index == node) nd = &x;
+    if (!nd) { set_last_error("no such HODLR node"); return HM_ERR_INVALID_ARG; }
+    rows_u = nd->mid - nd->lo; rows_v = nd->hi - nd->mid; cols = h.kl[level]; slot = nd->rank_slot;
+    ubase = sys->d_bo; u_off = h.bo_off + (int64_t)h.col[level] * h.np + nd->lo; ldu = h.np;
+    v_off = h.bo_off + (int64_t)h.col[level] * h.np + nd->mid; ldv = h.np;
+  }
+  if (m) *m = rows_u;
+  if (n) *n = rows_v;
+  if (k) *k = cols;
+  if (rank) {
+    int r = 0;
+    if (cols > 0) HM_TRY(copy_in(sys, &r, sys->d_ranks + slot, sizeof(int)));
+    *rank = r;
+  }
+  auto fetch = [&](const void* base, int64_t off, int64_t ld, int rows, double* out) -> int {
+    // the block spans (cols - 1) * ld + rows elements from its first entry
+    const size_t span = cols > 0 ? (size_t)(cols - 1) * ld + rows : 0;
+    std::vector<unsigned char> buf(span * es + 8);
+    if (span > 0) HM_TRY(copy_in(sys, buf.data(), (const char*)base + off * es, span * es));
+    for (int c = 0; c < cols; ++c)
+      for (int r = 0; r < rows; ++r) {
+        const size_t i = (size_t)r + (size_t)c * ld;
+        out[r + (size_t)c * rows] = es == 8 ? ((double*)buf.data())[i] : (double)((float*)buf.data())[i];
+      }
+    return HM_OK;
+  };
+  if (U) HM_TRY(fetch(ubase, u_off, ldu, rows_u, U));
+  if (V) HM_TRY(fetch(sys->d_bo, v_off, ldv, rows_v, V));
+  return HM_OK;
+}
+
+int hm_destroy(hm_sys_t sys) {
+  if (!sys) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(sys->ctx->opts.device);
+  destroy_sys(sys);
+  return HM_OK;
+}
+
+const char* hm_status_str(int s) {
+  switch (s) {
+    case HM_OK: return "ok";
+    case HM_ERR_INVALID_ARG: return "invalid argument";
+    case HM_ERR_NOT_SPD: return "matrix (pivot block) not positive definite";
+    case HM_ERR_NO_CONVERGENCE: return "GMRES did not converge";
+    case HM_ERR_OUT_OF_MEMORY: return "out of device memory or HBM budget";
+    case HM_ERR_CUDA: return "CUDA error";
+    case HM_ERR_CAPACITY: return "capacity exceeded";
+    case HM_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case HM_ERR_STATE: return "call out of order";
+    case HM_ERR_BREAKDOWN: return "breakdown (singular core)";
+    default: return "unknown status";
+  }
+}
+
+const char* hm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// hm_common.cuh -- shared device/host helpers of the HODLR multifrontal library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/hodlr_mf.h"
+
+namespace hm {
+
+// ------------------------------------------------------------------------------------
+// Host error reporting: the last failure message of the calling thread.
+// ------------------------------------------------------------------------------------
+void set_last_error(const std::string& msg);
+
+#define HM_CUDA(call)                                                               \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ::hm::set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_) +     \
+                           " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+      return HM_ERR_CUDA;                                                           \
+    }                                                                               \
+  } while (0)
+
+#define HM_TRY(expr)                 \
+  do {                               \
+    int s_ = (expr);                 \
+    if (s_ != HM_OK) return s_;      \
+  } while (0)
+
+// ------------------------------------------------------------------------------------
+// Device error word: err[0] = first status code raised, err[1], err[2] = detail.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void raise_error(int* err, int code, int a = 0, int b = 0) {
+  if (atomicCAS(err, 0, code) == 0) {
+    err[1] = a;
+    err[2] = b;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Block-wide sum in fixed order (deterministic). `red` holds >= 32 entries.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T s = T(0);
+  if (wid == 0) {
+    s = lane < nw ? red[lane] : T(0);
+    s = warp_sum(s);
+    if (lane == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its published definition:
+// ten rounds of (hi0,lo0)=mulhilo(M0,c0), (hi1,lo1)=mulhilo(M1,c2),
+// c <- (hi1^c1^k0, lo1, hi0^c3^k1, lo0); key += (W0, W1) between rounds.
+// ------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t p0 = (uint64_t)M0 * c[0];
+    const uint64_t p1 = (uint64_t)M1 * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Sketch entry (i, c) of block `blk`: ((w >> 8) - 2^23) / 2^23 with w = Philox word 0,
+// a 24-bit uniform grid on [-1, 1), exact in FP32 and FP64.
+__host__ __device__ __forceinline__ float sketch_entry(uint32_t i, uint32_t col, uint64_t blk,
+                                                      uint64_t seed) {
+  uint32_t c[4] = {i, col, (uint32_t)blk, (uint32_t)(blk >> 32)};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return (float)((int)(c[0] >> 8) - 8388608) * (1.0f / 8388608.0f);
+}
+
+// 64-bit id of a compressed block: kind 0 = off-diagonal block (level, node) of the
+// pivot block's HODLR tree, kind 1 = the coupling block F_fp.
+__host__ __device__ __forceinline__ uint64_t block_id(int front, int kind, int level, int node) {
+  return ((uint64_t)front << 24) | ((uint64_t)kind << 20) | ((uint64_t)level << 16) |
+         (uint64_t)node;
+}
+
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Opt a kernel into the largest dynamic shared memory the device allows per block
+// (the per-block opt-in limit minus the kernel's static shared memory).
+template <typename F>
+inline cudaError_t allow_max_dyn_smem(F* func, int max_smem) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, func);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              max_smem - (int)a.sharedSizeBytes);
+}
+
+}  // namespace hm

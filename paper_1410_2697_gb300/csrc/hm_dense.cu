@@ -1,0 +1,123 @@
+// hm_dense.cu -- batched dense kernels (FP32/FP64 SIMT) used by factor and apply.
+#include <algorithm>
+
+#include "hm_dense.cuh"
+
+namespace hm {
+
+// =====================================================================================
+// Batched GEMM: 64x64 output tiles, BK = 16, 256 threads, 4x4 outputs per thread
+// (rows ty + 16 i, columns tx + 16 j).  Operand tiles are staged through shared memory
+// with the next k-slice prefetched into registers while the current one is consumed.
+// =====================================================================================
+constexpr int BM = kGemmBM, BN = kGemmBN, BK = 16;
+
+template <typename T>
+__device__ __forceinline__ T load_op(const T* __restrict__ X, int op, int ld, int r, int c,
+                                     int nr, int nc) {
+  // element (r, c) of op(X), with op(X) of size nr x nc; zero outside
+  if (r >= nr || c >= nc) return T(0);
+  return op == 0 ? X[(size_t)r + (size_t)c * ld] : X[(size_t)c + (size_t)r * ld];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks,
+                                              const GemmTile* __restrict__ tiles) {
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask t = tasks[tl.task];
+  const int m0 = (tl.mn >> 16) * BM, n0 = (tl.mn & 0xffff) * BN;
+  const T* __restrict__ A = (const T*)t.A;
+  const T* __restrict__ B = (const T*)t.B;
+  T* __restrict__ C = (T*)t.C;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+  // load coordinates: 4 elements per thread per operand tile
+  T ra[4], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int r, p;
+      if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
+      ra[q] = load_op(A, t.opA, t.lda, m0 + r, k0 + p, t.m, t.k);
+      int c, pb;
+      if (t.opB == 0) { pb = e % BK; c = e / BK; } else { c = e % BN; pb = e / BN; }
+      rb[q] = load_op(B, t.opB, t.ldb, k0 + pb, n0 + c, t.k, t.n);
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int r, p;
+      if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
+      As[p][r] = ra[q];
+      int c, pb;
+      if (t.opB == 0) { pb = e % BK; c = e / BK; } else { c = e % BN; pb = e / BN; }
+      Bs[pb][c] = rb[q];
+    }
+  };
+
+  if (t.k > 0) fetch(0);
+  for (int k0 = 0; k0 < t.k; k0 += BK) {
+    __syncthreads();
+    stash();
+    __syncthreads();
+    if (k0 + BK < t.k) fetch(k0 + BK);
+#pragma unroll
+    for (int p = 0; p < BK; ++p) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[p][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[p][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  const T alpha = (T)t.alpha, beta = (T)t.beta;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = n0 + tx + 16 * j;
+    if (c >= t.n) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + ty + 16 * i;
+      if (r >= t.m) continue;
+      if (t.lower && r < c) continue;
+      T* dst = C + (size_t)r + (size_t)c * t.ldc;
+      const T v = alpha * acc[i][j];
+      *dst = (beta == T(0)) ? v : fma(beta, *dst, v);
+    }
+  }
+}
+
+void gemm_tiles_for(const GemmTask& t, int task_index, std::vector<GemmTile>* out) {
+  if (t.m <= 0 || t.n <= 0) return;
+  const int tm = (t.m + BM - 1) / BM, tn = (t.n + BN - 1) / BN;
+  for (int a = 0; a < tm; ++a)
+    for (int b = 0; b < tn; ++b) {
+      if (t.lower && (a + 1) * BM - 1 < b * BN) continue;  // tile strictly above diagonal
+      out->push_back(GemmTile{task_index, (a << 16) | b});
+    }
+}
+
+template <typename T>
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_gemm<T><<<ntiles, 256, 0, s>>>(tasks, tiles);
+}
+
+template void launch_gemm<float>(const GemmTask*, const GemmTile*, int, cudaStream_t);
+template void launch_gemm<double>(const GemmTask*, const GemmTile*, int, cudaStream_t);
+
+}  // namespace hm

@@ -1,0 +1,123 @@
+// hm_dense.cuh -- batched dense kernels (SIMT, FP32/FP64) used by the factorization and
+// the preconditioner apply.  Every kernel takes an array of task descriptors so that all
+// fronts (and all blocks of all fronts) of one elimination-tree level run in one launch.
+#pragma once
+
+#include <vector>
+
+#include "hm_common.cuh"
+
+namespace hm {
+
+// C[m x n] = alpha * op(A)[m x k] * op(B)[k x n] + beta * C.  Column-major; op 0 = N,
+// 1 = T.  lower = 1 writes only entries with row >= column (SYRK-style updates).
+struct GemmTask {
+  const void* A;
+  const void* B;
+  void* C;
+  int m, n, k;
+  int lda, ldb, ldc;
+  int opA, opB, lower, pad;
+  double alpha, beta;
+};
+
+// One 64x64 output tile: task index and tile coordinates (tm << 16 | tn).
+struct GemmTile {
+  int task;
+  int mn;
+};
+
+constexpr int kGemmBM = 64;
+constexpr int kGemmBN = 64;
+
+// In-place lower Cholesky of an n x n block (n <= 128), ld >= n.
+struct PotrfTask {
+  void* A;
+  int n, ld;
+  int front, pad;
+};
+
+// B[rows] <- B[rows] * L^{-T}; L n x n lower (n <= 128), B has `m` rows; one launch
+// item covers rows [row0, row0 + 64).
+struct TrsmTask {
+  const void* L;
+  void* B;
+  int n, ldl, m, ldb;
+  int row0, pad;
+};
+
+// X <- L^{-T} L^{-1} X for a Cholesky factor L (n <= 64 rows), ncols columns.
+struct CholSolveTask {
+  const void* L;
+  void* X;
+  int n, ldl, ldx, ncols;
+};
+
+// Householder QR of Y (m x k, ld): Q overwrites Y; R (k x k, ld k) written if non-null.
+struct QrTask {
+  void* Y;
+  void* R;
+  int m, k, ld, pad;
+};
+
+// SVD of M = R^T (R k x k upper triangular, ld k) by one-sided Jacobi; writes
+// UhS = Uhat_r Sigma_r (k x k, ld k; columns >= rank zero) and Vh = Vhat_r (same),
+// sorted by decreasing singular value; rank = #{sigma_i > tol * sigma_1}.
+struct SvdTask {
+  const void* R;
+  void* UhS;
+  void* Vh;
+  int* rank;
+  int k, pad;
+};
+
+// Sketch Omega (rows x cols, ld) of block `blk` (Philox4x32-10, 24-bit uniform).
+struct OmegaTask {
+  void* out;
+  uint64_t blk;
+  int rows, cols, ld, pad;
+};
+
+// Woodbury core C (n2 = 2k, ld n2): the GEMMs have written the two diagonal k x k
+// blocks; this sets the off-diagonal blocks to I and LU-factors C with partial pivoting.
+struct CoreLuTask {
+  void* C;
+  int* piv;
+  int k, front;
+};
+
+// B (n2 x ncols, ldb) <- C^{-1} B using the LU factors of a core.
+struct LuSolveTask {
+  const void* LU;
+  const int* piv;
+  void* B;
+  int n2, ldb, ncols, pad;
+};
+
+template <typename T>
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, cudaStream_t s);
+template <typename T>
+void launch_potrf(const PotrfTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s);
+template <typename T>
+void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s);
+template <typename T>
+void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStream_t s);
+template <typename T>
+void launch_qr(const QrTask* tasks, int ntasks, cudaStream_t s);
+template <typename T>
+void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStream_t s);
+template <typename T>
+void launch_omega(const OmegaTask* tasks, int ntasks, uint64_t seed, cudaStream_t s);
+template <typename T>
+void launch_core_lu(const CoreLuTask* tasks, int ntasks, int* err, cudaStream_t s);
+template <typename T>
+void launch_lu_solve(const LuSolveTask* tasks, int ntasks, int maxcols, cudaStream_t s);
+
+// Host-side: append the tiles of one task (all tiles, or those touching the lower
+// triangle when t.lower).
+void gemm_tiles_for(const GemmTask& t, int task_index, std::vector<GemmTile>* out);
+
+int dense_fact_setup(int max_dyn_smem);
+int dense_comp_setup(int max_dyn_smem);
+
+}  // namespace hm

@@ -1,0 +1,288 @@
+// hm_dense_fact.cu -- small batched factorizations: Cholesky (dense pivot blocks and
+// HODLR leaves), triangular solves, and the LU of the Woodbury cores.
+#include "hm_dense.cuh"
+
+namespace hm {
+
+// =====================================================================================
+// Cholesky of one pivot block per CTA (n <= 128), right-looking, in shared memory.
+// A non-positive pivot raises HM_ERR_NOT_SPD (front id, column) and the factorization of
+// that block continues on |d| so no NaN spreads; the host reports the error.
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf(const PotrfTask* __restrict__ tasks, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);
+  const PotrfTask t = tasks[blockIdx.x];
+  const int n = t.n, ls = n + 1;
+  T* A = (T*)t.A;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    if (i >= j) S[i + j * ls] = A[(size_t)i + (size_t)j * t.ld];
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      T d = S[j + j * ls];
+      if (!(d > T(0))) {
+        raise_error(err, HM_ERR_NOT_SPD, t.front, j);
+        d = fabs(d) > T(0) ? fabs(d) : T(1);
+      }
+      S[j + j * ls] = sqrt(d);
+    }
+    __syncthreads();
+    const T inv = T(1) / S[j + j * ls];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) S[i + j * ls] *= inv;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e % m, c = j + 1 + e / m;
+      if (i >= c) S[i + c * ls] -= S[i + j * ls] * S[c + j * ls];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    if (i >= j) A[(size_t)i + (size_t)j * t.ld] = S[i + j * ls];
+  }
+}
+
+template <typename T>
+void launch_potrf(const PotrfTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)maxn * (maxn + 1) * sizeof(T);
+  k_potrf<T><<<ntasks, 256, smem, s>>>(tasks, err);
+}
+
+// =====================================================================================
+// B <- B L^{-T}: each of 64 threads owns one row of a 64-row slab; the row lives in
+// shared memory as x[j][row] (row fastest) so the solve is conflict free.
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(64) k_trsm(const TrsmTask* __restrict__ tasks) {
+  extern __shared__ unsigned char smem_raw[];
+  const TrsmTask t = tasks[blockIdx.x];
+  const int n = t.n, ls = n + 1;
+  T* Ls = reinterpret_cast<T*>(smem_raw);
+  T* X = Ls + n * ls;  // [n][64]
+  const T* L = (const T*)t.L;
+  T* B = (T*)t.B;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    if (i >= j) Ls[i + j * ls] = L[(size_t)i + (size_t)j * t.ldl];
+  }
+  const int rows = min(64, t.m - t.row0);
+  for (int e = threadIdx.x; e < 64 * n; e += blockDim.x) {
+    const int r = e % 64, j = e / 64;
+    X[j * 64 + r] = r < rows ? B[(size_t)(t.row0 + r) + (size_t)j * t.ldb] : T(0);
+  }
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < rows) {
+    for (int j = 0; j < n; ++j) {
+      T v = X[j * 64 + r];
+      for (int i = 0; i < j; ++i) v -= X[i * 64 + r] * Ls[j + i * ls];
+      X[j * 64 + r] = v / Ls[j + j * ls];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * n; e += blockDim.x) {
+    const int rr = e % 64, j = e / 64;
+    if (rr < rows) B[(size_t)(t.row0 + rr) + (size_t)j * t.ldb] = X[j * 64 + rr];
+  }
+}
+
+template <typename T>
+void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const size_t smem = ((size_t)maxn * (maxn + 1) + 64 * (size_t)maxn) * sizeof(T);
+  k_trsm<T><<<ntasks, 64, smem, s>>>(tasks);
+}
+
+// =====================================================================================
+// X <- L^{-T} L^{-1} X for a leaf Cholesky factor; threads own columns, 128 at a time.
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(128) k_chol_solve(const CholSolveTask* __restrict__ tasks) {
+  extern __shared__ unsigned char smem_raw[];
+  const CholSolveTask t = tasks[blockIdx.x];
+  const int n = t.n, ls = n + 1;
+  T* Ls = reinterpret_cast<T*>(smem_raw);
+  T* X = Ls + n * ls;  // [n][128]
+  const T* L = (const T*)t.L;
+  T* Xg = (T*)t.X;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    if (i >= j) Ls[i + j * ls] = L[(size_t)i + (size_t)j * t.ldl];
+  }
+  for (int c0 = 0; c0 < t.ncols; c0 += 128) {
+    const int nc = min(128, t.ncols - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * nc; e += blockDim.x) {
+      const int i = e % n, c = e / n;
+      X[i * 128 + c] = Xg[(size_t)i + (size_t)(c0 + c) * t.ldx];
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c < nc) {
+      for (int j = 0; j < n; ++j) {  // L y = x
+        T v = X[j * 128 + c];
+        for (int i = 0; i < j; ++i) v -= Ls[j + i * ls] * X[i * 128 + c];
+        X[j * 128 + c] = v / Ls[j + j * ls];
+      }
+      for (int j = n - 1; j >= 0; --j) {  // L^T z = y
+        T v = X[j * 128 + c];
+        for (int i = j + 1; i < n; ++i) v -= Ls[i + j * ls] * X[i * 128 + c];
+        X[j * 128 + c] = v / Ls[j + j * ls];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * nc; e += blockDim.x) {
+      const int i = e % n, cc = e / n;
+      Xg[(size_t)i + (size_t)(c0 + cc) * t.ldx] = X[i * 128 + cc];
+    }
+  }
+}
+
+template <typename T>
+void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const size_t smem = ((size_t)maxn * (maxn + 1) + 128 * (size_t)maxn) * sizeof(T);
+  k_chol_solve<T><<<ntasks, 128, smem, s>>>(tasks);
+}
+
+// =====================================================================================
+// Woodbury core: C = [[U^T Uhat, I], [I, V^T Vhat]] (2k x 2k).  The diagonal blocks were
+// written by GEMMs; this kernel sets the identity blocks and LU-factors C with partial
+// pivoting (C is symmetric indefinite), in global memory (L2-resident), one CTA per core.
+// A zero pivot column raises HM_ERR_BREAKDOWN.
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ tasks, int* err) {
+  __shared__ T sval[32];
+  __shared__ int sidx[32];
+  __shared__ int piv_s;
+  const CoreLuTask t = tasks[blockIdx.x];
+  const int k = t.k, n = 2 * k;
+  T* C = (T*)t.C;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    const T v = (i == j) ? T(1) : T(0);
+    C[(size_t)i + (size_t)(k + j) * n] = v;
+    C[(size_t)(k + i) + (size_t)j * n] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < n; ++j) {
+    // pivot search in column j, rows j..n-1 (largest |.|, lowest row on ties)
+    T best = T(-1);
+    int bi = n;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+      const T v = fabs(C[(size_t)i + (size_t)j * n]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { sval[wid] = best; sidx[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T b = T(-1);
+      int ii = n;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (sval[w] > b || (sval[w] == b && sidx[w] < ii)) { b = sval[w]; ii = sidx[w]; }
+      if (!(b > T(0))) {
+        raise_error(err, HM_ERR_BREAKDOWN, t.front, j);
+        ii = j;
+      }
+      piv_s = ii;
+      t.piv[j] = ii;
+    }
+    __syncthreads();
+    const int p = piv_s;
+    if (p != j)
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const T a = C[(size_t)j + (size_t)c * n];
+        C[(size_t)j + (size_t)c * n] = C[(size_t)p + (size_t)c * n];
+        C[(size_t)p + (size_t)c * n] = a;
+      }
+    __syncthreads();
+    T d = C[(size_t)j + (size_t)j * n];
+    if (d == T(0)) d = T(1);
+    const T inv = T(1) / d;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) C[(size_t)i + (size_t)j * n] *= inv;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e % m, c = j + 1 + e / m;
+      C[(size_t)i + (size_t)c * n] -= C[(size_t)i + (size_t)j * n] * C[(size_t)j + (size_t)c * n];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_core_lu(const CoreLuTask* tasks, int ntasks, int* err, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  k_core_lu<T><<<ntasks, 256, 0, s>>>(tasks, err);
+}
+
+// B <- C^{-1} B with the pivoted LU of a core; one thread per column of B.
+template <typename T>
+__global__ void __launch_bounds__(128) k_lu_solve(const LuSolveTask* __restrict__ tasks) {
+  const LuSolveTask t = tasks[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= t.ncols) return;
+  const T* LU = (const T*)t.LU;
+  T* b = (T*)t.B + (size_t)c * t.ldb;
+  const int n = t.n2;
+  for (int j = 0; j < n; ++j) {
+    const int p = t.piv[j];
+    if (p != j) { const T a = b[j]; b[j] = b[p]; b[p] = a; }
+  }
+  for (int j = 0; j < n; ++j) {
+    const T v = b[j];
+    for (int i = j + 1; i < n; ++i) b[i] -= LU[(size_t)i + (size_t)j * n] * v;
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    T d = LU[(size_t)j + (size_t)j * n];
+    if (d == T(0)) d = T(1);
+    const T v = b[j] / d;
+    b[j] = v;
+    for (int i = 0; i < j; ++i) b[i] -= LU[(size_t)i + (size_t)j * n] * v;
+  }
+}
+
+template <typename T>
+void launch_lu_solve(const LuSolveTask* tasks, int ntasks, int maxcols, cudaStream_t s) {
+  if (ntasks <= 0 || maxcols <= 0) return;
+  // grid.x covers the widest task; narrower tasks exit early
+  dim3 grid((maxcols + 127) / 128, ntasks);
+  k_lu_solve<T><<<grid, 128, 0, s>>>(tasks);
+}
+
+template void launch_potrf<float>(const PotrfTask*, int, int, int*, cudaStream_t);
+template void launch_potrf<double>(const PotrfTask*, int, int, int*, cudaStream_t);
+template void launch_trsm<float>(const TrsmTask*, int, int, cudaStream_t);
+template void launch_trsm<double>(const TrsmTask*, int, int, cudaStream_t);
+template void launch_chol_solve<float>(const CholSolveTask*, int, int, cudaStream_t);
+template void launch_chol_solve<double>(const CholSolveTask*, int, int, cudaStream_t);
+template void launch_core_lu<float>(const CoreLuTask*, int, int*, cudaStream_t);
+template void launch_core_lu<double>(const CoreLuTask*, int, int*, cudaStream_t);
+template void launch_lu_solve<float>(const LuSolveTask*, int, int, cudaStream_t);
+template void launch_lu_solve<double>(const LuSolveTask*, int, int, cudaStream_t);
+
+int dense_fact_setup(int max_smem) {
+  HM_CUDA(allow_max_dyn_smem(k_potrf<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_potrf<double>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_trsm<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_trsm<double>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_chol_solve<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_chol_solve<double>, max_smem));
+  return HM_OK;
+}
+
+}  // namespace hm

@@ -1,0 +1,168 @@
+// hm_factor.cu -- numerical factorization (Sections 4.1.1 and 4.2.1 of the paper).
+//
+// Per elimination-tree level, deepest first:
+//   F_p = F_bar_p (+) U_c1 (+) ...            assembly (Eq. fbar) and extend-add
+//   dense fronts (|I_p| <= n_c):  F_pp = L L^T, L_fp = F_fp L^-T, U_p = F_ff - L_fp L_fp^T
+//   HODLR fronts: compress every off-diagonal block of F_pp's HODLR tree and F_fp ~ W Vf^T
+//   by the randomized range finder; factor F_pp^HODLR by recursive Woodbury on the column
+//   block X = [Vf | B_0 | ... | B_{L-1}] (each level's ancestor columns form a prefix);
+//   U_p = F_ff - W (Vf^T F_pp^-1 Vf) W^T  (Eq. update_HODLR_Parent).
+#include <cstdio>
+#include <cstdlib>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+// F[amap[k]] = A value of permuted entry k (lower triangle); also keeps the permuted
+// FP64 values for the GMRES residual.
+template <typename T>
+__global__ void k_scatter(const double* __restrict__ vals, const int64_t* __restrict__ psrc,
+                          const int64_t* __restrict__ amap, int64_t nnz, T* __restrict__ F,
+                          double* __restrict__ pvals) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = vals[psrc[k]];
+    pvals[k] = v;
+    const int64_t d = amap[k];
+    if (d >= 0) F[d] = (T)v;
+  }
+}
+
+// Extend-add: one warp adds column `col` (lower part) of child c's update matrix
+// U_c = F_ff of c into its parent's front at rows/columns relmap.
+template <typename T>
+__global__ void k_extend_add(const EaItem* __restrict__ items, int nitems,
+                             const int32_t* __restrict__ parent, const int64_t* __restrict__ front_off,
+                             const int* __restrict__ nhat, const int* __restrict__ npiv,
+                             const int64_t* __restrict__ ifoff, const int32_t* __restrict__ relmap,
+                             T* __restrict__ F) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nitems) return;
+  const EaItem it = items[w];
+  const int c = it.child, col = it.col, p = parent[c];
+  const int ldc = nhat[c], npc = npiv[c], nuc = ldc - npc, ldp = nhat[p];
+  const T* Fc = F + front_off[c] + npc + (int64_t)(npc + col) * ldc;
+  T* Fp = F + front_off[p];
+  const int32_t* rm = relmap + ifoff[c];
+  const int64_t cc = (int64_t)rm[col] * ldp;
+  for (int r = col + lane; r < nuc; r += 32) Fp[rm[r] + cc] += Fc[r];
+}
+
+// Debug facility (environment HM_DEBUG_SYNC=1): after each stage of the factorization,
+// synchronize, report the device error word and count non-finite entries of the arenas.
+template <typename T>
+__global__ void k_count_nonfinite(const T* __restrict__ p, int64_t n, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += isfinite((double)p[i]) ? 0ull : 1ull;
+  if (c) atomicAdd(out, c);
+}
+
+template <typename T>
+static void debug_stage(hm_sys_s* sys, const char* stage, int level) {
+  static const bool on = getenv("HM_DEBUG_SYNC") && getenv("HM_DEBUG_SYNC")[0] == '1';
+  if (!on) return;
+  cudaStream_t s = sys->ctx->stream;
+  const Plan& P = sys->plan;
+  unsigned long long* d = nullptr;
+  cudaMalloc(&d, 6 * sizeof(unsigned long long));
+  cudaMemsetAsync(d, 0, 6 * sizeof(unsigned long long), s);
+  const void* bufs[6] = {sys->d_front, sys->d_comp, sys->d_bo, sys->d_x, sys->d_core, sys->d_tb};
+  const int64_t lens[6] = {P.front_total, P.comp_total, P.bo_total, P.bo_total, P.core_total, P.tb_total};
+  for (int i = 0; i < 6; ++i)
+    if (lens[i] > 0) k_count_nonfinite<T><<<256, 256, 0, s>>>((const T*)bufs[i], lens[i], d + i);
+  unsigned long long h[6];
+  int e[4];
+  cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(e, sys->d_err, sizeof(e), cudaMemcpyDeviceToHost, s);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  cudaFree(d);
+  fprintf(stderr, "[hm debug] level %d %-10s cuda=%s err=%d(%d,%d) nonfinite front=%llu comp=%llu bo=%llu x=%llu core=%llu tb=%llu\n",
+          level, stage, cudaGetErrorString(ce), e[0], e[1], e[2], h[0], h[1], h[2], h[3], h[4], h[5]);
+}
+
+template <typename T>
+static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* base) {
+  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, sys->ctx->stream);
+}
+
+template <typename T>
+static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
+  Plan& P = sys->plan;
+  cudaStream_t s = sys->ctx->stream;
+  const unsigned char* base = P.d_tasks;
+  T* F = (T*)sys->d_front;
+  HM_CUDA(cudaMemsetAsync(sys->d_err, 0, 4 * sizeof(int), s));
+  HM_CUDA(cudaMemsetAsync(F, 0, (size_t)P.front_total * sizeof(T), s));
+  if (P.bo_total) HM_CUDA(cudaMemsetAsync(sys->d_bo, 0, (size_t)P.bo_total * sizeof(T), s));
+  if (P.w_total) HM_CUDA(cudaMemsetAsync(sys->d_w, 0, (size_t)P.w_total * sizeof(T), s));
+  {
+    const int64_t nnz = sys->nnz;
+    const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+    k_scatter<T><<<std::max(grid, 1), 256, 0, s>>>(d_values, sys->d_psrc, sys->d_amap, nnz, F,
+                                                  sys->d_pvals);
+  }
+  for (int l = P.nlevels - 1; l >= 0; --l) {
+    const LevelFactorPlan& lp = P.levels[l];
+    for (const auto& sl : lp.ea_slots) {
+      if (sl.count == 0) continue;
+      const int threads = 256;
+      const int64_t blocks = ((int64_t)sl.count * 32 + threads - 1) / threads;
+      k_extend_add<T><<<(unsigned)blocks, threads, 0, s>>>(sl.dev(base), sl.count, sys->d_parent,
+                                                           P.d_front_off, P.d_nhat, P.d_np, sys->d_ifoff,
+                                                           sys->d_relmap, F);
+    }
+    debug_stage<T>(sys, "extendadd", l);
+    if (lp.n_dense) {
+      launch_potrf<T>(lp.potrf.dev(base), lp.potrf.count, lp.potrf_maxn, sys->d_err, s);
+      launch_trsm<T>(lp.trsm.dev(base), lp.trsm.count, lp.trsm_maxn, s);
+      run_gemm<T>(sys, lp.syrk, base);
+      debug_stage<T>(sys, "dense", l);
+    }
+    if (lp.n_hodlr) {
+      launch_omega<T>(lp.omega.dev(base), lp.omega.count, sys->ctx->opts.seed, s);
+      run_gemm<T>(sys, lp.sampY, base);
+      launch_qr<T>(lp.qrY.dev(base), lp.qrY.count, s);
+      debug_stage<T>(sys, "qrY", l);
+      run_gemm<T>(sys, lp.sampZ, base);
+      launch_qr<T>(lp.qrZ.dev(base), lp.qrZ.count, s);
+      launch_svd<T>(lp.svd.dev(base), lp.svd.count, lp.svd_maxk, tol, s);
+      debug_stage<T>(sys, "svd", l);
+      run_gemm<T>(sys, lp.formU, base);
+      run_gemm<T>(sys, lp.formV, base);
+      debug_stage<T>(sys, "formUV", l);
+      if (lp.x_copy_len)
+        HM_CUDA(cudaMemcpyAsync((T*)sys->d_x + lp.x_copy_off, (T*)sys->d_bo + lp.x_copy_off,
+                                (size_t)lp.x_copy_len * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      launch_potrf<T>(lp.leaf_potrf.dev(base), lp.leaf_potrf.count, lp.leaf_maxn, sys->d_err, s);
+      launch_chol_solve<T>(lp.leaf_solve.dev(base), lp.leaf_solve.count, lp.leaf_maxn, s);
+      debug_stage<T>(sys, "leaves", l);
+      for (const auto& H : lp.heights) {
+        run_gemm<T>(sys, H.pre, base);
+        debug_stage<T>(sys, "core-pre", l);
+        launch_core_lu<T>(H.lu.dev(base), H.lu.count, sys->d_err, s);
+        debug_stage<T>(sys, "core-lu", l);
+        launch_lu_solve<T>(H.lus.dev(base), H.lus.count, H.lus_maxcols, s);
+        run_gemm<T>(sys, H.upd, base);
+        debug_stage<T>(sys, "core-upd", l);
+      }
+      run_gemm<T>(sys, lp.schurT, base);
+      run_gemm<T>(sys, lp.schurP, base);
+      run_gemm<T>(sys, lp.schurF, base);
+      debug_stage<T>(sys, "schur", l);
+    }
+  }
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+int factor_impl(hm_sys_s* sys, const double* d_values, double tol) {
+  int st = sys->precision == HM_PREC_FP64 ? factor_t<double>(sys, d_values, tol)
+                                          : factor_t<float>(sys, d_values, tol);
+  if (st != HM_OK) return st;
+  return check_device_error(sys, "factor");
+}
+
+}  // namespace hm

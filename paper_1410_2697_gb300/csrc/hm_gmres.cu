@@ -1,0 +1,354 @@
+// hm_gmres.cu -- right-preconditioned flexible GMRES(m) in FP64 (Sections 1 and 3 of the
+// paper: the approximate multifrontal solve preconditions GMRES, which restores the
+// accuracy).  nrhs systems run in lockstep; each keeps its own Krylov basis.
+//
+//   V_j  (FP64)  Krylov vectors; Z_j = M^{-1} V_j stored in the factor precision (the
+//               preconditioned vectors are exactly representable there);
+//   w = A Z_j in FP64; Arnoldi by classical Gram-Schmidt applied twice (CGS2) with
+//   block partial sums reduced in a fixed order (deterministic); Givens rotations and
+//   the least-squares solve on the device; x += Z y at the end of a cycle; the TRUE
+//   residual ||b - A x|| / ||b|| decides convergence.
+#include <algorithm>
+#include <cmath>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+constexpr int kDotThreads = 256;
+
+// y[r] = A x[r]  (mode 0)   or   y[r] = b[r] - A x[r]  (mode 1); rows in new numbering.
+template <typename XT>
+__global__ void k_spmv(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, int n, int nrhs, const XT* __restrict__ x,
+                       int64_t ldx, double* __restrict__ y, int64_t ldy, const double* __restrict__ b,
+                       int64_t ldb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t kb = rowptr[i], ke = rowptr[i + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    const XT* xr = x + r * ldx;
+    double s = 0.0;
+    for (int64_t k = kb; k < ke; ++k) s = fma(val[k], (double)xr[col[k]], s);
+    y[i + r * ldy] = b ? b[i + r * ldb] - s : s;
+  }
+}
+
+// part[(r*nblk + blk)*stride + i] = sum over the block's rows of V_i[r] . w[r], i < nvec.
+// V_i[r] starts at V + (i*nrhs + r)*n.
+__global__ void __launch_bounds__(kDotThreads) k_multidot(const double* __restrict__ V,
+                                                          const double* __restrict__ w, int n,
+                                                          int nrhs, int nvec, int stride,
+                                                          double* __restrict__ part) {
+  __shared__ double red[32];
+  const int r = blockIdx.y, nblk = gridDim.x, blk = blockIdx.x;
+  const int64_t chunk = ((int64_t)n + nblk - 1) / nblk;
+  const int64_t b = blk * chunk, e = std::min<int64_t>((int64_t)n, b + chunk);
+  const double* wr = w + (int64_t)r * n;
+  for (int i = 0; i < nvec; ++i) {
+    const double* vi = V + ((int64_t)i * nrhs + r) * n;
+    double s = 0.0;
+    for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) s = fma(vi[k], wr[k], s);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[((int64_t)r * nblk + blk) * stride + i] = s;
+  }
+}
+
+// h[r*stride + i] (=|+=) sum_blk part[...]  (fixed block order)
+__global__ void k_reduce_dots(const double* __restrict__ part, int nblk, int nrhs, int nvec,
+                              int stride, double* __restrict__ h, int accumulate) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nrhs * nvec) return;
+  const int r = e / nvec, i = e % nvec;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[((int64_t)r * nblk + b) * stride + i];
+  if (accumulate) h[(int64_t)r * stride + i] += s;
+  else h[(int64_t)r * stride + i] = s;
+}
+
+// a[r*stride + i] += b[r*stride + i], i < nvec
+__global__ void k_add_cols(double* __restrict__ a, const double* __restrict__ b, int nrhs, int nvec,
+                           int stride) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nrhs * nvec) return;
+  const int r = e / nvec, i = e % nvec;
+  a[(int64_t)r * stride + i] += b[(int64_t)r * stride + i];
+}
+
+// w[r] -= sum_{i < nvec} V_i[r] * c[r*stride + i]
+__global__ void k_gs_update(const double* __restrict__ V, double* __restrict__ w, int n, int nrhs,
+                            int nvec, int stride, const double* __restrict__ c) {
+  const int64_t total = (int64_t)n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n);
+    const int64_t k = e % n;
+    double s = w[e];
+    for (int i = 0; i < nvec; ++i) s -= V[((int64_t)i * nrhs + r) * n + k] * c[(int64_t)r * stride + i];
+    w[e] = s;
+  }
+}
+
+// dst[r] = src[r] * (nrm[r] > 0 ? 1/nrm[r] : 0); nrm[r] = sqrt(ss[r*stride])
+__global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, int n, int nrhs,
+                        const double* __restrict__ ss, int stride) {
+  const int64_t total = (int64_t)n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n);
+    const double nr = sqrt(ss[(int64_t)r * stride]);
+    dst[e] = nr > 0.0 ? src[e] / nr : 0.0;
+  }
+}
+
+// Givens step for column j (thread per RHS): H column = h (h1 + h2), H[j+1,j] = ||w||.
+__global__ void k_givens(double* __restrict__ H, const double* __restrict__ hv, int hstride,
+                         const double* __restrict__ ss, int ssstride, double* __restrict__ cs,
+                         double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ bnorm,
+                         double* __restrict__ res, int* __restrict__ len, int j, int m, int nrhs,
+                         double rtol) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double* Hr = H + (int64_t)r * (m + 1) * m;
+  double* col = Hr + (int64_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = hv[(int64_t)r * hstride + i];
+  col[j + 1] = sqrt(ss[(int64_t)r * ssstride]);
+  double* c = cs + (int64_t)r * m;
+  double* s = sn + (int64_t)r * m;
+  double* gr = g + (int64_t)r * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double t = c[i] * col[i] + s[i] * col[i + 1];
+    col[i + 1] = -s[i] * col[i] + c[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  if (den > 0.0) {
+    c[j] = col[j] / den;
+    s[j] = col[j + 1] / den;
+  } else {
+    c[j] = 1.0;
+    s[j] = 0.0;
+  }
+  col[j] = den;
+  col[j + 1] = 0.0;
+  gr[j + 1] = -s[j] * gr[j];
+  gr[j] = c[j] * gr[j];
+  const double est = bnorm[r] > 0.0 ? fabs(gr[j + 1]) / bnorm[r] : 0.0;
+  res[r] = est;
+  if (len[r] == 0 && est <= rtol) len[r] = j + 1;
+}
+
+// y = R^{-1} g over len[r] (thread per RHS); len[r] == 0 -> use jend.
+__global__ void k_backsolve(const double* __restrict__ H, const double* __restrict__ g,
+                            double* __restrict__ y, int* __restrict__ len, int jend, int m, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  int L = len[r];
+  if (L == 0 || L > jend) L = jend;
+  len[r] = L;
+  const double* Hr = H + (int64_t)r * (m + 1) * m;
+  const double* gr = g + (int64_t)r * (m + 1);
+  double* yr = y + (int64_t)r * m;
+  for (int i = L - 1; i >= 0; --i) {
+    double v = gr[i];
+    for (int k = i + 1; k < L; ++k) v -= Hr[i + (int64_t)k * (m + 1)] * yr[k];
+    const double d = Hr[i + (int64_t)i * (m + 1)];
+    yr[i] = d != 0.0 ? v / d : 0.0;
+  }
+  for (int i = L; i < m; ++i) yr[i] = 0.0;
+}
+
+// x[r] += sum_{j < len[r]} Z_j[r] y[r][j]
+template <typename ZT>
+__global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z, const double* __restrict__ y,
+                           const int* __restrict__ len, int n, int nrhs, int m) {
+  const int64_t total = (int64_t)n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n);
+    const int64_t k = e % n;
+    double s = x[e];
+    const int L = len[r];
+    for (int j = 0; j < L; ++j) s = fma((double)Z[((int64_t)j * nrhs + r) * n + k], y[(int64_t)r * m + j], s);
+    x[e] = s;
+  }
+}
+
+// Start of a cycle: V_0 = r / beta (inactive systems get 0), g = [beta, 0, ...], len = 0.
+__global__ void k_cycle_init(const double* __restrict__ rvec, double* __restrict__ V0, int n, int nrhs,
+                             const double* __restrict__ ss, const int* __restrict__ active) {
+  const int64_t total = (int64_t)n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n);
+    const double beta = sqrt(ss[r]);
+    V0[e] = (active[r] && beta > 0.0) ? rvec[e] / beta : 0.0;
+  }
+}
+
+__global__ void k_cycle_g(double* __restrict__ g, int* __restrict__ len, const double* __restrict__ ss,
+                          const int* __restrict__ active, int m, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double* gr = g + (int64_t)r * (m + 1);
+  for (int i = 0; i <= m; ++i) gr[i] = 0.0;
+  gr[0] = active[r] ? sqrt(ss[r]) : 0.0;
+  len[r] = 0;
+}
+
+// ------------------------------------------------------------------------------------
+// Host driver
+// ------------------------------------------------------------------------------------
+static int gm_alloc(hm_sys_s* sys, void** p, size_t bytes) {
+  return dev_alloc_ctx(sys->ctx, &sys->gm.allocs, p, bytes);
+}
+
+static int ensure_workspace(hm_sys_s* sys, int nrhs, int m) {
+  auto& G = sys->gm;
+  if (G.nrhs == nrhs && G.m == m) return HM_OK;
+  dev_free_all(sys->ctx, &G.allocs);
+  if (G.h_res) { cudaFreeHost(G.h_res); G.h_res = nullptr; }
+  const int64_t n = sys->n;
+  const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
+  G.nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 4095) / 4096, 2 * sys->ctx->num_sms));
+  const int stride = m + 2;
+  HM_TRY(gm_alloc(sys, (void**)&G.V, sizeof(double) * (m + 1) * nrhs * n));
+  HM_TRY(gm_alloc(sys, &G.Z, (size_t)es * m * nrhs * n));
+  HM_TRY(gm_alloc(sys, &G.wT, (size_t)es * nrhs * n));
+  HM_TRY(gm_alloc(sys, (void**)&G.w, sizeof(double) * nrhs * n));
+  HM_TRY(gm_alloc(sys, (void**)&G.b, sizeof(double) * nrhs * n));
+  HM_TRY(gm_alloc(sys, (void**)&G.x, sizeof(double) * nrhs * n));
+  HM_TRY(gm_alloc(sys, (void**)&G.r, sizeof(double) * nrhs * n));
+  HM_TRY(gm_alloc(sys, (void**)&G.H, sizeof(double) * nrhs * (m + 1) * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.cs, sizeof(double) * nrhs * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.sn, sizeof(double) * nrhs * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.g, sizeof(double) * nrhs * (m + 1)));
+  HM_TRY(gm_alloc(sys, (void**)&G.y, sizeof(double) * nrhs * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.bnorm, sizeof(double) * nrhs));
+  HM_TRY(gm_alloc(sys, (void**)&G.res, sizeof(double) * nrhs * 4));
+  HM_TRY(gm_alloc(sys, (void**)&G.part, sizeof(double) * (size_t)G.nblk * nrhs * stride));
+  HM_TRY(gm_alloc(sys, (void**)&G.hv, sizeof(double) * nrhs * stride * 3));
+  HM_TRY(gm_alloc(sys, (void**)&G.len, sizeof(int) * nrhs * 2));
+  HM_CUDA(cudaMallocHost((void**)&G.h_res, sizeof(double) * nrhs * 4 + sizeof(int) * nrhs * 2));
+  G.nrhs = nrhs;
+  G.m = m;
+  return HM_OK;
+}
+
+// ss[r*stride] = ||v[r]||^2 (deterministic)
+static void sqnorm(hm_sys_s* sys, const double* v, double* ss, int stride, int nrhs) {
+  auto& G = sys->gm;
+  cudaStream_t s = sys->ctx->stream;
+  k_multidot<<<dim3(G.nblk, nrhs), kDotThreads, 0, s>>>(v, v, sys->n, nrhs, 1, stride, G.part);
+  // note: with V = v and nvec = 1 the "basis" is v itself (stride of rhs = n)
+  k_reduce_dots<<<(nrhs + 127) / 128, 128, 0, s>>>(G.part, G.nblk, nrhs, 1, stride, ss, 0);
+}
+
+template <typename T>
+static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
+                   double* d_x, hm_solve_info* info) {
+  const int m = std::max(1, sys->ctx->opts.restart);
+  HM_TRY(ensure_workspace(sys, nrhs, m));
+  auto& G = sys->gm;
+  cudaStream_t s = sys->ctx->stream;
+  const int n = sys->n;
+  const int64_t nn = (int64_t)n * nrhs;
+  const int stride = m + 2;
+  const int gsz = (int)std::min<int64_t>((nn + 255) / 256, 152 * 8);
+  launch_permute_in(d_b, G.b, sys->d_perm, n, nrhs, s);
+  HM_CUDA(cudaMemsetAsync(G.x, 0, sizeof(double) * nn, s));
+  // ||b|| per RHS
+  double* bn2 = G.hv + 2 * nrhs * stride;  // scratch: squared norms (stride 1)
+  sqnorm(sys, G.b, bn2, 1, nrhs);
+  std::vector<double> hb(nrhs);
+  HM_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> bnorm(nrhs);
+  for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(hb[r]);
+  HM_CUDA(cudaMemcpyAsync(G.bnorm, bnorm.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+  // r = b (x0 = 0)
+  HM_CUDA(cudaMemcpyAsync(G.r, G.b, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> relres(nrhs);
+  std::vector<int> active(nrhs);
+  for (int r = 0; r < nrhs; ++r) relres[r] = bnorm[r] > 0 ? 1.0 : 0.0;
+  int iters = 0, cycles = 0;
+  int* d_active = G.len + nrhs;
+  double* rss = G.hv + 2 * nrhs * stride + nrhs;  // squared residual norms
+  HM_CUDA(cudaMemcpyAsync(rss, bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, s));
+  bool done = true;
+  for (int r = 0; r < nrhs; ++r) done = done && relres[r] <= rtol;
+  T* Z = (T*)G.Z;
+  while (!done && iters < max_iters) {
+    for (int r = 0; r < nrhs; ++r) active[r] = relres[r] > rtol ? 1 : 0;
+    HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    k_cycle_init<<<gsz, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active);
+    k_cycle_g<<<(nrhs + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, nrhs);
+    int j = 0;
+    for (; j < m && iters < max_iters; ++j) {
+      const double* Vj = G.V + (int64_t)j * nrhs * n;
+      T* Zj = Z + (int64_t)j * nrhs * n;
+      launch_cast_to<T>(Vj, (T*)G.wT, nn, s);
+      HM_TRY(apply_impl(sys, nrhs, G.wT, Zj));
+      k_spmv<T><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+                                                Zj, n, G.w, n, nullptr, 0);
+      double* h1 = G.hv;
+      double* h2 = G.hv + nrhs * stride;
+      const int nvec = j + 1;
+      for (int pass = 0; pass < 2; ++pass) {
+        double* h = pass == 0 ? h1 : h2;
+        k_multidot<<<dim3(G.nblk, nrhs), kDotThreads, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, G.part);
+        k_reduce_dots<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(G.part, G.nblk, nrhs, nvec, stride, h, 0);
+        k_gs_update<<<gsz, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h);
+      }
+      k_add_cols<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(h1, h2, nrhs, nvec, stride);  // h1 += h2
+      double* wss = G.hv + 2 * nrhs * stride + 2 * nrhs;  // ||w||^2 per RHS (stride 1)
+      sqnorm(sys, G.w, wss, 1, nrhs);
+      k_scale<<<gsz, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1);
+      k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, h1, stride, wss, 1, G.cs, G.sn, G.g, G.bnorm,
+                                               G.res, G.len, j, m, nrhs, rtol);
+      ++iters;
+      HM_CUDA(cudaMemcpyAsync(G.h_res, G.res, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+      HM_CUDA(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int r = 0; r < nrhs; ++r)
+        if (active[r] && !(G.h_res[r] <= rtol)) all = false;
+      if (all) { ++j; break; }
+    }
+    const int jend = std::min(j, m);
+    k_backsolve<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, G.g, G.y, G.len, jend, m, nrhs);
+    k_update_x<T><<<gsz, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m);
+    k_spmv<double><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+                                                   G.x, n, G.r, n, G.b, n);
+    sqnorm(sys, G.r, rss, 1, nrhs);
+    std::vector<double> hr(nrhs);
+    HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    ++cycles;
+    done = true;
+    for (int r = 0; r < nrhs; ++r) {
+      relres[r] = bnorm[r] > 0 ? std::sqrt(hr[r]) / bnorm[r] : 0.0;
+      if (!(relres[r] <= rtol)) done = false;
+    }
+  }
+  launch_permute_out(G.x, d_x, sys->d_perm, n, nrhs, s);
+  HM_CUDA(cudaStreamSynchronize(s));
+  HM_CUDA(cudaGetLastError());
+  if (info) {
+    info->iters = iters;
+    info->restarts = cycles;
+    double mx = 0;
+    for (double v : relres) mx = std::max(mx, v);
+    info->relres = mx;
+    info->converged = done ? 1 : 0;
+  }
+  HM_TRY(check_device_error(sys, "solve"));
+  return done ? HM_OK : HM_ERR_NO_CONVERGENCE;
+}
+
+int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters, double* d_x,
+               hm_solve_info* info) {
+  if (sys->precision == HM_PREC_FP64) return gmres_t<double>(sys, nrhs, d_b, rtol, max_iters, d_x, info);
+  return gmres_t<float>(sys, nrhs, d_b, rtol, max_iters, d_x, info);
+}
+
+}  // namespace hm

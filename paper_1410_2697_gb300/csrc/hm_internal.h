@@ -1,0 +1,288 @@
+// hm_internal.h -- host-side state of a context / system and the execution plan.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "hm_common.cuh"
+#include "hm_dense.cuh"
+
+struct hm_ctx_s;
+struct hm_sys_s;
+
+namespace hm {
+
+// A typed span inside the uploaded task buffer.
+template <typename TaskT>
+struct Span {
+  size_t off = 0;  // byte offset in the task buffer
+  int count = 0;
+  const TaskT* dev(const unsigned char* base) const {
+    return reinterpret_cast<const TaskT*>(base + off);
+  }
+};
+
+struct GemmBatch {
+  Span<GemmTask> tasks;
+  Span<GemmTile> tiles;
+};
+
+// Host builder of the task buffer (one upload after planning).
+struct TaskBuf {
+  std::vector<unsigned char> host;
+  template <typename TaskT>
+  Span<TaskT> add(const std::vector<TaskT>& v) {
+    Span<TaskT> s;
+    size_t a = (host.size() + 15) & ~size_t(15);
+    host.resize(a + v.size() * sizeof(TaskT));
+    if (!v.empty()) memcpy(host.data() + a, v.data(), v.size() * sizeof(TaskT));
+    s.off = a;
+    s.count = (int)v.size();
+    return s;
+  }
+  GemmBatch add_gemm(const std::vector<GemmTask>& t) {
+    std::vector<GemmTile> tiles;
+    for (size_t i = 0; i < t.size(); ++i) gemm_tiles_for(t[i], (int)i, &tiles);
+    GemmBatch b;
+    b.tasks = add(t);
+    b.tiles = add(tiles);
+    return b;
+  }
+};
+
+// Extend-add work item: one column `col` of child `child`'s update matrix.
+struct EaItem {
+  int child;
+  int col;
+};
+
+// Per-front geometry of the plan.
+struct FrontGeom {
+  int np = 0, nu = 0, nhat = 0;
+  int level = 0;
+  int hodlr = -1;          // index into Plan::hf, -1 for a dense front
+  int64_t off = 0;         // element offset of the dense front (nhat x nhat) in the arena
+};
+
+struct HNodeGeom {
+  int level, index, lo, mid, hi;
+  int kb;                  // sketch width of this node's off-diagonal block
+  int64_t core_off;        // (2 k_level)^2 elements in the core arena
+  int64_t piv_off;         // 2 k_level ints
+  int rank_slot;
+  int64_t om_off, y_off, z_off, r_off, uhs_off, vh_off;  // compression scratch
+  int64_t tb_off;          // factor-time t/s buffer, 2 k_level x A_level
+};
+
+struct HFront {
+  int q;                   // front id
+  int np, nu, L;
+  int kf;                  // sketch width (capacity) of F_fp, 0 if nu == 0
+  std::vector<int> kl;     // capacity per HODLR level
+  std::vector<int> col;    // column offset of each level in Bo / X
+  int xc;                  // total columns of Bo / X
+  int64_t bo_off;          // np x xc (same offsets in the Bo and X arenas)
+  int64_t w_off;           // nu x kf
+  int64_t t_off;           // kf x kf
+  int64_t p_off;           // nu x kf
+  int rank_slot_f;
+  int64_t fom_off, fy_off, fz_off, fr_off, fuhs_off, fvh_off;
+  std::vector<HNodeGeom> nodes;   // all internal nodes, level by level
+  std::vector<int> leaf_lo, leaf_hi;
+};
+
+struct LevelFactorPlan {
+  std::vector<Span<EaItem>> ea_slots;
+  Span<PotrfTask> potrf;       // dense fronts
+  int potrf_maxn = 0;
+  Span<TrsmTask> trsm;
+  int trsm_maxn = 0;
+  GemmBatch syrk;
+  // HODLR fronts
+  Span<OmegaTask> omega;
+  GemmBatch sampY, sampZ, formU, formV;
+  Span<QrTask> qrY, qrZ;
+  Span<SvdTask> svd;
+  int svd_maxk = 0;
+  int64_t x_copy_off = 0, x_copy_len = 0;  // Bo -> X copy (elements)
+  Span<PotrfTask> leaf_potrf;
+  int leaf_maxn = 0;
+  Span<CholSolveTask> leaf_solve;
+  struct Height {
+    GemmBatch pre;            // core diagonal blocks and t = Z^T X_anc
+    Span<CoreLuTask> lu;
+    Span<LuSolveTask> lus;
+    int lus_maxcols = 0;
+    GemmBatch upd;            // X_anc -= Zhat s
+  };
+  std::vector<Height> heights;
+  GemmBatch schurT, schurP, schurF;
+  int n_dense = 0, n_hodlr = 0;
+};
+
+// Solve-time plan for a given number of right-hand sides.
+struct UpItem {
+  int q;
+};
+struct LevelSolvePlan {
+  Span<int> fronts;            // all fronts of the level (gather + dense up / down)
+  int nfronts = 0;
+  Span<CholSolveTask> leaf;    // HODLR leaves
+  int leaf_maxn = 0;
+  struct Height {
+    GemmBatch t;               // t = [U^T y_a; V^T y_b]
+    Span<LuSolveTask> lus;
+    int lus_maxcols = 0;
+    GemmBatch upd;             // y -= Zhat s
+  };
+  std::vector<Height> heights;
+  GemmBatch fin1, fin2;        // tf = Vf^T y ; f -= W tf
+  GemmBatch down1, down2;      // tf = W^T x_f ; x_p -= Vtilde tf
+};
+
+struct SolvePlan {
+  int nrhs = 0;
+  std::vector<LevelSolvePlan> levels;
+  std::vector<int64_t> fv_off;  // per front, element offset of its (nhat x nrhs) vector
+  int64_t fv_total = 0;
+  int64_t sb_total = 0;         // node t/s buffers + tf buffers
+  std::vector<int64_t> node_sb_off;  // not used directly; offsets live in tasks
+  TaskBuf tb;
+  unsigned char* d_tasks = nullptr;
+  void* d_fv = nullptr;         // T
+  void* d_sb = nullptr;         // T
+  int64_t* d_fvoff = nullptr;
+};
+
+struct Plan {
+  std::vector<FrontGeom> fg;
+  std::vector<HFront> hf;
+  std::vector<std::vector<int>> level_fronts;   // fronts per depth
+  int nlevels = 0;
+  int64_t front_total = 0, bo_total = 0, w_total = 0, t_total = 0, p_total = 0;
+  int64_t core_total = 0, piv_total = 0, comp_total = 0, tb_total = 0;
+  int nrank = 0;
+  std::vector<int64_t> level_front_begin, level_front_end;   // element ranges per level
+  std::vector<LevelFactorPlan> levels;
+  TaskBuf tb;
+  unsigned char* d_tasks = nullptr;
+  int64_t* d_front_off = nullptr;
+  int* d_nhat = nullptr;
+  int* d_np = nullptr;
+  int* d_hkind = nullptr;  // per front: -1 dense, else HODLR index
+  int max_children = 0;
+  double factor_bytes = 0;
+};
+
+struct DevArena {
+  std::vector<void*> ptrs;
+};
+
+}  // namespace hm
+
+struct hm_ctx_s {
+  hm_opts opts;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t allocated = 0;
+  int max_smem = 0;
+  int num_sms = 0;
+  std::vector<void*> allocs;
+};
+
+struct hm_sys_s {
+  hm_ctx_s* ctx = nullptr;
+  int n = 0;
+  int64_t nnz = 0;
+  int nf = 0;
+  int dim = 0;
+  int precision = HM_PREC_MIXED;
+  // pattern and ordering (device)
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_colidx = nullptr;
+  int32_t* d_perm = nullptr;
+  int32_t* d_iperm = nullptr;
+  int32_t* d_first = nullptr;
+  int32_t* d_parent = nullptr;
+  int32_t* d_node_of = nullptr;
+  int32_t* d_child_ptr = nullptr;
+  int32_t* d_child_list = nullptr;
+  int64_t* d_prowptr = nullptr;
+  int32_t* d_pcol = nullptr;
+  int64_t* d_psrc = nullptr;
+  int64_t* d_amap = nullptr;
+  // symbolic (device)
+  int32_t* d_nupd = nullptr;
+  int64_t* d_ifoff = nullptr;
+  int32_t* d_iflist = nullptr;
+  int32_t* d_relmap = nullptr;
+  int64_t if_total = 0;
+  // host copies
+  std::vector<int32_t> h_first, h_parent, h_level, h_nupd;
+  std::vector<int64_t> h_ifoff;
+  std::vector<std::vector<int>> h_children;
+  // plan + numeric state
+  hm::Plan plan;
+  void* d_front = nullptr;   // T arena
+  void* d_bo = nullptr;      // T
+  void* d_x = nullptr;       // T
+  void* d_w = nullptr;       // T
+  void* d_tm = nullptr;      // T
+  void* d_pm = nullptr;      // T
+  void* d_core = nullptr;    // T
+  int* d_piv = nullptr;
+  void* d_comp = nullptr;    // T
+  void* d_tb = nullptr;      // T
+  int* d_ranks = nullptr;
+  double* d_pvals = nullptr; // permuted A values (FP64) for SpMV
+  int* d_err = nullptr;      // device error word (4 ints)
+  bool factored = false;
+  double tol = 0;
+  std::map<int, std::unique_ptr<hm::SolvePlan>> solve_plans;
+  std::vector<void*> allocs;
+  // GMRES workspace (grown on demand)
+  struct Gm {
+    int nrhs = 0, m = 0;
+    double *V = nullptr, *w = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
+    double *b = nullptr, *x = nullptr, *r = nullptr, *bnorm = nullptr, *res = nullptr, *y = nullptr;
+    double *part = nullptr, *hv = nullptr;
+    void* Z = nullptr;  // T, m x nrhs x n
+    void* wT = nullptr; // T, n x nrhs (apply input)
+    int* len = nullptr;
+    double* h_res = nullptr;  // pinned
+    std::vector<void*> allocs;
+    int nblk = 0;
+  } gm;
+};
+
+namespace hm {
+
+int dev_alloc(hm_sys_s* sys, void** p, size_t bytes);
+int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t bytes);
+void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner);
+int check_device_error(hm_sys_s* sys, const char* where);
+bool is_device_ptr(const void* p);
+int copy_in(hm_sys_s* sys, void* dst, const void* src, size_t bytes);
+
+int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, int dim,
+                 const int32_t* coords, const int32_t* perm_in, int nfronts_in,
+                 const int32_t* first_in, const int32_t* parent_in);
+int build_plan(hm_sys_s* sys);
+int factor_impl(hm_sys_s* sys, const double* d_values, double tol);
+int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out);
+// z (T, n x nrhs, ld n, new numbering) = M^{-1} r (T, same layout)
+int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
+int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
+               double* d_x, hm_solve_info* info);
+// permutation helpers (new <-> original numbering), FP64 n x nrhs
+void launch_permute_in(const double* src, double* dst, const int32_t* perm, int n, int nrhs,
+                       cudaStream_t s);
+void launch_permute_out(const double* src, double* dst, const int32_t* perm, int n, int nrhs,
+                        cudaStream_t s);
+template <typename T>
+void launch_cast_to(const double* src, T* dst, int64_t count, cudaStream_t s);
+template <typename T>
+void launch_cast_from(const T* src, double* dst, int64_t count, cudaStream_t s);
+
+}  // namespace hm

@@ -1,0 +1,516 @@
+// hm_plan.cu -- host-side planning: front geometry, HODLR block layout, device arenas and
+// the per-level task tables of the factorization and of the preconditioner apply.
+// Integer bookkeeping only; all arithmetic of the method runs in the kernels.
+#include <algorithm>
+#include <cstring>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+static inline void* at(void* base, int64_t off, int es) {
+  return (void*)((char*)base + off * (int64_t)es);
+}
+
+static int hodlr_depth(int n, int leaf) {
+  int L = 0;
+  while (ceil_div(n, 1 << L) > leaf) ++L;
+  return L;
+}
+
+static GemmTask gemm(const void* A, int lda, int opA, const void* B, int ldb, int opB, void* C,
+                     int ldc, int m, int n, int k, double alpha, double beta, int lower = 0) {
+  GemmTask t;
+  t.A = A; t.B = B; t.C = C;
+  t.m = m; t.n = n; t.k = k;
+  t.lda = lda; t.ldb = ldb; t.ldc = ldc;
+  t.opA = opA; t.opB = opB; t.lower = lower; t.pad = 0;
+  t.alpha = alpha; t.beta = beta;
+  return t;
+}
+
+int build_plan(hm_sys_s* sys) {
+  Plan& P = sys->plan;
+  const hm_opts& o = sys->ctx->opts;
+  const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
+  const int nf = sys->nf;
+  const int S = o.samples;
+  P.fg.assign(nf, FrontGeom());
+  int maxlev = 0;
+  for (int q = 0; q < nf; ++q) {
+    FrontGeom& g = P.fg[q];
+    g.np = sys->h_first[q + 1] - sys->h_first[q];
+    g.nu = sys->h_nupd[q];
+    g.nhat = g.np + g.nu;
+    g.level = sys->h_level[q];
+    maxlev = std::max(maxlev, g.level);
+  }
+  P.nlevels = maxlev + 1;
+  P.level_fronts.assign(P.nlevels, {});
+  for (int q = 0; q < nf; ++q) P.level_fronts[P.fg[q].level].push_back(q);
+  P.level_front_begin.assign(P.nlevels, 0);
+  P.level_front_end.assign(P.nlevels, 0);
+  int64_t off = 0;
+  for (int l = P.nlevels - 1; l >= 0; --l) {
+    P.level_front_begin[l] = off;
+    for (int q : P.level_fronts[l]) {
+      P.fg[q].off = off;
+      off += (int64_t)P.fg[q].nhat * P.fg[q].nhat;
+    }
+    P.level_front_end[l] = off;
+  }
+  P.front_total = off;
+  P.max_children = 0;
+  for (int q = 0; q < nf; ++q) P.max_children = std::max(P.max_children, (int)sys->h_children[q].size());
+
+  // ---------------------------------------------------------------- HODLR fronts
+  P.hf.clear();
+  P.bo_total = P.w_total = P.t_total = P.p_total = 0;
+  P.core_total = P.piv_total = P.comp_total = P.tb_total = 0;
+  P.nrank = 0;
+  std::vector<int64_t> level_bo_begin(P.nlevels, 0), level_bo_end(P.nlevels, 0);
+  for (int l = P.nlevels - 1; l >= 0; --l) {
+    level_bo_begin[l] = P.bo_total;
+    for (int q : P.level_fronts[l]) {
+      FrontGeom& g = P.fg[q];
+      if (g.np <= o.n_c) continue;
+      if (g.np < 2) continue;
+      HFront h;
+      h.q = q;
+      h.np = g.np;
+      h.nu = g.nu;
+      h.L = hodlr_depth(g.np, o.hodlr_leaf);
+      h.kf = g.nu > 0 ? std::min(S, std::min(g.nu, g.np)) : 0;
+      // node ranges level by level
+      std::vector<std::pair<int, int>> ranges = {{0, g.np}};
+      h.kl.assign(h.L, 0);
+      for (int lv = 0; lv < h.L; ++lv) {
+        std::vector<std::pair<int, int>> next;
+        for (size_t j = 0; j < ranges.size(); ++j) {
+          const int lo = ranges[j].first, hi = ranges[j].second;
+          const int mid = lo + (hi - lo) / 2;
+          HNodeGeom nd;
+          nd.level = lv;
+          nd.index = (int)j;
+          nd.lo = lo; nd.mid = mid; nd.hi = hi;
+          nd.kb = std::min(S, std::min(mid - lo, hi - mid));
+          h.kl[lv] = std::max(h.kl[lv], nd.kb);
+          h.nodes.push_back(nd);
+          next.push_back({lo, mid});
+          next.push_back({mid, hi});
+        }
+        ranges.swap(next);
+      }
+      for (auto& r : ranges) { h.leaf_lo.push_back(r.first); h.leaf_hi.push_back(r.second); }
+      h.col.assign(h.L + 1, 0);
+      h.col[0] = h.kf;
+      for (int lv = 0; lv < h.L; ++lv) h.col[lv + 1] = h.col[lv] + h.kl[lv];
+      h.xc = h.col[h.L];
+      h.bo_off = P.bo_total;
+      P.bo_total += (int64_t)h.np * h.xc;
+      h.w_off = P.w_total;
+      P.w_total += (int64_t)h.nu * h.kf;
+      h.t_off = P.t_total;
+      P.t_total += (int64_t)h.kf * h.kf;
+      h.p_off = P.p_total;
+      P.p_total += (int64_t)h.nu * h.kf;
+      h.rank_slot_f = P.nrank++;
+      // F_fp compression scratch
+      const int kf = h.kf;
+      h.fom_off = P.comp_total; P.comp_total += (int64_t)h.np * kf;
+      h.fy_off = P.comp_total; P.comp_total += (int64_t)h.nu * kf;
+      h.fz_off = P.comp_total; P.comp_total += (int64_t)h.np * kf;
+      h.fr_off = P.comp_total; P.comp_total += (int64_t)kf * kf;
+      h.fuhs_off = P.comp_total; P.comp_total += (int64_t)kf * kf;
+      h.fvh_off = P.comp_total; P.comp_total += (int64_t)kf * kf;
+      for (auto& nd : h.nodes) {
+        const int k = h.kl[nd.level];
+        const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid, kb = nd.kb;
+        nd.core_off = P.core_total; P.core_total += (int64_t)(2 * k) * (2 * k);
+        nd.piv_off = P.piv_total; P.piv_total += 2 * k;
+        nd.rank_slot = P.nrank++;
+        nd.om_off = P.comp_total; P.comp_total += (int64_t)nb * kb;
+        nd.y_off = P.comp_total; P.comp_total += (int64_t)na * kb;
+        nd.z_off = P.comp_total; P.comp_total += (int64_t)nb * kb;
+        nd.r_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
+        nd.uhs_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
+        nd.vh_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
+        nd.tb_off = P.tb_total; P.tb_total += (int64_t)(2 * k) * h.col[nd.level];
+      }
+      g.hodlr = (int)P.hf.size();
+      P.hf.push_back(std::move(h));
+    }
+    level_bo_end[l] = P.bo_total;
+  }
+
+  // ---------------------------------------------------------------- capacity checks
+  for (int q = 0; q < nf; ++q) {
+    const FrontGeom& g = P.fg[q];
+    if (g.hodlr < 0 && g.np > 128) {
+      set_last_error("dense pivot block larger than 128 (lower n_c)");
+      return HM_ERR_CAPACITY;
+    }
+  }
+
+  // ---------------------------------------------------------------- allocations
+  auto A = [&](void** p, int64_t elems, int size) -> int {
+    return dev_alloc(sys, p, (size_t)std::max<int64_t>(elems, 1) * size);
+  };
+  HM_TRY(A(&sys->d_front, P.front_total, es));
+  HM_TRY(A(&sys->d_bo, P.bo_total, es));
+  HM_TRY(A(&sys->d_x, P.bo_total, es));
+  HM_TRY(A(&sys->d_w, P.w_total, es));
+  HM_TRY(A(&sys->d_tm, P.t_total, es));
+  HM_TRY(A(&sys->d_pm, P.p_total, es));
+  HM_TRY(A(&sys->d_core, P.core_total, es));
+  HM_TRY(A((void**)&sys->d_piv, P.piv_total, 4));
+  HM_TRY(A(&sys->d_comp, P.comp_total, es));
+  HM_TRY(A(&sys->d_tb, P.tb_total, es));
+  HM_TRY(A((void**)&sys->d_ranks, P.nrank, 4));
+  HM_TRY(A((void**)&sys->d_pvals, sys->nnz, 8));
+  HM_TRY(A((void**)&P.d_front_off, nf, 8));
+  HM_TRY(A((void**)&P.d_nhat, nf, 4));
+  HM_TRY(A((void**)&P.d_np, nf, 4));
+  HM_TRY(A((void**)&P.d_hkind, nf, 4));
+  {
+    std::vector<int64_t> fo(nf);
+    std::vector<int> nh(nf), npv(nf), hk(nf);
+    for (int q = 0; q < nf; ++q) {
+      fo[q] = P.fg[q].off; nh[q] = P.fg[q].nhat; npv[q] = P.fg[q].np; hk[q] = P.fg[q].hodlr;
+    }
+    cudaStream_t s = sys->ctx->stream;
+    HM_CUDA(cudaMemcpyAsync(P.d_front_off, fo.data(), nf * 8, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(P.d_nhat, nh.data(), nf * 4, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(P.d_np, npv.data(), nf * 4, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(P.d_hkind, hk.data(), nf * 4, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ---------------------------------------------------------------- factor tasks
+  void* F = sys->d_front;
+  void* Bo = sys->d_bo;
+  void* X = sys->d_x;
+  void* W = sys->d_w;
+  void* Tm = sys->d_tm;
+  void* Pm = sys->d_pm;
+  void* Cm = sys->d_core;
+  void* Cp = sys->d_comp;
+  void* Tb = sys->d_tb;
+  int* piv = sys->d_piv;
+  int* ranks = sys->d_ranks;
+  TaskBuf& tb = P.tb;
+  tb.host.clear();
+  P.levels.assign(P.nlevels, LevelFactorPlan());
+  double fbytes = 0;
+  for (int l = P.nlevels - 1; l >= 0; --l) {
+    LevelFactorPlan& lp = P.levels[l];
+    const auto& fr = P.level_fronts[l];
+    // extend-add items per child slot
+    int slots = 0;
+    for (int q : fr) slots = std::max(slots, (int)sys->h_children[q].size());
+    for (int s = 0; s < slots; ++s) {
+      std::vector<EaItem> items;
+      for (int q : fr) {
+        const auto& ch = sys->h_children[q];
+        if (s >= (int)ch.size()) continue;
+        const int c = ch[s];
+        for (int col = 0; col < P.fg[c].nu; ++col) items.push_back(EaItem{c, col});
+      }
+      lp.ea_slots.push_back(tb.add(items));
+    }
+    // dense fronts
+    std::vector<PotrfTask> pot;
+    std::vector<TrsmTask> trs;
+    std::vector<GemmTask> syrk;
+    for (int q : fr) {
+      const FrontGeom& g = P.fg[q];
+      if (g.hodlr >= 0) continue;
+      lp.n_dense++;
+      void* Fq = at(F, g.off, es);
+      pot.push_back(PotrfTask{Fq, g.np, g.nhat, q, 0});
+      lp.potrf_maxn = std::max(lp.potrf_maxn, g.np);
+      if (g.nu > 0) {
+        for (int r0 = 0; r0 < g.nu; r0 += 64)
+          trs.push_back(TrsmTask{Fq, at(F, g.off + g.np, es), g.np, g.nhat, g.nu, g.nhat, r0, 0});
+        lp.trsm_maxn = std::max(lp.trsm_maxn, g.np);
+        syrk.push_back(gemm(at(F, g.off + g.np, es), g.nhat, 0, at(F, g.off + g.np, es), g.nhat, 1,
+                            at(F, g.off + g.np + (int64_t)g.np * g.nhat, es), g.nhat, g.nu, g.nu,
+                            g.np, -1.0, 1.0, 1));
+      }
+      fbytes += 2.0 * es * ((double)g.np * (g.np + 1) / 2 + (double)g.nu * g.np);
+    }
+    lp.potrf = tb.add(pot);
+    lp.trsm = tb.add(trs);
+    lp.syrk = tb.add_gemm(syrk);
+    // HODLR fronts
+    std::vector<OmegaTask> om;
+    std::vector<GemmTask> gy, gz, gu, gv;
+    std::vector<QrTask> qy, qz;
+    std::vector<SvdTask> sv;
+    std::vector<PotrfTask> lpot;
+    std::vector<CholSolveTask> lsol;
+    std::vector<GemmTask> sT, sP, sF;
+    int maxL = 0;
+    for (int q : fr) {
+      const FrontGeom& g = P.fg[q];
+      if (g.hodlr < 0) continue;
+      lp.n_hodlr++;
+      const HFront& h = P.hf[g.hodlr];
+      maxL = std::max(maxL, h.L);
+      const int np = h.np, nu = h.nu, nh = g.nhat;
+      const int64_t fo = g.off;
+      // pivot-block off-diagonal blocks: B = K[a, b] = K[b, a]^T (lower storage)
+      for (const auto& nd : h.nodes) {
+        const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid, kb = nd.kb, k = h.kl[nd.level];
+        const uint64_t blk = block_id(q, 0, nd.level, nd.index);
+        void* Kba = at(F, fo + nd.mid + (int64_t)nd.lo * nh, es);  // nb x na
+        om.push_back(OmegaTask{at(Cp, nd.om_off, es), blk, nb, kb, nb, 0});
+        gy.push_back(gemm(Kba, nh, 1, at(Cp, nd.om_off, es), nb, 0, at(Cp, nd.y_off, es), na, na, kb,
+                          nb, 1.0, 0.0));
+        qy.push_back(QrTask{at(Cp, nd.y_off, es), nullptr, na, kb, na, 0});
+        gz.push_back(gemm(Kba, nh, 0, at(Cp, nd.y_off, es), na, 0, at(Cp, nd.z_off, es), nb, nb, kb,
+                          na, 1.0, 0.0));
+        qz.push_back(QrTask{at(Cp, nd.z_off, es), at(Cp, nd.r_off, es), nb, kb, nb, 0});
+        sv.push_back(SvdTask{at(Cp, nd.r_off, es), at(Cp, nd.uhs_off, es), at(Cp, nd.vh_off, es),
+                             ranks + nd.rank_slot, kb, 0});
+        lp.svd_maxk = std::max(lp.svd_maxk, kb);
+        const int64_t colo = (int64_t)h.col[nd.level] * np;
+        gu.push_back(gemm(at(Cp, nd.y_off, es), na, 0, at(Cp, nd.uhs_off, es), kb, 0,
+                          at(Bo, h.bo_off + colo + nd.lo, es), np, na, kb, kb, 1.0, 0.0));
+        gv.push_back(gemm(at(Cp, nd.z_off, es), nb, 0, at(Cp, nd.vh_off, es), kb, 0,
+                          at(Bo, h.bo_off + colo + nd.mid, es), np, nb, kb, kb, 1.0, 0.0));
+        fbytes += es * (2.0 * (na + nb) * k * 2 + 4.0 * k * k);
+      }
+      if (nu > 0 && h.kf > 0) {
+        const int kf = h.kf;
+        const uint64_t blk = block_id(q, 1, 0, 0);
+        void* Ffp = at(F, fo + np, es);  // nu x np, ld nh
+        om.push_back(OmegaTask{at(Cp, h.fom_off, es), blk, np, kf, np, 0});
+        gy.push_back(gemm(Ffp, nh, 0, at(Cp, h.fom_off, es), np, 0, at(Cp, h.fy_off, es), nu, nu, kf,
+                          np, 1.0, 0.0));
+        qy.push_back(QrTask{at(Cp, h.fy_off, es), nullptr, nu, kf, nu, 0});
+        gz.push_back(gemm(Ffp, nh, 1, at(Cp, h.fy_off, es), nu, 0, at(Cp, h.fz_off, es), np, np, kf,
+                          nu, 1.0, 0.0));
+        qz.push_back(QrTask{at(Cp, h.fz_off, es), at(Cp, h.fr_off, es), np, kf, np, 0});
+        sv.push_back(SvdTask{at(Cp, h.fr_off, es), at(Cp, h.fuhs_off, es), at(Cp, h.fvh_off, es),
+                             ranks + h.rank_slot_f, kf, 0});
+        lp.svd_maxk = std::max(lp.svd_maxk, kf);
+        gu.push_back(gemm(at(Cp, h.fy_off, es), nu, 0, at(Cp, h.fuhs_off, es), kf, 0,
+                          at(W, h.w_off, es), nu, nu, kf, kf, 1.0, 0.0));
+        gv.push_back(gemm(at(Cp, h.fz_off, es), np, 0, at(Cp, h.fvh_off, es), kf, 0,
+                          at(Bo, h.bo_off, es), np, np, kf, kf, 1.0, 0.0));
+        // Schur complement: T = Vf^T Vtilde, P = W T, F_ff -= P W^T
+        sT.push_back(gemm(at(Bo, h.bo_off, es), np, 1, at(X, h.bo_off, es), np, 0, at(Tm, h.t_off, es),
+                          kf, kf, kf, np, 1.0, 0.0));
+        sP.push_back(gemm(at(W, h.w_off, es), nu, 0, at(Tm, h.t_off, es), kf, 0, at(Pm, h.p_off, es), nu,
+                          nu, kf, kf, 1.0, 0.0));
+        sF.push_back(gemm(at(Pm, h.p_off, es), nu, 0, at(W, h.w_off, es), nu, 1,
+                          at(F, fo + np + (int64_t)np * nh, es), nh, nu, nu, kf, -1.0, 1.0, 1));
+        fbytes += es * 4.0 * (double)(np + nu) * kf;
+      }
+      for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
+        const int lo = h.leaf_lo[li], n = h.leaf_hi[li] - lo;
+        void* Lq = at(F, fo + lo + (int64_t)lo * nh, es);
+        lpot.push_back(PotrfTask{Lq, n, nh, q, 0});
+        lp.leaf_maxn = std::max(lp.leaf_maxn, n);
+        if (h.xc > 0) lsol.push_back(CholSolveTask{Lq, at(X, h.bo_off + lo, es), n, nh, np, h.xc});
+        fbytes += es * (double)n * (n + 1) / 2;
+      }
+    }
+    lp.omega = tb.add(om);
+    lp.sampY = tb.add_gemm(gy);
+    lp.qrY = tb.add(qy);
+    lp.sampZ = tb.add_gemm(gz);
+    lp.qrZ = tb.add(qz);
+    lp.svd = tb.add(sv);
+    lp.formU = tb.add_gemm(gu);
+    lp.formV = tb.add_gemm(gv);
+    lp.x_copy_off = level_bo_begin[l];
+    lp.x_copy_len = level_bo_end[l] - level_bo_begin[l];
+    lp.leaf_potrf = tb.add(lpot);
+    lp.leaf_solve = tb.add(lsol);
+    // Woodbury levels, bottom-up (height 1 = parents of the leaves)
+    for (int ht = 1; ht <= maxL; ++ht) {
+      std::vector<GemmTask> pre, upd;
+      std::vector<CoreLuTask> lu;
+      std::vector<LuSolveTask> lus;
+      int lus_max = 0;
+      for (int q : fr) {
+        const FrontGeom& g = P.fg[q];
+        if (g.hodlr < 0) continue;
+        const HFront& h = P.hf[g.hodlr];
+        if (h.L < ht) continue;
+        const int lv = h.L - ht;
+        const int np = h.np, k = h.kl[lv], A_ = h.col[lv];
+        const int64_t colo = (int64_t)h.col[lv] * np;
+        for (const auto& nd : h.nodes) {
+          if (nd.level != lv) continue;
+          const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid;
+          void* core = at(Cm, nd.core_off, es);
+          void* Ua = at(Bo, h.bo_off + colo + nd.lo, es);
+          void* Vb = at(Bo, h.bo_off + colo + nd.mid, es);
+          void* Uh = at(X, h.bo_off + colo + nd.lo, es);
+          void* Vh = at(X, h.bo_off + colo + nd.mid, es);
+          pre.push_back(gemm(Ua, np, 1, Uh, np, 0, core, 2 * k, k, k, na, 1.0, 0.0));
+          pre.push_back(gemm(Vb, np, 1, Vh, np, 0, at(Cm, nd.core_off + (int64_t)k * 2 * k + k, es),
+                             2 * k, k, k, nb, 1.0, 0.0));
+          lu.push_back(CoreLuTask{core, piv + nd.piv_off, k, q});
+          if (A_ > 0) {
+            void* tbuf = at(Tb, nd.tb_off, es);
+            pre.push_back(gemm(Ua, np, 1, at(X, h.bo_off + nd.lo, es), np, 0, tbuf, 2 * k, k, A_, na,
+                               1.0, 0.0));
+            pre.push_back(gemm(Vb, np, 1, at(X, h.bo_off + nd.mid, es), np, 0,
+                               at(Tb, nd.tb_off + k, es), 2 * k, k, A_, nb, 1.0, 0.0));
+            lus.push_back(LuSolveTask{core, piv + nd.piv_off, tbuf, 2 * k, 2 * k, A_, 0});
+            lus_max = std::max(lus_max, A_);
+            upd.push_back(gemm(Uh, np, 0, tbuf, 2 * k, 0, at(X, h.bo_off + nd.lo, es), np, na, A_, k,
+                               -1.0, 1.0));
+            upd.push_back(gemm(Vh, np, 0, at(Tb, nd.tb_off + k, es), 2 * k, 0,
+                               at(X, h.bo_off + nd.mid, es), np, nb, A_, k, -1.0, 1.0));
+          }
+        }
+      }
+      LevelFactorPlan::Height H;
+      H.pre = tb.add_gemm(pre);
+      H.lu = tb.add(lu);
+      H.lus = tb.add(lus);
+      H.lus_maxcols = lus_max;
+      H.upd = tb.add_gemm(upd);
+      lp.heights.push_back(H);
+    }
+    lp.schurT = tb.add_gemm(sT);
+    lp.schurP = tb.add_gemm(sP);
+    lp.schurF = tb.add_gemm(sF);
+  }
+  P.factor_bytes = fbytes;
+  HM_TRY(dev_alloc(sys, (void**)&P.d_tasks, std::max<size_t>(tb.host.size(), 16)));
+  HM_CUDA(cudaMemcpyAsync(P.d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
+                          sys->ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
+  return HM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Solve plan for nrhs right-hand sides.
+// ------------------------------------------------------------------------------------
+int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
+  auto it = sys->solve_plans.find(nrhs);
+  if (it != sys->solve_plans.end()) { *out = it->second.get(); return HM_OK; }
+  Plan& P = sys->plan;
+  const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
+  const int nf = sys->nf;
+  std::unique_ptr<SolvePlan> sp(new SolvePlan());
+  sp->nrhs = nrhs;
+  sp->fv_off.assign(nf, 0);
+  int64_t fv = 0;
+  for (int q = 0; q < nf; ++q) { sp->fv_off[q] = fv; fv += (int64_t)P.fg[q].nhat * nrhs; }
+  sp->fv_total = fv;
+  // scratch: per HODLR node 2k x nrhs, per HODLR front kf x nrhs
+  std::vector<std::vector<int64_t>> node_sb(P.hf.size());
+  std::vector<int64_t> front_sb(P.hf.size());
+  int64_t sb = 0;
+  for (size_t i = 0; i < P.hf.size(); ++i) {
+    const HFront& h = P.hf[i];
+    for (const auto& nd : h.nodes) { node_sb[i].push_back(sb); sb += (int64_t)2 * h.kl[nd.level] * nrhs; }
+    front_sb[i] = sb;
+    sb += (int64_t)h.kf * nrhs;
+  }
+  sp->sb_total = sb;
+  HM_TRY(dev_alloc(sys, &sp->d_fv, (size_t)std::max<int64_t>(fv, 1) * es));
+  HM_TRY(dev_alloc(sys, &sp->d_sb, (size_t)std::max<int64_t>(sb, 1) * es));
+  HM_TRY(dev_alloc(sys, (void**)&sp->d_fvoff, (size_t)nf * 8));
+  HM_CUDA(cudaMemcpyAsync(sp->d_fvoff, sp->fv_off.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
+                          sys->ctx->stream));
+  void* F = sys->d_front;
+  void* Bo = sys->d_bo;
+  void* X = sys->d_x;
+  void* W = sys->d_w;
+  void* Cm = sys->d_core;
+  int* piv = sys->d_piv;
+  void* FV = sp->d_fv;
+  void* SB = sp->d_sb;
+  TaskBuf& tb = sp->tb;
+  sp->levels.assign(P.nlevels, LevelSolvePlan());
+  for (int l = 0; l < P.nlevels; ++l) {
+    LevelSolvePlan& lp = sp->levels[l];
+    const auto& fr = P.level_fronts[l];
+    lp.fronts = tb.add(fr);
+    lp.nfronts = (int)fr.size();
+    std::vector<CholSolveTask> leaf;
+    std::vector<GemmTask> f1, f2, d1, d2;
+    int maxL = 0;
+    for (int q : fr) {
+      const FrontGeom& g = P.fg[q];
+      if (g.hodlr < 0) continue;
+      const HFront& h = P.hf[g.hodlr];
+      maxL = std::max(maxL, h.L);
+      const int64_t fvq = sp->fv_off[q];
+      for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
+        const int lo = h.leaf_lo[li], n = h.leaf_hi[li] - lo;
+        leaf.push_back(CholSolveTask{at(F, g.off + lo + (int64_t)lo * g.nhat, es), at(FV, fvq + lo, es),
+                                     n, g.nhat, g.nhat, nrhs});
+        lp.leaf_maxn = std::max(lp.leaf_maxn, n);
+      }
+      if (h.kf > 0) {
+        void* tf = at(SB, front_sb[g.hodlr], es);
+        f1.push_back(gemm(at(Bo, h.bo_off, es), h.np, 1, at(FV, fvq, es), g.nhat, 0, tf, h.kf, h.kf,
+                          nrhs, h.np, 1.0, 0.0));
+        f2.push_back(gemm(at(W, h.w_off, es), h.nu, 0, tf, h.kf, 0, at(FV, fvq + h.np, es), g.nhat,
+                          h.nu, nrhs, h.kf, -1.0, 1.0));
+        d1.push_back(gemm(at(W, h.w_off, es), h.nu, 1, at(FV, fvq + h.np, es), g.nhat, 0, tf, h.kf,
+                          h.kf, nrhs, h.nu, 1.0, 0.0));
+        d2.push_back(gemm(at(X, h.bo_off, es), h.np, 0, tf, h.kf, 0, at(FV, fvq, es), g.nhat, h.np,
+                          nrhs, h.kf, -1.0, 1.0));
+      }
+    }
+    lp.leaf = tb.add(leaf);
+    for (int ht = 1; ht <= maxL; ++ht) {
+      std::vector<GemmTask> tt, upd;
+      std::vector<LuSolveTask> lus;
+      for (int q : fr) {
+        const FrontGeom& g = P.fg[q];
+        if (g.hodlr < 0) continue;
+        const HFront& h = P.hf[g.hodlr];
+        if (h.L < ht) continue;
+        const int lv = h.L - ht, k = h.kl[lv], np = h.np;
+        const int64_t colo = (int64_t)h.col[lv] * np, fvq = sp->fv_off[q];
+        for (size_t ni = 0; ni < h.nodes.size(); ++ni) {
+          const auto& nd = h.nodes[ni];
+          if (nd.level != lv) continue;
+          const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid;
+          void* sbn = at(SB, node_sb[g.hodlr][ni], es);
+          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.lo, es), np, 1, at(FV, fvq + nd.lo, es), g.nhat,
+                            0, sbn, 2 * k, k, nrhs, na, 1.0, 0.0));
+          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.mid, es), np, 1, at(FV, fvq + nd.mid, es),
+                            g.nhat, 0, at(SB, node_sb[g.hodlr][ni] + k, es), 2 * k, k, nrhs, nb, 1.0,
+                            0.0));
+          lus.push_back(LuSolveTask{at(Cm, nd.core_off, es), piv + nd.piv_off, sbn, 2 * k, 2 * k, nrhs, 0});
+          upd.push_back(gemm(at(X, h.bo_off + colo + nd.lo, es), np, 0, sbn, 2 * k, 0,
+                             at(FV, fvq + nd.lo, es), g.nhat, na, nrhs, k, -1.0, 1.0));
+          upd.push_back(gemm(at(X, h.bo_off + colo + nd.mid, es), np, 0,
+                             at(SB, node_sb[g.hodlr][ni] + k, es), 2 * k, 0, at(FV, fvq + nd.mid, es),
+                             g.nhat, nb, nrhs, k, -1.0, 1.0));
+        }
+      }
+      LevelSolvePlan::Height H;
+      H.t = tb.add_gemm(tt);
+      H.lus = tb.add(lus);
+      H.lus_maxcols = nrhs;
+      H.upd = tb.add_gemm(upd);
+      lp.heights.push_back(H);
+    }
+    lp.fin1 = tb.add_gemm(f1);
+    lp.fin2 = tb.add_gemm(f2);
+    lp.down1 = tb.add_gemm(d1);
+    lp.down2 = tb.add_gemm(d2);
+  }
+  HM_TRY(dev_alloc(sys, (void**)&sp->d_tasks, std::max<size_t>(tb.host.size(), 16)));
+  HM_CUDA(cudaMemcpyAsync(sp->d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
+                          sys->ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
+  *out = sp.get();
+  sys->solve_plans[nrhs] = std::move(sp);
+  return HM_OK;
+}
+
+}  // namespace hm

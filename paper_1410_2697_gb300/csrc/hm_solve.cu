@@ -1,0 +1,234 @@
+// hm_solve.cu -- preconditioner apply z = M^{-1} r: the multifrontal upward pass
+// (Eq. upward: b_f <- b_f - F_fp F_pp^-1 b_p, leaves to root) and downward pass
+// (Eq. downward: x_p = F_pp^-1 (b_p - F_pf x_f), root to leaves), with the HODLR pivot
+// solves and low-rank coupling blocks of Section 4.2.2 for HODLR fronts.
+//
+// Every front p owns a vector fv_p of length nhat_p = |I_p| + |I_p^f| (per RHS).  Upward:
+// fv_p = [r(I_p); 0] (+) children's update parts (extend-add of vectors, fixed child
+// order), then dense fronts run a column-oriented forward substitution over all nhat_p
+// rows (which also applies -L_fp z_p to the update part); HODLR fronts run y = F_pp^-1 b_p
+// and f <- f - W (Vf^T y).  Downward: x_f is gathered from the finished ancestors, dense
+// fronts solve L^T x_p = z_p - L_fp^T x_f, HODLR fronts x_p = y - Vtilde (W^T x_f) with
+// Vtilde = F_pp^-1 Vf kept by the factorization.
+#include "hm_internal.h"
+
+namespace hm {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_up(const int* __restrict__ fronts, int nrhs, int n,
+                                            const T* __restrict__ win, const int32_t* __restrict__ first,
+                                            const int* __restrict__ npiv, const int* __restrict__ nhat,
+                                            const int* __restrict__ hkind, const int64_t* __restrict__ front_off,
+                                            const int64_t* __restrict__ fvoff,
+                                            const int32_t* __restrict__ child_ptr,
+                                            const int32_t* __restrict__ child_list,
+                                            const int64_t* __restrict__ ifoff,
+                                            const int32_t* __restrict__ relmap, const T* __restrict__ F,
+                                            T* __restrict__ FV) {
+  const int q = fronts[blockIdx.x];
+  const int np = npiv[q], nh = nhat[q], nu = nh - np, b0 = first[q];
+  T* fv = FV + fvoff[q];
+  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
+    const int i = e % np, r = e / np;
+    fv[i + (int64_t)r * nh] = win[b0 + i + (int64_t)r * n];
+  }
+  for (int e = threadIdx.x; e < nu * nrhs; e += blockDim.x) {
+    const int t = e % nu, r = e / nu;
+    fv[np + t + (int64_t)r * nh] = T(0);
+  }
+  __syncthreads();
+  for (int ci = child_ptr[q]; ci < child_ptr[q + 1]; ++ci) {
+    const int c = child_list[ci];
+    const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
+    const T* fvc = FV + fvoff[c];
+    const int32_t* rm = relmap + ifoff[c];
+    for (int e = threadIdx.x; e < nuc * nrhs; e += blockDim.x) {
+      const int t = e % nuc, r = e / nuc;
+      fv[rm[t] + (int64_t)r * nh] += fvc[npc + t + (int64_t)r * nhc];
+    }
+    __syncthreads();
+  }
+  if (hkind[q] >= 0) return;
+  const T* L = F + front_off[q];
+  for (int j = 0; j < np; ++j) {
+    const T dj = L[j + (int64_t)j * nh];
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) fv[j + (int64_t)r * nh] /= dj;
+    __syncthreads();
+    const int rows = nh - j - 1;
+    for (int e = threadIdx.x; e < rows * nrhs; e += blockDim.x) {
+      const int i = j + 1 + e % rows, r = e / rows;
+      fv[i + (int64_t)r * nh] -= L[i + (int64_t)j * nh] * fv[j + (int64_t)r * nh];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_down(const int* __restrict__ fronts, int nrhs, int n,
+                                              T* __restrict__ xout, const int32_t* __restrict__ first,
+                                              const int* __restrict__ npiv, const int* __restrict__ nhat,
+                                              const int* __restrict__ hkind,
+                                              const int64_t* __restrict__ front_off,
+                                              const int64_t* __restrict__ fvoff,
+                                              const int64_t* __restrict__ ifoff,
+                                              const int32_t* __restrict__ iflist, const T* __restrict__ F,
+                                              T* __restrict__ FV) {
+  const int q = fronts[blockIdx.x];
+  const int np = npiv[q], nh = nhat[q], nu = nh - np, b0 = first[q];
+  T* fv = FV + fvoff[q];
+  const int32_t* If = iflist + ifoff[q];
+  for (int e = threadIdx.x; e < nu * nrhs; e += blockDim.x) {
+    const int t = e % nu, r = e / nu;
+    fv[np + t + (int64_t)r * nh] = xout[If[t] + (int64_t)r * n];
+  }
+  __syncthreads();
+  if (hkind[q] >= 0) return;
+  const T* L = F + front_off[q];
+  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
+    const int j = e % np, r = e / np;
+    const T* lc = L + np + (int64_t)j * nh;
+    const T* xf = fv + np + (int64_t)r * nh;
+    T s = T(0);
+    for (int t = 0; t < nu; ++t) s += lc[t] * xf[t];
+    fv[j + (int64_t)r * nh] -= s;
+  }
+  __syncthreads();
+  for (int j = np - 1; j >= 0; --j) {
+    const T dj = L[j + (int64_t)j * nh];
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) fv[j + (int64_t)r * nh] /= dj;
+    __syncthreads();
+    for (int e = threadIdx.x; e < j * nrhs; e += blockDim.x) {
+      const int i = e % j, r = e / j;
+      fv[i + (int64_t)r * nh] -= L[j + (int64_t)i * nh] * fv[j + (int64_t)r * nh];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
+    const int i = e % np, r = e / np;
+    xout[b0 + i + (int64_t)r * n] = fv[i + (int64_t)r * nh];
+  }
+}
+
+// HODLR fronts: x_p (already y - Vtilde W^T x_f in fv) -> output vector.
+template <typename T>
+__global__ void k_hodlr_out(const int* __restrict__ fronts, int nrhs, int n, T* __restrict__ xout,
+                            const int32_t* __restrict__ first, const int* __restrict__ npiv,
+                            const int* __restrict__ nhat, const int* __restrict__ hkind,
+                            const int64_t* __restrict__ fvoff, const T* __restrict__ FV) {
+  const int q = fronts[blockIdx.x];
+  if (hkind[q] < 0) return;
+  const int np = npiv[q], nh = nhat[q], b0 = first[q];
+  const T* fv = FV + fvoff[q];
+  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
+    const int i = e % np, r = e / np;
+    xout[b0 + i + (int64_t)r * n] = fv[i + (int64_t)r * nh];
+  }
+}
+
+template <typename T>
+static void gemm_b(const GemmBatch& b, const unsigned char* base, cudaStream_t s) {
+  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, s);
+}
+
+template <typename T>
+static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
+  SolvePlan* sp = nullptr;
+  HM_TRY(get_solve_plan(sys, nrhs, &sp));
+  Plan& P = sys->plan;
+  cudaStream_t s = sys->ctx->stream;
+  const unsigned char* base = sp->d_tasks;
+  const T* F = (const T*)sys->d_front;
+  T* FV = (T*)sp->d_fv;
+  const int n = sys->n;
+  for (int l = P.nlevels - 1; l >= 0; --l) {
+    const LevelSolvePlan& lp = sp->levels[l];
+    k_up<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, win, sys->d_first, P.d_np,
+                                       P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
+                                       sys->d_child_ptr, sys->d_child_list, sys->d_ifoff,
+                                       sys->d_relmap, F, FV);
+    launch_chol_solve<T>(lp.leaf.dev(base), lp.leaf.count, lp.leaf_maxn, s);
+    for (const auto& H : lp.heights) {
+      gemm_b<T>(H.t, base, s);
+      launch_lu_solve<T>(H.lus.dev(base), H.lus.count, H.lus_maxcols, s);
+      gemm_b<T>(H.upd, base, s);
+    }
+    gemm_b<T>(lp.fin1, base, s);
+    gemm_b<T>(lp.fin2, base, s);
+  }
+  for (int l = 0; l < P.nlevels; ++l) {
+    const LevelSolvePlan& lp = sp->levels[l];
+    k_down<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first, P.d_np,
+                                         P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
+                                         sys->d_ifoff, sys->d_iflist, F, FV);
+    gemm_b<T>(lp.down1, base, s);
+    gemm_b<T>(lp.down2, base, s);
+    k_hodlr_out<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first,
+                                              P.d_np, P.d_nhat, P.d_hkind, sp->d_fvoff, FV);
+  }
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT) {
+  if (sys->precision == HM_PREC_FP64) return apply_t<double>(sys, nrhs, (const double*)rT, (double*)zT);
+  return apply_t<float>(sys, nrhs, (const float*)rT, (float*)zT);
+}
+
+// ------------------------------------------------------------------------------------
+// Permutations and casts.
+// ------------------------------------------------------------------------------------
+__global__ void k_permute_in(const double* src, double* dst, const int32_t* perm, int n, int nrhs) {
+  const int64_t total = (int64_t)n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n);
+    const int64_t r = e / n;
+    dst[e] = src[perm[i] + r * n];
+  }
+}
+
+__global__ void k_permute_out(const double* src, double* dst, const int32_t* perm, int n, int nrhs) {
+  const int64_t total = (int64_t)n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n);
+    const int64_t r = e / n;
+    dst[perm[i] + r * n] = src[e];
+  }
+}
+
+void launch_permute_in(const double* src, double* dst, const int32_t* perm, int n, int nrhs,
+                       cudaStream_t s) {
+  k_permute_in<<<1216, 256, 0, s>>>(src, dst, perm, n, nrhs);
+}
+void launch_permute_out(const double* src, double* dst, const int32_t* perm, int n, int nrhs,
+                        cudaStream_t s) {
+  k_permute_out<<<1216, 256, 0, s>>>(src, dst, perm, n, nrhs);
+}
+
+template <typename T>
+__global__ void k_cast_to(const double* src, T* dst, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+template <typename T>
+__global__ void k_cast_from(const T* src, double* dst, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+template <typename T>
+void launch_cast_to(const double* src, T* dst, int64_t count, cudaStream_t s) {
+  k_cast_to<T><<<1216, 256, 0, s>>>(src, dst, count);
+}
+template <typename T>
+void launch_cast_from(const T* src, double* dst, int64_t count, cudaStream_t s) {
+  k_cast_from<T><<<1216, 256, 0, s>>>(src, dst, count);
+}
+template void launch_cast_to<float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_cast_to<double>(const double*, double*, int64_t, cudaStream_t);
+template void launch_cast_from<float>(const float*, double*, int64_t, cudaStream_t);
+template void launch_cast_from<double>(const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace hm

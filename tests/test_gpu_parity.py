@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer stages (ordering, tree, frontal index sets, relative maps) must be bit-exact.
+Floating-point stages are compared with tolerances derived from the arithmetic:
+FP64 dense fronts to 1e-11 relative (rounding order only), FP32 to 2e-4 relative
+(single-precision factorization over a tree of depth <= 15), final GMRES solutions to
+||x - x*|| / ||x*|| <= 1e-8 after the relative residual reached 1e-10.
+"""
+import numpy as np
+import pytest
+
+from fixtures import hex_cube, lognormal_coefficients, p1_jittered, q1_square, rhs_uniform
+from oracle import dense_mf, gmres, hodlr, hodlr_mf, nd, symbolic
+
+pytestmark = pytest.mark.gpu
+
+hm = pytest.importorskip("paper_1410_2697_gb300")
+
+
+def problems():
+    return {
+        "q1_64": q1_square(64),
+        "q1_33_lognormal": q1_square(33, lognormal_coefficients(33 * 33, 1.0, seed=1)),
+        "hex_9": hex_cube(9, lognormal_coefficients(9 ** 3, 0.5, seed=3)),
+        "p1_37": p1_jittered(37, seed=5),
+        "tiny": q1_square(3),
+    }
+
+
+PROBLEMS = problems()
+
+
+def make(p, precision, nd_leaf=64, hodlr_leaf=64, n_c=64, samples=48):
+    return hm.Solver(p.n, p.rowptr, p.colidx, grid_coords=p.coords, dim=p.dim, precision=precision,
+                     nd_leaf=nd_leaf, hodlr_leaf=hodlr_leaf, n_c=n_c, samples=samples)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("leaf", [64, 8])
+def test_ordering_and_symbolic_bit_exact(name, leaf):
+    p = PROBLEMS[name]
+    et = nd.nested_dissection(p.coords, leaf)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    s = make(p, hm.HM_PREC_FP64, nd_leaf=leaf)
+    perm, first, parent, level = hm.hm_get_ordering(s.sys)
+    assert np.array_equal(perm, et.perm)
+    assert np.array_equal(first, et.first)
+    assert np.array_equal(parent, et.parent)
+    assert np.array_equal(level, et.level)
+    nupd, off, lst, rel = hm.hm_get_symbolic(s.sys)
+    for q in range(et.nfronts):
+        assert nupd[q] == len(sym.If[q])
+        assert np.array_equal(lst[off[q]:off[q + 1]], sym.If[q]), q
+        if et.parent[q] >= 0:
+            assert np.array_equal(rel[off[q]:off[q + 1]], sym.relmap[q]), q
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["q1_64", "hex_9", "p1_37", "tiny"])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
+def test_dense_fronts_match_conventional_mf(name, prec, tol):
+    """All fronts dense (n_c above every pivot size): every Schur-complement update U_p
+    equals the oracle's conventional multifrontal update (Eqs. fbar, update)."""
+    p = PROBLEMS[name]
+    leaf = 16
+    et = nd.nested_dissection(p.coords, leaf)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    _, (F, U) = dense_mf.factor(Ap, et, sym, keep_fronts=True)
+    s = make(p, prec, nd_leaf=leaf, n_c=128)
+    s.factor(p.values, 0.0)
+    for q in range(et.nfronts):
+        nu = len(sym.If[q])
+        if nu == 0:
+            continue
+        Ug = hm.hm_get_update(s.sys, q, nu)
+        ref = np.tril(U[q])
+        err = np.abs(np.tril(Ug) - ref).max() / max(np.abs(ref).max(), 1e-300)
+        assert err <= tol, (q, err)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["q1_64", "q1_33_lognormal", "hex_9", "p1_37"])
+def test_tol0_hodlr_preconditioner_is_exact(name):
+    """FP64, HODLR fronts with every sampled direction kept and sketches as wide as the
+    blocks: the preconditioner is A^{-1} up to rounding."""
+    p = PROBLEMS[name]
+    s = make(p, hm.HM_PREC_FP64, nd_leaf=16, hodlr_leaf=8, n_c=8, samples=112)
+    info = s.factor(p.values, 0.0)
+    assert info["n_hodlr"] > 0
+    r = rhs_uniform(p.n, 3, 7)
+    z = np.zeros_like(r)
+    s.precond(r, z, nrhs=3)
+    A = p.scipy()
+    err = np.linalg.norm(A @ z - r) / np.linalg.norm(r)
+    assert err <= 1e-9, err
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["q1_64", "q1_33_lognormal", "hex_9"])
+def test_hodlr_updates_match_oracle_rrf(name):
+    """FP64 HODLR fronts compressed by the randomized range finder with the same
+    Philox sketch as the oracle: each update U_p agrees; ranks agree except where a
+    singular value sits at the truncation threshold (then by one, in <= 1% of fronts;
+    both truncations are correct and the updates still agree)."""
+    p = PROBLEMS[name]
+    leaf, hl, nc, k, tol = 16, 8, 8, 12, 1e-6
+    et = nd.nested_dissection(p.coords, leaf)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    prm = hodlr_mf.Params(tol=tol, n_c=nc, leaf=hl, compressor="rrf", samples=k, seed=0x5EED)
+    fr, trace = hodlr_mf.factor(Ap, et, sym, prm, keep=True)
+    s = make(p, hm.HM_PREC_FP64, nd_leaf=leaf, hodlr_leaf=hl, n_c=nc, samples=k)
+    s.factor(p.values, tol)
+    oranks = hodlr_mf.ranks(fr)
+    mismatched = 0
+    for q in range(et.nfronts):
+        kind, rk = hm.hm_get_front_ranks(s.sys, q)
+        assert kind == (1 if fr[q].kind == "hodlr" else 0)
+        if kind == 1:
+            expect = [oranks[q]["fp"]] + [r for (_, _, r) in oranks[q]["pp"]]
+            if list(rk) != expect:
+                mismatched += 1
+                assert np.abs(np.array(rk) - np.array(expect)).max() <= 1, (q, rk, expect)
+        nu = len(sym.If[q])
+        if nu == 0:
+            continue
+        Ug = hm.hm_get_update(s.sys, q, nu)
+        ref = np.tril(trace["U"][q])
+        err = np.abs(np.tril(Ug) - ref).max() / max(np.abs(ref).max(), 1e-300)
+        assert err <= 1e-8, (q, err)
+    assert mismatched <= max(1, len(oranks) // 100), mismatched
+    s.close()
+
+
+def _oracle_blocks(fr_q):
+    """(level, node) -> dense U V^T of the oracle's compressed blocks; -1 -> F_fp."""
+    out = {(-1, 0): fr_q.W @ fr_q.V.T}
+    for node in hodlr.iter_nodes(fr_q.H):
+        if node.children:
+            out[(node.level, node.index)] = node.U @ node.V.T
+    return out
+
+
+@pytest.mark.parametrize("name", ["q1_64", "hex_9", "p1_37"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_compressed_blocks_match_oracle_rrf(name, prec):
+    """Per-step parity of the randomized compression: every low-rank block U V^T of
+    every HODLR front (pivot-block off-diagonal blocks and F_fp) against the oracle's
+    range finder on the oracle's assembled front with the same sketch.  FP64: rounding
+    level; FP32: within a few times tol of the block (plus single-precision noise)."""
+    p = PROBLEMS[name]
+    leaf, hl, nc, k, tol = 64, 16, 16, 24, 1e-4
+    et = nd.nested_dissection(p.coords, leaf)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    prm = hodlr_mf.Params(tol=tol, n_c=nc, leaf=hl, compressor="rrf", samples=k, seed=0x5EED)
+    fr, _ = hodlr_mf.factor(Ap, et, sym, prm)
+    s = make(p, prec, nd_leaf=leaf, hodlr_leaf=hl, n_c=nc, samples=k)
+    s.factor(p.values, tol)
+    nblocks = 0
+    for q in range(et.nfronts):
+        if fr[q].kind != "hodlr":
+            continue
+        for (lv, nd_), Bo in _oracle_blocks(fr[q]).items():
+            if Bo.size == 0:
+                continue
+            U, V, r = hm.hm_get_hodlr_block(s.sys, q, lv, nd_)
+            err = np.linalg.norm(U @ V.T - Bo, 2) / max(np.linalg.norm(Bo, 2), 1e-300)
+            bound = 1e-10 if prec == 0 else 5 * tol + 1e-5
+            assert err <= bound, (q, lv, nd_, err)
+            nblocks += 1
+    assert nblocks > 0
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_gmres_solution_matches_oracle(name, prec):
+    p = PROBLEMS[name]
+    b = rhs_uniform(p.n, 2, 0)
+    xs = np.stack([dense_mf.direct_solve(p.rowptr, p.colidx, p.values, p.coords, b[:, c])
+                   for c in range(2)], 1)
+    s = make(p, prec, nd_leaf=64, hodlr_leaf=16, n_c=16, samples=32)
+    s.factor(p.values, 1e-6 if prec == 0 else 1e-4)
+    x = np.zeros_like(b)
+    x, info = s.solve(b, rtol=1e-10, max_iters=500, x=x)
+    assert info["converged"] == 1
+    A = p.scipy()
+    for c in range(2):
+        assert np.linalg.norm(b[:, c] - A @ x[:, c]) / np.linalg.norm(b[:, c]) <= 1e-10
+    err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+    assert err <= 1e-8, err
+    s.close()
+
+
+def test_gmres_iterations_close_to_oracle_on_poisson64():
+    """Configuration of the small workload: Q1 Poisson 64x64, FP64, tol 1e-6, one RHS."""
+    p = PROBLEMS["q1_64"]
+    b = rhs_uniform(p.n, 1, 0)
+    et = nd.nested_dissection(p.coords, 64)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    prm = hodlr_mf.Params(tol=1e-6, n_c=16, leaf=16, compressor="rrf", samples=32)
+    fr, _ = hodlr_mf.factor(Ap, et, sym, prm)
+    _, oinfo = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), b[:, 0][et.perm])
+    s = make(p, 0, nd_leaf=64, hodlr_leaf=16, n_c=16, samples=32)
+    s.factor(p.values, 1e-6)
+    x = np.zeros_like(b)
+    x, info = s.solve(b, x=x)
+    assert info["converged"] == 1
+    assert abs(info["iters"] - oinfo["iters"]) <= 1, (info, oinfo["iters"])
+    s.close()
+
+
+def test_multi_rhs_columns_equal_single_rhs():
+    p = PROBLEMS["q1_33_lognormal"]
+    b = rhs_uniform(p.n, 16, 3)
+    s = make(p, 1, nd_leaf=16, hodlr_leaf=16, n_c=16, samples=24)
+    s.factor(p.values, 1e-4)
+    x16 = np.zeros_like(b)
+    x16, info = s.solve(b, x=x16)
+    assert info["converged"] == 1
+    for c in [0, 7, 15]:
+        b1 = np.asfortranarray(b[:, c:c + 1])
+        x1 = np.zeros_like(b1)
+        x1, _ = s.solve(b1, x=x1)
+        assert np.linalg.norm(x1[:, 0] - x16[:, c]) / np.linalg.norm(x1[:, 0]) <= 1e-9
+    s.close()
