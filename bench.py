@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark of the HODLR-accelerated multifrontal preconditioner + GMRES on GB300.
+
+Workload: 2D Q1 diffusion on a 1024 x 1024 element grid (1,046,529 unknowns), lognormal
+element coefficient (mu 0, sigma 1, seed 1), HODLR truncation tol 1e-4, 16 right-hand
+sides U[-1, 1] (seed 2), GMRES(30) to relative residual 1e-10.
+
+A step is one pass of the whole path over one batch: nested-dissection analysis,
+HODLR-multifrontal factorization and the GMRES solve of all right-hand sides, through
+the C ABI (``hm_analyze`` / ``hm_factor`` / ``hm_solve`` / ``hm_destroy``).  ``value`` is
+solves per second (right-hand sides brought to rtol) with the inputs already resident in
+HBM; ``e2e`` is the same metric with the inputs in pinned host memory and the solution
+copied back, every step.  The FP64-plain path (the same method entirely in FP64) is
+measured beside the mixed-precision path (FP32 factor/apply, FP64 GMRES).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU (the method has no
+data-parallel exchange); the line reports the whole-job rate and max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to rel.resid 1e-10: mixed-prec HODLR-MF vs FP64 plain; p50/p99 ms"
+WORKLOAD = "q1_lognormal_1024x1024"
+RTOL = 1e-10
+MAX_ITERS = 4000
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--m", type=int, default=1024, help="elements per side (1024 = the workload)")
+    ap.add_argument("--n-c", type=int, default=64)
+    ap.add_argument("--hodlr-leaf", type=int, default=64)
+    ap.add_argument("--samples", type=int, default=48)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-out", default=None, help="write per-kernel profile JSON here")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ------------------------------------------------------------------------------------
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if _cuda() else "gloo")
+    return rank, world, local
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------
+# the mixed-precision / FP64 GPU arms
+# ------------------------------------------------------------------------------------
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def alu_peak_tflops(precision: str, sm_max_mhz: float | None) -> float:
+    """SIMT peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA;
+    FP64 is GB300's nominal 1.25 TFLOP/s."""
+    if precision == "f64":
+        return 1.25
+    mhz = sm_max_mhz or 2070.0
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+COMPUTE_CATS = {"gemm_factor", "gemm_apply", "dense_potrf", "dense_trsm", "householder_qr",
+                "jacobi_svd", "core_lu_inverse", "spd_inverse", "leaf_solve"}
+
+
+def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
+    cat = max(prof, key=lambda c: prof[c]["ms"])
+    e = prof[cat]
+    per_launch_ms = e["ms"] / max(e["launches"], 1)
+    if cat in COMPUTE_CATS:
+        achieved = (e["flops"] / max(e["launches"], 1)) / (per_launch_ms * 1e-3) / 1e12
+        peak = alu_peak_tflops(precision, (clocks or {}).get("sm_max_mhz"))
+        return {"kernel": cat, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "launches": e["launches"],
+                "avg_launch_ms": per_launch_ms, "share_of_profiled_time":
+                    e["ms"] / sum(v["ms"] for v in prof.values()),
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock" if precision != "f64"
+                else "nominal GB300 FP64 1.25 TFLOP/s"}
+    achieved = (e["bytes"] / max(e["launches"], 1)) / (per_launch_ms * 1e-3) / 1e9
+    peak = (peaks or {}).get("hbm_gbs") or 6800.0
+    return {"kernel": cat, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "launches": e["launches"],
+            "avg_launch_ms": per_launch_ms,
+            "share_of_profiled_time": e["ms"] / sum(v["ms"] for v in prof.values()),
+            "peak_source": "measured" if peaks else "fallback"}
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_1410_2697_gb300 as hm
+    from fixtures import lognormal_coefficients, q1_square, rhs_uniform
+
+    torch.cuda.set_device(local)
+    m = args.m
+    coef = lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=1)
+    P = q1_square(m, coef, name=f"q1_lognormal_{m}x{m}")
+    nrhs = args.nrhs
+    b = rhs_uniform(P.n, nrhs, 2)
+    tol = 1e-4
+    dev = torch.device("cuda", local)
+    d_rowptr = torch.from_numpy(P.rowptr).to(dev)
+    d_colidx = torch.from_numpy(P.colidx).to(dev)
+    d_values = torch.from_numpy(P.values).to(dev)
+    d_coords = torch.from_numpy(np.ascontiguousarray(P.coords)).to(dev)
+    d_b = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)  # (nrhs, n) = column-major n x nrhs
+    d_x = torch.zeros_like(d_b)
+    stream = torch.cuda.Stream(device=dev)
+
+    def make_ctx(precision):
+        o = hm.hm_default_opts()
+        o.device = local
+        o.precision = precision
+        o.nd_leaf = 64
+        o.hodlr_leaf = args.hodlr_leaf
+        o.n_c = args.n_c
+        o.samples = args.samples
+        o.restart = 30
+        o.stream = stream.cuda_stream
+        return hm.hm_create(o)
+
+    def step(ctx, rowptr, colidx, coords, values, bb, xx):
+        s = hm.hm_analyze(ctx, P.n, rowptr, colidx, 2, coords)
+        fi = hm.hm_factor(s, values, tol)
+        si = hm.hm_solve(s, nrhs, bb, RTOL, MAX_ITERS, xx)
+        hm.hm_destroy(s)
+        return fi, si
+
+    def timed(ctx, k, inputs, profile=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        barrier(world)
+        torch.cuda.synchronize()
+        if profile:
+            hm.hm_profile_enable(ctx, True)
+        infos = []
+        for i in range(k):
+            ev[i][0].record(stream)
+            infos.append(step(ctx, *inputs))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        per = [a.elapsed_time(z) for a, z in ev]
+        total = ev[0][0].elapsed_time(ev[-1][1])
+        prof = hm.hm_profile_read(ctx) if profile else None
+        if profile:
+            hm.hm_profile_enable(ctx, False)
+        return per, total, infos, prof
+
+    dev_inputs = (d_rowptr, d_colidx, d_coords, d_values, d_b, d_x)
+    # ---------------- mixed precision, device-resident inputs (the headline)
+    ctx = make_ctx(hm.HM_PREC_MIXED)
+    for _ in range(args.warmup):
+        step(ctx, *dev_inputs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    per, total, infos, prof = timed(ctx, args.steps, dev_inputs, profile=True)
+    clk = clocks.stop()
+    total_max = allreduce_max(total, world)
+    x = d_x.cpu().numpy().T
+    A = P.scipy()
+    relres = max(float(np.linalg.norm(b[:, c] - A @ x[:, c]) / np.linalg.norm(b[:, c])) for c in range(nrhs))
+
+    # ---------------- e2e: pinned host inputs, copies inside the timed region
+    def pinned(a):
+        t = torch.empty(a.shape, dtype={np.int64: torch.int64, np.int32: torch.int32,
+                                        np.float64: torch.float64}[a.dtype.type], pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+    h_inputs = (pinned(P.rowptr), pinned(P.colidx), pinned(np.ascontiguousarray(P.coords)),
+                pinned(P.values), pinned(np.ascontiguousarray(b.T)), pinned(np.zeros((nrhs, P.n))))
+    step(ctx, *h_inputs)
+    ke = max(1, min(args.steps, 3))
+    per_e, total_e, _, _ = timed(ctx, ke, h_inputs)
+    total_e = allreduce_max(total_e, world)
+    h2d = (P.rowptr.nbytes + P.colidx.nbytes + P.coords.astype(np.int32).nbytes + P.values.nbytes
+           + b.nbytes)
+    d2h = b.nbytes
+    hm.hm_ctx_destroy(ctx)
+
+    # ---------------- FP64 plain (same method entirely in FP64)
+    ctx64 = make_ctx(hm.HM_PREC_FP64)
+    step(ctx64, *dev_inputs)
+    k64 = max(1, args.fp64_steps)
+    per64, total64, infos64, _ = timed(ctx64, k64, dev_inputs)
+    total64 = allreduce_max(total64, world)
+    hm.hm_ctx_destroy(ctx64)
+
+    value = nrhs * args.steps * world / (total_max * 1e-3)
+    fi, si = infos[-1]
+    peaks = load_peaks()
+    rl = roofline(prof, "f32", peaks, clk)
+    kernels = sum(v["kernels"] for v in prof.values())
+    per_sorted = sorted(per)
+    p50 = statistics.median(per)
+    p99 = per_sorted[min(len(per_sorted) - 1, int(round(0.99 * (len(per_sorted) - 1))))]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 factor/apply + f64 GMRES",
+        "data": "synthetic",
+        "config": {"workload": f"q1_lognormal_{m}x{m}" if m != 1024 else WORKLOAD, "unknowns": P.n,
+                   "nnz": P.nnz, "nrhs": nrhs, "tol": tol, "rtol": RTOL, "restart": 30,
+                   "nd_leaf": 64, "hodlr_leaf": args.hodlr_leaf, "n_c": args.n_c,
+                   "samples": args.samples, "step": "analyze + factor + solve(nrhs) + destroy",
+                   "l2": "inputs larger than L2 (A: 139 MB CSR, fronts 1.4 GB)",
+                   "parallelism": f"replicas x{world}"},
+        "p50_ms": p50, "p99_ms": p99,
+        "gmres_iters": si["iters"], "relres": relres,
+        "factor": {"nfronts": fi["nfronts"], "n_hodlr": fi["n_hodlr"], "max_rank": fi["max_rank"],
+                   "rank_capped": fi["rank_capped"], "factor_bytes": fi["factor_bytes"]},
+        "fp64_plain": {"value": nrhs * k64 * world / (total64 * 1e-3), "ms_per_step": total64 / k64,
+                       "steps": k64, "gmres_iters": infos64[-1][1]["iters"]},
+        "roofline": rl,
+        "e2e": {"value": nrhs * ke * world / (total_e * 1e-3), "unit": "solves/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": ke},
+        "gpu_launches": int(kernels),
+        "clocks": clk,
+    }
+    line["speedup_vs_fp64_plain"] = line["value"] / line["fp64_plain"]["value"]
+    if args.profile_out and rank == 0:
+        json.dump({"mixed": prof}, open(args.profile_out, "w"), indent=1)
+    return line
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ------------------------------------------------------------------------------------
+def oracle_solve_once(m: int, rhs_cols: int):
+    """Time the oracle pipeline (ND, symbolic, HODLR-MF factor, GMRES per RHS) on the
+    q1 lognormal family with m x m elements.  Returns (seconds, solves, relres)."""
+    import numpy as np
+
+    from fixtures import lognormal_coefficients, q1_square, rhs_uniform
+    from oracle import dense_mf, gmres, hodlr_mf, nd, symbolic
+    coef = lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=1)
+    P = q1_square(m, coef)
+    b = rhs_uniform(P.n, rhs_cols, 2)
+    t0 = time.perf_counter()
+    et = nd.nested_dissection(P.coords, 64)
+    sym = symbolic.symbolic(P.rowptr, P.colidx, et)
+    Ap = dense_mf.permuted_matrix(P.rowptr, P.colidx, P.values, et)
+    fr, _ = hodlr_mf.factor(Ap, et, sym, hodlr_mf.Params(tol=1e-4, n_c=64, leaf=64))
+    worst = 0.0
+    for c in range(rhs_cols):
+        bn = b[:, c][et.perm]
+        x, info = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), bn, RTOL, 30)
+        worst = max(worst, info["relres"])
+    return time.perf_counter() - t0, rhs_cols, worst
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(m: int) -> dict:
+    sec, solves, rr = oracle_solve_once(m, 1)
+    return {"value": solves / sec, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"one of the 16 right-hand sides of the {m}x{m} workload: analyze + FP64 "
+                      f"HODLR-MF factor (SVD truncation) + GMRES to 1e-10 on the host, {sec:.1f} s "
+                      f"(BLAS threads = all cores); relres {rr:.1e}"}
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step a bounded sample of the
+    workload (a 128 x 128 grid of the same lognormal family, one right-hand side)."""
+    if rank != 0:
+        return None
+    m = 128
+    for _ in range(args.warmup):
+        oracle_solve_once(m, 1)
+    per = []
+    for _ in range(args.steps):
+        sec, _, rr = oracle_solve_once(m, 1)
+        per.append(sec * 1e3)
+    total = sum(per)
+    value = args.steps / (total * 1e-3)
+    sample = f"{m}x{m} grid of the same lognormal Q1 family ({(m - 1) ** 2} unknowns), 1 RHS per step"
+    return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "p50_ms": statistics.median(per), "relres_max": rr,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    # The host oracle runs before any GPU work in this process (no fork after CUDA init).
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.m)
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,22 @@ int hm_get_front_ranks(hm_sys_t sys, int32_t front, int32_t* kind, int32_t* rank
 int hm_get_hodlr_block(hm_sys_t sys, int32_t front, int32_t level, int32_t node, int32_t* m,
                        int32_t* n, int32_t* k, int32_t* rank, double* U, double* V);
 
+/* Launch profiler of a context.  While enabled, every kernel launch of the context's
+   systems is bracketed by CUDA events on the launching stream and tagged with a
+   category and its algorithmic work (minimum flops and HBM bytes of what it computes).
+   hm_profile_enable(ctx, 1) clears the records; hm_profile_read synchronizes and returns
+   one entry per category with launches, summed device time (ms), flops and bytes.   */
+typedef struct hm_prof_entry {
+  char name[24];
+  int32_t launches;      /* bracketed launch groups                                    */
+  int32_t kernels;       /* CUDA kernels inside them (copies and memsets count 0)      */
+  double ms;
+  double flops;
+  double bytes;
+} hm_prof_entry;
+int hm_profile_enable(hm_ctx_t ctx, int enable);
+int hm_profile_read(hm_ctx_t ctx, int32_t max_entries, hm_prof_entry* out, int32_t* n);
+
 int hm_destroy(hm_sys_t sys);
 
 const char* hm_status_str(int status);

@@ -30,7 +30,7 @@ HM_PREC_MIXED = 1
 
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_get_sizes",
             "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_solve", "hm_precond_apply",
-            "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_destroy", "hm_status_str", "hm_last_error"]
+            "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error"]
 
 
 class HmOpts(C.Structure):
@@ -49,6 +49,11 @@ class HmFactorInfo(C.Structure):
     _fields_ = [("nfronts", C.c_int32), ("nlevels", C.c_int32), ("n_hodlr", C.c_int32),
                 ("max_rank", C.c_int32), ("rank_capped", C.c_int32), ("factor_bytes", C.c_double),
                 ("front_bytes", C.c_double)]
+
+
+class HmProfEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int32), ("kernels", C.c_int32), ("ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
 
 
 class HmError(RuntimeError):
@@ -79,6 +84,8 @@ def _load():
     lib.hm_get_front_ranks.argtypes = [vp, i32, C.POINTER(i32), vp, C.POINTER(i32)]
     lib.hm_get_hodlr_block.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(i32),
                                        C.POINTER(i32), C.POINTER(i32), vp, vp]
+    lib.hm_profile_enable.argtypes = [vp, C.c_int]
+    lib.hm_profile_read.argtypes = [vp, i32, C.POINTER(HmProfEntry), C.POINTER(i32)]
     lib.hm_destroy.argtypes = [vp]
     lib.hm_status_str.argtypes = [C.c_int]
     lib.hm_status_str.restype = C.c_char_p
@@ -228,6 +235,20 @@ def hm_get_hodlr_block(sys_, front: int, level: int, node: int = 0):
                                    C.byref(k), C.byref(r), _ptr(U, np.float64, "U"),
                                    _ptr(V, np.float64, "V")), "hm_get_hodlr_block")
     return U, V, r.value
+
+
+def hm_profile_enable(ctx, enable: bool = True) -> None:
+    _check(_lib.hm_profile_enable(ctx, 1 if enable else 0), "hm_profile_enable")
+
+
+def hm_profile_read(ctx) -> dict:
+    """{category: {"launches", "ms", "flops", "bytes"}} since the last enable."""
+    buf = (HmProfEntry * 64)()
+    n = C.c_int32()
+    _check(_lib.hm_profile_read(ctx, 64, buf, C.byref(n)), "hm_profile_read")
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "kernels": buf[i].kernels, "ms": buf[i].ms,
+                                   "flops": buf[i].flops, "bytes": buf[i].bytes}
+            for i in range(n.value)}
 
 
 def hm_destroy(sys_) -> None:

@@ -619,13 +619,19 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_first_t, sizeof(int) * (cap + 1)));
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_parent_t, sizeof(int) * cap));
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_level_t, sizeof(int) * cap));
-    k_nd_tree<<<1, 1024, 0, s>>>(t, dim, e3, sys->ctx->opts.nd_leaf, cap, d_first_t, d_parent_t,
-                                 d_level_t, sys->d_err);
+    {
+      ProfScope ps(sys->ctx, PC_ND, Work{0.0, 64.0 * cap});
+      k_nd_tree<<<1, 1024, 0, s>>>(t, dim, e3, sys->ctx->opts.nd_leaf, cap, d_first_t, d_parent_t,
+                                   d_level_t, sys->d_err);
+    }
     int cnts[2];
     HM_CUDA(cudaMemcpyAsync(cnts, t.count, sizeof(cnts), cudaMemcpyDeviceToHost, s));
     HM_TRY(check_device_error(sys, "analyze: nested dissection"));
     nf = cnts[0];
-    k_nd_perm<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, lo0, t, sys->d_perm, sys->d_iperm);
+    {
+      ProfScope ps(sys->ctx, PC_ND, Work{0.0, (4.0 * dim + 8.0) * n});
+      k_nd_perm<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, lo0, t, sys->d_perm, sys->d_iperm);
+    }
     sys->h_first.resize(nf + 1);
     sys->h_parent.resize(nf);
     sys->h_level.resize(nf);
@@ -688,10 +694,13 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   HM_TRY(dev_alloc(sys, (void**)&sys->d_prowptr, sizeof(int64_t) * (n + 1)));
   HM_TRY(dev_alloc(sys, (void**)&sys->d_pcol, sizeof(int32_t) * sys->nnz));
   HM_TRY(dev_alloc(sys, (void**)&sys->d_psrc, sizeof(int64_t) * sys->nnz));
-  k_prow_len<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_perm, n, len);
-  exclusive_scan(len, sys->d_prowptr, bs, n, s);
-  k_prow_fill<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_colidx, sys->d_perm, sys->d_iperm,
-                                              sys->d_prowptr, n, sys->d_pcol, sys->d_psrc);
+  {
+    ProfScope ps(sys->ctx, PC_PERMUTE_CSR, Work{0.0, 32.0 * n + 16.0 * sys->nnz + 12.0 * sys->nnz}, 5);
+    k_prow_len<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_perm, n, len);
+    exclusive_scan(len, sys->d_prowptr, bs, n, s);
+    k_prow_fill<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_colidx, sys->d_perm, sys->d_iperm,
+                                                sys->d_prowptr, n, sys->d_pcol, sys->d_psrc);
+  }
   // symbolic, level by level (deepest first)
   int maxlev = 0;
   for (int q = 0; q < nf; ++q) maxlev = std::max(maxlev, sys->h_level[q]);
@@ -723,6 +732,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     for (int L = 0; L <= maxlev; ++L) {
       const int cntL = lvl_begin[L + 1] - lvl_begin[L];
       if (cntL == 0) continue;
+      ProfScope ps(sys->ctx, PC_SYMBOLIC, Work{});
       k_symbolic_level<<<cntL, 1024, kSymCap * sizeof(int), s>>>(
           d_order + lvl_begin[L], sys->d_first, sys->d_child_ptr, sys->d_child_list, sys->d_prowptr,
           sys->d_pcol, sys->d_nupd, sys->d_ifoff, sys->d_iflist, cursor, capacity, sys->d_err);
@@ -748,12 +758,18 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   sys->if_total = (int64_t)total;
   sys->h_ifoff[nf] = (int64_t)total;
   HM_TRY(dev_alloc(sys, (void**)&sys->d_relmap, sizeof(int32_t) * std::max<int64_t>(total, 1)));
-  k_relmap<<<nf, 256, 0, s>>>(sys->d_parent, sys->d_first, sys->d_nupd, sys->d_ifoff, sys->d_iflist, nf,
-                              sys->d_relmap, sys->d_err);
+  {
+    ProfScope ps(sys->ctx, PC_SYMBOLIC, Work{0.0, 12.0 * total});
+    k_relmap<<<nf, 256, 0, s>>>(sys->d_parent, sys->d_first, sys->d_nupd, sys->d_ifoff, sys->d_iflist, nf,
+                                sys->d_relmap, sys->d_err);
+  }
   HM_TRY(check_device_error(sys, "analyze: relative maps"));
   HM_TRY(build_plan(sys));
   HM_TRY(dev_alloc(sys, (void**)&sys->d_amap, sizeof(int64_t) * sys->nnz));
-  launch_amap(sys);
+  {
+    ProfScope ps(sys->ctx, PC_SYMBOLIC, Work{0.0, 24.0 * sys->nnz});
+    launch_amap(sys);
+  }
   return check_device_error(sys, "analyze: assembly map");
 }
 

@@ -29,7 +29,7 @@ int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t byt
                    std::to_string(ctx->opts.hbm_budget));
     return HM_ERR_OUT_OF_MEMORY;
   }
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -53,7 +53,7 @@ void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner) {
         break;
       }
     }
-    cudaFree(p);
+    cudaFreeAsync(p, ctx->stream);
   }
   owner->clear();
 }
@@ -77,6 +77,26 @@ int check_device_error(hm_sys_s* sys, const char* where) {
     return h[0];
   }
   return HM_OK;
+}
+
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+const char* prof_cat_name(int c) {
+  static const char* names[PC_COUNT] = {
+      "nd_order", "symbolic", "permute_csr", "scatter_A", "extend_add", "dense_potrf",
+      "dense_trsm", "gemm_factor", "sketch", "householder_qr", "jacobi_svd", "leaf_solve",
+      "core_lu_inverse", "spd_inverse", "apply_up", "apply_down", "gemm_apply", "spmv", "gmres_dots",
+      "gmres_gs_update", "gmres_small", "vector_ops", "memset"};
+  return (c >= 0 && c < PC_COUNT) ? names[c] : "?";
 }
 
 static void destroy_sys(hm_sys_s* sys) {
@@ -221,6 +241,22 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
     }
     ctx->own_stream = true;
   }
+  {
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = o.device;
+    if (cudaMemPoolCreate(&ctx->pool, &pp) != cudaSuccess) {
+      if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+      delete ctx;
+      set_last_error("cudaMemPoolCreate failed");
+      return HM_ERR_CUDA;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   cudaDeviceProp prop;
   HM_CUDA(cudaGetDeviceProperties(&prop, o.device));
   ctx->max_smem = (int)prop.sharedMemPerBlockOptin;
@@ -238,6 +274,13 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
 int hm_ctx_destroy(hm_ctx_t ctx) {
   if (!ctx) return HM_ERR_INVALID_ARG;
   cudaSetDevice(ctx->opts.device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& r : ctx->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto& e : ctx->prof.pool) cudaEventDestroy(e);
+  if (ctx->pool) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaMemPoolDestroy(ctx->pool);
+  }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return HM_OK;
@@ -447,6 +490,48 @@ int hm_get_hodlr_block(hm_sys_t sys, int32_t front, int32_t level, int32_t node,
   };
   if (U) HM_TRY(fetch(ubase, u_off, ldu, rows_u, U));
   if (V) HM_TRY(fetch(sys->d_bo, v_off, ldv, rows_v, V));
+  return HM_OK;
+}
+
+int hm_profile_enable(hm_ctx_t ctx, int enable) {
+  if (!ctx) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->opts.device);
+  HM_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& r : ctx->prof.recs) {
+    ctx->prof.pool.push_back(r.a);
+    ctx->prof.pool.push_back(r.b);
+  }
+  ctx->prof.recs.clear();
+  ctx->prof.on = enable != 0;
+  return HM_OK;
+}
+
+int hm_profile_read(hm_ctx_t ctx, int32_t max_entries, hm_prof_entry* out, int32_t* n) {
+  if (!ctx || !n) return HM_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->opts.device);
+  HM_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::vector<hm_prof_entry> agg(PC_COUNT);
+  for (int c = 0; c < PC_COUNT; ++c) {
+    memset(&agg[c], 0, sizeof(hm_prof_entry));
+    strncpy(agg[c].name, prof_cat_name(c), sizeof(agg[c].name) - 1);
+  }
+  for (const auto& r : ctx->prof.recs) {
+    float ms = 0.f;
+    HM_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    hm_prof_entry& e = agg[r.cat];
+    e.launches += 1;
+    e.kernels += r.kernels;
+    e.ms += ms;
+    e.flops += r.w.flops;
+    e.bytes += r.w.bytes;
+  }
+  int k = 0;
+  for (int c = 0; c < PC_COUNT; ++c) {
+    if (agg[c].launches == 0) continue;
+    if (out && k < max_entries) out[k] = agg[c];
+    ++k;
+  }
+  *n = k;
   return HM_OK;
 }
 

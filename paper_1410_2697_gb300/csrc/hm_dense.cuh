@@ -79,19 +79,22 @@ struct OmegaTask {
 };
 
 // Woodbury core C (n2 = 2k, ld n2): the GEMMs have written the two diagonal k x k
-// blocks; this sets the off-diagonal blocks to I and LU-factors C with partial pivoting.
+// blocks; this sets the off-diagonal blocks to I, LU-factors C with partial pivoting and
+// writes the explicit inverse to Cinv (n2 x n2, ld n2).
 struct CoreLuTask {
   void* C;
+  void* Cinv;
   int* piv;
   int k, front;
 };
 
-// B (n2 x ncols, ldb) <- C^{-1} B using the LU factors of a core.
-struct LuSolveTask {
-  const void* LU;
-  const int* piv;
+// From a Cholesky factor L (lower triangle of A, n <= 128, ld): A <- A^{-1} (full n x n)
+// and, if m > 0, B (m x n, ldb) <- B L^{-1}  (so that B L^{-1} = F_fp F_pp^{-1} when B
+// holds L_fp = F_fp L^{-T}).
+struct CholInvTask {
+  void* A;
   void* B;
-  int n2, ldb, ncols, pad;
+  int n, ld, m, ldb;
 };
 
 template <typename T>
@@ -111,7 +114,7 @@ void launch_omega(const OmegaTask* tasks, int ntasks, uint64_t seed, cudaStream_
 template <typename T>
 void launch_core_lu(const CoreLuTask* tasks, int ntasks, int* err, cudaStream_t s);
 template <typename T>
-void launch_lu_solve(const LuSolveTask* tasks, int ntasks, int maxcols, cudaStream_t s);
+void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStream_t s);
 
 // Host-side: append the tiles of one task (all tiles, or those touching the lower
 // triangle when t.lower).

@@ -222,46 +222,103 @@ __global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ 
     }
     __syncthreads();
   }
+  // explicit inverse: column c of C^{-1} solves L U x = P e_c (one thread per column)
+  T* Ci = (T*)t.Cinv;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    T* b = Ci + (size_t)c * n;
+    for (int i = 0; i < n; ++i) b[i] = (i == c) ? T(1) : T(0);
+    for (int j = 0; j < n; ++j) {
+      const int p = t.piv[j];
+      if (p != j) { const T a = b[j]; b[j] = b[p]; b[p] = a; }
+    }
+    for (int j = 0; j < n; ++j) {
+      const T v = b[j];
+      if (v != T(0))
+        for (int i = j + 1; i < n; ++i) b[i] -= C[(size_t)i + (size_t)j * n] * v;
+    }
+    for (int j = n - 1; j >= 0; --j) {
+      T d = C[(size_t)j + (size_t)j * n];
+      if (d == T(0)) d = T(1);
+      const T v = b[j] / d;
+      b[j] = v;
+      if (v != T(0))
+        for (int i = 0; i < j; ++i) b[i] -= C[(size_t)i + (size_t)j * n] * v;
+    }
+  }
+}
+
+// =====================================================================================
+// Explicit SPD inverse from a Cholesky factor (one CTA per block, n <= 128, in shared
+// memory).  L^{-1} is formed in place, last column first: with the trailing block
+// already inverted, column j becomes -Linv[j+1:, j+1:] L[j+1:, j] / L[j][j] (a parallel
+// triangular matrix-vector product).  Then A^{-1} = Linv^T Linv is written as a full
+// n x n block, and B <- B Linv for the m rows below (64 rows per pass).
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_inverse(const CholInvTask* __restrict__ tasks) {
+  extern __shared__ unsigned char smem_raw[];
+  const CholInvTask t = tasks[blockIdx.x];
+  const int n = t.n, ls = n + 1;
+  T* Li = reinterpret_cast<T*>(smem_raw);  // L, overwritten by Linv (lower), n x (n+1)
+  T* col = Li + (size_t)n * ls;            // saved column of L, n
+  T* R = col + n;                          // row slab [n][64]
+  T* A = (T*)t.A;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    Li[i + j * ls] = (i >= j) ? A[(size_t)i + (size_t)j * t.ld] : T(0);
+  }
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) col[i] = Li[i + j * ls];
+    __syncthreads();
+    const T dinv = T(1) / col[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      T s = T(0);
+      for (int k = j + 1; k <= i; ++k) s += Li[i + k * ls] * col[k];
+      Li[i + j * ls] = -s * dinv;
+    }
+    if (threadIdx.x == 0) Li[j + j * ls] = dinv;
+    __syncthreads();
+  }
+  // A^{-1}(i, j) = sum_{k >= max(i, j)} Linv(k, i) Linv(k, j)
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    T s = T(0);
+    for (int k = max(i, j); k < n; ++k) s += Li[k + i * ls] * Li[k + j * ls];
+    A[(size_t)i + (size_t)j * t.ld] = s;
+  }
+  if (t.m <= 0) return;
+  T* B = (T*)t.B;
+  for (int r0 = 0; r0 < t.m; r0 += 64) {
+    const int rows = min(64, t.m - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * n; e += blockDim.x) {
+      const int r = e % 64, j = e / 64;
+      R[j * 64 + r] = r < rows ? B[(size_t)(r0 + r) + (size_t)j * t.ldb] : T(0);
+    }
+    __syncthreads();
+    // row r of B Linv, column j: sum_{i >= j} B(r, i) Linv(i, j)
+    for (int e = threadIdx.x; e < 64 * n; e += blockDim.x) {
+      const int r = e % 64, j = e / 64;
+      if (r >= rows) continue;
+      T s = T(0);
+      for (int i = j; i < n; ++i) s += R[i * 64 + r] * Li[i + j * ls];
+      B[(size_t)(r0 + r) + (size_t)j * t.ldb] = s;
+    }
+  }
+}
+
+template <typename T>
+void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const size_t smem = ((size_t)maxn * (maxn + 1) + maxn + 64 * (size_t)maxn) * sizeof(T);
+  k_chol_inverse<T><<<ntasks, 256, smem, s>>>(tasks);
 }
 
 template <typename T>
 void launch_core_lu(const CoreLuTask* tasks, int ntasks, int* err, cudaStream_t s) {
   if (ntasks <= 0) return;
   k_core_lu<T><<<ntasks, 256, 0, s>>>(tasks, err);
-}
-
-// B <- C^{-1} B with the pivoted LU of a core; one thread per column of B.
-template <typename T>
-__global__ void __launch_bounds__(128) k_lu_solve(const LuSolveTask* __restrict__ tasks) {
-  const LuSolveTask t = tasks[blockIdx.y];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= t.ncols) return;
-  const T* LU = (const T*)t.LU;
-  T* b = (T*)t.B + (size_t)c * t.ldb;
-  const int n = t.n2;
-  for (int j = 0; j < n; ++j) {
-    const int p = t.piv[j];
-    if (p != j) { const T a = b[j]; b[j] = b[p]; b[p] = a; }
-  }
-  for (int j = 0; j < n; ++j) {
-    const T v = b[j];
-    for (int i = j + 1; i < n; ++i) b[i] -= LU[(size_t)i + (size_t)j * n] * v;
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    T d = LU[(size_t)j + (size_t)j * n];
-    if (d == T(0)) d = T(1);
-    const T v = b[j] / d;
-    b[j] = v;
-    for (int i = 0; i < j; ++i) b[i] -= LU[(size_t)i + (size_t)j * n] * v;
-  }
-}
-
-template <typename T>
-void launch_lu_solve(const LuSolveTask* tasks, int ntasks, int maxcols, cudaStream_t s) {
-  if (ntasks <= 0 || maxcols <= 0) return;
-  // grid.x covers the widest task; narrower tasks exit early
-  dim3 grid((maxcols + 127) / 128, ntasks);
-  k_lu_solve<T><<<grid, 128, 0, s>>>(tasks);
 }
 
 template void launch_potrf<float>(const PotrfTask*, int, int, int*, cudaStream_t);
@@ -272,8 +329,8 @@ template void launch_chol_solve<float>(const CholSolveTask*, int, int, cudaStrea
 template void launch_chol_solve<double>(const CholSolveTask*, int, int, cudaStream_t);
 template void launch_core_lu<float>(const CoreLuTask*, int, int*, cudaStream_t);
 template void launch_core_lu<double>(const CoreLuTask*, int, int*, cudaStream_t);
-template void launch_lu_solve<float>(const LuSolveTask*, int, int, cudaStream_t);
-template void launch_lu_solve<double>(const LuSolveTask*, int, int, cudaStream_t);
+template void launch_chol_inverse<float>(const CholInvTask*, int, int, cudaStream_t);
+template void launch_chol_inverse<double>(const CholInvTask*, int, int, cudaStream_t);
 
 int dense_fact_setup(int max_smem) {
   HM_CUDA(allow_max_dyn_smem(k_potrf<float>, max_smem));
@@ -282,6 +339,8 @@ int dense_fact_setup(int max_smem) {
   HM_CUDA(allow_max_dyn_smem(k_trsm<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_chol_solve<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_chol_solve<double>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_chol_inverse<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_chol_inverse<double>, max_smem));
   return HM_OK;
 }
 

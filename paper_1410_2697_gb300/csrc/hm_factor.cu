@@ -84,30 +84,40 @@ static void debug_stage(hm_sys_s* sys, const char* stage, int level) {
 }
 
 template <typename T>
-static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* base) {
+static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* base, int cat) {
+  if (b.tiles.count == 0) return;
+  ProfScope ps(sys->ctx, cat, b.tasks.work);
   launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, sys->ctx->stream);
 }
 
 template <typename T>
 static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
   Plan& P = sys->plan;
-  cudaStream_t s = sys->ctx->stream;
+  hm_ctx_s* ctx = sys->ctx;
+  cudaStream_t s = ctx->stream;
   const unsigned char* base = P.d_tasks;
   T* F = (T*)sys->d_front;
+  const int es = sizeof(T);
   HM_CUDA(cudaMemsetAsync(sys->d_err, 0, 4 * sizeof(int), s));
-  HM_CUDA(cudaMemsetAsync(F, 0, (size_t)P.front_total * sizeof(T), s));
-  if (P.bo_total) HM_CUDA(cudaMemsetAsync(sys->d_bo, 0, (size_t)P.bo_total * sizeof(T), s));
-  if (P.w_total) HM_CUDA(cudaMemsetAsync(sys->d_w, 0, (size_t)P.w_total * sizeof(T), s));
+  {
+    ProfScope ps(ctx, PC_MEMSET, Work{0.0, (double)es * (P.front_total + P.bo_total + P.w_total)}, 0);
+    HM_CUDA(cudaMemsetAsync(F, 0, (size_t)P.front_total * sizeof(T), s));
+    if (P.bo_total) HM_CUDA(cudaMemsetAsync(sys->d_bo, 0, (size_t)P.bo_total * sizeof(T), s));
+    if (P.w_total) HM_CUDA(cudaMemsetAsync(sys->d_w, 0, (size_t)P.w_total * sizeof(T), s));
+  }
   {
     const int64_t nnz = sys->nnz;
+    ProfScope ps(ctx, PC_SCATTER, Work{0.0, nnz * 32.0 + 0.5 * nnz * es});
     const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
     k_scatter<T><<<std::max(grid, 1), 256, 0, s>>>(d_values, sys->d_psrc, sys->d_amap, nnz, F,
                                                   sys->d_pvals);
   }
   for (int l = P.nlevels - 1; l >= 0; --l) {
     const LevelFactorPlan& lp = P.levels[l];
-    for (const auto& sl : lp.ea_slots) {
+    for (size_t si = 0; si < lp.ea_slots.size(); ++si) {
+      const auto& sl = lp.ea_slots[si];
       if (sl.count == 0) continue;
+      ProfScope ps(ctx, PC_EXTEND_ADD, lp.ea_work[si]);
       const int threads = 256;
       const int64_t blocks = ((int64_t)sl.count * 32 + threads - 1) / threads;
       k_extend_add<T><<<(unsigned)blocks, threads, 0, s>>>(sl.dev(base), sl.count, sys->d_parent,
@@ -116,41 +126,78 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
     }
     debug_stage<T>(sys, "extendadd", l);
     if (lp.n_dense) {
-      launch_potrf<T>(lp.potrf.dev(base), lp.potrf.count, lp.potrf_maxn, sys->d_err, s);
-      launch_trsm<T>(lp.trsm.dev(base), lp.trsm.count, lp.trsm_maxn, s);
-      run_gemm<T>(sys, lp.syrk, base);
+      {
+        ProfScope ps(ctx, PC_POTRF, lp.potrf.work);
+        launch_potrf<T>(lp.potrf.dev(base), lp.potrf.count, lp.potrf_maxn, sys->d_err, s);
+      }
+      if (lp.trsm.count) {
+        ProfScope ps(ctx, PC_TRSM, lp.trsm.work);
+        launch_trsm<T>(lp.trsm.dev(base), lp.trsm.count, lp.trsm_maxn, s);
+      }
+      run_gemm<T>(sys, lp.syrk, base, PC_GEMM_FACTOR);
+      {
+        ProfScope ps(ctx, PC_INVERSE, lp.dinv.work);
+        launch_chol_inverse<T>(lp.dinv.dev(base), lp.dinv.count, lp.potrf_maxn, s);
+      }
       debug_stage<T>(sys, "dense", l);
     }
     if (lp.n_hodlr) {
-      launch_omega<T>(lp.omega.dev(base), lp.omega.count, sys->ctx->opts.seed, s);
-      run_gemm<T>(sys, lp.sampY, base);
-      launch_qr<T>(lp.qrY.dev(base), lp.qrY.count, s);
+      {
+        ProfScope ps(ctx, PC_SKETCH, lp.omega.work);
+        launch_omega<T>(lp.omega.dev(base), lp.omega.count, ctx->opts.seed, s);
+      }
+      run_gemm<T>(sys, lp.sampY, base, PC_GEMM_FACTOR);
+      {
+        ProfScope ps(ctx, PC_QR, lp.qrY.work);
+        launch_qr<T>(lp.qrY.dev(base), lp.qrY.count, s);
+      }
       debug_stage<T>(sys, "qrY", l);
-      run_gemm<T>(sys, lp.sampZ, base);
-      launch_qr<T>(lp.qrZ.dev(base), lp.qrZ.count, s);
-      launch_svd<T>(lp.svd.dev(base), lp.svd.count, lp.svd_maxk, tol, s);
+      run_gemm<T>(sys, lp.sampZ, base, PC_GEMM_FACTOR);
+      {
+        ProfScope ps(ctx, PC_QR, lp.qrZ.work);
+        launch_qr<T>(lp.qrZ.dev(base), lp.qrZ.count, s);
+      }
+      {
+        ProfScope ps(ctx, PC_SVD, lp.svd.work);
+        launch_svd<T>(lp.svd.dev(base), lp.svd.count, lp.svd_maxk, tol, s);
+      }
       debug_stage<T>(sys, "svd", l);
-      run_gemm<T>(sys, lp.formU, base);
-      run_gemm<T>(sys, lp.formV, base);
+      run_gemm<T>(sys, lp.formU, base, PC_GEMM_FACTOR);
+      run_gemm<T>(sys, lp.formV, base, PC_GEMM_FACTOR);
       debug_stage<T>(sys, "formUV", l);
-      if (lp.x_copy_len)
+      if (lp.x_copy_len) {
+        ProfScope ps(ctx, PC_MEMSET, Work{0.0, 2.0 * es * lp.x_copy_len}, 0);
         HM_CUDA(cudaMemcpyAsync((T*)sys->d_x + lp.x_copy_off, (T*)sys->d_bo + lp.x_copy_off,
                                 (size_t)lp.x_copy_len * sizeof(T), cudaMemcpyDeviceToDevice, s));
-      launch_potrf<T>(lp.leaf_potrf.dev(base), lp.leaf_potrf.count, lp.leaf_maxn, sys->d_err, s);
-      launch_chol_solve<T>(lp.leaf_solve.dev(base), lp.leaf_solve.count, lp.leaf_maxn, s);
+      }
+      {
+        ProfScope ps(ctx, PC_POTRF, lp.leaf_potrf.work);
+        launch_potrf<T>(lp.leaf_potrf.dev(base), lp.leaf_potrf.count, lp.leaf_maxn, sys->d_err, s);
+      }
+      if (lp.leaf_solve.count) {
+        ProfScope ps(ctx, PC_CHOL_SOLVE, lp.leaf_solve.work);
+        launch_chol_solve<T>(lp.leaf_solve.dev(base), lp.leaf_solve.count, lp.leaf_maxn, s);
+      }
+      {
+        ProfScope ps(ctx, PC_INVERSE, lp.leaf_inv.work);
+        launch_chol_inverse<T>(lp.leaf_inv.dev(base), lp.leaf_inv.count, lp.leaf_maxn, s);
+      }
       debug_stage<T>(sys, "leaves", l);
       for (const auto& H : lp.heights) {
-        run_gemm<T>(sys, H.pre, base);
+        run_gemm<T>(sys, H.pre, base, PC_GEMM_FACTOR);
         debug_stage<T>(sys, "core-pre", l);
-        launch_core_lu<T>(H.lu.dev(base), H.lu.count, sys->d_err, s);
+        {
+          ProfScope ps(ctx, PC_CORE_LU, H.lu.work);
+          launch_core_lu<T>(H.lu.dev(base), H.lu.count, sys->d_err, s);
+        }
         debug_stage<T>(sys, "core-lu", l);
-        launch_lu_solve<T>(H.lus.dev(base), H.lus.count, H.lus_maxcols, s);
-        run_gemm<T>(sys, H.upd, base);
+        run_gemm<T>(sys, H.sg, base, PC_GEMM_FACTOR);
+        run_gemm<T>(sys, H.upd, base, PC_GEMM_FACTOR);
         debug_stage<T>(sys, "core-upd", l);
       }
-      run_gemm<T>(sys, lp.schurT, base);
-      run_gemm<T>(sys, lp.schurP, base);
-      run_gemm<T>(sys, lp.schurF, base);
+      run_gemm<T>(sys, lp.schurT, base, PC_GEMM_FACTOR);
+      run_gemm<T>(sys, lp.schurP, base, PC_GEMM_FACTOR);
+      run_gemm<T>(sys, lp.schurF, base, PC_GEMM_FACTOR);
       debug_stage<T>(sys, "schur", l);
     }
   }

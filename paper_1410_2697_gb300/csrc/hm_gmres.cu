@@ -239,6 +239,7 @@ static int ensure_workspace(hm_sys_s* sys, int nrhs, int m) {
 static void sqnorm(hm_sys_s* sys, const double* v, double* ss, int stride, int nrhs) {
   auto& G = sys->gm;
   cudaStream_t s = sys->ctx->stream;
+  ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * sys->n * nrhs, 8.0 * sys->n * nrhs}, 2);
   k_multidot<<<dim3(G.nblk, nrhs), kDotThreads, 0, s>>>(v, v, sys->n, nrhs, 1, stride, G.part);
   // note: with V = v and nvec = 1 the "basis" is v itself (stride of rhs = n)
   k_reduce_dots<<<(nrhs + 127) / 128, 128, 0, s>>>(G.part, G.nblk, nrhs, 1, stride, ss, 0);
@@ -255,8 +256,11 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
   const int64_t nn = (int64_t)n * nrhs;
   const int stride = m + 2;
   const int gsz = (int)std::min<int64_t>((nn + 255) / 256, 152 * 8);
-  launch_permute_in(d_b, G.b, sys->d_perm, n, nrhs, s);
-  HM_CUDA(cudaMemsetAsync(G.x, 0, sizeof(double) * nn, s));
+  {
+    ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, 20.0 * nn});
+    launch_permute_in(d_b, G.b, sys->d_perm, n, nrhs, s);
+    HM_CUDA(cudaMemsetAsync(G.x, 0, sizeof(double) * nn, s));
+  }
   // ||b|| per RHS
   double* bn2 = G.hv + 2 * nrhs * stride;  // scratch: squared norms (stride 1)
   sqnorm(sys, G.b, bn2, 1, nrhs);
@@ -281,31 +285,56 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
   while (!done && iters < max_iters) {
     for (int r = 0; r < nrhs; ++r) active[r] = relres[r] > rtol ? 1 : 0;
     HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
-    k_cycle_init<<<gsz, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active);
-    k_cycle_g<<<(nrhs + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, nrhs);
+    {
+      ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn}, 2);
+      k_cycle_init<<<gsz, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active);
+      k_cycle_g<<<(nrhs + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, nrhs);
+    }
     int j = 0;
     for (; j < m && iters < max_iters; ++j) {
       const double* Vj = G.V + (int64_t)j * nrhs * n;
       T* Zj = Z + (int64_t)j * nrhs * n;
-      launch_cast_to<T>(Vj, (T*)G.wT, nn, s);
+      {
+        ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, (8.0 + sizeof(T)) * nn});
+        launch_cast_to<T>(Vj, (T*)G.wT, nn, s);
+      }
       HM_TRY(apply_impl(sys, nrhs, G.wT, Zj));
-      k_spmv<T><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
-                                                Zj, n, G.w, n, nullptr, 0);
+      {
+        ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs,
+                                             12.0 * sys->nnz + 8.0 * n + (8.0 + sizeof(T)) * nn});
+        k_spmv<T><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+                                                  Zj, n, G.w, n, nullptr, 0);
+      }
       double* h1 = G.hv;
       double* h2 = G.hv + nrhs * stride;
       const int nvec = j + 1;
       for (int pass = 0; pass < 2; ++pass) {
         double* h = pass == 0 ? h1 : h2;
-        k_multidot<<<dim3(G.nblk, nrhs), kDotThreads, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, G.part);
-        k_reduce_dots<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(G.part, G.nblk, nrhs, nvec, stride, h, 0);
-        k_gs_update<<<gsz, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h);
+        {
+          ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
+          k_multidot<<<dim3(G.nblk, nrhs), kDotThreads, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, G.part);
+          k_reduce_dots<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(G.part, G.nblk, nrhs, nvec, stride, h, 0);
+        }
+        {
+          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
+          k_gs_update<<<gsz, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h);
+        }
       }
-      k_add_cols<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(h1, h2, nrhs, nvec, stride);  // h1 += h2
+      {
+        ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
+        k_add_cols<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(h1, h2, nrhs, nvec, stride);  // h1 += h2
+      }
       double* wss = G.hv + 2 * nrhs * stride + 2 * nrhs;  // ||w||^2 per RHS (stride 1)
       sqnorm(sys, G.w, wss, 1, nrhs);
-      k_scale<<<gsz, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1);
-      k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, h1, stride, wss, 1, G.cs, G.sn, G.g, G.bnorm,
-                                               G.res, G.len, j, m, nrhs, rtol);
+      {
+        ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn});
+        k_scale<<<gsz, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1);
+      }
+      {
+        ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
+        k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, h1, stride, wss, 1, G.cs, G.sn, G.g, G.bnorm,
+                                                 G.res, G.len, j, m, nrhs, rtol);
+      }
       ++iters;
       HM_CUDA(cudaMemcpyAsync(G.h_res, G.res, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
       HM_CUDA(cudaStreamSynchronize(s));
@@ -315,10 +344,19 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
       if (all) { ++j; break; }
     }
     const int jend = std::min(j, m);
-    k_backsolve<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, G.g, G.y, G.len, jend, m, nrhs);
-    k_update_x<T><<<gsz, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m);
-    k_spmv<double><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
-                                                   G.x, n, G.r, n, G.b, n);
+    {
+      ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
+      k_backsolve<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, G.g, G.y, G.len, jend, m, nrhs);
+    }
+    {
+      ProfScope ps(sys->ctx, PC_VECTOR, Work{2.0 * jend * nn, (16.0 + sizeof(T) * jend) * nn});
+      k_update_x<T><<<gsz, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m);
+    }
+    {
+      ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});
+      k_spmv<double><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+                                                     G.x, n, G.r, n, G.b, n);
+    }
     sqnorm(sys, G.r, rss, 1, nrhs);
     std::vector<double> hr(nrhs);
     HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
@@ -330,7 +368,10 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
       if (!(relres[r] <= rtol)) done = false;
     }
   }
-  launch_permute_out(G.x, d_x, sys->d_perm, n, nrhs, s);
+  {
+    ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, 20.0 * nn});
+    launch_permute_out(G.x, d_x, sys->d_perm, n, nrhs, s);
+  }
   HM_CUDA(cudaStreamSynchronize(s));
   HM_CUDA(cudaGetLastError());
   if (info) {

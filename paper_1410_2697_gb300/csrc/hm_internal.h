@@ -1,6 +1,8 @@
 // hm_internal.h -- host-side state of a context / system and the execution plan.
 #pragma once
 
+#include <algorithm>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <vector>
@@ -13,11 +15,54 @@ struct hm_sys_s;
 
 namespace hm {
 
+// Algorithmic work of one launch (minimum flops and HBM bytes of what it computes).
+struct Work {
+  double flops = 0, bytes = 0;
+  Work& operator+=(const Work& o) { flops += o.flops; bytes += o.bytes; return *this; }
+};
+
+inline Work work_of(const GemmTask& t, int es) {
+  Work w;
+  const double m = t.m, n = t.n, k = t.k;
+  w.flops = (t.lower ? 1.0 : 2.0) * m * n * k;
+  w.bytes = es * (m * k + k * n + (t.lower ? 0.5 : 1.0) * m * n * (t.beta != 0.0 ? 2.0 : 1.0));
+  return w;
+}
+inline Work work_of(const PotrfTask& t, int es) {
+  return Work{(double)t.n * t.n * t.n / 3.0, (double)es * t.n * (t.n + 1)};
+}
+inline Work work_of(const TrsmTask& t, int es) {
+  const double rows = std::min(64, t.m - t.row0);
+  return Work{rows * t.n * t.n, es * (2.0 * rows * t.n + 0.5 * t.n * t.n)};
+}
+inline Work work_of(const CholSolveTask& t, int es) {
+  return Work{2.0 * t.n * t.n * t.ncols, es * (0.5 * t.n * t.n + 2.0 * t.n * t.ncols)};
+}
+inline Work work_of(const QrTask& t, int es) {
+  return Work{4.0 * t.m * t.k * t.k, es * (3.0 * t.m * t.k + (t.R ? (double)t.k * t.k : 0.0))};
+}
+inline Work work_of(const SvdTask& t, int es) {
+  return Work{12.0 * t.k * t.k * t.k, es * 3.0 * t.k * t.k};  // ~ per-sweep cost x 2
+}
+inline Work work_of(const OmegaTask& t, int es) { return Work{0.0, (double)es * t.rows * t.cols}; }
+inline Work work_of(const CoreLuTask& t, int es) {
+  const double n2 = 2.0 * t.k;
+  return Work{2.0 * n2 * n2 * n2 / 3.0 + 2.0 * n2 * n2 * n2, es * 3.0 * n2 * n2};
+}
+inline Work work_of(const CholInvTask& t, int es) {
+  const double n = t.n, m = t.m;
+  return Work{n * n * n / 3.0 + n * n * n / 3.0 + m * n * n,
+              es * (1.5 * n * n + 2.0 * m * n)};
+}
+template <typename TaskT>
+inline Work work_of(const TaskT&, int) { return Work{}; }
+
 // A typed span inside the uploaded task buffer.
 template <typename TaskT>
 struct Span {
   size_t off = 0;  // byte offset in the task buffer
   int count = 0;
+  Work work;       // summed over the tasks
   const TaskT* dev(const unsigned char* base) const {
     return reinterpret_cast<const TaskT*>(base + off);
   }
@@ -31,6 +76,7 @@ struct GemmBatch {
 // Host builder of the task buffer (one upload after planning).
 struct TaskBuf {
   std::vector<unsigned char> host;
+  int es = 4;
   template <typename TaskT>
   Span<TaskT> add(const std::vector<TaskT>& v) {
     Span<TaskT> s;
@@ -39,6 +85,7 @@ struct TaskBuf {
     if (!v.empty()) memcpy(host.data() + a, v.data(), v.size() * sizeof(TaskT));
     s.off = a;
     s.count = (int)v.size();
+    for (const auto& t : v) s.work += work_of(t, es);
     return s;
   }
   GemmBatch add_gemm(const std::vector<GemmTask>& t) {
@@ -49,6 +96,32 @@ struct TaskBuf {
     b.tiles = add(tiles);
     return b;
   }
+};
+
+// ------------------------------------------------------------------------------------
+// Launch profiler: when enabled, every launch is bracketed by a pair of CUDA events on
+// its stream and tagged with a category and its algorithmic work.
+// ------------------------------------------------------------------------------------
+enum ProfCat {
+  PC_ND = 0, PC_SYMBOLIC, PC_PERMUTE_CSR, PC_SCATTER, PC_EXTEND_ADD, PC_POTRF, PC_TRSM,
+  PC_GEMM_FACTOR, PC_SKETCH, PC_QR, PC_SVD, PC_CHOL_SOLVE, PC_CORE_LU, PC_INVERSE,
+  PC_UP, PC_DOWN, PC_GEMM_APPLY, PC_SPMV, PC_DOTS, PC_GS_UPDATE, PC_GMRES_SMALL, PC_VECTOR,
+  PC_MEMSET, PC_COUNT
+};
+const char* prof_cat_name(int c);
+
+struct ProfRec {
+  int cat;
+  cudaEvent_t a, b;
+  Work w;
+  int kernels;  // kernel launches inside the bracket (0 for copies / memsets)
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
 };
 
 // Extend-add work item: one column `col` of child `child`'s update matrix.
@@ -68,11 +141,11 @@ struct FrontGeom {
 struct HNodeGeom {
   int level, index, lo, mid, hi;
   int kb;                  // sketch width of this node's off-diagonal block
-  int64_t core_off;        // (2 k_level)^2 elements in the core arena
+  int64_t core_off;        // C (LU) then C^{-1}: 2 (2 k_level)^2 elements in the core arena
   int64_t piv_off;         // 2 k_level ints
   int rank_slot;
   int64_t om_off, y_off, z_off, r_off, uhs_off, vh_off;  // compression scratch
-  int64_t tb_off;          // factor-time t/s buffer, 2 k_level x A_level
+  int64_t tb_off;          // factor-time t then s buffers, 2 x (2 k_level x A_level)
 };
 
 struct HFront {
@@ -94,11 +167,13 @@ struct HFront {
 
 struct LevelFactorPlan {
   std::vector<Span<EaItem>> ea_slots;
+  std::vector<Work> ea_work;
   Span<PotrfTask> potrf;       // dense fronts
   int potrf_maxn = 0;
   Span<TrsmTask> trsm;
   int trsm_maxn = 0;
   GemmBatch syrk;
+  Span<CholInvTask> dinv;      // F_pp^{-1} and K = F_fp F_pp^{-1} of the dense fronts
   // HODLR fronts
   Span<OmegaTask> omega;
   GemmBatch sampY, sampZ, formU, formV;
@@ -109,11 +184,11 @@ struct LevelFactorPlan {
   Span<PotrfTask> leaf_potrf;
   int leaf_maxn = 0;
   Span<CholSolveTask> leaf_solve;
+  Span<CholInvTask> leaf_inv;  // explicit leaf inverses for the apply
   struct Height {
     GemmBatch pre;            // core diagonal blocks and t = Z^T X_anc
-    Span<CoreLuTask> lu;
-    Span<LuSolveTask> lus;
-    int lus_maxcols = 0;
+    Span<CoreLuTask> lu;      // LU and explicit inverse of the cores
+    GemmBatch sg;             // s = C^{-1} t
     GemmBatch upd;            // X_anc -= Zhat s
   };
   std::vector<Height> heights;
@@ -128,17 +203,17 @@ struct UpItem {
 struct LevelSolvePlan {
   Span<int> fronts;            // all fronts of the level (gather + dense up / down)
   int nfronts = 0;
-  Span<CholSolveTask> leaf;    // HODLR leaves
-  int leaf_maxn = 0;
+  Work up_work, down_work;     // the up / down front kernels (dense GEMVs + gathers)
+  int n_hodlr = 0;
+  GemmBatch up1, up2;          // HODLR fronts, upward: tf = Vtilde^T b_p ; f -= W tf
+  GemmBatch leaf;              // HODLR fronts, downward: y_leaf = K_leaf^{-1} b_leaf
   struct Height {
     GemmBatch t;               // t = [U^T y_a; V^T y_b]
-    Span<LuSolveTask> lus;
-    int lus_maxcols = 0;
+    GemmBatch s;               // s = C^{-1} t
     GemmBatch upd;             // y -= Zhat s
   };
   std::vector<Height> heights;
-  GemmBatch fin1, fin2;        // tf = Vf^T y ; f -= W tf
-  GemmBatch down1, down2;      // tf = W^T x_f ; x_p -= Vtilde tf
+  GemmBatch down1, down2;      // tf = W^T x_f ; y -= Vtilde tf
 };
 
 struct SolvePlan {
@@ -153,6 +228,7 @@ struct SolvePlan {
   void* d_fv = nullptr;         // T
   void* d_sb = nullptr;         // T
   int64_t* d_fvoff = nullptr;
+  int64_t* d_yvoff = nullptr;   // per front: offset of y (np x nrhs) in the scratch, -1 if dense
 };
 
 struct Plan {
@@ -183,11 +259,13 @@ struct DevArena {
 
 struct hm_ctx_s {
   hm_opts opts;
+  hm::Profiler prof;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t allocated = 0;
   int max_smem = 0;
   int num_sms = 0;
+  cudaMemPool_t pool = nullptr;  // stream-ordered pool; freed memory is kept for reuse
   std::vector<void*> allocs;
 };
 
@@ -257,6 +335,29 @@ struct hm_sys_s {
 };
 
 namespace hm {
+
+// RAII launch bracket: records events around the launches in its scope when profiling.
+struct ProfScope {
+  hm_ctx_s* ctx;
+  int cat;
+  Work w;
+  int nk;
+  cudaEvent_t a = nullptr;
+  ProfScope(hm_ctx_s* c, int category, Work work, int kernels = 1)
+      : ctx(c), cat(category), w(work), nk(kernels) {
+    if (ctx->prof.on) {
+      a = ctx->prof.get();
+      cudaEventRecord(a, ctx->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = ctx->prof.get();
+      cudaEventRecord(b, ctx->stream);
+      ctx->prof.recs.push_back(ProfRec{cat, a, b, w, nk});
+    }
+  }
+};
 
 int dev_alloc(hm_sys_s* sys, void** p, size_t bytes);
 int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t bytes);

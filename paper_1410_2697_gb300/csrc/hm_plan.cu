@@ -126,7 +126,7 @@ int build_plan(hm_sys_s* sys) {
       for (auto& nd : h.nodes) {
         const int k = h.kl[nd.level];
         const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid, kb = nd.kb;
-        nd.core_off = P.core_total; P.core_total += (int64_t)(2 * k) * (2 * k);
+        nd.core_off = P.core_total; P.core_total += (int64_t)2 * (2 * k) * (2 * k);
         nd.piv_off = P.piv_total; P.piv_total += 2 * k;
         nd.rank_slot = P.nrank++;
         nd.om_off = P.comp_total; P.comp_total += (int64_t)nb * kb;
@@ -135,7 +135,7 @@ int build_plan(hm_sys_s* sys) {
         nd.r_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
         nd.uhs_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
         nd.vh_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
-        nd.tb_off = P.tb_total; P.tb_total += (int64_t)(2 * k) * h.col[nd.level];
+        nd.tb_off = P.tb_total; P.tb_total += (int64_t)2 * (2 * k) * h.col[nd.level];
       }
       g.hodlr = (int)P.hf.size();
       P.hf.push_back(std::move(h));
@@ -200,6 +200,7 @@ int build_plan(hm_sys_s* sys) {
   int* ranks = sys->d_ranks;
   TaskBuf& tb = P.tb;
   tb.host.clear();
+  tb.es = es;
   P.levels.assign(P.nlevels, LevelFactorPlan());
   double fbytes = 0;
   for (int l = P.nlevels - 1; l >= 0; --l) {
@@ -210,18 +211,24 @@ int build_plan(hm_sys_s* sys) {
     for (int q : fr) slots = std::max(slots, (int)sys->h_children[q].size());
     for (int s = 0; s < slots; ++s) {
       std::vector<EaItem> items;
+      Work w;
       for (int q : fr) {
         const auto& ch = sys->h_children[q];
         if (s >= (int)ch.size()) continue;
         const int c = ch[s];
+        const double nuc = P.fg[c].nu;
         for (int col = 0; col < P.fg[c].nu; ++col) items.push_back(EaItem{c, col});
+        w.flops += nuc * (nuc + 1) / 2;
+        w.bytes += 3.0 * es * nuc * (nuc + 1) / 2 + 4.0 * nuc;
       }
       lp.ea_slots.push_back(tb.add(items));
+      lp.ea_work.push_back(w);
     }
     // dense fronts
     std::vector<PotrfTask> pot;
     std::vector<TrsmTask> trs;
     std::vector<GemmTask> syrk;
+    std::vector<CholInvTask> dinv;
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
       if (g.hodlr >= 0) continue;
@@ -237,11 +244,13 @@ int build_plan(hm_sys_s* sys) {
                             at(F, g.off + g.np + (int64_t)g.np * g.nhat, es), g.nhat, g.nu, g.nu,
                             g.np, -1.0, 1.0, 1));
       }
-      fbytes += 2.0 * es * ((double)g.np * (g.np + 1) / 2 + (double)g.nu * g.np);
+      dinv.push_back(CholInvTask{Fq, at(F, g.off + g.np, es), g.np, g.nhat, g.nu, g.nhat});
+      fbytes += es * ((double)g.np * g.np + 2.0 * g.nu * g.np);
     }
     lp.potrf = tb.add(pot);
     lp.trsm = tb.add(trs);
     lp.syrk = tb.add_gemm(syrk);
+    lp.dinv = tb.add(dinv);
     // HODLR fronts
     std::vector<OmegaTask> om;
     std::vector<GemmTask> gy, gz, gu, gv;
@@ -249,6 +258,7 @@ int build_plan(hm_sys_s* sys) {
     std::vector<SvdTask> sv;
     std::vector<PotrfTask> lpot;
     std::vector<CholSolveTask> lsol;
+    std::vector<CholInvTask> linv;
     std::vector<GemmTask> sT, sP, sF;
     int maxL = 0;
     for (int q : fr) {
@@ -314,7 +324,8 @@ int build_plan(hm_sys_s* sys) {
         lpot.push_back(PotrfTask{Lq, n, nh, q, 0});
         lp.leaf_maxn = std::max(lp.leaf_maxn, n);
         if (h.xc > 0) lsol.push_back(CholSolveTask{Lq, at(X, h.bo_off + lo, es), n, nh, np, h.xc});
-        fbytes += es * (double)n * (n + 1) / 2;
+        linv.push_back(CholInvTask{Lq, nullptr, n, nh, 0, 0});
+        fbytes += es * (double)n * n;
       }
     }
     lp.omega = tb.add(om);
@@ -329,12 +340,11 @@ int build_plan(hm_sys_s* sys) {
     lp.x_copy_len = level_bo_end[l] - level_bo_begin[l];
     lp.leaf_potrf = tb.add(lpot);
     lp.leaf_solve = tb.add(lsol);
+    lp.leaf_inv = tb.add(linv);
     // Woodbury levels, bottom-up (height 1 = parents of the leaves)
     for (int ht = 1; ht <= maxL; ++ht) {
-      std::vector<GemmTask> pre, upd;
+      std::vector<GemmTask> pre, sg, upd;
       std::vector<CoreLuTask> lu;
-      std::vector<LuSolveTask> lus;
-      int lus_max = 0;
       for (int q : fr) {
         const FrontGeom& g = P.fg[q];
         if (g.hodlr < 0) continue;
@@ -347,6 +357,7 @@ int build_plan(hm_sys_s* sys) {
           if (nd.level != lv) continue;
           const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid;
           void* core = at(Cm, nd.core_off, es);
+          void* cinv = at(Cm, nd.core_off + (int64_t)4 * k * k, es);
           void* Ua = at(Bo, h.bo_off + colo + nd.lo, es);
           void* Vb = at(Bo, h.bo_off + colo + nd.mid, es);
           void* Uh = at(X, h.bo_off + colo + nd.lo, es);
@@ -354,18 +365,18 @@ int build_plan(hm_sys_s* sys) {
           pre.push_back(gemm(Ua, np, 1, Uh, np, 0, core, 2 * k, k, k, na, 1.0, 0.0));
           pre.push_back(gemm(Vb, np, 1, Vh, np, 0, at(Cm, nd.core_off + (int64_t)k * 2 * k + k, es),
                              2 * k, k, k, nb, 1.0, 0.0));
-          lu.push_back(CoreLuTask{core, piv + nd.piv_off, k, q});
+          lu.push_back(CoreLuTask{core, cinv, piv + nd.piv_off, k, q});
           if (A_ > 0) {
             void* tbuf = at(Tb, nd.tb_off, es);
+            void* sbuf = at(Tb, nd.tb_off + (int64_t)2 * k * A_, es);
             pre.push_back(gemm(Ua, np, 1, at(X, h.bo_off + nd.lo, es), np, 0, tbuf, 2 * k, k, A_, na,
                                1.0, 0.0));
             pre.push_back(gemm(Vb, np, 1, at(X, h.bo_off + nd.mid, es), np, 0,
                                at(Tb, nd.tb_off + k, es), 2 * k, k, A_, nb, 1.0, 0.0));
-            lus.push_back(LuSolveTask{core, piv + nd.piv_off, tbuf, 2 * k, 2 * k, A_, 0});
-            lus_max = std::max(lus_max, A_);
-            upd.push_back(gemm(Uh, np, 0, tbuf, 2 * k, 0, at(X, h.bo_off + nd.lo, es), np, na, A_, k,
+            sg.push_back(gemm(cinv, 2 * k, 0, tbuf, 2 * k, 0, sbuf, 2 * k, 2 * k, A_, 2 * k, 1.0, 0.0));
+            upd.push_back(gemm(Uh, np, 0, sbuf, 2 * k, 0, at(X, h.bo_off + nd.lo, es), np, na, A_, k,
                                -1.0, 1.0));
-            upd.push_back(gemm(Vh, np, 0, at(Tb, nd.tb_off + k, es), 2 * k, 0,
+            upd.push_back(gemm(Vh, np, 0, at(Tb, nd.tb_off + (int64_t)2 * k * A_ + k, es), 2 * k, 0,
                                at(X, h.bo_off + nd.mid, es), np, nb, A_, k, -1.0, 1.0));
           }
         }
@@ -373,8 +384,7 @@ int build_plan(hm_sys_s* sys) {
       LevelFactorPlan::Height H;
       H.pre = tb.add_gemm(pre);
       H.lu = tb.add(lu);
-      H.lus = tb.add(lus);
-      H.lus_maxcols = lus_max;
+      H.sg = tb.add_gemm(sg);
       H.upd = tb.add_gemm(upd);
       lp.heights.push_back(H);
     }
@@ -405,102 +415,124 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   int64_t fv = 0;
   for (int q = 0; q < nf; ++q) { sp->fv_off[q] = fv; fv += (int64_t)P.fg[q].nhat * nrhs; }
   sp->fv_total = fv;
-  // scratch: per HODLR node 2k x nrhs, per HODLR front kf x nrhs
+  // scratch: per HODLR node t and s (2k x nrhs each); per HODLR front tf (kf x nrhs)
+  // and the pivot-block solution y (np x nrhs)
   std::vector<std::vector<int64_t>> node_sb(P.hf.size());
-  std::vector<int64_t> front_sb(P.hf.size());
+  std::vector<int64_t> front_sb(P.hf.size()), front_yv(P.hf.size());
+  std::vector<int64_t> yvoff(nf, -1);
   int64_t sb = 0;
   for (size_t i = 0; i < P.hf.size(); ++i) {
     const HFront& h = P.hf[i];
-    for (const auto& nd : h.nodes) { node_sb[i].push_back(sb); sb += (int64_t)2 * h.kl[nd.level] * nrhs; }
+    for (const auto& nd : h.nodes) { node_sb[i].push_back(sb); sb += (int64_t)4 * h.kl[nd.level] * nrhs; }
     front_sb[i] = sb;
     sb += (int64_t)h.kf * nrhs;
+    front_yv[i] = sb;
+    yvoff[h.q] = sb;
+    sb += (int64_t)h.np * nrhs;
   }
   sp->sb_total = sb;
   HM_TRY(dev_alloc(sys, &sp->d_fv, (size_t)std::max<int64_t>(fv, 1) * es));
   HM_TRY(dev_alloc(sys, &sp->d_sb, (size_t)std::max<int64_t>(sb, 1) * es));
   HM_TRY(dev_alloc(sys, (void**)&sp->d_fvoff, (size_t)nf * 8));
+  HM_TRY(dev_alloc(sys, (void**)&sp->d_yvoff, (size_t)nf * 8));
   HM_CUDA(cudaMemcpyAsync(sp->d_fvoff, sp->fv_off.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
+                          sys->ctx->stream));
+  HM_CUDA(cudaMemcpyAsync(sp->d_yvoff, yvoff.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
                           sys->ctx->stream));
   void* F = sys->d_front;
   void* Bo = sys->d_bo;
   void* X = sys->d_x;
   void* W = sys->d_w;
   void* Cm = sys->d_core;
-  int* piv = sys->d_piv;
   void* FV = sp->d_fv;
   void* SB = sp->d_sb;
   TaskBuf& tb = sp->tb;
+  tb.es = es;
   sp->levels.assign(P.nlevels, LevelSolvePlan());
   for (int l = 0; l < P.nlevels; ++l) {
     LevelSolvePlan& lp = sp->levels[l];
     const auto& fr = P.level_fronts[l];
     lp.fronts = tb.add(fr);
     lp.nfronts = (int)fr.size();
-    std::vector<CholSolveTask> leaf;
-    std::vector<GemmTask> f1, f2, d1, d2;
+    for (int q : fr) {
+      const FrontGeom& g = P.fg[q];
+      const double np = g.np, nu = g.nu, nh = g.nhat, R = nrhs;
+      // vectors: gather r(I_p), write fv (nhat), children's update parts read
+      double vec = es * R * (np + 2.0 * nh);
+      for (int c : sys->h_children[q]) vec += es * R * 2.0 * P.fg[c].nu + 4.0 * P.fg[c].nu;
+      lp.up_work.bytes += vec;
+      lp.down_work.bytes += es * R * (2.0 * nu + 2.0 * np) + 4.0 * nu;
+      if (g.hodlr >= 0) {
+        lp.n_hodlr++;
+      } else {
+        lp.up_work.bytes += es * nu * np;              // K
+        lp.up_work.flops += 2.0 * R * nu * np;
+        lp.down_work.bytes += es * (np * np + nu * np);  // F_pp^{-1}, K
+        lp.down_work.flops += 2.0 * R * (np * np + nu * np);
+      }
+    }
+    std::vector<GemmTask> u1, u2, lf, d1, d2;
     int maxL = 0;
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
       if (g.hodlr < 0) continue;
       const HFront& h = P.hf[g.hodlr];
       maxL = std::max(maxL, h.L);
-      const int64_t fvq = sp->fv_off[q];
+      const int64_t fvq = sp->fv_off[q], yq = front_yv[g.hodlr];
       for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
         const int lo = h.leaf_lo[li], n = h.leaf_hi[li] - lo;
-        leaf.push_back(CholSolveTask{at(F, g.off + lo + (int64_t)lo * g.nhat, es), at(FV, fvq + lo, es),
-                                     n, g.nhat, g.nhat, nrhs});
-        lp.leaf_maxn = std::max(lp.leaf_maxn, n);
+        lf.push_back(gemm(at(F, g.off + lo + (int64_t)lo * g.nhat, es), g.nhat, 0, at(FV, fvq + lo, es),
+                          g.nhat, 0, at(SB, yq + lo, es), h.np, n, nrhs, n, 1.0, 0.0));
       }
       if (h.kf > 0) {
         void* tf = at(SB, front_sb[g.hodlr], es);
-        f1.push_back(gemm(at(Bo, h.bo_off, es), h.np, 1, at(FV, fvq, es), g.nhat, 0, tf, h.kf, h.kf,
+        u1.push_back(gemm(at(X, h.bo_off, es), h.np, 1, at(FV, fvq, es), g.nhat, 0, tf, h.kf, h.kf,
                           nrhs, h.np, 1.0, 0.0));
-        f2.push_back(gemm(at(W, h.w_off, es), h.nu, 0, tf, h.kf, 0, at(FV, fvq + h.np, es), g.nhat,
+        u2.push_back(gemm(at(W, h.w_off, es), h.nu, 0, tf, h.kf, 0, at(FV, fvq + h.np, es), g.nhat,
                           h.nu, nrhs, h.kf, -1.0, 1.0));
         d1.push_back(gemm(at(W, h.w_off, es), h.nu, 1, at(FV, fvq + h.np, es), g.nhat, 0, tf, h.kf,
                           h.kf, nrhs, h.nu, 1.0, 0.0));
-        d2.push_back(gemm(at(X, h.bo_off, es), h.np, 0, tf, h.kf, 0, at(FV, fvq, es), g.nhat, h.np,
+        d2.push_back(gemm(at(X, h.bo_off, es), h.np, 0, tf, h.kf, 0, at(SB, yq, es), h.np, h.np,
                           nrhs, h.kf, -1.0, 1.0));
       }
     }
-    lp.leaf = tb.add(leaf);
+    lp.up1 = tb.add_gemm(u1);
+    lp.up2 = tb.add_gemm(u2);
+    lp.leaf = tb.add_gemm(lf);
     for (int ht = 1; ht <= maxL; ++ht) {
-      std::vector<GemmTask> tt, upd;
-      std::vector<LuSolveTask> lus;
+      std::vector<GemmTask> tt, ss, upd;
       for (int q : fr) {
         const FrontGeom& g = P.fg[q];
         if (g.hodlr < 0) continue;
         const HFront& h = P.hf[g.hodlr];
         if (h.L < ht) continue;
         const int lv = h.L - ht, k = h.kl[lv], np = h.np;
-        const int64_t colo = (int64_t)h.col[lv] * np, fvq = sp->fv_off[q];
+        const int64_t colo = (int64_t)h.col[lv] * np, yq = front_yv[g.hodlr];
         for (size_t ni = 0; ni < h.nodes.size(); ++ni) {
           const auto& nd = h.nodes[ni];
           if (nd.level != lv) continue;
           const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid;
-          void* sbn = at(SB, node_sb[g.hodlr][ni], es);
-          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.lo, es), np, 1, at(FV, fvq + nd.lo, es), g.nhat,
-                            0, sbn, 2 * k, k, nrhs, na, 1.0, 0.0));
-          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.mid, es), np, 1, at(FV, fvq + nd.mid, es),
-                            g.nhat, 0, at(SB, node_sb[g.hodlr][ni] + k, es), 2 * k, k, nrhs, nb, 1.0,
-                            0.0));
-          lus.push_back(LuSolveTask{at(Cm, nd.core_off, es), piv + nd.piv_off, sbn, 2 * k, 2 * k, nrhs, 0});
-          upd.push_back(gemm(at(X, h.bo_off + colo + nd.lo, es), np, 0, sbn, 2 * k, 0,
-                             at(FV, fvq + nd.lo, es), g.nhat, na, nrhs, k, -1.0, 1.0));
+          void* tn = at(SB, node_sb[g.hodlr][ni], es);
+          void* sn = at(SB, node_sb[g.hodlr][ni] + (int64_t)2 * k * nrhs, es);
+          void* cinv = at(Cm, nd.core_off + (int64_t)4 * k * k, es);
+          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.lo, es), np, 1, at(SB, yq + nd.lo, es), np, 0,
+                            tn, 2 * k, k, nrhs, na, 1.0, 0.0));
+          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.mid, es), np, 1, at(SB, yq + nd.mid, es), np, 0,
+                            at(SB, node_sb[g.hodlr][ni] + k, es), 2 * k, k, nrhs, nb, 1.0, 0.0));
+          ss.push_back(gemm(cinv, 2 * k, 0, tn, 2 * k, 0, sn, 2 * k, 2 * k, nrhs, 2 * k, 1.0, 0.0));
+          upd.push_back(gemm(at(X, h.bo_off + colo + nd.lo, es), np, 0, sn, 2 * k, 0,
+                             at(SB, yq + nd.lo, es), np, na, nrhs, k, -1.0, 1.0));
           upd.push_back(gemm(at(X, h.bo_off + colo + nd.mid, es), np, 0,
-                             at(SB, node_sb[g.hodlr][ni] + k, es), 2 * k, 0, at(FV, fvq + nd.mid, es),
-                             g.nhat, nb, nrhs, k, -1.0, 1.0));
+                             at(SB, node_sb[g.hodlr][ni] + (int64_t)2 * k * nrhs + k, es), 2 * k, 0,
+                             at(SB, yq + nd.mid, es), np, nb, nrhs, k, -1.0, 1.0));
         }
       }
       LevelSolvePlan::Height H;
       H.t = tb.add_gemm(tt);
-      H.lus = tb.add(lus);
-      H.lus_maxcols = nrhs;
+      H.s = tb.add_gemm(ss);
       H.upd = tb.add_gemm(upd);
       lp.heights.push_back(H);
     }
-    lp.fin1 = tb.add_gemm(f1);
-    lp.fin2 = tb.add_gemm(f2);
     lp.down1 = tb.add_gemm(d1);
     lp.down2 = tb.add_gemm(d2);
   }

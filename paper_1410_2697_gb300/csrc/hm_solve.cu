@@ -3,13 +3,16 @@
 // (Eq. downward: x_p = F_pp^-1 (b_p - F_pf x_f), root to leaves), with the HODLR pivot
 // solves and low-rank coupling blocks of Section 4.2.2 for HODLR fronts.
 //
-// Every front p owns a vector fv_p of length nhat_p = |I_p| + |I_p^f| (per RHS).  Upward:
-// fv_p = [r(I_p); 0] (+) children's update parts (extend-add of vectors, fixed child
-// order), then dense fronts run a column-oriented forward substitution over all nhat_p
-// rows (which also applies -L_fp z_p to the update part); HODLR fronts run y = F_pp^-1 b_p
-// and f <- f - W (Vf^T y).  Downward: x_f is gathered from the finished ancestors, dense
-// fronts solve L^T x_p = z_p - L_fp^T x_f, HODLR fronts x_p = y - Vtilde (W^T x_f) with
-// Vtilde = F_pp^-1 Vf kept by the factorization.
+// Every front p owns a vector fv_p of length nhat_p = |I_p| + |I_p^f| (per RHS).
+// Upward: fv_p = [r(I_p); 0] (+) the children's update parts (extend-add of vectors in
+// fixed child order), then b_f <- b_f - F_fp F_pp^{-1} b_p: dense fronts keep
+// K = F_fp F_pp^{-1} from the factorization (a GEMV), HODLR fronts use
+// Vf^T F_pp^{-1} = Vtilde^T (F_pp^HODLR symmetric) so b_f -= W (Vtilde^T b_p) needs no
+// pivot solve.  Downward: x_f is gathered from the finished ancestors; dense fronts
+// x_p = F_pp^{-1} b_p - K^T x_f (F_pp^{-1} stored explicitly); HODLR fronts solve
+// y = F_pp^{-1} b_p by recursive Woodbury (explicit leaf inverses, then per level
+// y -= Zhat C^{-1} Z^T y with explicit core inverses) and x_p = y - Vtilde (W^T x_f).
+// Every step is a GEMV / batched GEMM; nothing is solved by sequential substitution.
 #include "hm_internal.h"
 
 namespace hm {
@@ -48,18 +51,14 @@ __global__ void __launch_bounds__(256) k_up(const int* __restrict__ fronts, int 
     }
     __syncthreads();
   }
-  if (hkind[q] >= 0) return;
-  const T* L = F + front_off[q];
-  for (int j = 0; j < np; ++j) {
-    const T dj = L[j + (int64_t)j * nh];
-    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) fv[j + (int64_t)r * nh] /= dj;
-    __syncthreads();
-    const int rows = nh - j - 1;
-    for (int e = threadIdx.x; e < rows * nrhs; e += blockDim.x) {
-      const int i = j + 1 + e % rows, r = e / rows;
-      fv[i + (int64_t)r * nh] -= L[i + (int64_t)j * nh] * fv[j + (int64_t)r * nh];
-    }
-    __syncthreads();
+  if (hkind[q] >= 0 || nu == 0) return;
+  const T* K = F + front_off[q] + np;  // K(t, j) = K[t + j * nh]
+  for (int e = threadIdx.x; e < nu * nrhs; e += blockDim.x) {
+    const int t = e % nu, r = e / nu;
+    const T* bp = fv + (int64_t)r * nh;
+    T s = T(0);
+    for (int j = 0; j < np; ++j) s += K[t + (int64_t)j * nh] * bp[j];
+    fv[np + t + (int64_t)r * nh] -= s;
   }
 }
 
@@ -83,51 +82,43 @@ __global__ void __launch_bounds__(256) k_down(const int* __restrict__ fronts, in
   }
   __syncthreads();
   if (hkind[q] >= 0) return;
-  const T* L = F + front_off[q];
-  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
+  // x_p(j) = sum_i Finv(i, j) b_p(i) - sum_t K(t, j) x_f(t): one warp per (j, r), lanes
+  // run over i and t (Finv is symmetric, so both reads are column-contiguous)
+  const T* Fq = F + front_off[q];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = wid; e < np * nrhs; e += nw) {
     const int j = e % np, r = e / np;
-    const T* lc = L + np + (int64_t)j * nh;
-    const T* xf = fv + np + (int64_t)r * nh;
+    const T* col = Fq + (int64_t)j * nh;  // Finv(:, j) then K(:, j)
+    const T* v = fv + (int64_t)r * nh;    // b_p then x_f
     T s = T(0);
-    for (int t = 0; t < nu; ++t) s += lc[t] * xf[t];
-    fv[j + (int64_t)r * nh] -= s;
-  }
-  __syncthreads();
-  for (int j = np - 1; j >= 0; --j) {
-    const T dj = L[j + (int64_t)j * nh];
-    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) fv[j + (int64_t)r * nh] /= dj;
-    __syncthreads();
-    for (int e = threadIdx.x; e < j * nrhs; e += blockDim.x) {
-      const int i = e % j, r = e / j;
-      fv[i + (int64_t)r * nh] -= L[j + (int64_t)i * nh] * fv[j + (int64_t)r * nh];
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
-    const int i = e % np, r = e / np;
-    xout[b0 + i + (int64_t)r * n] = fv[i + (int64_t)r * nh];
+    for (int i = lane; i < np; i += 32) s += col[i] * v[i];
+    for (int t = lane; t < nu; t += 32) s -= col[np + t] * v[np + t];
+    s = warp_sum(s);
+    if (lane == 0) xout[b0 + j + (int64_t)r * n] = s;
   }
 }
 
-// HODLR fronts: x_p (already y - Vtilde W^T x_f in fv) -> output vector.
+// HODLR fronts: x_p (= y - Vtilde W^T x_f, in the front's y buffer) -> output vector.
 template <typename T>
 __global__ void k_hodlr_out(const int* __restrict__ fronts, int nrhs, int n, T* __restrict__ xout,
                             const int32_t* __restrict__ first, const int* __restrict__ npiv,
-                            const int* __restrict__ nhat, const int* __restrict__ hkind,
-                            const int64_t* __restrict__ fvoff, const T* __restrict__ FV) {
+                            const int64_t* __restrict__ yvoff, const T* __restrict__ SB) {
   const int q = fronts[blockIdx.x];
-  if (hkind[q] < 0) return;
-  const int np = npiv[q], nh = nhat[q], b0 = first[q];
-  const T* fv = FV + fvoff[q];
+  const int64_t yo = yvoff[q];
+  if (yo < 0) return;
+  const int np = npiv[q], b0 = first[q];
+  const T* y = SB + yo;
   for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
     const int i = e % np, r = e / np;
-    xout[b0 + i + (int64_t)r * n] = fv[i + (int64_t)r * nh];
+    xout[b0 + i + (int64_t)r * n] = y[i + (int64_t)r * np];
   }
 }
 
 template <typename T>
-static void gemm_b(const GemmBatch& b, const unsigned char* base, cudaStream_t s) {
-  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, s);
+static void gemm_b(hm_ctx_s* ctx, const GemmBatch& b, const unsigned char* base) {
+  if (b.tiles.count == 0) return;
+  ProfScope ps(ctx, PC_GEMM_APPLY, b.tasks.work);
+  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, ctx->stream);
 }
 
 template <typename T>
@@ -135,35 +126,45 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
   SolvePlan* sp = nullptr;
   HM_TRY(get_solve_plan(sys, nrhs, &sp));
   Plan& P = sys->plan;
-  cudaStream_t s = sys->ctx->stream;
+  hm_ctx_s* ctx = sys->ctx;
+  cudaStream_t s = ctx->stream;
   const unsigned char* base = sp->d_tasks;
   const T* F = (const T*)sys->d_front;
   T* FV = (T*)sp->d_fv;
   const int n = sys->n;
   for (int l = P.nlevels - 1; l >= 0; --l) {
     const LevelSolvePlan& lp = sp->levels[l];
-    k_up<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, win, sys->d_first, P.d_np,
-                                       P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
-                                       sys->d_child_ptr, sys->d_child_list, sys->d_ifoff,
-                                       sys->d_relmap, F, FV);
-    launch_chol_solve<T>(lp.leaf.dev(base), lp.leaf.count, lp.leaf_maxn, s);
-    for (const auto& H : lp.heights) {
-      gemm_b<T>(H.t, base, s);
-      launch_lu_solve<T>(H.lus.dev(base), H.lus.count, H.lus_maxcols, s);
-      gemm_b<T>(H.upd, base, s);
+    {
+      ProfScope ps(ctx, PC_UP, lp.up_work);
+      k_up<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, win, sys->d_first, P.d_np,
+                                         P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
+                                         sys->d_child_ptr, sys->d_child_list, sys->d_ifoff,
+                                         sys->d_relmap, F, FV);
     }
-    gemm_b<T>(lp.fin1, base, s);
-    gemm_b<T>(lp.fin2, base, s);
+    gemm_b<T>(ctx, lp.up1, base);
+    gemm_b<T>(ctx, lp.up2, base);
   }
   for (int l = 0; l < P.nlevels; ++l) {
     const LevelSolvePlan& lp = sp->levels[l];
-    k_down<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first, P.d_np,
-                                         P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
-                                         sys->d_ifoff, sys->d_iflist, F, FV);
-    gemm_b<T>(lp.down1, base, s);
-    gemm_b<T>(lp.down2, base, s);
-    k_hodlr_out<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first,
-                                              P.d_np, P.d_nhat, P.d_hkind, sp->d_fvoff, FV);
+    {
+      ProfScope ps(ctx, PC_DOWN, lp.down_work);
+      k_down<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first, P.d_np,
+                                           P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
+                                           sys->d_ifoff, sys->d_iflist, F, FV);
+    }
+    if (lp.n_hodlr) {
+      gemm_b<T>(ctx, lp.leaf, base);
+      for (const auto& H : lp.heights) {
+        gemm_b<T>(ctx, H.t, base);
+        gemm_b<T>(ctx, H.s, base);
+        gemm_b<T>(ctx, H.upd, base);
+      }
+      gemm_b<T>(ctx, lp.down1, base);
+      gemm_b<T>(ctx, lp.down2, base);
+      ProfScope ps(ctx, PC_VECTOR, Work{});
+      k_hodlr_out<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first,
+                                                P.d_np, sp->d_yvoff, (const T*)sp->d_sb);
+    }
   }
   HM_CUDA(cudaGetLastError());
   return HM_OK;

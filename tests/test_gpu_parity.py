@@ -118,7 +118,7 @@ def test_hodlr_updates_match_oracle_rrf(name):
         kind, rk = hm.hm_get_front_ranks(s.sys, q)
         assert kind == (1 if fr[q].kind == "hodlr" else 0)
         if kind == 1:
-            expect = [oranks[q]["fp"]] + [r for (_, _, r) in oranks[q]["pp"]]
+            expect = [oranks[q]["fp"]] + [r for (_, _, r) in sorted(oranks[q]["pp"])]
             if list(rk) != expect:
                 mismatched += 1
                 assert np.abs(np.array(rk) - np.array(expect)).max() <= 1, (q, rk, expect)
