@@ -52,6 +52,10 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-out", default=None, help="write per-kernel profile JSON here")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="mixed arm only, no e2e / FP64 / CPU legs (for an ncu launch list)")
+    ap.add_argument("--cpu-m", type=int, default=256,
+                    help="grid of the bounded CPU-oracle sample (same family)")
     return ap.parse_args()
 
 
@@ -169,6 +173,23 @@ COMPUTE_CATS = {"gemm_factor", "gemm_apply", "dense_potrf", "dense_trsm", "house
                 "jacobi_svd", "core_lu_inverse", "spd_inverse", "leaf_solve"}
 
 
+def ncu_traffic(category: str):
+    """DRAM bytes per launch of `category` from the committed ncu summaries (a line
+    'TRAFFIC <category> <bytes> <sha1 of the source file>'), or None if none was
+    captured or the kernel's source changed since."""
+    import glob
+    import hashlib
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for ln in open(f):
+            parts = ln.split()
+            if len(parts) == 4 and parts[0] == "TRAFFIC" and parts[1] == category:
+                src = os.path.join(ROOT, "paper_1410_2697_gb300", "csrc", "hm_solve.cu")
+                if hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] != parts[3]:
+                    return None
+                return float(parts[2])
+    return None
+
+
 def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
     cat = max(prof, key=lambda c: prof[c]["ms"])
     e = prof[cat]
@@ -185,7 +206,7 @@ def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
     achieved = (e["bytes"] / max(e["launches"], 1)) / (per_launch_ms * 1e-3) / 1e9
     peak = (peaks or {}).get("hbm_gbs") or 6800.0
     return {"kernel": cat, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "launches": e["launches"],
+            "frac": achieved / peak, "traffic": ncu_traffic(cat), "launches": e["launches"],
             "avg_launch_ms": per_launch_ms,
             "share_of_profiled_time": e["ms"] / sum(v["ms"] for v in prof.values()),
             "peak_source": "measured" if peaks else "fallback"}
@@ -260,13 +281,19 @@ def run_ours(args, rank, world, local):
         step(ctx, *dev_inputs)
     clocks = ClockSampler(local)
     clocks.start()
-    per, total, infos, prof = timed(ctx, args.steps, dev_inputs, profile=True)
+    per, total, infos, _ = timed(ctx, args.steps, dev_inputs)
+    # the same steps again with every launch bracketed by CUDA events (launch profile)
+    _, _, _, prof = timed(ctx, args.steps, dev_inputs, profile=True)
     clk = clocks.stop()
     total_max = allreduce_max(total, world)
     x = d_x.cpu().numpy().T
     A = P.scipy()
     relres = max(float(np.linalg.norm(b[:, c] - A @ x[:, c]) / np.linalg.norm(b[:, c])) for c in range(nrhs))
 
+    if args.profile_run:
+        hm.hm_ctx_destroy(ctx)
+        return {"profile_run": True, "ms_per_step": total_max / args.steps, "relres": relres,
+                "gmres_iters": infos[-1][1]["iters"], "profile": prof}
     # ---------------- e2e: pinned host inputs, copies inside the timed region
     def pinned(a):
         t = torch.empty(a.shape, dtype={np.int64: torch.int64, np.int32: torch.int32,
@@ -296,7 +323,7 @@ def run_ours(args, rank, world, local):
     fi, si = infos[-1]
     peaks = load_peaks()
     rl = roofline(prof, "f32", peaks, clk)
-    kernels = sum(v["kernels"] for v in prof.values())
+    kernels = sum(v["kernels"] for v in prof.values())  # per profiled pass of K steps
     per_sorted = sorted(per)
     p50 = statistics.median(per)
     p99 = per_sorted[min(len(per_sorted) - 1, int(round(0.99 * (len(per_sorted) - 1))))]
@@ -363,11 +390,15 @@ def cpu_cores() -> int:
 
 
 def cpu_baseline(m: int) -> dict:
+    """The oracle as it stands on a bounded sample: one right-hand side on an m x m grid
+    of the same lognormal family (the full 1024 x 1024 factorization alone takes minutes
+    in the oracle), analyze + factor + GMRES, on all host cores."""
     sec, solves, rr = oracle_solve_once(m, 1)
     return {"value": solves / sec, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"one of the 16 right-hand sides of the {m}x{m} workload: analyze + FP64 "
-                      f"HODLR-MF factor (SVD truncation) + GMRES to 1e-10 on the host, {sec:.1f} s "
-                      f"(BLAS threads = all cores); relres {rr:.1e}"}
+            "sample": f"{m}x{m} grid of the same lognormal Q1 family ({(m - 1) ** 2} unknowns), one "
+                      f"right-hand side: analyze + FP64 HODLR-MF factor (SVD truncation) + GMRES to "
+                      f"1e-10 on the host in {sec:.1f} s (BLAS threads = all cores), relres {rr:.1e}; "
+                      f"not scaled to the 1024x1024 size"}
 
 
 def run_reference(args, rank, world):
@@ -406,11 +437,12 @@ def main():
         return
     # The host oracle runs before any GPU work in this process (no fork after CUDA init).
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.m)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_run:
+        cpu = cpu_baseline(min(args.cpu_m, args.m))
     line = run_ours(args, rank, world, local)
     if rank == 0:
-        line["cpu_baseline"] = cpu
+        if not args.profile_run:
+            line["cpu_baseline"] = cpu
         print(json.dumps(line))
 
 

@@ -263,6 +263,7 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   ctx->num_sms = prop.multiProcessorCount;
   int st = dense_fact_setup(ctx->max_smem);
   if (st == HM_OK) st = dense_comp_setup(ctx->max_smem);
+  if (st == HM_OK) st = solve_setup(ctx->max_smem);
   if (st != HM_OK) {
     delete ctx;
     return st;

@@ -112,7 +112,8 @@ void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStre
 template <typename T>
 void launch_omega(const OmegaTask* tasks, int ntasks, uint64_t seed, cudaStream_t s);
 template <typename T>
-void launch_core_lu(const CoreLuTask* tasks, int ntasks, int* err, cudaStream_t s);
+void launch_core_lu(const CoreLuTask* tasks, int ntasks, int maxk, int max_smem, int* err,
+                    cudaStream_t s);
 template <typename T>
 void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStream_t s);
 

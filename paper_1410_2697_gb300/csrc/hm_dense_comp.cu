@@ -123,14 +123,18 @@ void launch_qr(const QrTask* tasks, int ntasks, cudaStream_t s) {
 // =====================================================================================
 template <typename T>
 struct JacobiEps;
+// Rotation threshold |gamma| > eps sqrt(alpha beta): a few units of rounding of the
+// precision (singular values come out with that relative accuracy, far below any
+// truncation tolerance); sweeps are capped at kJacobiSweeps (convergence is quadratic).
 template <>
 struct JacobiEps<float> {
-  static constexpr float v = 1.2e-6f;
+  static constexpr float v = 4e-7f * 8;
 };
 template <>
 struct JacobiEps<double> {
-  static constexpr double v = 2.3e-15;
+  static constexpr double v = 2.3e-16 * 8;
 };
+constexpr int kJacobiSweeps = 12;
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, double tol) {
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int kk = k + (k & 1);
   const T eps = JacobiEps<T>::v;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < kk - 1; ++r) {

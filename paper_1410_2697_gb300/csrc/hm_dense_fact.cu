@@ -152,33 +152,54 @@ void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStr
 }
 
 // =====================================================================================
-// Woodbury core: C = [[U^T Uhat, I], [I, V^T Vhat]] (2k x 2k).  The diagonal blocks were
-// written by GEMMs; this kernel sets the identity blocks and LU-factors C with partial
-// pivoting (C is symmetric indefinite), in global memory (L2-resident), one CTA per core.
-// A zero pivot column raises HM_ERR_BREAKDOWN.
+// Woodbury core: C = [[U^T Uhat, I], [I, V^T Vhat]] (n = 2k).  The GEMMs have written the
+// two diagonal k x k blocks; this kernel sets the identity blocks and inverts C by
+// Gauss-Jordan elimination with partial pivoting on [C | I] (C is symmetric indefinite),
+// one CTA per core.  The augmented matrix lives in shared memory when it fits, otherwise
+// in place in global memory, where the core slot (C then C^{-1}, contiguous) is exactly
+// the n x 2n column-major [C | C^{-1}].  A zero pivot column raises HM_ERR_BREAKDOWN.
 // =====================================================================================
 template <typename T>
-__global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ tasks, int* err) {
+__global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ tasks, int* err,
+                                                 int use_smem) {
+  extern __shared__ unsigned char smem_raw[];
   __shared__ T sval[32];
   __shared__ int sidx[32];
   __shared__ int piv_s;
   const CoreLuTask t = tasks[blockIdx.x];
   const int k = t.k, n = 2 * k;
   T* C = (T*)t.C;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e % k, j = e / k;
-    const T v = (i == j) ? T(1) : T(0);
-    C[(size_t)i + (size_t)(k + j) * n] = v;
-    C[(size_t)(k + i) + (size_t)j * n] = v;
+  T* Ci = (T*)t.Cinv;
+  T* M;
+  int ld;
+  T* fcol = reinterpret_cast<T*>(smem_raw);  // multipliers of the pivot column, n
+  if (use_smem) {
+    ld = n + 1;
+    M = fcol + n;
+  } else {
+    ld = n;
+    M = C;  // [C | Cinv] contiguous, column-major n x 2n
+  }
+  // assemble [C | I]
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    const bool diag_blk = (i < k) == (c < k);
+    const T cv = diag_blk ? C[(size_t)i + (size_t)c * n] : ((i % k == c % k) ? T(1) : T(0));
+    M[i + (size_t)c * ld] = cv;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    M[i + (size_t)(n + c) * ld] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < n; ++j) {
-    // pivot search in column j, rows j..n-1 (largest |.|, lowest row on ties)
+    // pivot: largest |M(i, j)|, i >= j (lowest row on ties)
     T best = T(-1);
     int bi = n;
     for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-      const T v = fabs(C[(size_t)i + (size_t)j * n]);
+      const T v = fabs(M[i + (size_t)j * ld]);
       if (v > best) { best = v; bi = i; }
     }
 #pragma unroll
@@ -192,7 +213,7 @@ __global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ 
     if (threadIdx.x == 0) {
       T b = T(-1);
       int ii = n;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      for (int w = 0; w < nw; ++w)
         if (sval[w] > b || (sval[w] == b && sidx[w] < ii)) { b = sval[w]; ii = sidx[w]; }
       if (!(b > T(0))) {
         raise_error(err, HM_ERR_BREAKDOWN, t.front, j);
@@ -204,47 +225,44 @@ __global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ 
     __syncthreads();
     const int p = piv_s;
     if (p != j)
-      for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        const T a = C[(size_t)j + (size_t)c * n];
-        C[(size_t)j + (size_t)c * n] = C[(size_t)p + (size_t)c * n];
-        C[(size_t)p + (size_t)c * n] = a;
+      for (int c = j + threadIdx.x; c < 2 * n; c += blockDim.x) {
+        const T a = M[j + (size_t)c * ld];
+        M[j + (size_t)c * ld] = M[p + (size_t)c * ld];
+        M[p + (size_t)c * ld] = a;
       }
     __syncthreads();
-    T d = C[(size_t)j + (size_t)j * n];
+    T d = M[j + (size_t)j * ld];
     if (d == T(0)) d = T(1);
     const T inv = T(1) / d;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) C[(size_t)i + (size_t)j * n] *= inv;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) fcol[i] = (i == j) ? T(0) : M[i + (size_t)j * ld];
     __syncthreads();
-    const int m = n - j - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e % m, c = j + 1 + e / m;
-      C[(size_t)i + (size_t)c * n] -= C[(size_t)i + (size_t)j * n] * C[(size_t)j + (size_t)c * n];
+    // scale the pivot row and eliminate column j from every other row: a warp per column,
+    // lanes over rows; columns whose pivot-row entry is zero are untouched
+    for (int c = j + wid; c < 2 * n; c += nw) {
+      const T mjc = M[j + (size_t)c * ld] * inv;
+      __syncwarp();
+      if (lane == 0) M[j + (size_t)c * ld] = mjc;
+      if (mjc != T(0))
+        for (int i = lane; i < n; i += 32)
+          if (i != j) M[i + (size_t)c * ld] -= fcol[i] * mjc;
     }
     __syncthreads();
   }
-  // explicit inverse: column c of C^{-1} solves L U x = P e_c (one thread per column)
-  T* Ci = (T*)t.Cinv;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    T* b = Ci + (size_t)c * n;
-    for (int i = 0; i < n; ++i) b[i] = (i == c) ? T(1) : T(0);
-    for (int j = 0; j < n; ++j) {
-      const int p = t.piv[j];
-      if (p != j) { const T a = b[j]; b[j] = b[p]; b[p] = a; }
+  if (use_smem)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e % n, c = e / n;
+      Ci[(size_t)i + (size_t)c * n] = M[i + (size_t)(n + c) * ld];
     }
-    for (int j = 0; j < n; ++j) {
-      const T v = b[j];
-      if (v != T(0))
-        for (int i = j + 1; i < n; ++i) b[i] -= C[(size_t)i + (size_t)j * n] * v;
-    }
-    for (int j = n - 1; j >= 0; --j) {
-      T d = C[(size_t)j + (size_t)j * n];
-      if (d == T(0)) d = T(1);
-      const T v = b[j] / d;
-      b[j] = v;
-      if (v != T(0))
-        for (int i = 0; i < j; ++i) b[i] -= C[(size_t)i + (size_t)j * n] * v;
-    }
-  }
+}
+
+template <typename T>
+void launch_core_lu(const CoreLuTask* tasks, int ntasks, int maxk, int max_smem, int* err,
+                    cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const int n = 2 * maxk;
+  const size_t smem = ((size_t)(n + 1) * 2 * n + n) * sizeof(T);
+  const int use = smem + 1024 <= (size_t)max_smem ? 1 : 0;
+  k_core_lu<T><<<ntasks, 256, use ? smem : n * sizeof(T), s>>>(tasks, err, use);
 }
 
 // =====================================================================================
@@ -315,11 +333,6 @@ void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStr
   k_chol_inverse<T><<<ntasks, 256, smem, s>>>(tasks);
 }
 
-template <typename T>
-void launch_core_lu(const CoreLuTask* tasks, int ntasks, int* err, cudaStream_t s) {
-  if (ntasks <= 0) return;
-  k_core_lu<T><<<ntasks, 256, 0, s>>>(tasks, err);
-}
 
 template void launch_potrf<float>(const PotrfTask*, int, int, int*, cudaStream_t);
 template void launch_potrf<double>(const PotrfTask*, int, int, int*, cudaStream_t);
@@ -327,8 +340,8 @@ template void launch_trsm<float>(const TrsmTask*, int, int, cudaStream_t);
 template void launch_trsm<double>(const TrsmTask*, int, int, cudaStream_t);
 template void launch_chol_solve<float>(const CholSolveTask*, int, int, cudaStream_t);
 template void launch_chol_solve<double>(const CholSolveTask*, int, int, cudaStream_t);
-template void launch_core_lu<float>(const CoreLuTask*, int, int*, cudaStream_t);
-template void launch_core_lu<double>(const CoreLuTask*, int, int*, cudaStream_t);
+template void launch_core_lu<float>(const CoreLuTask*, int, int, int, int*, cudaStream_t);
+template void launch_core_lu<double>(const CoreLuTask*, int, int, int, int*, cudaStream_t);
 template void launch_chol_inverse<float>(const CholInvTask*, int, int, cudaStream_t);
 template void launch_chol_inverse<double>(const CholInvTask*, int, int, cudaStream_t);
 
@@ -341,6 +354,8 @@ int dense_fact_setup(int max_smem) {
   HM_CUDA(allow_max_dyn_smem(k_chol_solve<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<double>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_lu<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_lu<double>, max_smem));
   return HM_OK;
 }
 

@@ -188,7 +188,7 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
         debug_stage<T>(sys, "core-pre", l);
         {
           ProfScope ps(ctx, PC_CORE_LU, H.lu.work);
-          launch_core_lu<T>(H.lu.dev(base), H.lu.count, sys->d_err, s);
+          launch_core_lu<T>(H.lu.dev(base), H.lu.count, H.lu_maxk, ctx->max_smem, sys->d_err, s);
         }
         debug_stage<T>(sys, "core-lu", l);
         run_gemm<T>(sys, H.sg, base, PC_GEMM_FACTOR);

@@ -187,7 +187,8 @@ struct LevelFactorPlan {
   Span<CholInvTask> leaf_inv;  // explicit leaf inverses for the apply
   struct Height {
     GemmBatch pre;            // core diagonal blocks and t = Z^T X_anc
-    Span<CoreLuTask> lu;      // LU and explicit inverse of the cores
+    Span<CoreLuTask> lu;      // explicit inverse of the cores (Gauss-Jordan)
+    int lu_maxk = 0;
     GemmBatch sg;             // s = C^{-1} t
     GemmBatch upd;            // X_anc -= Zhat s
   };
@@ -374,6 +375,7 @@ int factor_impl(hm_sys_s* sys, const double* d_values, double tol);
 int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out);
 // z (T, n x nrhs, ld n, new numbering) = M^{-1} r (T, same layout)
 int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
+int solve_setup(int max_smem);
 int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
                double* d_x, hm_solve_info* info);
 // permutation helpers (new <-> original numbering), FP64 n x nrhs

@@ -384,6 +384,7 @@ int build_plan(hm_sys_s* sys) {
       LevelFactorPlan::Height H;
       H.pre = tb.add_gemm(pre);
       H.lu = tb.add(lu);
+      for (const auto& c : lu) H.lu_maxk = std::max(H.lu_maxk, c.k);
       H.sg = tb.add_gemm(sg);
       H.upd = tb.add_gemm(upd);
       lp.heights.push_back(H);

@@ -62,6 +62,14 @@ __global__ void __launch_bounds__(256) k_up(const int* __restrict__ fronts, int 
   }
 }
 
+// Downward pass of one front per CTA.  x_f is gathered from the finished ancestors into
+// the update part of fv.  Dense fronts: x_p = G^T [b_p; -x_f] with G = [F_pp^{-1}; K]
+// the front's first np columns (nhat x np, column-major, F_pp^{-1} symmetric), computed
+// as a small GEMM: 32-row slabs of G and of the vector block are staged in shared memory
+// (coalesced), each thread accumulates up to kDownAcc outputs (j, r) in registers.
+constexpr int kDownKC = 32;
+constexpr int kDownAcc = 32;  // np * nrhs <= 256 * kDownAcc (np <= 128, nrhs <= 64)
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_down(const int* __restrict__ fronts, int nrhs, int n,
                                               T* __restrict__ xout, const int32_t* __restrict__ first,
@@ -72,6 +80,7 @@ __global__ void __launch_bounds__(256) k_down(const int* __restrict__ fronts, in
                                               const int64_t* __restrict__ ifoff,
                                               const int32_t* __restrict__ iflist, const T* __restrict__ F,
                                               T* __restrict__ FV) {
+  extern __shared__ unsigned char smem_raw[];
   const int q = fronts[blockIdx.x];
   const int np = npiv[q], nh = nhat[q], nu = nh - np, b0 = first[q];
   T* fv = FV + fvoff[q];
@@ -82,19 +91,44 @@ __global__ void __launch_bounds__(256) k_down(const int* __restrict__ fronts, in
   }
   __syncthreads();
   if (hkind[q] >= 0) return;
-  // x_p(j) = sum_i Finv(i, j) b_p(i) - sum_t K(t, j) x_f(t): one warp per (j, r), lanes
-  // run over i and t (Finv is symmetric, so both reads are column-contiguous)
-  const T* Fq = F + front_off[q];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = wid; e < np * nrhs; e += nw) {
-    const int j = e % np, r = e / np;
-    const T* col = Fq + (int64_t)j * nh;  // Finv(:, j) then K(:, j)
-    const T* v = fv + (int64_t)r * nh;    // b_p then x_f
-    T s = T(0);
-    for (int i = lane; i < np; i += 32) s += col[i] * v[i];
-    for (int t = lane; t < nu; t += 32) s -= col[np + t] * v[np + t];
-    s = warp_sum(s);
-    if (lane == 0) xout[b0 + j + (int64_t)r * n] = s;
+  const T* G = F + front_off[q];
+  T* Gs = reinterpret_cast<T*>(smem_raw);   // [kDownKC][np + 1]
+  T* Vs = Gs + kDownKC * (np + 1);          // [kDownKC][nrhs]
+  const int nout = np * nrhs;
+  T acc[kDownAcc];
+#pragma unroll
+  for (int a = 0; a < kDownAcc; ++a) acc[a] = T(0);
+  for (int k0 = 0; k0 < nh; k0 += kDownKC) {
+    const int kc = min(kDownKC, nh - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kc * np; e += blockDim.x) {
+      const int kk = e % kc, j = e / kc;
+      Gs[kk * (np + 1) + j] = G[(k0 + kk) + (int64_t)j * nh];
+    }
+    for (int e = threadIdx.x; e < kc * nrhs; e += blockDim.x) {
+      const int kk = e % kc, r = e / kc;
+      const T v = fv[(k0 + kk) + (int64_t)r * nh];
+      Vs[kk * nrhs + r] = (k0 + kk < np) ? v : -v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < kDownAcc; ++a) {
+      const int e = threadIdx.x + a * 256;
+      if (e < nout) {
+        const int j = e % np, r = e / np;
+        T s = acc[a];
+        for (int kk = 0; kk < kc; ++kk) s += Gs[kk * (np + 1) + j] * Vs[kk * nrhs + r];
+        acc[a] = s;
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < kDownAcc; ++a) {
+    const int e = threadIdx.x + a * 256;
+    if (e < nout) {
+      const int j = e % np, r = e / np;
+      xout[b0 + j + (int64_t)r * n] = acc[a];
+    }
   }
 }
 
@@ -148,7 +182,8 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
     const LevelSolvePlan& lp = sp->levels[l];
     {
       ProfScope ps(ctx, PC_DOWN, lp.down_work);
-      k_down<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first, P.d_np,
+      const size_t smem = (size_t)kDownKC * (129 + nrhs) * sizeof(T);
+      k_down<T><<<lp.nfronts, 256, smem, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first, P.d_np,
                                            P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
                                            sys->d_ifoff, sys->d_iflist, F, FV);
     }
@@ -167,6 +202,12 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
     }
   }
   HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+int solve_setup(int max_smem) {
+  HM_CUDA(allow_max_dyn_smem(k_down<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_down<double>, max_smem));
   return HM_OK;
 }
 
