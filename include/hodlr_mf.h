@@ -157,6 +157,28 @@ int hm_solve(hm_sys_t sys, int32_t nrhs, const double* b, double rtol, int32_t m
    pivot solves of Section 4.2.2); r, z n x nrhs FP64, original numbering.             */
 int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
 
+/*
+ * hm_precond_apply without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library call cudaMalloc -- programs
+ * whose device memory is owned by another allocator (a framework's caching pool or a
+ * fixed budget), allocator callbacks that must not re-enter the CUDA allocator, and
+ * latency-critical loops that cannot wait on the driver.  It computes the same
+ * z = M^{-1} r as hm_precond_apply.
+ *   r, z      DEVICE pointers, n x nrhs column-major FP64, original numbering.
+ *   Limits    n * nrhs <= 262144 (HM_ERR_CAPACITY beyond).  The per-nrhs workspace of
+ *             the system must exist already: make one hm_precond_apply or hm_solve call
+ *             with the same nrhs first (HM_ERR_STATE otherwise; that call allocates).
+ *   Scratch   the per-call temporaries live in one file-scope device array of 6 MiB that
+ *             every GPU loading the library holds until the process exits.  All calls
+ *             share it, so calls that overlap on the GPU (from several threads or
+ *             streams) race; serialise them.  Each call overwrites every temporary it
+ *             reads, so nothing needs clearing between calls.
+ *   Set-up    the first call on a device looks up the array's device address
+ *             (cudaGetSymbolAddress) with that device current; make that first call
+ *             before any stream capture.
+ */
+int hm_precond_apply_noalloc(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
+
 /* Inspection for tests: the dense Schur-complement update U_p = F_ff - F_fp F_pp^-1 F_pf
    of front p as computed by the last hm_factor (nupd[p]^2 entries, column-major, lower
    triangle valid, FP64).  Host pointer.                                                */

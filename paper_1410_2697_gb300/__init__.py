@@ -16,7 +16,8 @@ from ._binding import (HM_PREC_FP64, HM_PREC_MIXED, HmError, hm_analyze, hm_crea
                        hm_ctx_destroy, hm_default_opts, hm_destroy, hm_factor, hm_get_front_ranks,
                        hm_get_hodlr_block, hm_profile_enable, hm_profile_read,
                        hm_get_ordering, hm_get_sizes, hm_get_symbolic, hm_get_update,
-                       hm_last_error, hm_precond_apply, hm_solve, hm_status_str)
+                       hm_last_error, hm_precond_apply, hm_precond_apply_noalloc, hm_solve,
+                       hm_status_str)
 
 
 class Solver:

@@ -30,6 +30,7 @@ HM_PREC_MIXED = 1
 
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_get_sizes",
             "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_solve", "hm_precond_apply",
+            "hm_precond_apply_noalloc",
             "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error"]
 
 
@@ -80,6 +81,7 @@ def _load():
     lib.hm_factor.argtypes = [vp, vp, dbl, C.POINTER(HmFactorInfo)]
     lib.hm_solve.argtypes = [vp, i32, vp, dbl, i32, vp, C.POINTER(HmSolveInfo)]
     lib.hm_precond_apply.argtypes = [vp, i32, vp, vp]
+    lib.hm_precond_apply_noalloc.argtypes = [vp, i32, vp, vp]
     lib.hm_get_update.argtypes = [vp, i32, vp]
     lib.hm_get_front_ranks.argtypes = [vp, i32, C.POINTER(i32), vp, C.POINTER(i32)]
     lib.hm_get_hodlr_block.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(i32),
@@ -206,6 +208,12 @@ def hm_solve(sys_, nrhs: int, b, rtol: float, max_iters: int, x, raise_on_no_con
 def hm_precond_apply(sys_, nrhs: int, r, z) -> None:
     _check(_lib.hm_precond_apply(sys_, int(nrhs), _ptr(r, np.float64, "r"), _ptr(z, np.float64, "z")),
            "hm_precond_apply")
+
+
+def hm_precond_apply_noalloc(sys_, nrhs: int, r, z) -> None:
+    """Allocation-free z = M^{-1} r: r, z are device tensors (n x nrhs column-major)."""
+    _check(_lib.hm_precond_apply_noalloc(sys_, int(nrhs), _ptr(r, np.float64, "r"),
+                                         _ptr(z, np.float64, "z")), "hm_precond_apply_noalloc")
 
 
 def hm_get_update(sys_, front: int, nupd: int) -> np.ndarray:
