@@ -6,11 +6,13 @@
 namespace hm {
 
 // =====================================================================================
-// Batched GEMM: 64x64 output tiles, BK = 16, 256 threads, 4x4 outputs per thread
-// (rows ty + 16 i, columns tx + 16 j).  Operand tiles are staged through shared memory
-// with the next k-slice prefetched into registers while the current one is consumed.
+// Batched GEMM: 64 x BN output tiles (BN = 64 or 16), BK = 16, 256 threads; a thread owns
+// rows ty + 16 i (i < 4) and columns tx + 16 j (j < BN / 16).  Operand tiles are staged
+// through shared memory with the next k-slice prefetched into registers while the
+// current one is consumed.  The narrow variant serves products with few columns
+// (one right-hand side block of the preconditioner apply).
 // =====================================================================================
-constexpr int BM = kGemmBM, BN = kGemmBN, BK = 16;
+constexpr int BM = kGemmBM, BK = 16;
 
 template <typename T>
 __device__ __forceinline__ T load_op(const T* __restrict__ X, int op, int ld, int r, int c,
@@ -20,9 +22,11 @@ __device__ __forceinline__ T load_op(const T* __restrict__ X, int op, int ld, in
   return op == 0 ? X[(size_t)r + (size_t)c * ld] : X[(size_t)c + (size_t)r * ld];
 }
 
-template <typename T>
+template <typename T, int BN>
 __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks,
                                               const GemmTile* __restrict__ tiles) {
+  constexpr int TN = BN / 16;       // columns per thread
+  constexpr int NB = BK * BN / 256; // B elements loaded per thread
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
   const GemmTile tl = tiles[blockIdx.x];
@@ -32,14 +36,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   const T* __restrict__ B = (const T*)t.B;
   T* __restrict__ C = (T*)t.C;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  T acc[4][4];
+  T acc[4][TN];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
-  // load coordinates: 4 elements per thread per operand tile
-  T ra[4], rb[4];
+  T ra[4], rb[NB];
   auto fetch = [&](int k0) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -47,6 +50,10 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
       int r, p;
       if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
       ra[q] = load_op(A, t.opA, t.lda, m0 + r, k0 + p, t.m, t.k);
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + 256 * q;
       int c, pb;
       if (t.opB == 0) { pb = e % BK; c = e / BK; } else { c = e % BN; pb = e / BN; }
       rb[q] = load_op(B, t.opB, t.ldb, k0 + pb, n0 + c, t.k, t.n);
@@ -59,6 +66,10 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
       int r, p;
       if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
       As[p][r] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + 256 * q;
       int c, pb;
       if (t.opB == 0) { pb = e % BK; c = e / BK; } else { c = e % BN; pb = e / BN; }
       Bs[pb][c] = rb[q];
@@ -73,20 +84,20 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     if (k0 + BK < t.k) fetch(k0 + BK);
 #pragma unroll
     for (int p = 0; p < BK; ++p) {
-      T a[4], b[4];
+      T a[4], b[TN];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[p][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[p][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[p][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
   }
   const T alpha = (T)t.alpha, beta = (T)t.beta;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < TN; ++j) {
     const int c = n0 + tx + 16 * j;
     if (c >= t.n) continue;
 #pragma unroll
@@ -101,23 +112,30 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   }
 }
 
-void gemm_tiles_for(const GemmTask& t, int task_index, std::vector<GemmTile>* out) {
+int gemm_bn_for(const std::vector<GemmTask>& t) {
+  int nmax = 0;
+  for (const auto& x : t) nmax = std::max(nmax, x.n);
+  return nmax <= 16 ? 16 : 64;
+}
+
+void gemm_tiles_for(const GemmTask& t, int task_index, int bn, std::vector<GemmTile>* out) {
   if (t.m <= 0 || t.n <= 0) return;
-  const int tm = (t.m + BM - 1) / BM, tn = (t.n + BN - 1) / BN;
+  const int tm = (t.m + BM - 1) / BM, tn = (t.n + bn - 1) / bn;
   for (int a = 0; a < tm; ++a)
     for (int b = 0; b < tn; ++b) {
-      if (t.lower && (a + 1) * BM - 1 < b * BN) continue;  // tile strictly above diagonal
+      if (t.lower && (a + 1) * BM - 1 < b * bn) continue;  // tile strictly above diagonal
       out->push_back(GemmTile{task_index, (a << 16) | b});
     }
 }
 
 template <typename T>
-void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, cudaStream_t s) {
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, cudaStream_t s) {
   if (ntiles <= 0) return;
-  k_gemm<T><<<ntiles, 256, 0, s>>>(tasks, tiles);
+  if (bn == 16) k_gemm<T, 16><<<ntiles, 256, 0, s>>>(tasks, tiles);
+  else k_gemm<T, 64><<<ntiles, 256, 0, s>>>(tasks, tiles);
 }
 
-template void launch_gemm<float>(const GemmTask*, const GemmTile*, int, cudaStream_t);
-template void launch_gemm<double>(const GemmTask*, const GemmTile*, int, cudaStream_t);
+template void launch_gemm<float>(const GemmTask*, const GemmTile*, int, int, cudaStream_t);
+template void launch_gemm<double>(const GemmTask*, const GemmTile*, int, int, cudaStream_t);
 
 }  // namespace hm

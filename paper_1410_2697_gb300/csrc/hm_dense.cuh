@@ -98,7 +98,7 @@ struct CholInvTask {
 };
 
 template <typename T>
-void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, cudaStream_t s);
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, cudaStream_t s);
 template <typename T>
 void launch_potrf(const PotrfTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s);
 template <typename T>
@@ -117,9 +117,10 @@ void launch_core_lu(const CoreLuTask* tasks, int ntasks, int maxk, int max_smem,
 template <typename T>
 void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStream_t s);
 
-// Host-side: append the tiles of one task (all tiles, or those touching the lower
-// triangle when t.lower).
-void gemm_tiles_for(const GemmTask& t, int task_index, std::vector<GemmTile>* out);
+// Host-side: tile width (64, or 16 when every task has at most 16 columns) and the tiles
+// of one task (all tiles, or those touching the lower triangle when t.lower).
+int gemm_bn_for(const std::vector<GemmTask>& t);
+void gemm_tiles_for(const GemmTask& t, int task_index, int bn, std::vector<GemmTile>* out);
 
 int dense_fact_setup(int max_dyn_smem);
 int dense_comp_setup(int max_dyn_smem);

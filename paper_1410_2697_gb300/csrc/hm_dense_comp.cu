@@ -152,41 +152,54 @@ __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, 
     V[i + c * ls] = (i == c) ? T(1) : T(0);
   }
   __syncthreads();
+  // one 16-lane group per column pair; every group runs the same number of passes so
+  // the width-16 shuffles are always executed by full warps
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gl = threadIdx.x & 15, gid = threadIdx.x >> 4, ng = blockDim.x >> 4;
   const int kk = k + (k & 1);
+  const int npairs = kk / 2;
   const T eps = JacobiEps<T>::v;
   for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < kk - 1; ++r) {
-      for (int pi = wid; pi < kk / 2; pi += nw) {
-        const int a = (pi == 0) ? 0 : 1 + ((pi - 1 + r) % (kk - 1));
-        const int b = 1 + ((kk - 2 - pi + r) % (kk - 1));
-        if (a >= k || b >= k) continue;
+      for (int base = 0; base < npairs; base += ng) {
+        const int pi = base + gid;
+        int a = 0, b = 0;
+        bool valid = pi < npairs;
+        if (valid) {
+          a = (pi == 0) ? 0 : 1 + ((pi - 1 + r) % (kk - 1));
+          b = 1 + ((kk - 2 - pi + r) % (kk - 1));
+          valid = a < k && b < k;
+        }
         const int p = min(a, b), q = max(a, b);
         T al = T(0), be = T(0), ga = T(0);
-        for (int i = lane; i < k; i += 32) {
-          const T mp = M[i + p * ls], mq = M[i + q * ls];
-          al += mp * mp;
-          be += mq * mq;
-          ga += mp * mq;
+        if (valid)
+          for (int i = gl; i < k; i += 16) {
+            const T mp = M[i + p * ls], mq = M[i + q * ls];
+            al += mp * mp;
+            be += mq * mq;
+            ga += mp * mq;
+          }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o, 16);
+          be += __shfl_xor_sync(0xffffffffu, be, o, 16);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o, 16);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga != T(0) && fabs(ga) > eps * sqrt(al * be)) {
+        if (valid && ga != T(0) && fabs(ga) > eps * sqrt(al * be)) {
           const T zeta = (be - al) / (T(2) * ga);
           const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          const T c = T(1) / sqrt(T(1) + tt * tt), s = c * tt;
-          for (int i = lane; i < k; i += 32) {
+          const T c = T(1) / sqrt(T(1) + tt * tt), sn = c * tt;
+          for (int i = gl; i < k; i += 16) {
             const T mp = M[i + p * ls], mq = M[i + q * ls];
-            M[i + p * ls] = c * mp - s * mq;
-            M[i + q * ls] = s * mp + c * mq;
+            M[i + p * ls] = c * mp - sn * mq;
+            M[i + q * ls] = sn * mp + c * mq;
             const T vp = V[i + p * ls], vq = V[i + q * ls];
-            V[i + p * ls] = c * vp - s * vq;
-            V[i + q * ls] = s * vp + c * vq;
+            V[i + p * ls] = c * vp - sn * vq;
+            V[i + q * ls] = sn * vp + c * vq;
           }
-          if (lane == 0) rotated = 1;
+          if (gl == 0) rotated = 1;
         }
       }
       __syncthreads();

@@ -17,22 +17,41 @@ namespace hm {
 
 constexpr int kDotThreads = 256;
 
-// y[r] = A x[r]  (mode 0)   or   y[r] = b[r] - A x[r]  (mode 1); rows in new numbering.
+// y[r] = A x[r]  (b == nullptr)   or   y[r] = b[r] - A x[r]; rows in new numbering.
+// One thread per row and four right-hand sides (blockIdx.y selects the group of four):
+// the row's column indices and values are read once and reused for the four products.
+constexpr int kSpmvR = 4;
+
 template <typename XT>
-__global__ void k_spmv(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                       const double* __restrict__ val, int n, int nrhs, const XT* __restrict__ x,
-                       int64_t ldx, double* __restrict__ y, int64_t ldy, const double* __restrict__ b,
-                       int64_t ldb) {
+__global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rowptr,
+                                              const int32_t* __restrict__ col,
+                                              const double* __restrict__ val, int n, int nrhs,
+                                              const XT* __restrict__ x, int64_t ldx,
+                                              double* __restrict__ y, int64_t ldy,
+                                              const double* __restrict__ b, int64_t ldb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int r0 = blockIdx.y * kSpmvR;
+  const int nr = min(kSpmvR, nrhs - r0);
   const int64_t kb = rowptr[i], ke = rowptr[i + 1];
-  for (int r = 0; r < nrhs; ++r) {
-    const XT* xr = x + r * ldx;
-    double s = 0.0;
-    for (int64_t k = kb; k < ke; ++k) s = fma(val[k], (double)xr[col[k]], s);
-    y[i + r * ldy] = b ? b[i + r * ldb] - s : s;
+  double s[kSpmvR] = {0.0, 0.0, 0.0, 0.0};
+  const XT* x0 = x + (int64_t)r0 * ldx;
+  for (int64_t k = kb; k < ke; ++k) {
+    const int c = col[k];
+    const double v = val[k];
+#pragma unroll
+    for (int q = 0; q < kSpmvR; ++q)
+      if (q < nr) s[q] = fma(v, (double)x0[c + (int64_t)q * ldx], s[q]);
   }
+#pragma unroll
+  for (int q = 0; q < kSpmvR; ++q)
+    if (q < nr) {
+      const int r = r0 + q;
+      y[i + (int64_t)r * ldy] = b ? b[i + (int64_t)r * ldb] - s[q] : s[q];
+    }
 }
+
+static dim3 spmv_grid(int n, int nrhs) { return dim3((n + 255) / 256, (nrhs + kSpmvR - 1) / kSpmvR); }
 
 // part[(r*nblk + blk)*stride + i] = sum over the block's rows of V_i[r] . w[r], i < nvec.
 // V_i[r] starts at V + (i*nrhs + r)*n.
@@ -75,30 +94,31 @@ __global__ void k_add_cols(double* __restrict__ a, const double* __restrict__ b,
   a[(int64_t)r * stride + i] += b[(int64_t)r * stride + i];
 }
 
-// w[r] -= sum_{i < nvec} V_i[r] * c[r*stride + i]
+// w[r] -= sum_{i < nvec} V_i[r] * c[r*stride + i]   (grid.y = r)
 __global__ void k_gs_update(const double* __restrict__ V, double* __restrict__ w, int n, int nrhs,
                             int nvec, int stride, const double* __restrict__ c) {
-  const int64_t total = (int64_t)n * nrhs;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / n);
-    const int64_t k = e % n;
-    double s = w[e];
-    for (int i = 0; i < nvec; ++i) s -= V[((int64_t)i * nrhs + r) * n + k] * c[(int64_t)r * stride + i];
-    w[e] = s;
+  __shared__ double cs[256];  // nvec <= restart + 1 <= 201
+  const int r = blockIdx.y;
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = c[(int64_t)r * stride + i];
+  __syncthreads();
+  double* wr = w + (int64_t)r * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    double s = wr[k];
+    for (int i = 0; i < nvec; ++i) s -= V[((int64_t)i * nrhs + r) * n + k] * cs[i];
+    wr[k] = s;
   }
 }
 
-// dst[r] = src[r] * (nrm[r] > 0 ? 1/nrm[r] : 0); nrm[r] = sqrt(ss[r*stride])
+// dst[r] = src[r] / ||.||, nrm = sqrt(ss[r*stride]) (0 if the norm is 0)   (grid.y = r)
 __global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, int n, int nrhs,
                         const double* __restrict__ ss, int stride) {
-  const int64_t total = (int64_t)n * nrhs;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / n);
-    const double nr = sqrt(ss[(int64_t)r * stride]);
-    dst[e] = nr > 0.0 ? src[e] / nr : 0.0;
-  }
+  const int r = blockIdx.y;
+  const double nr = sqrt(ss[(int64_t)r * stride]);
+  const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  const double* sr = src + (int64_t)r * n;
+  double* dr = dst + (int64_t)r * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    dr[k] = nr > 0.0 ? sr[k] * inv : 0.0;
 }
 
 // Givens step for column j (thread per RHS): H column = h (h1 + h2), H[j+1,j] = ||w||.
@@ -158,32 +178,34 @@ __global__ void k_backsolve(const double* __restrict__ H, const double* __restri
   for (int i = L; i < m; ++i) yr[i] = 0.0;
 }
 
-// x[r] += sum_{j < len[r]} Z_j[r] y[r][j]
+// x[r] += sum_{j < len[r]} Z_j[r] y[r][j]   (grid.y = r)
 template <typename ZT>
 __global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z, const double* __restrict__ y,
                            const int* __restrict__ len, int n, int nrhs, int m) {
-  const int64_t total = (int64_t)n * nrhs;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / n);
-    const int64_t k = e % n;
-    double s = x[e];
-    const int L = len[r];
-    for (int j = 0; j < L; ++j) s = fma((double)Z[((int64_t)j * nrhs + r) * n + k], y[(int64_t)r * m + j], s);
-    x[e] = s;
+  __shared__ double ys[256];
+  const int r = blockIdx.y;
+  const int L = len[r];
+  for (int j = threadIdx.x; j < L; j += blockDim.x) ys[j] = y[(int64_t)r * m + j];
+  __syncthreads();
+  double* xr = x + (int64_t)r * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    double s = xr[k];
+    for (int j = 0; j < L; ++j) s = fma((double)Z[((int64_t)j * nrhs + r) * n + k], ys[j], s);
+    xr[k] = s;
   }
 }
 
-// Start of a cycle: V_0 = r / beta (inactive systems get 0), g = [beta, 0, ...], len = 0.
+// Start of a cycle: V_0 = r / beta (inactive systems get 0)   (grid.y = r)
 __global__ void k_cycle_init(const double* __restrict__ rvec, double* __restrict__ V0, int n, int nrhs,
                              const double* __restrict__ ss, const int* __restrict__ active) {
-  const int64_t total = (int64_t)n * nrhs;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / n);
-    const double beta = sqrt(ss[r]);
-    V0[e] = (active[r] && beta > 0.0) ? rvec[e] / beta : 0.0;
-  }
+  const int r = blockIdx.y;
+  const double beta = sqrt(ss[r]);
+  const bool on = active[r] && beta > 0.0;
+  const double inv = on ? 1.0 / beta : 0.0;
+  const double* rr = rvec + (int64_t)r * n;
+  double* vr = V0 + (int64_t)r * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    vr[k] = on ? rr[k] * inv : 0.0;
 }
 
 __global__ void k_cycle_g(double* __restrict__ g, int* __restrict__ len, const double* __restrict__ ss,
@@ -255,7 +277,10 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
   const int n = sys->n;
   const int64_t nn = (int64_t)n * nrhs;
   const int stride = m + 2;
-  const int gsz = (int)std::min<int64_t>((nn + 255) / 256, 152 * 8);
+  // vector kernels: grid.y = right-hand side, grid.x covers n (about 8 waves in all)
+  const dim3 vgrid((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
+                                                                       (int64_t)152 * 8 / nrhs + 1)),
+                   (unsigned)nrhs);
   {
     ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, 20.0 * nn});
     launch_permute_in(d_b, G.b, sys->d_perm, n, nrhs, s);
@@ -287,7 +312,7 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
     HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
     {
       ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn}, 2);
-      k_cycle_init<<<gsz, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active);
+      k_cycle_init<<<vgrid, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active);
       k_cycle_g<<<(nrhs + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, nrhs);
     }
     int j = 0;
@@ -302,7 +327,7 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
       {
         ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs,
                                              12.0 * sys->nnz + 8.0 * n + (8.0 + sizeof(T)) * nn});
-        k_spmv<T><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+        k_spmv<T><<<spmv_grid(n, nrhs), 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
                                                   Zj, n, G.w, n, nullptr, 0);
       }
       double* h1 = G.hv;
@@ -317,7 +342,7 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
         }
         {
           ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
-          k_gs_update<<<gsz, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h);
+          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h);
         }
       }
       {
@@ -328,7 +353,7 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
       sqnorm(sys, G.w, wss, 1, nrhs);
       {
         ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn});
-        k_scale<<<gsz, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1);
+        k_scale<<<vgrid, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1);
       }
       {
         ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
@@ -350,11 +375,11 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
     }
     {
       ProfScope ps(sys->ctx, PC_VECTOR, Work{2.0 * jend * nn, (16.0 + sizeof(T) * jend) * nn});
-      k_update_x<T><<<gsz, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m);
+      k_update_x<T><<<vgrid, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m);
     }
     {
       ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});
-      k_spmv<double><<<(n + 255) / 256, 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+      k_spmv<double><<<spmv_grid(n, nrhs), 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
                                                      G.x, n, G.r, n, G.b, n);
     }
     sqnorm(sys, G.r, rss, 1, nrhs);

@@ -71,6 +71,7 @@ struct Span {
 struct GemmBatch {
   Span<GemmTask> tasks;
   Span<GemmTile> tiles;
+  int bn = 64;  // tile width of the batch
 };
 
 // Host builder of the task buffer (one upload after planning).
@@ -90,8 +91,9 @@ struct TaskBuf {
   }
   GemmBatch add_gemm(const std::vector<GemmTask>& t) {
     std::vector<GemmTile> tiles;
-    for (size_t i = 0; i < t.size(); ++i) gemm_tiles_for(t[i], (int)i, &tiles);
     GemmBatch b;
+    b.bn = gemm_bn_for(t);
+    for (size_t i = 0; i < t.size(); ++i) gemm_tiles_for(t[i], (int)i, b.bn, &tiles);
     b.tasks = add(t);
     b.tiles = add(tiles);
     return b;
@@ -202,19 +204,23 @@ struct UpItem {
   int q;
 };
 struct LevelSolvePlan {
-  Span<int> fronts;            // all fronts of the level (gather + dense up / down)
+  Span<int> fronts;            // all fronts of the level
   int nfronts = 0;
-  Work up_work, down_work;     // the up / down front kernels (dense GEMVs + gathers)
+  int max_nhat = 0, max_nu = 0;  // largest nhat_p and |I_p^f| of the level
+  std::vector<Span<int>> slots;  // slot j: fronts of the level with more than j children
+  std::vector<int> slot_max_nu;  // per slot, the largest update size of those children
+  Work up_work, down_work;     // the vector kernels (init + extend-add; gather)
   int n_hodlr = 0;
-  GemmBatch up1, up2;          // HODLR fronts, upward: tf = Vtilde^T b_p ; f -= W tf
-  GemmBatch leaf;              // HODLR fronts, downward: y_leaf = K_leaf^{-1} b_leaf
+  GemmBatch up_gemm;           // dense: f -= K b_p ; HODLR: tf = Vtilde^T b_p
+  GemmBatch up2;               // HODLR: f -= W tf
+  GemmBatch down_gemm;         // dense: x_p = [F_pp^{-1}; K]^T [b_p; -x_f] ; HODLR leaves: y = K^{-1} b
   struct Height {
     GemmBatch t;               // t = [U^T y_a; V^T y_b]
     GemmBatch s;               // s = C^{-1} t
     GemmBatch upd;             // y -= Zhat s
   };
   std::vector<Height> heights;
-  GemmBatch down1, down2;      // tf = W^T x_f ; y -= Vtilde tf
+  GemmBatch down1, down2;      // tf = W^T (-x_f) ; y += Vtilde tf
 };
 
 struct SolvePlan {
@@ -223,11 +229,11 @@ struct SolvePlan {
   std::vector<int64_t> fv_off;  // per front, element offset of its (nhat x nrhs) vector
   int64_t fv_total = 0;
   int64_t sb_total = 0;         // node t/s buffers + tf buffers
-  std::vector<int64_t> node_sb_off;  // not used directly; offsets live in tasks
   TaskBuf tb;
   unsigned char* d_tasks = nullptr;
   void* d_fv = nullptr;         // T
   void* d_sb = nullptr;         // T
+  void* d_xfix = nullptr;       // T, n x nrhs: the solution (task tables point into it)
   int64_t* d_fvoff = nullptr;
   int64_t* d_yvoff = nullptr;   // per front: offset of y (np x nrhs) in the scratch, -1 if dense
 };

@@ -436,6 +436,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   HM_TRY(dev_alloc(sys, &sp->d_sb, (size_t)std::max<int64_t>(sb, 1) * es));
   HM_TRY(dev_alloc(sys, (void**)&sp->d_fvoff, (size_t)nf * 8));
   HM_TRY(dev_alloc(sys, (void**)&sp->d_yvoff, (size_t)nf * 8));
+  HM_TRY(dev_alloc(sys, &sp->d_xfix, (size_t)std::max<int64_t>((int64_t)sys->n * nrhs, 1) * es));
   HM_CUDA(cudaMemcpyAsync(sp->d_fvoff, sp->fv_off.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
                           sys->ctx->stream));
   HM_CUDA(cudaMemcpyAsync(sp->d_yvoff, yvoff.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
@@ -447,6 +448,8 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   void* Cm = sys->d_core;
   void* FV = sp->d_fv;
   void* SB = sp->d_sb;
+  void* XS = sp->d_xfix;
+  const int n = sys->n;
   TaskBuf& tb = sp->tb;
   tb.es = es;
   sp->levels.assign(P.nlevels, LevelSolvePlan());
@@ -455,24 +458,45 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     const auto& fr = P.level_fronts[l];
     lp.fronts = tb.add(fr);
     lp.nfronts = (int)fr.size();
+    // child slots: slot j holds the fronts of the level with more than j children, so
+    // that the vector extend-add of slot j touches each parent once
+    std::vector<std::vector<int>> slot_fronts;
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
-      const double np = g.np, nu = g.nu, nh = g.nhat, R = nrhs;
-      // vectors: gather r(I_p), write fv (nhat), children's update parts read
-      double vec = es * R * (np + 2.0 * nh);
-      for (int c : sys->h_children[q]) vec += es * R * 2.0 * P.fg[c].nu + 4.0 * P.fg[c].nu;
-      lp.up_work.bytes += vec;
-      lp.down_work.bytes += es * R * (2.0 * nu + 2.0 * np) + 4.0 * nu;
-      if (g.hodlr >= 0) {
-        lp.n_hodlr++;
-      } else {
-        lp.up_work.bytes += es * nu * np;              // K
-        lp.up_work.flops += 2.0 * R * nu * np;
-        lp.down_work.bytes += es * (np * np + nu * np);  // F_pp^{-1}, K
-        lp.down_work.flops += 2.0 * R * (np * np + nu * np);
+      lp.max_nhat = std::max(lp.max_nhat, g.nhat);
+      lp.max_nu = std::max(lp.max_nu, g.nu);
+      const auto& ch = sys->h_children[q];
+      if (slot_fronts.size() < ch.size()) {
+        slot_fronts.resize(ch.size());
+        lp.slot_max_nu.resize(ch.size(), 0);
       }
+      for (size_t j = 0; j < ch.size(); ++j) {
+        slot_fronts[j].push_back(q);
+        lp.slot_max_nu[j] = std::max(lp.slot_max_nu[j], P.fg[ch[j]].nu);
+      }
+      const double np = g.np, nu = g.nu, nh = g.nhat, R = nrhs;
+      // up: read r(I_p), write fv (nhat); per child read its update part, read-modify-write
+      // the parent entries and read the relative map.  Down: read x(I_p^f) and the index
+      // list, write the update part.
+      lp.up_work.bytes += es * R * (np + nh);
+      for (int c : ch) lp.up_work.bytes += es * R * 3.0 * P.fg[c].nu + 4.0 * P.fg[c].nu;
+      lp.down_work.bytes += es * R * 2.0 * nu + 4.0 * nu;
+      if (g.hodlr >= 0) lp.n_hodlr++;
     }
-    std::vector<GemmTask> u1, u2, lf, d1, d2;
+    for (const auto& sf : slot_fronts) lp.slots.push_back(tb.add(sf));
+    // dense fronts: up f -= K b_p; down x_p = [F_pp^{-1}; K]^T [b_p; -x_f]
+    std::vector<GemmTask> ug, dg;
+    for (int q : fr) {
+      const FrontGeom& g = P.fg[q];
+      if (g.hodlr >= 0) continue;
+      const int64_t fvq = sp->fv_off[q];
+      if (g.nu > 0)
+        ug.push_back(gemm(at(F, g.off + g.np, es), g.nhat, 0, at(FV, fvq, es), g.nhat, 0,
+                          at(FV, fvq + g.np, es), g.nhat, g.nu, nrhs, g.np, -1.0, 1.0));
+      dg.push_back(gemm(at(F, g.off, es), g.nhat, 1, at(FV, fvq, es), g.nhat, 0,
+                        at(XS, sys->h_first[q], es), n, g.np, nrhs, g.nhat, 1.0, 0.0));
+    }
+    std::vector<GemmTask> u2, d1, d2;
     int maxL = 0;
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
@@ -481,25 +505,25 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
       maxL = std::max(maxL, h.L);
       const int64_t fvq = sp->fv_off[q], yq = front_yv[g.hodlr];
       for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
-        const int lo = h.leaf_lo[li], n = h.leaf_hi[li] - lo;
-        lf.push_back(gemm(at(F, g.off + lo + (int64_t)lo * g.nhat, es), g.nhat, 0, at(FV, fvq + lo, es),
-                          g.nhat, 0, at(SB, yq + lo, es), h.np, n, nrhs, n, 1.0, 0.0));
+        const int lo = h.leaf_lo[li], nl = h.leaf_hi[li] - lo;
+        dg.push_back(gemm(at(F, g.off + lo + (int64_t)lo * g.nhat, es), g.nhat, 0, at(FV, fvq + lo, es),
+                          g.nhat, 0, at(SB, yq + lo, es), h.np, nl, nrhs, nl, 1.0, 0.0));
       }
       if (h.kf > 0) {
         void* tf = at(SB, front_sb[g.hodlr], es);
-        u1.push_back(gemm(at(X, h.bo_off, es), h.np, 1, at(FV, fvq, es), g.nhat, 0, tf, h.kf, h.kf,
+        ug.push_back(gemm(at(X, h.bo_off, es), h.np, 1, at(FV, fvq, es), g.nhat, 0, tf, h.kf, h.kf,
                           nrhs, h.np, 1.0, 0.0));
         u2.push_back(gemm(at(W, h.w_off, es), h.nu, 0, tf, h.kf, 0, at(FV, fvq + h.np, es), g.nhat,
                           h.nu, nrhs, h.kf, -1.0, 1.0));
         d1.push_back(gemm(at(W, h.w_off, es), h.nu, 1, at(FV, fvq + h.np, es), g.nhat, 0, tf, h.kf,
                           h.kf, nrhs, h.nu, 1.0, 0.0));
         d2.push_back(gemm(at(X, h.bo_off, es), h.np, 0, tf, h.kf, 0, at(SB, yq, es), h.np, h.np,
-                          nrhs, h.kf, -1.0, 1.0));
+                          nrhs, h.kf, 1.0, 1.0));
       }
     }
-    lp.up1 = tb.add_gemm(u1);
+    lp.up_gemm = tb.add_gemm(ug);
     lp.up2 = tb.add_gemm(u2);
-    lp.leaf = tb.add_gemm(lf);
+    lp.down_gemm = tb.add_gemm(dg);
     for (int ht = 1; ht <= maxL; ++ht) {
       std::vector<GemmTask> tt, ss, upd;
       for (int q : fr) {

@@ -3,133 +3,86 @@
 // (Eq. downward: x_p = F_pp^-1 (b_p - F_pf x_f), root to leaves), with the HODLR pivot
 // solves and low-rank coupling blocks of Section 4.2.2 for HODLR fronts.
 //
-// Every front p owns a vector fv_p of length nhat_p = |I_p| + |I_p^f| (per RHS).
-// Upward: fv_p = [r(I_p); 0] (+) the children's update parts (extend-add of vectors in
-// fixed child order), then b_f <- b_f - F_fp F_pp^{-1} b_p: dense fronts keep
-// K = F_fp F_pp^{-1} from the factorization (a GEMV), HODLR fronts use
-// Vf^T F_pp^{-1} = Vtilde^T (F_pp^HODLR symmetric) so b_f -= W (Vtilde^T b_p) needs no
-// pivot solve.  Downward: x_f is gathered from the finished ancestors; dense fronts
-// x_p = F_pp^{-1} b_p - K^T x_f (F_pp^{-1} stored explicitly); HODLR fronts solve
+// Every front p owns a vector block fv_p (nhat_p x nrhs, nhat_p = |I_p| + |I_p^f|).
+// Upward, per tree level: fv_p = [r(I_p); 0] (flat kernel), then the children's update
+// parts are added through the relative maps one child slot at a time (fixed order), then
+// b_f <- b_f - F_fp F_pp^{-1} b_p as batched GEMMs: dense fronts keep K = F_fp F_pp^{-1}
+// from the factorization; HODLR fronts use Vf^T F_pp^{-1} = Vtilde^T (F_pp^HODLR is
+// symmetric), so b_f -= W (Vtilde^T b_p) needs no pivot solve.  Downward: fv_p's update
+// part receives -x(I_p^f) from the finished ancestors; a dense front's solution is the
+// single GEMM x_p = [F_pp^{-1}; K]^T fv_p = F_pp^{-1} b_p - K^T x_f; a HODLR front solves
 // y = F_pp^{-1} b_p by recursive Woodbury (explicit leaf inverses, then per level
 // y -= Zhat C^{-1} Z^T y with explicit core inverses) and x_p = y - Vtilde (W^T x_f).
-// Every step is a GEMV / batched GEMM; nothing is solved by sequential substitution.
+// Every step is a flat vector kernel or a batched GEMM; nothing is solved by sequential
+// substitution.
+#include <algorithm>
+
 #include "hm_internal.h"
 
 namespace hm {
 
+// Flat vector kernels of the apply: one warp per (front, right-hand side, chunk of 256
+// rows); grid = (ceil(fronts / 8), nrhs, chunks), 8 warps per block.
+constexpr int kVecChunk = 256;
+
+// fv_q = [r(I_q); 0] for every front q of the level.
 template <typename T>
-__global__ void __launch_bounds__(256) k_up(const int* __restrict__ fronts, int nrhs, int n,
-                                            const T* __restrict__ win, const int32_t* __restrict__ first,
-                                            const int* __restrict__ npiv, const int* __restrict__ nhat,
-                                            const int* __restrict__ hkind, const int64_t* __restrict__ front_off,
-                                            const int64_t* __restrict__ fvoff,
-                                            const int32_t* __restrict__ child_ptr,
-                                            const int32_t* __restrict__ child_list,
-                                            const int64_t* __restrict__ ifoff,
-                                            const int32_t* __restrict__ relmap, const T* __restrict__ F,
-                                            T* __restrict__ FV) {
-  const int q = fronts[blockIdx.x];
-  const int np = npiv[q], nh = nhat[q], nu = nh - np, b0 = first[q];
-  T* fv = FV + fvoff[q];
-  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
-    const int i = e % np, r = e / np;
-    fv[i + (int64_t)r * nh] = win[b0 + i + (int64_t)r * n];
-  }
-  for (int e = threadIdx.x; e < nu * nrhs; e += blockDim.x) {
-    const int t = e % nu, r = e / nu;
-    fv[np + t + (int64_t)r * nh] = T(0);
-  }
-  __syncthreads();
-  for (int ci = child_ptr[q]; ci < child_ptr[q + 1]; ++ci) {
-    const int c = child_list[ci];
-    const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
-    const T* fvc = FV + fvoff[c];
-    const int32_t* rm = relmap + ifoff[c];
-    for (int e = threadIdx.x; e < nuc * nrhs; e += blockDim.x) {
-      const int t = e % nuc, r = e / nuc;
-      fv[rm[t] + (int64_t)r * nh] += fvc[npc + t + (int64_t)r * nhc];
-    }
-    __syncthreads();
-  }
-  if (hkind[q] >= 0 || nu == 0) return;
-  const T* K = F + front_off[q] + np;  // K(t, j) = K[t + j * nh]
-  for (int e = threadIdx.x; e < nu * nrhs; e += blockDim.x) {
-    const int t = e % nu, r = e / nu;
-    const T* bp = fv + (int64_t)r * nh;
-    T s = T(0);
-    for (int j = 0; j < np; ++j) s += K[t + (int64_t)j * nh] * bp[j];
-    fv[np + t + (int64_t)r * nh] -= s;
-  }
+__global__ void __launch_bounds__(256) k_vinit(const int* __restrict__ fronts, int nfronts, int n,
+                                               const T* __restrict__ win, const int32_t* __restrict__ first,
+                                               const int* __restrict__ npiv, const int* __restrict__ nhat,
+                                               const int64_t* __restrict__ fvoff, T* __restrict__ FV) {
+  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (fi >= nfronts) return;
+  const int q = fronts[fi], r = blockIdx.y;
+  const int np = npiv[q], nh = nhat[q], b0 = first[q];
+  T* fv = FV + fvoff[q] + (int64_t)r * nh;
+  const T* w = win + b0 + (int64_t)r * n;
+  const int e0 = blockIdx.z * kVecChunk, e1 = min(nh, e0 + kVecChunk);
+  for (int e = e0 + lane; e < e1; e += 32) fv[e] = e < np ? w[e] : T(0);
 }
 
-// Downward pass of one front per CTA.  x_f is gathered from the finished ancestors into
-// the update part of fv.  Dense fronts: x_p = G^T [b_p; -x_f] with G = [F_pp^{-1}; K]
-// the front's first np columns (nhat x np, column-major, F_pp^{-1} symmetric), computed
-// as a small GEMM: 32-row slabs of G and of the vector block are staged in shared memory
-// (coalesced), each thread accumulates up to kDownAcc outputs (j, r) in registers.
-constexpr int kDownKC = 32;
-constexpr int kDownAcc = 32;  // np * nrhs <= 256 * kDownAcc (np <= 128, nrhs <= 64)
-
+// Extend-add of vectors for child slot `slot`: fv_parent[relmap] += update part of the
+// child (slots run one after another, so sums are formed in a fixed order).
 template <typename T>
-__global__ void __launch_bounds__(256) k_down(const int* __restrict__ fronts, int nrhs, int n,
-                                              T* __restrict__ xout, const int32_t* __restrict__ first,
+__global__ void __launch_bounds__(256) k_vadd(const int* __restrict__ parents, int nparents, int slot,
+                                              const int32_t* __restrict__ child_ptr,
+                                              const int32_t* __restrict__ child_list,
                                               const int* __restrict__ npiv, const int* __restrict__ nhat,
-                                              const int* __restrict__ hkind,
-                                              const int64_t* __restrict__ front_off,
                                               const int64_t* __restrict__ fvoff,
                                               const int64_t* __restrict__ ifoff,
-                                              const int32_t* __restrict__ iflist, const T* __restrict__ F,
-                                              T* __restrict__ FV) {
-  extern __shared__ unsigned char smem_raw[];
-  const int q = fronts[blockIdx.x];
-  const int np = npiv[q], nh = nhat[q], nu = nh - np, b0 = first[q];
-  T* fv = FV + fvoff[q];
+                                              const int32_t* __restrict__ relmap, T* __restrict__ FV) {
+  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (fi >= nparents) return;
+  const int q = parents[fi], r = blockIdx.y;
+  const int c = child_list[child_ptr[q] + slot];
+  const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
+  const int e0 = blockIdx.z * kVecChunk, e1 = min(nuc, e0 + kVecChunk);
+  if (e0 >= e1) return;
+  T* fv = FV + fvoff[q] + (int64_t)r * nhat[q];
+  const T* fc = FV + fvoff[c] + npc + (int64_t)r * nhc;
+  const int32_t* rm = relmap + ifoff[c];
+  for (int t = e0 + lane; t < e1; t += 32) fv[rm[t]] += fc[t];
+}
+
+// Downward gather: fv_q[np + t] = -x(I_q^f[t]) (negated, so that a dense front's solve
+// is the single product x_p = [F_pp^{-1}; K]^T fv_q).
+template <typename T>
+__global__ void __launch_bounds__(256) k_vgather(const int* __restrict__ fronts, int nfronts, int n,
+                                                 const T* __restrict__ xv, const int* __restrict__ npiv,
+                                                 const int* __restrict__ nhat,
+                                                 const int64_t* __restrict__ fvoff,
+                                                 const int64_t* __restrict__ ifoff,
+                                                 const int32_t* __restrict__ iflist, T* __restrict__ FV) {
+  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (fi >= nfronts) return;
+  const int q = fronts[fi], r = blockIdx.y;
+  const int np = npiv[q], nh = nhat[q], nu = nh - np;
+  const int e0 = blockIdx.z * kVecChunk, e1 = min(nu, e0 + kVecChunk);
+  if (e0 >= e1) return;
+  T* fv = FV + fvoff[q] + np + (int64_t)r * nh;
   const int32_t* If = iflist + ifoff[q];
-  for (int e = threadIdx.x; e < nu * nrhs; e += blockDim.x) {
-    const int t = e % nu, r = e / nu;
-    fv[np + t + (int64_t)r * nh] = xout[If[t] + (int64_t)r * n];
-  }
-  __syncthreads();
-  if (hkind[q] >= 0) return;
-  const T* G = F + front_off[q];
-  T* Gs = reinterpret_cast<T*>(smem_raw);   // [kDownKC][np + 1]
-  T* Vs = Gs + kDownKC * (np + 1);          // [kDownKC][nrhs]
-  const int nout = np * nrhs;
-  T acc[kDownAcc];
-#pragma unroll
-  for (int a = 0; a < kDownAcc; ++a) acc[a] = T(0);
-  for (int k0 = 0; k0 < nh; k0 += kDownKC) {
-    const int kc = min(kDownKC, nh - k0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kc * np; e += blockDim.x) {
-      const int kk = e % kc, j = e / kc;
-      Gs[kk * (np + 1) + j] = G[(k0 + kk) + (int64_t)j * nh];
-    }
-    for (int e = threadIdx.x; e < kc * nrhs; e += blockDim.x) {
-      const int kk = e % kc, r = e / kc;
-      const T v = fv[(k0 + kk) + (int64_t)r * nh];
-      Vs[kk * nrhs + r] = (k0 + kk < np) ? v : -v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < kDownAcc; ++a) {
-      const int e = threadIdx.x + a * 256;
-      if (e < nout) {
-        const int j = e % np, r = e / np;
-        T s = acc[a];
-        for (int kk = 0; kk < kc; ++kk) s += Gs[kk * (np + 1) + j] * Vs[kk * nrhs + r];
-        acc[a] = s;
-      }
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < kDownAcc; ++a) {
-    const int e = threadIdx.x + a * 256;
-    if (e < nout) {
-      const int j = e % np, r = e / np;
-      xout[b0 + j + (int64_t)r * n] = acc[a];
-    }
-  }
+  const T* x = xv + (int64_t)r * n;
+  for (int t = e0 + lane; t < e1; t += 32) fv[t] = -x[If[t]];
 }
 
 // HODLR fronts: x_p (= y - Vtilde W^T x_f, in the front's y buffer) -> output vector.
@@ -152,7 +105,12 @@ template <typename T>
 static void gemm_b(hm_ctx_s* ctx, const GemmBatch& b, const unsigned char* base) {
   if (b.tiles.count == 0) return;
   ProfScope ps(ctx, PC_GEMM_APPLY, b.tasks.work);
-  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, ctx->stream);
+  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, ctx->stream);
+}
+
+static dim3 vgrid(int nitems, int nrhs, int maxlen) {
+  return dim3((unsigned)((nitems + 7) / 8), (unsigned)nrhs,
+              (unsigned)std::max(1, (maxlen + kVecChunk - 1) / kVecChunk));
 }
 
 template <typename T>
@@ -163,32 +121,36 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
   hm_ctx_s* ctx = sys->ctx;
   cudaStream_t s = ctx->stream;
   const unsigned char* base = sp->d_tasks;
-  const T* F = (const T*)sys->d_front;
   T* FV = (T*)sp->d_fv;
+  T* xfix = (T*)sp->d_xfix;  // the task tables write the solution here
   const int n = sys->n;
   for (int l = P.nlevels - 1; l >= 0; --l) {
     const LevelSolvePlan& lp = sp->levels[l];
     {
-      ProfScope ps(ctx, PC_UP, lp.up_work);
-      k_up<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, win, sys->d_first, P.d_np,
-                                         P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
-                                         sys->d_child_ptr, sys->d_child_list, sys->d_ifoff,
-                                         sys->d_relmap, F, FV);
+      ProfScope ps(ctx, PC_UP, lp.up_work, 1 + (int)lp.slots.size());
+      k_vinit<T><<<vgrid(lp.nfronts, nrhs, lp.max_nhat), 256, 0, s>>>(
+          lp.fronts.dev(base), lp.nfronts, n, win, sys->d_first, P.d_np, P.d_nhat, sp->d_fvoff, FV);
+      for (size_t sl = 0; sl < lp.slots.size(); ++sl) {
+        const Span<int>& par = lp.slots[sl];
+        if (par.count == 0) continue;
+        k_vadd<T><<<vgrid(par.count, nrhs, lp.slot_max_nu[sl]), 256, 0, s>>>(
+            par.dev(base), par.count, (int)sl, sys->d_child_ptr, sys->d_child_list, P.d_np, P.d_nhat,
+            sp->d_fvoff, sys->d_ifoff, sys->d_relmap, FV);
+      }
     }
-    gemm_b<T>(ctx, lp.up1, base);
-    gemm_b<T>(ctx, lp.up2, base);
+    gemm_b<T>(ctx, lp.up_gemm, base);  // dense: f -= K b_p; HODLR: tf = Vtilde^T b_p
+    gemm_b<T>(ctx, lp.up2, base);      // HODLR: f -= W tf
   }
   for (int l = 0; l < P.nlevels; ++l) {
     const LevelSolvePlan& lp = sp->levels[l];
-    {
+    if (lp.max_nu > 0) {
       ProfScope ps(ctx, PC_DOWN, lp.down_work);
-      const size_t smem = (size_t)kDownKC * (129 + nrhs) * sizeof(T);
-      k_down<T><<<lp.nfronts, 256, smem, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first, P.d_np,
-                                           P.d_nhat, P.d_hkind, P.d_front_off, sp->d_fvoff,
-                                           sys->d_ifoff, sys->d_iflist, F, FV);
+      k_vgather<T><<<vgrid(lp.nfronts, nrhs, lp.max_nu), 256, 0, s>>>(
+          lp.fronts.dev(base), lp.nfronts, n, xfix, P.d_np, P.d_nhat, sp->d_fvoff, sys->d_ifoff,
+          sys->d_iflist, FV);
     }
+    gemm_b<T>(ctx, lp.down_gemm, base);  // dense: x_p = G^T fv; HODLR leaves: y = K_leaf^{-1} b
     if (lp.n_hodlr) {
-      gemm_b<T>(ctx, lp.leaf, base);
       for (const auto& H : lp.heights) {
         gemm_b<T>(ctx, H.t, base);
         gemm_b<T>(ctx, H.s, base);
@@ -197,17 +159,18 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
       gemm_b<T>(ctx, lp.down1, base);
       gemm_b<T>(ctx, lp.down2, base);
       ProfScope ps(ctx, PC_VECTOR, Work{});
-      k_hodlr_out<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xout, sys->d_first,
+      k_hodlr_out<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xfix, sys->d_first,
                                                 P.d_np, sp->d_yvoff, (const T*)sp->d_sb);
     }
   }
+  if (xout != xfix)
+    HM_CUDA(cudaMemcpyAsync(xout, xfix, sizeof(T) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, s));
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }
 
 int solve_setup(int max_smem) {
-  HM_CUDA(allow_max_dyn_smem(k_down<float>, max_smem));
-  HM_CUDA(allow_max_dyn_smem(k_down<double>, max_smem));
+  (void)max_smem;
   return HM_OK;
 }
 
