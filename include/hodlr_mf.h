@@ -138,7 +138,10 @@ int hm_get_symbolic(hm_sys_t sys, int32_t* nupd, int64_t* if_off, int32_t* if_li
  * hm_analyze.  values[nnz] are the CSR values (FP64).  tol is the relative truncation
  * tolerance of the low-rank compression (singular values <= tol * sigma_1 of a block
  * are dropped); tol <= 0 keeps every sampled direction.  May be called repeatedly with
- * new values (refactorization).  Errors: HM_ERR_NOT_SPD, HM_ERR_BREAKDOWN, CUDA errors.
+ * new values (refactorization).  While the factorization runs on the device, the host
+ * also prepares the preconditioner-apply workspace for the right-hand-side count of the
+ * context's most recent solve or apply (device memory of the system, freed by
+ * hm_destroy).  Errors: HM_ERR_NOT_SPD, HM_ERR_BREAKDOWN, CUDA errors.
  */
 int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* info);
 

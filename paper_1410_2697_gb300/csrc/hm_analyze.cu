@@ -551,6 +551,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     ~Guard() { dev_free_all(ctx, t); }
   } guard{sys->ctx, &tmp};
 
+  host_mark("analyze: enter");
   HM_TRY(dev_alloc(sys, (void**)&sys->d_err, 4 * sizeof(int)));
   HM_CUDA(cudaMemsetAsync(sys->d_err, 0, 4 * sizeof(int), s));
   // pattern
@@ -565,6 +566,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   HM_CUDA(cudaMemcpyAsync(sys->d_colidx, colidx, sizeof(int32_t) * sys->nnz, cudaMemcpyDefault, s));
   k_csr_check<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_colidx, n, sys->d_err);
   HM_TRY(check_device_error(sys, "analyze: CSR check"));
+  host_mark("analyze: CSR check");
 
   HM_TRY(dev_alloc(sys, (void**)&sys->d_perm, sizeof(int32_t) * n));
   HM_TRY(dev_alloc(sys, (void**)&sys->d_iperm, sizeof(int32_t) * n));
@@ -596,6 +598,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     const int3 e3 = make_int3(ext[0], ext[1], ext[2]);
     k_lattice_mark<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, lo0, e3, bitmap, sys->d_err);
     HM_TRY(check_device_error(sys, "analyze: lattice check"));
+  host_mark("analyze: bbox + lattice");
     // tree
     const int cap = n + 1;
     NdTree t;
@@ -627,6 +630,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     int cnts[2];
     HM_CUDA(cudaMemcpyAsync(cnts, t.count, sizeof(cnts), cudaMemcpyDeviceToHost, s));
     HM_TRY(check_device_error(sys, "analyze: nested dissection"));
+  host_mark("analyze: nd tree");
     nf = cnts[0];
     {
       ProfScope ps(sys->ctx, PC_ND, Work{0.0, (4.0 * dim + 8.0) * n});
@@ -639,6 +643,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     HM_CUDA(cudaMemcpyAsync(sys->h_parent.data(), d_parent_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(sys->h_level.data(), d_level_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
     HM_TRY(check_device_error(sys, "analyze: permutation"));
+    host_mark("analyze: permutation");
     sys->h_first[nf] = n;
   } else {
     nf = nfronts_in;
@@ -671,19 +676,23 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   HM_CUDA(cudaMemcpyAsync(sys->d_first, sys->h_first.data(), sizeof(int32_t) * (nf + 1), cudaMemcpyHostToDevice, s));
   HM_CUDA(cudaMemcpyAsync(sys->d_parent, sys->h_parent.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, s));
   // children (ascending) on host and device
-  sys->h_children.assign(nf, {});
+  auto& cptr = sys->h_child_ptr;
+  auto& clist = sys->h_child_list;
+  cptr.assign(nf + 1, 0);
   for (int q = 0; q < nf; ++q)
-    if (sys->h_parent[q] >= 0) sys->h_children[sys->h_parent[q]].push_back(q);
-  std::vector<int32_t> cptr(nf + 1, 0), clist;
-  for (int q = 0; q < nf; ++q) {
-    cptr[q + 1] = cptr[q] + (int)sys->h_children[q].size();
-    for (int c : sys->h_children[q]) clist.push_back(c);
+    if (sys->h_parent[q] >= 0) cptr[sys->h_parent[q] + 1]++;
+  for (int q = 0; q < nf; ++q) cptr[q + 1] += cptr[q];
+  clist.assign(std::max(cptr[nf], 1), 0);
+  {
+    std::vector<int32_t> cur(cptr.begin(), cptr.end() - 1);
+    for (int q = 0; q < nf; ++q)  // ascending q: children listed in ascending order
+      if (sys->h_parent[q] >= 0) clist[cur[sys->h_parent[q]]++] = q;
   }
   HM_TRY(dev_alloc(sys, (void**)&sys->d_child_ptr, sizeof(int32_t) * (nf + 1)));
-  HM_TRY(dev_alloc(sys, (void**)&sys->d_child_list, sizeof(int32_t) * std::max<size_t>(clist.size(), 1)));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_child_list, sizeof(int32_t) * clist.size()));
   HM_CUDA(cudaMemcpyAsync(sys->d_child_ptr, cptr.data(), sizeof(int32_t) * (nf + 1), cudaMemcpyHostToDevice, s));
-  if (!clist.empty())
-    HM_CUDA(cudaMemcpyAsync(sys->d_child_list, clist.data(), sizeof(int32_t) * clist.size(), cudaMemcpyHostToDevice, s));
+  HM_CUDA(cudaMemcpyAsync(sys->d_child_list, clist.data(), sizeof(int32_t) * clist.size(), cudaMemcpyHostToDevice, s));
+  host_mark("analyze: children");
   HM_TRY(dev_alloc(sys, (void**)&sys->d_node_of, sizeof(int32_t) * n));
   k_node_of<<<(n + 255) / 256, 256, 0, s>>>(sys->d_first, nf, n, sys->d_node_of);
   // permuted CSR
@@ -748,6 +757,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     if (herr[0] != 0) return check_device_error(sys, "analyze: symbolic");
     break;
   }
+  host_mark("analyze: symbolic");
   unsigned long long total = 0;
   HM_CUDA(cudaMemcpyAsync(&total, cursor, sizeof(total), cudaMemcpyDeviceToHost, s));
   sys->h_nupd.resize(nf);
@@ -764,7 +774,9 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
                                 sys->d_relmap, sys->d_err);
   }
   HM_TRY(check_device_error(sys, "analyze: relative maps"));
+  host_mark("analyze: relative maps");
   HM_TRY(build_plan(sys));
+  host_mark("analyze: build_plan");
   HM_TRY(dev_alloc(sys, (void**)&sys->d_amap, sizeof(int64_t) * sys->nnz));
   {
     ProfScope ps(sys->ctx, PC_SYMBOLIC, Work{0.0, 24.0 * sys->nnz});

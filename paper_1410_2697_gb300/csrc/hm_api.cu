@@ -1,5 +1,8 @@
 // hm_api.cu -- the extern "C" boundary (include/hodlr_mf.h) and host utilities.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -10,6 +13,17 @@ namespace hm {
 static thread_local std::string g_last_error;
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void host_mark(const char* what) {
+  static const bool on = getenv("HM_TRACE_HOST") && getenv("HM_TRACE_HOST")[0] == '1';
+  if (!on) return;
+  using clk = std::chrono::steady_clock;
+  static thread_local clk::time_point last = clk::now();
+  const clk::time_point now = clk::now();
+  fprintf(stderr, "[hm host] %-28s %9.3f ms\n", what,
+          std::chrono::duration<double, std::milli>(now - last).count());
+  last = now;
+}
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;

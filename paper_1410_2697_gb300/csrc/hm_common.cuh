@@ -15,6 +15,9 @@ namespace hm {
 // Host error reporting: the last failure message of the calling thread.
 // ------------------------------------------------------------------------------------
 void set_last_error(const std::string& msg);
+// Host-side phase trace (environment HM_TRACE_HOST=1): prints to stderr the host wall
+// time since the previous mark of the same thread.  Off by default.
+void host_mark(const char* what);
 
 #define HM_CUDA(call)                                                               \
   do {                                                                              \

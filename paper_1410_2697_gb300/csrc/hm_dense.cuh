@@ -95,6 +95,8 @@ struct CholInvTask {
   void* A;
   void* B;
   int n, ld, m, ldb;
+  void* BT;   // if set, (B Linv)^T is also written here (n x m, leading dimension ldbt)
+  int ldbt, pad;
 };
 
 template <typename T>

@@ -146,12 +146,19 @@ __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, 
   T* V = M + (size_t)k * ls;
   T* sig = V + (size_t)k * ls;
   const T* R = (const T*)t.R;
+  __shared__ T red[32];
+  T f2 = T(0);
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int i = e % k, c = e / k;
-    M[i + c * ls] = R[c + (size_t)i * k];  // M = R^T
+    const T v = R[c + (size_t)i * k];
+    M[i + c * ls] = v;  // M = R^T
     V[i + c * ls] = (i == c) ? T(1) : T(0);
+    f2 += v * v;
   }
-  __syncthreads();
+  // Pairs of columns that are both at rounding level of ||M||_F carry no information
+  // (their singular values fall far below any truncation tolerance) and are left alone;
+  // rotating them only shuffles rounding noise and keeps the sweeps from converging.
+  const T floor2 = block_sum(f2, red) * JacobiEps<T>::v * JacobiEps<T>::v;
   // one 16-lane group per column pair; every group runs the same number of passes so
   // the width-16 shuffles are always executed by full warps
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -187,7 +194,7 @@ __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, 
           be += __shfl_xor_sync(0xffffffffu, be, o, 16);
           ga += __shfl_xor_sync(0xffffffffu, ga, o, 16);
         }
-        if (valid && ga != T(0) && fabs(ga) > eps * sqrt(al * be)) {
+        if (valid && ga != T(0) && fabs(ga) > eps * sqrt(al * be) && (al > floor2 || be > floor2)) {
           const T zeta = (be - al) / (T(2) * ga);
           const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           const T c = T(1) / sqrt(T(1) + tt * tt), sn = c * tt;

@@ -255,10 +255,132 @@ __global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ 
     }
 }
 
+// =====================================================================================
+// Woodbury core by its Schur complement: with A = U^T Uhat and B = V^T Vhat (the two
+// diagonal k x k blocks the GEMMs wrote), C = [[A, I], [I, B]] is invertible exactly when
+// M = I - A B is, and
+//   C^{-1} = [[X11, X12], [X21, X22]],  X21 = M^{-1},  X11 = -B M^{-1},
+//            X22 = -M^{-1} A,           X12 = I - X11 A
+// (multiply out C C^{-1} = I block by block).  So one k x k Gauss-Jordan inversion with
+// partial pivoting replaces the 2k x 2k one, with k steps instead of 2k.  One CTA per
+// core, everything in shared memory (5 k^2 elements).  A zero pivot raises
+// HM_ERR_BREAKDOWN.
+// =====================================================================================
+
+// P (k x k) = alpha * X Y (+ I if add_identity); all k x k column-major in shared memory
+template <typename T>
+__device__ __forceinline__ void smem_gemm(T* __restrict__ P, const T* __restrict__ X, const T* __restrict__ Y,
+                                          int k, T alpha, bool add_identity) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    T s = T(0);
+    for (int p = 0; p < k; ++p) s = fma(X[i + p * k], Y[p + j * k], s);
+    P[e] = alpha * s + ((add_identity && i == j) ? T(1) : T(0));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_core_inv_schur(const CoreLuTask* __restrict__ tasks, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ T sval[8];
+  __shared__ int sidx[8];
+  __shared__ int piv_s;
+  const CoreLuTask t = tasks[blockIdx.x];
+  const int k = t.k, n = 2 * k;
+  const T* C = (const T*)t.C;
+  T* Ci = (T*)t.Cinv;
+  T* As = reinterpret_cast<T*>(smem_raw);  // k x k
+  T* Bs = As + k * k;                      // k x k
+  T* G = Bs + k * k;                       // [M | M^{-1}], k x 2k (ld k)
+  T* W = G + 2 * k * k;                    // k x k work
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    As[e] = C[(size_t)i + (size_t)j * n];
+    Bs[e] = C[(size_t)(k + i) + (size_t)(k + j) * n];
+  }
+  __syncthreads();
+  smem_gemm<T>(G, As, Bs, k, T(-1), true);  // M = I - A B
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[k * k + e] = (e % k == e / k) ? T(1) : T(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    // pivot: largest |M(i, j)|, i >= j (lowest row on ties), found by warp 0
+    if (wid == 0) {
+      T best = T(-1);
+      int bi = k;
+      for (int i = j + lane; i < k; i += 32) {
+        const T v = fabs(G[i + j * k]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        if (!(best > T(0))) {
+          raise_error(err, HM_ERR_BREAKDOWN, t.front, j);
+          bi = j;
+        }
+        piv_s = bi;
+        t.piv[j] = bi;
+      }
+    }
+    __syncthreads();
+    const int p = piv_s;
+    if (p != j)
+      for (int c = j + threadIdx.x; c < 2 * k; c += blockDim.x) {
+        const T a = G[j + c * k];
+        G[j + c * k] = G[p + c * k];
+        G[p + c * k] = a;
+      }
+    __syncthreads();
+    T d = G[j + j * k];
+    if (d == T(0)) d = T(1);
+    const T inv = T(1) / d;
+    // multipliers of the pivot column (W's first column), then a warp per column
+    for (int i = threadIdx.x; i < k; i += blockDim.x) W[i] = (i == j) ? T(0) : G[i + j * k];
+    __syncthreads();
+    for (int c = j + wid; c < 2 * k; c += nw) {
+      const T mjc = G[j + c * k] * inv;
+      __syncwarp();
+      if (lane == 0) G[j + c * k] = mjc;
+      if (mjc != T(0))
+        for (int i = lane; i < k; i += 32)
+          if (i != j) G[i + c * k] -= W[i] * mjc;
+    }
+    __syncthreads();
+  }
+  const T* Mi = G + k * k;
+  // X21 = M^{-1}; X11 = -B M^{-1} (into W); X22 = -M^{-1} A (into G's first half)
+  smem_gemm<T>(W, Bs, Mi, k, T(-1), false);
+  smem_gemm<T>(G, Mi, As, k, T(-1), false);
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    Ci[(size_t)i + (size_t)j * n] = W[e];                  // X11
+    Ci[(size_t)(k + i) + (size_t)j * n] = Mi[e];           // X21
+    Ci[(size_t)(k + i) + (size_t)(k + j) * n] = G[e];      // X22
+  }
+  // X12 = I - X11 A (into Bs, which is no longer needed)
+  smem_gemm<T>(Bs, W, As, k, T(-1), true);
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    Ci[(size_t)i + (size_t)(k + j) * n] = Bs[e];           // X12
+  }
+}
+
 template <typename T>
 void launch_core_lu(const CoreLuTask* tasks, int ntasks, int maxk, int max_smem, int* err,
                     cudaStream_t s) {
   if (ntasks <= 0) return;
+  const size_t schur = (size_t)5 * maxk * maxk * sizeof(T);
+  if (schur + 1024 <= (size_t)max_smem) {
+    k_core_inv_schur<T><<<ntasks, 256, schur, s>>>(tasks, err);
+    return;
+  }
   const int n = 2 * maxk;
   const size_t smem = ((size_t)(n + 1) * 2 * n + n) * sizeof(T);
   const int use = smem + 1024 <= (size_t)max_smem ? 1 : 0;
@@ -270,7 +392,8 @@ void launch_core_lu(const CoreLuTask* tasks, int ntasks, int maxk, int max_smem,
 // memory).  L^{-1} is formed in place, last column first: with the trailing block
 // already inverted, column j becomes -Linv[j+1:, j+1:] L[j+1:, j] / L[j][j] (a parallel
 // triangular matrix-vector product).  Then A^{-1} = Linv^T Linv is written as a full
-// n x n block, and B <- B Linv for the m rows below (64 rows per pass).
+// n x n block, and B <- B Linv for the m rows below (64 rows per pass), optionally also
+// stored transposed.
 // =====================================================================================
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol_inverse(const CholInvTask* __restrict__ tasks) {
@@ -323,6 +446,14 @@ __global__ void __launch_bounds__(256) k_chol_inverse(const CholInvTask* __restr
       for (int i = j; i < n; ++i) s += R[i * 64 + r] * Li[i + j * ls];
       B[(size_t)(r0 + r) + (size_t)j * t.ldb] = s;
     }
+    if (t.BT) {  // transpose of the finished rows (global writes of this block are visible)
+      __syncthreads();
+      T* BT = (T*)t.BT;
+      for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+        const int j = e % n, r = e / n;
+        BT[(size_t)j + (size_t)(r0 + r) * t.ldbt] = B[(size_t)(r0 + r) + (size_t)j * t.ldb];
+      }
+    }
   }
 }
 
@@ -355,6 +486,8 @@ int dense_fact_setup(int max_smem) {
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_lu<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_schur<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_schur<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_lu<double>, max_smem));
   return HM_OK;
 }

@@ -29,22 +29,26 @@ __global__ void k_scatter(const double* __restrict__ vals, const int64_t* __rest
   }
 }
 
-// Extend-add: one warp adds column `col` (lower part) of child c's update matrix
-// U_c = F_ff of c into its parent's front at rows/columns relmap.
+// Extend-add of child slot `slot` of every listed parent q: warp w of block (x, y) adds
+// column 8 y + w (lower part) of the child's update matrix U_c = F_ff of c into the front
+// of q at rows/columns relmap.  Slots run one launch after another, so every entry of a
+// parent receives its children's contributions in a fixed order.
 template <typename T>
-__global__ void k_extend_add(const EaItem* __restrict__ items, int nitems,
-                             const int32_t* __restrict__ parent, const int64_t* __restrict__ front_off,
-                             const int* __restrict__ nhat, const int* __restrict__ npiv,
-                             const int64_t* __restrict__ ifoff, const int32_t* __restrict__ relmap,
-                             T* __restrict__ F) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= nitems) return;
-  const EaItem it = items[w];
-  const int c = it.child, col = it.col, p = parent[c];
-  const int ldc = nhat[c], npc = npiv[c], nuc = ldc - npc, ldp = nhat[p];
+__global__ void __launch_bounds__(256) k_extend_add(const int* __restrict__ parents, int slot,
+                                                    const int32_t* __restrict__ child_ptr,
+                                                    const int32_t* __restrict__ child_list,
+                                                    const int64_t* __restrict__ front_off,
+                                                    const int* __restrict__ nhat, const int* __restrict__ npiv,
+                                                    const int64_t* __restrict__ ifoff,
+                                                    const int32_t* __restrict__ relmap, T* __restrict__ F) {
+  const int q = parents[blockIdx.x];
+  const int c = child_list[child_ptr[q] + slot];
+  const int col = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int ldc = nhat[c], npc = npiv[c], nuc = ldc - npc;
+  if (col >= nuc) return;
+  const int ldp = nhat[q];
   const T* Fc = F + front_off[c] + npc + (int64_t)(npc + col) * ldc;
-  T* Fp = F + front_off[p];
+  T* Fp = F + front_off[q];
   const int32_t* rm = relmap + ifoff[c];
   const int64_t cc = (int64_t)rm[col] * ldp;
   for (int r = col + lane; r < nuc; r += 32) Fp[rm[r] + cc] += Fc[r];
@@ -114,15 +118,13 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
   }
   for (int l = P.nlevels - 1; l >= 0; --l) {
     const LevelFactorPlan& lp = P.levels[l];
-    for (size_t si = 0; si < lp.ea_slots.size(); ++si) {
-      const auto& sl = lp.ea_slots[si];
-      if (sl.count == 0) continue;
+    for (size_t si = 0; si < lp.ea_parents.size(); ++si) {
+      const auto& par = lp.ea_parents[si];
+      if (par.count == 0 || lp.ea_max_nu[si] == 0) continue;
       ProfScope ps(ctx, PC_EXTEND_ADD, lp.ea_work[si]);
-      const int threads = 256;
-      const int64_t blocks = ((int64_t)sl.count * 32 + threads - 1) / threads;
-      k_extend_add<T><<<(unsigned)blocks, threads, 0, s>>>(sl.dev(base), sl.count, sys->d_parent,
-                                                           P.d_front_off, P.d_nhat, P.d_np, sys->d_ifoff,
-                                                           sys->d_relmap, F);
+      const dim3 grid((unsigned)par.count, (unsigned)((lp.ea_max_nu[si] + 7) / 8));
+      k_extend_add<T><<<grid, 256, 0, s>>>(par.dev(base), (int)si, sys->d_child_ptr, sys->d_child_list,
+                                           P.d_front_off, P.d_nhat, P.d_np, sys->d_ifoff, sys->d_relmap, F);
     }
     debug_stage<T>(sys, "extendadd", l);
     if (lp.n_dense) {
@@ -206,10 +208,20 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
 }
 
 int factor_impl(hm_sys_s* sys, const double* d_values, double tol) {
+  host_mark("factor: enter");
   int st = sys->precision == HM_PREC_FP64 ? factor_t<double>(sys, d_values, tol)
                                           : factor_t<float>(sys, d_values, tol);
   if (st != HM_OK) return st;
-  return check_device_error(sys, "factor");
+  host_mark("factor: launched");
+  // The apply plan depends only on the analysis, so the one for the most recent
+  // right-hand-side count is built on the host while the factorization runs.
+  if (sys->ctx->last_nrhs > 0) {
+    SolvePlan* sp = nullptr;
+    HM_TRY(get_solve_plan(sys, sys->ctx->last_nrhs, &sp));
+  }
+  st = check_device_error(sys, "factor");
+  host_mark("factor: device done");
+  return st;
 }
 
 }  // namespace hm

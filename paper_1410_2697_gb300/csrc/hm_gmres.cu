@@ -270,8 +270,10 @@ static void sqnorm(hm_sys_s* sys, const double* v, double* ss, int stride, int n
 template <typename T>
 static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
                    double* d_x, hm_solve_info* info) {
+  host_mark("gmres: enter");
   const int m = std::max(1, sys->ctx->opts.restart);
   HM_TRY(ensure_workspace(sys, nrhs, m));
+  host_mark("gmres: workspace");
   auto& G = sys->gm;
   cudaStream_t s = sys->ctx->stream;
   const int n = sys->n;
@@ -363,6 +365,7 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
       ++iters;
       HM_CUDA(cudaMemcpyAsync(G.h_res, G.res, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
       HM_CUDA(cudaStreamSynchronize(s));
+      host_mark("gmres: iteration");
       bool all = true;
       for (int r = 0; r < nrhs; ++r)
         if (active[r] && !(G.h_res[r] <= rtol)) all = false;
@@ -398,6 +401,7 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
     launch_permute_out(G.x, d_x, sys->d_perm, n, nrhs, s);
   }
   HM_CUDA(cudaStreamSynchronize(s));
+  host_mark("gmres: done");
   HM_CUDA(cudaGetLastError());
   if (info) {
     info->iters = iters;

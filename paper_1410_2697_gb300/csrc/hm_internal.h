@@ -126,12 +126,6 @@ struct Profiler {
   cudaEvent_t get();
 };
 
-// Extend-add work item: one column `col` of child `child`'s update matrix.
-struct EaItem {
-  int child;
-  int col;
-};
-
 // Per-front geometry of the plan.
 struct FrontGeom {
   int np = 0, nu = 0, nhat = 0;
@@ -168,7 +162,8 @@ struct HFront {
 };
 
 struct LevelFactorPlan {
-  std::vector<Span<EaItem>> ea_slots;
+  std::vector<Span<int>> ea_parents;  // slot j: fronts of the level with more than j children
+  std::vector<int> ea_max_nu;         // per slot, the largest update size of those children
   std::vector<Work> ea_work;
   Span<PotrfTask> potrf;       // dense fronts
   int potrf_maxn = 0;
@@ -204,16 +199,18 @@ struct UpItem {
   int q;
 };
 struct LevelSolvePlan {
-  Span<int> fronts;            // all fronts of the level
-  int nfronts = 0;
-  int max_nhat = 0, max_nu = 0;  // largest nhat_p and |I_p^f| of the level
-  std::vector<Span<int>> slots;  // slot j: fronts of the level with more than j children
-  std::vector<int> slot_max_nu;  // per slot, the largest update size of those children
-  Work up_work, down_work;     // the vector kernels (init + extend-add; gather)
+  Span<int> dense;             // dense fronts of the level (fused up / down kernels)
+  int dense_max_np = 0, dense_max_nhat = 0;
+  Work up_work, down_work;     // the fused dense kernels
+  Span<int> hfronts;           // HODLR fronts of the level
   int n_hodlr = 0;
-  GemmBatch up_gemm;           // dense: f -= K b_p ; HODLR: tf = Vtilde^T b_p
+  int hodlr_max_nhat = 0, hodlr_max_nu = 0;
+  std::vector<Span<int>> slots;  // slot j: HODLR fronts of the level with more than j children
+  std::vector<int> slot_max_nu;  // per slot, the largest update size of those children
+  Work hup_work, hdown_work;   // HODLR vector kernels (init + extend-add; gather)
+  GemmBatch up_gemm;           // HODLR: tf = Vtilde^T b_p
   GemmBatch up2;               // HODLR: f -= W tf
-  GemmBatch down_gemm;         // dense: x_p = [F_pp^{-1}; K]^T [b_p; -x_f] ; HODLR leaves: y = K^{-1} b
+  GemmBatch down_gemm;         // HODLR leaves: y = K^{-1} b
   struct Height {
     GemmBatch t;               // t = [U^T y_a; V^T y_b]
     GemmBatch s;               // s = C^{-1} t
@@ -227,6 +224,7 @@ struct SolvePlan {
   int nrhs = 0;
   std::vector<LevelSolvePlan> levels;
   std::vector<int64_t> fv_off;  // per front, element offset of its (nhat x nrhs) vector
+  std::vector<int64_t> yv_off;  // per front, offset of y in the scratch (-1: dense front)
   int64_t fv_total = 0;
   int64_t sb_total = 0;         // node t/s buffers + tf buffers
   TaskBuf tb;
@@ -254,6 +252,9 @@ struct Plan {
   int* d_nhat = nullptr;
   int* d_np = nullptr;
   int* d_hkind = nullptr;  // per front: -1 dense, else HODLR index
+  // host copies of the uploaded per-front arrays (kept while the copies may be in flight)
+  std::vector<int64_t> h_front_off;
+  std::vector<int> h_nhat, h_np, h_hkind;
   int max_children = 0;
   double factor_bytes = 0;
 };
@@ -272,6 +273,7 @@ struct hm_ctx_s {
   size_t allocated = 0;
   int max_smem = 0;
   int num_sms = 0;
+  int last_nrhs = 0;             // right-hand-side count of the most recent apply plan
   cudaMemPool_t pool = nullptr;  // stream-ordered pool; freed memory is kept for reuse
   std::vector<void*> allocs;
 };
@@ -306,7 +308,18 @@ struct hm_sys_s {
   // host copies
   std::vector<int32_t> h_first, h_parent, h_level, h_nupd;
   std::vector<int64_t> h_ifoff;
-  std::vector<std::vector<int>> h_children;
+  std::vector<int32_t> h_child_ptr, h_child_list;  // children (ascending), CSR by parent
+  struct Children {
+    const int32_t* b;
+    const int32_t* e;
+    const int32_t* begin() const { return b; }
+    const int32_t* end() const { return e; }
+    int size() const { return (int)(e - b); }
+    int32_t operator[](int i) const { return b[i]; }
+  };
+  Children children(int q) const {
+    return Children{h_child_list.data() + h_child_ptr[q], h_child_list.data() + h_child_ptr[q + 1]};
+  }
   // plan + numeric state
   hm::Plan plan;
   void* d_front = nullptr;   // T arena

@@ -61,7 +61,7 @@ int build_plan(hm_sys_s* sys) {
   }
   P.front_total = off;
   P.max_children = 0;
-  for (int q = 0; q < nf; ++q) P.max_children = std::max(P.max_children, (int)sys->h_children[q].size());
+  for (int q = 0; q < nf; ++q) P.max_children = std::max(P.max_children, sys->children(q).size());
 
   // ---------------------------------------------------------------- HODLR fronts
   P.hf.clear();
@@ -173,8 +173,12 @@ int build_plan(hm_sys_s* sys) {
   HM_TRY(A((void**)&P.d_np, nf, 4));
   HM_TRY(A((void**)&P.d_hkind, nf, 4));
   {
-    std::vector<int64_t> fo(nf);
-    std::vector<int> nh(nf), npv(nf), hk(nf);
+    // the host copies live as long as the plan, so the uploads need no synchronization
+    auto& fo = P.h_front_off;
+    auto& nh = P.h_nhat;
+    auto& npv = P.h_np;
+    auto& hk = P.h_hkind;
+    fo.resize(nf); nh.resize(nf); npv.resize(nf); hk.resize(nf);
     for (int q = 0; q < nf; ++q) {
       fo[q] = P.fg[q].off; nh[q] = P.fg[q].nhat; npv[q] = P.fg[q].np; hk[q] = P.fg[q].hodlr;
     }
@@ -183,7 +187,6 @@ int build_plan(hm_sys_s* sys) {
     HM_CUDA(cudaMemcpyAsync(P.d_nhat, nh.data(), nf * 4, cudaMemcpyHostToDevice, s));
     HM_CUDA(cudaMemcpyAsync(P.d_np, npv.data(), nf * 4, cudaMemcpyHostToDevice, s));
     HM_CUDA(cudaMemcpyAsync(P.d_hkind, hk.data(), nf * 4, cudaMemcpyHostToDevice, s));
-    HM_CUDA(cudaStreamSynchronize(s));
   }
 
   // ---------------------------------------------------------------- factor tasks
@@ -206,22 +209,25 @@ int build_plan(hm_sys_s* sys) {
   for (int l = P.nlevels - 1; l >= 0; --l) {
     LevelFactorPlan& lp = P.levels[l];
     const auto& fr = P.level_fronts[l];
-    // extend-add items per child slot
+    // extend-add: per child slot, the parents that have a child in that slot
     int slots = 0;
-    for (int q : fr) slots = std::max(slots, (int)sys->h_children[q].size());
+    for (int q : fr) slots = std::max(slots, sys->children(q).size());
     for (int s = 0; s < slots; ++s) {
-      std::vector<EaItem> items;
+      std::vector<int> par;
       Work w;
+      int max_nu = 0;
       for (int q : fr) {
-        const auto& ch = sys->h_children[q];
+        const auto ch = sys->children(q);
         if (s >= (int)ch.size()) continue;
+        par.push_back(q);
         const int c = ch[s];
         const double nuc = P.fg[c].nu;
-        for (int col = 0; col < P.fg[c].nu; ++col) items.push_back(EaItem{c, col});
+        max_nu = std::max(max_nu, P.fg[c].nu);
         w.flops += nuc * (nuc + 1) / 2;
         w.bytes += 3.0 * es * nuc * (nuc + 1) / 2 + 4.0 * nuc;
       }
-      lp.ea_slots.push_back(tb.add(items));
+      lp.ea_parents.push_back(tb.add(par));
+      lp.ea_max_nu.push_back(max_nu);
       lp.ea_work.push_back(w);
     }
     // dense fronts
@@ -244,7 +250,10 @@ int build_plan(hm_sys_s* sys) {
                             at(F, g.off + g.np + (int64_t)g.np * g.nhat, es), g.nhat, g.nu, g.nu,
                             g.np, -1.0, 1.0, 1));
       }
-      dinv.push_back(CholInvTask{Fq, at(F, g.off + g.np, es), g.np, g.nhat, g.nu, g.nhat});
+      // K = F_fp F_pp^{-1} below the pivot block and K^T beside it, so that both apply
+      // passes read the front with rows on consecutive threads
+      dinv.push_back(CholInvTask{Fq, at(F, g.off + g.np, es), g.np, g.nhat, g.nu, g.nhat,
+                                 at(F, g.off + (int64_t)g.np * g.nhat, es), g.nhat, 0});
       fbytes += es * ((double)g.np * g.np + 2.0 * g.nu * g.np);
     }
     lp.potrf = tb.add(pot);
@@ -324,7 +333,7 @@ int build_plan(hm_sys_s* sys) {
         lpot.push_back(PotrfTask{Lq, n, nh, q, 0});
         lp.leaf_maxn = std::max(lp.leaf_maxn, n);
         if (h.xc > 0) lsol.push_back(CholSolveTask{Lq, at(X, h.bo_off + lo, es), n, nh, np, h.xc});
-        linv.push_back(CholInvTask{Lq, nullptr, n, nh, 0, 0});
+        linv.push_back(CholInvTask{Lq, nullptr, n, nh, 0, 0, nullptr, 0, 0});
         fbytes += es * (double)n * n;
       }
     }
@@ -397,7 +406,6 @@ int build_plan(hm_sys_s* sys) {
   HM_TRY(dev_alloc(sys, (void**)&P.d_tasks, std::max<size_t>(tb.host.size(), 16)));
   HM_CUDA(cudaMemcpyAsync(P.d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));
-  HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
   return HM_OK;
 }
 
@@ -406,7 +414,9 @@ int build_plan(hm_sys_s* sys) {
 // ------------------------------------------------------------------------------------
 int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   auto it = sys->solve_plans.find(nrhs);
+  sys->ctx->last_nrhs = nrhs;
   if (it != sys->solve_plans.end()) { *out = it->second.get(); return HM_OK; }
+  host_mark("solve plan: enter");
   Plan& P = sys->plan;
   const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
   const int nf = sys->nf;
@@ -420,7 +430,8 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   // and the pivot-block solution y (np x nrhs)
   std::vector<std::vector<int64_t>> node_sb(P.hf.size());
   std::vector<int64_t> front_sb(P.hf.size()), front_yv(P.hf.size());
-  std::vector<int64_t> yvoff(nf, -1);
+  std::vector<int64_t>& yvoff = sp->yv_off;
+  yvoff.assign(nf, -1);
   int64_t sb = 0;
   for (size_t i = 0; i < P.hf.size(); ++i) {
     const HFront& h = P.hf[i];
@@ -448,54 +459,50 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   void* Cm = sys->d_core;
   void* FV = sp->d_fv;
   void* SB = sp->d_sb;
-  void* XS = sp->d_xfix;
-  const int n = sys->n;
   TaskBuf& tb = sp->tb;
   tb.es = es;
   sp->levels.assign(P.nlevels, LevelSolvePlan());
   for (int l = 0; l < P.nlevels; ++l) {
     LevelSolvePlan& lp = sp->levels[l];
     const auto& fr = P.level_fronts[l];
-    lp.fronts = tb.add(fr);
-    lp.nfronts = (int)fr.size();
-    // child slots: slot j holds the fronts of the level with more than j children, so
-    // that the vector extend-add of slot j touches each parent once
-    std::vector<std::vector<int>> slot_fronts;
+    std::vector<int> dense, hod;
+    std::vector<std::vector<int>> slot_fronts;  // slot j: HODLR fronts with more than j children
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
-      lp.max_nhat = std::max(lp.max_nhat, g.nhat);
-      lp.max_nu = std::max(lp.max_nu, g.nu);
-      const auto& ch = sys->h_children[q];
-      if (slot_fronts.size() < ch.size()) {
-        slot_fronts.resize(ch.size());
-        lp.slot_max_nu.resize(ch.size(), 0);
-      }
-      for (size_t j = 0; j < ch.size(); ++j) {
-        slot_fronts[j].push_back(q);
-        lp.slot_max_nu[j] = std::max(lp.slot_max_nu[j], P.fg[ch[j]].nu);
-      }
+      const auto ch = sys->children(q);
       const double np = g.np, nu = g.nu, nh = g.nhat, R = nrhs;
-      // up: read r(I_p), write fv (nhat); per child read its update part, read-modify-write
-      // the parent entries and read the relative map.  Down: read x(I_p^f) and the index
-      // list, write the update part.
-      lp.up_work.bytes += es * R * (np + nh);
-      for (int c : ch) lp.up_work.bytes += es * R * 3.0 * P.fg[c].nu + 4.0 * P.fg[c].nu;
-      lp.down_work.bytes += es * R * 2.0 * nu + 4.0 * nu;
-      if (g.hodlr >= 0) lp.n_hodlr++;
+      double vec = es * R * (np + nh);  // read r(I_p), write fv
+      for (int c : ch) vec += es * R * 3.0 * P.fg[c].nu + 4.0 * P.fg[c].nu;  // extend-add
+      if (g.hodlr < 0) {
+        dense.push_back(q);
+        lp.dense_max_np = std::max(lp.dense_max_np, g.np);
+        lp.dense_max_nhat = std::max(lp.dense_max_nhat, g.nhat);
+        // up: vectors + K (nu x np); down: [b_p; -x(I_f)] in, x_p out, the first np rows
+        lp.up_work.bytes += vec + es * nu * np;
+        lp.up_work.flops += 2.0 * R * nu * np;
+        lp.down_work.bytes += es * R * (2.0 * np + 2.0 * nu) + 4.0 * nu + es * np * nh;
+        lp.down_work.flops += 2.0 * R * np * nh;
+      } else {
+        hod.push_back(q);
+        lp.hodlr_max_nhat = std::max(lp.hodlr_max_nhat, g.nhat);
+        lp.hodlr_max_nu = std::max(lp.hodlr_max_nu, g.nu);
+        if ((int)slot_fronts.size() < ch.size()) {
+          slot_fronts.resize(ch.size());
+          lp.slot_max_nu.resize(ch.size(), 0);
+        }
+        for (int j = 0; j < ch.size(); ++j) {
+          slot_fronts[j].push_back(q);
+          lp.slot_max_nu[j] = std::max(lp.slot_max_nu[j], P.fg[ch[j]].nu);
+        }
+        lp.hup_work.bytes += vec;
+        lp.hdown_work.bytes += es * R * 2.0 * nu + 4.0 * nu;
+      }
     }
+    lp.dense = tb.add(dense);
+    lp.hfronts = tb.add(hod);
+    lp.n_hodlr = (int)hod.size();
     for (const auto& sf : slot_fronts) lp.slots.push_back(tb.add(sf));
-    // dense fronts: up f -= K b_p; down x_p = [F_pp^{-1}; K]^T [b_p; -x_f]
     std::vector<GemmTask> ug, dg;
-    for (int q : fr) {
-      const FrontGeom& g = P.fg[q];
-      if (g.hodlr >= 0) continue;
-      const int64_t fvq = sp->fv_off[q];
-      if (g.nu > 0)
-        ug.push_back(gemm(at(F, g.off + g.np, es), g.nhat, 0, at(FV, fvq, es), g.nhat, 0,
-                          at(FV, fvq + g.np, es), g.nhat, g.nu, nrhs, g.np, -1.0, 1.0));
-      dg.push_back(gemm(at(F, g.off, es), g.nhat, 1, at(FV, fvq, es), g.nhat, 0,
-                        at(XS, sys->h_first[q], es), n, g.np, nrhs, g.nhat, 1.0, 0.0));
-    }
     std::vector<GemmTask> u2, d1, d2;
     int maxL = 0;
     for (int q : fr) {
@@ -564,9 +571,9 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   HM_TRY(dev_alloc(sys, (void**)&sp->d_tasks, std::max<size_t>(tb.host.size(), 16)));
   HM_CUDA(cudaMemcpyAsync(sp->d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));
-  HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
   *out = sp.get();
   sys->solve_plans[nrhs] = std::move(sp);
+  host_mark("solve plan: built");
   return HM_OK;
 }
 

@@ -4,16 +4,16 @@
 // solves and low-rank coupling blocks of Section 4.2.2 for HODLR fronts.
 //
 // Every front p owns a vector block fv_p (nhat_p x nrhs, nhat_p = |I_p| + |I_p^f|).
-// Upward, per tree level: fv_p = [r(I_p); 0] (flat kernel), then the children's update
-// parts are added through the relative maps one child slot at a time (fixed order), then
-// b_f <- b_f - F_fp F_pp^{-1} b_p as batched GEMMs: dense fronts keep K = F_fp F_pp^{-1}
-// from the factorization; HODLR fronts use Vf^T F_pp^{-1} = Vtilde^T (F_pp^HODLR is
-// symmetric), so b_f -= W (Vtilde^T b_p) needs no pivot solve.  Downward: fv_p's update
-// part receives -x(I_p^f) from the finished ancestors; a dense front's solution is the
-// single GEMM x_p = [F_pp^{-1}; K]^T fv_p = F_pp^{-1} b_p - K^T x_f; a HODLR front solves
-// y = F_pp^{-1} b_p by recursive Woodbury (explicit leaf inverses, then per level
-// y -= Zhat C^{-1} Z^T y with explicit core inverses) and x_p = y - Vtilde (W^T x_f).
-// Every step is a flat vector kernel or a batched GEMM; nothing is solved by sequential
+// Dense fronts run one fused kernel per level and pass.  Upward: fv_p = [r(I_p); 0], the
+// children's update parts added through the relative maps (children in a fixed order),
+// then b_f <- b_f - K b_p with K = F_fp F_pp^{-1} kept by the factorization.  Downward:
+// x_p = F_pp^{-1} b_p - K^T x_f as one product with the first np rows of the front,
+// [F_pp^{-1} | K^T] (K^T is stored beside the pivot block), so both passes read the
+// front with one row per thread.  HODLR fronts use flat vector kernels and batched GEMMs:
+// Vf^T F_pp^{-1} = Vtilde^T (F_pp^HODLR is symmetric), so the upward coupling is
+// b_f -= W (Vtilde^T b_p) with no pivot solve; downward, y = F_pp^{-1} b_p by recursive
+// Woodbury (explicit leaf inverses, then per level y -= Zhat C^{-1} Z^T y with explicit
+// core inverses) and x_p = y - Vtilde (W^T x_f).  Nothing is solved by sequential
 // substitution.
 #include <algorithm>
 
@@ -85,6 +85,252 @@ __global__ void __launch_bounds__(256) k_vgather(const int* __restrict__ fronts,
   for (int t = e0 + lane; t < e1; t += 32) fv[t] = -x[If[t]];
 }
 
+// -------------------------------------------------------------------------------------
+// Dense fronts: one block of 256 threads per (front, group of RB right-hand sides).
+// Both passes are row-block products M (rows x kdim, column-major) times a staged
+// block X (kdim x RB) with one row of M per thread, so consecutive threads read
+// consecutive rows of a column (coalesced) and every thread reads the same X entries
+// (shared-memory broadcast).  When a front has fewer than 256 rows, the reduction
+// dimension is split over S warp slices whose partial sums meet in shared memory.
+//   up:   f -= K b_p,            K = F_fp F_pp^{-1}  (nu x np, below the pivot block)
+//   down: x_p = [F_pp^{-1} | K^T] [b_p; -x_f]        (np x nhat, the first np rows)
+// -------------------------------------------------------------------------------------
+constexpr int kDenseKC = 256;  // rows of the staged block per chunk in the down pass
+
+__device__ __forceinline__ int pow2_floor8(int v) { return v >= 8 ? 8 : v >= 4 ? 4 : v >= 2 ? 2 : 1; }
+
+// acc[r] += sum_{k in [k0, k1)} M[row + k ld] X[(k - kx) RB + r]
+template <typename T, int RB>
+__device__ __forceinline__ void rowblock_acc(const T* __restrict__ M, int64_t ld, int row, int k0, int k1,
+                                             const T* __restrict__ X, int kx, T (&acc)[RB]) {
+#pragma unroll 4
+  for (int k = k0; k < k1; ++k) {
+    const T m = M[row + (int64_t)k * ld];
+    const T* x = X + (k - kx) * RB;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = fma(m, x[r], acc[r]);
+  }
+}
+
+// Adds the partial sums of the S - 1 other slices of a warp group into acc of the group's
+// first warp (warps g S .. g S + S - 1 form group g).  Every thread of the block calls it.
+template <typename T, int RB>
+__device__ __forceinline__ void slice_reduce(T* __restrict__ red, int S, T (&acc)[RB]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < RB; ++r) red[(warp * RB + r) * 32 + lane] = acc[r];
+  __syncthreads();
+  if (warp % S == 0)
+    for (int s = 1; s < S; ++s) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) acc[r] += red[((warp + s) * RB + r) * 32 + lane];
+    }
+  __syncthreads();
+}
+
+// Upward pass of a dense front, NT threads.  The whole front vector [b_p; b_f] for RB
+// right-hand sides is formed in shared memory (r(I_p), then the children's update parts
+// through the relative maps, one child after another), then b_f -= K b_p with one row
+// of K per thread, and [b_p; b_f] is written to fv once.
+template <typename T, int RB, int NT>
+__global__ void __launch_bounds__(NT) k_dense_up(const int* __restrict__ fronts, int nrhs, int n,
+                                                 const T* __restrict__ win, const int32_t* __restrict__ first,
+                                                 const int* __restrict__ npiv, const int* __restrict__ nhat,
+                                                 const int64_t* __restrict__ front_off,
+                                                 const int64_t* __restrict__ fvoff,
+                                                 const int32_t* __restrict__ child_ptr,
+                                                 const int32_t* __restrict__ child_list,
+                                                 const int64_t* __restrict__ ifoff,
+                                                 const int32_t* __restrict__ relmap, const T* __restrict__ F,
+                                                 T* __restrict__ FV, int smem_rows) {
+  constexpr int W = NT / 32;
+  extern __shared__ unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);  // nhat x RB, row-major
+  T* red = X + smem_rows * RB;            // W x RB x 32
+  const int q = fronts[blockIdx.x];
+  const int r0 = blockIdx.y * RB, nr = min(RB, nrhs - r0);
+  const int np = npiv[q], nh = nhat[q], nu = nh - np, b0 = first[q];
+  for (int e = threadIdx.x; e < nh * RB; e += NT) {
+    const int i = e % nh, r = e / nh;
+    X[i * RB + r] = (i < np && r < nr) ? win[b0 + i + (int64_t)(r0 + r) * n] : T(0);
+  }
+  __syncthreads();
+  for (int ci = child_ptr[q]; ci < child_ptr[q + 1]; ++ci) {
+    const int c = child_list[ci];
+    const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
+    const T* fc = FV + fvoff[c] + npc;
+    const int32_t* rm = relmap + ifoff[c];
+    for (int e = threadIdx.x; e < nuc * nr; e += NT) {
+      const int t = e % nuc, r = e / nuc;
+      X[rm[t] * RB + r] += fc[t + (int64_t)(r0 + r) * nhc];
+    }
+    __syncthreads();
+  }
+  T* fv = FV + fvoff[q];
+  for (int e = threadIdx.x; e < np * nr; e += NT) {
+    const int i = e % np, r = e / np;
+    fv[i + (int64_t)(r0 + r) * nh] = X[i * RB + r];
+  }
+  if (nu == 0) return;
+  const T* K = F + front_off[q] + np;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrc = (nu + 31) / 32, ng = min(W, pow2_floor8(nrc)), S = W / ng;
+  const int g = warp / S, sl = warp % S;
+  const int j0 = sl * np / S, j1 = (sl + 1) * np / S;
+  for (int base = 0; base < nrc; base += ng) {
+    const int t = (base + g) * 32 + lane;
+    const bool active = base + g < nrc && t < nu;
+    T acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = T(0);
+    if (active) rowblock_acc<T, RB>(K, nh, t, j0, j1, X, 0, acc);
+    if (S > 1) slice_reduce<T, RB>(red, S, acc);
+    if (active && sl == 0) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r < nr) fv[np + t + (int64_t)(r0 + r) * nh] = X[(np + t) * RB + r] - acc[r];
+    }
+  }
+}
+
+// Downward pass of a dense front, NT threads: x_p = [F_pp^{-1} | K^T] [b_p; -x(I_p^f)],
+// the right-hand block staged in chunks of kDenseKC rows, one row of the product per
+// thread.
+template <typename T, int RB, int NT>
+__global__ void __launch_bounds__(NT) k_dense_down(const int* __restrict__ fronts, int nrhs, int n,
+                                                   T* __restrict__ xv, const int32_t* __restrict__ first,
+                                                   const int* __restrict__ npiv, const int* __restrict__ nhat,
+                                                   const int64_t* __restrict__ front_off,
+                                                   const int64_t* __restrict__ fvoff,
+                                                   const int64_t* __restrict__ ifoff,
+                                                   const int32_t* __restrict__ iflist, const T* __restrict__ F,
+                                                   const T* __restrict__ FV, int smem_rows) {
+  constexpr int W = NT / 32;
+  extern __shared__ unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);  // smem_rows x RB
+  T* red = X + smem_rows * RB;
+  const int q = fronts[blockIdx.x];
+  const int r0 = blockIdx.y * RB, nr = min(RB, nrhs - r0);
+  const int np = npiv[q], nh = nhat[q], b0 = first[q];
+  const T* fv = FV + fvoff[q];
+  const int32_t* If = iflist + ifoff[q];
+  const T* H = F + front_off[q];  // row j: [F_pp^{-1}(j, :) | K^T(j, :)]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrc = (np + 31) / 32, ng = min(W, pow2_floor8(nrc)), S = W / ng;
+  const int g = warp / S, sl = warp % S;
+  for (int base = 0; base < nrc; base += ng) {
+    const int j = (base + g) * 32 + lane;
+    const bool active = base + g < nrc && j < np;
+    T acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = T(0);
+    for (int kc0 = 0; kc0 < nh; kc0 += smem_rows) {
+      const int kc1 = min(nh, kc0 + smem_rows), len = kc1 - kc0;
+      __syncthreads();
+      for (int e = threadIdx.x; e < len * RB; e += NT) {
+        const int i = kc0 + e % len, r = e / len;
+        T v = T(0);
+        if (r < nr) v = i < np ? fv[i + (int64_t)(r0 + r) * nh] : -xv[If[i - np] + (int64_t)(r0 + r) * n];
+        X[(i - kc0) * RB + r] = v;
+      }
+      __syncthreads();
+      if (active) rowblock_acc<T, RB>(H, nh, j, kc0 + sl * len / S, kc0 + (sl + 1) * len / S, X, kc0, acc);
+    }
+    if (S > 1) slice_reduce<T, RB>(red, S, acc);
+    if (active && sl == 0) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r < nr) xv[b0 + j + (int64_t)(r0 + r) * n] = acc[r];
+    }
+  }
+}
+
+static int rhs_block(int nrhs) { return nrhs >= 16 ? 16 : nrhs > 4 ? 8 : nrhs > 2 ? 4 : nrhs; }
+
+// 64 threads per front when every front of the level is small (more fronts in flight per
+// SM); 256 otherwise.
+static bool small_level(const LevelSolvePlan& lp) { return lp.dense_max_nhat <= 128; }
+
+template <typename T, int RB, int NT>
+static void dense_up_launch(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys,
+                            SolvePlan* sp, int nrhs, const T* win, cudaStream_t s) {
+  const Plan& P = sys->plan;
+  const int rows = lp.dense_max_nhat;
+  const size_t smem = sizeof(T) * (size_t)RB * (rows + NT);
+  const dim3 grid((unsigned)lp.dense.count, (unsigned)((nrhs + RB - 1) / RB));
+  k_dense_up<T, RB, NT><<<grid, NT, smem, s>>>(lp.dense.dev(base), nrhs, sys->n, win, sys->d_first, P.d_np,
+                                               P.d_nhat, P.d_front_off, sp->d_fvoff, sys->d_child_ptr,
+                                               sys->d_child_list, sys->d_ifoff, sys->d_relmap,
+                                               (const T*)sys->d_front, (T*)sp->d_fv, rows);
+}
+
+template <typename T, int RB, int NT>
+static void dense_down_launch(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys,
+                              SolvePlan* sp, int nrhs, T* xv, cudaStream_t s) {
+  const Plan& P = sys->plan;
+  const int rows = std::min(lp.dense_max_nhat, kDenseKC);
+  const size_t smem = sizeof(T) * (size_t)RB * (rows + NT);
+  const dim3 grid((unsigned)lp.dense.count, (unsigned)((nrhs + RB - 1) / RB));
+  k_dense_down<T, RB, NT><<<grid, NT, smem, s>>>(lp.dense.dev(base), nrhs, sys->n, xv, sys->d_first, P.d_np,
+                                                 P.d_nhat, P.d_front_off, sp->d_fvoff, sys->d_ifoff,
+                                                 sys->d_iflist, (const T*)sys->d_front, (const T*)sp->d_fv,
+                                                 rows);
+}
+
+template <typename T, int RB>
+static void dense_up_rb(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
+                        int nrhs, const T* win, cudaStream_t s) {
+  if (small_level(lp)) dense_up_launch<T, RB, 64>(lp, base, sys, sp, nrhs, win, s);
+  else dense_up_launch<T, RB, 256>(lp, base, sys, sp, nrhs, win, s);
+}
+
+template <typename T, int RB>
+static void dense_down_rb(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
+                          int nrhs, T* xv, cudaStream_t s) {
+  if (small_level(lp)) dense_down_launch<T, RB, 64>(lp, base, sys, sp, nrhs, xv, s);
+  else dense_down_launch<T, RB, 256>(lp, base, sys, sp, nrhs, xv, s);
+}
+
+// Right-hand sides per block of the upward kernel: the block of the whole front vector
+// must fit in shared memory next to the reduction buffer.
+template <typename T>
+static int up_rhs_block(const LevelSolvePlan& lp, int nrhs, int max_smem) {
+  const int nt = small_level(lp) ? 64 : 256;
+  int rb = rhs_block(nrhs);
+  while (rb > 1 && sizeof(T) * (size_t)rb * (lp.dense_max_nhat + nt) > (size_t)max_smem) rb /= 2;
+  return rb;
+}
+
+template <typename T>
+static int dense_up(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
+                    int nrhs, const T* win, cudaStream_t s) {
+  const int rb = up_rhs_block<T>(lp, nrhs, sys->ctx->max_smem);
+  if (sizeof(T) * (size_t)rb * (lp.dense_max_nhat + 256) > (size_t)sys->ctx->max_smem) {
+    set_last_error("preconditioner apply: dense front too large for the upward kernel");
+    return HM_ERR_CAPACITY;
+  }
+  switch (rb) {
+    case 1: dense_up_rb<T, 1>(lp, base, sys, sp, nrhs, win, s); break;
+    case 2: dense_up_rb<T, 2>(lp, base, sys, sp, nrhs, win, s); break;
+    case 4: dense_up_rb<T, 4>(lp, base, sys, sp, nrhs, win, s); break;
+    case 8: dense_up_rb<T, 8>(lp, base, sys, sp, nrhs, win, s); break;
+    default: dense_up_rb<T, 16>(lp, base, sys, sp, nrhs, win, s); break;
+  }
+  return HM_OK;
+}
+
+template <typename T>
+static void dense_down(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
+                       int nrhs, T* xv, cudaStream_t s) {
+  switch (rhs_block(nrhs)) {
+    case 1: dense_down_rb<T, 1>(lp, base, sys, sp, nrhs, xv, s); break;
+    case 2: dense_down_rb<T, 2>(lp, base, sys, sp, nrhs, xv, s); break;
+    case 4: dense_down_rb<T, 4>(lp, base, sys, sp, nrhs, xv, s); break;
+    case 8: dense_down_rb<T, 8>(lp, base, sys, sp, nrhs, xv, s); break;
+    default: dense_down_rb<T, 16>(lp, base, sys, sp, nrhs, xv, s); break;
+  }
+}
+
 // HODLR fronts: x_p (= y - Vtilde W^T x_f, in the front's y buffer) -> output vector.
 template <typename T>
 __global__ void k_hodlr_out(const int* __restrict__ fronts, int nrhs, int n, T* __restrict__ xout,
@@ -126,31 +372,41 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
   const int n = sys->n;
   for (int l = P.nlevels - 1; l >= 0; --l) {
     const LevelSolvePlan& lp = sp->levels[l];
-    {
-      ProfScope ps(ctx, PC_UP, lp.up_work, 1 + (int)lp.slots.size());
-      k_vinit<T><<<vgrid(lp.nfronts, nrhs, lp.max_nhat), 256, 0, s>>>(
-          lp.fronts.dev(base), lp.nfronts, n, win, sys->d_first, P.d_np, P.d_nhat, sp->d_fvoff, FV);
-      for (size_t sl = 0; sl < lp.slots.size(); ++sl) {
-        const Span<int>& par = lp.slots[sl];
-        if (par.count == 0) continue;
-        k_vadd<T><<<vgrid(par.count, nrhs, lp.slot_max_nu[sl]), 256, 0, s>>>(
-            par.dev(base), par.count, (int)sl, sys->d_child_ptr, sys->d_child_list, P.d_np, P.d_nhat,
-            sp->d_fvoff, sys->d_ifoff, sys->d_relmap, FV);
-      }
+    if (lp.dense.count) {
+      ProfScope ps(ctx, PC_UP, lp.up_work);
+      HM_TRY(dense_up<T>(lp, base, sys, sp, nrhs, win, s));
     }
-    gemm_b<T>(ctx, lp.up_gemm, base);  // dense: f -= K b_p; HODLR: tf = Vtilde^T b_p
-    gemm_b<T>(ctx, lp.up2, base);      // HODLR: f -= W tf
+    if (lp.n_hodlr) {
+      {
+        ProfScope ps(ctx, PC_VECTOR, lp.hup_work, 1 + (int)lp.slots.size());
+        k_vinit<T><<<vgrid(lp.n_hodlr, nrhs, lp.hodlr_max_nhat), 256, 0, s>>>(
+            lp.hfronts.dev(base), lp.n_hodlr, n, win, sys->d_first, P.d_np, P.d_nhat, sp->d_fvoff, FV);
+        for (size_t sl = 0; sl < lp.slots.size(); ++sl) {
+          const Span<int>& par = lp.slots[sl];
+          if (par.count == 0) continue;
+          k_vadd<T><<<vgrid(par.count, nrhs, lp.slot_max_nu[sl]), 256, 0, s>>>(
+              par.dev(base), par.count, (int)sl, sys->d_child_ptr, sys->d_child_list, P.d_np, P.d_nhat,
+              sp->d_fvoff, sys->d_ifoff, sys->d_relmap, FV);
+        }
+      }
+      gemm_b<T>(ctx, lp.up_gemm, base);  // tf = Vtilde^T b_p
+      gemm_b<T>(ctx, lp.up2, base);      // f -= W tf
+    }
   }
   for (int l = 0; l < P.nlevels; ++l) {
     const LevelSolvePlan& lp = sp->levels[l];
-    if (lp.max_nu > 0) {
+    if (lp.dense.count) {
       ProfScope ps(ctx, PC_DOWN, lp.down_work);
-      k_vgather<T><<<vgrid(lp.nfronts, nrhs, lp.max_nu), 256, 0, s>>>(
-          lp.fronts.dev(base), lp.nfronts, n, xfix, P.d_np, P.d_nhat, sp->d_fvoff, sys->d_ifoff,
-          sys->d_iflist, FV);
+      dense_down<T>(lp, base, sys, sp, nrhs, xfix, s);
     }
-    gemm_b<T>(ctx, lp.down_gemm, base);  // dense: x_p = G^T fv; HODLR leaves: y = K_leaf^{-1} b
     if (lp.n_hodlr) {
+      if (lp.hodlr_max_nu > 0) {
+        ProfScope ps(ctx, PC_VECTOR, lp.hdown_work);
+        k_vgather<T><<<vgrid(lp.n_hodlr, nrhs, lp.hodlr_max_nu), 256, 0, s>>>(
+            lp.hfronts.dev(base), lp.n_hodlr, n, xfix, P.d_np, P.d_nhat, sp->d_fvoff, sys->d_ifoff,
+            sys->d_iflist, FV);
+      }
+      gemm_b<T>(ctx, lp.down_gemm, base);  // y = K_leaf^{-1} b on the HODLR leaves
       for (const auto& H : lp.heights) {
         gemm_b<T>(ctx, H.t, base);
         gemm_b<T>(ctx, H.s, base);
@@ -159,7 +415,7 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
       gemm_b<T>(ctx, lp.down1, base);
       gemm_b<T>(ctx, lp.down2, base);
       ProfScope ps(ctx, PC_VECTOR, Work{});
-      k_hodlr_out<T><<<lp.nfronts, 256, 0, s>>>(lp.fronts.dev(base), nrhs, n, xfix, sys->d_first,
+      k_hodlr_out<T><<<lp.n_hodlr, 256, 0, s>>>(lp.hfronts.dev(base), nrhs, n, xfix, sys->d_first,
                                                 P.d_np, sp->d_yvoff, (const T*)sp->d_sb);
     }
   }
@@ -169,8 +425,31 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
   return HM_OK;
 }
 
+template <typename T, int RB, int NT>
+static int dense_setup_one(int max_smem) {
+  HM_CUDA(allow_max_dyn_smem(k_dense_up<T, RB, NT>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_dense_down<T, RB, NT>, max_smem));
+  return HM_OK;
+}
+
+template <typename T>
+static int dense_setup(int max_smem) {
+  HM_TRY((dense_setup_one<T, 1, 64>(max_smem)));
+  HM_TRY((dense_setup_one<T, 2, 64>(max_smem)));
+  HM_TRY((dense_setup_one<T, 4, 64>(max_smem)));
+  HM_TRY((dense_setup_one<T, 8, 64>(max_smem)));
+  HM_TRY((dense_setup_one<T, 16, 64>(max_smem)));
+  HM_TRY((dense_setup_one<T, 1, 256>(max_smem)));
+  HM_TRY((dense_setup_one<T, 2, 256>(max_smem)));
+  HM_TRY((dense_setup_one<T, 4, 256>(max_smem)));
+  HM_TRY((dense_setup_one<T, 8, 256>(max_smem)));
+  HM_TRY((dense_setup_one<T, 16, 256>(max_smem)));
+  return HM_OK;
+}
+
 int solve_setup(int max_smem) {
-  (void)max_smem;
+  HM_TRY(dense_setup<float>(max_smem));
+  HM_TRY(dense_setup<double>(max_smem));
   return HM_OK;
 }
 
