@@ -109,7 +109,7 @@ const char* prof_cat_name(int c) {
       "nd_order", "symbolic", "permute_csr", "scatter_A", "extend_add", "dense_potrf",
       "dense_trsm", "gemm_factor", "sketch", "householder_qr", "jacobi_svd", "leaf_solve",
       "core_lu_inverse", "spd_inverse", "apply_up", "apply_down", "gemm_apply", "spmv", "gmres_dots",
-      "gmres_gs_update", "gmres_small", "vector_ops", "memset"};
+      "gmres_gs_update", "gmres_small", "vector_ops", "memset", "dense_sweep"};
   return (c >= 0 && c < PC_COUNT) ? names[c] : "?";
 }
 

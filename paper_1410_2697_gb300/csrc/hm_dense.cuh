@@ -60,6 +60,19 @@ struct QrTask {
   int m, k, ld, pad;
 };
 
+// Tall-skinny QR of an m x k panel (same contract as QrTask) in nb row blocks; the
+// stacked R factors and the block reflector scalars live at element offset soff of a
+// scratch arena (nb k x k, then nb k).
+struct TsqrTask {
+  void* Y;
+  void* R;
+  int64_t soff;
+  int m, k, ld, nb;
+};
+struct TsqrBlock {
+  int task, block;
+};
+
 // SVD of M = R^T (R k x k upper triangular, ld k) by one-sided Jacobi; writes
 // UhS = Uhat_r Sigma_r (k x k, ld k; columns >= rank zero) and Vh = Vhat_r (same),
 // sorted by decreasing singular value; rank = #{sigma_i > tol * sigma_1}.
@@ -81,6 +94,13 @@ struct OmegaTask {
 // Woodbury core C (n2 = 2k, ld n2): the GEMMs have written the two diagonal k x k
 // blocks; this sets the off-diagonal blocks to I, LU-factors C with partial pivoting and
 // writes the explicit inverse to Cinv (n2 x n2, ld n2).
+// A dense front (nhat x nhat, ld nhat, nhat <= 128) factored in one pass by np
+// Gauss-Jordan sweeps: F_pp^{-1}, K^T, K and U_p in place.
+struct SweepTask {
+  void* F;
+  int np, nhat, front, pad;
+};
+
 struct CoreLuTask {
   void* C;
   void* Cinv;
@@ -102,6 +122,8 @@ struct CholInvTask {
 template <typename T>
 void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, cudaStream_t s);
 template <typename T>
+void launch_front_sweep(const SweepTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s);
+template <typename T>
 void launch_potrf(const PotrfTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s);
 template <typename T>
 void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s);
@@ -109,6 +131,9 @@ template <typename T>
 void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStream_t s);
 template <typename T>
 void launch_qr(const QrTask* tasks, int ntasks, cudaStream_t s);
+template <typename T>
+void launch_tsqr(const TsqrTask* tasks, int ntasks, const TsqrBlock* blocks, int nblocks, size_t smem_block,
+                 size_t smem_stack, T* scratch, cudaStream_t s);
 template <typename T>
 void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStream_t s);
 template <typename T>

@@ -118,6 +118,193 @@ void launch_qr(const QrTask* tasks, int ntasks, cudaStream_t s) {
 }
 
 // =====================================================================================
+// Tall-skinny QR (TSQR) for the range finder's panels.  A panel's m rows are split into
+// nb balanced blocks (each at least k rows).  (1) every block is factored by Householder
+// in shared memory, its reflectors stay in the panel and its R_b goes to rows b k of a
+// stacked matrix S (nb k x k); (2) S is factored the same way, giving the panel's R, and
+// its explicit Q_S replaces S; (3) every block forms its rows of Q = diag(Q_b) Q_S as
+// H_0 ... H_{k-1} [S_b; 0] from its reflectors and the rows b k .. b k + k - 1 of Q_S.
+// Blocks of all panels of a level run in parallel; panels too large for shared memory
+// use the single-CTA kernel above.  Reflectors are the scale-safe ones of that kernel.
+// =====================================================================================
+
+// Householder factorization of A (m x k, ld, shared memory, m >= k) in place: R on and
+// above the diagonal, reflector tails below it, tau[j] per column.
+template <typename T>
+__device__ void hh_factor_smem(T* __restrict__ A, int m, int k, int ld, T* __restrict__ tau,
+                               T* __restrict__ red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    T* aj = A + (size_t)j * ld;
+    T s = T(0);
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) s += aj[i] * aj[i];
+    s = block_sum(s, red);
+    const T x0 = aj[j];
+    T tj = T(0), beta = x0, scale = T(1);
+    if (s > T(0)) {
+      const T nrm = sqrt(x0 * x0 + s);
+      beta = x0 >= T(0) ? -nrm : nrm;
+      tj = (beta - x0) / beta;
+      scale = T(1) / (x0 - beta);
+    }
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) aj[i] *= scale;
+    if (threadIdx.x == 0) {
+      aj[j] = beta;
+      tau[j] = tj;
+    }
+    __syncthreads();
+    if (tj != T(0)) {
+      for (int c = j + 1 + wid; c < k; c += nw) {
+        T* ac = A + (size_t)c * ld;
+        T w = T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) w += aj[i] * ac[i];
+        w = warp_sum(w) + ac[j];
+        const T f = tj * w;
+        __syncwarp();
+        if (lane == 0) ac[j] -= f;
+        for (int i = j + 1 + lane; i < m; i += 32) ac[i] -= f * aj[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// B (m x k, ld, shared memory) <- H_0 H_1 ... H_{k-1} B for reflectors with tails V
+// (column j: rows j+1 .. m-1 of V, implicit 1 at row j; any memory) and scalars tau.
+template <typename T>
+__device__ void hh_apply_backward(const T* __restrict__ V, int ldv, const T* __restrict__ tau,
+                                  T* __restrict__ B, int m, int k, int ldb) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = k - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    if (tj != T(0)) {
+      const T* vj = V + (size_t)j * ldv;
+      for (int c = wid; c < k; c += nw) {
+        T* bc = B + (size_t)c * ldb;
+        T w = T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) w += vj[i] * bc[i];
+        w = warp_sum(w) + bc[j];
+        const T f = tj * w;
+        __syncwarp();
+        if (lane == 0) bc[j] -= f;
+        for (int i = j + 1 + lane; i < m; i += 32) bc[i] -= f * vj[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tsqr_blocks(const TsqrTask* __restrict__ tasks,
+                                                     const TsqrBlock* __restrict__ blocks, T* __restrict__ scratch) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ T red[32];
+  const TsqrBlock bl = blocks[blockIdx.x];
+  const TsqrTask t = tasks[bl.task];
+  const int k = t.k, nb = t.nb;
+  const int r0 = (int)((int64_t)bl.block * t.m / nb), r1 = (int)((int64_t)(bl.block + 1) * t.m / nb);
+  const int mb = r1 - r0;
+  T* A = reinterpret_cast<T*>(smem_raw);  // mb x k, ld mb
+  T* Y = (T*)t.Y + r0;
+  for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+    const int i = e % mb, c = e / mb;
+    A[e] = Y[(size_t)i + (size_t)c * t.ld];
+  }
+  __syncthreads();
+  T* tau = scratch + t.soff + (int64_t)nb * k * k + (int64_t)bl.block * k;
+  hh_factor_smem<T>(A, mb, k, mb, tau, red);
+  T* S = scratch + t.soff;  // nb k x k, ld nb k
+  const int lds = nb * k;
+  for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+    const int i = e % mb, c = e / mb;
+    Y[(size_t)i + (size_t)c * t.ld] = A[e];
+    if (i < k) S[(size_t)(bl.block * k + i) + (size_t)c * lds] = i <= c ? A[e] : T(0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tsqr_stack(const TsqrTask* __restrict__ tasks, T* __restrict__ scratch) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ T red[32];
+  const TsqrTask t = tasks[blockIdx.x];
+  const int k = t.k, ms = t.nb * k;
+  T* A = reinterpret_cast<T*>(smem_raw);  // ms x k, ld ms
+  T* tau = A + (size_t)ms * k;            // k
+  T* S = scratch + t.soff;
+  for (int e = threadIdx.x; e < ms * k; e += blockDim.x) A[e] = S[e];
+  __syncthreads();
+  hh_factor_smem<T>(A, ms, k, ms, tau, red);
+  if (t.R) {
+    T* R = (T*)t.R;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int i = e % k, c = e / k;
+      R[i + (size_t)c * k] = i <= c ? A[(size_t)i + (size_t)c * ms] : T(0);
+    }
+  }
+  // explicit Q_S = H_0 ... H_{k-1} [I; 0], formed in place (column j's reflector is
+  // consumed at step j, after which the column holds Q_S's column j)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, c = e / k;
+    if (i < c) A[(size_t)i + (size_t)c * ms] = T(0);
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    T* aj = A + (size_t)j * ms;
+    for (int c = j + 1 + wid; c < k; c += nw) {
+      T* ac = A + (size_t)c * ms;
+      T w = T(0);
+      for (int i = j + 1 + lane; i < ms; i += 32) w += aj[i] * ac[i];
+      w = warp_sum(w);  // Q_S[j, c] is still zero here
+      const T f = tj * w;
+      if (lane == 0) ac[j] = -f;
+      for (int i = j + 1 + lane; i < ms; i += 32) ac[i] -= f * aj[i];
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < ms; i += blockDim.x) aj[i] *= -tj;
+    if (threadIdx.x == 0) aj[j] = T(1) - tj;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < ms * k; e += blockDim.x) S[e] = A[e];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tsqr_q(const TsqrTask* __restrict__ tasks,
+                                                const TsqrBlock* __restrict__ blocks, T* __restrict__ scratch) {
+  extern __shared__ unsigned char smem_raw[];
+  const TsqrBlock bl = blocks[blockIdx.x];
+  const TsqrTask t = tasks[bl.task];
+  const int k = t.k, nb = t.nb, lds = nb * k;
+  const int r0 = (int)((int64_t)bl.block * t.m / nb), r1 = (int)((int64_t)(bl.block + 1) * t.m / nb);
+  const int mb = r1 - r0;
+  T* B = reinterpret_cast<T*>(smem_raw);  // mb x k, ld mb
+  const T* S = scratch + t.soff;
+  for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+    const int i = e % mb, c = e / mb;
+    B[e] = i < k ? S[(size_t)(bl.block * k + i) + (size_t)c * lds] : T(0);
+  }
+  __syncthreads();
+  T* Y = (T*)t.Y + r0;
+  const T* tau = scratch + t.soff + (int64_t)nb * k * k + (int64_t)bl.block * k;
+  hh_apply_backward<T>(Y, t.ld, tau, B, mb, k, mb);
+  for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+    const int i = e % mb, c = e / mb;
+    Y[(size_t)i + (size_t)c * t.ld] = B[e];
+  }
+}
+
+template <typename T>
+void launch_tsqr(const TsqrTask* tasks, int ntasks, const TsqrBlock* blocks, int nblocks, size_t smem_block,
+                 size_t smem_stack, T* scratch, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  k_tsqr_blocks<T><<<nblocks, 256, smem_block, s>>>(tasks, blocks, scratch);
+  k_tsqr_stack<T><<<ntasks, 256, smem_stack, s>>>(tasks, scratch);
+  k_tsqr_q<T><<<nblocks, 256, smem_block, s>>>(tasks, blocks, scratch);
+}
+
+// =====================================================================================
 // SVD of M = R^T (k x k) by one-sided Jacobi (Hestenes) with the round-robin pair order;
 // a warp rotates one column pair at a time.  Sorted output, truncation at tol*sigma_1.
 // =====================================================================================
@@ -249,6 +436,12 @@ void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStre
 }
 
 int dense_comp_setup(int max_smem) {
+  HM_CUDA(allow_max_dyn_smem(k_tsqr_blocks<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_tsqr_blocks<double>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_tsqr_stack<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_tsqr_stack<double>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_tsqr_q<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_tsqr_q<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_svd<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_svd<double>, max_smem));
   return HM_OK;
@@ -258,6 +451,10 @@ template void launch_omega<float>(const OmegaTask*, int, uint64_t, cudaStream_t)
 template void launch_omega<double>(const OmegaTask*, int, uint64_t, cudaStream_t);
 template void launch_qr<float>(const QrTask*, int, cudaStream_t);
 template void launch_qr<double>(const QrTask*, int, cudaStream_t);
+template void launch_tsqr<float>(const TsqrTask*, int, const TsqrBlock*, int, size_t, size_t, float*,
+                                 cudaStream_t);
+template void launch_tsqr<double>(const TsqrTask*, int, const TsqrBlock*, int, size_t, size_t, double*,
+                                  cudaStream_t);
 template void launch_svd<float>(const SvdTask*, int, int, double, cudaStream_t);
 template void launch_svd<double>(const SvdTask*, int, int, double, cudaStream_t);
 

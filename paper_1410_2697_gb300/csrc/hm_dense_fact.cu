@@ -465,8 +465,111 @@ void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStr
 }
 
 
+// =====================================================================================
+// Dense front in one pass: np Gauss-Jordan sweeps of the whole front F (nhat x nhat,
+// rows/columns [I_p, I_p^f]) on the pivots 0 .. np-1.  The sweep on pivot k with d = F[k,k]
+// sets F[i,j] -= F[i,k] F[k,j] / d (i, j != k), F[i,k] /= d, F[k,j] /= d, F[k,k] = -1/d;
+// sweeps compose (the sweep operator of regression computing), and after the np sweeps
+//   F = [[-F_pp^{-1}, F_pp^{-1} F_pf], [F_fp F_pp^{-1}, F_ff - F_fp F_pp^{-1} F_pf]],
+// so negating the pivot block leaves exactly what the apply and the parent need:
+// F_pp^{-1}, K^T beside it, K = F_fp F_pp^{-1} below it and the update matrix U_p.  For an
+// SPD front every pivot is positive (a ratio of leading principal minors); a non-positive
+// one raises HM_ERR_NOT_SPD and the sweep goes on with |d|.  The input is the lower
+// triangle (what assembly and extend-add fill); the output is the full matrix.
+// One CTA of 16 x 16 threads per front: the front is staged through shared memory with
+// coalesced accesses, and thread (tx, ty) keeps the TT x TT entries (ty + 16 a, tx + 16 b)
+// in registers; a sweep costs every thread TT^2 FMAs and 2 TT shared-memory reads of the
+// published pivot row and column, with one barrier per sweep (double-buffered).
+// =====================================================================================
+template <typename T, int TT>
+__global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict__ tasks, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ T colk[2][16 * TT];
+  __shared__ T rowk[2][16 * TT];
+  const SweepTask t = tasks[blockIdx.x];
+  const int nh = t.nhat, np = t.np, ls = nh + 1;
+  T* S = reinterpret_cast<T*>(smem_raw);  // nh x nh staging, ld nh + 1
+  T* F = (T*)t.F;
+  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) S[e % nh + (e / nh) * ls] = F[e];
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T a[TT][TT];
+#pragma unroll
+  for (int i = 0; i < TT; ++i)
+#pragma unroll
+    for (int j = 0; j < TT; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;  // assembly fills the lower triangle
+      a[i][j] = (r < nh && c < nh) ? (r >= c ? S[r + c * ls] : S[c + r * ls]) : T(0);
+    }
+  // pivot k = 16 KB + kr: the block index KB is a compile-time constant of the unrolled
+  // outer loop, so the owners of row / column k address their registers statically
+#pragma unroll
+  for (int KB = 0; KB < TT; ++KB) {
+    for (int kr = 0; kr < 16; ++kr) {
+      const int k = 16 * KB + kr;
+      if (k >= np) break;  // uniform over the block
+      const int buf = k & 1;
+      if (tx == kr) {
+#pragma unroll
+        for (int i = 0; i < TT; ++i) colk[buf][ty + 16 * i] = a[i][KB];
+      }
+      if (ty == kr) {
+#pragma unroll
+        for (int j = 0; j < TT; ++j) rowk[buf][tx + 16 * j] = a[KB][j];
+      }
+      __syncthreads();
+      T d = rowk[buf][k];
+      if (!(d > T(0))) {
+        if (threadIdx.x == 0) raise_error(err, HM_ERR_NOT_SPD, t.front, k);
+        d = fabs(d) > T(0) ? fabs(d) : T(1);
+      }
+      const T inv = T(1) / d;
+      T ci[TT], rk[TT];
+#pragma unroll
+      for (int i = 0; i < TT; ++i) ci[i] = colk[buf][ty + 16 * i] * inv;
+#pragma unroll
+      for (int j = 0; j < TT; ++j) rk[j] = rowk[buf][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TT; ++i)
+#pragma unroll
+        for (int j = 0; j < TT; ++j) a[i][j] = fma(-ci[i], rk[j], a[i][j]);
+      // row k and column k (the generic update left them at zero)
+      if (tx == kr) {
+#pragma unroll
+        for (int i = 0; i < TT; ++i) a[i][KB] = (ty + 16 * i == k) ? -inv : ci[i];
+      }
+      if (ty == kr) {
+#pragma unroll
+        for (int j = 0; j < TT; ++j)
+          if (tx + 16 * j != k) a[KB][j] = rk[j] * inv;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < TT; ++i)
+#pragma unroll
+    for (int j = 0; j < TT; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < nh && c < nh) S[r + c * ls] = (r < np && c < np) ? -a[i][j] : a[i][j];
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) F[e] = S[e % nh + (e / nh) * ls];
+}
+
+template <typename T>
+void launch_front_sweep(const SweepTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)maxn * (maxn + 1) * sizeof(T);
+  if (maxn <= 64) k_front_sweep<T, 4><<<ntasks, 256, smem, s>>>(tasks, err);
+  else if (maxn <= 96) k_front_sweep<T, 6><<<ntasks, 256, smem, s>>>(tasks, err);
+  else k_front_sweep<T, 8><<<ntasks, 256, smem, s>>>(tasks, err);
+}
+
 template void launch_potrf<float>(const PotrfTask*, int, int, int*, cudaStream_t);
 template void launch_potrf<double>(const PotrfTask*, int, int, int*, cudaStream_t);
+template void launch_front_sweep<float>(const SweepTask*, int, int, int*, cudaStream_t);
+template void launch_front_sweep<double>(const SweepTask*, int, int, int*, cudaStream_t);
 template void launch_trsm<float>(const TrsmTask*, int, int, cudaStream_t);
 template void launch_trsm<double>(const TrsmTask*, int, int, cudaStream_t);
 template void launch_chol_solve<float>(const CholSolveTask*, int, int, cudaStream_t);
@@ -487,6 +590,12 @@ int dense_fact_setup(int max_smem) {
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_lu<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_inv_schur<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_front_sweep<float, 4>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_front_sweep<float, 6>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_front_sweep<float, 8>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_front_sweep<double, 4>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_front_sweep<double, 6>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_front_sweep<double, 8>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_inv_schur<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_lu<double>, max_smem));
   return HM_OK;

@@ -54,6 +54,16 @@ __global__ void __launch_bounds__(256) k_extend_add(const int* __restrict__ pare
   for (int r = col + lane; r < nuc; r += 32) Fp[rm[r] + cc] += Fc[r];
 }
 
+template <typename T>
+static void run_qr(hm_sys_s* sys, const QrBatch& b, const unsigned char* base) {
+  if (b.plain.count == 0 && b.ts.count == 0) return;
+  cudaStream_t s = sys->ctx->stream;
+  ProfScope ps(sys->ctx, PC_QR, b.work, (b.plain.count ? 1 : 0) + (b.ts.count ? 3 : 0));
+  launch_qr<T>(b.plain.dev(base), b.plain.count, s);
+  launch_tsqr<T>(b.ts.dev(base), b.ts.count, b.blocks.dev(base), b.blocks.count, b.smem_block, b.smem_stack,
+                 (T*)sys->d_qrs, s);
+}
+
 // Debug facility (environment HM_DEBUG_SYNC=1): after each stage of the factorization,
 // synchronize, report the device error word and count non-finite entries of the arenas.
 template <typename T>
@@ -127,7 +137,11 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
                                            P.d_front_off, P.d_nhat, P.d_np, sys->d_ifoff, sys->d_relmap, F);
     }
     debug_stage<T>(sys, "extendadd", l);
-    if (lp.n_dense) {
+    if (lp.sweep.count) {
+      ProfScope ps(ctx, PC_SWEEP, lp.sweep.work);
+      launch_front_sweep<T>(lp.sweep.dev(base), lp.sweep.count, lp.sweep_maxn, sys->d_err, s);
+    }
+    if (lp.potrf.count) {
       {
         ProfScope ps(ctx, PC_POTRF, lp.potrf.work);
         launch_potrf<T>(lp.potrf.dev(base), lp.potrf.count, lp.potrf_maxn, sys->d_err, s);
@@ -149,16 +163,10 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
         launch_omega<T>(lp.omega.dev(base), lp.omega.count, ctx->opts.seed, s);
       }
       run_gemm<T>(sys, lp.sampY, base, PC_GEMM_FACTOR);
-      {
-        ProfScope ps(ctx, PC_QR, lp.qrY.work);
-        launch_qr<T>(lp.qrY.dev(base), lp.qrY.count, s);
-      }
+      run_qr<T>(sys, lp.qrY, base);
       debug_stage<T>(sys, "qrY", l);
       run_gemm<T>(sys, lp.sampZ, base, PC_GEMM_FACTOR);
-      {
-        ProfScope ps(ctx, PC_QR, lp.qrZ.work);
-        launch_qr<T>(lp.qrZ.dev(base), lp.qrZ.count, s);
-      }
+      run_qr<T>(sys, lp.qrZ, base);
       {
         ProfScope ps(ctx, PC_SVD, lp.svd.work);
         launch_svd<T>(lp.svd.dev(base), lp.svd.count, lp.svd_maxk, tol, s);

@@ -28,6 +28,9 @@ inline Work work_of(const GemmTask& t, int es) {
   w.bytes = es * (m * k + k * n + (t.lower ? 0.5 : 1.0) * m * n * (t.beta != 0.0 ? 2.0 : 1.0));
   return w;
 }
+inline Work work_of(const SweepTask& t, int es) {
+  return Work{2.0 * t.np * (double)t.nhat * t.nhat, 2.0 * es * (double)t.nhat * t.nhat};
+}
 inline Work work_of(const PotrfTask& t, int es) {
   return Work{(double)t.n * t.n * t.n / 3.0, (double)es * t.n * (t.n + 1)};
 }
@@ -108,7 +111,7 @@ enum ProfCat {
   PC_ND = 0, PC_SYMBOLIC, PC_PERMUTE_CSR, PC_SCATTER, PC_EXTEND_ADD, PC_POTRF, PC_TRSM,
   PC_GEMM_FACTOR, PC_SKETCH, PC_QR, PC_SVD, PC_CHOL_SOLVE, PC_CORE_LU, PC_INVERSE,
   PC_UP, PC_DOWN, PC_GEMM_APPLY, PC_SPMV, PC_DOTS, PC_GS_UPDATE, PC_GMRES_SMALL, PC_VECTOR,
-  PC_MEMSET, PC_COUNT
+  PC_MEMSET, PC_SWEEP, PC_COUNT
 };
 const char* prof_cat_name(int c);
 
@@ -161,6 +164,16 @@ struct HFront {
   std::vector<int> leaf_lo, leaf_hi;
 };
 
+// Panel QRs of one launch group: shared-memory TSQR where the panel fits, the
+// single-CTA global-memory kernel otherwise.
+struct QrBatch {
+  Span<QrTask> plain;
+  Span<TsqrTask> ts;
+  Span<TsqrBlock> blocks;
+  size_t smem_block = 0, smem_stack = 0;
+  Work work;
+};
+
 struct LevelFactorPlan {
   std::vector<Span<int>> ea_parents;  // slot j: fronts of the level with more than j children
   std::vector<int> ea_max_nu;         // per slot, the largest update size of those children
@@ -171,10 +184,12 @@ struct LevelFactorPlan {
   int trsm_maxn = 0;
   GemmBatch syrk;
   Span<CholInvTask> dinv;      // F_pp^{-1} and K = F_fp F_pp^{-1} of the dense fronts
+  Span<SweepTask> sweep;       // dense fronts with nhat <= 128, factored in one pass
+  int sweep_maxn = 0;
   // HODLR fronts
   Span<OmegaTask> omega;
   GemmBatch sampY, sampZ, formU, formV;
-  Span<QrTask> qrY, qrZ;
+  QrBatch qrY, qrZ;
   Span<SvdTask> svd;
   int svd_maxk = 0;
   int64_t x_copy_off = 0, x_copy_len = 0;  // Bo -> X copy (elements)
@@ -243,6 +258,7 @@ struct Plan {
   int nlevels = 0;
   int64_t front_total = 0, bo_total = 0, w_total = 0, t_total = 0, p_total = 0;
   int64_t core_total = 0, piv_total = 0, comp_total = 0, tb_total = 0;
+  int64_t qr_scratch = 0;  // elements of the TSQR scratch arena (reused by every QR launch)
   int nrank = 0;
   std::vector<int64_t> level_front_begin, level_front_end;   // element ranges per level
   std::vector<LevelFactorPlan> levels;
@@ -331,6 +347,7 @@ struct hm_sys_s {
   void* d_core = nullptr;    // T
   int* d_piv = nullptr;
   void* d_comp = nullptr;    // T
+  void* d_qrs = nullptr;     // T, TSQR scratch
   void* d_tb = nullptr;      // T
   int* d_ranks = nullptr;
   double* d_pvals = nullptr; // permuted A values (FP64) for SpMV

@@ -29,6 +29,48 @@ static GemmTask gemm(const void* A, int lda, int opA, const void* B, int ldb, in
   return t;
 }
 
+// Splits the panel QRs of one launch group into TSQR panels (row blocks and the stacked
+// R factors in shared memory) and panels left to the global-memory kernel.
+static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, int max_smem,
+                             int64_t* scratch_need) {
+  QrBatch b;
+  std::vector<QrTask> plain;
+  std::vector<TsqrTask> ts;
+  std::vector<TsqrBlock> blocks;
+  const size_t budget = (size_t)std::max(0, max_smem - 2048);
+  int64_t off = 0;
+  for (const QrTask& t : v) {
+    b.work += work_of(t, es);
+    const int m = t.m, k = t.k;
+    const size_t kk = (size_t)k * k * es;
+    int nb = (m + std::max(256, 2 * k) - 1) / std::max(256, 2 * k);
+    const int nb_stack = kk > 0 ? (int)((budget - std::min(budget, (size_t)k * es)) / kk) : 0;
+    nb = std::min(nb, nb_stack);
+    // Below about a thousand rows the single-CTA kernel finishes first: the three TSQR
+    // stages cost about as much as one pass of it over that many rows.
+    const bool fits = m > 1024 && k > 0 && nb >= 1 && m / nb >= k &&
+                      (size_t)((m + nb - 1) / nb) * k * es <= budget;
+    if (!fits) {
+      plain.push_back(t);
+      continue;
+    }
+    for (int j = 0; j < nb; ++j) blocks.push_back(TsqrBlock{(int)ts.size(), j});
+    ts.push_back(TsqrTask{t.Y, t.R, off, m, k, t.ld, nb});
+    off += (int64_t)nb * k * k + (int64_t)nb * k;
+    b.smem_block = std::max(b.smem_block, (size_t)((m + nb - 1) / nb) * k * es);
+    b.smem_stack = std::max(b.smem_stack, ((size_t)nb * k * k + k) * es);
+  }
+  b.plain = tb.add(plain);
+  b.ts = tb.add(ts);
+  b.blocks = tb.add(blocks);
+  *scratch_need = std::max(*scratch_need, off);
+  return b;
+}
+
+// Dense fronts up to this size are factored by one sweep kernel (registers hold the
+// front); larger ones by Cholesky, triangular solve, update and inverse launches.
+constexpr int kSweepMaxN = 128;
+
 int build_plan(hm_sys_s* sys) {
   Plan& P = sys->plan;
   const hm_opts& o = sys->ctx->opts;
@@ -67,6 +109,7 @@ int build_plan(hm_sys_s* sys) {
   P.hf.clear();
   P.bo_total = P.w_total = P.t_total = P.p_total = 0;
   P.core_total = P.piv_total = P.comp_total = P.tb_total = 0;
+  P.qr_scratch = 0;
   P.nrank = 0;
   std::vector<int64_t> level_bo_begin(P.nlevels, 0), level_bo_end(P.nlevels, 0);
   for (int l = P.nlevels - 1; l >= 0; --l) {
@@ -235,11 +278,18 @@ int build_plan(hm_sys_s* sys) {
     std::vector<TrsmTask> trs;
     std::vector<GemmTask> syrk;
     std::vector<CholInvTask> dinv;
+    std::vector<SweepTask> sweep;
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
       if (g.hodlr >= 0) continue;
       lp.n_dense++;
       void* Fq = at(F, g.off, es);
+      fbytes += es * ((double)g.np * g.np + 2.0 * g.nu * g.np);
+      if (g.nhat <= kSweepMaxN) {
+        sweep.push_back(SweepTask{Fq, g.np, g.nhat, q, 0});
+        lp.sweep_maxn = std::max(lp.sweep_maxn, g.nhat);
+        continue;
+      }
       pot.push_back(PotrfTask{Fq, g.np, g.nhat, q, 0});
       lp.potrf_maxn = std::max(lp.potrf_maxn, g.np);
       if (g.nu > 0) {
@@ -254,12 +304,12 @@ int build_plan(hm_sys_s* sys) {
       // passes read the front with rows on consecutive threads
       dinv.push_back(CholInvTask{Fq, at(F, g.off + g.np, es), g.np, g.nhat, g.nu, g.nhat,
                                  at(F, g.off + (int64_t)g.np * g.nhat, es), g.nhat, 0});
-      fbytes += es * ((double)g.np * g.np + 2.0 * g.nu * g.np);
     }
     lp.potrf = tb.add(pot);
     lp.trsm = tb.add(trs);
     lp.syrk = tb.add_gemm(syrk);
     lp.dinv = tb.add(dinv);
+    lp.sweep = tb.add(sweep);
     // HODLR fronts
     std::vector<OmegaTask> om;
     std::vector<GemmTask> gy, gz, gu, gv;
@@ -339,9 +389,9 @@ int build_plan(hm_sys_s* sys) {
     }
     lp.omega = tb.add(om);
     lp.sampY = tb.add_gemm(gy);
-    lp.qrY = tb.add(qy);
+    lp.qrY = make_qr_batch(tb, qy, es, sys->ctx->max_smem, &P.qr_scratch);
     lp.sampZ = tb.add_gemm(gz);
-    lp.qrZ = tb.add(qz);
+    lp.qrZ = make_qr_batch(tb, qz, es, sys->ctx->max_smem, &P.qr_scratch);
     lp.svd = tb.add(sv);
     lp.formU = tb.add_gemm(gu);
     lp.formV = tb.add_gemm(gv);
@@ -403,6 +453,7 @@ int build_plan(hm_sys_s* sys) {
     lp.schurF = tb.add_gemm(sF);
   }
   P.factor_bytes = fbytes;
+  HM_TRY(dev_alloc(sys, &sys->d_qrs, (size_t)std::max<int64_t>(P.qr_scratch, 1) * es));
   HM_TRY(dev_alloc(sys, (void**)&P.d_tasks, std::max<size_t>(tb.host.size(), 16)));
   HM_CUDA(cudaMemcpyAsync(P.d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));
