@@ -24,7 +24,8 @@ __device__ __forceinline__ T load_op(const T* __restrict__ X, int op, int ld, in
 
 template <typename T, int BN>
 __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks,
-                                              const GemmTile* __restrict__ tiles) {
+                                              const GemmTile* __restrict__ tiles, T* __restrict__ split_ws,
+                                              unsigned* __restrict__ split_cnt) {
   constexpr int TN = BN / 16;       // columns per thread
   constexpr int NB = BK * BN / 256; // B elements loaded per thread
   __shared__ T As[BK][BM + 4];
@@ -76,12 +77,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     }
   };
 
-  if (t.k > 0) fetch(0);
-  for (int k0 = 0; k0 < t.k; k0 += BK) {
+  const int kend = tl.k1;
+  if (tl.k0 < kend) fetch(tl.k0);
+  for (int k0 = tl.k0; k0 < kend; k0 += BK) {
     __syncthreads();
     stash();
     __syncthreads();
-    if (k0 + BK < t.k) fetch(k0 + BK);
+    if (k0 + BK < kend) fetch(k0 + BK);
 #pragma unroll
     for (int p = 0; p < BK; ++p) {
       T a[4], b[TN];
@@ -94,6 +96,32 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
+  }
+  if (tl.slot >= 0) {
+    // split k: publish this part, and let the last part to arrive reduce in fixed order
+    __shared__ int last;
+    T* ws = split_ws + tl.woff;
+#pragma unroll
+    for (int j = 0; j < TN; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        ws[(size_t)tl.part * BM * BN + (ty + 16 * i) + (tx + 16 * j) * BM] = acc[i][j];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(split_cnt + tl.slot, 1u) == (unsigned)(tl.nsplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < TN; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        T v = T(0);
+        for (int p = 0; p < tl.nsplit; ++p)
+          v += __ldcg(ws + (size_t)p * BM * BN + (ty + 16 * i) + (tx + 16 * j) * BM);
+        acc[i][j] = v;
+      }
+    if (tid == 0) split_cnt[tl.slot] = 0u;  // ready for the next launch
   }
   const T alpha = (T)t.alpha, beta = (T)t.beta;
 #pragma unroll
@@ -118,24 +146,48 @@ int gemm_bn_for(const std::vector<GemmTask>& t) {
   return nmax <= 16 ? 16 : 64;
 }
 
-void gemm_tiles_for(const GemmTask& t, int task_index, int bn, std::vector<GemmTile>* out) {
+int gemm_tile_count(const GemmTask& t, int bn) {
+  if (t.m <= 0 || t.n <= 0) return 0;
+  const int tm = (t.m + BM - 1) / BM, tn = (t.n + bn - 1) / bn;
+  int c = 0;
+  for (int a = 0; a < tm; ++a)
+    for (int b = 0; b < tn; ++b) c += (t.lower && (a + 1) * BM - 1 < b * bn) ? 0 : 1;
+  return c;
+}
+
+void gemm_tiles_for(const GemmTask& t, int task_index, int bn, int nsplit, std::vector<GemmTile>* out,
+                    int* slots, int64_t* ws) {
   if (t.m <= 0 || t.n <= 0) return;
   const int tm = (t.m + BM - 1) / BM, tn = (t.n + bn - 1) / bn;
+  // k chunks are whole multiples of the k step
+  const int kc = nsplit > 1 ? ((t.k + nsplit - 1) / nsplit + BK - 1) / BK * BK : t.k;
+  const int parts = nsplit > 1 ? (t.k + kc - 1) / kc : 1;
   for (int a = 0; a < tm; ++a)
     for (int b = 0; b < tn; ++b) {
       if (t.lower && (a + 1) * BM - 1 < b * bn) continue;  // tile strictly above diagonal
-      out->push_back(GemmTile{task_index, (a << 16) | b});
+      if (parts <= 1) {
+        out->push_back(GemmTile{task_index, (a << 16) | b, 0, t.k, -1, 0, 1, 0, 0});
+        continue;
+      }
+      const int slot = (*slots)++;
+      const int64_t woff = *ws;
+      *ws += (int64_t)parts * BM * bn;
+      for (int p = 0; p < parts; ++p)
+        out->push_back(GemmTile{task_index, (a << 16) | b, p * kc, std::min(t.k, (p + 1) * kc), slot, p,
+                                parts, 0, woff});
     }
 }
 
 template <typename T>
-void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, cudaStream_t s) {
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, T* split_ws,
+                 unsigned* split_cnt, cudaStream_t s) {
   if (ntiles <= 0) return;
-  if (bn == 16) k_gemm<T, 16><<<ntiles, 256, 0, s>>>(tasks, tiles);
-  else k_gemm<T, 64><<<ntiles, 256, 0, s>>>(tasks, tiles);
+  if (bn == 16) k_gemm<T, 16><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
+  else k_gemm<T, 64><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
 }
 
-template void launch_gemm<float>(const GemmTask*, const GemmTile*, int, int, cudaStream_t);
-template void launch_gemm<double>(const GemmTask*, const GemmTile*, int, int, cudaStream_t);
+template void launch_gemm<float>(const GemmTask*, const GemmTile*, int, int, float*, unsigned*, cudaStream_t);
+template void launch_gemm<double>(const GemmTask*, const GemmTile*, int, int, double*, unsigned*,
+                                  cudaStream_t);
 
 }  // namespace hm

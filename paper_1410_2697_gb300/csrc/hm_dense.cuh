@@ -21,10 +21,17 @@ struct GemmTask {
   double alpha, beta;
 };
 
-// One 64x64 output tile: task index and tile coordinates (tm << 16 | tn).
+// One output tile (64 x BN) over the k range [k0, k1): task index and tile coordinates
+// (tm << 16 | tn).  A tile whose k range is split over nsplit CTAs has a slot >= 0: each
+// part writes its partial sums to the split workspace at woff + part * 64 * BN, and the
+// last part to finish (counted on the slot's counter) adds the parts in order 0 .. nsplit-1
+// and applies the epilogue, so the result does not depend on the finishing order.
 struct GemmTile {
   int task;
   int mn;
+  int k0, k1;
+  int slot, part, nsplit, pad;
+  int64_t woff;
 };
 
 constexpr int kGemmBM = 64;
@@ -120,7 +127,8 @@ struct CholInvTask {
 };
 
 template <typename T>
-void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, cudaStream_t s);
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, T* split_ws,
+                 unsigned* split_cnt, cudaStream_t s);
 template <typename T>
 void launch_front_sweep(const SweepTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s);
 template <typename T>
@@ -147,7 +155,11 @@ void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStr
 // Host-side: tile width (64, or 16 when every task has at most 16 columns) and the tiles
 // of one task (all tiles, or those touching the lower triangle when t.lower).
 int gemm_bn_for(const std::vector<GemmTask>& t);
-void gemm_tiles_for(const GemmTask& t, int task_index, int bn, std::vector<GemmTile>* out);
+int gemm_tile_count(const GemmTask& t, int bn);
+// Appends the tiles of task t; with nsplit > 1 every tile's k range is split into parts
+// that take consecutive split slots (*slots) and workspace (*ws elements).
+void gemm_tiles_for(const GemmTask& t, int task_index, int bn, int nsplit, std::vector<GemmTile>* out,
+                    int* slots, int64_t* ws);
 
 int dense_fact_setup(int max_dyn_smem);
 int dense_comp_setup(int max_dyn_smem);

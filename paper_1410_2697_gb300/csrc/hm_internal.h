@@ -92,11 +92,29 @@ struct TaskBuf {
     for (const auto& t : v) s.work += work_of(t, es);
     return s;
   }
+  // Split-k bookkeeping: the largest workspace (elements) and slot count of any batch
+  // (batches of one plan run one after another, so they share one workspace).
+  int64_t split_ws = 0;
+  int split_slots = 0;
+  // A batch with fewer tiles than about two waves of the GPU splits the k range of its
+  // long products (parts of at least kSplitMinK) so that more SMs share the work.
+  static constexpr int kSplitTarget = 304, kSplitMinK = 128, kSplitMax = 16;
   GemmBatch add_gemm(const std::vector<GemmTask>& t) {
     std::vector<GemmTile> tiles;
     GemmBatch b;
     b.bn = gemm_bn_for(t);
-    for (size_t i = 0; i < t.size(); ++i) gemm_tiles_for(t[i], (int)i, b.bn, &tiles);
+    int ntiles = 0;
+    for (const auto& x : t) ntiles += gemm_tile_count(x, b.bn);
+    int slots = 0;
+    int64_t ws = 0;
+    for (size_t i = 0; i < t.size(); ++i) {
+      int nsplit = 1;
+      if (ntiles < kSplitTarget && t[i].k >= 2 * kSplitMinK)
+        nsplit = std::min(std::min(kSplitTarget / std::max(ntiles, 1), t[i].k / kSplitMinK), kSplitMax);
+      gemm_tiles_for(t[i], (int)i, b.bn, nsplit, &tiles, &slots, &ws);
+    }
+    split_ws = std::max(split_ws, ws);
+    split_slots = std::max(split_slots, slots);
     b.tasks = add(t);
     b.tiles = add(tiles);
     return b;
@@ -244,6 +262,8 @@ struct SolvePlan {
   int64_t sb_total = 0;         // node t/s buffers + tf buffers
   TaskBuf tb;
   unsigned char* d_tasks = nullptr;
+  void* d_split_ws = nullptr;       // T, split-k partial sums of the apply GEMMs
+  unsigned* d_split_cnt = nullptr;
   void* d_fv = nullptr;         // T
   void* d_sb = nullptr;         // T
   void* d_xfix = nullptr;       // T, n x nrhs: the solution (task tables point into it)
@@ -264,6 +284,8 @@ struct Plan {
   std::vector<LevelFactorPlan> levels;
   TaskBuf tb;
   unsigned char* d_tasks = nullptr;
+  void* d_split_ws = nullptr;       // T, split-k partial sums of the factor GEMMs
+  unsigned* d_split_cnt = nullptr;  // split-k arrival counters (zero between launches)
   int64_t* d_front_off = nullptr;
   int* d_nhat = nullptr;
   int* d_np = nullptr;

@@ -454,6 +454,9 @@ int build_plan(hm_sys_s* sys) {
   }
   P.factor_bytes = fbytes;
   HM_TRY(dev_alloc(sys, &sys->d_qrs, (size_t)std::max<int64_t>(P.qr_scratch, 1) * es));
+  HM_TRY(dev_alloc(sys, &P.d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
+  HM_TRY(dev_alloc(sys, (void**)&P.d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));
+  HM_CUDA(cudaMemsetAsync(P.d_split_cnt, 0, sizeof(unsigned) * std::max(tb.split_slots, 1), sys->ctx->stream));
   HM_TRY(dev_alloc(sys, (void**)&P.d_tasks, std::max<size_t>(tb.host.size(), 16)));
   HM_CUDA(cudaMemcpyAsync(P.d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));
@@ -619,6 +622,10 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     lp.down1 = tb.add_gemm(d1);
     lp.down2 = tb.add_gemm(d2);
   }
+  HM_TRY(dev_alloc(sys, &sp->d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
+  HM_TRY(dev_alloc(sys, (void**)&sp->d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));
+  HM_CUDA(cudaMemsetAsync(sp->d_split_cnt, 0, sizeof(unsigned) * std::max(tb.split_slots, 1),
+                          sys->ctx->stream));
   HM_TRY(dev_alloc(sys, (void**)&sp->d_tasks, std::max<size_t>(tb.host.size(), 16)));
   HM_CUDA(cudaMemcpyAsync(sp->d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));

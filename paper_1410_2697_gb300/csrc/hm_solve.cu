@@ -348,10 +348,11 @@ __global__ void k_hodlr_out(const int* __restrict__ fronts, int nrhs, int n, T* 
 }
 
 template <typename T>
-static void gemm_b(hm_ctx_s* ctx, const GemmBatch& b, const unsigned char* base) {
+static void gemm_b(hm_ctx_s* ctx, const SolvePlan* sp, const GemmBatch& b) {
   if (b.tiles.count == 0) return;
   ProfScope ps(ctx, PC_GEMM_APPLY, b.tasks.work);
-  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, ctx->stream);
+  launch_gemm<T>(b.tasks.dev(sp->d_tasks), b.tiles.dev(sp->d_tasks), b.tiles.count, b.bn, (T*)sp->d_split_ws,
+                 sp->d_split_cnt, ctx->stream);
 }
 
 static dim3 vgrid(int nitems, int nrhs, int maxlen) {
@@ -389,8 +390,8 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
               sp->d_fvoff, sys->d_ifoff, sys->d_relmap, FV);
         }
       }
-      gemm_b<T>(ctx, lp.up_gemm, base);  // tf = Vtilde^T b_p
-      gemm_b<T>(ctx, lp.up2, base);      // f -= W tf
+      gemm_b<T>(ctx, sp, lp.up_gemm);  // tf = Vtilde^T b_p
+      gemm_b<T>(ctx, sp, lp.up2);      // f -= W tf
     }
   }
   for (int l = 0; l < P.nlevels; ++l) {
@@ -406,14 +407,14 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
             lp.hfronts.dev(base), lp.n_hodlr, n, xfix, P.d_np, P.d_nhat, sp->d_fvoff, sys->d_ifoff,
             sys->d_iflist, FV);
       }
-      gemm_b<T>(ctx, lp.down_gemm, base);  // y = K_leaf^{-1} b on the HODLR leaves
+      gemm_b<T>(ctx, sp, lp.down_gemm);  // y = K_leaf^{-1} b on the HODLR leaves
       for (const auto& H : lp.heights) {
-        gemm_b<T>(ctx, H.t, base);
-        gemm_b<T>(ctx, H.s, base);
-        gemm_b<T>(ctx, H.upd, base);
+        gemm_b<T>(ctx, sp, H.t);
+        gemm_b<T>(ctx, sp, H.s);
+        gemm_b<T>(ctx, sp, H.upd);
       }
-      gemm_b<T>(ctx, lp.down1, base);
-      gemm_b<T>(ctx, lp.down2, base);
+      gemm_b<T>(ctx, sp, lp.down1);
+      gemm_b<T>(ctx, sp, lp.down2);
       ProfScope ps(ctx, PC_VECTOR, Work{});
       k_hodlr_out<T><<<lp.n_hodlr, 256, 0, s>>>(lp.hfronts.dev(base), nrhs, n, xfix, sys->d_first,
                                                 P.d_np, sp->d_yvoff, (const T*)sp->d_sb);
