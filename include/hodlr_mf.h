@@ -47,8 +47,12 @@ enum hm_status {
 };
 
 enum hm_precision {
-  HM_PREC_FP64 = 0, /* factorization, compression and preconditioner apply in FP64     */
-  HM_PREC_MIXED = 1 /* factorization, compression and apply in FP32; GMRES in FP64     */
+  HM_PREC_FP64 = 0,      /* factorization, compression and preconditioner apply in FP64 */
+  HM_PREC_MIXED = 1,     /* factorization, compression and apply in FP32; GMRES in FP64 */
+  HM_PREC_MIXED_BF16 = 2 /* as MIXED, with the range finder's sampling products Y = B Omega
+                            and Z = B^T Q on the tensor cores (BF16 operands, FP32
+                            accumulation); the compression error then includes BF16
+                            rounding of the sampled blocks (about 2^-9 of their size)      */
 };
 
 typedef struct hm_opts {

@@ -27,6 +27,7 @@ HM_ERR_STATE = 8
 HM_ERR_BREAKDOWN = 9
 HM_PREC_FP64 = 0
 HM_PREC_MIXED = 1
+HM_PREC_MIXED_BF16 = 2
 
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_get_sizes",
             "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_solve", "hm_precond_apply",

@@ -225,8 +225,8 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   *out = nullptr;
   hm_opts o;
   if (opts) o = *opts; else hm_default_opts(&o);
-  if (o.precision != HM_PREC_FP64 && o.precision != HM_PREC_MIXED) {
-    set_last_error("precision must be HM_PREC_FP64 or HM_PREC_MIXED");
+  if (o.precision != HM_PREC_FP64 && o.precision != HM_PREC_MIXED && o.precision != HM_PREC_MIXED_BF16) {
+    set_last_error("precision must be HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_BF16");
     return HM_ERR_INVALID_ARG;
   }
   const int kmax = o.precision == HM_PREC_FP64 ? 112 : 128;
@@ -277,6 +277,7 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   ctx->num_sms = prop.multiProcessorCount;
   int st = dense_fact_setup(ctx->max_smem);
   if (st == HM_OK) st = dense_comp_setup(ctx->max_smem);
+  if (st == HM_OK) st = dense_tc_setup(ctx->max_smem);
   if (st == HM_OK) st = solve_setup(ctx->max_smem);
   if (st != HM_OK) {
     delete ctx;

@@ -146,32 +146,32 @@ int gemm_bn_for(const std::vector<GemmTask>& t) {
   return nmax <= 16 ? 16 : 64;
 }
 
-int gemm_tile_count(const GemmTask& t, int bn) {
+int gemm_tile_count(const GemmTask& t, int bm, int bn) {
   if (t.m <= 0 || t.n <= 0) return 0;
-  const int tm = (t.m + BM - 1) / BM, tn = (t.n + bn - 1) / bn;
+  const int tm = (t.m + bm - 1) / bm, tn = (t.n + bn - 1) / bn;
   int c = 0;
   for (int a = 0; a < tm; ++a)
-    for (int b = 0; b < tn; ++b) c += (t.lower && (a + 1) * BM - 1 < b * bn) ? 0 : 1;
+    for (int b = 0; b < tn; ++b) c += (t.lower && (a + 1) * bm - 1 < b * bn) ? 0 : 1;
   return c;
 }
 
-void gemm_tiles_for(const GemmTask& t, int task_index, int bn, int nsplit, std::vector<GemmTile>* out,
+void gemm_tiles_for(const GemmTask& t, int task_index, int bm, int bn, int nsplit, std::vector<GemmTile>* out,
                     int* slots, int64_t* ws) {
   if (t.m <= 0 || t.n <= 0) return;
-  const int tm = (t.m + BM - 1) / BM, tn = (t.n + bn - 1) / bn;
+  const int tm = (t.m + bm - 1) / bm, tn = (t.n + bn - 1) / bn;
   // k chunks are whole multiples of the k step
   const int kc = nsplit > 1 ? ((t.k + nsplit - 1) / nsplit + BK - 1) / BK * BK : t.k;
   const int parts = nsplit > 1 ? (t.k + kc - 1) / kc : 1;
   for (int a = 0; a < tm; ++a)
     for (int b = 0; b < tn; ++b) {
-      if (t.lower && (a + 1) * BM - 1 < b * bn) continue;  // tile strictly above diagonal
+      if (t.lower && (a + 1) * bm - 1 < b * bn) continue;  // tile strictly above diagonal
       if (parts <= 1) {
         out->push_back(GemmTile{task_index, (a << 16) | b, 0, t.k, -1, 0, 1, 0, 0});
         continue;
       }
       const int slot = (*slots)++;
       const int64_t woff = *ws;
-      *ws += (int64_t)parts * BM * bn;
+      *ws += (int64_t)parts * bm * bn;
       for (int p = 0; p < parts; ++p)
         out->push_back(GemmTile{task_index, (a << 16) | b, p * kc, std::min(t.k, (p + 1) * kc), slot, p,
                                 parts, 0, woff});

@@ -155,11 +155,17 @@ void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStr
 // Host-side: tile width (64, or 16 when every task has at most 16 columns) and the tiles
 // of one task (all tiles, or those touching the lower triangle when t.lower).
 int gemm_bn_for(const std::vector<GemmTask>& t);
-int gemm_tile_count(const GemmTask& t, int bn);
-// Appends the tiles of task t; with nsplit > 1 every tile's k range is split into parts
-// that take consecutive split slots (*slots) and workspace (*ws elements).
-void gemm_tiles_for(const GemmTask& t, int task_index, int bn, int nsplit, std::vector<GemmTile>* out,
+int gemm_tile_count(const GemmTask& t, int bm, int bn);
+// Appends the bm x bn tiles of task t; with nsplit > 1 every tile's k range is split into
+// parts that take consecutive split slots (*slots) and workspace (*ws elements).
+void gemm_tiles_for(const GemmTask& t, int task_index, int bm, int bn, int nsplit, std::vector<GemmTile>* out,
                     int* slots, int64_t* ws);
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation) batched GEMM on 128 x 64 tiles;
+// FP32 data in memory.  A mbarrier wait that runs out raises HM_ERR_DEVICE_TIMEOUT in err.
+constexpr int kTcBM = 128, kTcBN = 64;
+void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
+                    unsigned* split_cnt, int* err, cudaStream_t s);
+int dense_tc_setup(int max_smem);
 
 int dense_fact_setup(int max_dyn_smem);
 int dense_comp_setup(int max_dyn_smem);

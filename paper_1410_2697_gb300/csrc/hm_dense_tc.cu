@@ -1,0 +1,231 @@
+// hm_dense_tc.cu -- batched GEMM on the 5th-generation tensor cores (tcgen05), BF16
+// operands with FP32 accumulation in tensor memory, for the randomized range finder's
+// sampling products Y = B Omega and Z = B^T Q (the BF16 range-finder precision mode).
+//
+// One CTA (256 threads) per 128 x 64 output tile (or per k part of a split tile, with
+// the same fixed-order reduction as the SIMT GEMM).  Per 64-deep k slice the threads
+// read the FP32 operands from HBM (coalesced for either transpose), round them to BF16
+// and store them in shared memory in the K-major core-matrix layout (8 rows x 16 bytes
+// per 128-byte core matrix; K-adjacent core matrices 16 * rows bytes apart, row-group
+// adjacent ones 128 bytes apart).  One elected thread issues four
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 64, K = 16) on the slice and commits
+// them to the slice's mbarrier; the next slice is staged into the other buffer while the
+// tensor core runs.  The accumulator (128 lanes x 64 FP32 columns of tensor memory) is
+// read back with tcgen05.ld (warp w: lanes 32 (w % 4) .., columns 32 (w / 4) ..) for the
+// alpha / beta epilogue.  Every mbarrier wait is bounded; a wait that runs out sets the
+// device error word (HM_ERR_DEVICE_TIMEOUT), skips the rest of the tile and still frees
+// the tensor memory.
+#include <cuda_bf16.h>
+
+#include "hm_dense.cuh"
+
+namespace hm {
+
+namespace {
+
+constexpr int TM = 128, TN = 64, TK = 64;                 // tile and k slice
+constexpr int kStageA = TM * TK * 2, kStageB = TN * TK * 2;  // bytes of one slice (BF16)
+constexpr int kTcSmem = 2 * (kStageA + kStageB);           // double-buffered
+constexpr int kWaitLimit = 1 << 22;                        // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading (K-direction) and stride
+// (row-group direction) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N >> 3 and M >> 4.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+// byte offset of element (row, kk) of a K-major slice with `rows` rows
+__device__ __forceinline__ uint32_t kmaj(int row, int kk, int rows) {
+  return (uint32_t)((kk >> 3) * rows * 16 + (row >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// element (r, c) of op(X) (nr x nc); zero outside
+__device__ __forceinline__ float op_at(const float* __restrict__ X, int op, int ld, int r, int c, int nr, int nc) {
+  if (r >= nr || c >= nc) return 0.f;
+  return op == 0 ? X[(size_t)r + (size_t)c * ld] : X[(size_t)c + (size_t)r * ld];
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ tasks,
+                                                 const GemmTile* __restrict__ tiles, float* __restrict__ split_ws,
+                                                 unsigned* __restrict__ split_cnt, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_ok, s_last;
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask t = tasks[tl.task];
+  const int m0 = (tl.mn >> 16) * TM, n0 = (tl.mn & 0xffff) * TN;
+  const float* __restrict__ A = (const float*)t.A;
+  const float* __restrict__ B = (const float*)t.B;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_slot)), "r"(TN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const int nk = (tl.k1 - tl.k0 + TK - 1) / TK;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int s = kt & 1;
+    if (kt >= 2) {  // the MMAs that read this buffer two slices ago must be done
+      if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kt >> 1) - 1) & 1))) s_ok = 0;
+      __syncthreads();
+      if (!s_ok) break;
+    }
+    unsigned char* sA = smem + s * (kStageA + kStageB);
+    unsigned char* sB = sA + kStageA;
+    const int kb = tl.k0 + kt * TK;
+    // A slice: op(A)[m0 .. m0+127, kb .. kb+63]; consecutive threads follow the stored order
+    for (int e = tid; e < TM * TK; e += 256) {
+      int r, c;
+      if (t.opA == 0) { r = e % TM; c = e / TM; } else { c = e % TK; r = e / TK; }
+      const float v = (kb + c < tl.k1) ? op_at(A, t.opA, t.lda, m0 + r, kb + c, t.m, t.k) : 0.f;
+      *(__nv_bfloat16*)(sA + kmaj(r, c, TM)) = __float2bfloat16(v);
+    }
+    // B slice as N x K (row n = column n of op(B))
+    for (int e = tid; e < TN * TK; e += 256) {
+      int r, c;  // r: n, c: k
+      if (t.opB == 0) { c = e % TK; r = e / TK; } else { r = e % TN; c = e / TN; }
+      const float v = (kb + c < tl.k1) ? op_at(B, t.opB, t.ldb, kb + c, n0 + r, t.k, t.n) : 0.f;
+      *(__nv_bfloat16*)(sB + kmaj(r, c, TN)) = __float2bfloat16(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+      for (int j = 0; j < TK / 16; ++j) {
+        const uint64_t da = umma_desc(a0 + (uint32_t)(2 * j * TM * 16), TM * 16, 128);
+        const uint64_t db = umma_desc(b0 + (uint32_t)(2 * j * TN * 16), TN * 16, 128);
+        const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                     :: "r"(tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
+                     : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&mbar[s])) : "memory");
+    }
+  }
+  if (nk > 0 && s_ok) {
+    const int s = (nk - 1) & 1;
+    if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((nk - 1) >> 1) & 1))) s_ok = 0;
+  }
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  if (!ok && tid == 0) {
+    raise_error(err, HM_ERR_DEVICE_TIMEOUT, 20, blockIdx.x);
+    // give the slices still in flight a bounded chance to finish before the tensor
+    // memory is released
+    for (int s = 0; s < 2 && s < nk; ++s) {
+      const int uses = (nk - s + 1) / 2;  // slices kt = s, s + 2, ... committed to buffer s
+      (void)mbar_wait(smem_u32(&mbar[s]), (uint32_t)((uses - 1) & 1));
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // accumulator -> registers: row = lane quarter of the warp, 32 columns per warp half
+  const int row = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);
+  float acc[32];
+  if (ok && nk > 0) {
+    uint32_t v[32];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                   "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                   "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                   "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = __uint_as_float(v[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TN) : "memory");
+  if (!ok) return;
+  if (tl.slot >= 0) {  // split k: same fixed-order reduction as the SIMT GEMM
+    float* ws = split_ws + tl.woff;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) ws[(size_t)tl.part * TM * TN + row + (size_t)(c0 + j) * TM] = acc[j];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(split_cnt + tl.slot, 1u) == (unsigned)(tl.nsplit - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float v = 0.f;
+      for (int p = 0; p < tl.nsplit; ++p) v += __ldcg(ws + (size_t)p * TM * TN + row + (size_t)(c0 + j) * TM);
+      acc[j] = v;
+    }
+    if (tid == 0) split_cnt[tl.slot] = 0u;
+  }
+  float* C = (float*)t.C;
+  const float alpha = (float)t.alpha, beta = (float)t.beta;
+  const int r = m0 + row;
+  if (r >= t.m) return;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int c = n0 + c0 + j;
+    if (c >= t.n || (t.lower && r < c)) continue;
+    float* dst = C + (size_t)r + (size_t)c * t.ldc;
+    const float v = alpha * acc[j];
+    *dst = (beta == 0.f) ? v : fmaf(beta, *dst, v);
+  }
+}
+
+void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
+                    unsigned* split_cnt, int* err, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_gemm_tc<<<ntiles, 256, kTcSmem, s>>>(tasks, tiles, split_ws, split_cnt, err);
+}
+
+int dense_tc_setup(int max_smem) {
+  (void)max_smem;
+  HM_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  return HM_OK;
+}
+
+}  // namespace hm

@@ -101,8 +101,12 @@ template <typename T>
 static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* base, int cat) {
   if (b.tiles.count == 0) return;
   ProfScope ps(sys->ctx, cat, b.tasks.work);
-  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, (T*)sys->plan.d_split_ws,
-                 sys->plan.d_split_cnt, sys->ctx->stream);
+  if (b.tc && sizeof(T) == 4)
+    launch_gemm_tc(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, (float*)sys->plan.d_split_ws,
+                   sys->plan.d_split_cnt, sys->d_err, sys->ctx->stream);
+  else
+    launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, (T*)sys->plan.d_split_ws,
+                   sys->plan.d_split_cnt, sys->ctx->stream);
 }
 
 template <typename T>

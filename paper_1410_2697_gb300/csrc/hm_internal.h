@@ -75,6 +75,7 @@ struct GemmBatch {
   Span<GemmTask> tasks;
   Span<GemmTile> tiles;
   int bn = 64;  // tile width of the batch
+  int tc = 0;   // 1: tensor-core BF16 kernel (128 x 64 tiles)
 };
 
 // Host builder of the task buffer (one upload after planning).
@@ -99,19 +100,21 @@ struct TaskBuf {
   // A batch with fewer tiles than about two waves of the GPU splits the k range of its
   // long products (parts of at least kSplitMinK) so that more SMs share the work.
   static constexpr int kSplitTarget = 304, kSplitMinK = 128, kSplitMax = 16;
-  GemmBatch add_gemm(const std::vector<GemmTask>& t) {
+  GemmBatch add_gemm(const std::vector<GemmTask>& t, bool tc = false) {
     std::vector<GemmTile> tiles;
     GemmBatch b;
-    b.bn = gemm_bn_for(t);
+    b.tc = tc ? 1 : 0;
+    b.bn = tc ? kTcBN : gemm_bn_for(t);
+    const int bm = tc ? kTcBM : kGemmBM;
     int ntiles = 0;
-    for (const auto& x : t) ntiles += gemm_tile_count(x, b.bn);
+    for (const auto& x : t) ntiles += gemm_tile_count(x, bm, b.bn);
     int slots = 0;
     int64_t ws = 0;
     for (size_t i = 0; i < t.size(); ++i) {
       int nsplit = 1;
       if (ntiles < kSplitTarget && t[i].k >= 2 * kSplitMinK)
         nsplit = std::min(std::min(kSplitTarget / std::max(ntiles, 1), t[i].k / kSplitMinK), kSplitMax);
-      gemm_tiles_for(t[i], (int)i, b.bn, nsplit, &tiles, &slots, &ws);
+      gemm_tiles_for(t[i], (int)i, bm, b.bn, nsplit, &tiles, &slots, &ws);
     }
     split_ws = std::max(split_ws, ws);
     split_slots = std::max(split_slots, slots);

@@ -388,9 +388,10 @@ int build_plan(hm_sys_s* sys) {
       }
     }
     lp.omega = tb.add(om);
-    lp.sampY = tb.add_gemm(gy);
+    const bool tc = sys->precision == HM_PREC_MIXED_BF16;  // sampling products on tensor cores
+    lp.sampY = tb.add_gemm(gy, tc);
     lp.qrY = make_qr_batch(tb, qy, es, sys->ctx->max_smem, &P.qr_scratch);
-    lp.sampZ = tb.add_gemm(gz);
+    lp.sampZ = tb.add_gemm(gz, tc);
     lp.qrZ = make_qr_batch(tb, qz, es, sys->ctx->max_smem, &P.qr_scratch);
     lp.svd = tb.add(sv);
     lp.formU = tb.add_gemm(gu);
