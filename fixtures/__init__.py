@@ -15,4 +15,7 @@ from .meshes import (  # noqa: F401
     lognormal_coefficients,
     workload,
     WORKLOADS,
+    p1_batch_sizes,
+    p1_batch,
+    block_diagonal,
 )

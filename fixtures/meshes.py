@@ -258,3 +258,37 @@ def p1_batch_sizes(count: int = 256, seed: int = 5) -> np.ndarray:
     uses seed ``seed + i`` for its own geometry and coefficients."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.integers(32, 257, size=count)
+
+
+def block_diagonal(problems: list) -> tuple:
+    """Independent meshes as one block-diagonal problem: ``(Problem, block_ptr)`` with
+    mesh b's unknowns at ``[block_ptr[b], block_ptr[b+1])`` (each keeps its own lattice
+    coordinates)."""
+    block_ptr = np.zeros(len(problems) + 1, dtype=np.int32)
+    for b, p in enumerate(problems):
+        block_ptr[b + 1] = block_ptr[b] + p.n
+    rowptr = [np.zeros(1, dtype=np.int64)]
+    colidx, values, coords = [], [], []
+    nnz = 0
+    for b, p in enumerate(problems):
+        rowptr.append(p.rowptr[1:] + nnz)
+        colidx.append(p.colidx + block_ptr[b])
+        values.append(p.values)
+        coords.append(p.coords)
+        nnz += p.nnz
+    dims = {p.dim for p in problems}
+    assert len(dims) == 1
+    prob = Problem(f"batch_{len(problems)}", int(block_ptr[-1]), dims.pop(), np.concatenate(rowptr),
+                   np.concatenate(colidx).astype(np.int32), np.concatenate(values),
+                   np.ascontiguousarray(np.concatenate(coords)), (), {"blocks": len(problems)})
+    return prob, block_ptr
+
+
+def p1_batch(count: int = 256, seed: int = 5) -> tuple:
+    """The batch of unstructured P1 meshes: mesh i has ``n ~ U{32..256}`` cells per side
+    (from ``p1_batch_sizes``), geometry and coefficients from seed ``seed + i``.  Returns
+    ``(Problem, block_ptr, meshes)``."""
+    sizes = p1_batch_sizes(count, seed)
+    meshes = [p1_jittered(int(nc), seed=seed + i) for i, nc in enumerate(sizes)]
+    prob, block_ptr = block_diagonal(meshes)
+    return prob, block_ptr, meshes

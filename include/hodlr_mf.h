@@ -111,7 +111,8 @@ int hm_ctx_destroy(hm_ctx_t ctx);
  *                                 optional user ordering instead of grid_coords: perm_in[n]
  *                                 maps new -> original index; tree node p (postorder,
  *                                 children before parents) owns new indices
- *                                 [first_in[p], first_in[p+1]); parent_in[root] = -1.
+ *                                 [first_in[p], first_in[p+1]); parent_in[root] = -1
+ *                                 (a forest may have several roots).
  *                                 Pass NULL / 0 to use grid_coords.
  *   out                           receives the system handle.
  * Errors: HM_ERR_INVALID_ARG for a malformed CSR / lattice / tree, HM_ERR_CAPACITY if a
@@ -121,6 +122,23 @@ int hm_analyze(hm_ctx_t ctx, int32_t n, const int64_t* rowptr, const int32_t* co
                int32_t dim, const int32_t* grid_coords, const int32_t* perm_in,
                int32_t nfronts_in, const int32_t* first_in, const int32_t* parent_in,
                hm_sys_t* out);
+
+/*
+ * Batched analysis of independent meshes (a block-diagonal A): the unknowns are split
+ * into nblocks contiguous ranges [block_ptr[b], block_ptr[b+1]); every coupling of A stays
+ * inside its range, and each range's grid_coords fill that range's own bounding box.
+ * Every block is ordered by the nested dissection of hm_analyze (its unknowns keep their
+ * range in the new numbering), and the elimination tree is the forest of the blocks'
+ * trees, concatenated in postorder.  hm_factor then processes all fronts of one tree depth
+ * across every block in the same launches, and hm_solve runs GMRES independently on every
+ * (block, right-hand side) pair: each stops on its own relative residual
+ * ||b_b - A_b x_b|| / ||b_b||.  Host or device pointers; block_ptr[nblocks + 1] with
+ * block_ptr[0] = 0 and block_ptr[nblocks] = n.  Errors as hm_analyze, and
+ * HM_ERR_INVALID_ARG for a coupling between blocks.
+ */
+int hm_analyze_batch(hm_ctx_t ctx, int32_t n, const int64_t* rowptr, const int32_t* colidx,
+                     int32_t dim, const int32_t* grid_coords, int32_t nblocks,
+                     const int32_t* block_ptr, hm_sys_t* out);
 
 /* Number of tree nodes and unknowns (either pointer may be NULL).                     */
 int hm_get_sizes(hm_sys_t sys, int32_t* n, int32_t* nfronts);

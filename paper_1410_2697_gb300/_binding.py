@@ -29,7 +29,7 @@ HM_PREC_FP64 = 0
 HM_PREC_MIXED = 1
 HM_PREC_MIXED_BF16 = 2
 
-EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_get_sizes",
+EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_analyze_batch", "hm_get_sizes",
             "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_solve", "hm_precond_apply",
             "hm_precond_apply_noalloc",
             "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error"]
@@ -76,6 +76,7 @@ def _load():
     lib.hm_create.argtypes = [C.POINTER(vp), C.POINTER(HmOpts)]
     lib.hm_ctx_destroy.argtypes = [vp]
     lib.hm_analyze.argtypes = [vp, i32, vp, vp, i32, vp, vp, i32, vp, vp, C.POINTER(vp)]
+    lib.hm_analyze_batch.argtypes = [vp, i32, vp, vp, i32, vp, i32, vp, C.POINTER(vp)]
     lib.hm_get_sizes.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     lib.hm_get_ordering.argtypes = [vp, vp, vp, vp, vp]
     lib.hm_get_symbolic.argtypes = [vp, vp, vp, vp, vp]
@@ -155,6 +156,19 @@ def hm_analyze(ctx, n, rowptr, colidx, dim=0, grid_coords=None, perm_in=None, nf
                            _ptr(grid_coords, np.int32, "grid_coords"), _ptr(perm_in, np.int32, "perm_in"),
                            int(nfronts_in), _ptr(first_in, np.int32, "first_in"),
                            _ptr(parent_in, np.int32, "parent_in"), C.byref(sys_)), "hm_analyze")
+    return sys_
+
+
+def hm_analyze_batch(ctx, n, rowptr, colidx, dim, grid_coords, block_ptr) -> C.c_void_p:
+    """Independent meshes (block-diagonal A): block b owns unknowns
+    [block_ptr[b], block_ptr[b+1]); GMRES then converges per block and RHS."""
+    sys_ = C.c_void_p()
+    nblocks = len(block_ptr) - 1
+    _check(_lib.hm_analyze_batch(ctx, int(n), _ptr(rowptr, np.int64, "rowptr", n + 1),
+                                 _ptr(colidx, np.int32, "colidx"), int(dim),
+                                 _ptr(grid_coords, np.int32, "grid_coords"), int(nblocks),
+                                 _ptr(block_ptr, np.int32, "block_ptr", nblocks + 1), C.byref(sys_)),
+           "hm_analyze_batch")
     return sys_
 
 

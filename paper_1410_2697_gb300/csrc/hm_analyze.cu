@@ -8,26 +8,54 @@
 
 namespace hm {
 
+// One independent block (mesh) of a batched analysis: its lattice box and where its
+// unknowns, its tree scratch and its nodes in the forest start.  A single system is one
+// block.
+struct NdBlock {
+  int lo0[3], ext[3];
+  int unk_off, n;         // unknowns [unk_off, unk_off + n)
+  int node_off, cap;      // tree scratch nodes [node_off, node_off + cap)
+  int forest_off, nodes;  // the block's nodes in the forest (set after the tree kernel)
+};
+
 // ------------------------------------------------------------------------------------
 // Validation of the CSR pattern: monotone row pointers, columns in range, strictly
 // increasing within a row.
 // ------------------------------------------------------------------------------------
-__global__ void k_csr_check(const int64_t* rowptr, const int32_t* colidx, int n, int* err) {
+// Block of unknown i: largest b with bp[b] <= i.
+__device__ __forceinline__ int block_of(const int32_t* __restrict__ bp, int nblocks, int i) {
+  int lo = 0, hi = nblocks;
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (bp[m] <= i) lo = m; else hi = m;
+  }
+  return lo;
+}
+
+// Sorted, in-range column indices; with blocks, every coupling stays inside its block.
+__global__ void k_csr_check(const int64_t* rowptr, const int32_t* colidx, int n, const int32_t* bp,
+                            int nblocks, int* err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int blk = block_of(bp, nblocks, i);
+  const int lo = bp[blk], hi = bp[blk + 1];
   const int64_t b = rowptr[i], e = rowptr[i + 1];
   if (e < b) { raise_error(err, HM_ERR_INVALID_ARG, 1, i); return; }
   int prev = -1;
   for (int64_t k = b; k < e; ++k) {
     const int c = colidx[k];
     if (c < 0 || c >= n || c <= prev) { raise_error(err, HM_ERR_INVALID_ARG, 2, i); return; }
+    if (c < lo || c >= hi) { raise_error(err, HM_ERR_INVALID_ARG, 6, i); return; }
     prev = c;
   }
 }
 
-__global__ void k_bbox(const int32_t* coords, int n, int dim, int* bb) {
+// Bounding box of every block: CTA (b, c) reduces chunk c of block b's unknowns.
+__global__ void k_bbox(const int32_t* coords, int dim, const int32_t* bp, int chunk, int* bb) {
+  const int blk = blockIdx.x;
+  const int i0 = bp[blk] + blockIdx.y * chunk, i1 = min(bp[blk + 1], i0 + chunk);
   int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
     for (int d = 0; d < dim; ++d) {
       const int v = coords[(size_t)i * dim + d];
       lo[d] = min(lo[d], v);
@@ -37,21 +65,22 @@ __global__ void k_bbox(const int32_t* coords, int n, int dim, int* bb) {
     lo[d] = -warp_max(-lo[d]);
     hi[d] = warp_max(hi[d]);
     if ((threadIdx.x & 31) == 0) {
-      atomicMin(&bb[d], lo[d]);
-      atomicMax(&bb[3 + d], hi[d]);
+      atomicMin(&bb[6 * blk + d], lo[d]);
+      atomicMax(&bb[6 * blk + 3 + d], hi[d]);
     }
   }
 }
 
-// Every lattice point of the bounding box must hold exactly one unknown.
-__global__ void k_lattice_mark(const int32_t* coords, int n, int dim, int3 lo, int3 ext,
-                               unsigned* bitmap, int* err) {
+// Every lattice point of a block's bounding box must hold exactly one of its unknowns.
+__global__ void k_lattice_mark(const int32_t* coords, int n, int dim, const int32_t* bp, int nblocks,
+                               const NdBlock* blks, unsigned* bitmap, int* err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int x = coords[(size_t)i * dim] - lo.x;
-  const int y = dim > 1 ? coords[(size_t)i * dim + 1] - lo.y : 0;
-  const int z = dim > 2 ? coords[(size_t)i * dim + 2] - lo.z : 0;
-  const int64_t lin = (int64_t)x + (int64_t)ext.x * ((int64_t)y + (int64_t)ext.y * z);
+  const NdBlock bk = blks[block_of(bp, nblocks, i)];
+  const int x = coords[(size_t)i * dim] - bk.lo0[0];
+  const int y = dim > 1 ? coords[(size_t)i * dim + 1] - bk.lo0[1] : 0;
+  const int z = dim > 2 ? coords[(size_t)i * dim + 2] - bk.lo0[2] : 0;
+  const int64_t lin = bk.unk_off + (int64_t)x + (int64_t)bk.ext[0] * ((int64_t)y + (int64_t)bk.ext[1] * z);
   const unsigned bit = 1u << (lin & 31);
   if (atomicOr(&bitmap[lin >> 5], bit) & bit) raise_error(err, HM_ERR_INVALID_ARG, 3, i);
 }
@@ -79,6 +108,17 @@ struct NdTree {
   int* lvl_ptr; // BFS level boundaries (<= 64 levels)
   int* count;   // [0] nodes, [1] levels
 };
+
+// Block b's part of the tree scratch (nodes are numbered within the block).
+constexpr int kNdLvlPtr = 70;  // per-block BFS level slots
+__host__ __device__ inline NdTree nd_shift(NdTree t, int off, int b) {
+  t.lo += 3 * (size_t)off; t.hi += 3 * (size_t)off;
+  t.axis += off; t.mid += off; t.left += off; t.right += off; t.par += off; t.depth += off;
+  t.sub += off; t.post += off; t.own += off; t.pts += off;
+  t.lvl_ptr += kNdLvlPtr * (size_t)b;
+  t.count += 2 * (size_t)b;
+  return t;
+}
 
 __device__ __forceinline__ int64_t box_count(const int* lo, const int* hi, int dim) {
   int64_t c = 1;
@@ -113,8 +153,16 @@ __device__ int block_excl_scan(int v, int* total, int* sh) {
   return before + x - v;
 }
 
-__global__ void __launch_bounds__(1024) k_nd_tree(NdTree t, int dim, int3 ext, int leaf, int cap,
+// One CTA per block; outputs (block-local postorder) at the block's node offset.
+__global__ void __launch_bounds__(1024) k_nd_tree(NdTree t0, const NdBlock* blks, int dim, int leaf,
                                                   int* first, int* parent, int* level, int* err) {
+  const NdBlock bk = blks[blockIdx.x];
+  const NdTree t = nd_shift(t0, bk.node_off, blockIdx.x);
+  const int3 ext = make_int3(bk.ext[0], bk.ext[1], bk.ext[2]);
+  const int cap = bk.cap;
+  first += bk.node_off;
+  parent += bk.node_off;
+  level += bk.node_off;
   __shared__ int sh[40];
   __shared__ int s_nodes, s_lb, s_le, s_nlev;
   if (threadIdx.x == 0) {
@@ -228,14 +276,17 @@ __global__ void __launch_bounds__(1024) k_nd_tree(NdTree t, int dim, int3 ext, i
 }
 
 // New index of every unknown: descend the box tree to the node that owns it.
-__global__ void k_nd_perm(const int32_t* coords, int n, int dim, int3 lo0, NdTree t,
-                          int32_t* perm, int32_t* iperm) {
+__global__ void k_nd_perm(const int32_t* coords, int n, int dim, NdTree t0, const int32_t* bp,
+                          int nblocks, const NdBlock* blks, int32_t* perm, int32_t* iperm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int blk = block_of(bp, nblocks, i);
+  const NdBlock bk = blks[blk];
+  const NdTree t = nd_shift(t0, bk.node_off, blk);
   int c[3] = {0, 0, 0};
-  c[0] = coords[(size_t)i * dim] - lo0.x;
-  if (dim > 1) c[1] = coords[(size_t)i * dim + 1] - lo0.y;
-  if (dim > 2) c[2] = coords[(size_t)i * dim + 2] - lo0.z;
+  c[0] = coords[(size_t)i * dim] - bk.lo0[0];
+  if (dim > 1) c[1] = coords[(size_t)i * dim + 1] - bk.lo0[1];
+  if (dim > 2) c[2] = coords[(size_t)i * dim + 2] - bk.lo0[2];
   int v = 0;
   for (int guard = 0; guard < 64; ++guard) {
     const int ax = t.axis[v];
@@ -251,10 +302,23 @@ __global__ void k_nd_perm(const int32_t* coords, int n, int dim, int3 lo0, NdTre
     }
     const int e0 = bhi[0] - blo[0] + 1, e1 = bhi[1] - blo[1] + 1;
     const int rank = (c[0] - blo[0]) + e0 * ((c[1] - blo[1]) + e1 * (c[2] - blo[2]));
-    const int nw = t.own[v] + rank;
+    const int nw = bk.unk_off + t.own[v] + rank;
     perm[nw] = i;
     iperm[i] = nw;
     return;
+  }
+}
+
+// The blocks' trees side by side: a forest in postorder (each tree's root last in its
+// range, parent -1), first indices shifted by the block's unknown offset.
+__global__ void k_nd_forest(const NdBlock* blks, const int* first_t, const int* parent_t, const int* level_t,
+                            int32_t* first, int32_t* parent, int32_t* level) {
+  const NdBlock bk = blks[blockIdx.x];
+  for (int q = threadIdx.x; q < bk.nodes; q += blockDim.x) {
+    const int src = bk.node_off + q, dst = bk.forest_off + q;
+    first[dst] = bk.unk_off + first_t[src];
+    parent[dst] = parent_t[src] >= 0 ? bk.forest_off + parent_t[src] : -1;
+    level[dst] = level_t[src];
   }
 }
 
@@ -541,7 +605,8 @@ static int tmp_alloc(hm_sys_s* sys, std::vector<void*>* tmp, void** p, size_t by
 
 int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, int dim,
                  const int32_t* coords, const int32_t* perm_in, int nfronts_in,
-                 const int32_t* first_in, const int32_t* parent_in) {
+                 const int32_t* first_in, const int32_t* parent_in, int nblocks,
+                 const int32_t* block_ptr) {
   cudaStream_t s = sys->ctx->stream;
   const int n = sys->n;
   std::vector<void*> tmp;
@@ -564,7 +629,29 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   HM_TRY(dev_alloc(sys, (void**)&sys->d_colidx, sizeof(int32_t) * sys->nnz));
   HM_CUDA(cudaMemcpyAsync(sys->d_rowptr, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, s));
   HM_CUDA(cudaMemcpyAsync(sys->d_colidx, colidx, sizeof(int32_t) * sys->nnz, cudaMemcpyDefault, s));
-  k_csr_check<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_colidx, n, sys->d_err);
+  // independent blocks (one when no batch is given); GMRES runs per block and RHS
+  if (nblocks < 1 || (nblocks > 1 && block_ptr == nullptr)) {
+    set_last_error("nblocks >= 1 and block_ptr[nblocks + 1] required");
+    return HM_ERR_INVALID_ARG;
+  }
+  sys->h_seg_ptr.assign(nblocks + 1, 0);
+  if (block_ptr) HM_TRY(copy_in(sys, sys->h_seg_ptr.data(), block_ptr, sizeof(int32_t) * (nblocks + 1)));
+  else sys->h_seg_ptr[1] = n;
+  if (sys->h_seg_ptr[0] != 0 || sys->h_seg_ptr[nblocks] != n) {
+    set_last_error("block_ptr[0] must be 0 and block_ptr[nblocks] = n");
+    return HM_ERR_INVALID_ARG;
+  }
+  for (int b = 0; b < nblocks; ++b)
+    if (sys->h_seg_ptr[b + 1] <= sys->h_seg_ptr[b]) {
+      set_last_error("every block needs at least one unknown");
+      return HM_ERR_INVALID_ARG;
+    }
+  sys->nseg = nblocks;
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_seg_ptr, sizeof(int32_t) * (nblocks + 1)));
+  HM_CUDA(cudaMemcpyAsync(sys->d_seg_ptr, sys->h_seg_ptr.data(), sizeof(int32_t) * (nblocks + 1),
+                          cudaMemcpyHostToDevice, s));
+  k_csr_check<<<(n + 255) / 256, 256, 0, s>>>(sys->d_rowptr, sys->d_colidx, n, sys->d_seg_ptr, nblocks,
+                                              sys->d_err);
   HM_TRY(check_device_error(sys, "analyze: CSR check"));
   host_mark("analyze: CSR check");
 
@@ -580,68 +667,108 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
       return HM_ERR_INVALID_ARG;
     }
     sys->dim = dim;
+    const auto& bp = sys->h_seg_ptr;
     int32_t* d_coords = nullptr;
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_coords, sizeof(int32_t) * (size_t)n * dim));
     HM_CUDA(cudaMemcpyAsync(d_coords, coords, sizeof(int32_t) * (size_t)n * dim, cudaMemcpyDefault, s));
+    // bounding box of every block
     int* d_bb = nullptr;
-    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_bb, 6 * sizeof(int)));
-    int hbb[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-    HM_CUDA(cudaMemcpyAsync(d_bb, hbb, sizeof(hbb), cudaMemcpyHostToDevice, s));
-    k_bbox<<<std::min((n + 255) / 256, 1024), 256, 0, s>>>(d_coords, n, dim, d_bb);
-    HM_CUDA(cudaMemcpyAsync(hbb, d_bb, sizeof(hbb), cudaMemcpyDeviceToHost, s));
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_bb, 6 * sizeof(int) * (size_t)nblocks));
+    std::vector<int> hbb(6 * (size_t)nblocks);
+    for (int b = 0; b < nblocks; ++b)
+      for (int d = 0; d < 3; ++d) { hbb[6 * b + d] = INT_MAX; hbb[6 * b + 3 + d] = INT_MIN; }
+    HM_CUDA(cudaMemcpyAsync(d_bb, hbb.data(), hbb.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    int maxblk = 0;
+    for (int b = 0; b < nblocks; ++b) maxblk = std::max(maxblk, bp[b + 1] - bp[b]);
+    const int chunk = 256 * 16;
+    k_bbox<<<dim3(nblocks, (maxblk + chunk - 1) / chunk), 256, 0, s>>>(d_coords, dim, sys->d_seg_ptr, chunk, d_bb);
+    HM_CUDA(cudaMemcpyAsync(hbb.data(), d_bb, hbb.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
-    int ext[3] = {1, 1, 1};
-    int64_t cnt = 1;
-    for (int d = 0; d < dim; ++d) { ext[d] = hbb[3 + d] - hbb[d] + 1; cnt *= ext[d]; }
-    if (cnt != n) { set_last_error("grid_coords must fill their bounding box exactly"); return HM_ERR_INVALID_ARG; }
-    const int3 lo0 = make_int3(hbb[0], dim > 1 ? hbb[1] : 0, dim > 2 ? hbb[2] : 0);
-    const int3 e3 = make_int3(ext[0], ext[1], ext[2]);
-    k_lattice_mark<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, lo0, e3, bitmap, sys->d_err);
+    std::vector<NdBlock> blks(nblocks);
+    int node_total = 0;
+    for (int b = 0; b < nblocks; ++b) {
+      NdBlock& bk = blks[b];
+      int64_t cnt = 1;
+      for (int d = 0; d < 3; ++d) {
+        bk.lo0[d] = d < dim ? hbb[6 * b + d] : 0;
+        bk.ext[d] = d < dim ? hbb[6 * b + 3 + d] - hbb[6 * b + d] + 1 : 1;
+        cnt *= bk.ext[d];
+      }
+      bk.unk_off = bp[b];
+      bk.n = bp[b + 1] - bp[b];
+      if (cnt != bk.n) {
+        set_last_error("grid_coords of every block must fill their bounding box exactly");
+        return HM_ERR_INVALID_ARG;
+      }
+      bk.node_off = node_total;
+      bk.cap = bk.n + 1;
+      node_total += bk.cap;
+      bk.forest_off = 0;
+      bk.nodes = 0;
+    }
+    NdBlock* d_blks = nullptr;
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_blks, sizeof(NdBlock) * (size_t)nblocks));
+    HM_CUDA(cudaMemcpyAsync(d_blks, blks.data(), sizeof(NdBlock) * (size_t)nblocks, cudaMemcpyHostToDevice, s));
+    k_lattice_mark<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, sys->d_seg_ptr, nblocks, d_blks, bitmap,
+                                                   sys->d_err);
     HM_TRY(check_device_error(sys, "analyze: lattice check"));
-  host_mark("analyze: bbox + lattice");
-    // tree
-    const int cap = n + 1;
+    host_mark("analyze: bbox + lattice");
+    // trees, one CTA per block
     NdTree t;
     int* tree = nullptr;
-    HM_TRY(tmp_alloc(sys, &tmp, (void**)&tree, sizeof(int) * ((size_t)cap * 16 + 80)));
+    const size_t cap = (size_t)node_total;
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&tree,
+                     sizeof(int) * (cap * 16 + (size_t)(kNdLvlPtr + 2) * nblocks + 8)));
     t.lo = tree;
-    t.hi = tree + 3 * (size_t)cap;
-    t.axis = tree + 6 * (size_t)cap;
-    t.mid = tree + 7 * (size_t)cap;
-    t.left = tree + 8 * (size_t)cap;
-    t.right = tree + 9 * (size_t)cap;
-    t.par = tree + 10 * (size_t)cap;
-    t.depth = tree + 11 * (size_t)cap;
-    t.sub = tree + 12 * (size_t)cap;
-    t.post = tree + 13 * (size_t)cap;
-    t.own = tree + 14 * (size_t)cap;
-    t.pts = tree + 15 * (size_t)cap;
-    t.lvl_ptr = tree + 16 * (size_t)cap;
-    t.count = tree + 16 * (size_t)cap + 70;
+    t.hi = tree + 3 * cap;
+    t.axis = tree + 6 * cap;
+    t.mid = tree + 7 * cap;
+    t.left = tree + 8 * cap;
+    t.right = tree + 9 * cap;
+    t.par = tree + 10 * cap;
+    t.depth = tree + 11 * cap;
+    t.sub = tree + 12 * cap;
+    t.post = tree + 13 * cap;
+    t.own = tree + 14 * cap;
+    t.pts = tree + 15 * cap;
+    t.lvl_ptr = tree + 16 * cap;
+    t.count = tree + 16 * cap + (size_t)kNdLvlPtr * nblocks;
     int *d_first_t = nullptr, *d_parent_t = nullptr, *d_level_t = nullptr;
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_first_t, sizeof(int) * (cap + 1)));
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_parent_t, sizeof(int) * cap));
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_level_t, sizeof(int) * cap));
     {
       ProfScope ps(sys->ctx, PC_ND, Work{0.0, 64.0 * cap});
-      k_nd_tree<<<1, 1024, 0, s>>>(t, dim, e3, sys->ctx->opts.nd_leaf, cap, d_first_t, d_parent_t,
-                                   d_level_t, sys->d_err);
+      k_nd_tree<<<nblocks, 1024, 0, s>>>(t, d_blks, dim, sys->ctx->opts.nd_leaf, d_first_t, d_parent_t,
+                                         d_level_t, sys->d_err);
     }
-    int cnts[2];
-    HM_CUDA(cudaMemcpyAsync(cnts, t.count, sizeof(cnts), cudaMemcpyDeviceToHost, s));
+    std::vector<int> cnts(2 * (size_t)nblocks);
+    HM_CUDA(cudaMemcpyAsync(cnts.data(), t.count, sizeof(int) * cnts.size(), cudaMemcpyDeviceToHost, s));
     HM_TRY(check_device_error(sys, "analyze: nested dissection"));
-  host_mark("analyze: nd tree");
-    nf = cnts[0];
+    host_mark("analyze: nd tree");
+    for (int b = 0; b < nblocks; ++b) {
+      blks[b].forest_off = nf;
+      blks[b].nodes = cnts[2 * b];
+      nf += cnts[2 * b];
+    }
+    HM_CUDA(cudaMemcpyAsync(d_blks, blks.data(), sizeof(NdBlock) * (size_t)nblocks, cudaMemcpyHostToDevice, s));
+    int32_t *d_first_f = nullptr, *d_parent_f = nullptr, *d_level_f = nullptr;
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_first_f, sizeof(int32_t) * (nf + 1)));
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_parent_f, sizeof(int32_t) * nf));
+    HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_level_f, sizeof(int32_t) * nf));
     {
-      ProfScope ps(sys->ctx, PC_ND, Work{0.0, (4.0 * dim + 8.0) * n});
-      k_nd_perm<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, lo0, t, sys->d_perm, sys->d_iperm);
+      ProfScope ps(sys->ctx, PC_ND, Work{0.0, (4.0 * dim + 8.0) * n + 24.0 * nf}, 2);
+      k_nd_forest<<<nblocks, 256, 0, s>>>(d_blks, d_first_t, d_parent_t, d_level_t, d_first_f, d_parent_f,
+                                          d_level_f);
+      k_nd_perm<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, t, sys->d_seg_ptr, nblocks, d_blks,
+                                                sys->d_perm, sys->d_iperm);
     }
     sys->h_first.resize(nf + 1);
     sys->h_parent.resize(nf);
     sys->h_level.resize(nf);
-    HM_CUDA(cudaMemcpyAsync(sys->h_first.data(), d_first_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaMemcpyAsync(sys->h_parent.data(), d_parent_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaMemcpyAsync(sys->h_level.data(), d_level_t, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(sys->h_first.data(), d_first_f, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(sys->h_parent.data(), d_parent_f, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(sys->h_level.data(), d_level_f, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
     HM_TRY(check_device_error(sys, "analyze: permutation"));
     host_mark("analyze: permutation");
     sys->h_first[nf] = n;
@@ -662,13 +789,14 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     for (int q = 0; q < nf; ++q) {
       if (sys->h_first[q + 1] <= sys->h_first[q]) { set_last_error("every tree node needs >= 1 unknown"); return HM_ERR_INVALID_ARG; }
       const int p = sys->h_parent[q];
-      if ((q == nf - 1) != (p < 0) || (p >= 0 && (p <= q || p >= nf))) {
-        set_last_error("parent[] must be a postorder tree with the root last");
+      if ((q == nf - 1 && p >= 0) || (p >= 0 && (p <= q || p >= nf))) {
+        set_last_error("parent[] must list children before parents (postorder; roots have -1)");
         return HM_ERR_INVALID_ARG;
       }
     }
     sys->h_level.assign(nf, 0);
-    for (int q = nf - 2; q >= 0; --q) sys->h_level[q] = sys->h_level[sys->h_parent[q]] + 1;
+    for (int q = nf - 1; q >= 0; --q)
+      sys->h_level[q] = sys->h_parent[q] < 0 ? 0 : sys->h_level[sys->h_parent[q]] + 1;
   }
   sys->nf = nf;
   HM_TRY(dev_alloc(sys, (void**)&sys->d_first, sizeof(int32_t) * (nf + 1)));

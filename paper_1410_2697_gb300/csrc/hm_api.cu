@@ -315,7 +315,29 @@ int hm_analyze(hm_ctx_t ctx, int32_t n, const int64_t* rowptr, const int32_t* co
   sys->ctx = ctx;
   sys->n = n;
   sys->precision = ctx->opts.precision;
-  int st = analyze_impl(sys, rowptr, colidx, dim, grid_coords, perm_in, nfronts_in, first_in, parent_in);
+  int st = analyze_impl(sys, rowptr, colidx, dim, grid_coords, perm_in, nfronts_in, first_in, parent_in, 1,
+                        nullptr);
+  if (st != HM_OK) {
+    destroy_sys(sys);
+    return st;
+  }
+  *out = sys;
+  return HM_OK;
+}
+
+int hm_analyze_batch(hm_ctx_t ctx, int32_t n, const int64_t* rowptr, const int32_t* colidx, int32_t dim,
+                     const int32_t* grid_coords, int32_t nblocks, const int32_t* block_ptr, hm_sys_t* out) {
+  if (!ctx || !out || n <= 0 || !rowptr || !colidx || !grid_coords || nblocks < 1 || !block_ptr) {
+    set_last_error("hm_analyze_batch: null argument, n <= 0 or nblocks < 1");
+    return HM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  cudaSetDevice(ctx->opts.device);
+  hm_sys_s* sys = new hm_sys_s();
+  sys->ctx = ctx;
+  sys->n = n;
+  sys->precision = ctx->opts.precision;
+  int st = analyze_impl(sys, rowptr, colidx, dim, grid_coords, nullptr, 0, nullptr, nullptr, nblocks, block_ptr);
   if (st != HM_OK) {
     destroy_sys(sys);
     return st;

@@ -53,82 +53,91 @@ __global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rowptr
 
 static dim3 spmv_grid(int n, int nrhs) { return dim3((n + 255) / 256, (nrhs + kSpmvR - 1) / kSpmvR); }
 
-// part[(r*nblk + blk)*stride + i] = sum over the block's rows of V_i[r] . w[r], i < nvec.
+// Row chunks: every vector kernel runs on grid (nchunks, nrhs); chunk c covers rows
+// [crow[c], crow[c+1]) of one block cseg[c] (chunks never straddle blocks), so a CTA
+// serves one GMRES instance inst = r * nseg + cseg[c] and caches its scalars.
+
+// part[(r*nchunks + c)*stride + i] = sum over chunk c of V_i[r] . w[r], i < nvec.
 // V_i[r] starts at V + (i*nrhs + r)*n.
 __global__ void __launch_bounds__(kDotThreads) k_multidot(const double* __restrict__ V,
                                                           const double* __restrict__ w, int n,
                                                           int nrhs, int nvec, int stride,
+                                                          const int* __restrict__ crow,
                                                           double* __restrict__ part) {
   __shared__ double red[32];
-  const int r = blockIdx.y, nblk = gridDim.x, blk = blockIdx.x;
-  const int64_t chunk = ((int64_t)n + nblk - 1) / nblk;
-  const int64_t b = blk * chunk, e = std::min<int64_t>((int64_t)n, b + chunk);
+  const int r = blockIdx.y, nchunks = gridDim.x, c = blockIdx.x;
+  const int b = crow[c], e = crow[c + 1];
   const double* wr = w + (int64_t)r * n;
   for (int i = 0; i < nvec; ++i) {
     const double* vi = V + ((int64_t)i * nrhs + r) * n;
     double s = 0.0;
-    for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) s = fma(vi[k], wr[k], s);
+    for (int k = b + threadIdx.x; k < e; k += blockDim.x) s = fma(vi[k], wr[k], s);
     s = block_sum(s, red);
-    if (threadIdx.x == 0) part[((int64_t)r * nblk + blk) * stride + i] = s;
+    if (threadIdx.x == 0) part[((int64_t)r * nchunks + c) * stride + i] = s;
   }
 }
 
-// h[r*stride + i] (=|+=) sum_blk part[...]  (fixed block order)
-__global__ void k_reduce_dots(const double* __restrict__ part, int nblk, int nrhs, int nvec,
-                              int stride, double* __restrict__ h, int accumulate) {
+// h[inst*stride + i] (=|+=) sum of the block's chunk partials (fixed chunk order)
+__global__ void k_reduce_dots(const double* __restrict__ part, int nchunks, const int* __restrict__ cptr,
+                              int nseg, int ninst, int nvec, int stride, double* __restrict__ h,
+                              int accumulate) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nrhs * nvec) return;
-  const int r = e / nvec, i = e % nvec;
+  if (e >= ninst * nvec) return;
+  const int inst = e / nvec, i = e % nvec;
+  const int r = inst / nseg, sg = inst % nseg;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[((int64_t)r * nblk + b) * stride + i];
-  if (accumulate) h[(int64_t)r * stride + i] += s;
-  else h[(int64_t)r * stride + i] = s;
+  for (int c = cptr[sg]; c < cptr[sg + 1]; ++c) s += part[((int64_t)r * nchunks + c) * stride + i];
+  if (accumulate) h[(int64_t)inst * stride + i] += s;
+  else h[(int64_t)inst * stride + i] = s;
 }
 
-// a[r*stride + i] += b[r*stride + i], i < nvec
-__global__ void k_add_cols(double* __restrict__ a, const double* __restrict__ b, int nrhs, int nvec,
+// a[inst*stride + i] += b[inst*stride + i], i < nvec
+__global__ void k_add_cols(double* __restrict__ a, const double* __restrict__ b, int ninst, int nvec,
                            int stride) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nrhs * nvec) return;
-  const int r = e / nvec, i = e % nvec;
-  a[(int64_t)r * stride + i] += b[(int64_t)r * stride + i];
+  if (e >= ninst * nvec) return;
+  const int inst = e / nvec, i = e % nvec;
+  a[(int64_t)inst * stride + i] += b[(int64_t)inst * stride + i];
 }
 
-// w[r] -= sum_{i < nvec} V_i[r] * c[r*stride + i]   (grid.y = r)
+// w[r] -= sum_{i < nvec} V_i[r] * coef[inst*stride + i]
 __global__ void k_gs_update(const double* __restrict__ V, double* __restrict__ w, int n, int nrhs,
-                            int nvec, int stride, const double* __restrict__ c) {
+                            int nvec, int stride, const double* __restrict__ coef,
+                            const int* __restrict__ crow, const int* __restrict__ cseg, int nseg) {
   __shared__ double cs[256];  // nvec <= restart + 1 <= 201
-  const int r = blockIdx.y;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = c[(int64_t)r * stride + i];
+  const int r = blockIdx.y, c = blockIdx.x;
+  const int inst = r * nseg + cseg[c];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = coef[(int64_t)inst * stride + i];
   __syncthreads();
   double* wr = w + (int64_t)r * n;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+  for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) {
     double s = wr[k];
     for (int i = 0; i < nvec; ++i) s -= V[((int64_t)i * nrhs + r) * n + k] * cs[i];
     wr[k] = s;
   }
 }
 
-// dst[r] = src[r] / ||.||, nrm = sqrt(ss[r*stride]) (0 if the norm is 0)   (grid.y = r)
+// dst[r] = src[r] / ||.||, with ||.||^2 = ss[inst*stride] (0 if the norm is 0)
 __global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, int n, int nrhs,
-                        const double* __restrict__ ss, int stride) {
-  const int r = blockIdx.y;
-  const double nr = sqrt(ss[(int64_t)r * stride]);
+                        const double* __restrict__ ss, int stride, const int* __restrict__ crow,
+                        const int* __restrict__ cseg, int nseg) {
+  const int r = blockIdx.y, c = blockIdx.x;
+  const int inst = r * nseg + cseg[c];
+  const double nr = sqrt(ss[(int64_t)inst * stride]);
   const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
   const double* sr = src + (int64_t)r * n;
   double* dr = dst + (int64_t)r * n;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    dr[k] = nr > 0.0 ? sr[k] * inv : 0.0;
+  for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) dr[k] = nr > 0.0 ? sr[k] * inv : 0.0;
 }
 
-// Givens step for column j (thread per RHS): H column = h (h1 + h2), H[j+1,j] = ||w||.
+// Givens step for column j (thread per instance): H column = h (h1 + h2), H[j+1,j] = ||w||.
 __global__ void k_givens(double* __restrict__ H, const double* __restrict__ hv, int hstride,
                          const double* __restrict__ ss, int ssstride, double* __restrict__ cs,
                          double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ bnorm,
-                         double* __restrict__ res, int* __restrict__ len, int j, int m, int nrhs,
+                         double* __restrict__ res, int* __restrict__ len, int j, int m, int ninst,
                          double rtol) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
+  if (r >= ninst) return;
   double* Hr = H + (int64_t)r * (m + 1) * m;
   double* col = Hr + (int64_t)j * (m + 1);
   for (int i = 0; i <= j; ++i) col[i] = hv[(int64_t)r * hstride + i];
@@ -158,11 +167,11 @@ __global__ void k_givens(double* __restrict__ H, const double* __restrict__ hv, 
   if (len[r] == 0 && est <= rtol) len[r] = j + 1;
 }
 
-// y = R^{-1} g over len[r] (thread per RHS); len[r] == 0 -> use jend.
+// y = R^{-1} g over len[inst] (thread per instance); len == 0 -> use jend.
 __global__ void k_backsolve(const double* __restrict__ H, const double* __restrict__ g,
-                            double* __restrict__ y, int* __restrict__ len, int jend, int m, int nrhs) {
+                            double* __restrict__ y, int* __restrict__ len, int jend, int m, int ninst) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
+  if (r >= ninst) return;
   int L = len[r];
   if (L == 0 || L > jend) L = jend;
   len[r] = L;
@@ -178,40 +187,43 @@ __global__ void k_backsolve(const double* __restrict__ H, const double* __restri
   for (int i = L; i < m; ++i) yr[i] = 0.0;
 }
 
-// x[r] += sum_{j < len[r]} Z_j[r] y[r][j]   (grid.y = r)
+// x[r] += sum_{j < len[inst]} Z_j[r] y[inst][j]
 template <typename ZT>
 __global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z, const double* __restrict__ y,
-                           const int* __restrict__ len, int n, int nrhs, int m) {
+                           const int* __restrict__ len, int n, int nrhs, int m, const int* __restrict__ crow,
+                           const int* __restrict__ cseg, int nseg) {
   __shared__ double ys[256];
-  const int r = blockIdx.y;
-  const int L = len[r];
-  for (int j = threadIdx.x; j < L; j += blockDim.x) ys[j] = y[(int64_t)r * m + j];
+  const int r = blockIdx.y, c = blockIdx.x;
+  const int inst = r * nseg + cseg[c];
+  const int L = len[inst];
+  for (int j = threadIdx.x; j < L; j += blockDim.x) ys[j] = y[(int64_t)inst * m + j];
   __syncthreads();
   double* xr = x + (int64_t)r * n;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+  for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) {
     double s = xr[k];
     for (int j = 0; j < L; ++j) s = fma((double)Z[((int64_t)j * nrhs + r) * n + k], ys[j], s);
     xr[k] = s;
   }
 }
 
-// Start of a cycle: V_0 = r / beta (inactive systems get 0)   (grid.y = r)
+// Start of a cycle: V_0 = r / beta (inactive instances get 0)
 __global__ void k_cycle_init(const double* __restrict__ rvec, double* __restrict__ V0, int n, int nrhs,
-                             const double* __restrict__ ss, const int* __restrict__ active) {
-  const int r = blockIdx.y;
-  const double beta = sqrt(ss[r]);
-  const bool on = active[r] && beta > 0.0;
+                             const double* __restrict__ ss, const int* __restrict__ active,
+                             const int* __restrict__ crow, const int* __restrict__ cseg, int nseg) {
+  const int r = blockIdx.y, c = blockIdx.x;
+  const int inst = r * nseg + cseg[c];
+  const double beta = sqrt(ss[inst]);
+  const bool on = active[inst] && beta > 0.0;
   const double inv = on ? 1.0 / beta : 0.0;
   const double* rr = rvec + (int64_t)r * n;
   double* vr = V0 + (int64_t)r * n;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    vr[k] = on ? rr[k] * inv : 0.0;
+  for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) vr[k] = on ? rr[k] * inv : 0.0;
 }
 
 __global__ void k_cycle_g(double* __restrict__ g, int* __restrict__ len, const double* __restrict__ ss,
-                          const int* __restrict__ active, int m, int nrhs) {
+                          const int* __restrict__ active, int m, int ninst) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
+  if (r >= ninst) return;
   double* gr = g + (int64_t)r * (m + 1);
   for (int i = 0; i <= m; ++i) gr[i] = 0.0;
   gr[0] = active[r] ? sqrt(ss[r]) : 0.0;
@@ -231,8 +243,22 @@ static int ensure_workspace(hm_sys_s* sys, int nrhs, int m) {
   dev_free_all(sys->ctx, &G.allocs);
   if (G.h_res) { cudaFreeHost(G.h_res); G.h_res = nullptr; }
   const int64_t n = sys->n;
+  const int nseg = sys->nseg;
+  const int64_t ninst = (int64_t)nrhs * nseg;
   const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
-  G.nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 4095) / 4096, 2 * sys->ctx->num_sms));
+  // row chunks: about two per SM over the whole vector, never straddling a block
+  const int64_t L = std::max<int64_t>(1024, (n + 2 * sys->ctx->num_sms - 1) / (2 * sys->ctx->num_sms));
+  std::vector<int> crow(1, 0), cseg, cptr(1, 0);
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int b = sys->h_seg_ptr[sg], e = sys->h_seg_ptr[sg + 1];
+    const int64_t nc = std::max<int64_t>(1, (e - b + L - 1) / L);
+    for (int64_t c = 0; c < nc; ++c) {
+      crow.push_back((int)(b + (e - b) * (c + 1) / nc));
+      cseg.push_back(sg);
+    }
+    cptr.push_back((int)cseg.size());
+  }
+  G.nchunks = (int)cseg.size();
   const int stride = m + 2;
   HM_TRY(gm_alloc(sys, (void**)&G.V, sizeof(double) * (m + 1) * nrhs * n));
   HM_TRY(gm_alloc(sys, &G.Z, (size_t)es * m * nrhs * n));
@@ -241,30 +267,40 @@ static int ensure_workspace(hm_sys_s* sys, int nrhs, int m) {
   HM_TRY(gm_alloc(sys, (void**)&G.b, sizeof(double) * nrhs * n));
   HM_TRY(gm_alloc(sys, (void**)&G.x, sizeof(double) * nrhs * n));
   HM_TRY(gm_alloc(sys, (void**)&G.r, sizeof(double) * nrhs * n));
-  HM_TRY(gm_alloc(sys, (void**)&G.H, sizeof(double) * nrhs * (m + 1) * m));
-  HM_TRY(gm_alloc(sys, (void**)&G.cs, sizeof(double) * nrhs * m));
-  HM_TRY(gm_alloc(sys, (void**)&G.sn, sizeof(double) * nrhs * m));
-  HM_TRY(gm_alloc(sys, (void**)&G.g, sizeof(double) * nrhs * (m + 1)));
-  HM_TRY(gm_alloc(sys, (void**)&G.y, sizeof(double) * nrhs * m));
-  HM_TRY(gm_alloc(sys, (void**)&G.bnorm, sizeof(double) * nrhs));
-  HM_TRY(gm_alloc(sys, (void**)&G.res, sizeof(double) * nrhs * 4));
-  HM_TRY(gm_alloc(sys, (void**)&G.part, sizeof(double) * (size_t)G.nblk * nrhs * stride));
-  HM_TRY(gm_alloc(sys, (void**)&G.hv, sizeof(double) * nrhs * stride * 3));
-  HM_TRY(gm_alloc(sys, (void**)&G.len, sizeof(int) * nrhs * 2));
-  HM_CUDA(cudaMallocHost((void**)&G.h_res, sizeof(double) * nrhs * 4 + sizeof(int) * nrhs * 2));
+  HM_TRY(gm_alloc(sys, (void**)&G.H, sizeof(double) * ninst * (m + 1) * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.cs, sizeof(double) * ninst * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.sn, sizeof(double) * ninst * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.g, sizeof(double) * ninst * (m + 1)));
+  HM_TRY(gm_alloc(sys, (void**)&G.y, sizeof(double) * ninst * m));
+  HM_TRY(gm_alloc(sys, (void**)&G.bnorm, sizeof(double) * ninst));
+  HM_TRY(gm_alloc(sys, (void**)&G.res, sizeof(double) * ninst * 4));
+  HM_TRY(gm_alloc(sys, (void**)&G.part, sizeof(double) * (size_t)G.nchunks * nrhs * stride));
+  HM_TRY(gm_alloc(sys, (void**)&G.hv, sizeof(double) * ninst * stride * 3));
+  HM_TRY(gm_alloc(sys, (void**)&G.len, sizeof(int) * ninst * 2));
+  HM_TRY(gm_alloc(sys, (void**)&G.crow, sizeof(int) * crow.size()));
+  HM_TRY(gm_alloc(sys, (void**)&G.cseg, sizeof(int) * cseg.size()));
+  HM_TRY(gm_alloc(sys, (void**)&G.cptr, sizeof(int) * cptr.size()));
+  cudaStream_t s = sys->ctx->stream;
+  HM_CUDA(cudaMemcpyAsync(G.crow, crow.data(), sizeof(int) * crow.size(), cudaMemcpyHostToDevice, s));
+  HM_CUDA(cudaMemcpyAsync(G.cseg, cseg.data(), sizeof(int) * cseg.size(), cudaMemcpyHostToDevice, s));
+  HM_CUDA(cudaMemcpyAsync(G.cptr, cptr.data(), sizeof(int) * cptr.size(), cudaMemcpyHostToDevice, s));
+  HM_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  HM_CUDA(cudaMallocHost((void**)&G.h_res, sizeof(double) * ninst * 4 + sizeof(int) * ninst * 2));
   G.nrhs = nrhs;
   G.m = m;
   return HM_OK;
 }
 
-// ss[r*stride] = ||v[r]||^2 (deterministic)
+// ss[inst*stride] = ||v restricted to the instance||^2 (deterministic)
 static void sqnorm(hm_sys_s* sys, const double* v, double* ss, int stride, int nrhs) {
   auto& G = sys->gm;
   cudaStream_t s = sys->ctx->stream;
+  const int ninst = nrhs * sys->nseg;
   ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * sys->n * nrhs, 8.0 * sys->n * nrhs}, 2);
-  k_multidot<<<dim3(G.nblk, nrhs), kDotThreads, 0, s>>>(v, v, sys->n, nrhs, 1, stride, G.part);
-  // note: with V = v and nvec = 1 the "basis" is v itself (stride of rhs = n)
-  k_reduce_dots<<<(nrhs + 127) / 128, 128, 0, s>>>(G.part, G.nblk, nrhs, 1, stride, ss, 0);
+  k_multidot<<<dim3(G.nchunks, nrhs), kDotThreads, 0, s>>>(v, v, sys->n, nrhs, 1, stride, G.crow, G.part);
+  // with V = v and nvec = 1 the "basis" is v itself (stride of rhs = n)
+  k_reduce_dots<<<(ninst + 127) / 128, 128, 0, s>>>(G.part, G.nchunks, G.cptr, sys->nseg, ninst, 1, stride,
+                                                    ss, 0);
 }
 
 template <typename T>
@@ -279,43 +315,41 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
   const int n = sys->n;
   const int64_t nn = (int64_t)n * nrhs;
   const int stride = m + 2;
-  // vector kernels: grid.y = right-hand side, grid.x covers n (about 8 waves in all)
-  const dim3 vgrid((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
-                                                                       (int64_t)152 * 8 / nrhs + 1)),
-                   (unsigned)nrhs);
+  const int nseg = sys->nseg, ninst = nrhs * nseg;  // instance = r * nseg + block
+  const dim3 vgrid((unsigned)G.nchunks, (unsigned)nrhs);
   {
     ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, 20.0 * nn});
     launch_permute_in(d_b, G.b, sys->d_perm, n, nrhs, s);
     HM_CUDA(cudaMemsetAsync(G.x, 0, sizeof(double) * nn, s));
   }
-  // ||b|| per RHS
-  double* bn2 = G.hv + 2 * nrhs * stride;  // scratch: squared norms (stride 1)
+  // ||b|| per instance
+  double* bn2 = G.hv + 2 * (int64_t)ninst * stride;  // scratch: squared norms (stride 1)
   sqnorm(sys, G.b, bn2, 1, nrhs);
-  std::vector<double> hb(nrhs);
-  HM_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  std::vector<double> hb(ninst);
+  HM_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
-  std::vector<double> bnorm(nrhs);
-  for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(hb[r]);
-  HM_CUDA(cudaMemcpyAsync(G.bnorm, bnorm.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+  std::vector<double> bnorm(ninst);
+  for (int r = 0; r < ninst; ++r) bnorm[r] = std::sqrt(hb[r]);
+  HM_CUDA(cudaMemcpyAsync(G.bnorm, bnorm.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, s));
   // r = b (x0 = 0)
   HM_CUDA(cudaMemcpyAsync(G.r, G.b, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  std::vector<double> relres(nrhs);
-  std::vector<int> active(nrhs);
-  for (int r = 0; r < nrhs; ++r) relres[r] = bnorm[r] > 0 ? 1.0 : 0.0;
+  std::vector<double> relres(ninst);
+  std::vector<int> active(ninst);
+  for (int r = 0; r < ninst; ++r) relres[r] = bnorm[r] > 0 ? 1.0 : 0.0;
   int iters = 0, cycles = 0;
-  int* d_active = G.len + nrhs;
-  double* rss = G.hv + 2 * nrhs * stride + nrhs;  // squared residual norms
-  HM_CUDA(cudaMemcpyAsync(rss, bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, s));
+  int* d_active = G.len + ninst;
+  double* rss = G.hv + 2 * (int64_t)ninst * stride + ninst;  // squared residual norms
+  HM_CUDA(cudaMemcpyAsync(rss, bn2, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, s));
   bool done = true;
-  for (int r = 0; r < nrhs; ++r) done = done && relres[r] <= rtol;
+  for (int r = 0; r < ninst; ++r) done = done && relres[r] <= rtol;
   T* Z = (T*)G.Z;
   while (!done && iters < max_iters) {
-    for (int r = 0; r < nrhs; ++r) active[r] = relres[r] > rtol ? 1 : 0;
-    HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    for (int r = 0; r < ninst; ++r) active[r] = relres[r] > rtol ? 1 : 0;
+    HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s));
     {
       ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn}, 2);
-      k_cycle_init<<<vgrid, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active);
-      k_cycle_g<<<(nrhs + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, nrhs);
+      k_cycle_init<<<vgrid, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active, G.crow, G.cseg, nseg);
+      k_cycle_g<<<(ninst + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, ninst);
     }
     int j = 0;
     for (; j < m && iters < max_iters; ++j) {
@@ -333,52 +367,55 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
                                                   Zj, n, G.w, n, nullptr, 0);
       }
       double* h1 = G.hv;
-      double* h2 = G.hv + nrhs * stride;
+      double* h2 = G.hv + (int64_t)ninst * stride;
       const int nvec = j + 1;
       for (int pass = 0; pass < 2; ++pass) {
         double* h = pass == 0 ? h1 : h2;
         {
           ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
-          k_multidot<<<dim3(G.nblk, nrhs), kDotThreads, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, G.part);
-          k_reduce_dots<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(G.part, G.nblk, nrhs, nvec, stride, h, 0);
+          k_multidot<<<dim3(G.nchunks, nrhs), kDotThreads, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, G.crow,
+                                                                   G.part);
+          k_reduce_dots<<<(ninst * nvec + 127) / 128, 128, 0, s>>>(G.part, G.nchunks, G.cptr, nseg, ninst, nvec,
+                                                                  stride, h, 0);
         }
         {
           ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
-          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h);
+          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h, G.crow, G.cseg, nseg);
         }
       }
       {
         ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
-        k_add_cols<<<(nrhs * nvec + 127) / 128, 128, 0, s>>>(h1, h2, nrhs, nvec, stride);  // h1 += h2
+        k_add_cols<<<(ninst * nvec + 127) / 128, 128, 0, s>>>(h1, h2, ninst, nvec, stride);  // h1 += h2
       }
-      double* wss = G.hv + 2 * nrhs * stride + 2 * nrhs;  // ||w||^2 per RHS (stride 1)
+      double* wss = G.hv + 2 * (int64_t)ninst * stride + 2 * ninst;  // ||w||^2 per instance
       sqnorm(sys, G.w, wss, 1, nrhs);
       {
         ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn});
-        k_scale<<<vgrid, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1);
+        k_scale<<<vgrid, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1, G.crow, G.cseg,
+                                      nseg);
       }
       {
         ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
-        k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, h1, stride, wss, 1, G.cs, G.sn, G.g, G.bnorm,
-                                                 G.res, G.len, j, m, nrhs, rtol);
+        k_givens<<<(ninst + 63) / 64, 64, 0, s>>>(G.H, h1, stride, wss, 1, G.cs, G.sn, G.g, G.bnorm,
+                                                  G.res, G.len, j, m, ninst, rtol);
       }
       ++iters;
-      HM_CUDA(cudaMemcpyAsync(G.h_res, G.res, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+      HM_CUDA(cudaMemcpyAsync(G.h_res, G.res, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
       HM_CUDA(cudaStreamSynchronize(s));
       host_mark("gmres: iteration");
       bool all = true;
-      for (int r = 0; r < nrhs; ++r)
+      for (int r = 0; r < ninst; ++r)
         if (active[r] && !(G.h_res[r] <= rtol)) all = false;
       if (all) { ++j; break; }
     }
     const int jend = std::min(j, m);
     {
       ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
-      k_backsolve<<<(nrhs + 63) / 64, 64, 0, s>>>(G.H, G.g, G.y, G.len, jend, m, nrhs);
+      k_backsolve<<<(ninst + 63) / 64, 64, 0, s>>>(G.H, G.g, G.y, G.len, jend, m, ninst);
     }
     {
       ProfScope ps(sys->ctx, PC_VECTOR, Work{2.0 * jend * nn, (16.0 + sizeof(T) * jend) * nn});
-      k_update_x<T><<<vgrid, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m);
+      k_update_x<T><<<vgrid, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m, G.crow, G.cseg, nseg);
     }
     {
       ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});
@@ -386,12 +423,12 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
                                                      G.x, n, G.r, n, G.b, n);
     }
     sqnorm(sys, G.r, rss, 1, nrhs);
-    std::vector<double> hr(nrhs);
-    HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    std::vector<double> hr(ninst);
+    HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     ++cycles;
     done = true;
-    for (int r = 0; r < nrhs; ++r) {
+    for (int r = 0; r < ninst; ++r) {
       relres[r] = bnorm[r] > 0 ? std::sqrt(hr[r]) / bnorm[r] : 0.0;
       if (!(relres[r] <= rtol)) done = false;
     }

@@ -334,6 +334,11 @@ struct hm_sys_s {
   int32_t* d_first = nullptr;
   int32_t* d_parent = nullptr;
   int32_t* d_node_of = nullptr;
+  // independent blocks (batched meshes): unknowns [seg_ptr[b], seg_ptr[b+1]) in both
+  // numberings; GMRES runs one instance per block and right-hand side
+  int nseg = 1;
+  std::vector<int32_t> h_seg_ptr;
+  int32_t* d_seg_ptr = nullptr;
   int32_t* d_child_ptr = nullptr;
   int32_t* d_child_list = nullptr;
   int64_t* d_prowptr = nullptr;
@@ -392,7 +397,8 @@ struct hm_sys_s {
     int* len = nullptr;
     double* h_res = nullptr;  // pinned
     std::vector<void*> allocs;
-    int nblk = 0;
+    int nchunks = 0;                          // row chunks (never straddling a block)
+    int *crow = nullptr, *cseg = nullptr, *cptr = nullptr;  // chunk rows, block, chunks per block
   } gm;
 };
 
@@ -430,7 +436,8 @@ int copy_in(hm_sys_s* sys, void* dst, const void* src, size_t bytes);
 
 int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, int dim,
                  const int32_t* coords, const int32_t* perm_in, int nfronts_in,
-                 const int32_t* first_in, const int32_t* parent_in);
+                 const int32_t* first_in, const int32_t* parent_in, int nblocks,
+                 const int32_t* block_ptr);
 int build_plan(hm_sys_s* sys);
 int factor_impl(hm_sys_s* sys, const double* d_values, double tol);
 int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out);
