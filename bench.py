@@ -14,8 +14,13 @@ copied back, every step.  The FP64-plain path (the same method entirely in FP64)
 measured beside the mixed-precision path (FP32 factor/apply, FP64 GMRES).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload NAME]
 Under torchrun each rank runs an independent replica on its own GPU (the method has no
 data-parallel exchange); the line reports the whole-job rate and max-over-ranks time.
+Other workloads (for the parity/coverage record, not the headline line):
+``hex_lognormal_64^3`` (3D trilinear hex, BF16 tensor-core range finder, 1 RHS),
+``p1_batch_256`` (256 independent jittered P1 meshes analysed as one forest, 1 RHS each),
+``q1_poisson_64x64`` (the small FP64 case).
 """
 from __future__ import annotations
 
@@ -44,7 +49,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "hex_lognormal_64^3", "p1_batch_256", "q1_poisson_64x64"])
+    ap.add_argument("--nrhs", type=int, default=None, help="default: the workload's")
     ap.add_argument("--m", type=int, default=1024, help="elements per side (1024 = the workload)")
     ap.add_argument("--n-c", type=int, default=64)
     ap.add_argument("--hodlr-leaf", type=int, default=64)
@@ -170,7 +177,7 @@ def alu_peak_tflops(precision: str, sm_max_mhz: float | None) -> float:
 
 
 COMPUTE_CATS = {"gemm_factor", "gemm_apply", "dense_potrf", "dense_trsm", "householder_qr",
-                "jacobi_svd", "core_lu_inverse", "spd_inverse", "leaf_solve"}
+                "jacobi_svd", "core_lu_inverse", "spd_inverse", "leaf_solve", "dense_sweep"}
 
 
 def ncu_traffic(category: str):
@@ -212,20 +219,63 @@ def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
             "peak_source": "measured" if peaks else "fallback"}
 
 
+class Workload:
+    """Problem, right-hand sides and solver settings of one benchmark workload."""
+
+    def __init__(self, args):
+        import numpy as np
+
+        from fixtures import lognormal_coefficients, p1_batch, q1_square, rhs_uniform, workload
+        self.name = args.workload
+        self.block_ptr = None
+        self.nd_leaf, self.hodlr_leaf, self.n_c, self.samples = 64, args.hodlr_leaf, args.n_c, args.samples
+        if self.name == WORKLOAD:
+            m = args.m
+            coef = lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=1)
+            self.P = q1_square(m, coef, name=f"q1_lognormal_{m}x{m}")
+            self.label = f"q1_lognormal_{m}x{m}" if m != 1024 else WORKLOAD
+            self.nrhs, self.tol, self.rhs_seed, self.headline = 16, 1e-4, 2, "MIXED"
+        elif self.name == "hex_lognormal_64^3":
+            self.P, prm = workload(self.name)
+            self.label = self.name
+            self.nrhs, self.tol, self.rhs_seed, self.headline = 1, prm["tol"], prm["rhs_seed"], "MIXED_BF16"
+        elif self.name == "p1_batch_256":
+            self.P, self.block_ptr, _ = p1_batch(256, 5)
+            self.label = self.name
+            self.nrhs, self.tol, self.rhs_seed, self.headline = 1, 1e-4, 6, "MIXED"
+        else:  # q1_poisson_64x64: the small FP64 case
+            self.P, prm = workload(self.name)
+            self.label = self.name
+            self.nrhs, self.tol, self.rhs_seed, self.headline = 1, prm["tol"], prm["rhs_seed"], "FP64"
+        if args.nrhs:
+            self.nrhs = args.nrhs
+        self.b = rhs_uniform(self.P.n, self.nrhs, self.rhs_seed)
+        self.dtype = {"MIXED": "f32 factor/apply + f64 GMRES", "FP64": "f64",
+                      "MIXED_BF16": "bf16 tensor-core range finder, f32 factor/apply + f64 GMRES"}[self.headline]
+
+    def relres(self, x):
+        """Worst relative residual over right-hand sides (and over meshes of a batch)."""
+        import numpy as np
+        A = self.P.scipy()
+        bp = self.block_ptr if self.block_ptr is not None else np.array([0, self.P.n])
+        worst = 0.0
+        for c in range(self.nrhs):
+            r = self.b[:, c] - A @ x[:, c]
+            for k in range(len(bp) - 1):
+                sl = slice(bp[k], bp[k + 1])
+                worst = max(worst, float(np.linalg.norm(r[sl]) / np.linalg.norm(self.b[sl, c])))
+        return worst
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
 
     import paper_1410_2697_gb300 as hm
-    from fixtures import lognormal_coefficients, q1_square, rhs_uniform
 
     torch.cuda.set_device(local)
-    m = args.m
-    coef = lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=1)
-    P = q1_square(m, coef, name=f"q1_lognormal_{m}x{m}")
-    nrhs = args.nrhs
-    b = rhs_uniform(P.n, nrhs, 2)
-    tol = 1e-4
+    W = Workload(args)
+    P, b, nrhs, tol = W.P, W.b, W.nrhs, W.tol
     dev = torch.device("cuda", local)
     d_rowptr = torch.from_numpy(P.rowptr).to(dev)
     d_colidx = torch.from_numpy(P.colidx).to(dev)
@@ -233,22 +283,26 @@ def run_ours(args, rank, world, local):
     d_coords = torch.from_numpy(np.ascontiguousarray(P.coords)).to(dev)
     d_b = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)  # (nrhs, n) = column-major n x nrhs
     d_x = torch.zeros_like(d_b)
+    bp = W.block_ptr
     stream = torch.cuda.Stream(device=dev)
 
     def make_ctx(precision):
         o = hm.hm_default_opts()
         o.device = local
         o.precision = precision
-        o.nd_leaf = 64
-        o.hodlr_leaf = args.hodlr_leaf
-        o.n_c = args.n_c
-        o.samples = args.samples
+        o.nd_leaf = W.nd_leaf
+        o.hodlr_leaf = W.hodlr_leaf
+        o.n_c = W.n_c
+        o.samples = W.samples
         o.restart = 30
         o.stream = stream.cuda_stream
         return hm.hm_create(o)
 
     def step(ctx, rowptr, colidx, coords, values, bb, xx):
-        s = hm.hm_analyze(ctx, P.n, rowptr, colidx, 2, coords)
+        if bp is None:
+            s = hm.hm_analyze(ctx, P.n, rowptr, colidx, P.dim, coords)
+        else:
+            s = hm.hm_analyze_batch(ctx, P.n, rowptr, colidx, P.dim, coords, bp)
         fi = hm.hm_factor(s, values, tol)
         si = hm.hm_solve(s, nrhs, bb, RTOL, MAX_ITERS, xx)
         hm.hm_destroy(s)
@@ -275,8 +329,8 @@ def run_ours(args, rank, world, local):
         return per, total, infos, prof
 
     dev_inputs = (d_rowptr, d_colidx, d_coords, d_values, d_b, d_x)
-    # ---------------- mixed precision, device-resident inputs (the headline)
-    ctx = make_ctx(hm.HM_PREC_MIXED)
+    # ---------------- the workload's headline precision, device-resident inputs
+    ctx = make_ctx(getattr(hm, "HM_PREC_" + W.headline))
     for _ in range(args.warmup):
         step(ctx, *dev_inputs)
     clocks = ClockSampler(local)
@@ -287,8 +341,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     total_max = allreduce_max(total, world)
     x = d_x.cpu().numpy().T
-    A = P.scipy()
-    relres = max(float(np.linalg.norm(b[:, c] - A @ x[:, c]) / np.linalg.norm(b[:, c])) for c in range(nrhs))
+    relres = W.relres(x)
 
     if args.profile_run:
         hm.hm_ctx_destroy(ctx)
@@ -319,10 +372,11 @@ def run_ours(args, rank, world, local):
     total64 = allreduce_max(total64, world)
     hm.hm_ctx_destroy(ctx64)
 
-    value = nrhs * args.steps * world / (total_max * 1e-3)
+    nsolve = nrhs * (len(bp) - 1 if bp is not None else 1)  # (mesh, rhs) pairs per step
+    value = nsolve * args.steps * world / (total_max * 1e-3)
     fi, si = infos[-1]
     peaks = load_peaks()
-    rl = roofline(prof, "f32", peaks, clk)
+    rl = roofline(prof, "f64" if W.headline == "FP64" else "f32", peaks, clk)
     kernels = sum(v["kernels"] for v in prof.values())  # per profiled pass of K steps
     per_sorted = sorted(per)
     p50 = statistics.median(per)
@@ -330,22 +384,22 @@ def run_ours(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 factor/apply + f64 GMRES",
+        "scaling": "weak", "vs_baseline": None, "dtype": W.dtype,
         "data": "synthetic",
-        "config": {"workload": f"q1_lognormal_{m}x{m}" if m != 1024 else WORKLOAD, "unknowns": P.n,
-                   "nnz": P.nnz, "nrhs": nrhs, "tol": tol, "rtol": RTOL, "restart": 30,
-                   "nd_leaf": 64, "hodlr_leaf": args.hodlr_leaf, "n_c": args.n_c,
-                   "samples": args.samples, "step": "analyze + factor + solve(nrhs) + destroy",
-                   "l2": "inputs larger than L2 (A: 139 MB CSR, fronts 1.4 GB)",
+        "config": {"workload": W.label, "unknowns": P.n, "nnz": P.nnz, "nrhs": nrhs,
+                   "meshes": len(bp) - 1 if bp is not None else 1, "tol": tol, "rtol": RTOL,
+                   "restart": 30, "nd_leaf": W.nd_leaf, "hodlr_leaf": W.hodlr_leaf, "n_c": W.n_c,
+                   "samples": W.samples, "step": "analyze + factor + solve(nrhs) + destroy",
+                   "l2": f"inputs larger than L2 (A: {(P.nnz * 12 + P.n * 8) / 1e6:.0f} MB CSR)",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": p50, "p99_ms": p99,
         "gmres_iters": si["iters"], "relres": relres,
         "factor": {"nfronts": fi["nfronts"], "n_hodlr": fi["n_hodlr"], "max_rank": fi["max_rank"],
                    "rank_capped": fi["rank_capped"], "factor_bytes": fi["factor_bytes"]},
-        "fp64_plain": {"value": nrhs * k64 * world / (total64 * 1e-3), "ms_per_step": total64 / k64,
+        "fp64_plain": {"value": nsolve * k64 * world / (total64 * 1e-3), "ms_per_step": total64 / k64,
                        "steps": k64, "gmres_iters": infos64[-1][1]["iters"]},
         "roofline": rl,
-        "e2e": {"value": nrhs * ke * world / (total_e * 1e-3), "unit": "solves/s",
+        "e2e": {"value": nsolve * ke * world / (total_e * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": ke},
         "gpu_launches": int(kernels),
         "clocks": clk,
@@ -359,27 +413,43 @@ def run_ours(args, rank, world, local):
 # ------------------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ------------------------------------------------------------------------------------
-def oracle_solve_once(m: int, rhs_cols: int):
-    """Time the oracle pipeline (ND, symbolic, HODLR-MF factor, GMRES per RHS) on the
-    q1 lognormal family with m x m elements.  Returns (seconds, solves, relres)."""
-    import numpy as np
-
-    from fixtures import lognormal_coefficients, q1_square, rhs_uniform
-    from oracle import dense_mf, gmres, hodlr_mf, nd, symbolic
+def oracle_sample(workload: str, cpu_m: int):
+    """A bounded sample of the workload for the host oracle: (problems, tol, description)."""
+    from fixtures import hex_cube, lognormal_coefficients, p1_jittered, q1_square, workload as wl
+    if workload == "hex_lognormal_64^3":
+        m = 20
+        return ([hex_cube(m, lognormal_coefficients(m ** 3, sigma=0.5, mu=0.0, seed=3))], 1e-4,
+                f"{m}^3 hex grid of the same lognormal family ({(m - 1) ** 3} unknowns)")
+    if workload == "p1_batch_256":
+        from fixtures import p1_batch_sizes
+        sizes = p1_batch_sizes(256, 5)[:4]
+        return ([p1_jittered(int(nc), seed=5 + i) for i, nc in enumerate(sizes)], 1e-4,
+                f"the first 4 meshes of the batch (cells per side {list(map(int, sizes))})")
+    if workload == "q1_poisson_64x64":
+        return [wl(workload)[0]], 1e-6, "the full 64x64 Poisson problem (3969 unknowns)"
+    m = cpu_m
     coef = lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=1)
-    P = q1_square(m, coef)
-    b = rhs_uniform(P.n, rhs_cols, 2)
+    return ([q1_square(m, coef)], 1e-4,
+            f"{m}x{m} grid of the same lognormal Q1 family ({(m - 1) ** 2} unknowns)")
+
+
+def oracle_solve_once(problems, tol: float):
+    """Time the oracle pipeline (ND, symbolic, HODLR-MF factor, GMRES) once per problem
+    with one right-hand side each.  Returns (seconds, solves, worst relres)."""
+    from fixtures import rhs_uniform
+    from oracle import dense_mf, gmres, hodlr_mf, nd, symbolic
     t0 = time.perf_counter()
-    et = nd.nested_dissection(P.coords, 64)
-    sym = symbolic.symbolic(P.rowptr, P.colidx, et)
-    Ap = dense_mf.permuted_matrix(P.rowptr, P.colidx, P.values, et)
-    fr, _ = hodlr_mf.factor(Ap, et, sym, hodlr_mf.Params(tol=1e-4, n_c=64, leaf=64))
     worst = 0.0
-    for c in range(rhs_cols):
-        bn = b[:, c][et.perm]
+    for P in problems:
+        b = rhs_uniform(P.n, 1, 2)
+        et = nd.nested_dissection(P.coords, 64)
+        sym = symbolic.symbolic(P.rowptr, P.colidx, et)
+        Ap = dense_mf.permuted_matrix(P.rowptr, P.colidx, P.values, et)
+        fr, _ = hodlr_mf.factor(Ap, et, sym, hodlr_mf.Params(tol=tol, n_c=64, leaf=64))
+        bn = b[:, 0][et.perm]
         x, info = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), bn, RTOL, 30)
         worst = max(worst, info["relres"])
-    return time.perf_counter() - t0, rhs_cols, worst
+    return time.perf_counter() - t0, len(problems), worst
 
 
 def cpu_cores() -> int:
@@ -389,16 +459,15 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline(m: int) -> dict:
-    """The oracle as it stands on a bounded sample: one right-hand side on an m x m grid
-    of the same lognormal family (the full 1024 x 1024 factorization alone takes minutes
-    in the oracle), analyze + factor + GMRES, on all host cores."""
-    sec, solves, rr = oracle_solve_once(m, 1)
+def cpu_baseline(workload: str, cpu_m: int) -> dict:
+    """The oracle as it stands on a bounded sample of the workload (the full-size oracle
+    factorization takes minutes), analyze + factor + GMRES, on all host cores."""
+    problems, tol, desc = oracle_sample(workload, cpu_m)
+    sec, solves, rr = oracle_solve_once(problems, tol)
     return {"value": solves / sec, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"{m}x{m} grid of the same lognormal Q1 family ({(m - 1) ** 2} unknowns), one "
-                      f"right-hand side: analyze + FP64 HODLR-MF factor (SVD truncation) + GMRES to "
-                      f"1e-10 on the host in {sec:.1f} s (BLAS threads = all cores), relres {rr:.1e}; "
-                      f"not scaled to the 1024x1024 size"}
+            "sample": f"{desc}, one right-hand side each: analyze + FP64 HODLR-MF factor (SVD "
+                      f"truncation) + GMRES to 1e-10 on the host in {sec:.1f} s (BLAS threads = all "
+                      f"cores), relres {rr:.1e}; not scaled to the full size"}
 
 
 def run_reference(args, rank, world):
@@ -406,21 +475,23 @@ def run_reference(args, rank, world):
     workload (a 128 x 128 grid of the same lognormal family, one right-hand side)."""
     if rank != 0:
         return None
-    m = 128
+    problems, tol, desc = oracle_sample(args.workload, 128)
     for _ in range(args.warmup):
-        oracle_solve_once(m, 1)
+        oracle_solve_once(problems, tol)
     per = []
+    solves = 0
     for _ in range(args.steps):
-        sec, _, rr = oracle_solve_once(m, 1)
+        sec, ns, rr = oracle_solve_once(problems, tol)
         per.append(sec * 1e3)
+        solves += ns
     total = sum(per)
-    value = args.steps / (total * 1e-3)
-    sample = f"{m}x{m} grid of the same lognormal Q1 family ({(m - 1) ** 2} unknowns), 1 RHS per step"
+    value = solves / (total * 1e-3)
+    sample = f"{desc}, 1 RHS per problem per step"
     return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": args.workload, "sample": sample},
             "p50_ms": statistics.median(per), "relres_max": rr,
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
@@ -438,7 +509,7 @@ def main():
     # The host oracle runs before any GPU work in this process (no fork after CUDA init).
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_run:
-        cpu = cpu_baseline(min(args.cpu_m, args.m))
+        cpu = cpu_baseline(args.workload, min(args.cpu_m, args.m))
     line = run_ours(args, rank, world, local)
     if rank == 0:
         if not args.profile_run:
