@@ -138,7 +138,7 @@ void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s);
 template <typename T>
 void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStream_t s);
 template <typename T>
-void launch_qr(const QrTask* tasks, int ntasks, cudaStream_t s);
+void launch_qr(const QrTask* tasks, int ntasks, int maxm, int max_smem, cudaStream_t s);
 template <typename T>
 void launch_tsqr(const TsqrTask* tasks, int ntasks, const TsqrBlock* blocks, int nblocks, size_t smem_block,
                  size_t smem_stack, T* scratch, cudaStream_t s);

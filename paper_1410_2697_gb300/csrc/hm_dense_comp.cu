@@ -110,9 +110,246 @@ __global__ void __launch_bounds__(256) k_qr(const QrTask* __restrict__ tasks) {
   }
 }
 
+// =====================================================================================
+// Blocked Householder QR of a tall m x k panel (k <= m), one CTA per panel, in global
+// memory: panels of kQrNB columns are factored column by column (the updates stay inside
+// the panel), then their product H_p0 ... H_p0+nb-1 = I - V T V^T (compact WY form, T upper
+// triangular, built from V^T V) is applied to the trailing columns in one pass
+// (a -= V T^T V^T a).  Q is formed backwards panel by panel from [I; 0]: trailing
+// columns get (I - V T V^T) q, the panel's own columns e_j - V T V^T e_j.  Same
+// scale-safe reflectors as the unblocked kernel.  V of the current panel is staged in
+// shared memory (m x nb); T of every panel is kept for the Q pass.
+// =====================================================================================
+constexpr int kQrNB = 8;
+
 template <typename T>
-void launch_qr(const QrTask* tasks, int ntasks, cudaStream_t s) {
+__device__ __forceinline__ T warp_sum_all(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reflector of column j (rows j.. of a, global): tail scaled in place, a[j] = beta.
+// Returns tau; every thread of warp 0 calls it.
+template <typename T>
+__device__ __forceinline__ T make_reflector_warp(T* __restrict__ aj, int j, int m) {
+  const int lane = threadIdx.x & 31;
+  T s = T(0);
+  for (int i = j + 1 + lane; i < m; i += 32) s += aj[i] * aj[i];
+  s = warp_sum_all(s);
+  const T x0 = aj[j];
+  T tj = T(0), beta = x0, scale = T(1);
+  if (s > T(0)) {
+    const T nrm = sqrt(x0 * x0 + s);
+    beta = x0 >= T(0) ? -nrm : nrm;
+    tj = (beta - x0) / beta;
+    scale = T(1) / (x0 - beta);
+  }
+  for (int i = j + 1 + lane; i < m; i += 32) aj[i] *= scale;
+  __syncwarp();
+  if (lane == 0) aj[j] = beta;
+  return tj;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_qr_blocked(const QrTask* __restrict__ tasks) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ T tau[256];
+  __shared__ T Tall[256 / kQrNB][kQrNB][kQrNB];  // T of every panel (upper triangular)
+  __shared__ T G[kQrNB][kQrNB];
+  const QrTask t = tasks[blockIdx.x];
+  const int m = t.m, k = t.k, ld = t.ld;
+  T* Y = (T*)t.Y;
+  T* Vs = reinterpret_cast<T*>(smem_raw);  // (m - p0) x nb of the current panel, ld m
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int npanels = (k + kQrNB - 1) / kQrNB;
+  for (int pi = 0; pi < npanels; ++pi) {
+    const int p0 = pi * kQrNB, pw = min(kQrNB, k - p0), mv = m - p0;
+    // --- panel columns (rows p0..) into shared memory, factored there: reflector j by
+    //     warp 0, updates of the panel's later columns by one warp each; then written back
+    for (int e = threadIdx.x; e < mv * pw; e += blockDim.x) {
+      const int i = e % mv, c = e / mv;
+      Vs[i + (size_t)c * mv] = Y[(size_t)(p0 + i) + (size_t)(p0 + c) * ld];
+    }
+    __syncthreads();
+    for (int tt = 0; tt < pw; ++tt) {
+      T* vj = Vs + (size_t)tt * mv;  // column p0 + tt, local row index i <-> row p0 + i
+      if (wid == 0) {
+        const T tj = make_reflector_warp<T>(vj, tt, mv);
+        if (lane == 0) tau[p0 + tt] = tj;
+      }
+      __syncthreads();
+      const T tj = tau[p0 + tt];
+      if (tj != T(0))
+        for (int c = tt + 1 + wid; c < pw; c += nw) {
+          T* vc = Vs + (size_t)c * mv;
+          T w = T(0);
+          for (int i = tt + 1 + lane; i < mv; i += 32) w += vj[i] * vc[i];
+          w = warp_sum_all(w) + vc[tt];
+          const T f = tj * w;
+          __syncwarp();
+          if (lane == 0) vc[tt] -= f;
+          for (int i = tt + 1 + lane; i < mv; i += 32) vc[i] -= f * vj[i];
+        }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < mv * pw; e += blockDim.x) {
+      const int i = e % mv, c = e / mv;
+      Y[(size_t)(p0 + i) + (size_t)(p0 + c) * ld] = Vs[i + (size_t)c * mv];
+    }
+    __syncthreads();
+    // --- V (unit diagonal, zero above) in place
+    for (int e = threadIdx.x; e < mv * pw; e += blockDim.x) {
+      const int i = e % mv, c = e / mv;
+      if (i <= c) Vs[i + (size_t)c * mv] = i == c ? T(1) : T(0);
+    }
+    __syncthreads();
+    // --- G = V^T V (upper part), then T: T[s][s] = tau_s, T[0:s, s] = -tau_s T[0:s,0:s] G[0:s, s]
+    for (int e = wid; e < pw * pw; e += nw) {
+      const int a = e % pw, b = e / pw;
+      if (a >= b) continue;
+      T g = T(0);
+      for (int i = lane; i < mv; i += 32) g += Vs[i + (size_t)a * mv] * Vs[i + (size_t)b * mv];
+      g = warp_sum_all(g);
+      if (lane == 0) G[a][b] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T (*Tp)[kQrNB] = Tall[pi];
+      for (int s = 0; s < kQrNB; ++s)
+        for (int r = 0; r < kQrNB; ++r) Tp[r][s] = T(0);
+      for (int s = 0; s < pw; ++s) {
+        const T ts = tau[p0 + s];
+        for (int r = 0; r < s; ++r) {
+          T acc = T(0);
+          for (int q = r; q < s; ++q) acc += Tp[r][q] * G[q][s];
+          Tp[r][s] = -ts * acc;
+        }
+        Tp[s][s] = ts;
+      }
+    }
+    __syncthreads();
+    // --- trailing columns: a -= V (T^T (V^T a)), rows p0..m-1
+    const T (*Tp)[kQrNB] = Tall[pi];
+    for (int c = p0 + pw + wid; c < k; c += nw) {
+      T* ac = Y + (size_t)c * ld + p0;
+      T w[kQrNB];
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) w[s] = T(0);
+#pragma unroll 8
+      for (int i = lane; i < mv; i += 32) {
+        const T a = ac[i];
+#pragma unroll
+        for (int s = 0; s < kQrNB; ++s)
+          if (s < pw) w[s] += Vs[i + (size_t)s * mv] * a;
+      }
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) w[s] = warp_sum_all(w[s]);
+      T u[kQrNB];
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int r = 0; r < kQrNB; ++r)
+          if (r <= s) acc += Tp[r][s] * w[r];  // (T^T w)_s = sum_{r <= s} T[r][s] w[r]
+        u[s] = acc;
+      }
+#pragma unroll 8
+      for (int i = lane; i < mv; i += 32) {
+        T a = ac[i];
+#pragma unroll
+        for (int s = 0; s < kQrNB; ++s)
+          if (s < pw) a -= Vs[i + (size_t)s * mv] * u[s];
+        ac[i] = a;
+      }
+    }
+    __syncthreads();
+  }
+  if (t.R) {
+    T* R = (T*)t.R;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int i = e % k, c = e / k;
+      R[i + (size_t)c * k] = (i <= c) ? Y[(size_t)i + (size_t)c * ld] : T(0);
+    }
+  }
+  __syncthreads();
+  // --- Q = H_0 ... H_{k-1} [I; 0], panels backwards
+  for (int pi = npanels - 1; pi >= 0; --pi) {
+    const int p0 = pi * kQrNB, pw = min(kQrNB, k - p0), mv = m - p0;
+    for (int e = threadIdx.x; e < mv * pw; e += blockDim.x) {
+      const int i = e % mv, s = e / mv;
+      const T v = i < s ? T(0) : (i == s ? T(1) : Y[(size_t)(p0 + i) + (size_t)(p0 + s) * ld]);
+      Vs[i + (size_t)s * mv] = v;
+    }
+    __syncthreads();
+    const T (*Tp)[kQrNB] = Tall[pi];
+    // trailing Q columns c >= p0 + pw over rows p0..: rows p0 .. p0+pw-1 still hold R and
+    // are read as the zeros they are in Q at this stage (rows above p0 are handled by the
+    // earlier panels, processed after this one)
+    for (int c = p0 + pw + wid; c < k; c += nw) {
+      T* qc = Y + (size_t)c * ld + p0;
+      T w[kQrNB];
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) w[s] = T(0);
+#pragma unroll 8
+      for (int i = lane; i < mv; i += 32) {
+        const T q = i < pw ? T(0) : qc[i];
+#pragma unroll
+        for (int s = 0; s < kQrNB; ++s)
+          if (s < pw) w[s] += Vs[i + (size_t)s * mv] * q;
+      }
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) w[s] = warp_sum_all(w[s]);
+      T u[kQrNB];
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int r = 0; r < kQrNB; ++r)
+          if (r >= s) acc += Tp[s][r] * w[r];  // (T w)_s = sum_{r >= s} T[s][r] w[r]
+        u[s] = acc;
+      }
+#pragma unroll 8
+      for (int i = lane; i < mv; i += 32) {
+        T q = i < pw ? T(0) : qc[i];
+#pragma unroll
+        for (int s = 0; s < kQrNB; ++s)
+          if (s < pw) q -= Vs[i + (size_t)s * mv] * u[s];
+        qc[i] = q;
+      }
+    }
+    // the panel's own columns: e_j - V (T (V^T e_j)), V^T e_j = row j - p0 of V
+    for (int tt = wid; tt < pw; tt += nw) {
+      T* qc = Y + (size_t)(p0 + tt) * ld + p0;
+      T u[kQrNB];
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int r = 0; r < kQrNB; ++r)
+          if (r >= s && r < pw) acc += Tp[s][r] * Vs[tt + (size_t)r * mv];
+        u[s] = acc;
+      }
+      for (int i = lane; i < mv; i += 32) {
+        T q = (i == tt) ? T(1) : T(0);
+#pragma unroll
+        for (int s = 0; s < kQrNB; ++s)
+          if (s < pw) q -= Vs[i + (size_t)s * mv] * u[s];
+        qc[i] = q;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_qr(const QrTask* tasks, int ntasks, int maxm, int max_smem, cudaStream_t s) {
   if (ntasks <= 0) return;
+  const size_t vs = (size_t)maxm * kQrNB * sizeof(T);
+  if (vs + 8192 <= (size_t)max_smem) {
+    k_qr_blocked<T><<<ntasks, 512, vs, s>>>(tasks);
+    return;
+  }
   // dynamic shared memory: tau for up to 256 reflectors
   k_qr<T><<<ntasks, 256, 256 * sizeof(T), s>>>(tasks);
 }
@@ -436,6 +673,8 @@ void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStre
 }
 
 int dense_comp_setup(int max_smem) {
+  HM_CUDA(allow_max_dyn_smem(k_qr_blocked<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_qr_blocked<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_tsqr_blocks<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_tsqr_blocks<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_tsqr_stack<float>, max_smem));
@@ -449,8 +688,8 @@ int dense_comp_setup(int max_smem) {
 
 template void launch_omega<float>(const OmegaTask*, int, uint64_t, cudaStream_t);
 template void launch_omega<double>(const OmegaTask*, int, uint64_t, cudaStream_t);
-template void launch_qr<float>(const QrTask*, int, cudaStream_t);
-template void launch_qr<double>(const QrTask*, int, cudaStream_t);
+template void launch_qr<float>(const QrTask*, int, int, int, cudaStream_t);
+template void launch_qr<double>(const QrTask*, int, int, int, cudaStream_t);
 template void launch_tsqr<float>(const TsqrTask*, int, const TsqrBlock*, int, size_t, size_t, float*,
                                  cudaStream_t);
 template void launch_tsqr<double>(const TsqrTask*, int, const TsqrBlock*, int, size_t, size_t, double*,

@@ -59,7 +59,7 @@ static void run_qr(hm_sys_s* sys, const QrBatch& b, const unsigned char* base) {
   if (b.plain.count == 0 && b.ts.count == 0) return;
   cudaStream_t s = sys->ctx->stream;
   ProfScope ps(sys->ctx, PC_QR, b.work, (b.plain.count ? 1 : 0) + (b.ts.count ? 3 : 0));
-  launch_qr<T>(b.plain.dev(base), b.plain.count, s);
+  launch_qr<T>(b.plain.dev(base), b.plain.count, b.plain_maxm, sys->ctx->max_smem, s);
   launch_tsqr<T>(b.ts.dev(base), b.ts.count, b.blocks.dev(base), b.blocks.count, b.smem_block, b.smem_stack,
                  (T*)sys->d_qrs, s);
 }

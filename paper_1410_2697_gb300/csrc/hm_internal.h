@@ -189,6 +189,7 @@ struct HFront {
 // single-CTA global-memory kernel otherwise.
 struct QrBatch {
   Span<QrTask> plain;
+  int plain_maxm = 0;
   Span<TsqrTask> ts;
   Span<TsqrBlock> blocks;
   size_t smem_block = 0, smem_stack = 0;

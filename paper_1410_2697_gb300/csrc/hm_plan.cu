@@ -52,6 +52,7 @@ static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, 
                       (size_t)((m + nb - 1) / nb) * k * es <= budget;
     if (!fits) {
       plain.push_back(t);
+      b.plain_maxm = std::max(b.plain_maxm, m);
       continue;
     }
     for (int j = 0; j < nb; ++j) blocks.push_back(TsqrBlock{(int)ts.size(), j});
