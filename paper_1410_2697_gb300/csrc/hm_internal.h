@@ -273,6 +273,13 @@ struct SolvePlan {
   void* d_xfix = nullptr;       // T, n x nrhs: the solution (task tables point into it)
   int64_t* d_fvoff = nullptr;
   int64_t* d_yvoff = nullptr;   // per front: offset of y (np x nrhs) in the scratch, -1 if dense
+  // captured apply (graph of the launches for input graph_in) and the last input seen
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* graph_in = nullptr;
+  const void* last_in = nullptr;
+  ~SolvePlan() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  }
 };
 
 struct Plan {

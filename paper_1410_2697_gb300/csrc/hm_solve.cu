@@ -360,10 +360,9 @@ static dim3 vgrid(int nitems, int nrhs, int maxlen) {
               (unsigned)std::max(1, (maxlen + kVecChunk - 1) / kVecChunk));
 }
 
+// The launches of one apply (input win, output in the plan's fixed buffer).
 template <typename T>
-static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
-  SolvePlan* sp = nullptr;
-  HM_TRY(get_solve_plan(sys, nrhs, &sp));
+static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) {
   Plan& P = sys->plan;
   hm_ctx_s* ctx = sys->ctx;
   cudaStream_t s = ctx->stream;
@@ -420,8 +419,49 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
                                                 P.d_np, sp->d_yvoff, (const T*)sp->d_sb);
     }
   }
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+// z = M^{-1} r.  An apply whose input buffer repeats (GMRES applies the preconditioner to
+// the same staging buffer every iteration) is captured once into a CUDA graph and
+// replayed: its ~10^2 dependent launches then cost one graph launch.  The first apply
+// with a new input runs eagerly; with the launch profiler on, applies always run eagerly.
+template <typename T>
+static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
+  SolvePlan* sp = nullptr;
+  HM_TRY(get_solve_plan(sys, nrhs, &sp));
+  hm_ctx_s* ctx = sys->ctx;
+  cudaStream_t s = ctx->stream;
+  const bool graphs = !ctx->prof.on && s != nullptr;
+  if (graphs && sp->graph_exec && sp->graph_in == (const void*)win) {
+    HM_CUDA(cudaGraphLaunch(sp->graph_exec, s));
+  } else if (graphs && sp->last_in == (const void*)win) {
+    cudaGraph_t g = nullptr;
+    HM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int st = apply_launches<T>(sys, sp, nrhs, win);
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (st != HM_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (st != HM_OK) return st;
+      HM_CUDA(ce);
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    HM_CUDA(ie);
+    if (sp->graph_exec) cudaGraphExecDestroy(sp->graph_exec);
+    sp->graph_exec = ex;
+    sp->graph_in = win;
+    HM_CUDA(cudaGraphLaunch(sp->graph_exec, s));
+  } else {
+    HM_TRY(apply_launches<T>(sys, sp, nrhs, win));
+  }
+  sp->last_in = win;
+  T* xfix = (T*)sp->d_xfix;
   if (xout != xfix)
-    HM_CUDA(cudaMemcpyAsync(xout, xfix, sizeof(T) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(xout, xfix, sizeof(T) * (size_t)sys->n * nrhs, cudaMemcpyDeviceToDevice, s));
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }
