@@ -62,10 +62,42 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// element (r, c) of op(X) (nr x nc); zero outside
-__device__ __forceinline__ float op_at(const float* __restrict__ X, int op, int ld, int r, int c, int nr, int nc) {
-  if (r >= nr || c >= nc) return 0.f;
-  return op == 0 ? X[(size_t)r + (size_t)c * ld] : X[(size_t)c + (size_t)r * ld];
+// Stages rows row0 .. row0+R-1 and k indices k0 .. k0+TK-1 of an operand (FP32 in
+// memory, zero outside rows < nrows and k < kend) as BF16 into a K-major slice of R rows.
+// rows_fast: element (row, k) sits at X[row + k ld] (consecutive threads take consecutive
+// rows), else at X[k + row ld] (consecutive threads take consecutive k).  A thread issues
+// all its loads before converting and storing, so they are in flight together.
+template <int R>
+__device__ __forceinline__ void stage_slice(unsigned char* __restrict__ sl, const float* __restrict__ X,
+                                            bool rows_fast, int ld, int row0, int nrows, int k0, int kend,
+                                            int tid) {
+  constexpr int PER = R * TK / 256;
+  float v[PER];
+  if (rows_fast) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q, r = e % R, c = e / R;
+      const int gr = row0 + r, gk = k0 + c;
+      v[q] = (gr < nrows && gk < kend) ? X[(size_t)gr + (size_t)gk * ld] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q, r = e % R, c = e / R;
+      *(__nv_bfloat16*)(sl + kmaj(r, c, R)) = __float2bfloat16(v[q]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q, c = e % TK, r = e / TK;
+      const int gr = row0 + r, gk = k0 + c;
+      v[q] = (gr < nrows && gk < kend) ? X[(size_t)gk + (size_t)gr * ld] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q, c = e % TK, r = e / TK;
+      *(__nv_bfloat16*)(sl + kmaj(r, c, R)) = __float2bfloat16(v[q]);
+    }
+  }
 }
 
 }  // namespace
@@ -109,20 +141,9 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
     unsigned char* sA = smem + s * (kStageA + kStageB);
     unsigned char* sB = sA + kStageA;
     const int kb = tl.k0 + kt * TK;
-    // A slice: op(A)[m0 .. m0+127, kb .. kb+63]; consecutive threads follow the stored order
-    for (int e = tid; e < TM * TK; e += 256) {
-      int r, c;
-      if (t.opA == 0) { r = e % TM; c = e / TM; } else { c = e % TK; r = e / TK; }
-      const float v = (kb + c < tl.k1) ? op_at(A, t.opA, t.lda, m0 + r, kb + c, t.m, t.k) : 0.f;
-      *(__nv_bfloat16*)(sA + kmaj(r, c, TM)) = __float2bfloat16(v);
-    }
-    // B slice as N x K (row n = column n of op(B))
-    for (int e = tid; e < TN * TK; e += 256) {
-      int r, c;  // r: n, c: k
-      if (t.opB == 0) { c = e % TK; r = e / TK; } else { r = e % TN; c = e / TN; }
-      const float v = (kb + c < tl.k1) ? op_at(B, t.opB, t.ldb, kb + c, n0 + r, t.k, t.n) : 0.f;
-      *(__nv_bfloat16*)(sB + kmaj(r, c, TN)) = __float2bfloat16(v);
-    }
+    // A slice: op(A)[m0 .., kb ..]; B slice as N x K (row n = column n of op(B))
+    stage_slice<TM>(sA, A, t.opA == 0, t.lda, m0, t.m, kb, tl.k1, tid);
+    stage_slice<TN>(sB, B, t.opB != 0, t.ldb, n0, t.n, kb, tl.k1, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
