@@ -182,18 +182,20 @@ COMPUTE_CATS = {"gemm_factor", "gemm_apply", "dense_potrf", "dense_trsm", "house
 
 def ncu_traffic(category: str):
     """DRAM bytes per launch of `category` from the committed ncu summaries (a line
-    'TRAFFIC <category> <bytes> <sha1 of the source file>'), or None if none was
-    captured or the kernel's source changed since."""
+    'TRAFFIC <category> <bytes> <source file> <sha1[:12] of that file>'), or None if none
+    was captured or the kernel's source changed since."""
     import glob
     import hashlib
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         for ln in open(f):
             parts = ln.split()
-            if len(parts) == 4 and parts[0] == "TRAFFIC" and parts[1] == category:
-                src = os.path.join(ROOT, "paper_1410_2697_gb300", "csrc", "hm_solve.cu")
-                if hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] != parts[3]:
+            if len(parts) == 5 and parts[0] == "TRAFFIC" and parts[1] == category:
+                src = os.path.join(ROOT, "paper_1410_2697_gb300", "csrc", parts[3])
+                try:
+                    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+                except OSError:
                     return None
-                return float(parts[2])
+                return float(parts[2]) if sha == parts[4] else None
     return None
 
 
@@ -205,7 +207,7 @@ def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
         achieved = (e["flops"] / max(e["launches"], 1)) / (per_launch_ms * 1e-3) / 1e12
         peak = alu_peak_tflops(precision, (clocks or {}).get("sm_max_mhz"))
         return {"kernel": cat, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "launches": e["launches"],
+                "frac": achieved / peak, "traffic": ncu_traffic(cat), "launches": e["launches"],
                 "avg_launch_ms": per_launch_ms, "share_of_profiled_time":
                     e["ms"] / sum(v["ms"] for v in prof.values()),
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock" if precision != "f64"
