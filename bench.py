@@ -63,6 +63,10 @@ def parse_args():
                     help="mixed arm only, no e2e / FP64 / CPU legs (for an ncu launch list)")
     ap.add_argument("--cpu-m", type=int, default=256,
                     help="grid of the bounded CPU-oracle sample (same family)")
+    ap.add_argument("--probe", choices=["factor_apply", "hex_factor"], default=None,
+                    help="profiling driver for ncu: run analyze + factor (+ one apply) of the "
+                         "workload twice, the second factor / apply inside NVTX ranges "
+                         "'factor1' / 'apply1'; prints nothing else")
     return ap.parse_args()
 
 
@@ -500,8 +504,53 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_probe(args):
+    """Small fixed driver for ncu captures (see --probe)."""
+    import numpy as np
+    import torch
+
+    import paper_1410_2697_gb300 as hm
+    from fixtures import lognormal_coefficients, q1_square, rhs_uniform, workload
+    if args.probe == "hex_factor":
+        P, _ = workload("hex_lognormal_64^3")
+        precision, nrhs = hm.HM_PREC_MIXED_BF16, 0
+    else:
+        m = args.m
+        P = q1_square(m, lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=1))
+        precision, nrhs = hm.HM_PREC_MIXED, 16
+    dev = torch.device("cuda", 0)
+    rp, ci = torch.from_numpy(P.rowptr).to(dev), torch.from_numpy(P.colidx).to(dev)
+    va = torch.from_numpy(P.values).to(dev)
+    co = torch.from_numpy(np.ascontiguousarray(P.coords)).to(dev)
+    o = hm.hm_default_opts()
+    o.precision = precision
+    ctx = hm.hm_create(o)
+    if nrhs:
+        b = torch.from_numpy(np.ascontiguousarray(rhs_uniform(P.n, nrhs, 2).T)).to(dev)
+        z = torch.zeros_like(b)
+    for it in range(2):
+        s = hm.hm_analyze(ctx, P.n, rp, ci, P.dim, co)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(f"factor{it}")
+        hm.hm_factor(s, va, 1e-4)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        if nrhs:
+            hm.hm_precond_apply(s, nrhs, b, z)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push(f"apply{it}")
+            hm.hm_precond_apply(s, nrhs, b, z)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+        hm.hm_destroy(s)
+    hm.hm_ctx_destroy(ctx)
+
+
 def main():
     args = parse_args()
+    if args.probe:
+        run_probe(args)
+        return
     rank, world, local = dist_init()
     if args.impl == "reference":
         line = run_reference(args, rank, world)
