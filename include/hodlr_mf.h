@@ -246,6 +246,47 @@ int hm_destroy(hm_sys_t sys);
 const char* hm_status_str(int status);
 const char* hm_last_error(void);
 
+/*
+ * Serving (many matrices, requests arriving over time).  A server owns nworkers worker
+ * threads, each with its own context (stream, memory pool and hbm_budget / nworkers of
+ * the budget in *opts; opts->stream is ignored).  Registered matrices (host copies of
+ * the CSR, FP64 values and lattice coordinates) are bound to workers round robin and
+ * analysed + factored on their first request; the factorization then stays resident
+ * until evicted (least recently used first) to admit another matrix within the budget.
+ * A free worker takes its oldest waiting request and joins every waiting request for
+ * the same matrix, up to max_batch_rhs right-hand sides, into one hm_solve (continuous
+ * batching); workers run concurrently, so different matrices overlap on the GPU.  Each
+ * right-hand side is its own GMRES instance, so a request's answer equals (to rounding)
+ * the answer it gets alone.  Latency = completion - submission, host clock.
+ *
+ *   hm_server_submit: b, x are host arrays (n x nrhs column-major) that must stay valid
+ *   until hm_server_wait returns for the request; nrhs <= max_batch_rhs.
+ *   hm_server_wait: blocks until the request completes; returns its status (HM_OK,
+ *   HM_ERR_NO_CONVERGENCE, HM_ERR_OUT_OF_MEMORY if the matrix does not fit the budget
+ *   alone, ...) and, if non-null, its solve info, latency and the number of right-hand
+ *   sides in the solve that served it.
+ */
+typedef struct hm_server_s* hm_server_t;
+typedef struct hm_server_stats {
+  int64_t completed, failed;     /* requests finished with / without success            */
+  int64_t batches, batched_rhs;  /* solves run and right-hand sides they carried        */
+  int64_t factorizations;        /* analyze + factor runs (misses)                      */
+  int64_t evictions;             /* resident systems destroyed to admit others          */
+  double p50_ms, p99_ms;         /* latency percentiles of the successful requests      */
+  double device_bytes;           /* device memory held by the workers' contexts         */
+} hm_server_stats;
+
+int hm_server_create(const hm_opts* opts, int32_t nworkers, int32_t max_batch_rhs, hm_server_t* out);
+int hm_server_add_matrix(hm_server_t server, int32_t n, const int64_t* rowptr, const int32_t* colidx,
+                         const double* values, int32_t dim, const int32_t* grid_coords, double tol,
+                         int32_t* matrix_id);
+int hm_server_submit(hm_server_t server, int32_t matrix_id, int32_t nrhs, const double* b, double* x,
+                     double rtol, int64_t* request_id);
+int hm_server_wait(hm_server_t server, int64_t request_id, hm_solve_info* info, double* latency_ms,
+                   int32_t* batch_rhs);
+int hm_server_get_stats(hm_server_t server, hm_server_stats* stats);
+int hm_server_destroy(hm_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

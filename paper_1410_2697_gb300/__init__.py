@@ -17,8 +17,9 @@ from ._binding import (HM_PREC_FP64, HM_PREC_MIXED, HM_PREC_MIXED_BF16, HmError,
                        hm_ctx_destroy, hm_default_opts, hm_destroy, hm_factor, hm_get_front_ranks,
                        hm_get_hodlr_block, hm_profile_enable, hm_profile_read,
                        hm_get_ordering, hm_get_sizes, hm_get_symbolic, hm_get_update,
-                       hm_last_error, hm_precond_apply, hm_precond_apply_noalloc, hm_solve,
-                       hm_status_str)
+                       hm_last_error, hm_precond_apply, hm_precond_apply_noalloc, hm_server_add_matrix,
+                       hm_server_create, hm_server_destroy, hm_server_get_stats, hm_server_submit,
+                       hm_server_wait, hm_solve, hm_status_str)
 
 
 class Solver:

@@ -32,7 +32,9 @@ HM_PREC_MIXED_BF16 = 2
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_analyze_batch", "hm_get_sizes",
             "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_solve", "hm_precond_apply",
             "hm_precond_apply_noalloc",
-            "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error"]
+            "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error",
+            "hm_server_create", "hm_server_add_matrix", "hm_server_submit", "hm_server_wait",
+            "hm_server_get_stats", "hm_server_destroy"]
 
 
 class HmOpts(C.Structure):
@@ -51,6 +53,12 @@ class HmFactorInfo(C.Structure):
     _fields_ = [("nfronts", C.c_int32), ("nlevels", C.c_int32), ("n_hodlr", C.c_int32),
                 ("max_rank", C.c_int32), ("rank_capped", C.c_int32), ("factor_bytes", C.c_double),
                 ("front_bytes", C.c_double)]
+
+
+class HmServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("batches", C.c_int64),
+                ("batched_rhs", C.c_int64), ("factorizations", C.c_int64), ("evictions", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("device_bytes", C.c_double)]
 
 
 class HmProfEntry(C.Structure):
@@ -90,6 +98,12 @@ def _load():
                                        C.POINTER(i32), C.POINTER(i32), vp, vp]
     lib.hm_profile_enable.argtypes = [vp, C.c_int]
     lib.hm_profile_read.argtypes = [vp, i32, C.POINTER(HmProfEntry), C.POINTER(i32)]
+    lib.hm_server_create.argtypes = [C.POINTER(HmOpts), i32, i32, C.POINTER(vp)]
+    lib.hm_server_add_matrix.argtypes = [vp, i32, vp, vp, vp, i32, vp, dbl, C.POINTER(i32)]
+    lib.hm_server_submit.argtypes = [vp, i32, i32, vp, vp, dbl, C.POINTER(C.c_int64)]
+    lib.hm_server_wait.argtypes = [vp, C.c_int64, C.POINTER(HmSolveInfo), C.POINTER(dbl), C.POINTER(i32)]
+    lib.hm_server_get_stats.argtypes = [vp, C.POINTER(HmServerStats)]
+    lib.hm_server_destroy.argtypes = [vp]
     lib.hm_destroy.argtypes = [vp]
     lib.hm_status_str.argtypes = [C.c_int]
     lib.hm_status_str.restype = C.c_char_p
@@ -284,3 +298,54 @@ def hm_status_str(status: int) -> str:
 
 def hm_last_error() -> str:
     return _lib.hm_last_error().decode()
+
+
+# ------------------------------------------------------------------------------------
+# serving
+# ------------------------------------------------------------------------------------
+def hm_server_create(opts=None, nworkers: int = 2, max_batch_rhs: int = 64) -> C.c_void_p:
+    srv = C.c_void_p()
+    o = opts if opts is not None else hm_default_opts()
+    _check(_lib.hm_server_create(C.byref(o), int(nworkers), int(max_batch_rhs), C.byref(srv)), "hm_server_create")
+    return srv
+
+
+def hm_server_add_matrix(srv, problem, tol: float) -> int:
+    """Registers a matrix (host copies are kept by the server); returns its id."""
+    mid = C.c_int32()
+    p = problem
+    coords = np.ascontiguousarray(p.coords, dtype=np.int32)
+    _check(_lib.hm_server_add_matrix(srv, int(p.n), _ptr(p.rowptr, np.int64, "rowptr", p.n + 1),
+                                     _ptr(p.colidx, np.int32, "colidx"), _ptr(p.values, np.float64, "values"),
+                                     int(p.dim), _ptr(coords, np.int32, "grid_coords"), float(tol), C.byref(mid)),
+           "hm_server_add_matrix")
+    return mid.value
+
+
+def hm_server_submit(srv, matrix_id: int, b, x, rtol: float = 1e-10) -> int:
+    """b, x: F-contiguous host arrays (n x nrhs) kept alive until hm_server_wait."""
+    nrhs = 1 if b.ndim == 1 else b.shape[1]
+    rid = C.c_int64()
+    _check(_lib.hm_server_submit(srv, int(matrix_id), int(nrhs), _ptr(b, np.float64, "b"),
+                                 _ptr(x, np.float64, "x"), float(rtol), C.byref(rid)), "hm_server_submit")
+    return rid.value
+
+
+def hm_server_wait(srv, request_id: int) -> dict:
+    info = HmSolveInfo()
+    lat = C.c_double()
+    brhs = C.c_int32()
+    st = _lib.hm_server_wait(srv, C.c_int64(request_id), C.byref(info), C.byref(lat), C.byref(brhs))
+    d = {f: getattr(info, f) for f, _ in HmSolveInfo._fields_}
+    d.update(status=st, latency_ms=lat.value, batch_rhs=brhs.value)
+    return d
+
+
+def hm_server_get_stats(srv) -> dict:
+    st = HmServerStats()
+    _check(_lib.hm_server_get_stats(srv, C.byref(st)), "hm_server_get_stats")
+    return {f: getattr(st, f) for f, _ in HmServerStats._fields_}
+
+
+def hm_server_destroy(srv) -> None:
+    _check(_lib.hm_server_destroy(srv), "hm_server_destroy")

@@ -1,0 +1,120 @@
+"""Serving runtime (hm_server_*): requests for several matrices arriving together are
+batched per matrix and run on concurrent workers; each result must equal, within the
+stated tolerance, the answer the same request gets alone (the mix-vs-alone property),
+with its own relative residual <= rtol.  The HBM budget admits matrices by evicting the
+least recently used factorization, and a matrix that cannot fit alone fails cleanly."""
+import numpy as np
+import pytest
+
+from fixtures import hex_cube, lognormal_coefficients, p1_jittered, q1_square, rhs_uniform
+
+pytestmark = pytest.mark.gpu
+
+try:
+    import paper_1410_2697_gb300 as hm
+except ImportError:  # the library is built on the GPU machine; a CPU-only machine skips
+    import torch
+    if torch.cuda.is_available():
+        raise
+    pytest.skip("CUDA library not built on this CPU-only machine", allow_module_level=True)
+
+TOL = 1e-4
+
+
+def matrices():
+    return [q1_square(33, lognormal_coefficients(33 * 33, 1.0, seed=1)),
+            q1_square(41, lognormal_coefficients(41 * 41, 1.0, seed=2)),
+            hex_cube(9, lognormal_coefficients(9 ** 3, 0.5, seed=3)),
+            p1_jittered(37, seed=5)]
+
+
+def opts(budget=0):
+    o = hm.hm_default_opts()
+    o.nd_leaf, o.hodlr_leaf, o.n_c, o.samples = 16, 16, 16, 24
+    o.hbm_budget = budget
+    return o
+
+
+def solve_alone(p, b):
+    s = hm.Solver(p.n, p.rowptr, p.colidx, grid_coords=p.coords, dim=p.dim, nd_leaf=16, hodlr_leaf=16,
+                  n_c=16, samples=24)
+    s.factor(p.values, TOL)
+    x = np.zeros_like(b)
+    x, info = s.solve(b, rtol=1e-10, x=x)
+    s.close()
+    return x
+
+
+def test_results_are_the_same_alone_and_in_the_mix():
+    mats = matrices()
+    srv = hm.hm_server_create(opts(), nworkers=2, max_batch_rhs=64)
+    try:
+        ids = [hm.hm_server_add_matrix(srv, p, TOL) for p in mats]
+        rng = np.random.default_rng(7)
+        reqs = []
+        for k in range(24):  # submitted back to back: requests for one matrix share solves
+            mi = int(rng.integers(0, len(mats)))
+            nrhs = int(rng.integers(1, 9))
+            b = np.asfortranarray(rhs_uniform(mats[mi].n, nrhs, 100 + k))
+            x = np.zeros_like(b, order="F")
+            reqs.append((mi, b, x, hm.hm_server_submit(srv, ids[mi], b, x)))
+        for mi, b, x, rid in reqs:
+            r = hm.hm_server_wait(srv, rid)
+            assert r["status"] == hm.abi.HM_OK and r["converged"] == 1
+            A = mats[mi].scipy()
+            for c in range(b.shape[1]):
+                assert np.linalg.norm(b[:, c] - A @ x[:, c]) / np.linalg.norm(b[:, c]) <= 1e-10
+            xa = solve_alone(mats[mi], b)
+            assert np.linalg.norm(x - xa) / np.linalg.norm(xa) <= 1e-8
+        st = hm.hm_server_get_stats(srv)
+        assert st["completed"] == len(reqs) and st["failed"] == 0
+        assert st["factorizations"] == len(mats)
+        assert st["batched_rhs"] == sum(b.shape[1] for _, b, _, _ in reqs)
+        assert st["batches"] < len(reqs)  # some requests shared a solve
+        assert 0 < st["p50_ms"] <= st["p99_ms"]
+    finally:
+        hm.hm_server_destroy(srv)
+
+
+def test_budget_evicts_least_recently_used_factorizations():
+    mats = matrices()[:3]
+    # measure one worker's footprint of the largest matrix, then allow about one at a time
+    probe = hm.hm_server_create(opts(), nworkers=1, max_batch_rhs=8)
+    try:
+        mid = hm.hm_server_add_matrix(probe, mats[1], TOL)
+        b = np.asfortranarray(rhs_uniform(mats[1].n, 2, 1))
+        x = np.zeros_like(b, order="F")
+        assert hm.hm_server_wait(probe, hm.hm_server_submit(probe, mid, b, x))["status"] == hm.abi.HM_OK
+        one = hm.hm_server_get_stats(probe)["device_bytes"]
+    finally:
+        hm.hm_server_destroy(probe)
+    srv = hm.hm_server_create(opts(int(1.5 * one)), nworkers=1, max_batch_rhs=8)
+    try:
+        ids = [hm.hm_server_add_matrix(srv, p, TOL) for p in mats]
+        for rnd in range(2):
+            for mi in range(len(mats)):
+                b = np.asfortranarray(rhs_uniform(mats[mi].n, 2, 10 * rnd + mi))
+                x = np.zeros_like(b, order="F")
+                r = hm.hm_server_wait(srv, hm.hm_server_submit(srv, ids[mi], b, x))
+                assert r["status"] == hm.abi.HM_OK
+                A = mats[mi].scipy()
+                assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-9
+        st = hm.hm_server_get_stats(srv)
+        assert st["evictions"] > 0 and st["factorizations"] > len(mats)
+        assert st["device_bytes"] <= 1.5 * one
+    finally:
+        hm.hm_server_destroy(srv)
+
+
+def test_matrix_larger_than_the_budget_fails_cleanly():
+    srv = hm.hm_server_create(opts(1 << 16), nworkers=1, max_batch_rhs=4)  # 64 KiB
+    try:
+        p = matrices()[0]
+        mid = hm.hm_server_add_matrix(srv, p, TOL)
+        b = np.asfortranarray(rhs_uniform(p.n, 1, 3))
+        x = np.zeros_like(b, order="F")
+        r = hm.hm_server_wait(srv, hm.hm_server_submit(srv, mid, b, x))
+        assert r["status"] == hm.abi.HM_ERR_OUT_OF_MEMORY
+        assert hm.hm_server_get_stats(srv)["failed"] == 1
+    finally:
+        hm.hm_server_destroy(srv)
