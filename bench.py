@@ -18,6 +18,8 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 Under torchrun each rank runs an independent replica on its own GPU (the method has no
 data-parallel exchange); the line reports the whole-job rate and max-over-ranks time.
 Other workloads (for the parity/coverage record, not the headline line):
+``serving`` (Poisson arrivals at 200 requests/s over 24 cached matrices of the three mesh
+sizes, 1-64 right-hand sides each, through the hm_server runtime; requests/s, p50/p99),
 ``hex_lognormal_64^3`` (3D trilinear hex, BF16 tensor-core range finder, 1 RHS),
 ``p1_batch_256`` (256 independent jittered P1 meshes analysed as one forest, 1 RHS each),
 ``q1_poisson_64x64`` (the small FP64 case).
@@ -50,7 +52,13 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "hex_lognormal_64^3", "p1_batch_256", "q1_poisson_64x64"])
+                    choices=[WORKLOAD, "hex_lognormal_64^3", "p1_batch_256", "q1_poisson_64x64", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving: length of the arrival trace")
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-outstanding", type=int, default=64,
+                    help="serving: the client waits while this many requests are unanswered")
+    ap.add_argument("--serve-seq", type=int, default=6,
+                    help="serving: requests of the trace replayed sequentially in FP64 (baseline)")
     ap.add_argument("--nrhs", type=int, default=None, help="default: the workload's")
     ap.add_argument("--m", type=int, default=1024, help="elements per side (1024 = the workload)")
     ap.add_argument("--n-c", type=int, default=64)
@@ -504,6 +512,88 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_serving(args):
+    """Serving stream: Poisson arrivals (mean 200 requests/s, seed 6) over 24 matrices --
+    8 each of the Q1 64^2, Q1 1024^2 (lognormal sigma 1) and hex 64^3 (lognormal sigma 0.5)
+    sizes with coefficient seeds 11-18, 21-28, 31-38 -- picked uniformly (seed 7), 1-64
+    right-hand sides each (seed 7), served by hm_server (factor on first miss, resident
+    after, 150 GB HBM budget, continuous batching per matrix).  The client submits at the
+    arrival times but holds back while `--serve-outstanding` requests are unanswered (host
+    memory for the answers).  Baseline: the first `--serve-seq` requests replayed one
+    after another through an FP64 server with one worker."""
+    import numpy as np
+
+    import paper_1410_2697_gb300 as hm
+    from fixtures import hex_cube, lognormal_coefficients, q1_square
+    mats = ([q1_square(64, lognormal_coefficients(64 * 64, 1.0, seed=11 + i)) for i in range(8)]
+            + [q1_square(1024, lognormal_coefficients(1024 * 1024, 1.0, seed=21 + i)) for i in range(8)]
+            + [hex_cube(64, lognormal_coefficients(64 ** 3, 0.5, seed=31 + i)) for i in range(8)])
+    rng_a = np.random.Generator(np.random.PCG64(6))
+    rng_p = np.random.Generator(np.random.PCG64(7))
+    t, trace = 0.0, []
+    while True:
+        t += rng_a.exponential(1.0 / 200.0)
+        if t > args.serve_seconds:
+            break
+        trace.append((t, int(rng_p.integers(0, len(mats))), int(rng_p.integers(1, 65))))
+    # one read-only block of right-hand sides per matrix; request k uses its first nrhs columns
+    rhs = [np.asfortranarray(np.random.Generator(np.random.PCG64(100 + i)).uniform(-1, 1, (m.n, 64)))
+           for i, m in enumerate(mats)]
+
+    def serve(precision, nworkers, reqs, sequential):
+        o = hm.hm_default_opts()
+        o.precision = precision
+        o.hbm_budget = 150 * (1 << 30)
+        srv = hm.hm_server_create(o, nworkers=nworkers, max_batch_rhs=64)
+        ids = [hm.hm_server_add_matrix(srv, m, 1e-4) for m in mats]
+        pending, lat, worst, t0 = [], [], 0.0, time.perf_counter()
+
+        def finish(item):
+            nonlocal worst
+            mi, x, rid = item
+            r = hm.hm_server_wait(srv, rid)
+            assert r["status"] == 0, r
+            lat.append(r["latency_ms"])
+            worst = max(worst, r["relres"])
+
+        for (ta, mi, nr) in reqs:
+            if not sequential:
+                while time.perf_counter() - t0 < ta:
+                    time.sleep(0.0002)
+                while len(pending) >= args.serve_outstanding:
+                    finish(pending.pop(0))
+            x = np.zeros((mats[mi].n, nr), order="F")
+            pending.append((mi, x, hm.hm_server_submit(srv, ids[mi], rhs[mi][:, :nr], x)))
+            if sequential:
+                finish(pending.pop(0))
+        while pending:
+            finish(pending.pop(0))
+        elapsed = time.perf_counter() - t0
+        st = hm.hm_server_get_stats(srv)
+        hm.hm_server_destroy(srv)
+        return elapsed, st, lat, worst
+
+    el, st, lat, worst = serve(hm.HM_PREC_MIXED, args.serve_workers, trace, False)
+    k = min(args.serve_seq, len(trace))
+    el64, st64, lat64, _ = serve(hm.HM_PREC_FP64, 1, trace[:k], True)
+    rhs_total = sum(nr for _, _, nr in trace)
+    return {
+        "metric": METRIC, "value": len(trace) / el, "unit": "requests/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 factor/apply + f64 GMRES", "data": "synthetic",
+        "config": {"workload": "serving", "matrices": "8 x Q1 64^2, 8 x Q1 1024^2, 8 x hex 64^3",
+                   "arrivals": f"Poisson 200/s for {args.serve_seconds} s ({len(trace)} requests, "
+                               f"{rhs_total} right-hand sides)", "rtol": RTOL, "tol": 1e-4,
+                   "workers": args.serve_workers, "max_batch_rhs": 64, "hbm_budget_gb": 150,
+                   "client_outstanding_cap": args.serve_outstanding},
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "rhs_per_s": rhs_total / el, "relres": worst,
+        "server": {k2: st[k2] for k2 in ("completed", "failed", "batches", "batched_rhs", "factorizations",
+                                          "evictions", "device_bytes")},
+        "fp64_sequential": {"value": k / el64, "unit": "requests/s", "requests": k,
+                            "p50_ms": st64["p50_ms"], "p99_ms": st64["p99_ms"]},
+    }
+
+
 def run_probe(args):
     """Small fixed driver for ncu captures (see --probe)."""
     import numpy as np
@@ -556,6 +646,10 @@ def main():
         line = run_reference(args, rank, world)
         if line is not None:
             print(json.dumps(line))
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            print(json.dumps(run_serving(args)))
         return
     # The host oracle runs before any GPU work in this process (no fork after CUDA init).
     cpu = None

@@ -179,7 +179,10 @@ int hm_solve(hm_sys_t sys, int32_t nrhs, const double* b, double rtol, int32_t m
              double* x, hm_solve_info* info);
 
 /* One preconditioner application z = M^{-1} r (Eqs. upward / downward with the HODLR
-   pivot solves of Section 4.2.2); r, z n x nrhs FP64, original numbering.             */
+   pivot solves of Section 4.2.2); r, z n x nrhs FP64, original numbering.  The apply
+   workspace is built per right-hand-side count on first use (a system keeps the four
+   most recently used ones); an apply whose input buffer repeats is replayed from a
+   captured CUDA graph.                                                                 */
 int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
 
 /*
@@ -193,6 +196,7 @@ int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
  *   Limits    n * nrhs <= 262144 (HM_ERR_CAPACITY beyond).  The per-nrhs workspace of
  *             the system must exist already: make one hm_precond_apply or hm_solve call
  *             with the same nrhs first (HM_ERR_STATE otherwise; that call allocates).
+ *             A system keeps the workspaces of its four most recently used nrhs values.
  *   Scratch   the per-call temporaries live in one file-scope device array of 6 MiB that
  *             every GPU loading the library holds until the process exits.  All calls
  *             share it, so calls that overlap on the GPU (from several threads or

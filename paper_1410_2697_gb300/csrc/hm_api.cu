@@ -116,7 +116,7 @@ const char* prof_cat_name(int c) {
 static void destroy_sys(hm_sys_s* sys) {
   if (!sys) return;
   cudaStreamSynchronize(sys->ctx->stream);
-  for (auto& kv : sys->solve_plans) (void)kv;
+  for (auto& kv : sys->solve_plans) dev_free_all(sys->ctx, &kv.second->allocs);
   sys->solve_plans.clear();
   dev_free_all(sys->ctx, &sys->gm.allocs);
   if (sys->gm.h_res) cudaFreeHost(sys->gm.h_res);

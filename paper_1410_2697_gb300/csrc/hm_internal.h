@@ -274,6 +274,8 @@ struct SolvePlan {
   int64_t* d_fvoff = nullptr;
   int64_t* d_yvoff = nullptr;   // per front: offset of y (np x nrhs) in the scratch, -1 if dense
   // captured apply (graph of the launches for input graph_in) and the last input seen
+  std::vector<void*> allocs;    // device memory of this plan (freed when it is dropped)
+  int64_t last_use = 0;
   cudaGraphExec_t graph_exec = nullptr;
   const void* graph_in = nullptr;
   const void* last_in = nullptr;
@@ -393,6 +395,7 @@ struct hm_sys_s {
   bool factored = false;
   double tol = 0;
   std::map<int, std::unique_ptr<hm::SolvePlan>> solve_plans;
+  int64_t plan_clock = 0;
   std::vector<void*> allocs;
   // GMRES workspace (grown on demand)
   struct Gm {
@@ -448,7 +451,12 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
                  const int32_t* block_ptr);
 int build_plan(hm_sys_s* sys);
 int factor_impl(hm_sys_s* sys, const double* d_values, double tol);
+// Apply plans are kept for at most this many right-hand-side counts per system.
+constexpr int kMaxSolvePlans = 4;
 int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out);
+// Frees the per-right-hand-side-count state of a system (apply plans, GMRES workspace);
+// it is rebuilt on the next solve.
+void release_solve_state(hm_sys_s* sys);
 // z (T, n x nrhs, ld n, new numbering) = M^{-1} r (T, same layout)
 int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 int solve_setup(int max_smem);

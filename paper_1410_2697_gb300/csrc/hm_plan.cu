@@ -468,10 +468,34 @@ int build_plan(hm_sys_s* sys) {
 // ------------------------------------------------------------------------------------
 // Solve plan for nrhs right-hand sides.
 // ------------------------------------------------------------------------------------
+void release_solve_state(hm_sys_s* sys) {
+  cudaStreamSynchronize(sys->ctx->stream);
+  for (auto& kv : sys->solve_plans) dev_free_all(sys->ctx, &kv.second->allocs);
+  sys->solve_plans.clear();
+  dev_free_all(sys->ctx, &sys->gm.allocs);
+  if (sys->gm.h_res) cudaFreeHost(sys->gm.h_res);
+  sys->gm.h_res = nullptr;
+  sys->gm.nrhs = 0;
+  sys->gm.m = 0;
+}
+
 int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   auto it = sys->solve_plans.find(nrhs);
   sys->ctx->last_nrhs = nrhs;
-  if (it != sys->solve_plans.end()) { *out = it->second.get(); return HM_OK; }
+  if (it != sys->solve_plans.end()) {
+    it->second->last_use = ++sys->plan_clock;
+    *out = it->second.get();
+    return HM_OK;
+  }
+  // keep at most kMaxSolvePlans right-hand-side counts: drop the least recently used
+  if ((int)sys->solve_plans.size() >= kMaxSolvePlans) {
+    auto lru = sys->solve_plans.begin();
+    for (auto jt = sys->solve_plans.begin(); jt != sys->solve_plans.end(); ++jt)
+      if (jt->second->last_use < lru->second->last_use) lru = jt;
+    HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));  // no launch of it may still run
+    dev_free_all(sys->ctx, &lru->second->allocs);
+    sys->solve_plans.erase(lru);
+  }
   host_mark("solve plan: enter");
   Plan& P = sys->plan;
   const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
@@ -499,11 +523,11 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     sb += (int64_t)h.np * nrhs;
   }
   sp->sb_total = sb;
-  HM_TRY(dev_alloc(sys, &sp->d_fv, (size_t)std::max<int64_t>(fv, 1) * es));
-  HM_TRY(dev_alloc(sys, &sp->d_sb, (size_t)std::max<int64_t>(sb, 1) * es));
-  HM_TRY(dev_alloc(sys, (void**)&sp->d_fvoff, (size_t)nf * 8));
-  HM_TRY(dev_alloc(sys, (void**)&sp->d_yvoff, (size_t)nf * 8));
-  HM_TRY(dev_alloc(sys, &sp->d_xfix, (size_t)std::max<int64_t>((int64_t)sys->n * nrhs, 1) * es));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_fv, (size_t)std::max<int64_t>(fv, 1) * es));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_sb, (size_t)std::max<int64_t>(sb, 1) * es));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_fvoff, (size_t)nf * 8));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_yvoff, (size_t)nf * 8));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_xfix, (size_t)std::max<int64_t>((int64_t)sys->n * nrhs, 1) * es));
   HM_CUDA(cudaMemcpyAsync(sp->d_fvoff, sp->fv_off.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
                           sys->ctx->stream));
   HM_CUDA(cudaMemcpyAsync(sp->d_yvoff, yvoff.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
@@ -624,13 +648,14 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     lp.down1 = tb.add_gemm(d1);
     lp.down2 = tb.add_gemm(d2);
   }
-  HM_TRY(dev_alloc(sys, &sp->d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
-  HM_TRY(dev_alloc(sys, (void**)&sp->d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));
   HM_CUDA(cudaMemsetAsync(sp->d_split_cnt, 0, sizeof(unsigned) * std::max(tb.split_slots, 1),
                           sys->ctx->stream));
-  HM_TRY(dev_alloc(sys, (void**)&sp->d_tasks, std::max<size_t>(tb.host.size(), 16)));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_tasks, std::max<size_t>(tb.host.size(), 16)));
   HM_CUDA(cudaMemcpyAsync(sp->d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));
+  sp->last_use = ++sys->plan_clock;
   *out = sp.get();
   sys->solve_plans[nrhs] = std::move(sp);
   host_mark("solve plan: built");

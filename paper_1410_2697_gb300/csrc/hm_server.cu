@@ -61,6 +61,7 @@ struct SrvWorker {
   std::thread th;
   std::deque<SrvRequest*> q;
   int64_t clock = 0;
+  SrvMatrix* last = nullptr;  // matrix of the previous batch
 };
 
 }  // namespace hm
@@ -98,6 +99,7 @@ static bool evict_one(hm_server_s* S, int w, int keep) {
   hm_destroy(victim->sys);
   victim->sys = nullptr;
   victim->bytes = 0;
+  if (S->workers[w].last == victim) S->workers[w].last = nullptr;
   return true;
 }
 
@@ -157,6 +159,9 @@ static void worker_loop(hm_server_s* S, int w) {
       Mp = S->matrices[m].get();
     }
     SrvMatrix& M = *Mp;
+    // one system's transient solve state (apply plans, GMRES workspace) per worker
+    if (W.last && W.last != Mp && W.last->sys) release_solve_state(W.last->sys);
+    W.last = Mp;
     int st = make_resident(S, w, m, M);
     int nrhs = 0;
     double rtol = 1.0;
