@@ -259,7 +259,8 @@ const char* hm_last_error(void);
  * until evicted (least recently used first) to admit another matrix within the budget.
  * A free worker takes its oldest waiting request and joins every waiting request for
  * the same matrix, up to max_batch_rhs right-hand sides, into one hm_solve (continuous
- * batching); workers run concurrently, so different matrices overlap on the GPU.  Each
+ * batching), in column chunks that keep the GMRES workspace within a quarter of the
+ * worker's budget; workers run concurrently, so different matrices overlap on the GPU.  Each
  * right-hand side is its own GMRES instance, so a request's answer equals (to rounding)
  * the answer it gets alone.  Latency = completion - submission, host clock.
  *

@@ -177,10 +177,27 @@ static void worker_loop(hm_server_s* S, int w) {
         std::copy(r->b, r->b + n * r->nrhs, B.begin() + n * c);
         c += r->nrhs;
       }
-      st = hm_solve(M.sys, nrhs, B.data(), rtol, 4000, X.data(), &info);
-      if (st == HM_ERR_OUT_OF_MEMORY) {  // workspace for this batch size: make room once
-        while (st == HM_ERR_OUT_OF_MEMORY && evict_one(S, w, m))
-          st = hm_solve(M.sys, nrhs, B.data(), rtol, 4000, X.data(), &info);
+      // The GMRES workspace grows with n x right-hand sides ((2 restart + 6) FP64 vectors
+      // per column); columns are solved in chunks that keep it within a quarter of the
+      // worker's budget, so large systems do not evict their neighbours for workspace.
+      const hm_opts& o = W.ctx->opts;
+      int chunk = nrhs;
+      if (o.hbm_budget) {
+        const double per_col = (2.0 * o.restart + 6.0) * 8.0 * (double)n;
+        chunk = std::max(1, std::min(nrhs, (int)(0.25 * (double)o.hbm_budget / per_col)));
+      }
+      info.converged = 1;
+      for (int c0 = 0; c0 < nrhs && (st == HM_OK || st == HM_ERR_NO_CONVERGENCE); c0 += chunk) {
+        const int nc = std::min(chunk, nrhs - c0);
+        hm_solve_info ci{};
+        int cs = hm_solve(M.sys, nc, B.data() + n * c0, rtol, 4000, X.data() + n * c0, &ci);
+        while (cs == HM_ERR_OUT_OF_MEMORY && evict_one(S, w, m))  // workspace: make room
+          cs = hm_solve(M.sys, nc, B.data() + n * c0, rtol, 4000, X.data() + n * c0, &ci);
+        if (st == HM_OK) st = cs;
+        info.iters = std::max(info.iters, ci.iters);
+        info.restarts = std::max(info.restarts, ci.restarts);
+        info.relres = std::max(info.relres, ci.relres);
+        info.converged = info.converged && ci.converged;
       }
       if (st == HM_OK || st == HM_ERR_NO_CONVERGENCE) {
         c = 0;
