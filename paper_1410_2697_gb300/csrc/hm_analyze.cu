@@ -314,7 +314,7 @@ __global__ void k_nd_perm(const int32_t* coords, int n, int dim, NdTree t0, cons
 __global__ void k_nd_forest(const NdBlock* blks, const int* first_t, const int* parent_t, const int* level_t,
                             int32_t* first, int32_t* parent, int32_t* level) {
   const NdBlock bk = blks[blockIdx.x];
-  for (int q = threadIdx.x; q < bk.nodes; q += blockDim.x) {
+  for (int q = blockIdx.y * blockDim.x + threadIdx.x; q < bk.nodes; q += gridDim.y * blockDim.x) {
     const int src = bk.node_off + q, dst = bk.forest_off + q;
     first[dst] = bk.unk_off + first_t[src];
     parent[dst] = parent_t[src] >= 0 ? bk.forest_off + parent_t[src] : -1;
@@ -435,17 +435,19 @@ __global__ void k_prow_fill(const int64_t* rowptr, const int32_t* colidx, const 
 // Candidates are gathered in shared memory, bitonic-sorted and de-duplicated; the list
 // is appended to the I^f arena at an atomically claimed offset.
 // ------------------------------------------------------------------------------------
-constexpr int kSymCap = 32768;
+constexpr int kSymCap = 32768;  // largest candidate list (one CTA's shared memory)
+constexpr int kSymFast = 2048;  // candidate capacity of the first pass
+constexpr int kSymSlowCtas = 152;
 
-__global__ void __launch_bounds__(1024) k_symbolic_level(
-    const int* fronts, const int32_t* first, const int32_t* child_ptr, const int32_t* child_list,
-    const int64_t* prowptr, const int32_t* pcol, int32_t* nupd, int64_t* ifoff, int32_t* iflist,
-    unsigned long long* cursor, int64_t capacity, int* err) {
-  extern __shared__ int buf[];
+// I_p^f of front q with a candidate buffer of `cap` entries in shared memory.  Returns
+// false (nothing written) if the candidate list does not fit.  Every thread calls it.
+__device__ bool symbolic_front(int q, int* buf, int cap, const int32_t* first, const int32_t* child_ptr,
+                               const int32_t* child_list, const int64_t* prowptr, const int32_t* pcol,
+                               int32_t* nupd, int64_t* ifoff, int32_t* iflist, unsigned long long* cursor,
+                               int64_t capacity, int* err) {
   __shared__ int cnt;
   __shared__ int sh[40];
   __shared__ long long s_off;
-  const int q = fronts[blockIdx.x];
   const int b = first[q], e = first[q + 1];
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(1024) k_symbolic_level(
       const int j = pcol[k];
       if (j >= e) {
         const int pos = atomicAdd(&cnt, 1);
-        if (pos < kSymCap) buf[pos] = j;
+        if (pos < cap) buf[pos] = j;
       }
     }
   }
@@ -469,16 +471,14 @@ __global__ void __launch_bounds__(1024) k_symbolic_level(
       const int j = iflist[o + t];
       if (j >= e) {
         const int pos = atomicAdd(&cnt, 1);
-        if (pos < kSymCap) buf[pos] = j;
+        if (pos < cap) buf[pos] = j;
       }
     }
   }
   __syncthreads();
   const int total = cnt;
-  if (total > kSymCap) {
-    if (threadIdx.x == 0) raise_error(err, HM_ERR_CAPACITY, q, total);
-    return;
-  }
+  __syncthreads();  // cnt is reused by the next front of a persistent CTA
+  if (total > cap) return false;
   int n2 = 1;
   while (n2 < total) n2 <<= 1;
   for (int t = total + threadIdx.x; t < n2; t += blockDim.x) buf[t] = INT_MAX;
@@ -518,11 +518,49 @@ __global__ void __launch_bounds__(1024) k_symbolic_level(
     ifoff[q] = (int64_t)off;
   }
   __syncthreads();
-  if (s_off < 0) return;
-  int w = pre;
-  for (int t = t0; t < min(t0 + per, n2); ++t) {
-    const int v = buf[t];
-    if (v != INT_MAX && (t == 0 || buf[t - 1] != v)) iflist[s_off + w++] = v;
+  if (s_off >= 0) {
+    int w = pre;
+    for (int t = t0; t < min(t0 + per, n2); ++t) {
+      const int v = buf[t];
+      if (v != INT_MAX && (t == 0 || buf[t - 1] != v)) iflist[s_off + w++] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// First pass of a level: one CTA per front with a small candidate buffer (many CTAs per
+// SM); fronts whose candidates do not fit are queued for the second pass.
+__global__ void __launch_bounds__(512) k_symbolic_fast(
+    const int* fronts, const int32_t* first, const int32_t* child_ptr, const int32_t* child_list,
+    const int64_t* prowptr, const int32_t* pcol, int32_t* nupd, int64_t* ifoff, int32_t* iflist,
+    unsigned long long* cursor, int64_t capacity, int* deferred, int* ndeferred, int* err) {
+  __shared__ int buf[kSymFast];
+  const int q = fronts[blockIdx.x];
+  if (!symbolic_front(q, buf, kSymFast, first, child_ptr, child_list, prowptr, pcol, nupd, ifoff, iflist,
+                      cursor, capacity, err) &&
+      threadIdx.x == 0)
+    deferred[atomicAdd(ndeferred, 1)] = q;
+}
+
+// Second pass: persistent CTAs with the full buffer take the queued fronts.
+__global__ void __launch_bounds__(1024) k_symbolic_slow(
+    const int32_t* first, const int32_t* child_ptr, const int32_t* child_list, const int64_t* prowptr,
+    const int32_t* pcol, int32_t* nupd, int64_t* ifoff, int32_t* iflist, unsigned long long* cursor,
+    int64_t capacity, const int* deferred, const int* ndeferred, int* next, int* err) {
+  extern __shared__ int bufl[];
+  __shared__ int idx;
+  for (;;) {
+    if (threadIdx.x == 0) idx = atomicAdd(next, 1);
+    __syncthreads();
+    const int i = idx;
+    __syncthreads();
+    if (i >= *ndeferred) return;
+    const int q = deferred[i];
+    if (!symbolic_front(q, bufl, kSymCap, first, child_ptr, child_list, prowptr, pcol, nupd, ifoff, iflist,
+                        cursor, capacity, err) &&
+        threadIdx.x == 0)
+      raise_error(err, HM_ERR_CAPACITY, q, kSymCap);
   }
 }
 
@@ -758,8 +796,10 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_level_f, sizeof(int32_t) * nf));
     {
       ProfScope ps(sys->ctx, PC_ND, Work{0.0, (4.0 * dim + 8.0) * n + 24.0 * nf}, 2);
-      k_nd_forest<<<nblocks, 256, 0, s>>>(d_blks, d_first_t, d_parent_t, d_level_t, d_first_f, d_parent_f,
-                                          d_level_f);
+      int maxnodes = 1;
+      for (const auto& bk : blks) maxnodes = std::max(maxnodes, bk.nodes);
+      k_nd_forest<<<dim3(nblocks, (maxnodes + 255) / 256), 256, 0, s>>>(d_blks, d_first_t, d_parent_t, d_level_t,
+                                                                       d_first_f, d_parent_f, d_level_f);
       k_nd_perm<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, t, sys->d_seg_ptr, nblocks, d_blks,
                                                 sys->d_perm, sys->d_iperm);
     }
@@ -859,20 +899,29 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   HM_TRY(dev_alloc(sys, (void**)&sys->d_ifoff, sizeof(int64_t) * (nf + 1)));
   unsigned long long* cursor = nullptr;
   HM_TRY(tmp_alloc(sys, &tmp, (void**)&cursor, sizeof(unsigned long long)));
-  HM_CUDA(cudaFuncSetAttribute(k_symbolic_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HM_CUDA(cudaFuncSetAttribute(k_symbolic_slow, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kSymCap * (int)sizeof(int)));  // 128 KB + < 1 KB static
+  // per level: deferred-front count and queue cursor, then the queue itself
+  int* dq = nullptr;
+  HM_TRY(tmp_alloc(sys, &tmp, (void**)&dq, sizeof(int) * (2 * (size_t)(maxlev + 1) + nf)));
   int64_t capacity = (int64_t)32 * n + 65536;
   for (int attempt = 0; attempt < 4; ++attempt) {
     HM_TRY(dev_alloc(sys, (void**)&sys->d_iflist, sizeof(int32_t) * capacity));
     HM_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
     HM_CUDA(cudaMemsetAsync(sys->d_err, 0, 4 * sizeof(int), s));
+    HM_CUDA(cudaMemsetAsync(dq, 0, sizeof(int) * 2 * (size_t)(maxlev + 1), s));
+    int* queue = dq + 2 * (maxlev + 1);
     for (int L = 0; L <= maxlev; ++L) {
       const int cntL = lvl_begin[L + 1] - lvl_begin[L];
       if (cntL == 0) continue;
-      ProfScope ps(sys->ctx, PC_SYMBOLIC, Work{});
-      k_symbolic_level<<<cntL, 1024, kSymCap * sizeof(int), s>>>(
-          d_order + lvl_begin[L], sys->d_first, sys->d_child_ptr, sys->d_child_list, sys->d_prowptr,
-          sys->d_pcol, sys->d_nupd, sys->d_ifoff, sys->d_iflist, cursor, capacity, sys->d_err);
+      ProfScope ps(sys->ctx, PC_SYMBOLIC, Work{}, 2);
+      k_symbolic_fast<<<cntL, 512, 0, s>>>(d_order + lvl_begin[L], sys->d_first, sys->d_child_ptr,
+                                            sys->d_child_list, sys->d_prowptr, sys->d_pcol, sys->d_nupd,
+                                            sys->d_ifoff, sys->d_iflist, cursor, capacity, queue,
+                                            dq + 2 * L, sys->d_err);
+      k_symbolic_slow<<<std::min(cntL, kSymSlowCtas), 1024, kSymCap * sizeof(int), s>>>(
+          sys->d_first, sys->d_child_ptr, sys->d_child_list, sys->d_prowptr, sys->d_pcol, sys->d_nupd,
+          sys->d_ifoff, sys->d_iflist, cursor, capacity, queue, dq + 2 * L, dq + 2 * L + 1, sys->d_err);
     }
     int herr[4];
     HM_CUDA(cudaMemcpyAsync(herr, sys->d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
