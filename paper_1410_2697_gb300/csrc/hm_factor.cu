@@ -19,11 +19,14 @@ namespace hm {
 template <typename T>
 __global__ void k_scatter(const double* __restrict__ vals, const int64_t* __restrict__ psrc,
                           const int64_t* __restrict__ amap, int64_t nnz, T* __restrict__ F,
-                          double* __restrict__ pvals) {
+                          double* __restrict__ pvals, float2* __restrict__ pvals2) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
        k += (int64_t)gridDim.x * blockDim.x) {
     const double v = vals[psrc[k]];
     pvals[k] = v;
+    // v = hi + lo with hi, lo FP32 (48 of the 53 bits), for the double-float SpMV
+    const float hi = (float)v;
+    pvals2[k] = make_float2(hi, (float)(v - (double)hi));
     const int64_t d = amap[k];
     if (d >= 0) F[d] = (T)v;
   }
@@ -129,7 +132,7 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
     ProfScope ps(ctx, PC_SCATTER, Work{0.0, nnz * 32.0 + 0.5 * nnz * es});
     const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
     k_scatter<T><<<std::max(grid, 1), 256, 0, s>>>(d_values, sys->d_psrc, sys->d_amap, nnz, F,
-                                                  sys->d_pvals);
+                                                  sys->d_pvals, sys->d_pvals2);
   }
   for (int l = P.nlevels - 1; l >= 0; --l) {
     const LevelFactorPlan& lp = P.levels[l];

@@ -3,7 +3,8 @@
 // accuracy).  nrhs systems run in lockstep; each keeps its own Krylov basis.
 //
 //   V_j  (FP64)  Krylov vectors; Z_j = M^{-1} V_j stored in the factor precision (the
-//               preconditioned vectors are exactly representable there);
+//               preconditioned vectors are exactly representable there), row-major (the
+//               right-hand sides of a row side by side) for the multi-RHS SpMV;
 //   w = A Z_j in FP64; Arnoldi by classical Gram-Schmidt applied twice (CGS2) with
 //   block partial sums reduced in a fixed order (deterministic); Givens rotations and
 //   the least-squares solve on the device; x += Z y at the end of a cycle; the TRUE
@@ -52,6 +53,111 @@ __global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rowptr
 }
 
 static dim3 spmv_grid(int n, int nrhs) { return dim3((n + 255) / 256, (nrhs + kSpmvR - 1) / kSpmvR); }
+
+// Double-float SpMV for FP32 directions: y = A z with A = a_hi + a_lo (FP32 pair, 48 bits
+// of each FP64 entry) and z exact in FP32.  Every product a_hi z is split exactly into
+// p + e (FMA), a_lo z is added to the error term, and the row sum is carried as an
+// unevaluated FP32 pair (hi, lo) with Knuth's two-sum, so the result carries about 2^-46
+// relative error per term (native FP64: 2^-53) at FP32 instruction rates: GB300 issues
+// FP64 FMAs at 1/64 of the FP32 rate, and this product is the inner loop of every GMRES
+// iteration.  The convergence test keeps the native FP64 residual b - A x.
+constexpr int kSpmvDF = 16;
+
+// (the _rn intrinsics keep the compiler from contracting these into FMAs, which would
+// break the exactness of the error terms)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float p, float e) {
+  const float s = __fadd_rn(hi, p);
+  const float bv = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+__global__ void __launch_bounds__(256) k_spmv_df(const int64_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ col,
+                                                 const float2* __restrict__ val2, int n, int nrhs,
+                                                 const float* __restrict__ z, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int r0 = blockIdx.y * kSpmvDF;
+  const int nr = min(kSpmvDF, nrhs - r0);
+  const int64_t kb = rowptr[i], ke = rowptr[i + 1];
+  float hi[kSpmvDF], lo[kSpmvDF];
+#pragma unroll
+  for (int q = 0; q < kSpmvDF; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+  const bool vec = nr == kSpmvDF && (nrhs & 3) == 0;
+  for (int64_t k = kb; k < ke; ++k) {
+    const float2 a = val2[k];
+    const float* zc = z + (int64_t)col[k] * nrhs + r0;
+    float zz[kSpmvDF];
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < kSpmvDF / 4; ++q) {
+        const float4 t = reinterpret_cast<const float4*>(zc)[q];
+        zz[4 * q] = t.x; zz[4 * q + 1] = t.y; zz[4 * q + 2] = t.z; zz[4 * q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kSpmvDF; ++q) zz[q] = q < nr ? zc[q] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kSpmvDF; ++q) {
+      const float p = __fmul_rn(a.x, zz[q]);
+      const float e = fmaf(a.y, zz[q], fmaf(a.x, zz[q], -p));
+      df_add(hi[q], lo[q], p, e);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kSpmvDF; ++q)
+    if (q < nr) y[i + (int64_t)(r0 + q) * n] = (double)hi[q] + (double)lo[q];
+}
+
+// y[r] = A z[r] with z stored row-major (the nrhs values of a row contiguous, as the
+// preconditioned directions Z_j are kept): one thread per row and group of kSpmvRM
+// right-hand sides, so a row's column indices and values are read once per group and
+// each neighbour's values arrive as one contiguous run.
+constexpr int kSpmvRM = 16;
+
+template <typename ZT>
+__global__ void __launch_bounds__(256) k_spmv_rm(const int64_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ col,
+                                                 const double* __restrict__ val, int n, int nrhs,
+                                                 const ZT* __restrict__ z, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int r0 = blockIdx.y * kSpmvRM;
+  const int nr = min(kSpmvRM, nrhs - r0);
+  const int64_t kb = rowptr[i], ke = rowptr[i + 1];
+  double s[kSpmvRM];
+#pragma unroll
+  for (int q = 0; q < kSpmvRM; ++q) s[q] = 0.0;
+  if (nr == kSpmvRM && (nrhs & 3) == 0 && sizeof(ZT) == 4) {
+    // 16 FP32 values per neighbour as four 16-byte loads (rows are 16-byte aligned)
+    for (int64_t k = kb; k < ke; ++k) {
+      const double v = val[k];
+      const float4* zc = reinterpret_cast<const float4*>(z + (int64_t)col[k] * nrhs + r0);
+#pragma unroll
+      for (int q = 0; q < kSpmvRM / 4; ++q) {
+        const float4 t = zc[q];
+        s[4 * q] = fma(v, (double)t.x, s[4 * q]);
+        s[4 * q + 1] = fma(v, (double)t.y, s[4 * q + 1]);
+        s[4 * q + 2] = fma(v, (double)t.z, s[4 * q + 2]);
+        s[4 * q + 3] = fma(v, (double)t.w, s[4 * q + 3]);
+      }
+    }
+  } else {
+    for (int64_t k = kb; k < ke; ++k) {
+      const double v = val[k];
+      const ZT* zc = z + (int64_t)col[k] * nrhs + r0;
+#pragma unroll
+      for (int q = 0; q < kSpmvRM; ++q)
+        if (q < nr) s[q] = fma(v, (double)zc[q], s[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kSpmvRM; ++q)
+    if (q < nr) y[i + (int64_t)(r0 + q) * n] = s[q];
+}
 
 // Row chunks: every vector kernel runs on grid (nchunks, nrhs); chunk c covers rows
 // [crow[c], crow[c+1]) of one block cseg[c] (chunks never straddle blocks), so a CTA
@@ -187,7 +293,7 @@ __global__ void k_backsolve(const double* __restrict__ H, const double* __restri
   for (int i = L; i < m; ++i) yr[i] = 0.0;
 }
 
-// x[r] += sum_{j < len[inst]} Z_j[r] y[inst][j]
+// x[r] += sum_{j < len[inst]} Z_j[r] y[inst][j]   (Z_j row-major: element (k, r) at k nrhs + r)
 template <typename ZT>
 __global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z, const double* __restrict__ y,
                            const int* __restrict__ len, int n, int nrhs, int m, const int* __restrict__ crow,
@@ -201,7 +307,7 @@ __global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z, con
   double* xr = x + (int64_t)r * n;
   for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) {
     double s = xr[k];
-    for (int j = 0; j < L; ++j) s = fma((double)Z[((int64_t)j * nrhs + r) * n + k], ys[j], s);
+    for (int j = 0; j < L; ++j) s = fma((double)Z[((int64_t)j * n + k) * nrhs + r], ys[j], s);
     xr[k] = s;
   }
 }
@@ -359,12 +465,16 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
         ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, (8.0 + sizeof(T)) * nn});
         launch_cast_to<T>(Vj, (T*)G.wT, nn, s);
       }
-      HM_TRY(apply_impl(sys, nrhs, G.wT, Zj));
+      HM_TRY(apply_impl_rowmajor(sys, nrhs, G.wT, Zj));  // Z_j row-major
       {
         ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs,
                                              12.0 * sys->nnz + 8.0 * n + (8.0 + sizeof(T)) * nn});
-        k_spmv<T><<<spmv_grid(n, nrhs), 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
-                                                  Zj, n, G.w, n, nullptr, 0);
+        if (sizeof(T) == 4)
+          k_spmv_df<<<dim3((n + 255) / 256, (nrhs + kSpmvDF - 1) / kSpmvDF), 256, 0, s>>>(
+              sys->d_prowptr, sys->d_pcol, sys->d_pvals2, n, nrhs, (const float*)Zj, G.w);
+        else
+          k_spmv_rm<T><<<dim3((n + 255) / 256, (nrhs + kSpmvRM - 1) / kSpmvRM), 256, 0, s>>>(
+              sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs, Zj, G.w);
       }
       double* h1 = G.hv;
       double* h2 = G.hv + (int64_t)ninst * stride;

@@ -391,6 +391,7 @@ struct hm_sys_s {
   void* d_tb = nullptr;      // T
   int* d_ranks = nullptr;
   double* d_pvals = nullptr; // permuted A values (FP64) for SpMV
+  float2* d_pvals2 = nullptr;  // the same split as FP32 hi + lo (double-float SpMV)
   int* d_err = nullptr;      // device error word (4 ints)
   bool factored = false;
   double tol = 0;
@@ -459,6 +460,8 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out);
 void release_solve_state(hm_sys_s* sys);
 // z (T, n x nrhs, ld n, new numbering) = M^{-1} r (T, same layout)
 int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
+// As apply_impl, with z written row-major (element (i, r) at i nrhs + r).
+int apply_impl_rowmajor(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 int solve_setup(int max_smem);
 int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
                double* d_x, hm_solve_info* info);

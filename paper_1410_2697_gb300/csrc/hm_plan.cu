@@ -212,6 +212,7 @@ int build_plan(hm_sys_s* sys) {
   HM_TRY(A(&sys->d_tb, P.tb_total, es));
   HM_TRY(A((void**)&sys->d_ranks, P.nrank, 4));
   HM_TRY(A((void**)&sys->d_pvals, sys->nnz, 8));
+  HM_TRY(A((void**)&sys->d_pvals2, sys->nnz, 8));
   HM_TRY(A((void**)&P.d_front_off, nf, 8));
   HM_TRY(A((void**)&P.d_nhat, nf, 4));
   HM_TRY(A((void**)&P.d_np, nf, 4));

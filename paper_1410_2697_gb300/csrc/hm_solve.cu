@@ -427,8 +427,25 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
 // the same staging buffer every iteration) is captured once into a CUDA graph and
 // replayed: its ~10^2 dependent launches then cost one graph launch.  The first apply
 // with a new input runs eagerly; with the launch profiler on, applies always run eagerly.
+// dst (row-major n x nrhs: element (i, r) at i nrhs + r) = src (column-major, ld n),
+// through 32 x 32 shared-memory tiles so both sides are coalesced.
 template <typename T>
-static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
+__global__ void k_to_rowmajor(const T* __restrict__ src, T* __restrict__ dst, int n, int nrhs) {
+  __shared__ T tile[32][33];
+  const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int i = i0 + threadIdx.x, r = r0 + rr;
+    if (i < n && r < nrhs) tile[rr][threadIdx.x] = src[i + (int64_t)r * n];
+  }
+  __syncthreads();
+  for (int ii = threadIdx.y; ii < 32; ii += blockDim.y) {
+    const int i = i0 + ii, r = r0 + threadIdx.x;
+    if (i < n && r < nrhs) dst[(int64_t)i * nrhs + r] = tile[threadIdx.x][ii];
+  }
+}
+
+template <typename T>
+static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout, bool rowmajor_out = false) {
   SolvePlan* sp = nullptr;
   HM_TRY(get_solve_plan(sys, nrhs, &sp));
   hm_ctx_s* ctx = sys->ctx;
@@ -460,8 +477,12 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout) {
   }
   sp->last_in = win;
   T* xfix = (T*)sp->d_xfix;
-  if (xout != xfix)
+  if (rowmajor_out) {
+    ProfScope ps(ctx, PC_VECTOR, Work{0.0, 2.0 * sizeof(T) * (double)sys->n * nrhs});
+    k_to_rowmajor<T><<<dim3((sys->n + 31) / 32, (nrhs + 31) / 32), dim3(32, 8), 0, s>>>(xfix, xout, sys->n, nrhs);
+  } else if (xout != xfix) {
     HM_CUDA(cudaMemcpyAsync(xout, xfix, sizeof(T) * (size_t)sys->n * nrhs, cudaMemcpyDeviceToDevice, s));
+  }
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }
@@ -497,6 +518,11 @@ int solve_setup(int max_smem) {
 int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT) {
   if (sys->precision == HM_PREC_FP64) return apply_t<double>(sys, nrhs, (const double*)rT, (double*)zT);
   return apply_t<float>(sys, nrhs, (const float*)rT, (float*)zT);
+}
+
+int apply_impl_rowmajor(hm_sys_s* sys, int nrhs, const void* rT, void* zT) {
+  if (sys->precision == HM_PREC_FP64) return apply_t<double>(sys, nrhs, (const double*)rT, (double*)zT, true);
+  return apply_t<float>(sys, nrhs, (const float*)rT, (float*)zT, true);
 }
 
 // ------------------------------------------------------------------------------------
