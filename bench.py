@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--n-c", type=int, default=64)
     ap.add_argument("--hodlr-leaf", type=int, default=64)
     ap.add_argument("--samples", type=int, default=48)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner pass of the warm-up (built-in launch variants)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-out", default=None, help="write per-kernel profile JSON here")
@@ -188,10 +190,6 @@ def alu_peak_tflops(precision: str, sm_max_mhz: float | None) -> float:
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
-COMPUTE_CATS = {"gemm_factor", "gemm_apply", "dense_potrf", "dense_trsm", "householder_qr",
-                "jacobi_svd", "core_lu_inverse", "spd_inverse", "leaf_solve", "dense_sweep"}
-
-
 def ncu_traffic(category: str):
     """DRAM bytes per launch of `category` from the committed ncu summaries (a line
     'TRAFFIC <category> <bytes> <source file> <sha1[:12] of that file>'), or None if none
@@ -211,26 +209,45 @@ def ncu_traffic(category: str):
     return None
 
 
-def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
-    cat = max(prof, key=lambda c: prof[c]["ms"])
-    e = prof[cat]
-    per_launch_ms = e["ms"] / max(e["launches"], 1)
-    if cat in COMPUTE_CATS:
-        achieved = (e["flops"] / max(e["launches"], 1)) / (per_launch_ms * 1e-3) / 1e12
-        peak = alu_peak_tflops(precision, (clocks or {}).get("sm_max_mhz"))
-        return {"kernel": cat, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(cat), "launches": e["launches"],
-                "avg_launch_ms": per_launch_ms, "share_of_profiled_time":
-                    e["ms"] / sum(v["ms"] for v in prof.values()),
+def kernel_roofline(e: dict, precision: str, peaks, clocks) -> dict:
+    """One launch category against its roofline.  The bound follows the category's
+    algorithmic intensity: below the ridge point (SIMT peak / HBM peak) it is HBM-bound
+    and reported in GB/s, above it ALU-bound in TFLOP/s; categories with no flops are
+    HBM-bound."""
+    launches = max(e["launches"], 1)
+    per_launch_ms = e["ms"] / launches
+    hbm = (peaks or {}).get("hbm_gbs") or 6800.0
+    alu = alu_peak_tflops(precision, (clocks or {}).get("sm_max_mhz"))
+    ridge = alu * 1e12 / (hbm * 1e9)
+    if e["flops"] > 0 and e["flops"] >= ridge * e["bytes"]:
+        achieved = (e["flops"] / launches) / (per_launch_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s", "frac": achieved / alu,
+                "launches": e["launches"], "avg_launch_ms": per_launch_ms,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock" if precision != "f64"
                 else "nominal GB300 FP64 1.25 TFLOP/s"}
-    achieved = (e["bytes"] / max(e["launches"], 1)) / (per_launch_ms * 1e-3) / 1e9
-    peak = (peaks or {}).get("hbm_gbs") or 6800.0
-    return {"kernel": cat, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(cat), "launches": e["launches"],
-            "avg_launch_ms": per_launch_ms,
-            "share_of_profiled_time": e["ms"] / sum(v["ms"] for v in prof.values()),
+    achieved = (e["bytes"] / launches) / (per_launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "launches": e["launches"], "avg_launch_ms": per_launch_ms,
             "peak_source": "measured" if peaks else "fallback"}
+
+
+def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
+    """The dominant launch category (most device time) against its roofline, plus every
+    category's line under "kernels"."""
+    total = sum(v["ms"] for v in prof.values()) or 1.0
+    table = {}
+    for c, e in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        if e["ms"] <= 0:
+            continue
+        r = kernel_roofline(e, precision, peaks, clocks)
+        table[c] = {"bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"], "frac": r["frac"],
+                    "share": e["ms"] / total, "launches": e["launches"]}
+    cat = max(prof, key=lambda c: prof[c]["ms"])
+    rl = {"kernel": cat, **kernel_roofline(prof[cat], precision, peaks, clocks)}
+    rl["traffic"] = ncu_traffic(cat)
+    rl["share_of_profiled_time"] = prof[cat]["ms"] / total
+    rl["kernels"] = table
+    return rl
 
 
 class Workload:
@@ -342,9 +359,23 @@ def run_ours(args, rank, world, local):
             hm.hm_profile_enable(ctx, False)
         return per, total, infos, prof
 
+    def tune(ctx):
+        """Autotuner pass on this workload's shapes (untimed; the context keeps the choices)."""
+        if args.no_autotune:
+            return 0
+        if bp is None:
+            s = hm.hm_analyze(ctx, P.n, d_rowptr, d_colidx, P.dim, d_coords)
+        else:
+            s = hm.hm_analyze_batch(ctx, P.n, d_rowptr, d_colidx, P.dim, d_coords, bp)
+        hm.hm_factor(s, d_values, tol)
+        nsites = hm.hm_autotune(s, d_values, tol, nrhs, reps=2)
+        hm.hm_destroy(s)
+        return nsites
+
     dev_inputs = (d_rowptr, d_colidx, d_coords, d_values, d_b, d_x)
     # ---------------- the workload's headline precision, device-resident inputs
     ctx = make_ctx(getattr(hm, "HM_PREC_" + W.headline))
+    tuned_sites = tune(ctx)
     for _ in range(args.warmup):
         step(ctx, *dev_inputs)
     clocks = ClockSampler(local)
@@ -376,10 +407,31 @@ def run_ours(args, rank, world, local):
     h2d = (P.rowptr.nbytes + P.colidx.nbytes + P.coords.astype(np.int32).nbytes + P.values.nbytes
            + b.nbytes)
     d2h = b.nbytes
+    # ---------------- solve only: the factor resident, the solve repeated
+    if bp is None:
+        s_res = hm.hm_analyze(ctx, P.n, d_rowptr, d_colidx, P.dim, d_coords)
+    else:
+        s_res = hm.hm_analyze_batch(ctx, P.n, d_rowptr, d_colidx, P.dim, d_coords, bp)
+    hm.hm_factor(s_res, d_values, tol)
+    for _ in range(2):
+        hm.hm_solve(s_res, nrhs, d_b, RTOL, MAX_ITERS, d_x)
+    ks = max(3, args.steps)
+    ev_s = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    barrier(world)
+    torch.cuda.synchronize()
+    ev_s[0].record(stream)
+    for _ in range(ks):
+        hm.hm_solve(s_res, nrhs, d_b, RTOL, MAX_ITERS, d_x)
+    ev_s[1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    total_s = allreduce_max(ev_s[0].elapsed_time(ev_s[1]), world)
+    hm.hm_destroy(s_res)
     hm.hm_ctx_destroy(ctx)
 
     # ---------------- FP64 plain (same method entirely in FP64)
     ctx64 = make_ctx(hm.HM_PREC_FP64)
+    tune(ctx64)
     step(ctx64, *dev_inputs)
     k64 = max(1, args.fp64_steps)
     per64, total64, infos64, _ = timed(ctx64, k64, dev_inputs)
@@ -404,6 +456,7 @@ def run_ours(args, rank, world, local):
                    "meshes": len(bp) - 1 if bp is not None else 1, "tol": tol, "rtol": RTOL,
                    "restart": 30, "nd_leaf": W.nd_leaf, "hodlr_leaf": W.hodlr_leaf, "n_c": W.n_c,
                    "samples": W.samples, "step": "analyze + factor + solve(nrhs) + destroy",
+                   "autotuned_sites": tuned_sites,
                    "l2": f"inputs larger than L2 (A: {(P.nnz * 12 + P.n * 8) / 1e6:.0f} MB CSR)",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": p50, "p99_ms": p99,
@@ -415,6 +468,9 @@ def run_ours(args, rank, world, local):
         "roofline": rl,
         "e2e": {"value": nsolve * ke * world / (total_e * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": ke},
+        "solve_only": {"value": nsolve * ks * world / (total_s * 1e-3), "unit": "solves/s",
+                       "ms_per_solve_call": total_s / ks, "steps": ks,
+                       "step": "solve(nrhs) with the factor resident"},
         "gpu_launches": int(kernels),
         "clocks": clk,
     }

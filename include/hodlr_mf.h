@@ -168,6 +168,25 @@ int hm_get_symbolic(hm_sys_t sys, int32_t* nupd, int64_t* if_off, int32_t* if_li
 int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* info);
 
 /*
+ * Autotuner of the batched launches (one launch per elimination-tree level and stage,
+ * Section 4): every tunable launch site -- the batched GEMMs of factorization and apply
+ * (k-slice depth, register- or cp.async-staged operands), the range finder's panel QR
+ * (shared-memory-resident or global), the
+ * dense fronts' apply kernels (threads per front) -- is keyed by the shapes of its batch.
+ * Runs the factorization with values[] and tol plus two GMRES iterations on nrhs
+ * right-hand sides, reps times per variant, with every site forced to each variant in
+ * turn; keeps per site the variant with the least mean launch time (the default unless
+ * another is more than 3% faster) in the CONTEXT, so later systems of the same shapes
+ * analysed on it use the choices too; then refactors sys with them.  values may be host
+ * or device memory.  *nsites (may be NULL) = number of sites timed.  The variants
+ * compute the same quantities (GEMM variants bit-identically; the QR variants to
+ * rounding).  Requires the launch profiler off (HM_ERR_STATE).  1 <= nrhs <= 64,
+ * 1 <= reps <= 16.
+ */
+int hm_autotune(hm_sys_t sys, const double* values, double tol, int32_t nrhs, int32_t reps,
+                int32_t* nsites);
+
+/*
  * Solve A X = B by GMRES(restart) preconditioned with the factorization (Section 3):
  * right preconditioning, flexible form (the preconditioned vectors are stored), FP64
  * residuals, Arnoldi by classical Gram-Schmidt applied twice, Givens least squares.

@@ -30,7 +30,7 @@ HM_PREC_MIXED = 1
 HM_PREC_MIXED_BF16 = 2
 
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_analyze_batch", "hm_get_sizes",
-            "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_solve", "hm_precond_apply",
+            "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_autotune", "hm_solve", "hm_precond_apply",
             "hm_precond_apply_noalloc",
             "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error",
             "hm_server_create", "hm_server_add_matrix", "hm_server_submit", "hm_server_wait",
@@ -89,6 +89,7 @@ def _load():
     lib.hm_get_ordering.argtypes = [vp, vp, vp, vp, vp]
     lib.hm_get_symbolic.argtypes = [vp, vp, vp, vp, vp]
     lib.hm_factor.argtypes = [vp, vp, dbl, C.POINTER(HmFactorInfo)]
+    lib.hm_autotune.argtypes = [vp, vp, dbl, i32, i32, C.POINTER(i32)]
     lib.hm_solve.argtypes = [vp, i32, vp, dbl, i32, vp, C.POINTER(HmSolveInfo)]
     lib.hm_precond_apply.argtypes = [vp, i32, vp, vp]
     lib.hm_precond_apply_noalloc.argtypes = [vp, i32, vp, vp]
@@ -107,6 +108,7 @@ def _load():
     lib.hm_destroy.argtypes = [vp]
     lib.hm_status_str.argtypes = [C.c_int]
     lib.hm_status_str.restype = C.c_char_p
+    lib.hm_last_error.argtypes = []
     lib.hm_last_error.restype = C.c_char_p
     for name in EXPORTED:
         if name not in ("hm_status_str", "hm_last_error"):
@@ -223,6 +225,15 @@ def hm_factor(sys_, values, tol: float) -> dict:
     _check(_lib.hm_factor(sys_, _ptr(values, np.float64, "values"), float(tol), C.byref(info)),
            "hm_factor")
     return {f: getattr(info, f) for f, _ in HmFactorInfo._fields_}
+
+
+def hm_autotune(sys_, values, tol: float, nrhs: int, reps: int = 2) -> int:
+    """Time every tunable launch site in each variant on this system; the context keeps
+    the faster ones.  Returns the number of sites timed."""
+    n = C.c_int32(0)
+    _check(_lib.hm_autotune(sys_, _ptr(values, np.float64, "values"), float(tol), int(nrhs), int(reps),
+                            C.byref(n)), "hm_autotune")
+    return n.value
 
 
 def hm_solve(sys_, nrhs: int, b, rtol: float, max_iters: int, x, raise_on_no_convergence=True) -> dict:

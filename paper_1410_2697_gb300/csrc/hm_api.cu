@@ -1,5 +1,6 @@
 // hm_api.cu -- the extern "C" boundary (include/hodlr_mf.h) and host utilities.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -102,6 +103,21 @@ cudaEvent_t Profiler::get() {
   cudaEvent_t e;
   cudaEventCreate(&e);
   return e;
+}
+
+cudaEvent_t Tuner::get() {
+  if (next < pool.size()) return pool[next++];
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  pool.push_back(e);
+  ++next;
+  return e;
+}
+
+// Right-hand sides of a tuning pass: a fixed, nonzero pattern.
+__global__ void k_tune_rhs(double* b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)((uint32_t)(i * 2654435761ull) % 1024u) / 1024.0 - 0.5;
 }
 
 const char* prof_cat_name(int c) {
@@ -278,6 +294,7 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   int st = dense_fact_setup(ctx->max_smem);
   if (st == HM_OK) st = dense_comp_setup(ctx->max_smem);
   if (st == HM_OK) st = dense_tc_setup(ctx->max_smem);
+  if (st == HM_OK) st = gemm_async_setup(ctx->max_smem);
   if (st == HM_OK) st = solve_setup(ctx->max_smem);
   if (st != HM_OK) {
     delete ctx;
@@ -293,6 +310,7 @@ int hm_ctx_destroy(hm_ctx_t ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& r : ctx->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto& e : ctx->prof.pool) cudaEventDestroy(e);
+  for (auto& e : ctx->tune.pool) cudaEventDestroy(e);
   if (ctx->pool) {
     cudaStreamSynchronize(ctx->stream);
     cudaMemPoolDestroy(ctx->pool);
@@ -427,6 +445,88 @@ int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* in
     info->front_bytes = (double)P.front_total * (sys->precision == HM_PREC_FP64 ? 8 : 4);
   }
   return HM_OK;
+}
+
+int hm_autotune(hm_sys_t sys, const double* values, double tol, int32_t nrhs, int32_t reps, int32_t* nsites) {
+  if (!sys || !values || nrhs < 1 || nrhs > 64 || reps < 1 || reps > 16) return HM_ERR_INVALID_ARG;
+  hm_ctx_s* ctx = sys->ctx;
+  if (ctx->prof.on) { set_last_error("hm_autotune while the launch profiler is on"); return HM_ERR_STATE; }
+  cudaSetDevice(ctx->opts.device);
+  cudaStream_t s = ctx->stream;
+  std::vector<void*> tmp;
+  const double* d_vals = values;
+  void *pv = nullptr, *pb = nullptr, *px = nullptr;
+  const int64_t nn = (int64_t)sys->n * nrhs;
+  if (!is_device_ptr(values)) {
+    HM_TRY(dev_alloc_ctx(ctx, &tmp, &pv, sizeof(double) * sys->nnz));
+    HM_CUDA(cudaMemcpyAsync(pv, values, sizeof(double) * sys->nnz, cudaMemcpyHostToDevice, s));
+    d_vals = (const double*)pv;
+  }
+  int st = dev_alloc_ctx(ctx, &tmp, &pb, sizeof(double) * nn);
+  if (st == HM_OK) st = dev_alloc_ctx(ctx, &tmp, &px, sizeof(double) * nn);
+  if (st != HM_OK) { dev_free_all(ctx, &tmp); return st; }
+  k_tune_rhs<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>((double*)pb, nn);
+  // every pass: the factorization and two GMRES iterations with all sites forced to one
+  // variant; per site the mean time of one launch, the best over the repetitions
+  constexpr int kVariants = 3;  // the GEMM sites have three, the others two (2 acts as 0)
+  std::unordered_map<uint64_t, std::array<double, kVariants>> best;
+  for (int rep = 0; rep < reps && st == HM_OK; ++rep)
+    for (int v = 0; v < kVariants && st == HM_OK; ++v) {
+      ctx->tune.force = v;
+      ctx->tune.rec = true;
+      ctx->tune.recs.clear();
+      ctx->tune.next = 0;
+      st = factor_impl(sys, d_vals, tol);
+      if (st == HM_OK) {
+        sys->factored = true;
+        const int gs = gmres_impl(sys, nrhs, (const double*)pb, 1e-300, 2, (double*)px, nullptr);
+        if (gs != HM_OK && gs != HM_ERR_NO_CONVERGENCE) st = gs;
+      }
+      if (cudaStreamSynchronize(s) != cudaSuccess && st == HM_OK) st = HM_ERR_CUDA;
+      if (st != HM_OK) break;
+      std::unordered_map<uint64_t, std::pair<double, int>> sum;
+      for (const auto& r : ctx->tune.recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+        auto& e = sum[r.key];
+        e.first += ms;
+        e.second += 1;
+      }
+      for (const auto& kv : sum) {
+        auto it = best.find(kv.first);
+        if (it == best.end()) it = best.emplace(kv.first, std::array<double, kVariants>{1e30, 1e30, 1e30}).first;
+        it->second[v] = std::min(it->second[v], kv.second.first / kv.second.second);
+      }
+    }
+  ctx->tune.force = -1;
+  ctx->tune.rec = false;
+  ctx->tune.recs.clear();
+  int tuned = 0;
+  if (st == HM_OK) {
+    // the default stays unless another variant is clearly faster (3%: timing noise)
+    for (const auto& kv : best) {
+      int c = 0;
+      for (int v = 1; v < kVariants; ++v)
+        if (kv.second[v] < 0.97 * kv.second[0] && kv.second[v] < kv.second[c]) c = v;
+      ctx->tune.choice[kv.first] = c;
+      ++tuned;
+    }
+    // graphs captured before tuning keep the old variants
+    for (auto& kv : sys->solve_plans) {
+      SolvePlan* sp = kv.second.get();
+      if (sp->graph_exec) cudaGraphExecDestroy(sp->graph_exec);
+      sp->graph_exec = nullptr;
+      sp->graph_in = nullptr;
+      sp->last_in = nullptr;
+    }
+    st = factor_impl(sys, d_vals, tol);
+  }
+  cudaStreamSynchronize(s);
+  dev_free_all(ctx, &tmp);
+  sys->factored = st == HM_OK;
+  if (st == HM_OK) sys->tol = tol;
+  if (nsites) *nsites = tuned;
+  return st;
 }
 
 int hm_solve(hm_sys_t sys, int32_t nrhs, const double* b, double rtol, int32_t max_iters, double* x,

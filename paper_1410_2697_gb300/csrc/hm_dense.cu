@@ -6,13 +6,16 @@
 namespace hm {
 
 // =====================================================================================
-// Batched GEMM: 64 x BN output tiles (BN = 64 or 16), BK = 16, 256 threads; a thread owns
-// rows ty + 16 i (i < 4) and columns tx + 16 j (j < BN / 16).  Operand tiles are staged
+// Batched GEMM: 64 x BN output tiles (BN = 64 or 16), 256 threads; a thread owns rows
+// ty + 16 i (i < 4) and columns tx + 16 j (j < BN / 16).  Operand tiles are staged
 // through shared memory with the next k-slice prefetched into registers while the
-// current one is consumed.  The narrow variant serves products with few columns
-// (one right-hand side block of the preconditioner apply).
+// current one is consumed.  The narrow variant serves products with few columns (one
+// right-hand side block of the preconditioner apply).  Each width comes with a shallow
+// k-slice (16: few registers, more resident CTAs) and a deep one (64 for the narrow
+// tiles, 32 for the wide: fewer memory round trips along k); a batch's variant is its
+// GemmBatch::bk, set by the autotuner.
 // =====================================================================================
-constexpr int BM = kGemmBM, BK = 16;
+constexpr int BM = kGemmBM;
 
 template <typename T>
 __device__ __forceinline__ T load_op(const T* __restrict__ X, int op, int ld, int r, int c,
@@ -22,12 +25,14 @@ __device__ __forceinline__ T load_op(const T* __restrict__ X, int op, int ld, in
   return op == 0 ? X[(size_t)r + (size_t)c * ld] : X[(size_t)c + (size_t)r * ld];
 }
 
-template <typename T, int BN>
-__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks,
-                                              const GemmTile* __restrict__ tiles, T* __restrict__ split_ws,
-                                              unsigned* __restrict__ split_cnt) {
-  constexpr int TN = BN / 16;       // columns per thread
-  constexpr int NB = BK * BN / 256; // B elements loaded per thread
+template <typename T, int BN, int BK>
+__global__ void __launch_bounds__(256, BK == 16 ? 1 : 2) k_gemm(const GemmTask* __restrict__ tasks,
+                                                                const GemmTile* __restrict__ tiles,
+                                                                T* __restrict__ split_ws,
+                                                                unsigned* __restrict__ split_cnt) {
+  constexpr int TN = BN / 16;        // columns per thread
+  constexpr int NA = BK * BM / 256;  // A elements loaded per thread
+  constexpr int NB = BK * BN / 256;  // B elements loaded per thread
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
   const GemmTile tl = tiles[blockIdx.x];
@@ -43,26 +48,29 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
-  T ra[4], rb[NB];
+  // k beyond this tile's part [k0, k1) reads as zero, so a part need not be a whole
+  // number of k-slices
+  const int kend = tl.k1;
+  T ra[NA], rb[NB];
   auto fetch = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NA; ++q) {
       const int e = tid + 256 * q;
       int r, p;
       if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
-      ra[q] = load_op(A, t.opA, t.lda, m0 + r, k0 + p, t.m, t.k);
+      ra[q] = load_op(A, t.opA, t.lda, m0 + r, k0 + p, t.m, kend);
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int e = tid + 256 * q;
       int c, pb;
       if (t.opB == 0) { pb = e % BK; c = e / BK; } else { c = e % BN; pb = e / BN; }
-      rb[q] = load_op(B, t.opB, t.ldb, k0 + pb, n0 + c, t.k, t.n);
+      rb[q] = load_op(B, t.opB, t.ldb, k0 + pb, n0 + c, kend, t.n);
     }
   };
   auto stash = [&]() {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NA; ++q) {
       const int e = tid + 256 * q;
       int r, p;
       if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
@@ -77,7 +85,6 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     }
   };
 
-  const int kend = tl.k1;
   if (tl.k0 < kend) fetch(tl.k0);
   for (int k0 = tl.k0; k0 < kend; k0 += BK) {
     __syncthreads();
@@ -140,6 +147,159 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   }
 }
 
+// =====================================================================================
+// Pipelined variant: the same 64 x BN tiles and thread layout, with the operand slices
+// (32 deep) copied global -> shared by cp.async (4- or 8-byte copies, zero-filled
+// outside the operands) kGemmStages slices ahead, so a tile waits on about one memory
+// round trip instead of one per slice.  Dynamic shared memory: kGemmStages x
+// (32 x (64 + 4) + 32 x (BN + 4)) elements.
+// =====================================================================================
+constexpr int kGemmStages = 4, kAsyncBK = 32;
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? (int)sizeof(T) : 0;
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename T, int BN>
+__host__ __device__ constexpr int gemm_async_stage_elems() { return kAsyncBK * (BM + 4) + kAsyncBK * (BN + 4); }
+
+template <typename T, int BN>
+__global__ void __launch_bounds__(256) k_gemm_async(const GemmTask* __restrict__ tasks,
+                                                    const GemmTile* __restrict__ tiles, T* __restrict__ split_ws,
+                                                    unsigned* __restrict__ split_cnt) {
+  constexpr int BK = kAsyncBK, TN = BN / 16, NA = BK * BM / 256, NB = BK * BN / 256;
+  constexpr int SE = gemm_async_stage_elems<T, BN>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask t = tasks[tl.task];
+  const int m0 = (tl.mn >> 16) * BM, n0 = (tl.mn & 0xffff) * BN;
+  const T* __restrict__ A = (const T*)t.A;
+  const T* __restrict__ B = (const T*)t.B;
+  T* __restrict__ C = (T*)t.C;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int kbeg = tl.k0, kend = tl.k1;
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  auto issue = [&](int kt) {
+    T* As = smem + (kt % kGemmStages) * SE;
+    T* Bs = As + BK * (BM + 4);
+    const int k0 = kbeg + kt * BK;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + 256 * q;
+      int r, pp;
+      if (t.opA == 0) { r = e % BM; pp = e / BM; } else { pp = e % BK; r = e / BK; }
+      const int gr = m0 + r, gk = k0 + pp;
+      const bool ok = gr < t.m && gk < kend;
+      const T* src = ok ? (t.opA == 0 ? A + (size_t)gr + (size_t)gk * t.lda : A + (size_t)gk + (size_t)gr * t.lda) : A;
+      cp_async_elem(As + pp * (BM + 4) + r, src, ok);
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + 256 * q;
+      int c, pb;
+      if (t.opB == 0) { pb = e % BK; c = e / BK; } else { c = e % BN; pb = e / BN; }
+      const int gc = n0 + c, gk = k0 + pb;
+      const bool ok = gc < t.n && gk < kend;
+      const T* src = ok ? (t.opB == 0 ? B + (size_t)gk + (size_t)gc * t.ldb : B + (size_t)gc + (size_t)gk * t.ldb) : B;
+      cp_async_elem(Bs + pb * (BN + 4) + c, src, ok);
+    }
+  };
+  T acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+#pragma unroll
+  for (int s = 0; s < kGemmStages - 1; ++s) {
+    if (s < nk) issue(s);
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < nk; ++kt) {
+    cp_async_wait<kGemmStages - 2>();
+    __syncthreads();  // slice kt visible to all; slice kt - 1's buffer free
+    if (kt + kGemmStages - 1 < nk) issue(kt + kGemmStages - 1);
+    cp_async_commit();
+    const T* As = smem + (kt % kGemmStages) * SE;
+    const T* Bs = As + BK * (BM + 4);
+#pragma unroll
+    for (int p = 0; p < BK; ++p) {
+      T a[4], b[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[p * (BM + 4) + ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[p * (BN + 4) + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  cp_async_wait<0>();
+  if (tl.slot >= 0) {
+    __shared__ int last;
+    T* ws = split_ws + tl.woff;
+#pragma unroll
+    for (int j = 0; j < TN; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        ws[(size_t)tl.part * BM * BN + (ty + 16 * i) + (tx + 16 * j) * BM] = acc[i][j];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(split_cnt + tl.slot, 1u) == (unsigned)(tl.nsplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < TN; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        T v = T(0);
+        for (int p = 0; p < tl.nsplit; ++p)
+          v += __ldcg(ws + (size_t)p * BM * BN + (ty + 16 * i) + (tx + 16 * j) * BM);
+        acc[i][j] = v;
+      }
+    if (tid == 0) split_cnt[tl.slot] = 0u;
+  }
+  const T alpha = (T)t.alpha, beta = (T)t.beta;
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int c = n0 + tx + 16 * j;
+    if (c >= t.n) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + ty + 16 * i;
+      if (r >= t.m) continue;
+      if (t.lower && r < c) continue;
+      T* dst = C + (size_t)r + (size_t)c * t.ldc;
+      const T v = alpha * acc[i][j];
+      *dst = (beta == T(0)) ? v : fma(beta, *dst, v);
+    }
+  }
+}
+
+int gemm_async_setup(int max_smem) {
+  (void)max_smem;
+  HM_CUDA(cudaFuncSetAttribute(k_gemm_async<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kGemmStages * gemm_async_stage_elems<float, 16>() * sizeof(float))));
+  HM_CUDA(cudaFuncSetAttribute(k_gemm_async<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kGemmStages * gemm_async_stage_elems<float, 64>() * sizeof(float))));
+  HM_CUDA(cudaFuncSetAttribute(k_gemm_async<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kGemmStages * gemm_async_stage_elems<double, 16>() * sizeof(double))));
+  HM_CUDA(cudaFuncSetAttribute(k_gemm_async<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kGemmStages * gemm_async_stage_elems<double, 64>() * sizeof(double))));
+  return HM_OK;
+}
+
 int gemm_bn_for(const std::vector<GemmTask>& t) {
   int nmax = 0;
   for (const auto& x : t) nmax = std::max(nmax, x.n);
@@ -159,8 +319,8 @@ void gemm_tiles_for(const GemmTask& t, int task_index, int bm, int bn, int nspli
                     int* slots, int64_t* ws) {
   if (t.m <= 0 || t.n <= 0) return;
   const int tm = (t.m + bm - 1) / bm, tn = (t.n + bn - 1) / bn;
-  // k chunks are whole multiples of the k step
-  const int kc = nsplit > 1 ? ((t.k + nsplit - 1) / nsplit + BK - 1) / BK * BK : t.k;
+  // k chunks are whole multiples of 16 (every kernel masks k beyond its part's end)
+  const int kc = nsplit > 1 ? ((t.k + nsplit - 1) / nsplit + 15) / 16 * 16 : t.k;
   const int parts = nsplit > 1 ? (t.k + kc - 1) / kc : 1;
   for (int a = 0; a < tm; ++a)
     for (int b = 0; b < tn; ++b) {
@@ -179,15 +339,30 @@ void gemm_tiles_for(const GemmTask& t, int task_index, int bm, int bn, int nspli
 }
 
 template <typename T>
-void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, T* split_ws,
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, int deep, T* split_ws,
                  unsigned* split_cnt, cudaStream_t s) {
   if (ntiles <= 0) return;
-  if (bn == 16) k_gemm<T, 16><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
-  else k_gemm<T, 64><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
+  if (deep == 2) {
+    if (bn == 16)
+      k_gemm_async<T, 16><<<ntiles, 256, kGemmStages * gemm_async_stage_elems<T, 16>() * sizeof(T), s>>>(
+          tasks, tiles, split_ws, split_cnt);
+    else
+      k_gemm_async<T, 64><<<ntiles, 256, kGemmStages * gemm_async_stage_elems<T, 64>() * sizeof(T), s>>>(
+          tasks, tiles, split_ws, split_cnt);
+    return;
+  }
+  if (bn == 16) {
+    if (deep) k_gemm<T, 16, 64><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
+    else k_gemm<T, 16, 16><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
+  } else {
+    if (deep) k_gemm<T, 64, 32><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
+    else k_gemm<T, 64, 16><<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
+  }
 }
 
-template void launch_gemm<float>(const GemmTask*, const GemmTile*, int, int, float*, unsigned*, cudaStream_t);
-template void launch_gemm<double>(const GemmTask*, const GemmTile*, int, int, double*, unsigned*,
+template void launch_gemm<float>(const GemmTask*, const GemmTile*, int, int, int, float*, unsigned*,
+                                 cudaStream_t);
+template void launch_gemm<double>(const GemmTask*, const GemmTile*, int, int, int, double*, unsigned*,
                                   cudaStream_t);
 
 }  // namespace hm

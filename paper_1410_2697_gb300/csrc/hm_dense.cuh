@@ -126,8 +126,10 @@ struct CholInvTask {
   int ldbt, pad;
 };
 
+// deep: 0 = 16-deep k-slices, 1 = the deeper variant (64 for bn 16, 32 for bn 64),
+// 2 = 32-deep slices copied by cp.async several slices ahead.
 template <typename T>
-void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, T* split_ws,
+void launch_gemm(const GemmTask* tasks, const GemmTile* tiles, int ntiles, int bn, int deep, T* split_ws,
                  unsigned* split_cnt, cudaStream_t s);
 template <typename T>
 void launch_front_sweep(const SweepTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s);
@@ -138,7 +140,7 @@ void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s);
 template <typename T>
 void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStream_t s);
 template <typename T>
-void launch_qr(const QrTask* tasks, int ntasks, int maxm, int max_smem, cudaStream_t s);
+void launch_qr(const QrTask* tasks, int ntasks, int maxm, int64_t maxmk, int max_smem, cudaStream_t s);
 template <typename T>
 void launch_tsqr(const TsqrTask* tasks, int ntasks, const TsqrBlock* blocks, int nblocks, size_t smem_block,
                  size_t smem_stack, T* scratch, cudaStream_t s);
@@ -169,5 +171,6 @@ int dense_tc_setup(int max_smem);
 
 int dense_fact_setup(int max_dyn_smem);
 int dense_comp_setup(int max_dyn_smem);
+int gemm_async_setup(int max_dyn_smem);
 
 }  // namespace hm

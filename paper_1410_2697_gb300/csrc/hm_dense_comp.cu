@@ -342,9 +342,385 @@ __global__ void __launch_bounds__(512) k_qr_blocked(const QrTask* __restrict__ t
   }
 }
 
+// =====================================================================================
+// Panel QR with the whole panel resident in shared memory (m k elements) plus a
+// row-major copy of the current block of reflectors (m x 8).  Same blocked compact-WY
+// Householder algorithm as k_qr_blocked, but every trailing update and the backward
+// formation of Q run on shared memory instead of round trips to global memory, and a
+// row of V (unit diagonal and zeros above it written out) is two 16-byte loads.  The
+// trailing columns go to warps in groups of four (two in FP64).
+// =====================================================================================
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+// V of the current panel at local row i, reflector s (reflector tails in place below
+// the diagonal of S).
 template <typename T>
-void launch_qr(const QrTask* tasks, int ntasks, int maxm, int max_smem, cudaStream_t s) {
+__device__ __forceinline__ T vget(const T* __restrict__ Vp, int m, int i, int s) {
+  return i > s ? Vp[i + (size_t)s * m] : (i == s ? T(1) : T(0));
+}
+
+// Row-major reflector block: plane p (m rows of 16 bytes) holds reflectors p NV .. p NV + NV - 1.
+template <typename T>
+__device__ __forceinline__ T& vr_at(T* __restrict__ Vr, int m, int i, int s) {
+  constexpr int NV = 16 / sizeof(T);
+  return Vr[(size_t)(s / NV) * NV * m + (size_t)i * NV + s % NV];
+}
+template <typename T>
+__device__ __forceinline__ void vr_row(const T* __restrict__ Vr, int m, int i, T (&v)[kQrNB]) {
+  using V = typename Vec16<T>::type;
+  constexpr int NV = 16 / sizeof(T);
+#pragma unroll
+  for (int p = 0; p < kQrNB / NV; ++p) {
+    const V x = reinterpret_cast<const V*>(Vr + (size_t)p * NV * m)[i];
+    const T* e = reinterpret_cast<const T*>(&x);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[p * NV + q] = e[q];
+  }
+}
+
+// Reflector of column j (rows j.. of aj in shared memory): tail scaled in place,
+// aj[j] = beta; returns tau.  Every lane of one warp calls it; four partial sums per
+// lane keep several loads in flight.
+template <typename T>
+__device__ __forceinline__ T reflector_warp_ilp(T* __restrict__ aj, int j, int m) {
+  const int lane = threadIdx.x & 31;
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int i = j + 1 + lane;
+  for (; i + 96 < m; i += 128) {
+    const T a0 = aj[i], a1 = aj[i + 32], a2 = aj[i + 64], a3 = aj[i + 96];
+    s0 += a0 * a0; s1 += a1 * a1; s2 += a2 * a2; s3 += a3 * a3;
+  }
+  for (; i < m; i += 32) s0 += aj[i] * aj[i];
+  const T s = warp_sum_all((s0 + s1) + (s2 + s3));
+  const T x0 = aj[j];
+  T tj = T(0), beta = x0, scale = T(1);
+  if (s > T(0)) {
+    const T nrm = sqrt(x0 * x0 + s);
+    beta = x0 >= T(0) ? -nrm : nrm;
+    tj = (beta - x0) / beta;
+    scale = T(1) / (x0 - beta);
+  }
+  for (int r = j + 1 + lane; r < m; r += 32) aj[r] *= scale;
+  __syncwarp();
+  if (lane == 0) aj[j] = beta;
+  return tj;
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_4or8(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+
+// Trailing update of one reflector block (rows p0.., columns p0 + pw ..), CW columns per
+// warp pass so that a row of V is read once per pass: the factorization applies
+// (I - V T V^T)^T (u = T^T w), the backward formation of Q applies I - V T V^T
+// (u = T w) and reads the block's own rows 0..pw-1 of those columns as zero.  Groups
+// narrow as the trailing part shrinks, so all warps stay busy.
+template <typename T, int CW, bool QFORM>
+__device__ __forceinline__ void qr_trail(T* __restrict__ S, const T* __restrict__ Vr, const T (*Tp)[kQrNB], int m,
+                                         int k, int p0, int pw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int mv = m - p0, c0 = p0 + pw, ngroups = (k - c0 + CW - 1) / CW;
+  for (int g = wid; g < ngroups; g += nw) {
+    const int cb = c0 + g * CW, ncol = min(CW, k - cb);
+    T* A0 = S + (size_t)cb * m + p0;
+    T w[CW][kQrNB];
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) w[c][s] = T(0);
+    for (int i = (QFORM ? pw : 0) + lane; i < mv; i += 32) {
+      T v[kQrNB];
+      vr_row(Vr, m, i, v);
+#pragma unroll
+      for (int c = 0; c < CW; ++c)
+        if (c < ncol) {
+          const T a = A0[i + (size_t)c * m];
+#pragma unroll
+          for (int s = 0; s < kQrNB; ++s) w[c][s] += v[s] * a;
+        }
+    }
+    T u[CW][kQrNB];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) w[c][s] = warp_sum_all(w[c][s]);
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) {
+        T acc = T(0);
+        if (QFORM) {
+#pragma unroll
+          for (int r = s; r < kQrNB; ++r) acc += Tp[s][r] * w[c][r];  // (T w)_s
+        } else {
+#pragma unroll
+          for (int r = 0; r <= s; ++r) acc += Tp[r][s] * w[c][r];  // (T^T w)_s
+        }
+        u[c][s] = acc;
+      }
+    }
+    for (int i = lane; i < mv; i += 32) {
+      T v[kQrNB], a[CW];
+      vr_row(Vr, m, i, v);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) a[c] = c < ncol && (!QFORM || i >= pw) ? A0[i + (size_t)c * m] : T(0);
+#pragma unroll
+      for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int s = 0; s < kQrNB; ++s) a[c] -= v[s] * u[c][s];
+#pragma unroll
+      for (int c = 0; c < CW; ++c)
+        if (c < ncol) A0[i + (size_t)c * m] = a[c];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_qr_smem(const QrTask* __restrict__ tasks, int64_t vr_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T tau[256];
+  __shared__ T vscale[256];
+  __shared__ T Tall[256 / kQrNB][kQrNB][kQrNB];
+  __shared__ T Gred[16][kQrNB * (kQrNB - 1) / 2];
+  __shared__ T U8[kQrNB][kQrNB];
+  constexpr int CWMAX = sizeof(T) == 8 ? 2 : 4;  // widest trailing column group
+  const QrTask t = tasks[blockIdx.x];
+  const int m = t.m, k = t.k, ld = t.ld;
+  T* __restrict__ Y = (T*)t.Y;
+  T* __restrict__ S = reinterpret_cast<T*>(smem_raw);  // the panel, m x k, ld m
+  T* __restrict__ Vr = S + vr_off;                     // current reflector block, row-major
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wid; c < k; c += nw)  // all copies in flight at once
+    for (int i = lane; i < m; i += 32) cp_async_4or8(S + i + (size_t)c * m, Y + i + (size_t)c * ld);
+  asm volatile("cp.async.wait_all;\n" ::);
+  __syncthreads();
+  const int npanels = (k + kQrNB - 1) / kQrNB;
+  for (int pi = 0; pi < npanels; ++pi) {
+    const int p0 = pi * kQrNB, pw = min(kQrNB, k - p0), mv = m - p0;
+    T* Vp = S + (size_t)p0 * m + p0;
+    // --- panel, with look-ahead: after reflector tt is known, warp 0 applies it to
+    //     column tt + 1 and at once forms reflector tt + 1 (its norm accumulated while
+    //     updating), while warps 1.. apply it to the panel's later columns; one barrier
+    //     per column
+    //     A reflector's tail stays unscaled in S (v_i = sc_j x_i, sc_j in vscale) until
+    //     the row-major copy is built, which saves a pass over the column.
+    if (wid == 0) {
+      T s0 = T(0), s1 = T(0);
+      for (int r = 1 + lane; r < mv; r += 32) {
+        const T v = Vp[r];
+        if (r & 32) s1 += v * v; else s0 += v * v;
+      }
+      const T s = warp_sum_all(s0 + s1);
+      const T x0 = Vp[0];
+      T tn = T(0), beta = x0, scale = T(1);
+      if (s > T(0)) {
+        const T nrm = sqrt(x0 * x0 + s);
+        beta = x0 >= T(0) ? -nrm : nrm;
+        tn = (beta - x0) / beta;
+        scale = T(1) / (x0 - beta);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        Vp[0] = beta;
+        tau[p0] = tn;
+        vscale[p0] = scale;
+      }
+    }
+    __syncthreads();
+    for (int tt = 0; tt + 1 < pw; ++tt) {
+      const T* vj = Vp + (size_t)tt * m;
+      const T tj = tau[p0 + tt], sj = vscale[p0 + tt];
+      for (int c = tt + 1 + wid; c < pw; c += nw) {
+        T* vc = Vp + (size_t)c * m;
+        T f = T(0);  // the update is vc -= f v_j = (f sc_j) x
+        if (tj != T(0)) {
+          T w0 = T(0), w1 = T(0), w2 = T(0), w3 = T(0);
+          int i = tt + 1 + lane;
+          for (; i + 96 < mv; i += 128) {
+            w0 += vj[i] * vc[i];
+            w1 += vj[i + 32] * vc[i + 32];
+            w2 += vj[i + 64] * vc[i + 64];
+            w3 += vj[i + 96] * vc[i + 96];
+          }
+          for (; i < mv; i += 32) w0 += vj[i] * vc[i];
+          const T ft = tj * (sj * warp_sum_all((w0 + w1) + (w2 + w3)) + vc[tt]);
+          __syncwarp();
+          if (lane == 0) vc[tt] -= ft;
+          f = ft * sj;
+        }
+        T s0 = T(0), s1 = T(0);
+        int r = tt + 1 + lane;
+        for (; r + 96 < mv; r += 128) {  // loads first: the stores cannot alias them
+          T a0 = vc[r], a1 = vc[r + 32], a2 = vc[r + 64], a3 = vc[r + 96];
+          const T b0 = vj[r], b1 = vj[r + 32], b2 = vj[r + 64], b3 = vj[r + 96];
+          a0 -= f * b0; a1 -= f * b1; a2 -= f * b2; a3 -= f * b3;
+          vc[r] = a0; vc[r + 32] = a1; vc[r + 64] = a2; vc[r + 96] = a3;
+          if (r > c) s0 += a0 * a0;
+          s1 += a1 * a1 + a2 * a2;
+          s0 += a3 * a3;
+        }
+        for (; r < mv; r += 32) {
+          const T a = vc[r] - f * vj[r];
+          vc[r] = a;
+          if (r > c) s1 += a * a;
+        }
+        if (c == tt + 1) {  // warp 0: the next reflector, from the column just updated
+          const T s = warp_sum_all(s0 + s1);
+          __syncwarp();
+          const T x0 = vc[c];
+          T tn = T(0), beta = x0, scale = T(1);
+          if (s > T(0)) {
+            const T nrm = sqrt(x0 * x0 + s);
+            beta = x0 >= T(0) ? -nrm : nrm;
+            tn = (beta - x0) / beta;
+            scale = T(1) / (x0 - beta);
+          }
+          __syncwarp();
+          if (lane == 0) {
+            vc[c] = beta;
+            tau[p0 + c] = tn;
+            vscale[p0 + c] = scale;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // --- the block's V, row-major, unit diagonal and zeros above written out
+    for (int i = threadIdx.x; i < mv; i += blockDim.x)
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s)
+        vr_at(Vr, m, i, s) = s < pw ? (i > s ? vscale[p0 + s] * Vp[i + (size_t)s * m] : (i == s ? T(1) : T(0))) : T(0);
+    __syncthreads();
+    // --- G = V^T V (strict upper part) in one pass over the rows, then the panel's T
+    //     column by column (lane r of warp 0 holds row r of T)
+    {
+      T gacc[kQrNB * (kQrNB - 1) / 2];
+#pragma unroll
+      for (int e = 0; e < kQrNB * (kQrNB - 1) / 2; ++e) gacc[e] = T(0);
+      for (int i = threadIdx.x; i < mv; i += blockDim.x) {
+        T v[kQrNB];
+        vr_row(Vr, m, i, v);
+        int e = 0;
+#pragma unroll
+        for (int b = 1; b < kQrNB; ++b)
+#pragma unroll
+          for (int a = 0; a < b; ++a) gacc[e++] += v[a] * v[b];
+      }
+#pragma unroll
+      for (int e = 0; e < kQrNB * (kQrNB - 1) / 2; ++e) {
+        const T g = warp_sum_all(gacc[e]);
+        if (lane == 0) Gred[wid][e] = g;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kQrNB * (kQrNB - 1) / 2) {
+      T g = T(0);
+      for (int w = 0; w < nw; ++w) g += Gred[w][threadIdx.x];
+      Gred[0][threadIdx.x] = g;  // packed: pair (a, b), a < b, at b (b - 1) / 2 + a
+    }
+    __syncthreads();
+    if (wid == 0) {
+      T trow[kQrNB];
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) trow[s] = T(0);
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s) {
+        if (s < pw) {
+          const T ts = tau[p0 + s];
+          T acc = T(0);
+#pragma unroll
+          for (int q = 0; q < s; ++q)
+            if (q >= lane) acc += trow[q] * Gred[0][s * (s - 1) / 2 + q];
+          trow[s] = lane < s ? -ts * acc : (lane == s ? ts : T(0));
+        }
+      }
+      if (lane < kQrNB)
+#pragma unroll
+        for (int s = 0; s < kQrNB; ++s) Tall[pi][lane][s] = trow[s];
+    }
+    __syncthreads();
+    // --- trailing columns: a -= V (T^T (V^T a)), local rows 0..mv-1
+    {
+      const int ntr = k - (p0 + pw);
+      if (CWMAX >= 4 && ntr > 32) qr_trail<T, 4, false>(S, Vr, Tall[pi], m, k, p0, pw);
+      else if (ntr > 16) qr_trail<T, 2, false>(S, Vr, Tall[pi], m, k, p0, pw);
+      else qr_trail<T, 1, false>(S, Vr, Tall[pi], m, k, p0, pw);
+    }
+    __syncthreads();
+  }
+  if (t.R) {
+    T* R = (T*)t.R;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int i = e % k, c = e / k;
+      R[i + (size_t)c * k] = (i <= c) ? S[i + (size_t)c * m] : T(0);
+    }
+  }
+  __syncthreads();
+  // --- Q = H_0 ... H_{k-1} [I; 0], panels backwards
+  for (int pi = npanels - 1; pi >= 0; --pi) {
+    const int p0 = pi * kQrNB, pw = min(kQrNB, k - p0), mv = m - p0;
+    T* Vp = S + (size_t)p0 * m + p0;
+    const T (*Tp)[kQrNB] = Tall[pi];
+    for (int i = threadIdx.x; i < mv; i += blockDim.x)
+#pragma unroll
+      for (int s = 0; s < kQrNB; ++s)
+        vr_at(Vr, m, i, s) = s < pw ? (i > s ? vscale[p0 + s] * Vp[i + (size_t)s * m] : (i == s ? T(1) : T(0))) : T(0);
+    __syncthreads();
+    if (threadIdx.x < kQrNB * kQrNB) {  // U8[j] = T V^T e_j for the panel's own columns
+      const int j = threadIdx.x / kQrNB, s = threadIdx.x % kQrNB;
+      T acc = T(0);
+      if (j < pw && s < pw)
+        for (int r = s; r < pw; ++r) acc += Tp[s][r] * vr_at(Vr, m, j, r);
+      U8[j][s] = acc;
+    }
+    __syncthreads();
+    // trailing Q columns c >= p0 + pw: local rows 0..pw-1 still hold R and are read as
+    // the zeros they are in Q at this stage (rows above p0 belong to earlier panels,
+    // which run after this one and write them)
+    {
+      const int ntr = k - (p0 + pw);
+      if (CWMAX >= 4 && ntr > 32) qr_trail<T, 4, true>(S, Vr, Tall[pi], m, k, p0, pw);
+      else if (ntr > 16) qr_trail<T, 2, true>(S, Vr, Tall[pi], m, k, p0, pw);
+      else qr_trail<T, 1, true>(S, Vr, Tall[pi], m, k, p0, pw);
+    }
+    // the panel's own columns: Q(i, j) = delta_ij - sum_s V(i, s) (T V^T e_j)_s
+    for (int i = threadIdx.x; i < mv; i += blockDim.x) {
+      T v[kQrNB];
+      vr_row(Vr, m, i, v);
+#pragma unroll
+      for (int j = 0; j < kQrNB; ++j)
+        if (j < pw) {
+          T q = i == j ? T(1) : T(0);
+#pragma unroll
+          for (int s = 0; s < kQrNB; ++s) q -= v[s] * U8[j][s];
+          Vp[i + (size_t)j * m] = q;
+        }
+    }
+    __syncthreads();
+  }
+  for (int c = wid; c < k; c += nw)
+    for (int i = lane; i < m; i += 32) Y[i + (size_t)c * ld] = S[i + (size_t)c * m];
+}
+
+// Static shared memory of k_qr_smem (tau, every panel's T, the G partial sums, U8).
+template <typename T>
+constexpr size_t qr_smem_static() {
+  return (512 + 256 / kQrNB * kQrNB * kQrNB + 16 * kQrNB * (kQrNB - 1) / 2 + kQrNB * kQrNB) * sizeof(T);
+}
+
+template <typename T>
+void launch_qr(const QrTask* tasks, int ntasks, int maxm, int64_t maxmk, int max_smem, cudaStream_t s) {
   if (ntasks <= 0) return;
+  // the panels, then (16-byte aligned) the row-major reflector block of the largest panel
+  const int64_t vr_off = (maxmk + 15) / 16 * 16;
+  const size_t whole = (size_t)(vr_off + (int64_t)kQrNB * maxm) * sizeof(T);
+  if (whole + qr_smem_static<T>() + 1024 <= (size_t)max_smem) {
+    k_qr_smem<T><<<ntasks, 512, whole, s>>>(tasks, vr_off);
+    return;
+  }
   const size_t vs = (size_t)maxm * kQrNB * sizeof(T);
   if (vs + 8192 <= (size_t)max_smem) {
     k_qr_blocked<T><<<ntasks, 512, vs, s>>>(tasks);
@@ -673,6 +1049,8 @@ void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStre
 }
 
 int dense_comp_setup(int max_smem) {
+  HM_CUDA(allow_max_dyn_smem(k_qr_smem<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_qr_smem<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_qr_blocked<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_qr_blocked<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_tsqr_blocks<float>, max_smem));
@@ -688,8 +1066,8 @@ int dense_comp_setup(int max_smem) {
 
 template void launch_omega<float>(const OmegaTask*, int, uint64_t, cudaStream_t);
 template void launch_omega<double>(const OmegaTask*, int, uint64_t, cudaStream_t);
-template void launch_qr<float>(const QrTask*, int, int, int, cudaStream_t);
-template void launch_qr<double>(const QrTask*, int, int, int, cudaStream_t);
+template void launch_qr<float>(const QrTask*, int, int, int64_t, int, cudaStream_t);
+template void launch_qr<double>(const QrTask*, int, int, int64_t, int, cudaStream_t);
 template void launch_tsqr<float>(const TsqrTask*, int, const TsqrBlock*, int, size_t, size_t, float*,
                                  cudaStream_t);
 template void launch_tsqr<double>(const TsqrTask*, int, const TsqrBlock*, int, size_t, size_t, double*,

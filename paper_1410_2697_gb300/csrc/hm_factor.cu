@@ -62,7 +62,10 @@ static void run_qr(hm_sys_s* sys, const QrBatch& b, const unsigned char* base) {
   if (b.plain.count == 0 && b.ts.count == 0) return;
   cudaStream_t s = sys->ctx->stream;
   ProfScope ps(sys->ctx, PC_QR, b.work, (b.plain.count ? 1 : 0) + (b.ts.count ? 3 : 0));
-  launch_qr<T>(b.plain.dev(base), b.plain.count, b.plain_maxm, sys->ctx->max_smem, s);
+  TuneScope ts(sys->ctx, TS_QR, b.sig);
+  // variant 1: keep the panels in global memory even where they fit in shared memory
+  const int64_t maxmk = sys->ctx->tune.variant(TS_QR, b.sig) == 1 ? INT64_MAX / 16 : b.plain_maxmk;
+  launch_qr<T>(b.plain.dev(base), b.plain.count, b.plain_maxm, maxmk, sys->ctx->max_smem, s);
   launch_tsqr<T>(b.ts.dev(base), b.ts.count, b.blocks.dev(base), b.blocks.count, b.smem_block, b.smem_stack,
                  (T*)sys->d_qrs, s);
 }
@@ -104,12 +107,14 @@ template <typename T>
 static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* base, int cat) {
   if (b.tiles.count == 0) return;
   ProfScope ps(sys->ctx, cat, b.tasks.work);
-  if (b.tc && sizeof(T) == 4)
+  if (b.tc && sizeof(T) == 4) {
     launch_gemm_tc(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, (float*)sys->plan.d_split_ws,
                    sys->plan.d_split_cnt, sys->d_err, sys->ctx->stream);
-  else
-    launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, (T*)sys->plan.d_split_ws,
-                   sys->plan.d_split_cnt, sys->ctx->stream);
+    return;
+  }
+  TuneScope ts(sys->ctx, TS_GEMM, b.sig);
+  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, sys->ctx->tune.variant(TS_GEMM, b.sig),
+                 (T*)sys->plan.d_split_ws, sys->plan.d_split_cnt, sys->ctx->stream);
 }
 
 template <typename T>

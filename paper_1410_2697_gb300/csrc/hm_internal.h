@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <unordered_map>
 #include <vector>
 
 #include "hm_common.cuh"
@@ -74,9 +75,27 @@ struct Span {
 struct GemmBatch {
   Span<GemmTask> tasks;
   Span<GemmTile> tiles;
-  int bn = 64;  // tile width of the batch
-  int tc = 0;   // 1: tensor-core BF16 kernel (128 x 64 tiles)
+  int bn = 64;       // tile width of the batch
+  int tc = 0;        // 1: tensor-core BF16 kernel (128 x 64 tiles)
+  uint64_t sig = 0;  // shape signature (autotuner key)
 };
+
+// Shape signatures: FNV-1a over the integers that fix a launch's shape, so the same
+// problem analysed again maps to the same autotuner choices.
+struct Sig {
+  uint64_t h = 1469598103934665603ull;
+  Sig& operator<<(int64_t v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (uint64_t)((v >> (8 * i)) & 0xff);
+      h *= 1099511628211ull;
+    }
+    return *this;
+  }
+};
+
+// Tunable launch sites and their variants (variant 0 is the built-in default).
+enum TuneSite { TS_GEMM = 1, TS_QR = 2, TS_DENSE_UP = 3, TS_DENSE_DOWN = 4 };
+inline uint64_t tune_key(int site, uint64_t sig) { return sig ^ ((uint64_t)site * 0x9e3779b97f4a7c15ull); }
 
 // Host builder of the task buffer (one upload after planning).
 struct TaskBuf {
@@ -118,6 +137,10 @@ struct TaskBuf {
     }
     split_ws = std::max(split_ws, ws);
     split_slots = std::max(split_slots, slots);
+    Sig sg;
+    sg << b.bn << b.tc << (int64_t)t.size() << (int64_t)tiles.size();
+    for (const auto& x : t) sg << x.m << x.n << x.k << (x.opA + 2 * x.opB + 4 * x.lower);
+    b.sig = sg.h;
     b.tasks = add(t);
     b.tiles = add(tiles);
     return b;
@@ -148,6 +171,27 @@ struct Profiler {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   cudaEvent_t get();
+};
+
+// Autotuner state of a context: the chosen variant per (site, shape signature), and,
+// while a tuning pass runs, the forced variant and one event pair per timed launch.
+struct TuneRec {
+  uint64_t key;
+  cudaEvent_t a, b;
+};
+struct Tuner {
+  std::unordered_map<uint64_t, int> choice;
+  int force = -1;   // >= 0 while tuning: every tunable site takes this variant
+  bool rec = false;
+  std::vector<TuneRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  cudaEvent_t get();
+  int variant(int site, uint64_t sig) const {
+    if (force >= 0) return force;
+    auto it = choice.find(tune_key(site, sig));
+    return it == choice.end() ? 0 : it->second;
+  }
 };
 
 // Per-front geometry of the plan.
@@ -190,10 +234,12 @@ struct HFront {
 struct QrBatch {
   Span<QrTask> plain;
   int plain_maxm = 0;
+  int64_t plain_maxmk = 0;  // largest m k of the plain panels (shared-memory-resident kernel)
   Span<TsqrTask> ts;
   Span<TsqrBlock> blocks;
   size_t smem_block = 0, smem_stack = 0;
   Work work;
+  uint64_t sig = 0;  // shape signature of the plain panels (autotuner key)
 };
 
 struct LevelFactorPlan {
@@ -325,6 +371,7 @@ struct hm_ctx_s {
   int max_smem = 0;
   int num_sms = 0;
   int last_nrhs = 0;             // right-hand-side count of the most recent apply plan
+  hm::Tuner tune;
   cudaMemPool_t pool = nullptr;  // stream-ordered pool; freed memory is kept for reuse
   std::vector<void*> allocs;
 };
@@ -435,6 +482,26 @@ struct ProfScope {
       cudaEvent_t b = ctx->prof.get();
       cudaEventRecord(b, ctx->stream);
       ctx->prof.recs.push_back(ProfRec{cat, a, b, w, nk});
+    }
+  }
+};
+
+// Times one tunable launch while a tuning pass runs (events on the context's stream).
+struct TuneScope {
+  hm_ctx_s* ctx;
+  uint64_t key;
+  cudaEvent_t a = nullptr;
+  TuneScope(hm_ctx_s* c, int site, uint64_t sig) : ctx(c), key(tune_key(site, sig)) {
+    if (ctx->tune.rec) {
+      a = ctx->tune.get();
+      cudaEventRecord(a, ctx->stream);
+    }
+  }
+  ~TuneScope() {
+    if (a) {
+      cudaEvent_t b = ctx->tune.get();
+      cudaEventRecord(b, ctx->stream);
+      ctx->tune.recs.push_back(TuneRec{key, a, b});
     }
   }
 };

@@ -46,13 +46,15 @@ static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, 
     int nb = (m + std::max(256, 2 * k) - 1) / std::max(256, 2 * k);
     const int nb_stack = kk > 0 ? (int)((budget - std::min(budget, (size_t)k * es)) / kk) : 0;
     nb = std::min(nb, nb_stack);
-    // Below about a thousand rows the single-CTA kernel finishes first: the three TSQR
-    // stages cost about as much as one pass of it over that many rows.
-    const bool fits = m > 1024 && k > 0 && nb >= 1 && m / nb >= k &&
+    // Up to two thousand rows a single CTA per panel finishes first (in shared memory
+    // where the launch's panels fit, else in global memory); the three TSQR stages
+    // cost more than that.
+    const bool fits = m > 2048 && k > 0 && nb >= 1 && m / nb >= k &&
                       (size_t)((m + nb - 1) / nb) * k * es <= budget;
     if (!fits) {
       plain.push_back(t);
       b.plain_maxm = std::max(b.plain_maxm, m);
+      b.plain_maxmk = std::max(b.plain_maxmk, (int64_t)m * k);
       continue;
     }
     for (int j = 0; j < nb; ++j) blocks.push_back(TsqrBlock{(int)ts.size(), j});
@@ -61,6 +63,9 @@ static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, 
     b.smem_block = std::max(b.smem_block, (size_t)((m + nb - 1) / nb) * k * es);
     b.smem_stack = std::max(b.smem_stack, ((size_t)nb * k * k + k) * es);
   }
+  Sig sg;
+  for (const QrTask& t : plain) sg << t.m << t.k;
+  b.sig = sg.h;
   b.plain = tb.add(plain);
   b.ts = tb.add(ts);
   b.blocks = tb.add(blocks);

@@ -248,8 +248,15 @@ __global__ void __launch_bounds__(NT) k_dense_down(const int* __restrict__ front
 static int rhs_block(int nrhs) { return nrhs >= 16 ? 16 : nrhs > 4 ? 8 : nrhs > 2 ? 4 : nrhs; }
 
 // 64 threads per front when every front of the level is small (more fronts in flight per
-// SM); 256 otherwise.
-static bool small_level(const LevelSolvePlan& lp) { return lp.dense_max_nhat <= 128; }
+// SM); 256 otherwise.  The autotuner's variant 1 takes the other width.
+static uint64_t dense_sig(const LevelSolvePlan& lp, int nrhs) {
+  Sig sg;
+  sg << nrhs << lp.dense.count << lp.dense_max_nhat << lp.dense_max_np;
+  return sg.h;
+}
+static bool narrow_level(const hm_ctx_s* ctx, int site, const LevelSolvePlan& lp, int nrhs) {
+  return (lp.dense_max_nhat <= 128) != (ctx->tune.variant(site, dense_sig(lp, nrhs)) == 1);
+}
 
 template <typename T, int RB, int NT>
 static void dense_up_launch(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys,
@@ -280,22 +287,22 @@ static void dense_down_launch(const LevelSolvePlan& lp, const unsigned char* bas
 template <typename T, int RB>
 static void dense_up_rb(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
                         int nrhs, const T* win, cudaStream_t s) {
-  if (small_level(lp)) dense_up_launch<T, RB, 64>(lp, base, sys, sp, nrhs, win, s);
+  if (narrow_level(sys->ctx, TS_DENSE_UP, lp, nrhs)) dense_up_launch<T, RB, 64>(lp, base, sys, sp, nrhs, win, s);
   else dense_up_launch<T, RB, 256>(lp, base, sys, sp, nrhs, win, s);
 }
 
 template <typename T, int RB>
 static void dense_down_rb(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
                           int nrhs, T* xv, cudaStream_t s) {
-  if (small_level(lp)) dense_down_launch<T, RB, 64>(lp, base, sys, sp, nrhs, xv, s);
+  if (narrow_level(sys->ctx, TS_DENSE_DOWN, lp, nrhs)) dense_down_launch<T, RB, 64>(lp, base, sys, sp, nrhs, xv, s);
   else dense_down_launch<T, RB, 256>(lp, base, sys, sp, nrhs, xv, s);
 }
 
 // Right-hand sides per block of the upward kernel: the block of the whole front vector
 // must fit in shared memory next to the reduction buffer.
 template <typename T>
-static int up_rhs_block(const LevelSolvePlan& lp, int nrhs, int max_smem) {
-  const int nt = small_level(lp) ? 64 : 256;
+static int up_rhs_block(const hm_ctx_s* ctx, const LevelSolvePlan& lp, int nrhs, int max_smem) {
+  const int nt = narrow_level(ctx, TS_DENSE_UP, lp, nrhs) ? 64 : 256;
   int rb = rhs_block(nrhs);
   while (rb > 1 && sizeof(T) * (size_t)rb * (lp.dense_max_nhat + nt) > (size_t)max_smem) rb /= 2;
   return rb;
@@ -304,7 +311,7 @@ static int up_rhs_block(const LevelSolvePlan& lp, int nrhs, int max_smem) {
 template <typename T>
 static int dense_up(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
                     int nrhs, const T* win, cudaStream_t s) {
-  const int rb = up_rhs_block<T>(lp, nrhs, sys->ctx->max_smem);
+  const int rb = up_rhs_block<T>(sys->ctx, lp, nrhs, sys->ctx->max_smem);
   if (sizeof(T) * (size_t)rb * (lp.dense_max_nhat + 256) > (size_t)sys->ctx->max_smem) {
     set_last_error("preconditioner apply: dense front too large for the upward kernel");
     return HM_ERR_CAPACITY;
@@ -351,7 +358,9 @@ template <typename T>
 static void gemm_b(hm_ctx_s* ctx, const SolvePlan* sp, const GemmBatch& b) {
   if (b.tiles.count == 0) return;
   ProfScope ps(ctx, PC_GEMM_APPLY, b.tasks.work);
-  launch_gemm<T>(b.tasks.dev(sp->d_tasks), b.tiles.dev(sp->d_tasks), b.tiles.count, b.bn, (T*)sp->d_split_ws,
+  TuneScope ts(ctx, TS_GEMM, b.sig);
+  launch_gemm<T>(b.tasks.dev(sp->d_tasks), b.tiles.dev(sp->d_tasks), b.tiles.count, b.bn,
+                 ctx->tune.variant(TS_GEMM, b.sig), (T*)sp->d_split_ws,
                  sp->d_split_cnt, ctx->stream);
 }
 
@@ -374,6 +383,7 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
     const LevelSolvePlan& lp = sp->levels[l];
     if (lp.dense.count) {
       ProfScope ps(ctx, PC_UP, lp.up_work);
+      TuneScope ts(ctx, TS_DENSE_UP, dense_sig(lp, nrhs));
       HM_TRY(dense_up<T>(lp, base, sys, sp, nrhs, win, s));
     }
     if (lp.n_hodlr) {
@@ -397,6 +407,7 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
     const LevelSolvePlan& lp = sp->levels[l];
     if (lp.dense.count) {
       ProfScope ps(ctx, PC_DOWN, lp.down_work);
+      TuneScope ts(ctx, TS_DENSE_DOWN, dense_sig(lp, nrhs));
       dense_down<T>(lp, base, sys, sp, nrhs, xfix, s);
     }
     if (lp.n_hodlr) {
@@ -450,7 +461,7 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout, bool rowmajor
   HM_TRY(get_solve_plan(sys, nrhs, &sp));
   hm_ctx_s* ctx = sys->ctx;
   cudaStream_t s = ctx->stream;
-  const bool graphs = !ctx->prof.on && s != nullptr;
+  const bool graphs = !ctx->prof.on && !ctx->tune.rec && s != nullptr;
   if (graphs && sp->graph_exec && sp->graph_in == (const void*)win) {
     HM_CUDA(cudaGraphLaunch(sp->graph_exec, s));
   } else if (graphs && sp->last_in == (const void*)win) {

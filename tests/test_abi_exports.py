@@ -44,6 +44,8 @@ def test_binding_mirrors_header(lib_path):
     for name in b.EXPORTED:
         if name not in ("hm_status_str", "hm_last_error"):
             assert callable(getattr(b, name))
+        # every entry point has its C argument types (ctypes cannot pass a float without them)
+        assert getattr(b._lib, name).argtypes is not None, name
 
 
 def test_status_strings_without_gpu(lib_path):
