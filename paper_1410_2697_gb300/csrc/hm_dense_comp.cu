@@ -939,7 +939,8 @@ constexpr int kJacobiSweeps = 12;
 template <typename T>
 __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, double tol) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ int rotated;
+  __shared__ int rotated, nlive;
+  __shared__ int live[256];
   const SvdTask t = tasks[blockIdx.x];
   const int k = t.k, ls = k + 1;
   T* M = reinterpret_cast<T*>(smem_raw);
@@ -955,31 +956,43 @@ __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, 
     V[i + c * ls] = (i == c) ? T(1) : T(0);
     f2 += v * v;
   }
-  // Pairs of columns that are both at rounding level of ||M||_F carry no information
-  // (their singular values fall far below any truncation tolerance) and are left alone;
-  // rotating them only shuffles rounding noise and keeps the sweeps from converging.
+  // A column at rounding level of ||M||_F carries no information (its singular value
+  // falls far below any truncation tolerance): pairs involving one are left alone, so
+  // such columns are compacted away and the sweeps run over the other columns only.
   const T floor2 = block_sum(f2, red) * JacobiEps<T>::v * JacobiEps<T>::v;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wid; c < k; c += nw) {
+    T s2 = T(0);
+    for (int i = lane; i < k; i += 32) s2 += M[i + c * ls] * M[i + c * ls];
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[c] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int c = 0; c < k; ++c)
+      if (sig[c] > floor2) live[n++] = c;
+    nlive = n;
+  }
+  __syncthreads();
+  const int kl = nlive, kk = kl + (kl & 1), npairs = kk / 2;
   // one 16-lane group per column pair; every group runs the same number of passes so
   // the width-16 shuffles are always executed by full warps
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gl = threadIdx.x & 15, gid = threadIdx.x >> 4, ng = blockDim.x >> 4;
-  const int kk = k + (k & 1);
-  const int npairs = kk / 2;
-  const T eps = JacobiEps<T>::v;
-  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+  const T eps2 = JacobiEps<T>::v * JacobiEps<T>::v;
+  for (int sweep = 0; sweep < kJacobiSweeps && kk > 1; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < kk - 1; ++r) {
       for (int base = 0; base < npairs; base += ng) {
+        // round-robin order over the live columns (position 0 fixed, the others rotate)
         const int pi = base + gid;
-        int a = 0, b = 0;
-        bool valid = pi < npairs;
-        if (valid) {
-          a = (pi == 0) ? 0 : 1 + ((pi - 1 + r) % (kk - 1));
-          b = 1 + ((kk - 2 - pi + r) % (kk - 1));
-          valid = a < k && b < k;
-        }
-        const int p = min(a, b), q = max(a, b);
+        int x = pi - 1 + r, y = kk - 2 - pi + r;
+        if (x >= kk - 1) x -= kk - 1;
+        if (y >= kk - 1) y -= kk - 1;
+        const int a = pi == 0 ? 0 : 1 + x, b = 1 + y;
+        const bool valid = pi < npairs && a < kl && b < kl;
+        const int p = valid ? min(live[a], live[b]) : 0, q = valid ? max(live[a], live[b]) : 0;
         T al = T(0), be = T(0), ga = T(0);
         if (valid)
           for (int i = gl; i < k; i += 16) {
@@ -994,7 +1007,7 @@ __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, 
           be += __shfl_xor_sync(0xffffffffu, be, o, 16);
           ga += __shfl_xor_sync(0xffffffffu, ga, o, 16);
         }
-        if (valid && ga != T(0) && fabs(ga) > eps * sqrt(al * be) && (al > floor2 || be > floor2)) {
+        if (valid && ga != T(0) && ga * ga > eps2 * (al * be)) {
           const T zeta = (be - al) / (T(2) * ga);
           const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           const T c = T(1) / sqrt(T(1) + tt * tt), sn = c * tt;
