@@ -10,6 +10,7 @@ from .meshes import (  # noqa: F401
     Problem,
     q1_square,
     hex_cube,
+    hex_elasticity,
     p1_jittered,
     rhs_uniform,
     lognormal_coefficients,

@@ -163,6 +163,85 @@ def hex_cube(m: int, coef: np.ndarray | None = None, name: str | None = None) ->
                    (m - 1, m - 1, m - 1), {"m": m, "h": h})
 
 
+def _hex_elasticity_ke(nu: float) -> np.ndarray:
+    """24 x 24 stiffness of isotropic linear elasticity (Young's modulus 1, Poisson ratio
+    nu) on a trilinear cube element of side 1, by 2 x 2 x 2 Gauss quadrature (exact for
+    this element); local node a = dx + 2 dy + 4 dz, unknown 3 a + c for component c.
+    For side h it scales by h."""
+    lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = 1.0 / (2.0 * (1.0 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] += 2.0 * mu
+    D[np.arange(3, 6), np.arange(3, 6)] = mu
+    g = 1.0 / np.sqrt(3.0)
+    K = np.zeros((24, 24))
+    sa = np.array([[2 * (a & 1) - 1, 2 * ((a >> 1) & 1) - 1, 2 * ((a >> 2) & 1) - 1] for a in range(8)], float)
+    for xi in (-g, g):
+        for eta in (-g, g):
+            for zeta in (-g, g):
+                p = np.array([xi, eta, zeta])
+                # dN_a/dx on the unit cube (x = (xi + 1) / 2): 2 * dN_a/dxi
+                dN = np.empty((8, 3))
+                for a in range(8):
+                    f = 1.0 + sa[a] * p
+                    dN[a, 0] = sa[a, 0] * f[1] * f[2] / 8.0 * 2.0
+                    dN[a, 1] = sa[a, 1] * f[0] * f[2] / 8.0 * 2.0
+                    dN[a, 2] = sa[a, 2] * f[0] * f[1] / 8.0 * 2.0
+                B = np.zeros((6, 24))
+                for a in range(8):
+                    dx, dy, dz = dN[a]
+                    c = 3 * a
+                    B[0, c] = dx
+                    B[1, c + 1] = dy
+                    B[2, c + 2] = dz
+                    B[3, c], B[3, c + 1] = dy, dx
+                    B[4, c + 1], B[4, c + 2] = dz, dy
+                    B[5, c], B[5, c + 2] = dz, dx
+                K += B.T @ D @ B * (1.0 / 8.0)  # Gauss weight 1, Jacobian (1/2)^3
+    return K
+
+
+def hex_elasticity(m: int, young: np.ndarray | None = None, nu: float = 0.3, name: str | None = None,
+                   dirichlet: bool = True) -> Problem:
+    """3D linear elasticity (3 displacement components per node) on the unit cube with
+    ``m^3`` trilinear hex elements, Young's modulus ``young[e]`` per element, Poisson
+    ratio ``nu``.  Every boundary node is clamped (eliminated): ``3 (m-1)^3`` unknowns,
+    unknown ``3 k + c`` = component c of interior node k (nodes lexicographic, x fastest);
+    all three components carry their node's lattice coordinates (``meta['dofs_per_node']``
+    = 3).  ``dirichlet=False`` keeps every node (the singular operator, for patch tests)."""
+    if young is None:
+        young = np.ones(m ** 3)
+    young = np.asarray(young, dtype=np.float64)
+    assert young.shape == (m ** 3,)
+    h = 1.0 / m
+    nn = m + 1
+    ez, ey, ex = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    ex, ey, ez = ex.reshape(-1), ey.reshape(-1), ez.reshape(-1)
+    node = lambda i, j, k: i + nn * (j + nn * k)  # noqa: E731
+    nconn = np.stack([node(ex + (a & 1), ey + ((a >> 1) & 1), ez + ((a >> 2) & 1)) for a in range(8)], axis=1)
+    conn = (3 * nconn[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 24)
+    ke = (young * h)[:, None, None] * _hex_elasticity_ke(nu)[None, :, :]
+    gk, gj, gi = np.meshgrid(np.arange(nn), np.arange(nn), np.arange(nn), indexing="ij")
+    gi, gj, gk = gi.reshape(-1), gj.reshape(-1), gk.reshape(-1)
+    if dirichlet:
+        keep = (gi > 0) & (gi < m) & (gj > 0) & (gj < m) & (gk > 0) & (gk < m)
+        lo, ext = 1, m - 1
+    else:
+        keep = np.ones(nn ** 3, dtype=bool)
+        lo, ext = 0, nn
+    node_index = np.full(nn ** 3, -1, dtype=np.int64)
+    node_index[keep] = (gi[keep] - lo) + ext * ((gj[keep] - lo) + ext * (gk[keep] - lo))
+    nodes = ext ** 3
+    dof_index = np.where(node_index[:, None] >= 0, 3 * node_index[:, None] + np.arange(3)[None, :], -1).reshape(-1)
+    rowptr, colidx, values = _assemble(3 * nn ** 3, conn, ke, dof_index, 3 * nodes)
+    kk, jj, ii = np.meshgrid(np.arange(ext), np.arange(ext), np.arange(ext), indexing="ij")
+    ncoords = np.stack([ii.reshape(-1), jj.reshape(-1), kk.reshape(-1)], axis=1).astype(np.int32)
+    coords = np.repeat(ncoords, 3, axis=0)
+    return Problem(name or f"hex_elasticity_{m}", 3 * nodes, 3, rowptr, colidx, values, coords,
+                   (ext, ext, ext), {"m": m, "h": h, "nu": nu, "dofs_per_node": 3})
+
+
 def p1_jittered(n_cells: int, seed: int, sigma: float = 1.0, jitter: float = 0.3,
                 name: str | None = None) -> Problem:
     """Unstructured 2D P1 triangle mesh: an ``n x n`` cell grid on the unit square,
@@ -240,10 +319,18 @@ def _cfg_hex64(m: int = 64):
                "nrhs": 1}
 
 
+def _cfg_elasticity40(m: int = 40):
+    young = lognormal_coefficients(m ** 3, sigma=0.5, mu=0.0, seed=51)
+    p = hex_elasticity(m, young, nu=0.3, name=f"elasticity_hex_{m}^3")
+    return p, {"tol": 1e-4, "leaf": 64, "n_c": 64, "restart": 30, "rtol": 1e-10, "rhs_seed": 52,
+               "nrhs": 1}
+
+
 WORKLOADS = {
     "q1_poisson_64x64": _cfg_poisson64,
     "q1_lognormal_1024x1024": _cfg_lognormal1024,
     "hex_lognormal_64^3": _cfg_hex64,
+    "elasticity_hex_40^3": _cfg_elasticity40,
 }
 
 

@@ -67,6 +67,10 @@ typedef struct hm_opts {
   int restart;           /* GMRES restart length m (30)                                  */
   size_t hbm_budget;     /* bytes the context may allocate on the device; 0 = no limit  */
   void* stream;          /* cudaStream_t to run on; NULL = a stream the context owns     */
+  int dofs_per_node;     /* unknowns per mesh node for geometric nested dissection (1;
+                            3 for 3D elasticity): unknown b k + c is component c of node
+                            k, all b share the node's grid_coords; separators then hold
+                            whole nodes, and a node's unknowns stay consecutive          */
 } hm_opts;
 
 typedef struct hm_solve_info {
@@ -87,7 +91,8 @@ typedef struct hm_factor_info {
 } hm_factor_info;
 
 /* Fill *opts with defaults (device 0, mixed precision, nd_leaf 64, hodlr_leaf 64,
-   n_c 64, samples 48, restart 30).  Never fails for a non-null pointer.              */
+   n_c 64, samples 48, restart 30, dofs_per_node 1).  Never fails for a non-null
+   pointer.                                                                           */
 int hm_default_opts(hm_opts* opts);
 
 /* Create a context on opts->device.  The context owns a CUDA stream (unless one is
@@ -166,6 +171,19 @@ int hm_get_symbolic(hm_sys_t sys, int32_t* nupd, int64_t* if_off, int32_t* if_li
  * hm_destroy).  Errors: HM_ERR_NOT_SPD, HM_ERR_BREAKDOWN, CUDA errors.
  */
 int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* info);
+
+/*
+ * Direct mode (the solver used on its own at a tight tolerance, Section 6): x = M^{-1} b
+ * with the factorization M of A, followed by `refine` steps of iterative refinement
+ * x += M^{-1} (b - A x) with the residual in FP64; no Krylov method.  b and x are
+ * n x nrhs column-major FP64 in the ORIGINAL numbering (host or device), nrhs <= 64,
+ * 0 <= refine <= 100.  info (may be NULL): iters = number of applications of M^{-1},
+ * relres = largest ||b - A x|| / ||b|| over the right-hand sides (and blocks of a batch),
+ * converged = 1.  The accuracy is what the factorization's tolerance delivers: tol = 0
+ * (every sampled direction kept) with FP64 gives x to rounding.
+ */
+int hm_direct_solve(hm_sys_t sys, int32_t nrhs, const double* b, int32_t refine, double* x,
+                    hm_solve_info* info);
 
 /*
  * Autotuner of the batched launches (one launch per elimination-tree level and stage,

@@ -100,12 +100,13 @@ def solve(fronts, et: ETree, sym: Symbolic, b_new: np.ndarray) -> np.ndarray:
     return x
 
 
-def direct_solve(rowptr, colidx, values, coords, b, leaf_size: int = 64, refine: int = 2):
+def direct_solve(rowptr, colidx, values, coords, b, leaf_size: int = 64, refine: int = 2,
+                 dofs_per_node: int = 1):
     """Exact ``x* = A^{-1} b`` (original numbering) by the conventional multifrontal
     method plus ``refine`` steps of FP64 iterative refinement."""
     from .nd import nested_dissection
     from .symbolic import symbolic
-    et = nested_dissection(coords, leaf_size)
+    et = nested_dissection(coords, leaf_size, dofs_per_node)
     sym = symbolic(rowptr, colidx, et)
     Ap = permuted_matrix(rowptr, colidx, values, et)
     fronts, _ = factor(Ap, et, sym)

@@ -19,6 +19,12 @@ oracle uses the following rule (shared, as a specification, with the CUDA path):
   separator's children are the roots of its two half-boxes, ``parent[root] = -1``.
 
 Every lattice point of the bounding box must be an unknown (full grids).
+
+Vector problems (``dofs_per_node`` b > 1, e.g. 3D elasticity): unknown ``b k + d`` is
+component d of node k, and all b components share the node's lattice point.  The rule
+above is applied to the nodes (leaf test: at most ``leaf_size // b`` nodes), and every
+node is then expanded into its b unknowns, consecutive in the new numbering, so that
+separators hold whole nodes.
 """
 from __future__ import annotations
 
@@ -56,8 +62,19 @@ def _box_points(lo, hi, lattice_to_old, ext):
     return lattice_to_old[lin]
 
 
-def nested_dissection(coords: np.ndarray, leaf_size: int = 64) -> ETree:
+def nested_dissection(coords: np.ndarray, leaf_size: int = 64, dofs_per_node: int = 1) -> ETree:
     """Postorder separator tree and permutation for unknowns at lattice ``coords``."""
+    if dofs_per_node > 1:
+        b = dofs_per_node
+        coords = np.asarray(coords, dtype=np.int64)
+        if coords.shape[0] % b or np.any(coords.reshape(-1, b, coords.shape[1]) != coords[::b, None, :]):
+            raise ValueError("nested_dissection: the b unknowns of a node must be consecutive and share coords")
+        et = nested_dissection(coords[::b], max(1, leaf_size // b))
+        d = np.arange(b, dtype=np.int32)
+        perm = (b * et.perm[:, None] + d[None, :]).reshape(-1).astype(np.int32)
+        iperm = np.empty_like(perm)
+        iperm[perm] = np.arange(perm.shape[0], dtype=np.int32)
+        return ETree(perm, iperm, (b * et.first).astype(np.int32), et.parent, et.level)
     coords = np.asarray(coords, dtype=np.int64)
     n, dim = coords.shape
     lo0 = coords.min(axis=0)

@@ -14,7 +14,7 @@ from __future__ import annotations
 from . import _binding as abi  # noqa: F401  (raises if the CUDA library is missing)
 from ._binding import (HM_PREC_FP64, HM_PREC_MIXED, HM_PREC_MIXED_BF16, HmError, hm_analyze,  # noqa: F401
                        hm_analyze_batch, hm_autotune, hm_create,
-                       hm_ctx_destroy, hm_default_opts, hm_destroy, hm_factor, hm_get_front_ranks,
+                       hm_ctx_destroy, hm_default_opts, hm_destroy, hm_direct_solve, hm_factor, hm_get_front_ranks,
                        hm_get_hodlr_block, hm_profile_enable, hm_profile_read,
                        hm_get_ordering, hm_get_sizes, hm_get_symbolic, hm_get_update,
                        hm_last_error, hm_precond_apply, hm_precond_apply_noalloc, hm_server_add_matrix,

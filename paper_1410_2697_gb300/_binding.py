@@ -30,7 +30,8 @@ HM_PREC_MIXED = 1
 HM_PREC_MIXED_BF16 = 2
 
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_analyze_batch", "hm_get_sizes",
-            "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_autotune", "hm_solve", "hm_precond_apply",
+            "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_autotune", "hm_solve", "hm_direct_solve",
+            "hm_precond_apply",
             "hm_precond_apply_noalloc",
             "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error",
             "hm_server_create", "hm_server_add_matrix", "hm_server_submit", "hm_server_wait",
@@ -41,7 +42,7 @@ class HmOpts(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("nd_leaf", C.c_int),
                 ("hodlr_leaf", C.c_int), ("n_c", C.c_int), ("samples", C.c_int),
                 ("seed", C.c_uint64), ("restart", C.c_int), ("hbm_budget", C.c_size_t),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("dofs_per_node", C.c_int)]
 
 
 class HmSolveInfo(C.Structure):
@@ -91,6 +92,7 @@ def _load():
     lib.hm_factor.argtypes = [vp, vp, dbl, C.POINTER(HmFactorInfo)]
     lib.hm_autotune.argtypes = [vp, vp, dbl, i32, i32, C.POINTER(i32)]
     lib.hm_solve.argtypes = [vp, i32, vp, dbl, i32, vp, C.POINTER(HmSolveInfo)]
+    lib.hm_direct_solve.argtypes = [vp, i32, vp, i32, vp, C.POINTER(HmSolveInfo)]
     lib.hm_precond_apply.argtypes = [vp, i32, vp, vp]
     lib.hm_precond_apply_noalloc.argtypes = [vp, i32, vp, vp]
     lib.hm_get_update.argtypes = [vp, i32, vp]
@@ -242,6 +244,14 @@ def hm_solve(sys_, nrhs: int, b, rtol: float, max_iters: int, x, raise_on_no_con
                        _ptr(x, np.float64, "x"), C.byref(info))
     ok = (HM_OK,) if raise_on_no_convergence else (HM_OK, HM_ERR_NO_CONVERGENCE)
     _check(st, "hm_solve", ok)
+    return {f: getattr(info, f) for f, _ in HmSolveInfo._fields_}
+
+
+def hm_direct_solve(sys_, nrhs: int, b, refine: int, x) -> dict:
+    """x = M^{-1} b plus `refine` steps of iterative refinement (no Krylov method)."""
+    info = HmSolveInfo()
+    _check(_lib.hm_direct_solve(sys_, int(nrhs), _ptr(b, np.float64, "b"), int(refine), _ptr(x, np.float64, "x"),
+                                C.byref(info)), "hm_direct_solve")
     return {f: getattr(info, f) for f, _ in HmSolveInfo._fields_}
 
 

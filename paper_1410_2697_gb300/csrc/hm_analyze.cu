@@ -71,6 +71,29 @@ __global__ void k_bbox(const int32_t* coords, int dim, const int32_t* bp, int ch
   }
 }
 
+// Vector problems: node k's coordinates (those of its first unknown b k); every one of
+// its b unknowns must carry the same ones.
+__global__ void k_node_coords(const int32_t* coords, int npts, int b, int dim, int32_t* pc, int* err) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npts) return;
+  for (int d = 0; d < dim; ++d) {
+    const int32_t v = coords[((size_t)k * b) * dim + d];
+    pc[(size_t)k * dim + d] = v;
+    for (int c = 1; c < b; ++c)
+      if (coords[((size_t)k * b + c) * dim + d] != v) raise_error(err, HM_ERR_INVALID_ARG, 7, k);
+  }
+}
+
+// Node ordering -> unknown ordering: node j's b unknowns take new indices b j .. b j + b - 1.
+__global__ void k_expand_perm(const int32_t* nperm, const int32_t* niperm, int npts, int b, int32_t* perm,
+                              int32_t* iperm) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= npts * b) return;
+  const int k = u / b, c = u - k * b;
+  perm[u] = b * nperm[k] + c;
+  iperm[u] = b * niperm[k] + c;
+}
+
 // Every lattice point of a block's bounding box must hold exactly one of its unknowns.
 __global__ void k_lattice_mark(const int32_t* coords, int n, int dim, const int32_t* bp, int nblocks,
                                const NdBlock* blks, unsigned* bitmap, int* err) {
@@ -705,10 +728,30 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
       return HM_ERR_INVALID_ARG;
     }
     sys->dim = dim;
-    const auto& bp = sys->h_seg_ptr;
+    // vector problems: the dissection runs on the nodes (points), b unknowns each
+    const int bdof = sys->ctx->opts.dofs_per_node;
+    if (n % bdof) { set_last_error("n must be a multiple of dofs_per_node"); return HM_ERR_INVALID_ARG; }
+    const int npts = n / bdof;
+    std::vector<int> bp(sys->h_seg_ptr.begin(), sys->h_seg_ptr.end());
+    for (auto& v : bp) {
+      if (v % bdof) { set_last_error("block boundaries must be multiples of dofs_per_node"); return HM_ERR_INVALID_ARG; }
+      v /= bdof;
+    }
+    int32_t* d_segp = sys->d_seg_ptr;
     int32_t* d_coords = nullptr;
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_coords, sizeof(int32_t) * (size_t)n * dim));
     HM_CUDA(cudaMemcpyAsync(d_coords, coords, sizeof(int32_t) * (size_t)n * dim, cudaMemcpyDefault, s));
+    int32_t* d_pc = d_coords;  // point coordinates
+    int32_t *d_pperm = sys->d_perm, *d_piperm = sys->d_iperm;
+    if (bdof > 1) {
+      HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_segp, sizeof(int32_t) * bp.size()));
+      HM_CUDA(cudaMemcpyAsync(d_segp, bp.data(), sizeof(int32_t) * bp.size(), cudaMemcpyHostToDevice, s));
+      HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_pc, sizeof(int32_t) * (size_t)npts * dim));
+      HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_pperm, sizeof(int32_t) * (size_t)npts));
+      HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_piperm, sizeof(int32_t) * (size_t)npts));
+      k_node_coords<<<(npts + 255) / 256, 256, 0, s>>>(d_coords, npts, bdof, dim, d_pc, sys->d_err);
+      HM_TRY(check_device_error(sys, "analyze: node coordinates"));
+    }
     // bounding box of every block
     int* d_bb = nullptr;
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_bb, 6 * sizeof(int) * (size_t)nblocks));
@@ -719,7 +762,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     int maxblk = 0;
     for (int b = 0; b < nblocks; ++b) maxblk = std::max(maxblk, bp[b + 1] - bp[b]);
     const int chunk = 256 * 16;
-    k_bbox<<<dim3(nblocks, (maxblk + chunk - 1) / chunk), 256, 0, s>>>(d_coords, dim, sys->d_seg_ptr, chunk, d_bb);
+    k_bbox<<<dim3(nblocks, (maxblk + chunk - 1) / chunk), 256, 0, s>>>(d_pc, dim, d_segp, chunk, d_bb);
     HM_CUDA(cudaMemcpyAsync(hbb.data(), d_bb, hbb.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     std::vector<NdBlock> blks(nblocks);
@@ -747,8 +790,8 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     NdBlock* d_blks = nullptr;
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_blks, sizeof(NdBlock) * (size_t)nblocks));
     HM_CUDA(cudaMemcpyAsync(d_blks, blks.data(), sizeof(NdBlock) * (size_t)nblocks, cudaMemcpyHostToDevice, s));
-    k_lattice_mark<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, sys->d_seg_ptr, nblocks, d_blks, bitmap,
-                                                   sys->d_err);
+    k_lattice_mark<<<(npts + 255) / 256, 256, 0, s>>>(d_pc, npts, dim, d_segp, nblocks, d_blks, bitmap,
+                                                      sys->d_err);
     HM_TRY(check_device_error(sys, "analyze: lattice check"));
     host_mark("analyze: bbox + lattice");
     // trees, one CTA per block
@@ -777,7 +820,8 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     HM_TRY(tmp_alloc(sys, &tmp, (void**)&d_level_t, sizeof(int) * cap));
     {
       ProfScope ps(sys->ctx, PC_ND, Work{0.0, 64.0 * cap});
-      k_nd_tree<<<nblocks, 1024, 0, s>>>(t, d_blks, dim, sys->ctx->opts.nd_leaf, d_first_t, d_parent_t,
+      k_nd_tree<<<nblocks, 1024, 0, s>>>(t, d_blks, dim, std::max(1, sys->ctx->opts.nd_leaf / bdof), d_first_t,
+                                         d_parent_t,
                                          d_level_t, sys->d_err);
     }
     std::vector<int> cnts(2 * (size_t)nblocks);
@@ -800,8 +844,10 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
       for (const auto& bk : blks) maxnodes = std::max(maxnodes, bk.nodes);
       k_nd_forest<<<dim3(nblocks, (maxnodes + 255) / 256), 256, 0, s>>>(d_blks, d_first_t, d_parent_t, d_level_t,
                                                                        d_first_f, d_parent_f, d_level_f);
-      k_nd_perm<<<(n + 255) / 256, 256, 0, s>>>(d_coords, n, dim, t, sys->d_seg_ptr, nblocks, d_blks,
-                                                sys->d_perm, sys->d_iperm);
+      k_nd_perm<<<(npts + 255) / 256, 256, 0, s>>>(d_pc, npts, dim, t, d_segp, nblocks, d_blks, d_pperm,
+                                                   d_piperm);
+      if (bdof > 1)
+        k_expand_perm<<<(n + 255) / 256, 256, 0, s>>>(d_pperm, d_piperm, npts, bdof, sys->d_perm, sys->d_iperm);
     }
     sys->h_first.resize(nf + 1);
     sys->h_parent.resize(nf);
@@ -811,6 +857,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     HM_CUDA(cudaMemcpyAsync(sys->h_level.data(), d_level_f, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
     HM_TRY(check_device_error(sys, "analyze: permutation"));
     host_mark("analyze: permutation");
+    for (int q = 0; q < nf; ++q) sys->h_first[q] *= bdof;  // points -> unknowns
     sys->h_first[nf] = n;
   } else {
     nf = nfronts_in;

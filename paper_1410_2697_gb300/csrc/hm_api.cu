@@ -180,6 +180,16 @@ struct SolveArgs {
   hm_solve_info* info;
 };
 
+struct DirectArgs {
+  int refine;
+  hm_solve_info* info;
+};
+
+static int direct_fn(hm_sys_t sys, int nrhs, const double* b, double* x, void* arg) {
+  DirectArgs* a = (DirectArgs*)arg;
+  return direct_impl(sys, nrhs, b, a->refine, x, a->info);
+}
+
 static int solve_fn(hm_sys_t sys, int nrhs, const double* b, double* x, void* arg) {
   SolveArgs* a = (SolveArgs*)arg;
   return gmres_impl(sys, nrhs, b, a->rtol, a->max_iters, x, a->info);
@@ -233,6 +243,7 @@ int hm_default_opts(hm_opts* o) {
   o->restart = 30;
   o->hbm_budget = 0;
   o->stream = nullptr;
+  o->dofs_per_node = 1;
   return HM_OK;
 }
 
@@ -247,9 +258,10 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   }
   const int kmax = o.precision == HM_PREC_FP64 ? 112 : 128;
   if (o.nd_leaf < 1 || o.hodlr_leaf < 2 || o.hodlr_leaf > 64 || o.n_c < 0 || o.n_c > 128 ||
-      o.samples < 1 || o.samples > kmax || o.restart < 1 || o.restart > 200) {
+      o.samples < 1 || o.samples > kmax || o.restart < 1 || o.restart > 200 || o.dofs_per_node < 1 ||
+      o.dofs_per_node > 8) {
     set_last_error("option out of range: nd_leaf>=1, 2<=hodlr_leaf<=64, 0<=n_c<=128, "
-                   "1<=samples<=" + std::to_string(kmax) + ", 1<=restart<=200");
+                   "1<=samples<=" + std::to_string(kmax) + ", 1<=restart<=200, 1<=dofs_per_node<=8");
     return HM_ERR_INVALID_ARG;
   }
   int ndev = 0;
@@ -536,6 +548,15 @@ int hm_solve(hm_sys_t sys, int32_t nrhs, const double* b, double rtol, int32_t m
   cudaSetDevice(sys->ctx->opts.device);
   SolveArgs a{rtol, max_iters, info};
   return with_device_io(sys, nrhs, b, x, solve_fn, &a);
+}
+
+int hm_direct_solve(hm_sys_t sys, int32_t nrhs, const double* b, int32_t refine, double* x,
+                    hm_solve_info* info) {
+  if (!sys || !b || !x || nrhs < 1 || nrhs > 64 || refine < 0 || refine > 100) return HM_ERR_INVALID_ARG;
+  if (!sys->factored) { set_last_error("hm_direct_solve before hm_factor"); return HM_ERR_STATE; }
+  cudaSetDevice(sys->ctx->opts.device);
+  DirectArgs a{refine, info};
+  return with_device_io(sys, nrhs, b, x, direct_fn, &a);
 }
 
 int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z) {

@@ -562,6 +562,78 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
   return done ? HM_OK : HM_ERR_NO_CONVERGENCE;
 }
 
+// x += z (z in the factor's precision), column-major n x nrhs.
+template <typename T>
+__global__ void k_add_cast(double* __restrict__ x, const T* __restrict__ z, int64_t nn) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += (double)z[e];
+}
+
+// Direct mode: x = M^{-1} b, then `refine` steps x += M^{-1} (b - A x) with the FP64
+// residual; the relative residual of every instance is reported.
+template <typename T>
+static int direct_t(hm_sys_s* sys, int nrhs, const double* d_b, int refine, double* d_x, hm_solve_info* info) {
+  const int m = std::max(1, sys->ctx->opts.restart);
+  HM_TRY(ensure_workspace(sys, nrhs, m));  // the GMRES workspace: b, x, r, staging, norms
+  auto& G = sys->gm;
+  cudaStream_t s = sys->ctx->stream;
+  const int n = sys->n;
+  const int64_t nn = (int64_t)n * nrhs;
+  const int stride = m + 2;
+  const int ninst = nrhs * sys->nseg;
+  T* zT = (T*)G.Z;  // first Krylov block as the apply's output
+  const unsigned eg = (unsigned)std::min<int64_t>((nn + 255) / 256, 4096);
+  {
+    ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, 20.0 * nn});
+    launch_permute_in(d_b, G.b, sys->d_perm, n, nrhs, s);
+    HM_CUDA(cudaMemsetAsync(G.x, 0, sizeof(double) * nn, s));
+    HM_CUDA(cudaMemcpyAsync(G.r, G.b, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  }
+  for (int it = 0; it <= refine; ++it) {
+    {
+      ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, (8.0 + sizeof(T)) * nn});
+      launch_cast_to<T>(G.r, (T*)G.wT, nn, s);
+    }
+    HM_TRY(apply_impl(sys, nrhs, G.wT, zT));
+    {
+      ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, (16.0 + sizeof(T)) * nn});
+      k_add_cast<T><<<eg, 256, 0, s>>>(G.x, zT, nn);
+    }
+    {
+      ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});
+      k_spmv<double><<<spmv_grid(n, nrhs), 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+                                                        G.x, n, G.r, n, G.b, n);
+    }
+  }
+  double* bn2 = G.hv + 2 * (int64_t)ninst * stride;
+  double* rss = bn2 + ninst;
+  sqnorm(sys, G.b, bn2, 1, nrhs);
+  sqnorm(sys, G.r, rss, 1, nrhs);
+  std::vector<double> hb(ninst), hr(ninst);
+  HM_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
+  {
+    ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, 20.0 * nn});
+    launch_permute_out(G.x, d_x, sys->d_perm, n, nrhs, s);
+  }
+  HM_CUDA(cudaStreamSynchronize(s));
+  HM_CUDA(cudaGetLastError());
+  if (info) {
+    double mx = 0;
+    for (int r = 0; r < ninst; ++r) mx = std::max(mx, hb[r] > 0 ? std::sqrt(hr[r] / hb[r]) : 0.0);
+    info->iters = refine + 1;
+    info->restarts = 0;
+    info->relres = mx;
+    info->converged = 1;
+  }
+  return check_device_error(sys, "direct solve");
+}
+
+int direct_impl(hm_sys_s* sys, int nrhs, const double* d_b, int refine, double* d_x, hm_solve_info* info) {
+  if (sys->precision == HM_PREC_FP64) return direct_t<double>(sys, nrhs, d_b, refine, d_x, info);
+  return direct_t<float>(sys, nrhs, d_b, refine, d_x, info);
+}
+
 int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters, double* d_x,
                hm_solve_info* info) {
   if (sys->precision == HM_PREC_FP64) return gmres_t<double>(sys, nrhs, d_b, rtol, max_iters, d_x, info);

@@ -530,6 +530,7 @@ int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 // As apply_impl, with z written row-major (element (i, r) at i nrhs + r).
 int apply_impl_rowmajor(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 int solve_setup(int max_smem);
+int direct_impl(hm_sys_s* sys, int nrhs, const double* d_b, int refine, double* d_x, hm_solve_info* info);
 int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
                double* d_x, hm_solve_info* info);
 // permutation helpers (new <-> original numbering), FP64 n x nrhs

@@ -9,7 +9,7 @@ import pytest
 import scipy.linalg as sla
 import scipy.sparse.linalg as spl
 
-from fixtures import hex_cube, p1_jittered, q1_square, rhs_uniform, lognormal_coefficients
+from fixtures import hex_cube, hex_elasticity, p1_jittered, q1_square, rhs_uniform, lognormal_coefficients
 from oracle import dense_mf, gmres, hodlr, hodlr_mf, nd, symbolic
 from oracle.philox import philox4x32_10, sketch
 
@@ -42,6 +42,46 @@ def test_hex_closed_form_eigenvalues(m):
     ev = np.linalg.eigvalsh(p.scipy().toarray())
     np.testing.assert_allclose(np.sort(ev), np.sort(lam.ravel()), atol=1e-13)
     assert p.nnz == (3 * (m - 1) - 2) ** 3
+
+
+def test_elasticity_element_closed_forms():
+    """Trilinear-hex elasticity element: (i) nu = 0 diagonal entry = 2/9 on the unit cube
+    (E times the x-part of the hex Laplacian diagonal, 1/9, plus mu = 1/2 times its y and
+    z parts, 2/9); (ii) the null space is exactly the 6 rigid-body motions; (iii) scaling
+    with Young's modulus and side h."""
+    from fixtures.meshes import _hex_elasticity_ke
+    K0 = _hex_elasticity_ke(0.0)
+    assert abs(K0[0, 0] - 2.0 / 9.0) < 1e-14
+    K = _hex_elasticity_ke(0.3)
+    assert np.abs(K - K.T).max() < 1e-15
+    x = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], float)
+    modes = []
+    for c in range(3):  # translations
+        u = np.zeros((8, 3)); u[:, c] = 1.0; modes.append(u.reshape(-1))
+    for w in np.eye(3):  # infinitesimal rotations u = w x x
+        modes.append(np.cross(w, x).reshape(-1))
+    R = np.array(modes).T
+    assert np.abs(K @ R).max() < 1e-14
+    ev = np.linalg.eigvalsh(K)
+    assert np.all(np.abs(ev[:6]) < 1e-14) and ev[6] > 1e-2
+    p1, p2 = hex_elasticity(3), hex_elasticity(3, 2.5 * np.ones(27))
+    np.testing.assert_allclose(p2.values, 2.5 * p1.values, rtol=1e-13, atol=1e-15)
+
+
+def test_elasticity_patch_test():
+    """Constant strain is exact: with uniform moduli the full (unclamped) operator
+    applied to an affine displacement field vanishes at every interior node; a quadratic
+    field does not (so the check sees the assembly)."""
+    m = 5
+    p = hex_elasticity(m, 1.7 * np.ones(m ** 3), nu=0.27, dirichlet=False)
+    nodes = p.coords[::3].astype(float) / m
+    G = np.array([[0.3, -1.1, 0.2], [0.5, 0.1, -0.4], [-0.7, 0.9, 0.6]])
+    u = (nodes @ G.T + np.array([0.1, -0.2, 0.3])).reshape(-1)
+    r = (p.scipy() @ u).reshape(-1, 3)
+    inner = np.all((p.coords[::3] > 0) & (p.coords[::3] < m), axis=1)
+    assert np.abs(r[inner]).max() < 1e-12 * np.abs(p.values).max()
+    q = (nodes ** 2 @ G.T).reshape(-1)
+    assert np.abs((p.scipy() @ q).reshape(-1, 3)[inner]).max() > 1e-3
 
 
 def test_p1_mesh_spd_and_consistent():
@@ -104,13 +144,18 @@ def _dense_symbolic_cholesky(Ap):
 
 
 @pytest.mark.parametrize("maker", [lambda: q1_square(10), lambda: q1_square(13),
-                                   lambda: hex_cube(6), lambda: p1_jittered(11, 9)])
+                                   lambda: hex_cube(6), lambda: p1_jittered(11, 9),
+                                   lambda: hex_elasticity(5, lognormal_coefficients(125, 0.5, seed=3))])
 def test_nd_and_front_sets_match_brute_force_fill(maker):
     """I_p^f equals the rows (after I_p) of the Cholesky fill of P A P^T in the
     columns of I_p; the permutation is one; the tree is a postorder; the two halves
-    below a separator are not adjacent."""
+    below a separator are not adjacent (vector problems: with whole nodes)."""
     p = maker()
-    et = nd.nested_dissection(p.coords, leaf_size=8)
+    bdof = p.meta.get("dofs_per_node", 1)
+    et = nd.nested_dissection(p.coords, leaf_size=8 * bdof, dofs_per_node=bdof)
+    if bdof > 1:  # a node's components stay consecutive, in component order
+        assert np.all(et.perm.reshape(-1, bdof) == et.perm[::bdof, None] + np.arange(bdof))
+        assert np.all(et.first % bdof == 0)
     assert np.array_equal(np.sort(et.perm), np.arange(p.n))
     assert np.array_equal(et.iperm[et.perm], np.arange(p.n))
     nf = et.nfronts
@@ -171,12 +216,13 @@ def test_nd_rule_on_a_hand_checked_grid():
 
 # ----------------------------------------------------------------------------- dense MF
 @pytest.mark.parametrize("maker", [lambda: q1_square(12), lambda: hex_cube(5),
-                                   lambda: p1_jittered(10, 3)])
+                                   lambda: p1_jittered(10, 3), lambda: hex_elasticity(4)])
 def test_dense_mf_equals_global_cholesky(maker):
     """Front factors are the blocks of numpy's Cholesky of P A P^T (Eq. update is the
     Schur complement), and the solve inverts A."""
     p = maker()
-    et = nd.nested_dissection(p.coords, leaf_size=8)
+    bdof = p.meta.get("dofs_per_node", 1)
+    et = nd.nested_dissection(p.coords, leaf_size=8 * bdof, dofs_per_node=bdof)
     sym = symbolic.symbolic(p.rowptr, p.colidx, et)
     Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
     Lg = np.linalg.cholesky(Ap.toarray())
@@ -190,7 +236,7 @@ def test_dense_mf_equals_global_cholesky(maker):
     rng = np.random.default_rng(0)
     xs = rng.standard_normal(p.n)
     A = p.scipy()
-    x = dense_mf.direct_solve(p.rowptr, p.colidx, p.values, p.coords, A @ xs, leaf_size=8)
+    x = dense_mf.direct_solve(p.rowptr, p.colidx, p.values, p.coords, A @ xs, leaf_size=8 * bdof, dofs_per_node=bdof)
     np.testing.assert_allclose(x, xs, rtol=0, atol=1e-10 * np.abs(xs).max())
 
 
