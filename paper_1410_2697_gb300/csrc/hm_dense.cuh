@@ -63,8 +63,10 @@ struct CholSolveTask {
 // Householder QR of Y (m x k, ld): Q overwrites Y; R (k x k, ld k) written if non-null.
 struct QrTask {
   void* Y;
-  void* R;
+  void* R;         // upper k x k factor (NULL: not wanted), leading dimension ldr (0: k)
   int m, k, ld, pad;
+  void* Q;         // the explicit Q goes here (leading dimension ldq) instead of into Y
+  int ldr, ldq;    // (shared-memory kernel only)
 };
 
 // Tall-skinny QR of an m x k panel (same contract as QrTask) in nb row blocks; the

@@ -653,9 +653,10 @@ __global__ void __launch_bounds__(512) k_qr_smem(const QrTask* __restrict__ task
   }
   if (t.R) {
     T* R = (T*)t.R;
+    const int ldr = t.ldr > 0 ? t.ldr : k;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
       const int i = e % k, c = e / k;
-      R[i + (size_t)c * k] = (i <= c) ? S[i + (size_t)c * m] : T(0);
+      R[i + (size_t)c * ldr] = (i <= c) ? S[i + (size_t)c * m] : T(0);
     }
   }
   __syncthreads();
@@ -701,8 +702,10 @@ __global__ void __launch_bounds__(512) k_qr_smem(const QrTask* __restrict__ task
     }
     __syncthreads();
   }
+  T* __restrict__ Qo = t.Q ? (T*)t.Q : Y;
+  const int ldo = t.Q ? t.ldq : ld;
   for (int c = wid; c < k; c += nw)
-    for (int i = lane; i < m; i += 32) Y[i + (size_t)c * ld] = S[i + (size_t)c * m];
+    for (int i = lane; i < m; i += 32) Qo[i + (size_t)c * ldo] = S[i + (size_t)c * m];
 }
 
 // Static shared memory of k_qr_smem (tau, every panel's T, the G partial sums, U8).

@@ -59,15 +59,22 @@ __global__ void __launch_bounds__(256) k_extend_add(const int* __restrict__ pare
 
 template <typename T>
 static void run_qr(hm_sys_s* sys, const QrBatch& b, const unsigned char* base) {
-  if (b.plain.count == 0 && b.ts.count == 0) return;
+  if (b.plain.count == 0 && b.ts.count == 0 && b.stack.count == 0) return;
   cudaStream_t s = sys->ctx->stream;
-  ProfScope ps(sys->ctx, PC_QR, b.work, (b.plain.count ? 1 : 0) + (b.ts.count ? 3 : 0));
+  ProfScope ps(sys->ctx, PC_QR, b.work, (b.plain.count ? 1 : 0) + (b.ts.count ? 3 : 0) + (b.stack.count ? 2 : 0));
   TuneScope ts(sys->ctx, TS_QR, b.sig);
   // variant 1: keep the panels in global memory even where they fit in shared memory
-  const int64_t maxmk = sys->ctx->tune.variant(TS_QR, b.sig) == 1 ? INT64_MAX / 16 : b.plain_maxmk;
+  // (not with row blocks, whose outputs only the shared-memory kernel redirects)
+  const bool global = sys->ctx->tune.variant(TS_QR, b.sig) == 1 && b.stack.count == 0;
+  const int64_t maxmk = global ? INT64_MAX / 16 : b.plain_maxmk;
   launch_qr<T>(b.plain.dev(base), b.plain.count, b.plain_maxm, maxmk, sys->ctx->max_smem, s);
   launch_tsqr<T>(b.ts.dev(base), b.ts.count, b.blocks.dev(base), b.blocks.count, b.smem_block, b.smem_stack,
                  (T*)sys->d_qrs, s);
+  if (b.stack.count) {  // row-blocked panels: the stacked R factors, then Y_b = Q_b Q_stack,b
+    launch_qr<T>(b.stack.dev(base), b.stack.count, b.stack_maxm, b.stack_maxmk, sys->ctx->max_smem, s);
+    launch_gemm<T>(b.combine.tasks.dev(base), b.combine.tiles.dev(base), b.combine.tiles.count, b.combine.bn, 0,
+                   (T*)sys->plan.d_split_ws, sys->plan.d_split_cnt, s);
+  }
 }
 
 // Debug facility (environment HM_DEBUG_SYNC=1): after each stage of the factorization,

@@ -101,6 +101,18 @@ inline uint64_t tune_key(int site, uint64_t sig) { return sig ^ ((uint64_t)site 
 struct TaskBuf {
   std::vector<unsigned char> host;
   int es = 4;
+  // Byte positions of pointer fields that hold byte offsets into an arena allocated
+  // after planning (the panel-QR scratch); the base is added before the upload.
+  std::vector<size_t> relocs;
+  void relocate(const void* base) {
+    for (size_t pos : relocs) {
+      uintptr_t v;
+      memcpy(&v, host.data() + pos, sizeof(v));
+      v += (uintptr_t)base;
+      memcpy(host.data() + pos, &v, sizeof(v));
+    }
+    relocs.clear();
+  }
   template <typename TaskT>
   Span<TaskT> add(const std::vector<TaskT>& v) {
     Span<TaskT> s;
@@ -240,6 +252,13 @@ struct QrBatch {
   size_t smem_block = 0, smem_stack = 0;
   Work work;
   uint64_t sig = 0;  // shape signature of the plain panels (autotuner key)
+  // Panels beyond shared memory, in row blocks: the blocks go with the plain panels
+  // (Q_b to scratch, R_b stacked), then the stacks of R_b (stack), then
+  // Y_b = Q_b Q_stack,b (combine).
+  Span<QrTask> stack;
+  int stack_maxm = 0;
+  int64_t stack_maxmk = 0;
+  GemmBatch combine;
 };
 
 struct LevelFactorPlan {

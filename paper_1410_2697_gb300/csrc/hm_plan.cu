@@ -1,6 +1,7 @@
 // hm_plan.cu -- host-side planning: front geometry, HODLR block layout, device arenas and
 // the per-level task tables of the factorization and of the preconditioner apply.
 // Integer bookkeeping only; all arithmetic of the method runs in the kernels.
+#include <cstddef>
 #include <algorithm>
 #include <cstring>
 
@@ -29,32 +30,75 @@ static GemmTask gemm(const void* A, int lda, int opA, const void* B, int ldb, in
   return t;
 }
 
-// Splits the panel QRs of one launch group into TSQR panels (row blocks and the stacked
-// R factors in shared memory) and panels left to the global-memory kernel.
+// Splits the panel QRs of one launch group.  A panel that fits in shared memory whole
+// (with its row-major reflector block) goes to the shared-memory kernel.  A larger one
+// is cut into row blocks that fit: each block is factored by the same kernel (Q_b to
+// scratch, R_b into a stack of the blocks' R factors), the stack is factored next
+// (its Q in place, the panel's R), and Y_b = Q_b (rows b of the stack's Q) by a batched
+// GEMM.  Panels whose stack would not fit either use the three-stage TSQR, else the
+// global-memory kernel.
 static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, int max_smem,
                              int64_t* scratch_need) {
   QrBatch b;
-  std::vector<QrTask> plain;
+  std::vector<QrTask> plain, stack;
   std::vector<TsqrTask> ts;
   std::vector<TsqrBlock> blocks;
+  std::vector<GemmTask> cmb;
+  std::vector<int> plain_rel;  // plain tasks whose R and Q hold scratch offsets
   const size_t budget = (size_t)std::max(0, max_smem - 2048);
+  auto smem_fits = [&](int64_t m, int k) {
+    return ((size_t)((m * k + 15) / 16 * 16) + (size_t)8 * m) * es + (size_t)20 * 1024 <= (size_t)max_smem;
+  };
+  auto scratch = [&](int64_t elems) { return (void*)(uintptr_t)(elems * es); };
   int64_t off = 0;
   for (const QrTask& t : v) {
     b.work += work_of(t, es);
     const int m = t.m, k = t.k;
+    if (k <= 0 || smem_fits(m, k)) {
+      plain.push_back(t);
+      continue;
+    }
+    int mfit = (int)(((int64_t)max_smem - 20 * 1024) / es / (k + 8)) - 16;
+    while (mfit > k && !smem_fits(mfit, k)) --mfit;
+    const int nbr = mfit > 0 ? (m + mfit - 1) / mfit : 0;
+    const int mb = nbr > 0 ? (m + nbr - 1) / nbr : 0;
+    if (nbr >= 2 && m - (nbr - 1) * mb >= k && smem_fits((int64_t)nbr * k, k)) {
+      const int64_t qoff = off, soff = off + (int64_t)m * k;
+      off = soff + (int64_t)nbr * k * k;
+      for (int bi = 0, r0 = 0; bi < nbr; ++bi, r0 += mb) {
+        const int rows = std::min(mb, m - r0);
+        QrTask bt{};
+        bt.Y = (unsigned char*)t.Y + (size_t)r0 * es;
+        bt.R = scratch(soff + (int64_t)bi * k);
+        bt.m = rows;
+        bt.k = k;
+        bt.ld = t.ld;
+        bt.Q = scratch(qoff + (int64_t)r0 * k);
+        bt.ldr = nbr * k;
+        bt.ldq = rows;
+        plain_rel.push_back((int)plain.size());
+        plain.push_back(bt);
+        cmb.push_back(gemm(bt.Q, rows, 0, scratch(soff + (int64_t)bi * k), nbr * k, 0,
+                           (unsigned char*)t.Y + (size_t)r0 * es, t.ld, rows, k, k, 1.0, 0.0));
+      }
+      QrTask st{};
+      st.Y = scratch(soff);
+      st.R = t.R;
+      st.m = nbr * k;
+      st.k = k;
+      st.ld = nbr * k;
+      stack.push_back(st);
+      b.stack_maxm = std::max(b.stack_maxm, nbr * k);
+      b.stack_maxmk = std::max(b.stack_maxmk, (int64_t)nbr * k * k);
+      continue;
+    }
     const size_t kk = (size_t)k * k * es;
     int nb = (m + std::max(256, 2 * k) - 1) / std::max(256, 2 * k);
     const int nb_stack = kk > 0 ? (int)((budget - std::min(budget, (size_t)k * es)) / kk) : 0;
     nb = std::min(nb, nb_stack);
-    // Up to two thousand rows a single CTA per panel finishes first (in shared memory
-    // where the launch's panels fit, else in global memory); the three TSQR stages
-    // cost more than that.
-    const bool fits = m > 2048 && k > 0 && nb >= 1 && m / nb >= k &&
-                      (size_t)((m + nb - 1) / nb) * k * es <= budget;
+    const bool fits = nb >= 1 && m / nb >= k && (size_t)((m + nb - 1) / nb) * k * es <= budget;
     if (!fits) {
       plain.push_back(t);
-      b.plain_maxm = std::max(b.plain_maxm, m);
-      b.plain_maxmk = std::max(b.plain_maxmk, (int64_t)m * k);
       continue;
     }
     for (int j = 0; j < nb; ++j) blocks.push_back(TsqrBlock{(int)ts.size(), j});
@@ -64,9 +108,27 @@ static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, 
     b.smem_stack = std::max(b.smem_stack, ((size_t)nb * k * k + k) * es);
   }
   Sig sg;
-  for (const QrTask& t : plain) sg << t.m << t.k;
+  for (const QrTask& t : plain) {
+    sg << t.m << t.k;
+    b.plain_maxm = std::max(b.plain_maxm, t.m);
+    b.plain_maxmk = std::max(b.plain_maxmk, (int64_t)t.m * t.k);
+  }
   b.sig = sg.h;
   b.plain = tb.add(plain);
+  for (int i : plain_rel) {
+    const size_t base = b.plain.off + (size_t)i * sizeof(QrTask);
+    tb.relocs.push_back(base + offsetof(QrTask, R));
+    tb.relocs.push_back(base + offsetof(QrTask, Q));
+  }
+  b.stack = tb.add(stack);
+  for (int i = 0; i < (int)stack.size(); ++i)
+    tb.relocs.push_back(b.stack.off + (size_t)i * sizeof(QrTask) + offsetof(QrTask, Y));
+  b.combine = tb.add_gemm(cmb);
+  for (int i = 0; i < (int)cmb.size(); ++i) {
+    const size_t base = b.combine.tasks.off + (size_t)i * sizeof(GemmTask);
+    tb.relocs.push_back(base + offsetof(GemmTask, A));
+    tb.relocs.push_back(base + offsetof(GemmTask, B));
+  }
   b.ts = tb.add(ts);
   b.blocks = tb.add(blocks);
   *scratch_need = std::max(*scratch_need, off);
@@ -462,6 +524,7 @@ int build_plan(hm_sys_s* sys) {
   }
   P.factor_bytes = fbytes;
   HM_TRY(dev_alloc(sys, &sys->d_qrs, (size_t)std::max<int64_t>(P.qr_scratch, 1) * es));
+  tb.relocate(sys->d_qrs);  // row-block QR tasks address the scratch by offset until now
   HM_TRY(dev_alloc(sys, &P.d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
   HM_TRY(dev_alloc(sys, (void**)&P.d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));
   HM_CUDA(cudaMemsetAsync(P.d_split_cnt, 0, sizeof(unsigned) * std::max(tb.split_slots, 1), sys->ctx->stream));
