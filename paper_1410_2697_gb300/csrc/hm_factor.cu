@@ -223,6 +223,7 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
         debug_stage<T>(sys, "core-lu", l);
         run_gemm<T>(sys, H.sg, base, PC_GEMM_FACTOR);
         run_gemm<T>(sys, H.upd, base, PC_GEMM_FACTOR);
+        run_gemm<T>(sys, H.gm, base, PC_GEMM_FACTOR);
         debug_stage<T>(sys, "core-upd", l);
       }
       run_gemm<T>(sys, lp.schurT, base, PC_GEMM_FACTOR);

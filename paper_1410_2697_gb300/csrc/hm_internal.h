@@ -232,6 +232,7 @@ struct HFront {
   std::vector<int> col;    // column offset of each level in Bo / X
   int xc;                  // total columns of Bo / X
   int64_t bo_off;          // np x xc (same offsets in the Bo and X arenas)
+  int64_t g_off;           // np x 2 (xc - kf): G of every level (the apply's Zhat C^{-1})
   int64_t w_off;           // nu x kf
   int64_t t_off;           // kf x kf
   int64_t p_off;           // nu x kf
@@ -290,6 +291,7 @@ struct LevelFactorPlan {
     int lu_maxk = 0;
     GemmBatch sg;             // s = C^{-1} t
     GemmBatch upd;            // X_anc -= Zhat s
+    GemmBatch gm;             // G = [Zhat_a C^{-1}[0:k, :]; Zhat_b C^{-1}[k:2k, :]] for the apply
   };
   std::vector<Height> heights;
   GemmBatch schurT, schurP, schurF;
@@ -315,8 +317,7 @@ struct LevelSolvePlan {
   GemmBatch down_gemm;         // HODLR leaves: y = K^{-1} b
   struct Height {
     GemmBatch t;               // t = [U^T y_a; V^T y_b]
-    GemmBatch s;               // s = C^{-1} t
-    GemmBatch upd;             // y -= Zhat s
+    GemmBatch upd;             // y -= G t  (G = Zhat C^{-1}, formed by the factorization)
   };
   std::vector<Height> heights;
   GemmBatch down1, down2;      // tf = W^T (-x_f) ; y += Vtilde tf
@@ -354,7 +355,7 @@ struct Plan {
   std::vector<HFront> hf;
   std::vector<std::vector<int>> level_fronts;   // fronts per depth
   int nlevels = 0;
-  int64_t front_total = 0, bo_total = 0, w_total = 0, t_total = 0, p_total = 0;
+  int64_t front_total = 0, bo_total = 0, w_total = 0, t_total = 0, p_total = 0, g_total = 0;
   int64_t core_total = 0, piv_total = 0, comp_total = 0, tb_total = 0;
   int64_t qr_scratch = 0;  // elements of the TSQR scratch arena (reused by every QR launch)
   int nrank = 0;
@@ -447,6 +448,7 @@ struct hm_sys_s {
   void* d_front = nullptr;   // T arena
   void* d_bo = nullptr;      // T
   void* d_x = nullptr;       // T
+  void* d_g = nullptr;       // T, the apply's G = Zhat C^{-1} per HODLR level
   void* d_w = nullptr;       // T
   void* d_tm = nullptr;      // T
   void* d_pm = nullptr;      // T

@@ -175,7 +175,7 @@ int build_plan(hm_sys_s* sys) {
 
   // ---------------------------------------------------------------- HODLR fronts
   P.hf.clear();
-  P.bo_total = P.w_total = P.t_total = P.p_total = 0;
+  P.bo_total = P.w_total = P.t_total = P.p_total = P.g_total = 0;
   P.core_total = P.piv_total = P.comp_total = P.tb_total = 0;
   P.qr_scratch = 0;
   P.nrank = 0;
@@ -219,6 +219,8 @@ int build_plan(hm_sys_s* sys) {
       h.xc = h.col[h.L];
       h.bo_off = P.bo_total;
       P.bo_total += (int64_t)h.np * h.xc;
+      h.g_off = P.g_total;
+      P.g_total += (int64_t)h.np * 2 * (h.xc - h.kf);
       h.w_off = P.w_total;
       P.w_total += (int64_t)h.nu * h.kf;
       h.t_off = P.t_total;
@@ -270,6 +272,7 @@ int build_plan(hm_sys_s* sys) {
   HM_TRY(A(&sys->d_front, P.front_total, es));
   HM_TRY(A(&sys->d_bo, P.bo_total, es));
   HM_TRY(A(&sys->d_x, P.bo_total, es));
+  HM_TRY(A(&sys->d_g, P.g_total, es));
   HM_TRY(A(&sys->d_w, P.w_total, es));
   HM_TRY(A(&sys->d_tm, P.t_total, es));
   HM_TRY(A(&sys->d_pm, P.p_total, es));
@@ -308,6 +311,7 @@ int build_plan(hm_sys_s* sys) {
   void* W = sys->d_w;
   void* Tm = sys->d_tm;
   void* Pm = sys->d_pm;
+  void* Gm = sys->d_g;
   void* Cm = sys->d_core;
   void* Cp = sys->d_comp;
   void* Tb = sys->d_tb;
@@ -417,7 +421,7 @@ int build_plan(hm_sys_s* sys) {
                           at(Bo, h.bo_off + colo + nd.lo, es), np, na, kb, kb, 1.0, 0.0));
         gv.push_back(gemm(at(Cp, nd.z_off, es), nb, 0, at(Cp, nd.vh_off, es), kb, 0,
                           at(Bo, h.bo_off + colo + nd.mid, es), np, nb, kb, kb, 1.0, 0.0));
-        fbytes += es * (2.0 * (na + nb) * k * 2 + 4.0 * k * k);
+        fbytes += es * (3.0 * (na + nb) * k);  // the apply reads U / V (k) and G (2k) rows
       }
       if (nu > 0 && h.kf > 0) {
         const int kf = h.kf;
@@ -472,7 +476,7 @@ int build_plan(hm_sys_s* sys) {
     lp.leaf_inv = tb.add(linv);
     // Woodbury levels, bottom-up (height 1 = parents of the leaves)
     for (int ht = 1; ht <= maxL; ++ht) {
-      std::vector<GemmTask> pre, sg, upd;
+      std::vector<GemmTask> pre, sg, upd, gmv;
       std::vector<CoreLuTask> lu;
       for (int q : fr) {
         const FrontGeom& g = P.fg[q];
@@ -495,6 +499,12 @@ int build_plan(hm_sys_s* sys) {
           pre.push_back(gemm(Vb, np, 1, Vh, np, 0, at(Cm, nd.core_off + (int64_t)k * 2 * k + k, es),
                              2 * k, k, k, nb, 1.0, 0.0));
           lu.push_back(CoreLuTask{core, cinv, piv + nd.piv_off, k, q});
+          {  // G for the apply: Zhat_a C^{-1}[0:k, :] and Zhat_b C^{-1}[k:2k, :]
+            void* Gl = at(Gm, h.g_off + (int64_t)2 * (h.col[lv] - h.kf) * np, es);
+            gmv.push_back(gemm(Uh, np, 0, cinv, 2 * k, 0, at(Gl, nd.lo, es), np, na, 2 * k, k, 1.0, 0.0));
+            gmv.push_back(gemm(Vh, np, 0, at(cinv, k, es), 2 * k, 0, at(Gl, nd.mid, es), np, nb, 2 * k, k, 1.0,
+                               0.0));
+          }
           if (A_ > 0) {
             void* tbuf = at(Tb, nd.tb_off, es);
             void* sbuf = at(Tb, nd.tb_off + (int64_t)2 * k * A_, es);
@@ -516,6 +526,7 @@ int build_plan(hm_sys_s* sys) {
       for (const auto& c : lu) H.lu_maxk = std::max(H.lu_maxk, c.k);
       H.sg = tb.add_gemm(sg);
       H.upd = tb.add_gemm(upd);
+      H.gm = tb.add_gemm(gmv);
       lp.heights.push_back(H);
     }
     lp.schurT = tb.add_gemm(sT);
@@ -605,6 +616,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   void* Bo = sys->d_bo;
   void* X = sys->d_x;
   void* W = sys->d_w;
+  void* Gm = sys->d_g;
   void* Cm = sys->d_core;
   void* FV = sp->d_fv;
   void* SB = sp->d_sb;
@@ -681,7 +693,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     lp.up2 = tb.add_gemm(u2);
     lp.down_gemm = tb.add_gemm(dg);
     for (int ht = 1; ht <= maxL; ++ht) {
-      std::vector<GemmTask> tt, ss, upd;
+      std::vector<GemmTask> tt, upd;
       for (int q : fr) {
         const FrontGeom& g = P.fg[q];
         if (g.hodlr < 0) continue;
@@ -694,23 +706,20 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
           if (nd.level != lv) continue;
           const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid;
           void* tn = at(SB, node_sb[g.hodlr][ni], es);
-          void* sn = at(SB, node_sb[g.hodlr][ni] + (int64_t)2 * k * nrhs, es);
-          void* cinv = at(Cm, nd.core_off + (int64_t)4 * k * k, es);
+          void* Gl = at(Gm, h.g_off + (int64_t)2 * (h.col[lv] - h.kf) * np, es);
           tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.lo, es), np, 1, at(SB, yq + nd.lo, es), np, 0,
                             tn, 2 * k, k, nrhs, na, 1.0, 0.0));
           tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.mid, es), np, 1, at(SB, yq + nd.mid, es), np, 0,
                             at(SB, node_sb[g.hodlr][ni] + k, es), 2 * k, k, nrhs, nb, 1.0, 0.0));
-          ss.push_back(gemm(cinv, 2 * k, 0, tn, 2 * k, 0, sn, 2 * k, 2 * k, nrhs, 2 * k, 1.0, 0.0));
-          upd.push_back(gemm(at(X, h.bo_off + colo + nd.lo, es), np, 0, sn, 2 * k, 0,
-                             at(SB, yq + nd.lo, es), np, na, nrhs, k, -1.0, 1.0));
-          upd.push_back(gemm(at(X, h.bo_off + colo + nd.mid, es), np, 0,
-                             at(SB, node_sb[g.hodlr][ni] + (int64_t)2 * k * nrhs + k, es), 2 * k, 0,
-                             at(SB, yq + nd.mid, es), np, nb, nrhs, k, -1.0, 1.0));
+          // y_a -= Zhat_a s_a = (Zhat_a C^{-1}[0:k, :]) t, likewise y_b
+          upd.push_back(gemm(at(Gl, nd.lo, es), np, 0, tn, 2 * k, 0, at(SB, yq + nd.lo, es), np, na, nrhs,
+                             2 * k, -1.0, 1.0));
+          upd.push_back(gemm(at(Gl, nd.mid, es), np, 0, tn, 2 * k, 0, at(SB, yq + nd.mid, es), np, nb, nrhs,
+                             2 * k, -1.0, 1.0));
         }
       }
       LevelSolvePlan::Height H;
       H.t = tb.add_gemm(tt);
-      H.s = tb.add_gemm(ss);
       H.upd = tb.add_gemm(upd);
       lp.heights.push_back(H);
     }

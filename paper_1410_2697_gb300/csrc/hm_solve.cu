@@ -420,7 +420,6 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
       gemm_b<T>(ctx, sp, lp.down_gemm);  // y = K_leaf^{-1} b on the HODLR leaves
       for (const auto& H : lp.heights) {
         gemm_b<T>(ctx, sp, H.t);
-        gemm_b<T>(ctx, sp, H.s);
         gemm_b<T>(ctx, sp, H.upd);
       }
       gemm_b<T>(ctx, sp, lp.down1);
