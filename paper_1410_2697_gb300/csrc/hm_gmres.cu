@@ -295,20 +295,33 @@ __global__ void k_backsolve(const double* __restrict__ H, const double* __restri
 
 // x[r] += sum_{j < len[inst]} Z_j[r] y[inst][j]   (Z_j row-major: element (k, r) at k nrhs + r)
 template <typename ZT>
-__global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z, const double* __restrict__ y,
-                           const int* __restrict__ len, int n, int nrhs, int m, const int* __restrict__ crow,
-                           const int* __restrict__ cseg, int nseg) {
-  __shared__ double ys[256];
-  const int r = blockIdx.y, c = blockIdx.x;
-  const int inst = r * nseg + cseg[c];
-  const int L = len[inst];
-  for (int j = threadIdx.x; j < L; j += blockDim.x) ys[j] = y[(int64_t)inst * m + j];
-  __syncthreads();
-  double* xr = x + (int64_t)r * n;
-  for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) {
-    double s = xr[k];
-    for (int j = 0; j < L; ++j) s = fma((double)Z[((int64_t)j * n + k) * nrhs + r], ys[j], s);
-    xr[k] = s;
+__global__ void __launch_bounds__(256) k_update_x(double* __restrict__ x, const ZT* __restrict__ Z,
+                                                  const double* __restrict__ y, const int* __restrict__ len, int n,
+                                                  int nrhs, int m, const int* __restrict__ crow,
+                                                  const int* __restrict__ cseg, int nseg) {
+  // x_r += sum_j y_{r,j} Z_j[:, r] on rows [crow[c], crow[c+1]) of one block; Z_j is
+  // row-major (element (i, r) at i nrhs + r): a tile of 64 rows x every right-hand side
+  // is read along rows (coalesced), then written to the column-major x through shared
+  // memory
+  __shared__ double tile[64][65];
+  const int c = blockIdx.x, seg = cseg[c];
+  for (int k0 = crow[c]; k0 < crow[c + 1]; k0 += 64) {
+    const int rows = min(64, crow[c + 1] - k0), cnt = rows * nrhs;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int kk = e / nrhs, r = e - kk * nrhs;
+      const int inst = r * nseg + seg, L = len[inst];
+      const ZT* zp = Z + (int64_t)(k0 + kk) * nrhs + r;
+      const double* yp = y + (int64_t)inst * m;
+      double s = 0.0;
+      for (int j = 0; j < L; ++j) s = fma((double)zp[(int64_t)j * n * nrhs], yp[j], s);
+      tile[kk][r] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e / rows, kk = e - r * rows;
+      x[(int64_t)r * n + k0 + kk] += tile[kk][r];
+    }
+    __syncthreads();
   }
 }
 
@@ -525,7 +538,7 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
     }
     {
       ProfScope ps(sys->ctx, PC_VECTOR, Work{2.0 * jend * nn, (16.0 + sizeof(T) * jend) * nn});
-      k_update_x<T><<<vgrid, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m, G.crow, G.cseg, nseg);
+      k_update_x<T><<<G.nchunks, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m, G.crow, G.cseg, nseg);
     }
     {
       ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});

@@ -438,19 +438,22 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
 // replayed: its ~10^2 dependent launches then cost one graph launch.  The first apply
 // with a new input runs eagerly; with the launch profiler on, applies always run eagerly.
 // dst (row-major n x nrhs: element (i, r) at i nrhs + r) = src (column-major, ld n),
-// through 32 x 32 shared-memory tiles so both sides are coalesced.
+// 64 rows and every right-hand side (<= 64) per tile through shared memory, so both
+// sides are coalesced.
+constexpr int kRmRows = 64;
 template <typename T>
-__global__ void k_to_rowmajor(const T* __restrict__ src, T* __restrict__ dst, int n, int nrhs) {
-  __shared__ T tile[32][33];
-  const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
-    const int i = i0 + threadIdx.x, r = r0 + rr;
-    if (i < n && r < nrhs) tile[rr][threadIdx.x] = src[i + (int64_t)r * n];
+__global__ void __launch_bounds__(256) k_to_rowmajor(const T* __restrict__ src, T* __restrict__ dst, int n,
+                                                     int nrhs) {
+  __shared__ T tile[kRmRows][65];
+  const int i0 = blockIdx.x * kRmRows, rows = min(kRmRows, n - i0), cnt = rows * nrhs;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int r = e / rows, ii = e - r * rows;
+    tile[ii][r] = src[i0 + ii + (int64_t)r * n];
   }
   __syncthreads();
-  for (int ii = threadIdx.y; ii < 32; ii += blockDim.y) {
-    const int i = i0 + ii, r = r0 + threadIdx.x;
-    if (i < n && r < nrhs) dst[(int64_t)i * nrhs + r] = tile[threadIdx.x][ii];
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int ii = e / nrhs, r = e - ii * nrhs;
+    dst[(int64_t)(i0 + ii) * nrhs + r] = tile[ii][r];
   }
 }
 
@@ -489,7 +492,7 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout, bool rowmajor
   T* xfix = (T*)sp->d_xfix;
   if (rowmajor_out) {
     ProfScope ps(ctx, PC_VECTOR, Work{0.0, 2.0 * sizeof(T) * (double)sys->n * nrhs});
-    k_to_rowmajor<T><<<dim3((sys->n + 31) / 32, (nrhs + 31) / 32), dim3(32, 8), 0, s>>>(xfix, xout, sys->n, nrhs);
+    k_to_rowmajor<T><<<(sys->n + kRmRows - 1) / kRmRows, 256, 0, s>>>(xfix, xout, sys->n, nrhs);
   } else if (xout != xfix) {
     HM_CUDA(cudaMemcpyAsync(xout, xfix, sizeof(T) * (size_t)sys->n * nrhs, cudaMemcpyDeviceToDevice, s));
   }
