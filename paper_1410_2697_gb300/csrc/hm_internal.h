@@ -309,8 +309,6 @@ struct LevelSolvePlan {
   Span<int> hfronts;           // HODLR fronts of the level
   int n_hodlr = 0;
   int hodlr_max_nhat = 0, hodlr_max_nu = 0;
-  std::vector<Span<int>> slots;  // slot j: HODLR fronts of the level with more than j children
-  std::vector<int> slot_max_nu;  // per slot, the largest update size of those children
   Work hup_work, hdown_work;   // HODLR vector kernels (init + extend-add; gather)
   GemmBatch up_gemm;           // HODLR: tf = Vtilde^T b_p
   GemmBatch up2;               // HODLR: f -= W tf

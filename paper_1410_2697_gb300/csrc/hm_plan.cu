@@ -627,7 +627,6 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     LevelSolvePlan& lp = sp->levels[l];
     const auto& fr = P.level_fronts[l];
     std::vector<int> dense, hod;
-    std::vector<std::vector<int>> slot_fronts;  // slot j: HODLR fronts with more than j children
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
       const auto ch = sys->children(q);
@@ -647,14 +646,6 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
         hod.push_back(q);
         lp.hodlr_max_nhat = std::max(lp.hodlr_max_nhat, g.nhat);
         lp.hodlr_max_nu = std::max(lp.hodlr_max_nu, g.nu);
-        if ((int)slot_fronts.size() < ch.size()) {
-          slot_fronts.resize(ch.size());
-          lp.slot_max_nu.resize(ch.size(), 0);
-        }
-        for (int j = 0; j < ch.size(); ++j) {
-          slot_fronts[j].push_back(q);
-          lp.slot_max_nu[j] = std::max(lp.slot_max_nu[j], P.fg[ch[j]].nu);
-        }
         lp.hup_work.bytes += vec;
         lp.hdown_work.bytes += es * R * 2.0 * nu + 4.0 * nu;
       }
@@ -662,7 +653,6 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     lp.dense = tb.add(dense);
     lp.hfronts = tb.add(hod);
     lp.n_hodlr = (int)hod.size();
-    for (const auto& sf : slot_fronts) lp.slots.push_back(tb.add(sf));
     std::vector<GemmTask> ug, dg;
     std::vector<GemmTask> u2, d1, d2;
     int maxL = 0;

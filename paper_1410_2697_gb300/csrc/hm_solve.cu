@@ -25,43 +25,31 @@ namespace hm {
 // rows); grid = (ceil(fronts / 8), nrhs, chunks), 8 warps per block.
 constexpr int kVecChunk = 256;
 
-// fv_q = [r(I_q); 0] for every front q of the level.
+// Upward assembly of HODLR fronts in one launch: one block per (front, right-hand side)
+// forms fv_q = [r(I_q); 0] and adds the children's update parts through the relative
+// maps, one child after another (a fixed order of the sums).
 template <typename T>
-__global__ void __launch_bounds__(256) k_vinit(const int* __restrict__ fronts, int nfronts, int n,
-                                               const T* __restrict__ win, const int32_t* __restrict__ first,
-                                               const int* __restrict__ npiv, const int* __restrict__ nhat,
-                                               const int64_t* __restrict__ fvoff, T* __restrict__ FV) {
-  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (fi >= nfronts) return;
-  const int q = fronts[fi], r = blockIdx.y;
-  const int np = npiv[q], nh = nhat[q], b0 = first[q];
+__global__ void __launch_bounds__(256) k_vassemble(const int* __restrict__ fronts, int n,
+                                                   const T* __restrict__ win, const int32_t* __restrict__ first,
+                                                   const int* __restrict__ npiv, const int* __restrict__ nhat,
+                                                   const int64_t* __restrict__ fvoff,
+                                                   const int32_t* __restrict__ child_ptr,
+                                                   const int32_t* __restrict__ child_list,
+                                                   const int64_t* __restrict__ ifoff,
+                                                   const int32_t* __restrict__ relmap, T* __restrict__ FV) {
+  const int q = fronts[blockIdx.x], r = blockIdx.y;
+  const int np = npiv[q], nh = nhat[q];
   T* fv = FV + fvoff[q] + (int64_t)r * nh;
-  const T* w = win + b0 + (int64_t)r * n;
-  const int e0 = blockIdx.z * kVecChunk, e1 = min(nh, e0 + kVecChunk);
-  for (int e = e0 + lane; e < e1; e += 32) fv[e] = e < np ? w[e] : T(0);
-}
-
-// Extend-add of vectors for child slot `slot`: fv_parent[relmap] += update part of the
-// child (slots run one after another, so sums are formed in a fixed order).
-template <typename T>
-__global__ void __launch_bounds__(256) k_vadd(const int* __restrict__ parents, int nparents, int slot,
-                                              const int32_t* __restrict__ child_ptr,
-                                              const int32_t* __restrict__ child_list,
-                                              const int* __restrict__ npiv, const int* __restrict__ nhat,
-                                              const int64_t* __restrict__ fvoff,
-                                              const int64_t* __restrict__ ifoff,
-                                              const int32_t* __restrict__ relmap, T* __restrict__ FV) {
-  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (fi >= nparents) return;
-  const int q = parents[fi], r = blockIdx.y;
-  const int c = child_list[child_ptr[q] + slot];
-  const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
-  const int e0 = blockIdx.z * kVecChunk, e1 = min(nuc, e0 + kVecChunk);
-  if (e0 >= e1) return;
-  T* fv = FV + fvoff[q] + (int64_t)r * nhat[q];
-  const T* fc = FV + fvoff[c] + npc + (int64_t)r * nhc;
-  const int32_t* rm = relmap + ifoff[c];
-  for (int t = e0 + lane; t < e1; t += 32) fv[rm[t]] += fc[t];
+  const T* w = win + first[q] + (int64_t)r * n;
+  for (int e = threadIdx.x; e < nh; e += blockDim.x) fv[e] = e < np ? w[e] : T(0);
+  for (int ci = child_ptr[q]; ci < child_ptr[q + 1]; ++ci) {
+    __syncthreads();
+    const int c = child_list[ci];
+    const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
+    const T* fc = FV + fvoff[c] + npc + (int64_t)r * nhc;
+    const int32_t* rm = relmap + ifoff[c];
+    for (int t = threadIdx.x; t < nuc; t += blockDim.x) fv[rm[t]] += fc[t];
+  }
 }
 
 // Downward gather: fv_q[np + t] = -x(I_q^f[t]) (negated, so that a dense front's solve
@@ -99,12 +87,25 @@ constexpr int kDenseKC = 256;  // rows of the staged block per chunk in the down
 
 __device__ __forceinline__ int pow2_floor8(int v) { return v >= 8 ? 8 : v >= 4 ? 4 : v >= 2 ? 2 : 1; }
 
-// acc[r] += sum_{k in [k0, k1)} M[row + k ld] X[(k - kx) RB + r]
+// acc[r] += sum_{k in [k0, k1)} M[row + k ld] X[(k - kx) RB + r]; eight loads of M are
+// issued before their products, so each thread keeps several HBM requests in flight.
 template <typename T, int RB>
 __device__ __forceinline__ void rowblock_acc(const T* __restrict__ M, int64_t ld, int row, int k0, int k1,
                                              const T* __restrict__ X, int kx, T (&acc)[RB]) {
-#pragma unroll 4
-  for (int k = k0; k < k1; ++k) {
+  constexpr int U = 8;
+  int k = k0;
+  for (; k + U <= k1; k += U) {
+    T m[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) m[u] = M[row + (int64_t)(k + u) * ld];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const T* x = X + (k + u - kx) * RB;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) acc[r] = fma(m[u], x[r], acc[r]);
+    }
+  }
+  for (; k < k1; ++k) {
     const T m = M[row + (int64_t)k * ld];
     const T* x = X + (k - kx) * RB;
 #pragma unroll
@@ -388,16 +389,10 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
     }
     if (lp.n_hodlr) {
       {
-        ProfScope ps(ctx, PC_VECTOR, lp.hup_work, 1 + (int)lp.slots.size());
-        k_vinit<T><<<vgrid(lp.n_hodlr, nrhs, lp.hodlr_max_nhat), 256, 0, s>>>(
-            lp.hfronts.dev(base), lp.n_hodlr, n, win, sys->d_first, P.d_np, P.d_nhat, sp->d_fvoff, FV);
-        for (size_t sl = 0; sl < lp.slots.size(); ++sl) {
-          const Span<int>& par = lp.slots[sl];
-          if (par.count == 0) continue;
-          k_vadd<T><<<vgrid(par.count, nrhs, lp.slot_max_nu[sl]), 256, 0, s>>>(
-              par.dev(base), par.count, (int)sl, sys->d_child_ptr, sys->d_child_list, P.d_np, P.d_nhat,
-              sp->d_fvoff, sys->d_ifoff, sys->d_relmap, FV);
-        }
+        ProfScope ps(ctx, PC_VECTOR, lp.hup_work);
+        k_vassemble<T><<<dim3((unsigned)lp.n_hodlr, (unsigned)nrhs), 256, 0, s>>>(
+            lp.hfronts.dev(base), n, win, sys->d_first, P.d_np, P.d_nhat, sp->d_fvoff, sys->d_child_ptr,
+            sys->d_child_list, sys->d_ifoff, sys->d_relmap, FV);
       }
       gemm_b<T>(ctx, sp, lp.up_gemm);  // tf = Vtilde^T b_p
       gemm_b<T>(ctx, sp, lp.up2);      // f -= W tf
