@@ -204,6 +204,15 @@ int hm_direct_solve(hm_sys_t sys, int32_t nrhs, const double* b, int32_t refine,
 int hm_autotune(hm_sys_t sys, const double* values, double tol, int32_t nrhs, int32_t reps,
                 int32_t* nsites);
 
+/* Fix every tunable launch site of the context to one variant (0 = the built-in
+   default; GEMM sites: 1 deeper k-slices, 2 cp.async staging, 3 FP32 128 x 128 tiles
+   where the batch has such products; QR sites: 1 global memory; dense apply levels:
+   1 the other thread count; a variant a site lacks acts as 0), or -1 to return to the
+   autotuner's choices.  For reproducing a configuration and for tests; hm_autotune
+   clears it.  Applies to launches issued afterwards (apply graphs captured earlier
+   keep their variants until the solve plan is rebuilt).                              */
+int hm_tune_force(hm_ctx_t ctx, int32_t variant);
+
 /*
  * Solve A X = B by GMRES(restart) preconditioned with the factorization (Section 3):
  * right preconditioning, flexible form (the preconditioned vectors are stored), FP64

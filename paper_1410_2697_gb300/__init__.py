@@ -19,7 +19,7 @@ from ._binding import (HM_PREC_FP64, HM_PREC_MIXED, HM_PREC_MIXED_BF16, HmError,
                        hm_get_ordering, hm_get_sizes, hm_get_symbolic, hm_get_update,
                        hm_last_error, hm_precond_apply, hm_precond_apply_noalloc, hm_server_add_matrix,
                        hm_server_create, hm_server_destroy, hm_server_get_stats, hm_server_submit,
-                       hm_server_wait, hm_solve, hm_status_str)
+                       hm_server_wait, hm_solve, hm_status_str, hm_tune_force)
 
 
 class Solver:

@@ -30,7 +30,7 @@ HM_PREC_MIXED = 1
 HM_PREC_MIXED_BF16 = 2
 
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_analyze_batch", "hm_get_sizes",
-            "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_autotune", "hm_solve", "hm_direct_solve",
+            "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_autotune", "hm_tune_force", "hm_solve", "hm_direct_solve",
             "hm_precond_apply",
             "hm_precond_apply_noalloc",
             "hm_get_update", "hm_get_front_ranks", "hm_get_hodlr_block", "hm_profile_enable", "hm_profile_read", "hm_destroy", "hm_status_str", "hm_last_error",
@@ -91,6 +91,7 @@ def _load():
     lib.hm_get_symbolic.argtypes = [vp, vp, vp, vp, vp]
     lib.hm_factor.argtypes = [vp, vp, dbl, C.POINTER(HmFactorInfo)]
     lib.hm_autotune.argtypes = [vp, vp, dbl, i32, i32, C.POINTER(i32)]
+    lib.hm_tune_force.argtypes = [vp, i32]
     lib.hm_solve.argtypes = [vp, i32, vp, dbl, i32, vp, C.POINTER(HmSolveInfo)]
     lib.hm_direct_solve.argtypes = [vp, i32, vp, i32, vp, C.POINTER(HmSolveInfo)]
     lib.hm_precond_apply.argtypes = [vp, i32, vp, vp]
@@ -236,6 +237,11 @@ def hm_autotune(sys_, values, tol: float, nrhs: int, reps: int = 2) -> int:
     _check(_lib.hm_autotune(sys_, _ptr(values, np.float64, "values"), float(tol), int(nrhs), int(reps),
                             C.byref(n)), "hm_autotune")
     return n.value
+
+
+def hm_tune_force(ctx, variant: int) -> None:
+    """Fix every tunable launch site to `variant` (-1: back to the autotuner's choices)."""
+    _check(_lib.hm_tune_force(ctx, int(variant)), "hm_tune_force")
 
 
 def hm_solve(sys_, nrhs: int, b, rtol: float, max_iters: int, x, raise_on_no_convergence=True) -> dict:

@@ -480,7 +480,7 @@ int hm_autotune(hm_sys_t sys, const double* values, double tol, int32_t nrhs, in
   k_tune_rhs<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>((double*)pb, nn);
   // every pass: the factorization and two GMRES iterations with all sites forced to one
   // variant; per site the mean time of one launch, the best over the repetitions
-  constexpr int kVariants = 3;  // the GEMM sites have three, the others two (2 acts as 0)
+  constexpr int kVariants = 4;  // GEMM sites: four (3 = large tiles, where built); others two
   std::unordered_map<uint64_t, std::array<double, kVariants>> best;
   for (int rep = 0; rep < reps && st == HM_OK; ++rep)
     for (int v = 0; v < kVariants && st == HM_OK; ++v) {
@@ -506,7 +506,7 @@ int hm_autotune(hm_sys_t sys, const double* values, double tol, int32_t nrhs, in
       }
       for (const auto& kv : sum) {
         auto it = best.find(kv.first);
-        if (it == best.end()) it = best.emplace(kv.first, std::array<double, kVariants>{1e30, 1e30, 1e30}).first;
+        if (it == best.end()) it = best.emplace(kv.first, std::array<double, kVariants>{1e30, 1e30, 1e30, 1e30}).first;
         it->second[v] = std::min(it->second[v], kv.second.first / kv.second.second);
       }
     }
@@ -539,6 +539,12 @@ int hm_autotune(hm_sys_t sys, const double* values, double tol, int32_t nrhs, in
   if (st == HM_OK) sys->tol = tol;
   if (nsites) *nsites = tuned;
   return st;
+}
+
+int hm_tune_force(hm_ctx_t ctx, int32_t variant) {
+  if (!ctx || variant < -1 || variant > 3) return HM_ERR_INVALID_ARG;
+  ctx->tune.force = variant;
+  return HM_OK;
 }
 
 int hm_solve(hm_sys_t sys, int32_t nrhs, const double* b, double rtol, int32_t max_iters, double* x,

@@ -300,6 +300,146 @@ int gemm_async_setup(int max_smem) {
   return HM_OK;
 }
 
+// =====================================================================================
+// Large-tile variant (FP32): 128 x 128 output tiles, 256 threads, each thread an 8 x 8
+// register block (rows ty*4 + {0..3, 64..67}, columns tx*4 + {0..3, 64..67}), so one
+// k step reads 2 + 2 float4 from shared memory for 64 FMAs.  k-slices of 8, staged
+// k-major in double-buffered shared memory with the next slice prefetched into
+// registers.  Same tile/split contract as k_gemm with 128 x 128 tiles; each output adds
+// its products in increasing k, as the other variants do.
+// =====================================================================================
+constexpr int kBigBM = 128, kBigBK = 8;
+
+__global__ void __launch_bounds__(256, 2) k_gemm_big(const GemmTask* __restrict__ tasks,
+                                                     const GemmTile* __restrict__ tiles,
+                                                     float* __restrict__ split_ws, unsigned* __restrict__ split_cnt) {
+  constexpr int BM = kBigBM, BN = kBigBM, BK = kBigBK;
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask t = tasks[tl.task];
+  const int m0 = (tl.mn >> 16) * BM, n0 = (tl.mn & 0xffff) * BN;
+  const float* __restrict__ A = (const float*)t.A;
+  const float* __restrict__ B = (const float*)t.B;
+  float* __restrict__ C = (float*)t.C;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int kend = tl.k1;
+  float ra[4], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int r, p;
+      if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
+      const int gr = m0 + r, gk = k0 + p;
+      ra[q] = (gr < t.m && gk < kend) ? (t.opA == 0 ? A[(size_t)gr + (size_t)gk * t.lda]
+                                                     : A[(size_t)gk + (size_t)gr * t.lda]) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int c, p;
+      if (t.opB == 0) { p = e % BK; c = e / BK; } else { c = e % BN; p = e / BN; }
+      const int gc = n0 + c, gk = k0 + p;
+      rb[q] = (gc < t.n && gk < kend) ? (t.opB == 0 ? B[(size_t)gk + (size_t)gc * t.ldb]
+                                                     : B[(size_t)gc + (size_t)gk * t.ldb]) : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int r, p;
+      if (t.opA == 0) { r = e % BM; p = e / BM; } else { p = e % BK; r = e / BK; }
+      As[buf][p][r] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int c, p;
+      if (t.opB == 0) { p = e % BK; c = e / BK; } else { c = e % BN; p = e / BN; }
+      Bs[buf][p][c] = rb[q];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  int buf = 0;
+  if (tl.k0 < kend) {
+    fetch(tl.k0);
+    stash(0);
+  }
+  __syncthreads();
+  for (int k0 = tl.k0; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) fetch(k0 + BK);
+#pragma unroll
+    for (int p = 0; p < BK; ++p) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][p][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][p][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][p][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][p][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  auto row_of = [&](int i) { return (i < 4 ? 0 : 64) + ty * 4 + (i & 3); };
+  auto col_of = [&](int j) { return (j < 4 ? 0 : 64) + tx * 4 + (j & 3); };
+  if (tl.slot >= 0) {
+    __shared__ int last;
+    float* ws = split_ws + tl.woff;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ws[(size_t)tl.part * BM * BN + row_of(i) + col_of(j) * BM] = acc[i][j];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(split_cnt + tl.slot, 1u) == (unsigned)(tl.nsplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float v = 0.f;
+        for (int q = 0; q < tl.nsplit; ++q) v += __ldcg(ws + (size_t)q * BM * BN + row_of(i) + col_of(j) * BM);
+        acc[i][j] = v;
+      }
+    if (tid == 0) split_cnt[tl.slot] = 0u;
+  }
+  const float alpha = (float)t.alpha, beta = (float)t.beta;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = n0 + col_of(j);
+    if (c >= t.n) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = m0 + row_of(i);
+      if (r >= t.m) continue;
+      if (t.lower && r < c) continue;
+      float* dst = C + (size_t)r + (size_t)c * t.ldc;
+      const float v = alpha * acc[i][j];
+      *dst = (beta == 0.f) ? v : fmaf(beta, *dst, v);
+    }
+  }
+}
+
+void launch_gemm_big(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
+                     unsigned* split_cnt, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_gemm_big<<<ntiles, 256, 0, s>>>(tasks, tiles, split_ws, split_cnt);
+}
+
 int gemm_bn_for(const std::vector<GemmTask>& t) {
   int nmax = 0;
   for (const auto& x : t) nmax = std::max(nmax, x.n);

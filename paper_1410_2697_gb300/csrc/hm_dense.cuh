@@ -174,5 +174,9 @@ int dense_tc_setup(int max_smem);
 int dense_fact_setup(int max_dyn_smem);
 int dense_comp_setup(int max_dyn_smem);
 int gemm_async_setup(int max_dyn_smem);
+// FP32 128 x 128-tile variant (tiles built with kBigTile x kBigTile).
+constexpr int kBigTile = 128;
+void launch_gemm_big(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
+                     unsigned* split_cnt, cudaStream_t s);
 
 }  // namespace hm

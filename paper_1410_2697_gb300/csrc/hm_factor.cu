@@ -120,7 +120,13 @@ static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* bas
     return;
   }
   TuneScope ts(sys->ctx, TS_GEMM, b.sig);
-  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, sys->ctx->tune.variant(TS_GEMM, b.sig),
+  const int v = sys->ctx->tune.variant(TS_GEMM, b.sig);
+  if (v == 3 && b.tiles_big.count > 0 && sizeof(T) == 4) {  // FP32 large-tile kernel
+    launch_gemm_big(b.tasks.dev(base), b.tiles_big.dev(base), b.tiles_big.count, (float*)sys->plan.d_split_ws,
+                    sys->plan.d_split_cnt, sys->ctx->stream);
+    return;
+  }
+  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, v == 3 ? 0 : v,
                  (T*)sys->plan.d_split_ws, sys->plan.d_split_cnt, sys->ctx->stream);
 }
 

@@ -75,6 +75,7 @@ struct Span {
 struct GemmBatch {
   Span<GemmTask> tasks;
   Span<GemmTile> tiles;
+  Span<GemmTile> tiles_big;  // 128 x 128 tiles for the FP32 large-tile variant (if eligible)
   int bn = 64;       // tile width of the batch
   int tc = 0;        // 1: tensor-core BF16 kernel (128 x 64 tiles)
   uint64_t sig = 0;  // shape signature (autotuner key)
@@ -149,12 +150,33 @@ struct TaskBuf {
     }
     split_ws = std::max(split_ws, ws);
     split_slots = std::max(split_slots, slots);
+    // FP32 batches with a product of at least one 128 x 128 tile also get the tiles of
+    // the large-tile kernel (an autotuner variant)
+    std::vector<GemmTile> big;
+    bool eligible = !tc && es == 4 && b.bn == 64;
+    bool large = false;
+    for (const auto& x : t) large = large || (x.m >= kBigTile && x.n >= kBigTile && x.k >= 32);
+    if (eligible && large) {
+      int nbig = 0;
+      for (const auto& x : t) nbig += gemm_tile_count(x, kBigTile, kBigTile);
+      int bslots = 0;
+      int64_t bws = 0;
+      for (size_t i = 0; i < t.size(); ++i) {
+        int nsplit = 1;
+        if (nbig < kSplitTarget && t[i].k >= 2 * kSplitMinK)
+          nsplit = std::min(std::min(kSplitTarget / std::max(nbig, 1), t[i].k / kSplitMinK), kSplitMax);
+        gemm_tiles_for(t[i], (int)i, kBigTile, kBigTile, nsplit, &big, &bslots, &bws);
+      }
+      split_ws = std::max(split_ws, bws);
+      split_slots = std::max(split_slots, bslots);
+    }
     Sig sg;
     sg << b.bn << b.tc << (int64_t)t.size() << (int64_t)tiles.size();
     for (const auto& x : t) sg << x.m << x.n << x.k << (x.opA + 2 * x.opB + 4 * x.lower);
     b.sig = sg.h;
     b.tasks = add(t);
     b.tiles = add(tiles);
+    b.tiles_big = add(big);
     return b;
   }
 };

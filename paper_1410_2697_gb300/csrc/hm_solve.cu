@@ -360,8 +360,14 @@ static void gemm_b(hm_ctx_s* ctx, const SolvePlan* sp, const GemmBatch& b) {
   if (b.tiles.count == 0) return;
   ProfScope ps(ctx, PC_GEMM_APPLY, b.tasks.work);
   TuneScope ts(ctx, TS_GEMM, b.sig);
+  const int v = ctx->tune.variant(TS_GEMM, b.sig);
+  if (v == 3 && b.tiles_big.count > 0 && sizeof(T) == 4) {  // FP32 large-tile kernel
+    launch_gemm_big(b.tasks.dev(sp->d_tasks), b.tiles_big.dev(sp->d_tasks), b.tiles_big.count,
+                    (float*)sp->d_split_ws, sp->d_split_cnt, ctx->stream);
+    return;
+  }
   launch_gemm<T>(b.tasks.dev(sp->d_tasks), b.tiles.dev(sp->d_tasks), b.tiles.count, b.bn,
-                 ctx->tune.variant(TS_GEMM, b.sig), (T*)sp->d_split_ws,
+                 v == 3 ? 0 : v, (T*)sp->d_split_ws,
                  sp->d_split_cnt, ctx->stream);
 }
 

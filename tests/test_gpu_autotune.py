@@ -66,3 +66,35 @@ def test_autotune_refuses_while_profiling():
     hm.hm_profile_enable(ctx, False)
     hm.hm_destroy(s)
     hm.hm_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", ["HM_PREC_MIXED", "HM_PREC_FP64"])
+def test_every_forced_variant_solves(precision):
+    """Each launch variant, forced on every site, gives the same solution (the GEMM
+    variants add in the same order; QR and apply variants differ in rounding only)."""
+    m = 160
+    P = q1_square(m, lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=13))
+    o = hm.hm_default_opts()
+    o.precision = getattr(hm, precision)
+    o.n_c = 32
+    o.hodlr_leaf = 32
+    ctx = hm.hm_create(o)
+    b = rhs_uniform(P.n, 2, 14)
+    A = P.scipy()
+    xs = []
+    for v in (0, 1, 2, 3):
+        hm.hm_tune_force(ctx, v)
+        s = hm.hm_analyze(ctx, P.n, P.rowptr, P.colidx, 2, P.coords)
+        hm.hm_factor(s, P.values, 1e-4)
+        x = np.zeros_like(b)
+        info = hm.hm_solve(s, 2, b, 1e-10, 2000, x)
+        assert info["converged"] == 1, v
+        for c in range(2):
+            assert np.linalg.norm(b[:, c] - A @ x[:, c]) / np.linalg.norm(b[:, c]) <= 1e-10, v
+        xs.append(x)
+        hm.hm_destroy(s)
+    for v in (1, 2, 3):
+        assert np.linalg.norm(xs[v] - xs[0]) / np.linalg.norm(xs[0]) <= 1e-8, v
+    with pytest.raises(hm.HmError):
+        hm.hm_tune_force(ctx, 7)
+    hm.hm_ctx_destroy(ctx)
