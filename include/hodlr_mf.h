@@ -55,6 +55,16 @@ enum hm_precision {
                             rounding of the sampled blocks (about 2^-9 of their size)      */
 };
 
+/* Off-diagonal compressor of the HODLR fronts (Section 2.2). */
+enum hm_compressor {
+  HM_COMP_RRF = 0,       /* randomized range finder (Philox sketch of width `samples`, QR,
+                            small SVD; singular values <= tol sigma_1 dropped)            */
+  HM_COMP_BDLR = 1       /* boundary-distance low-rank approximation: rows and columns
+                            within graph distance bdlr_depth of the other index set (graph
+                            of A on the front's unknowns, at most `samples` of each),
+                            complete-pivoting LU, rank by |u_rr / u_11| >= tol           */
+};
+
 typedef struct hm_opts {
   int device;            /* CUDA device ordinal                                          */
   int precision;         /* enum hm_precision                                            */
@@ -71,6 +81,8 @@ typedef struct hm_opts {
                             3 for 3D elasticity): unknown b k + c is component c of node
                             k, all b share the node's grid_coords; separators then hold
                             whole nodes, and a node's unknowns stay consecutive          */
+  int compressor;        /* enum hm_compressor (HM_COMP_RRF)                              */
+  int bdlr_depth;        /* BDLR graph-distance depth d (1, the paper's usual setting)   */
 } hm_opts;
 
 typedef struct hm_solve_info {
@@ -91,8 +103,8 @@ typedef struct hm_factor_info {
 } hm_factor_info;
 
 /* Fill *opts with defaults (device 0, mixed precision, nd_leaf 64, hodlr_leaf 64,
-   n_c 64, samples 48, restart 30, dofs_per_node 1).  Never fails for a non-null
-   pointer.                                                                           */
+   n_c 64, samples 48, restart 30, dofs_per_node 1, compressor HM_COMP_RRF,
+   bdlr_depth 1).  Never fails for a non-null pointer.                                */
 int hm_default_opts(hm_opts* opts);
 
 /* Create a context on opts->device.  The context owns a CUDA stream (unless one is

@@ -87,12 +87,13 @@ class HNode:
 def build(K: np.ndarray, leaf: int, tol: float, compressor=None) -> HNode:
     """HODLR representation of the dense symmetric matrix ``K``.
 
-    ``compressor(B, level, index)`` returns ``(U, V)`` for the upper off-diagonal block
-    of the node at (level, index); the default is ``truncated_svd(B, tol)``."""
+    ``compressor(B, level, index, lo=, mid=, hi=)`` returns ``(U, V)`` for the upper
+    off-diagonal block ``K[lo:mid, mid:hi]`` of the node at (level, index); the default
+    is ``truncated_svd(B, tol)``."""
     n = K.shape[0]
     L = hodlr_depth(n, leaf)
     if compressor is None:
-        compressor = lambda B, level, index: truncated_svd(B, tol)  # noqa: E731
+        compressor = lambda B, level, index, **kw: truncated_svd(B, tol)  # noqa: E731
 
     def rec(lo, hi, level, index):
         node = HNode(lo, hi, level, index)
@@ -101,7 +102,7 @@ def build(K: np.ndarray, leaf: int, tol: float, compressor=None) -> HNode:
             return node
         mid = lo + (hi - lo) // 2
         node.children = [rec(lo, mid, level + 1, 2 * index), rec(mid, hi, level + 1, 2 * index + 1)]
-        node.U, node.V = compressor(K[lo:mid, mid:hi], level, index)
+        node.U, node.V = compressor(K[lo:mid, mid:hi], level, index, lo=lo, mid=mid, hi=hi)
         return node
 
     return rec(0, n, 0, 0)

@@ -32,8 +32,8 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-from . import hodlr
-from .dense_mf import assemble_fbar, extend_add
+from . import bdlr, hodlr
+from .dense_mf import assemble_fbar, extend_add, front_indices
 from .nd import ETree
 from .philox import block_id, sketch
 from .symbolic import Symbolic
@@ -44,7 +44,8 @@ class Params:
     tol: float = 1e-6
     n_c: int = 64
     leaf: int = 64
-    compressor: str = "svd"        # "svd" | "rrf"
+    compressor: str = "svd"        # "svd" | "rrf" | "bdlr"
+    bdlr_depth: int = 1            # BDLR graph-distance depth
     samples: int = 64              # RRF sketch width k (capped by the block's size)
     seed: int = 0x5EED             # RRF sketch seed
     compress_ff: bool = False
@@ -61,10 +62,19 @@ class Front:
     V: np.ndarray | None = None
 
 
-def _compressor(prm: Params, front: int, kind: int):
-    def comp(B, level, index):
+def _compressor(prm: Params, front: int, kind: int, graph=None, npv: int = 0):
+    def comp(B, level, index, lo=None, mid=None, hi=None):
         if prm.compressor == "svd":
             return hodlr.truncated_svd(B, prm.tol)
+        if prm.compressor == "bdlr":
+            # rows / columns of B as positions in the front: pivot-block nodes [lo, mid) x
+            # [mid, hi); the coupling block F_fp has the update rows and the pivot columns
+            off = npv if kind == 2 else 0  # F_ff nodes sit after the pivot positions
+            X = np.arange(off + lo, off + mid) if kind != 1 else np.arange(npv, npv + B.shape[0])
+            Y = np.arange(off + mid, off + hi) if kind != 1 else np.arange(0, npv)
+            cap = min(prm.samples, B.shape[0], B.shape[1])
+            I, J = bdlr.select(graph, X, Y, prm.bdlr_depth, cap)
+            return bdlr.compress(B, I, J, prm.tol)
         k = min(prm.samples, B.shape[0], B.shape[1])
         Om = sketch(B.shape[1], k, block_id(front, kind, level, index), prm.seed)
         return hodlr.randomized_range_finder(B, prm.tol, Om)
@@ -91,12 +101,13 @@ def factor(Ap: sp.csr_matrix, et: ETree, sym: Symbolic, prm: Params, keep: bool 
             updates[p] = Fff - Ffp @ sla.cho_solve(cho, Ffp.T)
             fronts[p] = Front(npv, "dense", cho=cho, Ffp=Ffp.copy())
         else:
-            H = hodlr.build(Fpp, prm.leaf, prm.tol, _compressor(prm, p, 0))
+            graph = bdlr.front_graph(Ap, front_indices(et, sym, p)) if prm.compressor == "bdlr" else None
+            H = hodlr.build(Fpp, prm.leaf, prm.tol, _compressor(prm, p, 0, graph, npv))
             hodlr.factor(H)
-            W, V = _compressor(prm, p, 1)(Ffp, 0, 0) if Ffp.shape[0] else \
+            W, V = _compressor(prm, p, 1, graph, npv)(Ffp, 0, 0) if Ffp.shape[0] else \
                 (np.zeros((0, 0)), np.zeros((npv, 0)))
             if prm.compress_ff and Fff.shape[0]:
-                Fff = hodlr.to_dense(hodlr.build(Fff, prm.leaf, prm.tol, _compressor(prm, p, 2)))
+                Fff = hodlr.to_dense(hodlr.build(Fff, prm.leaf, prm.tol, _compressor(prm, p, 2, graph, npv)))
             T = V.T @ hodlr.solve(H, V)
             updates[p] = Fff - W @ T @ W.T
             fronts[p] = Front(npv, "hodlr", H=H, W=W, V=V)

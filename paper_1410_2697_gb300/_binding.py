@@ -28,6 +28,7 @@ HM_ERR_BREAKDOWN = 9
 HM_PREC_FP64 = 0
 HM_PREC_MIXED = 1
 HM_PREC_MIXED_BF16 = 2
+HM_COMP_RRF, HM_COMP_BDLR = 0, 1
 
 EXPORTED = ["hm_default_opts", "hm_create", "hm_ctx_destroy", "hm_analyze", "hm_analyze_batch", "hm_get_sizes",
             "hm_get_ordering", "hm_get_symbolic", "hm_factor", "hm_autotune", "hm_tune_force", "hm_solve", "hm_direct_solve",
@@ -42,7 +43,8 @@ class HmOpts(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("nd_leaf", C.c_int),
                 ("hodlr_leaf", C.c_int), ("n_c", C.c_int), ("samples", C.c_int),
                 ("seed", C.c_uint64), ("restart", C.c_int), ("hbm_budget", C.c_size_t),
-                ("stream", C.c_void_p), ("dofs_per_node", C.c_int)]
+                ("stream", C.c_void_p), ("dofs_per_node", C.c_int), ("compressor", C.c_int),
+                ("bdlr_depth", C.c_int)]
 
 
 class HmSolveInfo(C.Structure):

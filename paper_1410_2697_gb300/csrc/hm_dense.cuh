@@ -85,6 +85,22 @@ struct TsqrBlock {
 // SVD of M = R^T (R k x k upper triangular, ld k) by one-sided Jacobi; writes
 // UhS = Uhat_r Sigma_r (k x k, ld k; columns >= rank zero) and Vh = Vhat_r (same),
 // sorted by decreasing singular value; rank = #{sigma_i > tol * sigma_1}.
+// Boundary-distance low-rank approximation (BDLR, Section 2.2) of one off-diagonal block
+// B = K[x0 : x0 + mx, y0 : y0 + my] of front q (nhat x nhat, column-major, lower triangle
+// assembled; trans = 1: B(i, j) is stored at (y0 + j, x0 + i)).  Rows of X within graph
+// distance depth of Y and columns of Y within depth of X (graph of A restricted to the
+// front's unknowns; at most cap each, nearer first, then lower position) give B^ =
+// B(I, J); complete-pivoting LU of B^ with rank r = pivots while |u_ss| >= tol |u_11|;
+// U = B(:, J_q) U_r^{-1} (mx x r, ld ldu) and V = (L_r^{-1} B(I_p, :))^T (my x r, ld
+// ldv), so B ~ U V^T; *rank = r.  Columns r.. of U and V are left as they are (zero).
+struct BdlrTask {
+  const void* F;
+  void* U;
+  void* V;
+  int* rank;
+  int q, nh, x0, mx, y0, my, trans, ldu, ldv, cap;
+};
+
 struct SvdTask {
   const void* R;
   void* UhS;
@@ -148,6 +164,10 @@ void launch_tsqr(const TsqrTask* tasks, int ntasks, const TsqrBlock* blocks, int
                  size_t smem_stack, T* scratch, cudaStream_t s);
 template <typename T>
 void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStream_t s);
+template <typename T>
+void launch_bdlr(const BdlrTask* tasks, int ntasks, int maxnh, int maxcap, int depth, double tol,
+                 const int32_t* first, const int* npiv, const int64_t* ifoff, const int32_t* iflist,
+                 const int64_t* prowptr, const int32_t* pcol, cudaStream_t s);
 template <typename T>
 void launch_omega(const OmegaTask* tasks, int ntasks, uint64_t seed, cudaStream_t s);
 template <typename T>

@@ -1057,6 +1057,193 @@ __global__ void __launch_bounds__(512) k_svd(const SvdTask* __restrict__ tasks, 
   if (threadIdx.x == 0 && t.rank) *t.rank = rank;
 }
 
+// =====================================================================================
+// BDLR (Section 2.2, Eq. Bhat): one block of 256 threads per off-diagonal block.
+// (1) Breadth-first distances (up to depth) from Y and from X over the graph of A
+//     restricted to the front's unknowns [I_p, I_p^f] (local position p <-> global new
+//     index first[q] + p for p < np, else the sorted I_p^f list, found by bisection).
+// (2) I = rows of X with distance <= depth from Y, J likewise, nearer first then lower
+//     position, at most cap each (warp-ballot compaction in position order).
+// (3) Complete-pivoting LU of B^ = B(I, J) in shared memory (argmax of |entry|, ties to
+//     the lower (i, j) in selection order), stopping at the first pivot below tol |u_11|.
+// (4) U rows = B(x, J_q) U_r^{-1} (one row of X per thread), V rows = L_r^{-1} B(I_p, y)
+//     (one column of Y per thread).
+// =====================================================================================
+constexpr unsigned char kBdlrFar = 255;
+
+__device__ __forceinline__ int bdlr_local(int u, int b0, int np, const int32_t* __restrict__ If, int nu) {
+  if (u >= b0 && u < b0 + np) return u - b0;
+  int lo = 0, hi = nu;  // first position with If[pos] >= u
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (If[mid] < u) lo = mid + 1; else hi = mid;
+  }
+  return (lo < nu && If[lo] == u) ? np + lo : -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bdlr(const BdlrTask* __restrict__ tasks, int depth, double tol,
+                                              const int32_t* __restrict__ first, const int* __restrict__ npiv,
+                                              const int64_t* __restrict__ ifoff, const int32_t* __restrict__ iflist,
+                                              const int64_t* __restrict__ prowptr, const int32_t* __restrict__ pcol,
+                                              int maxcap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BdlrTask t = tasks[blockIdx.x];
+  const int nh = t.nh, cap = t.cap, q = t.q;
+  const int np = npiv[q], nu = nh - np, b0 = first[q];
+  const int32_t* If = iflist + ifoff[q];
+  // shared memory: Bh (maxcap^2 T), row/col lists, pivot orders, then the two distance arrays
+  T* Bh = reinterpret_cast<T*>(smem_raw);
+  int* Il = reinterpret_cast<int*>(Bh + (size_t)maxcap * maxcap);
+  int* Jl = Il + maxcap;
+  int* pr = Jl + maxcap;
+  int* pc = pr + maxcap;
+  unsigned char* rowUsed = reinterpret_cast<unsigned char*>(pc + maxcap);
+  unsigned char* colUsed = rowUsed + maxcap;
+  unsigned char* dY = colUsed + maxcap;
+  unsigned char* dX = dY + nh;
+  __shared__ int s_n[2], s_rank, s_stop;
+  __shared__ T s_val[8];
+  __shared__ int s_idx[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = threadIdx.x; v < nh; v += blockDim.x) {
+    dY[v] = (v >= t.y0 && v < t.y0 + t.my) ? 0 : kBdlrFar;
+    dX[v] = (v >= t.x0 && v < t.x0 + t.mx) ? 0 : kBdlrFar;
+  }
+  __syncthreads();
+  for (int l = 0; l < depth; ++l) {
+    for (int v = threadIdx.x; v < nh; v += blockDim.x) {
+      const bool fy = dY[v] == l, fx = dX[v] == l;
+      if (!fy && !fx) continue;
+      const int g = v < np ? b0 + v : If[v - np];
+      for (int64_t e = prowptr[g]; e < prowptr[g + 1]; ++e) {
+        const int p = bdlr_local(pcol[e], b0, np, If, nu);
+        if (p < 0) continue;
+        if (fy && dY[p] == kBdlrFar) dY[p] = (unsigned char)(l + 1);
+        if (fx && dX[p] == kBdlrFar) dX[p] = (unsigned char)(l + 1);
+      }
+    }
+    __syncthreads();
+  }
+  // selection in (distance, position) order
+  if (wid < 2) {
+    const unsigned char* d = wid == 0 ? dY : dX;
+    const int lo = wid == 0 ? t.x0 : t.y0, m = wid == 0 ? t.mx : t.my;
+    int* out = wid == 0 ? Il : Jl;
+    int cnt = 0;
+    for (int l = 1; l <= depth && cnt < cap; ++l)
+      for (int base = 0; base < m && cnt < cap; base += 32) {
+        const int i = base + lane;
+        const bool sel = i < m && d[lo + i] == l;
+        const unsigned bal = __ballot_sync(0xffffffffu, sel);
+        const int before = __popc(bal & ((1u << lane) - 1u));
+        if (sel && cnt + before < cap) out[cnt + before] = i;
+        cnt = min(cap, cnt + __popc(bal));
+      }
+    if (lane == 0) s_n[wid] = cnt;
+  }
+  __syncthreads();
+  const int nI = s_n[0], nJ = s_n[1];
+  auto Bel = [&](int i, int j) -> T {  // B(i, j), i in X, j in Y (block-relative)
+    const T* F = (const T*)t.F;
+    return t.trans ? F[(size_t)(t.y0 + j) + (size_t)(t.x0 + i) * nh] : F[(size_t)(t.x0 + i) + (size_t)(t.y0 + j) * nh];
+  };
+  for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
+    const int i = e / nJ, j = e % nJ;
+    Bh[i * maxcap + j] = Bel(Il[i], Jl[j]);
+  }
+  for (int a = threadIdx.x; a < maxcap; a += blockDim.x) { rowUsed[a] = 0; colUsed[a] = 0; }
+  if (threadIdx.x == 0) { s_rank = 0; s_stop = 0; }
+  __syncthreads();
+  // complete-pivoting LU; rows/columns already pivoted are marked by pr/pc entries
+  T u11 = T(0);
+  const int rmax = min(nI, nJ);
+  for (int s = 0; s < rmax; ++s) {
+    T best = T(-1);
+    int bidx = INT_MAX;
+    for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
+      const int i = e / nJ, j = e % nJ;
+      if (rowUsed[i] || colUsed[j]) continue;
+      const T v = fabs(Bh[i * maxcap + j]);
+      if (v > best || (v == best && e < bidx)) { best = v; bidx = e; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if (lane == 0) { s_val[wid] = best; s_idx[wid] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T bv = s_val[0];
+      int bi = s_idx[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bi)) { bv = s_val[w]; bi = s_idx[w]; }
+      if (s == 0) u11 = bv;
+      const T u1 = s == 0 ? bv : fabs(Bh[pr[0] * maxcap + pc[0]]);
+      if (bv <= T(0) || (s > 0 && tol > 0.0 && bv < (T)tol * u1)) s_stop = 1;
+      else {
+        pr[s] = bi / nJ;
+        pc[s] = bi % nJ;
+        s_rank = s + 1;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int ip = pr[s], jp = pc[s];
+    const T piv = Bh[ip * maxcap + jp];
+    // eliminate: multipliers into column jp of the remaining rows, update the rest
+    for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
+      const int i = e / nJ, j = e % nJ;
+      if (i == ip || j == jp || rowUsed[i] || colUsed[j]) continue;
+      const T l = Bh[i * maxcap + jp] / piv;
+      Bh[i * maxcap + j] -= l * Bh[ip * maxcap + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nI; i += blockDim.x)
+      if (i != ip && !rowUsed[i]) Bh[i * maxcap + jp] /= piv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      rowUsed[ip] = 1;
+      colUsed[jp] = 1;
+    }
+    __syncthreads();
+  }
+  (void)u11;
+  const int r = s_rank;
+  // L_r(a, b) = Bh[pr[a], pc[b]] (a > b), U_r(a, b) = Bh[pr[a], pc[b]] (a <= b)
+  T* U = (T*)t.U;
+  T* V = (T*)t.V;
+  for (int x = threadIdx.x; x < t.mx; x += blockDim.x) {
+    // c~ U_r = B(x, J_q): c~_b = (B(x, J[pc[b]]) - sum_{a < b} c~_a U_r(a, b)) / U_r(b, b)
+    for (int b = 0; b < r; ++b) {
+      T v = Bel(x, Jl[pc[b]]);
+      for (int a = 0; a < b; ++a) v -= U[x + (size_t)a * t.ldu] * Bh[pr[a] * maxcap + pc[b]];
+      U[x + (size_t)b * t.ldu] = v / Bh[pr[b] * maxcap + pc[b]];
+    }
+  }
+  for (int y = threadIdx.x; y < t.my; y += blockDim.x) {
+    // L_r w~ = B(I_p, y): w~_a = B(I[pr[a]], y) - sum_{b < a} L_r(a, b) w~_b
+    for (int a = 0; a < r; ++a) {
+      T v = Bel(Il[pr[a]], y);
+      for (int b = 0; b < a; ++b) v -= Bh[pr[a] * maxcap + pc[b]] * V[y + (size_t)b * t.ldv];
+      V[y + (size_t)a * t.ldv] = v;
+    }
+  }
+  if (threadIdx.x == 0 && t.rank) *t.rank = r;
+}
+
+template <typename T>
+void launch_bdlr(const BdlrTask* tasks, int ntasks, int maxnh, int maxcap, int depth, double tol,
+                 const int32_t* first, const int* npiv, const int64_t* ifoff, const int32_t* iflist,
+                 const int64_t* prowptr, const int32_t* pcol, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)maxcap * maxcap * sizeof(T) + 4 * sizeof(int) * maxcap + 2 * (size_t)maxcap +
+                      2 * (size_t)maxnh;
+  k_bdlr<T><<<ntasks, 256, smem, s>>>(tasks, depth, tol, first, npiv, ifoff, iflist, prowptr, pcol, maxcap);
+}
+
 template <typename T>
 void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStream_t s) {
   if (ntasks <= 0) return;
@@ -1065,6 +1252,8 @@ void launch_svd(const SvdTask* tasks, int ntasks, int maxk, double tol, cudaStre
 }
 
 int dense_comp_setup(int max_smem) {
+  HM_CUDA(allow_max_dyn_smem(k_bdlr<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_bdlr<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_qr_smem<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_qr_smem<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_qr_blocked<float>, max_smem));
@@ -1089,6 +1278,10 @@ template void launch_tsqr<float>(const TsqrTask*, int, const TsqrBlock*, int, si
 template void launch_tsqr<double>(const TsqrTask*, int, const TsqrBlock*, int, size_t, size_t, double*,
                                   cudaStream_t);
 template void launch_svd<float>(const SvdTask*, int, int, double, cudaStream_t);
+template void launch_bdlr<float>(const BdlrTask*, int, int, int, int, double, const int32_t*, const int*,
+                                 const int64_t*, const int32_t*, const int64_t*, const int32_t*, cudaStream_t);
+template void launch_bdlr<double>(const BdlrTask*, int, int, int, int, double, const int32_t*, const int*,
+                                  const int64_t*, const int32_t*, const int64_t*, const int32_t*, cudaStream_t);
 template void launch_svd<double>(const SvdTask*, int, int, double, cudaStream_t);
 
 }  // namespace hm

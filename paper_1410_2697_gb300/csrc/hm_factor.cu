@@ -183,8 +183,13 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
       }
       debug_stage<T>(sys, "dense", l);
     }
+    if (lp.n_hodlr && lp.bdlr.count) {
+      ProfScope ps(ctx, PC_BDLR, lp.bdlr.work);
+      launch_bdlr<T>(lp.bdlr.dev(base), lp.bdlr.count, lp.bdlr_maxnh, lp.bdlr_maxcap, ctx->opts.bdlr_depth, tol,
+                     sys->d_first, P.d_np, sys->d_ifoff, sys->d_iflist, sys->d_prowptr, sys->d_pcol, s);
+    }
     if (lp.n_hodlr) {
-      {
+      if (lp.omega.count) {
         ProfScope ps(ctx, PC_SKETCH, lp.omega.work);
         launch_omega<T>(lp.omega.dev(base), lp.omega.count, ctx->opts.seed, s);
       }
@@ -193,7 +198,7 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
       debug_stage<T>(sys, "qrY", l);
       run_gemm<T>(sys, lp.sampZ, base, PC_GEMM_FACTOR);
       run_qr<T>(sys, lp.qrZ, base);
-      {
+      if (lp.svd.count) {
         ProfScope ps(ctx, PC_SVD, lp.svd.work);
         launch_svd<T>(lp.svd.dev(base), lp.svd.count, lp.svd_maxk, tol, s);
       }

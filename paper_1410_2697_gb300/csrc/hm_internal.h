@@ -45,6 +45,10 @@ inline Work work_of(const CholSolveTask& t, int es) {
 inline Work work_of(const QrTask& t, int es) {
   return Work{4.0 * t.m * t.k * t.k, es * (3.0 * t.m * t.k + (t.R ? (double)t.k * t.k : 0.0))};
 }
+inline Work work_of(const BdlrTask& t, int es) {
+  const double c = t.cap, mm = (double)t.mx + t.my;
+  return Work{c * c * c + mm * c * c, es * (2.0 * mm * c + c * c)};
+}
 inline Work work_of(const SvdTask& t, int es) {
   return Work{12.0 * t.k * t.k * t.k, es * 3.0 * t.k * t.k};  // ~ per-sweep cost x 2
 }
@@ -189,7 +193,7 @@ enum ProfCat {
   PC_ND = 0, PC_SYMBOLIC, PC_PERMUTE_CSR, PC_SCATTER, PC_EXTEND_ADD, PC_POTRF, PC_TRSM,
   PC_GEMM_FACTOR, PC_SKETCH, PC_QR, PC_SVD, PC_CHOL_SOLVE, PC_CORE_LU, PC_INVERSE,
   PC_UP, PC_DOWN, PC_GEMM_APPLY, PC_SPMV, PC_DOTS, PC_GS_UPDATE, PC_GMRES_SMALL, PC_VECTOR,
-  PC_MEMSET, PC_SWEEP, PC_COUNT
+  PC_MEMSET, PC_SWEEP, PC_BDLR, PC_COUNT
 };
 const char* prof_cat_name(int c);
 
@@ -302,6 +306,8 @@ struct LevelFactorPlan {
   QrBatch qrY, qrZ;
   Span<SvdTask> svd;
   int svd_maxk = 0;
+  Span<BdlrTask> bdlr;         // BDLR compressor: every off-diagonal block of the level
+  int bdlr_maxnh = 0, bdlr_maxcap = 0;
   int64_t x_copy_off = 0, x_copy_len = 0;  // Bo -> X copy (elements)
   Span<PotrfTask> leaf_potrf;
   int leaf_maxn = 0;

@@ -392,6 +392,8 @@ int build_plan(hm_sys_s* sys) {
     std::vector<CholSolveTask> lsol;
     std::vector<CholInvTask> linv;
     std::vector<GemmTask> sT, sP, sF;
+    std::vector<BdlrTask> bd;
+    const bool bdlr = o.compressor == HM_COMP_BDLR;
     int maxL = 0;
     for (int q : fr) {
       const FrontGeom& g = P.fg[q];
@@ -406,6 +408,16 @@ int build_plan(hm_sys_s* sys) {
         const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid, kb = nd.kb, k = h.kl[nd.level];
         const uint64_t blk = block_id(q, 0, nd.level, nd.index);
         void* Kba = at(F, fo + nd.mid + (int64_t)nd.lo * nh, es);  // nb x na
+        if (bdlr) {
+          const int64_t colb = (int64_t)h.col[nd.level] * np;
+          bd.push_back(BdlrTask{at(F, fo, es), at(Bo, h.bo_off + colb + nd.lo, es),
+                                at(Bo, h.bo_off + colb + nd.mid, es), ranks + nd.rank_slot, q, nh, nd.lo, na,
+                                nd.mid, nb, 1, np, np, kb});
+          lp.bdlr_maxnh = std::max(lp.bdlr_maxnh, nh);
+          lp.bdlr_maxcap = std::max(lp.bdlr_maxcap, kb);
+          fbytes += es * (3.0 * (na + nb) * k);
+          continue;
+        }
         om.push_back(OmegaTask{at(Cp, nd.om_off, es), blk, nb, kb, nb, 0});
         gy.push_back(gemm(Kba, nh, 1, at(Cp, nd.om_off, es), nb, 0, at(Cp, nd.y_off, es), na, na, kb,
                           nb, 1.0, 0.0));
@@ -427,6 +439,12 @@ int build_plan(hm_sys_s* sys) {
         const int kf = h.kf;
         const uint64_t blk = block_id(q, 1, 0, 0);
         void* Ffp = at(F, fo + np, es);  // nu x np, ld nh
+        if (bdlr) {
+          bd.push_back(BdlrTask{at(F, fo, es), at(W, h.w_off, es), at(Bo, h.bo_off, es), ranks + h.rank_slot_f, q,
+                                nh, np, nu, 0, np, 0, nu, np, kf});
+          lp.bdlr_maxnh = std::max(lp.bdlr_maxnh, nh);
+          lp.bdlr_maxcap = std::max(lp.bdlr_maxcap, kf);
+        } else {
         om.push_back(OmegaTask{at(Cp, h.fom_off, es), blk, np, kf, np, 0});
         gy.push_back(gemm(Ffp, nh, 0, at(Cp, h.fom_off, es), np, 0, at(Cp, h.fy_off, es), nu, nu, kf,
                           np, 1.0, 0.0));
@@ -441,6 +459,7 @@ int build_plan(hm_sys_s* sys) {
                           at(W, h.w_off, es), nu, nu, kf, kf, 1.0, 0.0));
         gv.push_back(gemm(at(Cp, h.fz_off, es), np, 0, at(Cp, h.fvh_off, es), kf, 0,
                           at(Bo, h.bo_off, es), np, np, kf, kf, 1.0, 0.0));
+        }
         // Schur complement: T = Vf^T Vtilde, P = W T, F_ff -= P W^T
         sT.push_back(gemm(at(Bo, h.bo_off, es), np, 1, at(X, h.bo_off, es), np, 0, at(Tm, h.t_off, es),
                           kf, kf, kf, np, 1.0, 0.0));
@@ -460,6 +479,7 @@ int build_plan(hm_sys_s* sys) {
         fbytes += es * (double)n * n;
       }
     }
+    lp.bdlr = tb.add(bd);
     lp.omega = tb.add(om);
     const bool tc = sys->precision == HM_PREC_MIXED_BF16;  // sampling products on tensor cores
     lp.sampY = tb.add_gemm(gy, tc);

@@ -1,0 +1,106 @@
+"""BDLR (Section 2.2), the paper's own compressor, on the GPU against the oracle: every
+low-rank block of every HODLR front (same selected rows and columns, same complete
+pivoting, same rank) and the preconditioned solve."""
+import numpy as np
+import pytest
+
+from fixtures import hex_cube, lognormal_coefficients, q1_square, rhs_uniform
+from oracle import dense_mf, gmres, hodlr, hodlr_mf, nd, symbolic
+
+pytestmark = pytest.mark.gpu
+
+try:
+    import paper_1410_2697_gb300 as hm
+except ImportError:
+    import torch
+    if torch.cuda.is_available():
+        raise
+    pytest.skip("CUDA library not built on this CPU-only machine", allow_module_level=True)
+
+LEAF, HL, NC, K = 64, 8, 8, 24
+
+
+def problems():
+    return {"q1_32": q1_square(32, lognormal_coefficients(32 * 32, 1.0, seed=81)),
+            "hex_8": hex_cube(8, lognormal_coefficients(8 ** 3, 0.5, seed=82))}
+
+
+PROBLEMS = problems()
+
+
+def gpu_system(p, precision, depth, tol):
+    o = hm.hm_default_opts()
+    o.precision = precision
+    o.nd_leaf, o.hodlr_leaf, o.n_c, o.samples = LEAF, HL, NC, K
+    o.compressor = hm.abi.HM_COMP_BDLR
+    o.bdlr_depth = depth
+    ctx = hm.hm_create(o)
+    s = hm.hm_analyze(ctx, p.n, p.rowptr, p.colidx, p.dim, p.coords)
+    hm.hm_factor(s, p.values, tol)
+    return ctx, s
+
+
+def oracle_factor(p, depth, tol):
+    et = nd.nested_dissection(p.coords, LEAF)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    prm = hodlr_mf.Params(tol=tol, n_c=NC, leaf=HL, compressor="bdlr", samples=K, bdlr_depth=depth)
+    fr, _ = hodlr_mf.factor(Ap, et, sym, prm)
+    return et, sym, Ap, fr
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("depth", [1, 2])
+def test_bdlr_blocks_match_oracle_fp64(name, depth):
+    p = PROBLEMS[name]
+    tol = 1e-4
+    et, sym, Ap, fr = oracle_factor(p, depth, tol)
+    ctx, s = gpu_system(p, hm.HM_PREC_FP64, depth, tol)
+    nblocks = 0
+    for q in range(et.nfronts):
+        if fr[q].kind != "hodlr":
+            continue
+        blocks = {(-1, 0): (fr[q].W, fr[q].V)}
+        for node in hodlr.iter_nodes(fr[q].H):
+            if node.children:
+                blocks[(node.level, node.index)] = (node.U, node.V)
+        for (lv, ni), (Uo, Vo) in blocks.items():
+            U, V, r = hm.hm_get_hodlr_block(s, q, lv, ni)
+            assert r == Uo.shape[1], (q, lv, ni, r, Uo.shape)
+            Bo = Uo @ Vo.T
+            if Bo.size == 0 or r == 0:
+                continue
+            err = np.linalg.norm(U @ V.T - Bo) / max(np.linalg.norm(Bo), 1e-300)
+            assert err <= 1e-10, (q, lv, ni, err)
+            nblocks += 1
+    assert nblocks > 0
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", ["HM_PREC_FP64", "HM_PREC_MIXED"])
+def test_bdlr_solve_matches_oracle(precision):
+    p = PROBLEMS["q1_32"]
+    tol, depth = 1e-4, 1
+    et, sym, Ap, fr = oracle_factor(p, depth, tol)
+    b = rhs_uniform(p.n, 2, 83)
+    _, oinfo = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), b[:, 0][et.perm],
+                           1e-10, 30)
+    ctx, s = gpu_system(p, getattr(hm, precision), depth, tol)
+    x = np.zeros_like(b)
+    info = hm.hm_solve(s, 2, b, 1e-10, 2000, x)
+    assert info["converged"] == 1
+    assert abs(info["iters"] - oinfo["iters"]) <= 3, (info["iters"], oinfo["iters"])
+    for c in range(2):
+        xs = dense_mf.direct_solve(p.rowptr, p.colidx, p.values, p.coords, b[:, c])
+        assert np.linalg.norm(x[:, c] - xs) / np.linalg.norm(xs) <= 1e-8
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(ctx)
+
+
+def test_compressor_option_is_checked():
+    o = hm.hm_default_opts()
+    o.compressor = 5
+    with pytest.raises(hm.HmError) as e:
+        hm.hm_create(o)
+    assert e.value.status == hm.abi.HM_ERR_INVALID_ARG
