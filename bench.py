@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--n-c", type=int, default=64)
     ap.add_argument("--hodlr-leaf", type=int, default=64)
     ap.add_argument("--samples", type=int, default=48)
+    ap.add_argument("--compressor", choices=["rrf", "bdlr"], default="rrf",
+                    help="off-diagonal compressor: randomized range finder or BDLR (the paper's)")
+    ap.add_argument("--bdlr-depth", type=int, default=1, help="BDLR graph-distance depth")
     ap.add_argument("--sweep-tol", action="store_true",
                     help="accuracy sweep over the compression tolerance (Q1 lognormal, --m elements)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -335,6 +338,8 @@ def run_ours(args, rank, world, local):
         o.samples = W.samples
         o.restart = 30
         o.dofs_per_node = W.dofs
+        o.compressor = hm.abi.HM_COMP_BDLR if args.compressor == "bdlr" else hm.abi.HM_COMP_RRF
+        o.bdlr_depth = args.bdlr_depth
         o.stream = stream.cuda_stream
         return hm.hm_create(o)
 
@@ -470,6 +475,7 @@ def run_ours(args, rank, world, local):
                    "restart": 30, "nd_leaf": W.nd_leaf, "hodlr_leaf": W.hodlr_leaf, "n_c": W.n_c,
                    "samples": W.samples, "step": "analyze + factor + solve(nrhs) + destroy",
                    "autotuned_sites": tuned_sites,
+                   "compressor": args.compressor if args.compressor == "rrf" else f"bdlr (depth {args.bdlr_depth})",
                    "l2": f"inputs larger than L2 (A: {(P.nnz * 12 + P.n * 8) / 1e6:.0f} MB CSR)",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": p50, "p99_ms": p99,

