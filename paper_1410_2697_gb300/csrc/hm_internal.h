@@ -353,7 +353,6 @@ struct SolvePlan {
   int nrhs = 0;
   std::vector<LevelSolvePlan> levels;
   std::vector<int64_t> fv_off;  // per front, element offset of its (nhat x nrhs) vector
-  std::vector<int64_t> yv_off;  // per front, offset of y in the scratch (-1: dense front)
   int64_t fv_total = 0;
   int64_t sb_total = 0;         // node t/s buffers + tf buffers
   TaskBuf tb;
@@ -364,7 +363,6 @@ struct SolvePlan {
   void* d_sb = nullptr;         // T
   void* d_xfix = nullptr;       // T, n x nrhs: the solution (task tables point into it)
   int64_t* d_fvoff = nullptr;
-  int64_t* d_yvoff = nullptr;   // per front: offset of y (np x nrhs) in the scratch, -1 if dense
   // captured apply (graph of the launches for input graph_in) and the last input seen
   std::vector<void*> allocs;    // device memory of this plan (freed when it is dropped)
   int64_t last_use = 0;

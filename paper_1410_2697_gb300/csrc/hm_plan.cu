@@ -606,32 +606,27 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   int64_t fv = 0;
   for (int q = 0; q < nf; ++q) { sp->fv_off[q] = fv; fv += (int64_t)P.fg[q].nhat * nrhs; }
   sp->fv_total = fv;
-  // scratch: per HODLR node t and s (2k x nrhs each); per HODLR front tf (kf x nrhs)
-  // and the pivot-block solution y (np x nrhs)
+  // scratch: per HODLR node t (2k x nrhs); per HODLR front tf (kf x nrhs).  A HODLR
+  // front's pivot-block solution y lives in its own rows of the solution xfix (ld n), so
+  // the downward pass needs no copy-out.
   std::vector<std::vector<int64_t>> node_sb(P.hf.size());
-  std::vector<int64_t> front_sb(P.hf.size()), front_yv(P.hf.size());
-  std::vector<int64_t>& yvoff = sp->yv_off;
-  yvoff.assign(nf, -1);
+  std::vector<int64_t> front_sb(P.hf.size());
   int64_t sb = 0;
   for (size_t i = 0; i < P.hf.size(); ++i) {
     const HFront& h = P.hf[i];
-    for (const auto& nd : h.nodes) { node_sb[i].push_back(sb); sb += (int64_t)4 * h.kl[nd.level] * nrhs; }
+    for (const auto& nd : h.nodes) { node_sb[i].push_back(sb); sb += (int64_t)2 * h.kl[nd.level] * nrhs; }
     front_sb[i] = sb;
     sb += (int64_t)h.kf * nrhs;
-    front_yv[i] = sb;
-    yvoff[h.q] = sb;
-    sb += (int64_t)h.np * nrhs;
   }
   sp->sb_total = sb;
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_fv, (size_t)std::max<int64_t>(fv, 1) * es));
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_sb, (size_t)std::max<int64_t>(sb, 1) * es));
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_fvoff, (size_t)nf * 8));
-  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_yvoff, (size_t)nf * 8));
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_xfix, (size_t)std::max<int64_t>((int64_t)sys->n * nrhs, 1) * es));
   HM_CUDA(cudaMemcpyAsync(sp->d_fvoff, sp->fv_off.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
                           sys->ctx->stream));
-  HM_CUDA(cudaMemcpyAsync(sp->d_yvoff, yvoff.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
-                          sys->ctx->stream));
+  void* XF = sp->d_xfix;
+  const int n = sys->n;
   void* F = sys->d_front;
   void* Bo = sys->d_bo;
   void* X = sys->d_x;
@@ -681,11 +676,11 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
       if (g.hodlr < 0) continue;
       const HFront& h = P.hf[g.hodlr];
       maxL = std::max(maxL, h.L);
-      const int64_t fvq = sp->fv_off[q], yq = front_yv[g.hodlr];
+      const int64_t fvq = sp->fv_off[q], yq = sys->h_first[q];  // y = xfix rows of I_q
       for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
         const int lo = h.leaf_lo[li], nl = h.leaf_hi[li] - lo;
         dg.push_back(gemm(at(F, g.off + lo + (int64_t)lo * g.nhat, es), g.nhat, 0, at(FV, fvq + lo, es),
-                          g.nhat, 0, at(SB, yq + lo, es), h.np, nl, nrhs, nl, 1.0, 0.0));
+                          g.nhat, 0, at(XF, yq + lo, es), n, nl, nrhs, nl, 1.0, 0.0));
       }
       if (h.kf > 0) {
         void* tf = at(SB, front_sb[g.hodlr], es);
@@ -695,7 +690,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
                           h.nu, nrhs, h.kf, -1.0, 1.0));
         d1.push_back(gemm(at(W, h.w_off, es), h.nu, 1, at(FV, fvq + h.np, es), g.nhat, 0, tf, h.kf,
                           h.kf, nrhs, h.nu, 1.0, 0.0));
-        d2.push_back(gemm(at(X, h.bo_off, es), h.np, 0, tf, h.kf, 0, at(SB, yq, es), h.np, h.np,
+        d2.push_back(gemm(at(X, h.bo_off, es), h.np, 0, tf, h.kf, 0, at(XF, yq, es), n, h.np,
                           nrhs, h.kf, 1.0, 1.0));
       }
     }
@@ -710,21 +705,21 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
         const HFront& h = P.hf[g.hodlr];
         if (h.L < ht) continue;
         const int lv = h.L - ht, k = h.kl[lv], np = h.np;
-        const int64_t colo = (int64_t)h.col[lv] * np, yq = front_yv[g.hodlr];
+        const int64_t colo = (int64_t)h.col[lv] * np, yq = sys->h_first[q];
         for (size_t ni = 0; ni < h.nodes.size(); ++ni) {
           const auto& nd = h.nodes[ni];
           if (nd.level != lv) continue;
           const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid;
           void* tn = at(SB, node_sb[g.hodlr][ni], es);
           void* Gl = at(Gm, h.g_off + (int64_t)2 * (h.col[lv] - h.kf) * np, es);
-          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.lo, es), np, 1, at(SB, yq + nd.lo, es), np, 0,
+          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.lo, es), np, 1, at(XF, yq + nd.lo, es), n, 0,
                             tn, 2 * k, k, nrhs, na, 1.0, 0.0));
-          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.mid, es), np, 1, at(SB, yq + nd.mid, es), np, 0,
+          tt.push_back(gemm(at(Bo, h.bo_off + colo + nd.mid, es), np, 1, at(XF, yq + nd.mid, es), n, 0,
                             at(SB, node_sb[g.hodlr][ni] + k, es), 2 * k, k, nrhs, nb, 1.0, 0.0));
           // y_a -= Zhat_a s_a = (Zhat_a C^{-1}[0:k, :]) t, likewise y_b
-          upd.push_back(gemm(at(Gl, nd.lo, es), np, 0, tn, 2 * k, 0, at(SB, yq + nd.lo, es), np, na, nrhs,
+          upd.push_back(gemm(at(Gl, nd.lo, es), np, 0, tn, 2 * k, 0, at(XF, yq + nd.lo, es), n, na, nrhs,
                              2 * k, -1.0, 1.0));
-          upd.push_back(gemm(at(Gl, nd.mid, es), np, 0, tn, 2 * k, 0, at(SB, yq + nd.mid, es), np, nb, nrhs,
+          upd.push_back(gemm(at(Gl, nd.mid, es), np, 0, tn, 2 * k, 0, at(XF, yq + nd.mid, es), n, nb, nrhs,
                              2 * k, -1.0, 1.0));
         }
       }

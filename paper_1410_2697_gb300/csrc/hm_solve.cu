@@ -339,22 +339,6 @@ static void dense_down(const LevelSolvePlan& lp, const unsigned char* base, hm_s
   }
 }
 
-// HODLR fronts: x_p (= y - Vtilde W^T x_f, in the front's y buffer) -> output vector.
-template <typename T>
-__global__ void k_hodlr_out(const int* __restrict__ fronts, int nrhs, int n, T* __restrict__ xout,
-                            const int32_t* __restrict__ first, const int* __restrict__ npiv,
-                            const int64_t* __restrict__ yvoff, const T* __restrict__ SB) {
-  const int q = fronts[blockIdx.x];
-  const int64_t yo = yvoff[q];
-  if (yo < 0) return;
-  const int np = npiv[q], b0 = first[q];
-  const T* y = SB + yo;
-  for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
-    const int i = e % np, r = e / np;
-    xout[b0 + i + (int64_t)r * n] = y[i + (int64_t)r * np];
-  }
-}
-
 template <typename T>
 static void gemm_b(hm_ctx_s* ctx, const SolvePlan* sp, const GemmBatch& b) {
   if (b.tiles.count == 0) return;
@@ -424,10 +408,7 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
         gemm_b<T>(ctx, sp, H.upd);
       }
       gemm_b<T>(ctx, sp, lp.down1);
-      gemm_b<T>(ctx, sp, lp.down2);
-      ProfScope ps(ctx, PC_VECTOR, Work{});
-      k_hodlr_out<T><<<lp.n_hodlr, 256, 0, s>>>(lp.hfronts.dev(base), nrhs, n, xfix, sys->d_first,
-                                                P.d_np, sp->d_yvoff, (const T*)sp->d_sb);
+      gemm_b<T>(ctx, sp, lp.down2);  // x_p = y - Vtilde (W^T x_f), in place in xfix
     }
   }
   HM_CUDA(cudaGetLastError());
