@@ -110,6 +110,12 @@ def barrier(world):
         dist.barrier()
 
 
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, total_ms_max: float) -> float:
+    """Replicas: every rank processes the same units per step, so the job's rate is the
+    units of all ranks over the slowest rank's time (max over ranks of the timed region)."""
+    return units_per_rank_step * steps * world / (total_ms_max * 1e-3)
+
+
 def allreduce_max(v: float, world: int) -> float:
     if world == 1:
         return v
@@ -457,7 +463,7 @@ def run_ours(args, rank, world, local):
     hm.hm_ctx_destroy(ctx64)
 
     nsolve = nrhs * (len(bp) - 1 if bp is not None else 1)  # (mesh, rhs) pairs per step
-    value = nsolve * args.steps * world / (total_max * 1e-3)
+    value = whole_job_rate(nsolve, args.steps, world, total_max)
     fi, si = infos[-1]
     peaks = load_peaks()
     rl = roofline(prof, "f64" if W.headline == "FP64" else "f32", peaks, clk)
