@@ -53,13 +53,6 @@ struct TrsmTask {
   int row0, pad;
 };
 
-// X <- L^{-T} L^{-1} X for a Cholesky factor L (n <= 64 rows), ncols columns.
-struct CholSolveTask {
-  const void* L;
-  void* X;
-  int n, ldl, ldx, ncols;
-};
-
 // Householder QR of Y (m x k, ld): Q overwrites Y; R (k x k, ld k) written if non-null.
 struct QrTask {
   void* Y;
@@ -155,8 +148,6 @@ template <typename T>
 void launch_potrf(const PotrfTask* tasks, int ntasks, int maxn, int* err, cudaStream_t s);
 template <typename T>
 void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s);
-template <typename T>
-void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStream_t s);
 template <typename T>
 void launch_qr(const QrTask* tasks, int ntasks, int maxm, int64_t maxmk, int max_smem, cudaStream_t s);
 template <typename T>

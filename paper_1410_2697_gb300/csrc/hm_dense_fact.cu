@@ -100,58 +100,6 @@ void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s) {
 }
 
 // =====================================================================================
-// X <- L^{-T} L^{-1} X for a leaf Cholesky factor; threads own columns, 128 at a time.
-// =====================================================================================
-template <typename T>
-__global__ void __launch_bounds__(128) k_chol_solve(const CholSolveTask* __restrict__ tasks) {
-  extern __shared__ unsigned char smem_raw[];
-  const CholSolveTask t = tasks[blockIdx.x];
-  const int n = t.n, ls = n + 1;
-  T* Ls = reinterpret_cast<T*>(smem_raw);
-  T* X = Ls + n * ls;  // [n][128]
-  const T* L = (const T*)t.L;
-  T* Xg = (T*)t.X;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    if (i >= j) Ls[i + j * ls] = L[(size_t)i + (size_t)j * t.ldl];
-  }
-  for (int c0 = 0; c0 < t.ncols; c0 += 128) {
-    const int nc = min(128, t.ncols - c0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * nc; e += blockDim.x) {
-      const int i = e % n, c = e / n;
-      X[i * 128 + c] = Xg[(size_t)i + (size_t)(c0 + c) * t.ldx];
-    }
-    __syncthreads();
-    const int c = threadIdx.x;
-    if (c < nc) {
-      for (int j = 0; j < n; ++j) {  // L y = x
-        T v = X[j * 128 + c];
-        for (int i = 0; i < j; ++i) v -= Ls[j + i * ls] * X[i * 128 + c];
-        X[j * 128 + c] = v / Ls[j + j * ls];
-      }
-      for (int j = n - 1; j >= 0; --j) {  // L^T z = y
-        T v = X[j * 128 + c];
-        for (int i = j + 1; i < n; ++i) v -= Ls[i + j * ls] * X[i * 128 + c];
-        X[j * 128 + c] = v / Ls[j + j * ls];
-      }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * nc; e += blockDim.x) {
-      const int i = e % n, cc = e / n;
-      Xg[(size_t)i + (size_t)(c0 + cc) * t.ldx] = X[i * 128 + cc];
-    }
-  }
-}
-
-template <typename T>
-void launch_chol_solve(const CholSolveTask* tasks, int ntasks, int maxn, cudaStream_t s) {
-  if (ntasks <= 0) return;
-  const size_t smem = ((size_t)maxn * (maxn + 1) + 128 * (size_t)maxn) * sizeof(T);
-  k_chol_solve<T><<<ntasks, 128, smem, s>>>(tasks);
-}
-
-// =====================================================================================
 // Woodbury core: C = [[U^T Uhat, I], [I, V^T Vhat]] (n = 2k).  The GEMMs have written the
 // two diagonal k x k blocks; this kernel sets the identity blocks and inverts C by
 // Gauss-Jordan elimination with partial pivoting on [C | I] (C is symmetric indefinite),
@@ -572,8 +520,6 @@ template void launch_front_sweep<float>(const SweepTask*, int, int, int*, cudaSt
 template void launch_front_sweep<double>(const SweepTask*, int, int, int*, cudaStream_t);
 template void launch_trsm<float>(const TrsmTask*, int, int, cudaStream_t);
 template void launch_trsm<double>(const TrsmTask*, int, int, cudaStream_t);
-template void launch_chol_solve<float>(const CholSolveTask*, int, int, cudaStream_t);
-template void launch_chol_solve<double>(const CholSolveTask*, int, int, cudaStream_t);
 template void launch_core_lu<float>(const CoreLuTask*, int, int, int, int*, cudaStream_t);
 template void launch_core_lu<double>(const CoreLuTask*, int, int, int, int*, cudaStream_t);
 template void launch_chol_inverse<float>(const CholInvTask*, int, int, cudaStream_t);
@@ -584,8 +530,6 @@ int dense_fact_setup(int max_smem) {
   HM_CUDA(allow_max_dyn_smem(k_potrf<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_trsm<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_trsm<double>, max_smem));
-  HM_CUDA(allow_max_dyn_smem(k_chol_solve<float>, max_smem));
-  HM_CUDA(allow_max_dyn_smem(k_chol_solve<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_lu<float>, max_smem));

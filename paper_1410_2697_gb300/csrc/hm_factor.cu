@@ -206,23 +206,15 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
       run_gemm<T>(sys, lp.formU, base, PC_GEMM_FACTOR);
       run_gemm<T>(sys, lp.formV, base, PC_GEMM_FACTOR);
       debug_stage<T>(sys, "formUV", l);
-      if (lp.x_copy_len) {
-        ProfScope ps(ctx, PC_MEMSET, Work{0.0, 2.0 * es * lp.x_copy_len}, 0);
-        HM_CUDA(cudaMemcpyAsync((T*)sys->d_x + lp.x_copy_off, (T*)sys->d_bo + lp.x_copy_off,
-                                (size_t)lp.x_copy_len * sizeof(T), cudaMemcpyDeviceToDevice, s));
-      }
       {
         ProfScope ps(ctx, PC_POTRF, lp.leaf_potrf.work);
         launch_potrf<T>(lp.leaf_potrf.dev(base), lp.leaf_potrf.count, lp.leaf_maxn, sys->d_err, s);
-      }
-      if (lp.leaf_solve.count) {
-        ProfScope ps(ctx, PC_CHOL_SOLVE, lp.leaf_solve.work);
-        launch_chol_solve<T>(lp.leaf_solve.dev(base), lp.leaf_solve.count, lp.leaf_maxn, s);
       }
       {
         ProfScope ps(ctx, PC_INVERSE, lp.leaf_inv.work);
         launch_chol_inverse<T>(lp.leaf_inv.dev(base), lp.leaf_inv.count, lp.leaf_maxn, s);
       }
+      run_gemm<T>(sys, lp.leaf_x, base, PC_GEMM_FACTOR);  // X = D^{-1} Bo on the leaf rows
       debug_stage<T>(sys, "leaves", l);
       for (const auto& H : lp.heights) {
         run_gemm<T>(sys, H.pre, base, PC_GEMM_FACTOR);

@@ -39,9 +39,6 @@ inline Work work_of(const TrsmTask& t, int es) {
   const double rows = std::min(64, t.m - t.row0);
   return Work{rows * t.n * t.n, es * (2.0 * rows * t.n + 0.5 * t.n * t.n)};
 }
-inline Work work_of(const CholSolveTask& t, int es) {
-  return Work{2.0 * t.n * t.n * t.ncols, es * (0.5 * t.n * t.n + 2.0 * t.n * t.ncols)};
-}
 inline Work work_of(const QrTask& t, int es) {
   return Work{4.0 * t.m * t.k * t.k, es * (3.0 * t.m * t.k + (t.R ? (double)t.k * t.k : 0.0))};
 }
@@ -308,11 +305,10 @@ struct LevelFactorPlan {
   int svd_maxk = 0;
   Span<BdlrTask> bdlr;         // BDLR compressor: every off-diagonal block of the level
   int bdlr_maxnh = 0, bdlr_maxcap = 0;
-  int64_t x_copy_off = 0, x_copy_len = 0;  // Bo -> X copy (elements)
   Span<PotrfTask> leaf_potrf;
   int leaf_maxn = 0;
-  Span<CholSolveTask> leaf_solve;
-  Span<CholInvTask> leaf_inv;  // explicit leaf inverses for the apply
+  Span<CholInvTask> leaf_inv;  // explicit leaf inverses (factorization and apply)
+  GemmBatch leaf_x;            // X (leaf rows) = K_leaf^{-1} Bo (leaf rows): the first Woodbury sweep
   struct Height {
     GemmBatch pre;            // core diagonal blocks and t = Z^T X_anc
     Span<CoreLuTask> lu;      // explicit inverse of the cores (Gauss-Jordan)

@@ -179,9 +179,7 @@ int build_plan(hm_sys_s* sys) {
   P.core_total = P.piv_total = P.comp_total = P.tb_total = 0;
   P.qr_scratch = 0;
   P.nrank = 0;
-  std::vector<int64_t> level_bo_begin(P.nlevels, 0), level_bo_end(P.nlevels, 0);
   for (int l = P.nlevels - 1; l >= 0; --l) {
-    level_bo_begin[l] = P.bo_total;
     for (int q : P.level_fronts[l]) {
       FrontGeom& g = P.fg[q];
       if (g.np <= o.n_c) continue;
@@ -253,7 +251,6 @@ int build_plan(hm_sys_s* sys) {
       g.hodlr = (int)P.hf.size();
       P.hf.push_back(std::move(h));
     }
-    level_bo_end[l] = P.bo_total;
   }
 
   // ---------------------------------------------------------------- capacity checks
@@ -389,7 +386,7 @@ int build_plan(hm_sys_s* sys) {
     std::vector<QrTask> qy, qz;
     std::vector<SvdTask> sv;
     std::vector<PotrfTask> lpot;
-    std::vector<CholSolveTask> lsol;
+    std::vector<GemmTask> lxg;
     std::vector<CholInvTask> linv;
     std::vector<GemmTask> sT, sP, sF;
     std::vector<BdlrTask> bd;
@@ -474,7 +471,10 @@ int build_plan(hm_sys_s* sys) {
         void* Lq = at(F, fo + lo + (int64_t)lo * nh, es);
         lpot.push_back(PotrfTask{Lq, n, nh, q, 0});
         lp.leaf_maxn = std::max(lp.leaf_maxn, n);
-        if (h.xc > 0) lsol.push_back(CholSolveTask{Lq, at(X, h.bo_off + lo, es), n, nh, np, h.xc});
+        // X (leaf rows) = K_leaf^{-1} Bo (leaf rows), once the explicit inverse is formed
+        if (h.xc > 0)
+          lxg.push_back(gemm(Lq, nh, 0, at(Bo, h.bo_off + lo, es), np, 0, at(X, h.bo_off + lo, es), np, n, h.xc,
+                             n, 1.0, 0.0));
         linv.push_back(CholInvTask{Lq, nullptr, n, nh, 0, 0, nullptr, 0, 0});
         fbytes += es * (double)n * n;
       }
@@ -489,11 +489,9 @@ int build_plan(hm_sys_s* sys) {
     lp.svd = tb.add(sv);
     lp.formU = tb.add_gemm(gu);
     lp.formV = tb.add_gemm(gv);
-    lp.x_copy_off = level_bo_begin[l];
-    lp.x_copy_len = level_bo_end[l] - level_bo_begin[l];
     lp.leaf_potrf = tb.add(lpot);
-    lp.leaf_solve = tb.add(lsol);
     lp.leaf_inv = tb.add(linv);
+    lp.leaf_x = tb.add_gemm(lxg);
     // Woodbury levels, bottom-up (height 1 = parents of the leaves)
     for (int ht = 1; ht <= maxL; ++ht) {
       std::vector<GemmTask> pre, sg, upd, gmv;
