@@ -116,7 +116,7 @@ struct OmegaTask {
 // Gauss-Jordan sweeps: F_pp^{-1}, K^T, K and U_p in place.
 struct SweepTask {
   void* F;
-  int np, nhat, front, pad;
+  int np, nhat, front, ld;  // ld: leading dimension of F (0: nhat)
 };
 
 struct CoreLuTask {

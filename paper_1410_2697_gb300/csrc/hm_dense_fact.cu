@@ -435,10 +435,10 @@ __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict
   __shared__ T colk[2][16 * TT];
   __shared__ T rowk[2][16 * TT];
   const SweepTask t = tasks[blockIdx.x];
-  const int nh = t.nhat, np = t.np, ls = nh + 1;
+  const int nh = t.nhat, np = t.np, ls = nh + 1, ldf = t.ld > 0 ? t.ld : nh;
   T* S = reinterpret_cast<T*>(smem_raw);  // nh x nh staging, ld nh + 1
   T* F = (T*)t.F;
-  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) S[e % nh + (e / nh) * ls] = F[e];
+  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) S[e % nh + (e / nh) * ls] = F[e % nh + (size_t)(e / nh) * ldf];
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T a[TT][TT];
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict
       if (r < nh && c < nh) S[r + c * ls] = (r < np && c < np) ? -a[i][j] : a[i][j];
     }
   __syncthreads();
-  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) F[e] = S[e % nh + (e / nh) * ls];
+  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) F[e % nh + (size_t)(e / nh) * ldf] = S[e % nh + (e / nh) * ls];
 }
 
 template <typename T>

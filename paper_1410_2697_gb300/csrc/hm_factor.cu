@@ -207,12 +207,8 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
       run_gemm<T>(sys, lp.formV, base, PC_GEMM_FACTOR);
       debug_stage<T>(sys, "formUV", l);
       {
-        ProfScope ps(ctx, PC_POTRF, lp.leaf_potrf.work);
-        launch_potrf<T>(lp.leaf_potrf.dev(base), lp.leaf_potrf.count, lp.leaf_maxn, sys->d_err, s);
-      }
-      {
-        ProfScope ps(ctx, PC_INVERSE, lp.leaf_inv.work);
-        launch_chol_inverse<T>(lp.leaf_inv.dev(base), lp.leaf_inv.count, lp.leaf_maxn, s);
+        ProfScope ps(ctx, PC_INVERSE, lp.leaf_sweep.work);
+        launch_front_sweep<T>(lp.leaf_sweep.dev(base), lp.leaf_sweep.count, lp.leaf_maxn, sys->d_err, s);
       }
       run_gemm<T>(sys, lp.leaf_x, base, PC_GEMM_FACTOR);  // X = D^{-1} Bo on the leaf rows
       debug_stage<T>(sys, "leaves", l);

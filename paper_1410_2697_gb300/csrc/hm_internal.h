@@ -305,9 +305,8 @@ struct LevelFactorPlan {
   int svd_maxk = 0;
   Span<BdlrTask> bdlr;         // BDLR compressor: every off-diagonal block of the level
   int bdlr_maxnh = 0, bdlr_maxcap = 0;
-  Span<PotrfTask> leaf_potrf;
   int leaf_maxn = 0;
-  Span<CholInvTask> leaf_inv;  // explicit leaf inverses (factorization and apply)
+  Span<SweepTask> leaf_sweep;  // explicit leaf inverses (factorization and apply), one sweep each
   GemmBatch leaf_x;            // X (leaf rows) = K_leaf^{-1} Bo (leaf rows): the first Woodbury sweep
   struct Height {
     GemmBatch pre;            // core diagonal blocks and t = Z^T X_anc

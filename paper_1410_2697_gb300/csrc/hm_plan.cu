@@ -385,9 +385,8 @@ int build_plan(hm_sys_s* sys) {
     std::vector<GemmTask> gy, gz, gu, gv;
     std::vector<QrTask> qy, qz;
     std::vector<SvdTask> sv;
-    std::vector<PotrfTask> lpot;
+    std::vector<SweepTask> lsw;
     std::vector<GemmTask> lxg;
-    std::vector<CholInvTask> linv;
     std::vector<GemmTask> sT, sP, sF;
     std::vector<BdlrTask> bd;
     const bool bdlr = o.compressor == HM_COMP_BDLR;
@@ -469,13 +468,12 @@ int build_plan(hm_sys_s* sys) {
       for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
         const int lo = h.leaf_lo[li], n = h.leaf_hi[li] - lo;
         void* Lq = at(F, fo + lo + (int64_t)lo * nh, es);
-        lpot.push_back(PotrfTask{Lq, n, nh, q, 0});
+        lsw.push_back(SweepTask{Lq, n, n, q, nh});  // the leaf's inverse in one sweep kernel
         lp.leaf_maxn = std::max(lp.leaf_maxn, n);
         // X (leaf rows) = K_leaf^{-1} Bo (leaf rows), once the explicit inverse is formed
         if (h.xc > 0)
           lxg.push_back(gemm(Lq, nh, 0, at(Bo, h.bo_off + lo, es), np, 0, at(X, h.bo_off + lo, es), np, n, h.xc,
                              n, 1.0, 0.0));
-        linv.push_back(CholInvTask{Lq, nullptr, n, nh, 0, 0, nullptr, 0, 0});
         fbytes += es * (double)n * n;
       }
     }
@@ -489,8 +487,7 @@ int build_plan(hm_sys_s* sys) {
     lp.svd = tb.add(sv);
     lp.formU = tb.add_gemm(gu);
     lp.formV = tb.add_gemm(gv);
-    lp.leaf_potrf = tb.add(lpot);
-    lp.leaf_inv = tb.add(linv);
+    lp.leaf_sweep = tb.add(lsw);
     lp.leaf_x = tb.add_gemm(lxg);
     // Woodbury levels, bottom-up (height 1 = parents of the leaves)
     for (int ht = 1; ht <= maxL; ++ht) {
