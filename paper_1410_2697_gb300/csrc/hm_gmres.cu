@@ -19,9 +19,10 @@ namespace hm {
 constexpr int kDotThreads = 256;
 
 // y[r] = A x[r]  (b == nullptr)   or   y[r] = b[r] - A x[r]; rows in new numbering.
-// One thread per row and four right-hand sides (blockIdx.y selects the group of four):
-// the row's column indices and values are read once and reused for the four products.
-constexpr int kSpmvR = 4;
+// One thread per row and up to kSpmvR right-hand sides (blockIdx.y selects the group):
+// the row's column indices and values are read once and reused for every product, and
+// two nonzeros are in flight per iteration.
+constexpr int kSpmvR = 16;
 
 template <typename XT>
 __global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rowptr,
@@ -35,8 +36,11 @@ __global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rowptr
   const int r0 = blockIdx.y * kSpmvR;
   const int nr = min(kSpmvR, nrhs - r0);
   const int64_t kb = rowptr[i], ke = rowptr[i + 1];
-  double s[kSpmvR] = {0.0, 0.0, 0.0, 0.0};
+  double s[kSpmvR];
+#pragma unroll
+  for (int q = 0; q < kSpmvR; ++q) s[q] = 0.0;
   const XT* x0 = x + (int64_t)r0 * ldx;
+#pragma unroll 2
   for (int64_t k = kb; k < ke; ++k) {
     const int c = col[k];
     const double v = val[k];
@@ -86,6 +90,7 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int64_t* __restrict__ row
 #pragma unroll
   for (int q = 0; q < kSpmvDF; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
   const bool vec = nr == kSpmvDF && (nrhs & 3) == 0;
+#pragma unroll 2
   for (int64_t k = kb; k < ke; ++k) {
     const float2 a = val2[k];
     const float* zc = z + (int64_t)col[k] * nrhs + r0;
@@ -162,48 +167,197 @@ __global__ void __launch_bounds__(256) k_spmv_rm(const int64_t* __restrict__ row
 // Row chunks: every vector kernel runs on grid (nchunks, nrhs); chunk c covers rows
 // [crow[c], crow[c+1]) of one block cseg[c] (chunks never straddle blocks), so a CTA
 // serves one GMRES instance inst = r * nseg + cseg[c] and caches its scalars.
-
-// part[(r*nchunks + c)*stride + i] = sum over chunk c of V_i[r] . w[r], i < nvec.
 // V_i[r] starts at V + (i*nrhs + r)*n.
-__global__ void __launch_bounds__(kDotThreads) k_multidot(const double* __restrict__ V,
-                                                          const double* __restrict__ w, int n,
-                                                          int nrhs, int nvec, int stride,
-                                                          const int* __restrict__ crow,
-                                                          double* __restrict__ part) {
-  __shared__ double red[32];
-  const int r = blockIdx.y, nchunks = gridDim.x, c = blockIdx.x;
+
+// out[i] = d[i] summed over the CTA, i < cnt: warp shuffles, then the warps' partials
+// added in a fixed order by thread i (one barrier pair for all cnt sums; deterministic).
+template <int NV>
+__device__ __forceinline__ void block_store_sums(const double (&d)[NV], int cnt, double* red,
+                                                 double* __restrict__ out) {
+  constexpr int kWarps = kDotThreads / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (i < cnt) {
+      const double v = warp_sum(d[i]);
+      if (lane == 0) red[wid * NV + i] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) t += red[q * NV + threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();  // red is reused by the next group
+}
+
+// Rows a thread keeps in flight in the chunk kernels: a thread issues the loads of R rows
+// (R kDotThreads apart) before it uses any, so that enough bytes are in flight per SM to
+// cover the DRAM latency.  The vector count NV is a template constant and every one of the
+// NV vectors is read: a load guarded by a runtime count inside an unrolled loop may be
+// issued whatever the guard says, so the kernels never see more vectors than they use.
+template <int NV>
+struct ChunkRows {
+  static constexpr int v = NV == 1 ? 8 : NV <= 4 ? 4 : 2;
+};
+
+// part[(r*nchunks + c)*stride + i0 + i] = sum over chunk c of V_{i0+i}[r] . w[r], i < NV:
+// w is read once, the NV products of a row are independent loads accumulated in registers
+// (rows in the plain strided order), one block reduction for the NV sums.
+template <int NV>
+__global__ void __launch_bounds__(kDotThreads, NV <= 4 ? 3 : 2) k_multidot(const double* __restrict__ V,
+                                                                           const double* __restrict__ w,
+                                                                           int n, int nrhs, int i0, int stride,
+                                                                           const int* __restrict__ crow,
+                                                                           double* __restrict__ part) {
+  constexpr int R = ChunkRows<NV>::v;
+  __shared__ double red[kDotThreads / 32 * NV];
+  const int r = blockIdx.y, c = blockIdx.x;
   const int b = crow[c], e = crow[c + 1];
   const double* wr = w + (int64_t)r * n;
-  for (int i = 0; i < nvec; ++i) {
-    const double* vi = V + ((int64_t)i * nrhs + r) * n;
-    double s = 0.0;
-    for (int k = b + threadIdx.x; k < e; k += blockDim.x) s = fma(vi[k], wr[k], s);
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part[((int64_t)r * nchunks + c) * stride + i] = s;
+  const int64_t vs = (int64_t)nrhs * n;
+  const double* v0 = V + (int64_t)i0 * vs + (int64_t)r * n;
+  double d[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) d[i] = 0.0;
+  for (int k0 = b + threadIdx.x; k0 < e; k0 += kDotThreads * R) {
+    double x[R], v[R][NV];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int k = k0 + j * kDotThreads;
+      const bool in = k < e;
+      x[j] = in ? wr[k] : 0.0;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[j][i] = in ? v0[i * vs + k] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) d[i] = fma(v[j][i], x[j], d[i]);
+  }
+  block_store_sums<NV>(d, NV, red, part + ((int64_t)r * gridDim.x + c) * stride + i0);
+}
+
+// Fused Gram-Schmidt step over exactly NV basis vectors: over the chunk's rows
+// w[r] -= sum_i V_i[r] coef_i, then the chunk's partial sums of the updated rows --
+// V_i[r] . w[r] for i < NV (norm == 0: the next CGS pass's projections) or w[r] . w[r]
+// (norm == 1: the squared norm that normalises the new basis vector) ->
+// part[(r*nchunks + c)*pstride + i].
+template <int NV>
+__global__ void __launch_bounds__(kDotThreads, NV <= 4 ? 3 : 2) k_gs_update_dots(
+    const double* __restrict__ V, double* __restrict__ w, int n, int nrhs, int stride,
+    const double* __restrict__ coef, const int* __restrict__ crow, const int* __restrict__ cseg, int nseg,
+    int norm, int pstride, double* __restrict__ part) {
+  constexpr int R = ChunkRows<NV>::v;
+  __shared__ double cs[NV];
+  __shared__ double red[kDotThreads / 32 * NV];
+  const int r = blockIdx.y, c = blockIdx.x;
+  const int inst = r * nseg + cseg[c];
+  if (threadIdx.x < NV) cs[threadIdx.x] = coef[(int64_t)inst * stride + threadIdx.x];
+  __syncthreads();
+  double* wr = w + (int64_t)r * n;
+  const double* v0 = V + (int64_t)r * n;
+  const int64_t vs = (int64_t)nrhs * n;
+  const int e = crow[c + 1];
+  double d[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) d[i] = 0.0;
+  for (int k0 = crow[c] + threadIdx.x; k0 < e; k0 += kDotThreads * R) {
+    double vk[R][NV], sv[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int k = k0 + j * kDotThreads;
+      const bool in = k < e;
+      sv[j] = in ? wr[k] : 0.0;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) vk[j][i] = in ? v0[i * vs + k] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int k = k0 + j * kDotThreads;
+      double t = sv[j];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) t -= vk[j][i] * cs[i];
+      if (k < e) wr[k] = t;
+      if (norm) {
+        d[0] = fma(t, t, d[0]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) d[i] = fma(vk[j][i], t, d[i]);
+      }
+    }
+  }
+  block_store_sums<NV>(d, norm ? 1 : NV, red, part + ((int64_t)r * gridDim.x + c) * pstride);
+}
+
+// The fused step covers bases of up to kFusedGs vectors; wider ones take k_gs_update
+// followed by k_multidot.
+constexpr int kFusedGs = 8;
+
+#define HM_NV_SWITCH(cnt, CALL) \
+  switch (cnt) {                \
+    case 1: CALL(1); break;     \
+    case 2: CALL(2); break;     \
+    case 3: CALL(3); break;     \
+    case 4: CALL(4); break;     \
+    case 5: CALL(5); break;     \
+    case 6: CALL(6); break;     \
+    case 7: CALL(7); break;     \
+    default: CALL(8); break;    \
+  }
+
+// Partial dot products with all nvec basis vectors: groups of at most eight vectors,
+// each group one launch of the kernel instantiated for its exact size.
+static void launch_multidot(const double* V, const double* w, int n, int nrhs, int nvec, int stride,
+                            const int* crow, double* part, int nchunks, cudaStream_t s) {
+  const dim3 g((unsigned)nchunks, (unsigned)nrhs);
+  for (int i0 = 0; i0 < nvec; i0 += 8) {
+    const int cnt = std::min(8, nvec - i0);
+#define HM_MD(NV) k_multidot<NV><<<g, kDotThreads, 0, s>>>(V, w, n, nrhs, i0, stride, crow, part)
+    HM_NV_SWITCH(cnt, HM_MD)
+#undef HM_MD
   }
 }
 
-// h[inst*stride + i] (=|+=) sum of the block's chunk partials (fixed chunk order)
+// nvec in [1, kFusedGs]
+static void launch_gs_update_dots(const double* V, double* w, int n, int nrhs, int nvec, int stride,
+                                  const double* coef, const int* crow, const int* cseg, int nseg, int norm,
+                                  int pstride, double* part, int nchunks, cudaStream_t s) {
+  const dim3 g((unsigned)nchunks, (unsigned)nrhs);
+#define HM_GSU(NV) \
+  k_gs_update_dots<NV><<<g, kDotThreads, 0, s>>>(V, w, n, nrhs, stride, coef, crow, cseg, nseg, norm, pstride, part)
+  HM_NV_SWITCH(nvec, HM_GSU)
+#undef HM_GSU
+}
+#undef HM_NV_SWITCH
+
+// h[inst*stride + i] = sum of the block's chunk partials, and h_acc[inst*stride + i] += the
+// same sum when h_acc is given.  One warp per output: lane l adds chunks l, l+32, ... in
+// order, then a fixed butterfly across the lanes (deterministic; the chunk loads of a
+// lane are independent, so the sum costs a few L2 round trips, not one per chunk).
 __global__ void k_reduce_dots(const double* __restrict__ part, int nchunks, const int* __restrict__ cptr,
                               int nseg, int ninst, int nvec, int stride, double* __restrict__ h,
-                              int accumulate) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ninst * nvec) return;
+                              double* __restrict__ h_acc) {
+  const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= ninst * nvec) return;  // uniform per warp
   const int inst = e / nvec, i = e % nvec;
   const int r = inst / nseg, sg = inst % nseg;
   double s = 0.0;
-  for (int c = cptr[sg]; c < cptr[sg + 1]; ++c) s += part[((int64_t)r * nchunks + c) * stride + i];
-  if (accumulate) h[(int64_t)inst * stride + i] += s;
-  else h[(int64_t)inst * stride + i] = s;
+  for (int c = cptr[sg] + lane; c < cptr[sg + 1]; c += 32) s += part[((int64_t)r * nchunks + c) * stride + i];
+  s = warp_sum(s);
+  if (lane == 0) {
+    h[(int64_t)inst * stride + i] = s;
+    if (h_acc) h_acc[(int64_t)inst * stride + i] += s;
+  }
 }
 
-// a[inst*stride + i] += b[inst*stride + i], i < nvec
-__global__ void k_add_cols(double* __restrict__ a, const double* __restrict__ b, int ninst, int nvec,
-                           int stride) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ninst * nvec) return;
-  const int inst = e / nvec, i = e % nvec;
-  a[(int64_t)inst * stride + i] += b[(int64_t)inst * stride + i];
+static void launch_reduce_dots(const double* part, int nchunks, const int* cptr, int nseg, int ninst, int nvec,
+                               int stride, double* h, double* h_acc, cudaStream_t s) {
+  const int64_t threads = (int64_t)ninst * nvec * 32;
+  k_reduce_dots<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(part, nchunks, cptr, nseg, ninst, nvec, stride,
+                                                                  h, h_acc);
 }
 
 // w[r] -= sum_{i < nvec} V_i[r] * coef[inst*stride + i]
@@ -223,9 +377,11 @@ __global__ void k_gs_update(const double* __restrict__ V, double* __restrict__ w
   }
 }
 
-// dst[r] = src[r] / ||.||, with ||.||^2 = ss[inst*stride] (0 if the norm is 0)
-__global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, int n, int nrhs,
-                        const double* __restrict__ ss, int stride, const int* __restrict__ crow,
+// dst[r] = src[r] / ||.||, with ||.||^2 = ss[inst*stride] (0 if the norm is 0); the same
+// values also go to cast (the factor precision: the next preconditioner input).
+template <typename T>
+__global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, T* __restrict__ cast, int n,
+                        int nrhs, const double* __restrict__ ss, int stride, const int* __restrict__ crow,
                         const int* __restrict__ cseg, int nseg) {
   const int r = blockIdx.y, c = blockIdx.x;
   const int inst = r * nseg + cseg[c];
@@ -233,7 +389,13 @@ __global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst
   const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
   const double* sr = src + (int64_t)r * n;
   double* dr = dst + (int64_t)r * n;
-  for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) dr[k] = nr > 0.0 ? sr[k] * inv : 0.0;
+  T* cr = cast + (int64_t)r * n;
+  const int e = crow[c + 1];
+  for (int k = crow[c] + threadIdx.x; k < e; k += blockDim.x) {
+    const double t = nr > 0.0 ? sr[k] * inv : 0.0;
+    dr[k] = t;
+    cr[k] = (T)t;
+  }
 }
 
 // Givens step for column j (thread per instance): H column = h (h1 + h2), H[j+1,j] = ||w||.
@@ -293,41 +455,86 @@ __global__ void k_backsolve(const double* __restrict__ H, const double* __restri
   for (int i = L; i < m; ++i) yr[i] = 0.0;
 }
 
-// x[r] += sum_{j < len[inst]} Z_j[r] y[inst][j]   (Z_j row-major: element (k, r) at k nrhs + r)
+// x[r] += sum_{j < len[inst]} Z_j[r] y[inst][j]   (Z_j row-major: element (k, r) at k nrhs + r).
+// A tile of rt = min(256, 1024 / nrhs) rows x every right-hand side (at most 1024 values,
+// kUxVals per thread) is read along rows (coalesced) and transposed through shared memory
+// into the column-major x.  A thread issues the loads of its values together (j outer),
+// and reads its x values before it writes any; a chunk's tiles are spread over gridDim.y
+// CTAs.
+constexpr int kUxVals = 4;
 template <typename ZT>
 __global__ void __launch_bounds__(256) k_update_x(double* __restrict__ x, const ZT* __restrict__ Z,
                                                   const double* __restrict__ y, const int* __restrict__ len, int n,
                                                   int nrhs, int m, const int* __restrict__ crow,
                                                   const int* __restrict__ cseg, int nseg) {
-  // x_r += sum_j y_{r,j} Z_j[:, r] on rows [crow[c], crow[c+1]) of one block; Z_j is
-  // row-major (element (i, r) at i nrhs + r): a tile of 64 rows x every right-hand side
-  // is read along rows (coalesced), then written to the column-major x through shared
-  // memory
-  __shared__ double tile[64][65];
+  __shared__ double tile[1024 + 256];  // rt x (nrhs + 1)
   const int c = blockIdx.x, seg = cseg[c];
-  for (int k0 = crow[c]; k0 < crow[c + 1]; k0 += 64) {
-    const int rows = min(64, crow[c + 1] - k0), cnt = rows * nrhs;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int kk = e / nrhs, r = e - kk * nrhs;
-      const int inst = r * nseg + seg, L = len[inst];
-      const ZT* zp = Z + (int64_t)(k0 + kk) * nrhs + r;
-      const double* yp = y + (int64_t)inst * m;
-      double s = 0.0;
-      for (int j = 0; j < L; ++j) s = fma((double)zp[(int64_t)j * n * nrhs], yp[j], s);
-      tile[kk][r] = s;
+  const int rt = min(256, 1024 / nrhs), ld = nrhs + 1;
+  const int64_t zs = (int64_t)n * nrhs;
+  for (int k0 = crow[c] + rt * blockIdx.y; k0 < crow[c + 1]; k0 += rt * gridDim.y) {
+    const int rows = min(rt, crow[c + 1] - k0), cnt = rows * nrhs;
+    double acc[kUxVals];
+    const ZT* zp[kUxVals];
+    const double* yp[kUxVals];
+    int L[kUxVals], lmax = 0;
+#pragma unroll
+    for (int q = 0; q < kUxVals; ++q) {
+      const int e = threadIdx.x + q * 256;
+      acc[q] = 0.0;
+      L[q] = 0;
+      zp[q] = Z;
+      yp[q] = y;
+      if (e < cnt) {
+        const int kk = e / nrhs, r = e - kk * nrhs;
+        const int inst = r * nseg + seg;
+        L[q] = len[inst];
+        zp[q] = Z + (int64_t)(k0 + kk) * nrhs + r;
+        yp[q] = y + (int64_t)inst * m;
+        lmax = max(lmax, L[q]);
+      }
+    }
+    // (every address below stays inside Z and y for j < lmax <= m, whatever q)
+    for (int j = 0; j < lmax; ++j) {
+#pragma unroll
+      for (int q = 0; q < kUxVals; ++q)
+        if (j < L[q]) acc[q] = fma((double)zp[q][j * zs], yp[q][j], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kUxVals; ++q) {
+      const int e = threadIdx.x + q * 256;
+      if (e < cnt) {
+        const int kk = e / nrhs, r = e - kk * nrhs;
+        tile[kk * ld + r] = acc[q];
+      }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int r = e / rows, kk = e - r * rows;
-      x[(int64_t)r * n + k0 + kk] += tile[kk][r];
+    double xv[kUxVals];
+#pragma unroll
+    for (int q = 0; q < kUxVals; ++q) {
+      const int e = threadIdx.x + q * 256;
+      xv[q] = 0.0;
+      if (e < cnt) {
+        const int r = e / rows, kk = e - r * rows;
+        xv[q] = x[(int64_t)r * n + k0 + kk];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kUxVals; ++q) {
+      const int e = threadIdx.x + q * 256;
+      if (e < cnt) {
+        const int r = e / rows, kk = e - r * rows;
+        x[(int64_t)r * n + k0 + kk] = xv[q] + tile[kk * ld + r];
+      }
     }
     __syncthreads();
   }
 }
 
-// Start of a cycle: V_0 = r / beta (inactive instances get 0)
-__global__ void k_cycle_init(const double* __restrict__ rvec, double* __restrict__ V0, int n, int nrhs,
-                             const double* __restrict__ ss, const int* __restrict__ active,
+// Start of a cycle: V_0 = r / beta (inactive instances get 0), also cast to the factor
+// precision (the first preconditioner input of the cycle).
+template <typename T>
+__global__ void k_cycle_init(const double* __restrict__ rvec, double* __restrict__ V0, T* __restrict__ cast,
+                             int n, int nrhs, const double* __restrict__ ss, const int* __restrict__ active,
                              const int* __restrict__ crow, const int* __restrict__ cseg, int nseg) {
   const int r = blockIdx.y, c = blockIdx.x;
   const int inst = r * nseg + cseg[c];
@@ -336,7 +543,13 @@ __global__ void k_cycle_init(const double* __restrict__ rvec, double* __restrict
   const double inv = on ? 1.0 / beta : 0.0;
   const double* rr = rvec + (int64_t)r * n;
   double* vr = V0 + (int64_t)r * n;
-  for (int k = crow[c] + threadIdx.x; k < crow[c + 1]; k += blockDim.x) vr[k] = on ? rr[k] * inv : 0.0;
+  T* cr = cast + (int64_t)r * n;
+  const int e = crow[c + 1];
+  for (int k = crow[c] + threadIdx.x; k < e; k += blockDim.x) {
+    const double t = on ? rr[k] * inv : 0.0;
+    vr[k] = t;
+    cr[k] = (T)t;
+  }
 }
 
 __global__ void k_cycle_g(double* __restrict__ g, int* __restrict__ len, const double* __restrict__ ss,
@@ -365,7 +578,8 @@ static int ensure_workspace(hm_sys_s* sys, int nrhs, int m) {
   const int nseg = sys->nseg;
   const int64_t ninst = (int64_t)nrhs * nseg;
   const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
-  // row chunks: about two per SM over the whole vector, never straddling a block
+  // row chunks: about two per SM over the whole vector, never straddling a block (the
+  // vector kernels run one CTA per (chunk, right-hand side))
   const int64_t L = std::max<int64_t>(1024, (n + 2 * sys->ctx->num_sms - 1) / (2 * sys->ctx->num_sms));
   std::vector<int> crow(1, 0), cseg, cptr(1, 0);
   for (int sg = 0; sg < nseg; ++sg) {
@@ -416,10 +630,9 @@ static void sqnorm(hm_sys_s* sys, const double* v, double* ss, int stride, int n
   cudaStream_t s = sys->ctx->stream;
   const int ninst = nrhs * sys->nseg;
   ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * sys->n * nrhs, 8.0 * sys->n * nrhs}, 2);
-  k_multidot<<<dim3(G.nchunks, nrhs), kDotThreads, 0, s>>>(v, v, sys->n, nrhs, 1, stride, G.crow, G.part);
-  // with V = v and nvec = 1 the "basis" is v itself (stride of rhs = n)
-  k_reduce_dots<<<(ninst + 127) / 128, 128, 0, s>>>(G.part, G.nchunks, G.cptr, sys->nseg, ninst, 1, stride,
-                                                    ss, 0);
+  // with V = v and nvec = 1 the "basis" is v itself
+  launch_multidot(v, v, sys->n, nrhs, 1, stride, G.crow, G.part, G.nchunks, s);
+  launch_reduce_dots(G.part, G.nchunks, G.cptr, sys->nseg, ninst, 1, stride, ss, nullptr, s);
 }
 
 template <typename T>
@@ -466,18 +679,14 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
     for (int r = 0; r < ninst; ++r) active[r] = relres[r] > rtol ? 1 : 0;
     HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s));
     {
-      ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn}, 2);
-      k_cycle_init<<<vgrid, 256, 0, s>>>(G.r, G.V, n, nrhs, rss, d_active, G.crow, G.cseg, nseg);
+      ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, (16.0 + sizeof(T)) * nn}, 2);
+      k_cycle_init<T><<<vgrid, 256, 0, s>>>(G.r, G.V, (T*)G.wT, n, nrhs, rss, d_active, G.crow, G.cseg, nseg);
       k_cycle_g<<<(ninst + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, ninst);
     }
     int j = 0;
     for (; j < m && iters < max_iters; ++j) {
-      const double* Vj = G.V + (int64_t)j * nrhs * n;
       T* Zj = Z + (int64_t)j * nrhs * n;
-      {
-        ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, (8.0 + sizeof(T)) * nn});
-        launch_cast_to<T>(Vj, (T*)G.wT, nn, s);
-      }
+      // G.wT holds V_j in the factor precision (written with V_j by k_cycle_init / k_scale)
       HM_TRY(apply_impl_rowmajor(sys, nrhs, G.wT, Zj));  // Z_j row-major
       {
         ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs,
@@ -489,33 +698,49 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
           k_spmv_rm<T><<<dim3((n + 255) / 256, (nrhs + kSpmvRM - 1) / kSpmvRM), 256, 0, s>>>(
               sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs, Zj, G.w);
       }
+      // CGS2: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
       double* h1 = G.hv;
       double* h2 = G.hv + (int64_t)ninst * stride;
+      double* wss = G.hv + 2 * (int64_t)ninst * stride + 2 * ninst;  // ||w||^2 per instance
       const int nvec = j + 1;
-      for (int pass = 0; pass < 2; ++pass) {
-        double* h = pass == 0 ? h1 : h2;
+      {
+        ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
+        launch_multidot(G.V, G.w, n, nrhs, nvec, stride, G.crow, G.part, G.nchunks, s);
+        launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h1, nullptr, s);
+      }
+      if (nvec <= kFusedGs) {
+        {
+          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{4.0 * nvec * nn, 8.0 * (nvec + 2) * nn}, 2);
+          launch_gs_update_dots(G.V, G.w, n, nrhs, nvec, stride, h1, G.crow, G.cseg, nseg, 0, stride, G.part,
+                                G.nchunks, s);
+          launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h2, h1, s);  // h1 += h2
+        }
+        {
+          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * (nvec + 1) * nn, 8.0 * (nvec + 2) * nn}, 2);
+          launch_gs_update_dots(G.V, G.w, n, nrhs, nvec, stride, h2, G.crow, G.cseg, nseg, 1, 1, G.part,
+                                G.nchunks, s);
+          launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, 1, 1, wss, nullptr, s);
+        }
+      } else {
+        {
+          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
+          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h1, G.crow, G.cseg, nseg);
+        }
         {
           ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
-          k_multidot<<<dim3(G.nchunks, nrhs), kDotThreads, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, G.crow,
-                                                                   G.part);
-          k_reduce_dots<<<(ninst * nvec + 127) / 128, 128, 0, s>>>(G.part, G.nchunks, G.cptr, nseg, ninst, nvec,
-                                                                  stride, h, 0);
+          launch_multidot(G.V, G.w, n, nrhs, nvec, stride, G.crow, G.part, G.nchunks, s);
+          launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h2, h1, s);  // h1 += h2
         }
         {
           ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
-          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h, G.crow, G.cseg, nseg);
+          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h2, G.crow, G.cseg, nseg);
         }
+        sqnorm(sys, G.w, wss, 1, nrhs);
       }
       {
-        ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
-        k_add_cols<<<(ninst * nvec + 127) / 128, 128, 0, s>>>(h1, h2, ninst, nvec, stride);  // h1 += h2
-      }
-      double* wss = G.hv + 2 * (int64_t)ninst * stride + 2 * ninst;  // ||w||^2 per instance
-      sqnorm(sys, G.w, wss, 1, nrhs);
-      {
-        ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, 16.0 * nn});
-        k_scale<<<vgrid, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, n, nrhs, wss, 1, G.crow, G.cseg,
-                                      nseg);
+        ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, (16.0 + sizeof(T)) * nn});
+        k_scale<T><<<vgrid, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, (T*)G.wT, n, nrhs, wss, 1,
+                                         G.crow, G.cseg, nseg);
       }
       {
         ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
@@ -538,7 +763,8 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
     }
     {
       ProfScope ps(sys->ctx, PC_VECTOR, Work{2.0 * jend * nn, (16.0 + sizeof(T) * jend) * nn});
-      k_update_x<T><<<G.nchunks, 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m, G.crow, G.cseg, nseg);
+      const int split = std::max(1, (6 * sys->ctx->num_sms + G.nchunks - 1) / G.nchunks);
+      k_update_x<T><<<dim3(G.nchunks, split), 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m, G.crow, G.cseg, nseg);
     }
     {
       ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});
