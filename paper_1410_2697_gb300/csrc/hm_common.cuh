@@ -62,6 +62,10 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
+// 1/x correctly rounded (the value of the IEEE division 1/x) by the reciprocal intrinsic.
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+
 // Block-wide sum in fixed order (deterministic). `red` holds >= 32 entries.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {

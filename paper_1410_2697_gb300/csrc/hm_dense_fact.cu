@@ -216,116 +216,337 @@ __global__ void __launch_bounds__(256) k_core_lu(const CoreLuTask* __restrict__ 
 // =====================================================================================
 
 // P (k x k) = alpha * X Y (+ I if add_identity); all k x k column-major in shared memory
+// with leading dimension ld.  Thread (tx, ty) of a 16 x 16 layout computes the 4 x 4
+// entries (i0 + ty + 16 a, j0 + tx + 16 b) of each 64 x 64 tile of P, so every pair of
+// shared-memory loads feeds two FMAs instead of one (sums over p in order, as a plain
+// inner product).  With ld odd the 16 column reads of a row of Y fall in distinct banks.
 template <typename T>
 __device__ __forceinline__ void smem_gemm(T* __restrict__ P, const T* __restrict__ X, const T* __restrict__ Y,
-                                          int k, T alpha, bool add_identity) {
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e % k, j = e / k;
-    T s = T(0);
-    for (int p = 0; p < k; ++p) s = fma(X[i + p * k], Y[p + j * k], s);
-    P[e] = alpha * s + ((add_identity && i == j) ? T(1) : T(0));
-  }
+                                          int k, int ld, T alpha, bool add_identity) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int i0 = 0; i0 < k; i0 += 64)
+    for (int j0 = 0; j0 < k; j0 += 64) {
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+      for (int p = 0; p < k; ++p) {
+        T x[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int r = i0 + ty + 16 * a;
+          x[a] = r < k ? X[r + p * ld] : T(0);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = j0 + tx + 16 * b;
+          y[b] = c < k ? Y[p + c * ld] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int r = i0 + ty + 16 * a, c = j0 + tx + 16 * b;
+          if (r < k && c < k) P[r + c * ld] = alpha * acc[a][b] + ((add_identity && r == c) ? T(1) : T(0));
+        }
+    }
 }
+
+// Rows per lane in the Gauss-Jordan steps (k <= 32 kCoreRows).
+constexpr int kCoreRows = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_core_inv_schur(const CoreLuTask* __restrict__ tasks, int* err) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ T sval[8];
-  __shared__ int sidx[8];
-  __shared__ int piv_s;
   const CoreLuTask t = tasks[blockIdx.x];
-  const int k = t.k, n = 2 * k;
+  const int k = t.k, n = 2 * k, ld = k | 1;
   const T* C = (const T*)t.C;
   T* Ci = (T*)t.Cinv;
-  T* As = reinterpret_cast<T*>(smem_raw);  // k x k
-  T* Bs = As + k * k;                      // k x k
-  T* G = Bs + k * k;                       // [M | M^{-1}], k x 2k (ld k)
-  T* W = G + 2 * k * k;                    // k x k work
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e % k, j = e / k;
-    As[e] = C[(size_t)i + (size_t)j * n];
-    Bs[e] = C[(size_t)(k + i) + (size_t)(k + j) * n];
-  }
-  __syncthreads();
-  smem_gemm<T>(G, As, Bs, k, T(-1), true);  // M = I - A B
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[k * k + e] = (e % k == e / k) ? T(1) : T(0);
-  __syncthreads();
+  T* As = reinterpret_cast<T*>(smem_raw);  // k x k (ld)
+  T* Bs = As + ld * k;                     // k x k
+  T* G = Bs + ld * k;                      // [M | M^{-1}], k x 2k (ld)
+  T* W = G + 2 * ld * k;                   // k x k work
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wid; c < k; c += nw)
+    for (int i = lane; i < k; i += 32) {
+      As[i + c * ld] = C[(size_t)i + (size_t)c * n];
+      Bs[i + c * ld] = C[(size_t)(k + i) + (size_t)(k + c) * n];
+      G[i + (k + c) * ld] = i == c ? T(1) : T(0);
+    }
+  __syncthreads();
+  smem_gemm<T>(G, As, Bs, k, ld, T(-1), true);  // M = I - A B
+  __syncthreads();
+  // [M | I] -> [. | M^{-1}] by Gauss-Jordan with partial pivoting.  Each warp reads the
+  // multipliers (column j) and picks the pivot itself, and owns whole columns of the
+  // working set (c > j; column j is only read), so the swap and the elimination need no
+  // barrier and a step ends with one.
   for (int j = 0; j < k; ++j) {
-    // pivot: largest |M(i, j)|, i >= j (lowest row on ties), found by warp 0
-    if (wid == 0) {
-      T best = T(-1);
-      int bi = k;
-      for (int i = j + lane; i < k; i += 32) {
-        const T v = fabs(G[i + j * k]);
+    T m[kCoreRows];
+    T best = T(-1);
+    int bi = k;
+#pragma unroll
+    for (int r = 0; r < kCoreRows; ++r) {
+      const int i = lane + 32 * r;
+      m[r] = i < k ? G[i + j * ld] : T(0);
+      if (i >= j && i < k) {
+        const T v = fabs(m[r]);
         if (v > best) { best = v; bi = i; }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) {
-        if (!(best > T(0))) {
-          raise_error(err, HM_ERR_BREAKDOWN, t.front, j);
-          bi = j;
-        }
-        piv_s = bi;
-        t.piv[j] = bi;
-      }
     }
-    __syncthreads();
-    const int p = piv_s;
-    if (p != j)
-      for (int c = j + threadIdx.x; c < 2 * k; c += blockDim.x) {
-        const T a = G[j + c * k];
-        G[j + c * k] = G[p + c * k];
-        G[p + c * k] = a;
-      }
-    __syncthreads();
-    T d = G[j + j * k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {  // largest |M(i, j)|, i >= j, lowest row on ties
+      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    const bool ok = best > T(0);
+    const int p = ok ? bi : j;
+    if (threadIdx.x == 0) {
+      if (!ok) raise_error(err, HM_ERR_BREAKDOWN, t.front, j);
+      t.piv[j] = p;
+    }
+    T d = G[p + j * ld];
     if (d == T(0)) d = T(1);
     const T inv = T(1) / d;
-    // multipliers of the pivot column (W's first column), then a warp per column
-    for (int i = threadIdx.x; i < k; i += blockDim.x) W[i] = (i == j) ? T(0) : G[i + j * k];
-    __syncthreads();
-    for (int c = j + wid; c < 2 * k; c += nw) {
-      const T mjc = G[j + c * k] * inv;
+    const T mjj = G[j + j * ld];  // the multiplier of row p after the swap
+    for (int c = j + 1 + wid; c < 2 * k; c += nw) {
+      const T mjc = G[p + c * ld] * inv;  // new pivot row (old row p), scaled
+      const T rj = G[j + c * ld];         // old row j, moving to row p
       __syncwarp();
-      if (lane == 0) G[j + c * k] = mjc;
-      if (mjc != T(0))
-        for (int i = lane; i < k; i += 32)
-          if (i != j) G[i + c * k] -= W[i] * mjc;
+#pragma unroll
+      for (int r = 0; r < kCoreRows; ++r) {
+        const int i = lane + 32 * r;
+        if (i < k) {
+          T v;
+          if (i == j) v = mjc;
+          else if (i == p) v = rj - mjj * mjc;
+          else v = G[i + c * ld] - m[r] * mjc;
+          G[i + c * ld] = v;
+        }
+      }
     }
     __syncthreads();
   }
-  const T* Mi = G + k * k;
+  const T* Mi = G + ld * k;
   // X21 = M^{-1}; X11 = -B M^{-1} (into W); X22 = -M^{-1} A (into G's first half)
-  smem_gemm<T>(W, Bs, Mi, k, T(-1), false);
-  smem_gemm<T>(G, Mi, As, k, T(-1), false);
+  smem_gemm<T>(W, Bs, Mi, k, ld, T(-1), false);
+  smem_gemm<T>(G, Mi, As, k, ld, T(-1), false);
   __syncthreads();
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e % k, j = e / k;
-    Ci[(size_t)i + (size_t)j * n] = W[e];                  // X11
-    Ci[(size_t)(k + i) + (size_t)j * n] = Mi[e];           // X21
-    Ci[(size_t)(k + i) + (size_t)(k + j) * n] = G[e];      // X22
-  }
+  for (int c = wid; c < k; c += nw)
+    for (int i = lane; i < k; i += 32) {
+      Ci[(size_t)i + (size_t)c * n] = W[i + c * ld];                  // X11
+      Ci[(size_t)(k + i) + (size_t)c * n] = Mi[i + c * ld];           // X21
+      Ci[(size_t)(k + i) + (size_t)(k + c) * n] = G[i + c * ld];      // X22
+    }
   // X12 = I - X11 A (into Bs, which is no longer needed)
-  smem_gemm<T>(Bs, W, As, k, T(-1), true);
+  smem_gemm<T>(Bs, W, As, k, ld, T(-1), true);
   __syncthreads();
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e % k, j = e / k;
-    Ci[(size_t)i + (size_t)(k + j) * n] = Bs[e];           // X12
+  for (int c = wid; c < k; c += nw)
+    for (int i = lane; i < k; i += 32) Ci[(size_t)i + (size_t)(k + c) * n] = Bs[i + c * ld];  // X12
+}
+
+// P (k x k) = alpha * X Y (+ I if add_identity), k <= 16 RA, column-major in shared memory
+// (ld): thread (tx, ty) of a 16 x 16 layout computes the RA x RA entries
+// (ty + 16 a, tx + 16 b), sums over p in order.
+template <typename T, int RA>
+__device__ __forceinline__ void smem_gemm_r(T* __restrict__ P, const T* __restrict__ X, const T* __restrict__ Y,
+                                            int k, int ld, T alpha, bool add_identity) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[RA][RA];
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < RA; ++b) acc[a][b] = T(0);
+  for (int p = 0; p < k; ++p) {
+    T x[RA], y[RA];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int r = ty + 16 * a;
+      x[a] = r < k ? X[r + p * ld] : T(0);
+    }
+#pragma unroll
+    for (int b = 0; b < RA; ++b) {
+      const int c = tx + 16 * b;
+      y[b] = c < k ? Y[p + c * ld] : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int b = 0; b < RA; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
   }
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < RA; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      if (r < k && c < k) P[r + c * ld] = alpha * acc[a][b] + ((add_identity && r == c) ? T(1) : T(0));
+    }
+}
+
+// The same Woodbury core inverse for k <= 16 RA with [M | I] held in registers: thread
+// (tx, ty) keeps rows ty + 16 a and columns tx + 16 b of the k x 2k working matrix.
+// Gauss-Jordan with partial pivoting by row selection instead of row swaps: step j takes
+// as pivot the unused row p_j with the largest |M(p_j, j)| (lowest row on ties), scales
+// it and eliminates column j from every other row.  The row operations E then satisfy
+// E M = Pi with Pi(p_j, j) = 1, so row j of M^{-1} = Pi^T E is row p_j of the right half.
+// A step costs two barriers (the candidates of column j, then the pivot row) and RA x 2RA
+// FMAs per thread; the multipliers and the pivot row go through double-buffered shared
+// memory.
+template <typename T, int RA>
+__global__ void __launch_bounds__(256) k_core_inv_reg(const CoreLuTask* __restrict__ tasks, int* err) {
+  constexpr int RB = 2 * RA;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ T pcol[2][16 * RA];  // column j, by row
+  __shared__ T prow[2][32 * RA];  // pivot row, by column
+  __shared__ T cabs[2][16], cval[2][16];
+  __shared__ int cidx[2][16];
+  __shared__ int invp[16 * RA];
+  const CoreLuTask t = tasks[blockIdx.x];
+  const int k = t.k, n = 2 * k, ld = k | 1;
+  const T* C = (const T*)t.C;
+  T* Ci = (T*)t.Cinv;
+  T* As = reinterpret_cast<T*>(smem_raw);  // k x k (ld)
+  T* Bs = As + ld * k;
+  T* Mi = Bs + ld * k;                     // M, then M^{-1}
+  T* W = Mi + ld * k;
+  T* P2 = W + ld * k;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int c = wid; c < k; c += nw)
+    for (int i = lane; i < k; i += 32) {
+      As[i + c * ld] = C[(size_t)i + (size_t)c * n];
+      Bs[i + c * ld] = C[(size_t)(k + i) + (size_t)(k + c) * n];
+    }
+  __syncthreads();
+  smem_gemm_r<T, RA>(Mi, As, Bs, k, ld, T(-1), true);  // M = I - A B
+  __syncthreads();
+  T g[RA][RB];
+  bool used[RA];
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    used[a] = false;
+    const int r = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      const int c = tx + 16 * b;
+      g[a][b] = r >= k ? T(0) : c < k ? Mi[r + c * ld] : (c - k == r ? T(1) : T(0));
+    }
+  }
+  // pivot column j = 16 JB + jt: JB is a compile-time constant of the unrolled loop, so
+  // the owners of column j address their registers statically
+#pragma unroll
+  for (int JB = 0; JB < RA; ++JB) {
+    for (int jt = 0; jt < 16; ++jt) {
+      const int j = 16 * JB + jt;
+      if (j >= k) break;  // uniform over the block
+      const int buf = j & 1;
+      if (tx == jt) {
+        T best = T(-1), bval = T(0);
+        int bi = k;
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+          const int r = ty + 16 * a;
+          if (r < k) {
+            const T v = g[a][JB];
+            pcol[buf][r] = v;
+            if (!used[a] && fabs(v) > best) { best = fabs(v); bi = r; bval = v; }
+          }
+        }
+        cabs[buf][ty] = best;
+        cidx[buf][ty] = bi;
+        cval[buf][ty] = bval;
+      }
+      __syncthreads();
+      T best = T(-1), d = T(0);
+      int p = k;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const T v = cabs[buf][q];
+        const int i = cidx[buf][q];
+        if (v > best || (v == best && i < p)) { best = v; p = i; d = cval[buf][q]; }
+      }
+      if (threadIdx.x == 0) {
+        if (!(best > T(0))) raise_error(err, HM_ERR_BREAKDOWN, t.front, j);
+        t.piv[j] = p;
+        invp[p] = j;
+      }
+      if (d == T(0)) d = T(1);
+      const T inv = T(1) / d;
+      const int pa = p >> 4;
+      const bool prow_owner = ty == (p & 15);
+      if (prow_owner) {
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+          if (a == pa) {
+            used[a] = true;
+#pragma unroll
+            for (int b = 0; b < RB; ++b) prow[buf][tx + 16 * b] = g[a][b];
+          }
+      }
+      __syncthreads();
+      T pr[RB];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) pr[b] = prow[buf][tx + 16 * b] * inv;
+#pragma unroll
+      for (int a = 0; a < RA; ++a) {
+        const int r = ty + 16 * a;
+        const T mult = r < k ? pcol[buf][r] : T(0);
+        const bool isp = prow_owner && a == pa;
+#pragma unroll
+        for (int b = 0; b < RB; ++b) g[a][b] = isp ? pr[b] : g[a][b] - mult * pr[b];
+      }
+    }
+  }
+  __syncthreads();  // invp complete; M no longer read
+  // M^{-1}(invp[r], c) = E(r, c) for the right-half columns
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int r = ty + 16 * a;
+    if (r < k) {
+      const int row = invp[r];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int c = tx + 16 * b - k;
+        if (c >= 0 && c < k) Mi[row + c * ld] = g[a][b];
+      }
+    }
+  }
+  __syncthreads();
+  // X21 = M^{-1}; X11 = -B M^{-1} (W); X22 = -M^{-1} A (P2); X12 = I - X11 A (Bs)
+  smem_gemm_r<T, RA>(W, Bs, Mi, k, ld, T(-1), false);
+  smem_gemm_r<T, RA>(P2, Mi, As, k, ld, T(-1), false);
+  __syncthreads();
+  smem_gemm_r<T, RA>(Bs, W, As, k, ld, T(-1), true);
+  for (int c = wid; c < k; c += nw)
+    for (int i = lane; i < k; i += 32) {
+      Ci[(size_t)i + (size_t)c * n] = W[i + c * ld];              // X11
+      Ci[(size_t)(k + i) + (size_t)c * n] = Mi[i + c * ld];       // X21
+      Ci[(size_t)(k + i) + (size_t)(k + c) * n] = P2[i + c * ld];  // X22
+    }
+  __syncthreads();
+  for (int c = wid; c < k; c += nw)
+    for (int i = lane; i < k; i += 32) Ci[(size_t)i + (size_t)(k + c) * n] = Bs[i + c * ld];  // X12
 }
 
 template <typename T>
 void launch_core_lu(const CoreLuTask* tasks, int ntasks, int maxk, int max_smem, int* err,
                     cudaStream_t s) {
   if (ntasks <= 0) return;
-  const size_t schur = (size_t)5 * maxk * maxk * sizeof(T);
-  if (schur + 1024 <= (size_t)max_smem) {
+  const size_t schur = (size_t)5 * (maxk | 1) * maxk * sizeof(T);
+  if (maxk <= 64 && schur + 1024 <= (size_t)max_smem) {
+    if (maxk <= 16) k_core_inv_reg<T, 1><<<ntasks, 256, schur, s>>>(tasks, err);
+    else if (maxk <= 32) k_core_inv_reg<T, 2><<<ntasks, 256, schur, s>>>(tasks, err);
+    else if (maxk <= 48) k_core_inv_reg<T, 3><<<ntasks, 256, schur, s>>>(tasks, err);
+    else k_core_inv_reg<T, 4><<<ntasks, 256, schur, s>>>(tasks, err);
+    return;
+  }
+  if (maxk <= 32 * kCoreRows && schur + 1024 <= (size_t)max_smem) {
     k_core_inv_schur<T><<<ntasks, 256, schur, s>>>(tasks, err);
     return;
   }
@@ -438,7 +659,10 @@ __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict
   const int nh = t.nhat, np = t.np, ls = nh + 1, ldf = t.ld > 0 ? t.ld : nh;
   T* S = reinterpret_cast<T*>(smem_raw);  // nh x nh staging, ld nh + 1
   T* F = (T*)t.F;
-  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) S[e % nh + (e / nh) * ls] = F[e % nh + (size_t)(e / nh) * ldf];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // lower triangle in, a warp per column (no index division)
+  for (int c = warp; c < nh; c += 8)
+    for (int r = c + lane; r < nh; r += 32) S[r + c * ls] = F[r + (size_t)c * ldf];
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T a[TT][TT];
@@ -471,7 +695,7 @@ __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict
         if (threadIdx.x == 0) raise_error(err, HM_ERR_NOT_SPD, t.front, k);
         d = fabs(d) > T(0) ? fabs(d) : T(1);
       }
-      const T inv = T(1) / d;
+      const T inv = recip_rn(d);
       T ci[TT], rk[TT];
 #pragma unroll
       for (int i = 0; i < TT; ++i) ci[i] = colk[buf][ty + 16 * i] * inv;
@@ -502,7 +726,8 @@ __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict
       if (r < nh && c < nh) S[r + c * ls] = (r < np && c < np) ? -a[i][j] : a[i][j];
     }
   __syncthreads();
-  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) F[e % nh + (size_t)(e / nh) * ldf] = S[e % nh + (e / nh) * ls];
+  for (int c = warp; c < nh; c += 8)
+    for (int r = lane; r < nh; r += 32) F[r + (size_t)c * ldf] = S[r + c * ls];
 }
 
 template <typename T>
@@ -534,6 +759,15 @@ int dense_fact_setup(int max_smem) {
   HM_CUDA(allow_max_dyn_smem(k_chol_inverse<double>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_lu<float>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_core_inv_schur<float>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_schur<double>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<float, 1>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<float, 2>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<float, 3>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<float, 4>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<double, 1>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<double, 2>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<double, 3>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_core_inv_reg<double, 4>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_front_sweep<float, 4>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_front_sweep<float, 6>, max_smem));
   HM_CUDA(allow_max_dyn_smem(k_front_sweep<float, 8>, max_smem));
