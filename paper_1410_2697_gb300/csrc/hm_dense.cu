@@ -25,8 +25,37 @@ __device__ __forceinline__ T load_op(const T* __restrict__ X, int op, int ld, in
   return op == 0 ? X[(size_t)r + (size_t)c * ld] : X[(size_t)c + (size_t)r * ld];
 }
 
+// C = alpha acc + beta C on the valid entries of a thread's NI x NJ outputs (rows
+// r0 + 16 i, columns c0 + 16 j).  Every old C value is read before the first store: the
+// compiler must assume a store may alias a later load, so interleaved read-modify-writes
+// would each wait a full memory round trip.
+template <typename T, int NI, int NJ>
+__device__ __forceinline__ void store_tile(const GemmTask& t, T* __restrict__ C, const T (&acc)[NI][NJ], int r0,
+                                           int c0) {
+  const T alpha = (T)t.alpha, beta = (T)t.beta;
+  T old[NI][NJ];
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int r = r0 + 16 * i, c = c0 + 16 * j;
+      const bool ok = r < t.m && c < t.n && !(t.lower && r < c);
+      old[i][j] = (ok && beta != T(0)) ? C[(size_t)r + (size_t)c * t.ldc] : T(0);
+    }
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int r = r0 + 16 * i, c = c0 + 16 * j;
+      if (r < t.m && c < t.n && !(t.lower && r < c)) {
+        const T v = alpha * acc[i][j];
+        C[(size_t)r + (size_t)c * t.ldc] = (beta == T(0)) ? v : fma(beta, old[i][j], v);
+      }
+    }
+}
+
 template <typename T, int BN, int BK>
-__global__ void __launch_bounds__(256, BK == 16 ? 1 : 2) k_gemm(const GemmTask* __restrict__ tasks,
+__global__ void __launch_bounds__(256, BK == 16 ? 4 : 3) k_gemm(const GemmTask* __restrict__ tasks,
                                                                 const GemmTile* __restrict__ tiles,
                                                                 T* __restrict__ split_ws,
                                                                 unsigned* __restrict__ split_cnt) {
@@ -130,21 +159,7 @@ __global__ void __launch_bounds__(256, BK == 16 ? 1 : 2) k_gemm(const GemmTask* 
       }
     if (tid == 0) split_cnt[tl.slot] = 0u;  // ready for the next launch
   }
-  const T alpha = (T)t.alpha, beta = (T)t.beta;
-#pragma unroll
-  for (int j = 0; j < TN; ++j) {
-    const int c = n0 + tx + 16 * j;
-    if (c >= t.n) continue;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = m0 + ty + 16 * i;
-      if (r >= t.m) continue;
-      if (t.lower && r < c) continue;
-      T* dst = C + (size_t)r + (size_t)c * t.ldc;
-      const T v = alpha * acc[i][j];
-      *dst = (beta == T(0)) ? v : fma(beta, *dst, v);
-    }
-  }
+  store_tile<T, 4, TN>(t, C, acc, m0 + ty, n0 + tx);
 }
 
 // =====================================================================================
@@ -173,7 +188,7 @@ template <typename T, int BN>
 __host__ __device__ constexpr int gemm_async_stage_elems() { return kAsyncBK * (BM + 4) + kAsyncBK * (BN + 4); }
 
 template <typename T, int BN>
-__global__ void __launch_bounds__(256) k_gemm_async(const GemmTask* __restrict__ tasks,
+__global__ void __launch_bounds__(256, BN == 16 ? 4 : 3) k_gemm_async(const GemmTask* __restrict__ tasks,
                                                     const GemmTile* __restrict__ tiles, T* __restrict__ split_ws,
                                                     unsigned* __restrict__ split_cnt) {
   constexpr int BK = kAsyncBK, TN = BN / 16, NA = BK * BM / 256, NB = BK * BN / 256;
@@ -270,21 +285,7 @@ __global__ void __launch_bounds__(256) k_gemm_async(const GemmTask* __restrict__
       }
     if (tid == 0) split_cnt[tl.slot] = 0u;
   }
-  const T alpha = (T)t.alpha, beta = (T)t.beta;
-#pragma unroll
-  for (int j = 0; j < TN; ++j) {
-    const int c = n0 + tx + 16 * j;
-    if (c >= t.n) continue;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = m0 + ty + 16 * i;
-      if (r >= t.m) continue;
-      if (t.lower && r < c) continue;
-      T* dst = C + (size_t)r + (size_t)c * t.ldc;
-      const T v = alpha * acc[i][j];
-      *dst = (beta == T(0)) ? v : fma(beta, *dst, v);
-    }
-  }
+  store_tile<T, 4, TN>(t, C, acc, m0 + ty, n0 + tx);
 }
 
 int gemm_async_setup(int max_smem) {
@@ -417,20 +418,30 @@ __global__ void __launch_bounds__(256, 2) k_gemm_big(const GemmTask* __restrict_
       }
     if (tid == 0) split_cnt[tl.slot] = 0u;
   }
+  // C = alpha acc + beta C, two columns at a time with their old values read before the
+  // first store (see store_tile)
   const float alpha = (float)t.alpha, beta = (float)t.beta;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int c = n0 + col_of(j);
-    if (c >= t.n) continue;
+  for (int j0 = 0; j0 < 8; j0 += 2) {
+    float old[2][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = m0 + row_of(i);
-      if (r >= t.m) continue;
-      if (t.lower && r < c) continue;
-      float* dst = C + (size_t)r + (size_t)c * t.ldc;
-      const float v = alpha * acc[i][j];
-      *dst = (beta == 0.f) ? v : fmaf(beta, *dst, v);
-    }
+    for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = m0 + row_of(i), c = n0 + col_of(j0 + jj);
+        const bool ok = r < t.m && c < t.n && !(t.lower && r < c);
+        old[jj][i] = (ok && beta != 0.f) ? C[(size_t)r + (size_t)c * t.ldc] : 0.f;
+      }
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = m0 + row_of(i), c = n0 + col_of(j0 + jj);
+        if (r < t.m && c < t.n && !(t.lower && r < c)) {
+          const float v = alpha * acc[i][j0 + jj];
+          C[(size_t)r + (size_t)c * t.ldc] = (beta == 0.f) ? v : fmaf(beta, old[jj][i], v);
+        }
+      }
   }
 }
 

@@ -227,13 +227,24 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
   const float alpha = (float)t.alpha, beta = (float)t.beta;
   const int r = m0 + row;
   if (r >= t.m) return;
+  // eight columns at a time, their old values read before the first store (a store may
+  // alias a later load as far as the compiler knows)
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const int c = n0 + c0 + j;
-    if (c >= t.n || (t.lower && r < c)) continue;
-    float* dst = C + (size_t)r + (size_t)c * t.ldc;
-    const float v = alpha * acc[j];
-    *dst = (beta == 0.f) ? v : fmaf(beta, *dst, v);
+  for (int j0 = 0; j0 < 32; j0 += 8) {
+    float old[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = n0 + c0 + j0 + j;
+      const bool ok = c < t.n && !(t.lower && r < c);
+      old[j] = (ok && beta != 0.f) ? C[(size_t)r + (size_t)c * t.ldc] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = n0 + c0 + j0 + j;
+      if (c >= t.n || (t.lower && r < c)) continue;
+      const float v = alpha * acc[j0 + j];
+      C[(size_t)r + (size_t)c * t.ldc] = (beta == 0.f) ? v : fmaf(beta, old[j], v);
+    }
   }
 }
 
