@@ -227,9 +227,10 @@ __global__ void __launch_bounds__(kDotThreads, NV <= 4 ? 3 : 2) k_multidot(const
     for (int j = 0; j < R; ++j) {
       const int k = k0 + j * kDotThreads;
       const bool in = k < e;
-      x[j] = in ? wr[k] : 0.0;
+      const int kc = in ? k : b;  // an in-range address even for a slot past the end
+      x[j] = in ? wr[kc] : 0.0;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) v[j][i] = in ? v0[i * vs + k] : 0.0;
+      for (int i = 0; i < NV; ++i) v[j][i] = in ? v0[i * vs + kc] : 0.0;
     }
 #pragma unroll
     for (int j = 0; j < R; ++j)
@@ -269,9 +270,10 @@ __global__ void __launch_bounds__(kDotThreads, NV <= 4 ? 3 : 2) k_gs_update_dots
     for (int j = 0; j < R; ++j) {
       const int k = k0 + j * kDotThreads;
       const bool in = k < e;
-      sv[j] = in ? wr[k] : 0.0;
+      const int kc = in ? k : crow[c];  // an in-range address even for a slot past the end
+      sv[j] = in ? wr[kc] : 0.0;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) vk[j][i] = in ? v0[i * vs + k] : 0.0;
+      for (int i = 0; i < NV; ++i) vk[j][i] = in ? v0[i * vs + kc] : 0.0;
     }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -512,11 +514,9 @@ __global__ void __launch_bounds__(256) k_update_x(double* __restrict__ x, const 
 #pragma unroll
     for (int q = 0; q < kUxVals; ++q) {
       const int e = threadIdx.x + q * 256;
-      xv[q] = 0.0;
-      if (e < cnt) {
-        const int r = e / rows, kk = e - r * rows;
-        xv[q] = x[(int64_t)r * n + k0 + kk];
-      }
+      const int ec = e < cnt ? e : 0;  // an in-range address even for a slot past the end
+      const int r = ec / rows, kk = ec - r * rows;
+      xv[q] = e < cnt ? x[(int64_t)r * n + k0 + kk] : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < kUxVals; ++q) {

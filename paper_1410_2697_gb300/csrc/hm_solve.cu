@@ -25,6 +25,13 @@ namespace hm {
 // rows); grid = (ceil(fronts / 8), nrhs, chunks), 8 warps per block.
 constexpr int kVecChunk = 256;
 
+// The vector assembly loops go kLdBatch iterations at a time, all loads of the batch
+// before its stores: the compiler must assume that a store may alias a later load, so
+// one load-then-store iteration at a time waits a full memory round trip (two where an
+// index is loaded first) per element.  A batch slot past the end reads an in-range
+// element (its index is clamped) and stores nothing.
+constexpr int kLdBatch = 4;
+
 // Upward assembly of HODLR fronts in one launch: one block per (front, right-hand side)
 // forms fv_q = [r(I_q); 0] and adds the children's update parts through the relative
 // maps, one child after another (a fixed order of the sums).
@@ -48,7 +55,21 @@ __global__ void __launch_bounds__(256) k_vassemble(const int* __restrict__ front
     const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
     const T* fc = FV + fvoff[c] + npc + (int64_t)r * nhc;
     const int32_t* rm = relmap + ifoff[c];
-    for (int t = threadIdx.x; t < nuc; t += blockDim.x) fv[rm[t]] += fc[t];
+    for (int t0 = threadIdx.x; t0 < nuc; t0 += blockDim.x * kLdBatch) {
+      int d[kLdBatch];
+      T a[kLdBatch], o[kLdBatch];
+#pragma unroll
+      for (int u = 0; u < kLdBatch; ++u) {
+        const int t = min(t0 + u * (int)blockDim.x, nuc - 1);
+        d[u] = rm[t];
+        a[u] = fc[t];
+      }
+#pragma unroll
+      for (int u = 0; u < kLdBatch; ++u) o[u] = fv[d[u]];
+#pragma unroll
+      for (int u = 0; u < kLdBatch; ++u)  // relmap is injective: no two updates meet
+        if (t0 + u * (int)blockDim.x < nuc) fv[d[u]] = o[u] + a[u];
+    }
   }
 }
 
@@ -70,7 +91,19 @@ __global__ void __launch_bounds__(256) k_vgather(const int* __restrict__ fronts,
   T* fv = FV + fvoff[q] + np + (int64_t)r * nh;
   const int32_t* If = iflist + ifoff[q];
   const T* x = xv + (int64_t)r * n;
-  for (int t = e0 + lane; t < e1; t += 32) fv[t] = -x[If[t]];
+  for (int t0 = e0 + lane; t0 < e1; t0 += 32 * kLdBatch) {
+    int g[kLdBatch];
+    T v[kLdBatch];
+#pragma unroll
+    for (int u = 0; u < kLdBatch; ++u) g[u] = If[min(t0 + 32 * u, e1 - 1)];
+#pragma unroll
+    for (int u = 0; u < kLdBatch; ++u) v[u] = -x[g[u]];
+#pragma unroll
+    for (int u = 0; u < kLdBatch; ++u) {
+      const int t = t0 + 32 * u;
+      if (t < e1) fv[t] = v[u];
+    }
+  }
 }
 
 // -------------------------------------------------------------------------------------
