@@ -627,7 +627,6 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   void* X = sys->d_x;
   void* W = sys->d_w;
   void* Gm = sys->d_g;
-  void* Cm = sys->d_core;
   void* FV = sp->d_fv;
   void* SB = sp->d_sb;
   TaskBuf& tb = sp->tb;
