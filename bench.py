@@ -77,6 +77,12 @@ def parse_args():
     ap.add_argument("--profile-out", default=None, help="write per-kernel profile JSON here")
     ap.add_argument("--profile-run", action="store_true",
                     help="mixed arm only, no e2e / FP64 / CPU legs (for an ncu launch list)")
+    ap.add_argument("--cpu-sample", choices=["full", "bounded"], default="full",
+                    help="cpu_baseline: the oracle on the full workload (1 RHS), or on the bounded "
+                         "sample of --cpu-m")
+    ap.add_argument("--cpu-baseline-only", action="store_true",
+                    help="print the cpu_baseline object alone (no GPU); set OPENBLAS_NUM_THREADS=1 "
+                         "for the single-threaded oracle")
     ap.add_argument("--cpu-m", type=int, default=256,
                     help="grid of the bounded CPU-oracle sample (same family)")
     ap.add_argument("--probe", choices=["factor_apply", "hex_factor"], default=None,
@@ -193,13 +199,21 @@ def load_peaks():
         return None
 
 
+def sm_count() -> int:
+    """Streaming multiprocessors of the device in use (152 on a GB300)."""
+    import torch
+    if torch.cuda.is_available():
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    return 152
+
+
 def alu_peak_tflops(precision: str, sm_max_mhz: float | None) -> float:
-    """SIMT peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA;
-    FP64 is GB300's nominal 1.25 TFLOP/s."""
+    """SIMT peak from unit counts and clock: the device's SMs x 128 FP32 lanes x
+    2 flop/FMA x max SM clock; FP64 is GB300's nominal 1.25 TFLOP/s."""
     if precision == "f64":
         return 1.25
     mhz = sm_max_mhz or 2070.0
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+    return sm_count() * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def ncu_traffic(category: str):
@@ -235,7 +249,7 @@ def kernel_roofline(e: dict, precision: str, peaks, clocks) -> dict:
         achieved = (e["flops"] / launches) / (per_launch_ms * 1e-3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s", "frac": achieved / alu,
                 "launches": e["launches"], "avg_launch_ms": per_launch_ms,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock" if precision != "f64"
+                "peak_source": f"derived: {sm_count()} SM x 128 FP32 lanes x 2 x max SM clock" if precision != "f64"
                 else "nominal GB300 FP64 1.25 TFLOP/s"}
     achieved = (e["bytes"] / launches) / (per_launch_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -500,6 +514,7 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
     }
     line["speedup_vs_fp64_plain"] = line["value"] / line["fp64_plain"]["value"]
+    line["_x0"] = x[:, 0].copy()
     if args.profile_out and rank == 0:
         json.dump({"mixed": prof}, open(args.profile_out, "w"), indent=1)
     return line
@@ -560,14 +575,57 @@ def cpu_cores() -> int:
 
 
 def cpu_baseline(workload: str, cpu_m: int) -> dict:
-    """The oracle as it stands on a bounded sample of the workload (the full-size oracle
-    factorization takes minutes), analyze + factor + GMRES, on all host cores."""
+    """The oracle as it stands on a bounded sample of the workload, analyze + factor +
+    GMRES, on all host cores."""
     problems, tol, desc = oracle_sample(workload, cpu_m)
     sec, solves, rr = oracle_solve_once(problems, tol)
     return {"value": solves / sec, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
             "sample": f"{desc}, one right-hand side each: analyze + FP64 HODLR-MF factor (SVD "
                       f"truncation) + GMRES to 1e-10 on the host in {sec:.1f} s (BLAS threads = all "
                       f"cores), relres {rr:.1e}; not scaled to the full size"}
+
+
+def blas_threads() -> int:
+    """BLAS threads the oracle's NumPy uses (the environment's limit, else all cores)."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(k)
+        if v and v.isdigit():
+            return min(int(v), cpu_cores())
+    return cpu_cores()
+
+
+def cpu_baseline_full(args) -> tuple[dict, object]:
+    """The oracle as it stands on the full workload: nested dissection, symbolic sets,
+    FP64 HODLR-MF factorization with the range finder at the workload's tolerance and
+    sketch width (the same method and settings as the GPU path), then GMRES(30) to 1e-10
+    on the first right-hand side of the bench's batch.  Returns the cpu_baseline object
+    and the oracle's solution (original numbering) for the error of the GPU solution."""
+    import numpy as np
+
+    from oracle import dense_mf, gmres, hodlr_mf, nd, symbolic
+    W = Workload(args)
+    P = W.P
+    b = W.b[:, 0]
+    t0 = time.perf_counter()
+    et = nd.nested_dissection(P.coords, 64, W.dofs)
+    sym = symbolic.symbolic(P.rowptr, P.colidx, et)
+    Ap = dense_mf.permuted_matrix(P.rowptr, P.colidx, P.values, et)
+    t1 = time.perf_counter()
+    prm = hodlr_mf.Params(tol=W.tol, n_c=W.n_c, leaf=W.hodlr_leaf, compressor="rrf", samples=W.samples)
+    fr, _ = hodlr_mf.factor(Ap, et, sym, prm)
+    t2 = time.perf_counter()
+    xn, info = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), b[et.perm], RTOL, 30)
+    t3 = time.perf_counter()
+    x = np.empty_like(xn)
+    x[et.perm] = xn
+    sec = t3 - t0
+    obj = {"value": 1.0 / sec, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
+           "sample": f"the full workload ({P.n} unknowns), right-hand side 0 of the batch: analyze "
+                     f"{t1 - t0:.1f} s + FP64 HODLR-MF factor (range finder, tol {W.tol:g}, "
+                     f"{W.samples} samples) {t2 - t1:.1f} s + GMRES(30) to 1e-10 {t3 - t2:.1f} s "
+                     f"({info['iters']} iterations, relres {info['relres']:.1e}) on the host",
+           "analyze_s": t1 - t0, "factor_s": t2 - t1, "solve_s": t3 - t2, "gmres_iters": info["iters"]}
+    return obj, x
 
 
 def run_reference(args, rank, world):
@@ -780,6 +838,11 @@ def run_probe(args):
 
 def main():
     args = parse_args()
+    if args.cpu_baseline_only:  # host only: no GPU, no process group
+        full = args.cpu_sample == "full" and args.workload != "p1_batch_256"
+        cpu = cpu_baseline_full(args)[0] if full else cpu_baseline(args.workload, min(args.cpu_m, args.m))
+        print(json.dumps(cpu))
+        return
     if args.probe:
         run_probe(args)
         return
@@ -798,13 +861,25 @@ def main():
             print(json.dumps(run_tol_sweep(args)))
         return
     # The host oracle runs before any GPU work in this process (no fork after CUDA init).
-    cpu = None
+    cpu, x_oracle = None, None
+    full = args.cpu_sample == "full" and args.workload != "p1_batch_256"
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_run:
-        cpu = cpu_baseline(args.workload, min(args.cpu_m, args.m))
+        if full:
+            cpu, x_oracle = cpu_baseline_full(args)
+        else:
+            cpu = cpu_baseline(args.workload, min(args.cpu_m, args.m))
     line = run_ours(args, rank, world, local)
     if rank == 0:
+        x0 = line.pop("_x0", None)
         if not args.profile_run:
             line["cpu_baseline"] = cpu
+            if x_oracle is not None and x0 is not None:
+                import numpy as np
+                line["err_vs_oracle"] = {
+                    "value": float(np.linalg.norm(x0 - x_oracle) / np.linalg.norm(x_oracle)),
+                    "against": "the oracle's FP64 HODLR-MF + GMRES solution (rtol 1e-10) of right-hand "
+                               "side 0 on the full workload; both solutions lie within kappa(A) * 1e-10 "
+                               "of x*"}
         print(json.dumps(line))
 
 

@@ -83,6 +83,11 @@ typedef struct hm_opts {
                             whole nodes, and a node's unknowns stay consecutive          */
   int compressor;        /* enum hm_compressor (HM_COMP_RRF)                              */
   int bdlr_depth;        /* BDLR graph-distance depth d (1, the paper's usual setting)   */
+  int wait_limit;        /* polls of a bounded device-side wait (the tensor-core GEMM's
+                            mbarrier waits on its MMAs) before the kernel gives up with
+                            HM_ERR_DEVICE_TIMEOUT; 0 = the default, 2^22.  A kernel that
+                            gives up still waits (with the default limit) for the MMAs it
+                            issued and frees its tensor memory before it returns.        */
 } hm_opts;
 
 typedef struct hm_solve_info {
@@ -104,7 +109,7 @@ typedef struct hm_factor_info {
 
 /* Fill *opts with defaults (device 0, mixed precision, nd_leaf 64, hodlr_leaf 64,
    n_c 64, samples 48, restart 30, dofs_per_node 1, compressor HM_COMP_RRF,
-   bdlr_depth 1).  Never fails for a non-null pointer.                                */
+   bdlr_depth 1, wait_limit 0).  Never fails for a non-null pointer.                  */
 int hm_default_opts(hm_opts* opts);
 
 /* Create a context on opts->device.  The context owns a CUDA stream (unless one is
@@ -249,8 +254,15 @@ int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
  * whose device memory is owned by another allocator (a framework's caching pool or a
  * fixed budget), allocator callbacks that must not re-enter the CUDA allocator, and
  * latency-critical loops that cannot wait on the driver.  It computes the same
- * z = M^{-1} r as hm_precond_apply.
- *   r, z      DEVICE pointers, n x nrhs column-major FP64, original numbering.
+ * z = M^{-1} r as hm_precond_apply with the same kernels, launched one by one: it never
+ * captures or instantiates a CUDA graph.
+ *   r, z      DEVICE pointers, n x nrhs column-major FP64, original numbering.  The call
+ *             runs on the context's stream (hm_opts.stream, else the context's own
+ *             non-blocking stream): r must already hold its values when the call is made
+ *             -- work that produces r on another stream must be complete (synchronize
+ *             that stream) unless the context was created on that same stream.
+ *   Returns   after synchronizing the context's stream: z is complete on return.  The
+ *             call is blocking.
  *   Limits    n * nrhs <= 262144 (HM_ERR_CAPACITY beyond).  The per-nrhs workspace of
  *             the system must exist already: make one hm_precond_apply or hm_solve call
  *             with the same nrhs first (HM_ERR_STATE otherwise; that call allocates).
@@ -260,9 +272,9 @@ int hm_precond_apply(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
  *             share it, so calls that overlap on the GPU (from several threads or
  *             streams) race; serialise them.  Each call overwrites every temporary it
  *             reads, so nothing needs clearing between calls.
- *   Set-up    the first call on a device looks up the array's device address
- *             (cudaGetSymbolAddress) with that device current; make that first call
- *             before any stream capture.
+ *   Set-up    the first call on each context looks up the array's device address
+ *             (cudaGetSymbolAddress, which allocates nothing) with the context's device
+ *             current; make that first call before any stream capture.
  */
 int hm_precond_apply_noalloc(hm_sys_t sys, int32_t nrhs, const double* r, double* z);
 

@@ -20,4 +20,6 @@ follows):
                    (Section 4.2, Eqs. HODLR_EA .. update_HODLR_Parent).
 * ``gmres``     -- right-preconditioned restarted GMRES (Sections 1, 3, 6).
 * ``philox``    -- Philox4x32-10 (published definition) for the range-finder sketch.
+* ``condest``   -- Lanczos estimate of kappa(A), the factor between the residual GMRES
+                   stops at (Section 3) and the error bound of the solution.
 """

@@ -460,7 +460,6 @@ __global__ void k_prow_fill(const int64_t* rowptr, const int32_t* colidx, const 
 // ------------------------------------------------------------------------------------
 constexpr int kSymCap = 32768;  // largest candidate list (one CTA's shared memory)
 constexpr int kSymFast = 2048;  // candidate capacity of the first pass
-constexpr int kSymSlowCtas = 152;
 
 // I_p^f of front q with a candidate buffer of `cap` entries in shared memory.  Returns
 // false (nothing written) if the candidate list does not fit.  Every thread calls it.
@@ -966,7 +965,7 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
                                             sys->d_child_list, sys->d_prowptr, sys->d_pcol, sys->d_nupd,
                                             sys->d_ifoff, sys->d_iflist, cursor, capacity, queue,
                                             dq + 2 * L, sys->d_err);
-      k_symbolic_slow<<<std::min(cntL, kSymSlowCtas), 1024, kSymCap * sizeof(int), s>>>(
+      k_symbolic_slow<<<std::min(cntL, sys->ctx->num_sms), 1024, kSymCap * sizeof(int), s>>>(
           sys->d_first, sys->d_child_ptr, sys->d_child_list, sys->d_prowptr, sys->d_pcol, sys->d_nupd,
           sys->d_ifoff, sys->d_iflist, cursor, capacity, queue, dq + 2 * L, dq + 2 * L + 1, sys->d_err);
     }

@@ -246,6 +246,7 @@ int hm_default_opts(hm_opts* o) {
   o->dofs_per_node = 1;
   o->compressor = HM_COMP_RRF;
   o->bdlr_depth = 1;
+  o->wait_limit = 0;
   return HM_OK;
 }
 
@@ -262,10 +263,10 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   if (o.nd_leaf < 1 || o.hodlr_leaf < 2 || o.hodlr_leaf > 64 || o.n_c < 0 || o.n_c > 128 ||
       o.samples < 1 || o.samples > kmax || o.restart < 1 || o.restart > 200 || o.dofs_per_node < 1 ||
       o.dofs_per_node > 8 || (o.compressor != HM_COMP_RRF && o.compressor != HM_COMP_BDLR) ||
-      o.bdlr_depth < 1 || o.bdlr_depth > 8) {
+      o.bdlr_depth < 1 || o.bdlr_depth > 8 || o.wait_limit < 0) {
     set_last_error("option out of range: nd_leaf>=1, 2<=hodlr_leaf<=64, 0<=n_c<=128, "
                    "1<=samples<=" + std::to_string(kmax) + ", 1<=restart<=200, 1<=dofs_per_node<=8, "
-                   "compressor RRF or BDLR, 1<=bdlr_depth<=8");
+                   "compressor RRF or BDLR, 1<=bdlr_depth<=8, wait_limit>=0");
     return HM_ERR_INVALID_ARG;
   }
   int ndev = 0;

@@ -176,10 +176,11 @@ int gemm_tile_count(const GemmTask& t, int bm, int bn);
 void gemm_tiles_for(const GemmTask& t, int task_index, int bm, int bn, int nsplit, std::vector<GemmTile>* out,
                     int* slots, int64_t* ws);
 // Tensor-core (tcgen05, BF16 operands, FP32 accumulation) batched GEMM on 128 x 64 tiles;
-// FP32 data in memory.  A mbarrier wait that runs out raises HM_ERR_DEVICE_TIMEOUT in err.
+// FP32 data in memory.  A mbarrier wait that runs out (after wait_limit polls; <= 0: the
+// default) raises HM_ERR_DEVICE_TIMEOUT in err.
 constexpr int kTcBM = 128, kTcBN = 64;
 void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
-                    unsigned* split_cnt, int* err, cudaStream_t s);
+                    unsigned* split_cnt, int* err, int wait_limit, cudaStream_t s);
 int dense_tc_setup(int max_smem);
 
 int dense_fact_setup(int max_dyn_smem);

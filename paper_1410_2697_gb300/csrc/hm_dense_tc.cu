@@ -12,9 +12,11 @@
 // them to the slice's mbarrier; the next slice is staged into the other buffer while the
 // tensor core runs.  The accumulator (128 lanes x 64 FP32 columns of tensor memory) is
 // read back with tcgen05.ld (warp w: lanes 32 (w % 4) .., columns 32 (w / 4) ..) for the
-// alpha / beta epilogue.  Every mbarrier wait is bounded; a wait that runs out sets the
-// device error word (HM_ERR_DEVICE_TIMEOUT), skips the rest of the tile and still frees
-// the tensor memory.
+// alpha / beta epilogue.  Every mbarrier wait is bounded (wait_limit polls); a wait that
+// runs out sets the device error word (HM_ERR_DEVICE_TIMEOUT) and skips the rest of the
+// tile, but first waits, with the default limit, for the last MMA group it committed
+// (tcgen05.commit tracks every MMA issued before it), so the tensor memory is freed only
+// once no MMA can still write it.
 #include <cuda_bf16.h>
 
 #include "hm_dense.cuh"
@@ -26,7 +28,7 @@ namespace {
 constexpr int TM = 128, TN = 64, TK = 64;                 // tile and k slice
 constexpr int kStageA = TM * TK * 2, kStageB = TN * TK * 2;  // bytes of one slice (BF16)
 constexpr int kTcSmem = 2 * (kStageA + kStageB);           // double-buffered
-constexpr int kWaitLimit = 1 << 22;                        // mbarrier polls before giving up
+constexpr int kWaitLimit = 1 << 22;                        // default mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -49,8 +51,8 @@ __device__ __forceinline__ uint32_t kmaj(int row, int kk, int rows) {
   return (uint32_t)((kk >> 3) * rows * 16 + (row >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
@@ -104,11 +106,12 @@ __device__ __forceinline__ void stage_slice(unsigned char* __restrict__ sl, cons
 
 __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ tasks,
                                                  const GemmTile* __restrict__ tiles, float* __restrict__ split_ws,
-                                                 unsigned* __restrict__ split_cnt, int* __restrict__ err) {
+                                                 unsigned* __restrict__ split_cnt, int* __restrict__ err,
+                                                 int wait_limit) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_ok, s_last;
+  __shared__ int s_ok, s_last, s_committed;
   const GemmTile tl = tiles[blockIdx.x];
   const GemmTask t = tasks[tl.task];
   const int m0 = (tl.mn >> 16) * TM, n0 = (tl.mn & 0xffff) * TN;
@@ -120,6 +123,7 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
+    s_committed = 0;  // k slices whose MMAs have been committed
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
   for (int kt = 0; kt < nk; ++kt) {
     const int s = kt & 1;
     if (kt >= 2) {  // the MMAs that read this buffer two slices ago must be done
-      if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kt >> 1) - 1) & 1))) s_ok = 0;
+      if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kt >> 1) - 1) & 1), wait_limit)) s_ok = 0;
       __syncthreads();
       if (!s_ok) break;
     }
@@ -161,22 +165,22 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_u32(&mbar[s])) : "memory");
+      s_committed = kt + 1;
     }
   }
   if (nk > 0 && s_ok) {
     const int s = (nk - 1) & 1;
-    if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((nk - 1) >> 1) & 1))) s_ok = 0;
+    if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((nk - 1) >> 1) & 1), wait_limit)) s_ok = 0;
   }
   __syncthreads();
   const bool ok = s_ok != 0;
   if (!ok && tid == 0) {
     raise_error(err, HM_ERR_DEVICE_TIMEOUT, 20, blockIdx.x);
-    // give the slices still in flight a bounded chance to finish before the tensor
-    // memory is released
-    for (int s = 0; s < 2 && s < nk; ++s) {
-      const int uses = (nk - s + 1) / 2;  // slices kt = s, s + 2, ... committed to buffer s
-      (void)mbar_wait(smem_u32(&mbar[s]), (uint32_t)((uses - 1) & 1));
-    }
+    // Drain before the tensor memory is released: slice c = s_committed - 1 was the last
+    // one committed, to buffer c & 1, as that buffer's (c >> 1)-th use; its commit
+    // completes once every MMA issued before it has.  The default limit applies here.
+    const int c = s_committed - 1;
+    if (c >= 0) (void)mbar_wait(smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1), kWaitLimit);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // accumulator -> registers: row = lane quarter of the warp, 32 columns per warp half
@@ -249,9 +253,10 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
 }
 
 void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
-                    unsigned* split_cnt, int* err, cudaStream_t s) {
+                    unsigned* split_cnt, int* err, int wait_limit, cudaStream_t s) {
   if (ntiles <= 0) return;
-  k_gemm_tc<<<ntiles, 256, kTcSmem, s>>>(tasks, tiles, split_ws, split_cnt, err);
+  k_gemm_tc<<<ntiles, 256, kTcSmem, s>>>(tasks, tiles, split_ws, split_cnt, err,
+                                          wait_limit > 0 ? wait_limit : kWaitLimit);
 }
 
 int dense_tc_setup(int max_smem) {

@@ -116,7 +116,7 @@ static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* bas
   ProfScope ps(sys->ctx, cat, b.tasks.work);
   if (b.tc && sizeof(T) == 4) {
     launch_gemm_tc(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, (float*)sys->plan.d_split_ws,
-                   sys->plan.d_split_cnt, sys->d_err, sys->ctx->stream);
+                   sys->plan.d_split_cnt, sys->d_err, sys->ctx->opts.wait_limit, sys->ctx->stream);
     return;
   }
   TuneScope ts(sys->ctx, TS_GEMM, b.sig);
@@ -148,7 +148,7 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
   {
     const int64_t nnz = sys->nnz;
     ProfScope ps(ctx, PC_SCATTER, Work{0.0, nnz * 32.0 + 0.5 * nnz * es});
-    const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+    const int grid = (int)std::min<int64_t>((nnz + 255) / 256, (int64_t)ctx->num_sms * 16);
     k_scatter<T><<<std::max(grid, 1), 256, 0, s>>>(d_values, sys->d_psrc, sys->d_amap, nnz, F,
                                                   sys->d_pvals, sys->d_pvals2);
   }

@@ -130,9 +130,11 @@ struct TaskBuf {
   // (batches of one plan run one after another, so they share one workspace).
   int64_t split_ws = 0;
   int split_slots = 0;
-  // A batch with fewer tiles than about two waves of the GPU splits the k range of its
-  // long products (parts of at least kSplitMinK) so that more SMs share the work.
-  static constexpr int kSplitTarget = 304, kSplitMinK = 128, kSplitMax = 16;
+  // A batch with fewer tiles than about two waves of the GPU (split_target = two tiles
+  // per SM, set from the device's SM count) splits the k range of its long products
+  // (parts of at least kSplitMinK) so that more SMs share the work.
+  int split_target = 304;
+  static constexpr int kSplitMinK = 128, kSplitMax = 16;
   GemmBatch add_gemm(const std::vector<GemmTask>& t, bool tc = false) {
     std::vector<GemmTile> tiles;
     GemmBatch b;
@@ -145,8 +147,8 @@ struct TaskBuf {
     int64_t ws = 0;
     for (size_t i = 0; i < t.size(); ++i) {
       int nsplit = 1;
-      if (ntiles < kSplitTarget && t[i].k >= 2 * kSplitMinK)
-        nsplit = std::min(std::min(kSplitTarget / std::max(ntiles, 1), t[i].k / kSplitMinK), kSplitMax);
+      if (ntiles < split_target && t[i].k >= 2 * kSplitMinK)
+        nsplit = std::min(std::min(split_target / std::max(ntiles, 1), t[i].k / kSplitMinK), kSplitMax);
       gemm_tiles_for(t[i], (int)i, bm, b.bn, nsplit, &tiles, &slots, &ws);
     }
     split_ws = std::max(split_ws, ws);
@@ -164,8 +166,8 @@ struct TaskBuf {
       int64_t bws = 0;
       for (size_t i = 0; i < t.size(); ++i) {
         int nsplit = 1;
-        if (nbig < kSplitTarget && t[i].k >= 2 * kSplitMinK)
-          nsplit = std::min(std::min(kSplitTarget / std::max(nbig, 1), t[i].k / kSplitMinK), kSplitMax);
+        if (nbig < split_target && t[i].k >= 2 * kSplitMinK)
+          nsplit = std::min(std::min(split_target / std::max(nbig, 1), t[i].k / kSplitMinK), kSplitMax);
         gemm_tiles_for(t[i], (int)i, kBigTile, kBigTile, nsplit, &big, &bslots, &bws);
       }
       split_ws = std::max(split_ws, bws);
@@ -413,6 +415,7 @@ struct hm_ctx_s {
   hm::Tuner tune;
   cudaMemPool_t pool = nullptr;  // stream-ordered pool; freed memory is kept for reuse
   std::vector<void*> allocs;
+  void* noalloc_scratch = nullptr;  // device address of the allocation-free apply's array
 };
 
 struct hm_sys_s {
@@ -567,6 +570,9 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out);
 void release_solve_state(hm_sys_s* sys);
 // z (T, n x nrhs, ld n, new numbering) = M^{-1} r (T, same layout)
 int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
+// As apply_impl, always launched kernel by kernel: never captures or instantiates a
+// CUDA graph (the driver allocates for those).
+int apply_impl_eager(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 // As apply_impl, with z written row-major (element (i, r) at i nrhs + r).
 int apply_impl_rowmajor(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 int solve_setup(int max_smem);

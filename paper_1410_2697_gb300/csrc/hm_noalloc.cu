@@ -5,8 +5,10 @@
 // budget that must not be exceeded behind its back), allocator or memory-pressure
 // callbacks that must not re-enter the CUDA allocator, and latency-critical loops that
 // cannot wait on the driver's allocator.  hm_precond_apply allocates three temporary
-// n x nrhs blocks per call; this variant keeps them in one file-scope device array of
-// fixed size instead, and otherwise runs the same kernels.
+// n x nrhs blocks per call, and replays its launches from a CUDA graph it captures and
+// instantiates (the driver allocates for both); this variant keeps the temporaries in
+// one file-scope device array of fixed size instead and launches the same kernels one by
+// one, never through a graph.  It synchronizes the context's stream before returning.
 #include <mutex>
 
 #include "hm_internal.h"
@@ -21,28 +23,27 @@ constexpr int64_t kNoAllocMaxElems = 262144;
 // the library holds this array until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMaxElems];
 
-// Device address of g_noalloc_scratch, looked up once per device with that device
-// current (in host code the symbol is only a host-side stand-in, not a device address).
+// Device address of g_noalloc_scratch.  In host code the symbol is only a host-side
+// stand-in, not a device address, so the address is looked up with cudaGetSymbolAddress,
+// with the context's device current, at the first allocation-free call on each context
+// (the lookup allocates nothing).  Keeping it per context rather than per process means
+// a context created after a device reset never reuses an address from before the reset.
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[256] = {nullptr};
 
-static int noalloc_scratch(int device, double** out) {
-  if (device < 0 || device >= 256) {
-    set_last_error("hm_precond_apply_noalloc: device ordinal out of range");
-    return HM_ERR_INVALID_ARG;
-  }
+static int noalloc_scratch(hm_ctx_s* ctx, double** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[device]) {
+  if (!ctx->noalloc_scratch) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
       set_last_error(std::string("hm_precond_apply_noalloc: cudaGetSymbolAddress: ") +
                      cudaGetErrorString(e));
       return HM_ERR_CUDA;
     }
-    g_noalloc_addr[device] = p;
+    ctx->noalloc_scratch = p;
   }
-  *out = (double*)g_noalloc_addr[device];
+  *out = (double*)ctx->noalloc_scratch;
   return HM_OK;
 }
 
@@ -56,7 +57,7 @@ static int apply_noalloc_t(hm_sys_s* sys, int nrhs, const double* r, double* z, 
   T* zT = (T*)(scratch + 2 * kNoAllocMaxElems);
   launch_permute_in(r, rp, sys->d_perm, n, nrhs, s);
   launch_cast_to<T>(rp, rT, nn, s);
-  HM_TRY(apply_impl(sys, nrhs, rT, zT));
+  HM_TRY(apply_impl_eager(sys, nrhs, rT, zT));  // kernel launches only: no graph, no allocation
   launch_cast_from<T>(zT, rp, nn, s);
   launch_permute_out(rp, z, sys->d_perm, n, nrhs, s);
   HM_CUDA(cudaStreamSynchronize(s));
@@ -98,7 +99,7 @@ extern "C" int hm_precond_apply_noalloc(hm_sys_t sys, int32_t nrhs, const double
     return HM_ERR_INVALID_ARG;
   }
   double* scratch = nullptr;
-  HM_TRY(noalloc_scratch(dev, &scratch));
+  HM_TRY(noalloc_scratch(sys->ctx, &scratch));
   return sys->precision == HM_PREC_FP64 ? apply_noalloc_t<double>(sys, nrhs, r, z, scratch)
                                         : apply_noalloc_t<float>(sys, nrhs, r, z, scratch);
 }

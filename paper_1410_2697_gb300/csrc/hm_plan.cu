@@ -317,6 +317,7 @@ int build_plan(hm_sys_s* sys) {
   TaskBuf& tb = P.tb;
   tb.host.clear();
   tb.es = es;
+  tb.split_target = 2 * sys->ctx->num_sms;
   P.levels.assign(P.nlevels, LevelFactorPlan());
   double fbytes = 0;
   for (int l = P.nlevels - 1; l >= 0; --l) {
@@ -631,6 +632,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   void* SB = sp->d_sb;
   TaskBuf& tb = sp->tb;
   tb.es = es;
+  tb.split_target = 2 * sys->ctx->num_sms;
   sp->levels.assign(P.nlevels, LevelSolvePlan());
   for (int l = 0; l < P.nlevels; ++l) {
     LevelSolvePlan& lp = sp->levels[l];

@@ -473,12 +473,13 @@ __global__ void __launch_bounds__(256) k_to_rowmajor(const T* __restrict__ src, 
 }
 
 template <typename T>
-static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout, bool rowmajor_out = false) {
+static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout, bool rowmajor_out = false,
+                   bool eager = false) {
   SolvePlan* sp = nullptr;
   HM_TRY(get_solve_plan(sys, nrhs, &sp));
   hm_ctx_s* ctx = sys->ctx;
   cudaStream_t s = ctx->stream;
-  const bool graphs = !ctx->prof.on && !ctx->tune.rec && s != nullptr;
+  const bool graphs = !eager && !ctx->prof.on && !ctx->tune.rec && s != nullptr;
   if (graphs && sp->graph_exec && sp->graph_in == (const void*)win) {
     HM_CUDA(cudaGraphLaunch(sp->graph_exec, s));
   } else if (graphs && sp->last_in == (const void*)win) {
@@ -503,7 +504,7 @@ static int apply_t(hm_sys_s* sys, int nrhs, const T* win, T* xout, bool rowmajor
   } else {
     HM_TRY(apply_launches<T>(sys, sp, nrhs, win));
   }
-  sp->last_in = win;
+  if (!eager) sp->last_in = win;
   T* xfix = (T*)sp->d_xfix;
   if (rowmajor_out) {
     ProfScope ps(ctx, PC_VECTOR, Work{0.0, 2.0 * sizeof(T) * (double)sys->n * nrhs});
@@ -548,6 +549,12 @@ int apply_impl(hm_sys_s* sys, int nrhs, const void* rT, void* zT) {
   return apply_t<float>(sys, nrhs, (const float*)rT, (float*)zT);
 }
 
+int apply_impl_eager(hm_sys_s* sys, int nrhs, const void* rT, void* zT) {
+  if (sys->precision == HM_PREC_FP64)
+    return apply_t<double>(sys, nrhs, (const double*)rT, (double*)zT, false, true);
+  return apply_t<float>(sys, nrhs, (const float*)rT, (float*)zT, false, true);
+}
+
 int apply_impl_rowmajor(hm_sys_s* sys, int nrhs, const void* rT, void* zT) {
   if (sys->precision == HM_PREC_FP64) return apply_t<double>(sys, nrhs, (const double*)rT, (double*)zT, true);
   return apply_t<float>(sys, nrhs, (const float*)rT, (float*)zT, true);
@@ -576,13 +583,21 @@ __global__ void k_permute_out(const double* src, double* dst, const int32_t* per
   }
 }
 
+// Grid of the grid-stride vector kernels: eight CTAs per SM of the current device.
+static unsigned stride_grid() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return 8u * (unsigned)std::max(sms, 1);
+}
+
 void launch_permute_in(const double* src, double* dst, const int32_t* perm, int n, int nrhs,
                        cudaStream_t s) {
-  k_permute_in<<<1216, 256, 0, s>>>(src, dst, perm, n, nrhs);
+  k_permute_in<<<stride_grid(), 256, 0, s>>>(src, dst, perm, n, nrhs);
 }
 void launch_permute_out(const double* src, double* dst, const int32_t* perm, int n, int nrhs,
                         cudaStream_t s) {
-  k_permute_out<<<1216, 256, 0, s>>>(src, dst, perm, n, nrhs);
+  k_permute_out<<<stride_grid(), 256, 0, s>>>(src, dst, perm, n, nrhs);
 }
 
 template <typename T>
@@ -599,11 +614,11 @@ __global__ void k_cast_from(const T* src, double* dst, int64_t count) {
 }
 template <typename T>
 void launch_cast_to(const double* src, T* dst, int64_t count, cudaStream_t s) {
-  k_cast_to<T><<<1216, 256, 0, s>>>(src, dst, count);
+  k_cast_to<T><<<stride_grid(), 256, 0, s>>>(src, dst, count);
 }
 template <typename T>
 void launch_cast_from(const T* src, double* dst, int64_t count, cudaStream_t s) {
-  k_cast_from<T><<<1216, 256, 0, s>>>(src, dst, count);
+  k_cast_from<T><<<stride_grid(), 256, 0, s>>>(src, dst, count);
 }
 template void launch_cast_to<float>(const double*, float*, int64_t, cudaStream_t);
 template void launch_cast_to<double>(const double*, double*, int64_t, cudaStream_t);

@@ -124,3 +124,56 @@ def test_calls_out_of_order_and_bad_inputs():
         hm.hm_analyze(c, P.n, P.rowptr, P.colidx, 4, P.coords)  # dim must be 2 or 3
     assert e.value.status == hm.abi.HM_ERR_INVALID_ARG
     hm.hm_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("precision", ["HM_PREC_FP64", "HM_PREC_MIXED"])
+def test_iteration_cap_reports_no_convergence(precision):
+    """A cap of 2 GMRES iterations on a problem that needs more: HM_ERR_NO_CONVERGENCE,
+    info reports the cap and a residual above rtol, x holds the last iterate (its residual
+    is the reported one, and below that of x0 = 0); the system stays usable."""
+    P = q1_square(48, lognormal_coefficients(48 * 48, 1.0, seed=95))
+    c = ctx(getattr(hm, precision), nd_leaf=16, hodlr_leaf=16, n_c=16, samples=8)
+    s = hm.hm_analyze(c, P.n, P.rowptr, P.colidx, 2, P.coords)
+    hm.hm_factor(s, P.values, 1e-1)
+    b = rhs_uniform(P.n, 2, 96)
+    x = np.zeros_like(b)
+    with pytest.raises(hm.HmError) as e:
+        hm.hm_solve(s, 2, b, 1e-12, 2, x)
+    assert e.value.status == hm.abi.HM_ERR_NO_CONVERGENCE
+    x = np.zeros_like(b)
+    info = hm.hm_solve(s, 2, b, 1e-12, 2, x, raise_on_no_convergence=False)
+    assert info["converged"] == 0 and info["iters"] == 2 and info["relres"] > 1e-12
+    A = P.scipy()
+    rr = max(np.linalg.norm(b[:, k] - A @ x[:, k]) / np.linalg.norm(b[:, k]) for k in range(2))
+    assert abs(rr - info["relres"]) <= 1e-6 * rr and rr < 1.0
+    info = hm.hm_solve(s, 2, b, 1e-10, 4000, x)  # the same system converges without the cap
+    assert info["converged"] == 1
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(c)
+
+
+def test_tensor_core_wait_that_runs_out_reports_timeout():
+    """The BF16 mode's tensor-core GEMM waits on its MMAs through a bounded mbarrier
+    poll.  With a limit of one poll the wait gives up before the MMAs finish (no fault,
+    no hang: the kernel still drains the MMAs it issued, with the default limit, before
+    it frees its tensor memory): the factorization reports HM_ERR_DEVICE_TIMEOUT.  A new
+    context with the default limit on the same device then factors and solves."""
+    from fixtures import hex_cube
+    P = hex_cube(20, lognormal_coefficients(20 ** 3, 0.5, seed=97))
+    c = ctx(hm.HM_PREC_MIXED_BF16, wait_limit=1)
+    s = hm.hm_analyze(c, P.n, P.rowptr, P.colidx, 3, P.coords)
+    with pytest.raises(hm.HmError) as e:
+        hm.hm_factor(s, P.values, 1e-4)
+    assert e.value.status == hm.abi.HM_ERR_DEVICE_TIMEOUT
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(c)
+    c = ctx(hm.HM_PREC_MIXED_BF16)
+    s = hm.hm_analyze(c, P.n, P.rowptr, P.colidx, 3, P.coords)
+    hm.hm_factor(s, P.values, 1e-4)
+    b = rhs_uniform(P.n, 1, 98)
+    x = np.zeros_like(b)
+    info = hm.hm_solve(s, 1, b, 1e-10, 4000, x)
+    assert info["converged"] == 1
+    assert np.linalg.norm(b[:, 0] - P.scipy() @ x[:, 0]) / np.linalg.norm(b[:, 0]) <= 1e-10
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(c)

@@ -436,3 +436,90 @@ def test_hodlr_mf_with_bdlr_converges():
         x, info = gmres.gmres(lambda v: Ap @ v, lambda v: hodlr_mf.apply(fr, et, sym, v), b, 1e-10, 30)
         assert info["converged"] and info["relres"] <= 1e-10
         assert 3 * info["iters"] < none["iters"], (depth, info["iters"], none["iters"])
+
+
+def test_bdlr_select_orders_by_distance_then_position_and_caps_last():
+    """Hand-worked selection on an 8-vertex graph, X = {0, 1, 2, 3}, Y = {4, 5, 6, 7},
+    edges 0-4, 3-5, 0-1, 2-3, 4-6, 6-7.  Distances to Y: vertex 0 -> 1 (edge 0-4),
+    3 -> 1 (3-5), 1 -> 2 (via 0), 2 -> 2 (via 3).  Distances to X: 4 -> 1, 5 -> 1,
+    6 -> 2 (via 4), 7 -> 3.  Ordered by distance, then position: I = [0, 3, 1, 2],
+    J = [0, 1, 2] (7 is beyond depth 2).  The cap applies after that ordering: cap 3
+    gives I = [0, 3, 1] -- ordering by position first ([0, 1, 2]) or cutting to the cap
+    before filtering by distance would both give another list."""
+    import scipy.sparse as sp
+    from oracle import bdlr
+    e = np.array([[0, 4], [3, 5], [0, 1], [2, 3], [4, 6], [6, 7]])
+    G = sp.coo_matrix((np.ones(12), (np.r_[e[:, 0], e[:, 1]], np.r_[e[:, 1], e[:, 0]])), shape=(8, 8)).tocsr()
+    X, Y = np.arange(4), np.arange(4, 8)
+    I, J = bdlr.select(G, X, Y, 2, 8)
+    assert I.tolist() == [0, 3, 1, 2] and J.tolist() == [0, 1, 2]
+    I, J = bdlr.select(G, X, Y, 2, 3)
+    assert I.tolist() == [0, 3, 1] and J.tolist() == [0, 1, 2]
+    I, J = bdlr.select(G, X, Y, 2, 2)
+    assert I.tolist() == [0, 3] and J.tolist() == [0, 1]
+    I, J = bdlr.select(G, X, Y, 1, 8)  # depth 1: only the direct neighbours
+    assert I.tolist() == [0, 3] and J.tolist() == [0, 1]
+
+
+def test_hodlr_mf_compress_ff_update_is_hodlr_of_f_ff():
+    """compress_ff=True (the paper's F_ff^HODLR, Section 4.2.1): the update of every
+    HODLR front is U_p = H(F_ff) - W T W^T.  Adding W T W^T back must give a matrix whose
+    leaf diagonal blocks equal F_ff's exactly and whose off-diagonal blocks are F_ff's
+    truncated at tol (Eckart-Young with the SVD compressor: 2-norm error = the first
+    dropped singular value <= tol sigma_1).  At tol 0 nothing is dropped and the
+    preconditioner is A^{-1}."""
+    p = q1_square(40, lognormal_coefficients(40 * 40, 1.0, seed=3))
+    et, sym, Ap = _setup(p, 16)
+    tol = 1e-3
+    prm = hodlr_mf.Params(tol=tol, n_c=8, leaf=8, compress_ff=True)
+    fr, tr = hodlr_mf.factor(Ap, et, sym, prm, keep=True)
+    checked = 0
+    for q, f in enumerate(fr):
+        if f.kind != "hodlr" or f.W.shape[0] == 0:
+            continue
+        npv = f.npiv
+        Fff = tr["F"][q][npv:, npv:]
+        T = f.V.T @ hodlr.solve(f.H, f.V)
+        Hff = tr["U"][q] + f.W @ T @ f.W.T       # = to_dense(H(F_ff))
+        ref = hodlr.build(Fff, prm.leaf, 0.0)    # the partition, blocks exact
+        for node in hodlr.iter_nodes(ref):
+            if node.children:
+                a, b = node.children[0], node.children[1]
+                B = Fff[a.lo:a.hi, b.lo:b.hi]
+                E = Hff[a.lo:a.hi, b.lo:b.hi] - B
+                s = np.linalg.svd(B, compute_uv=False)
+                assert np.linalg.norm(E, 2) <= tol * s[0] * (1 + 1e-9) + 1e-12, (q, node.level)
+                np.testing.assert_allclose(Hff[b.lo:b.hi, a.lo:a.hi], Hff[a.lo:a.hi, b.lo:b.hi].T, atol=1e-12)
+            else:
+                np.testing.assert_allclose(Hff[node.lo:node.hi, node.lo:node.hi],
+                                           Fff[node.lo:node.hi, node.lo:node.hi], atol=1e-10 * np.abs(Fff).max())
+        checked += 1
+    assert checked > 0
+    prm0 = hodlr_mf.Params(tol=0.0, n_c=8, leaf=8, compress_ff=True)
+    fr0, _ = hodlr_mf.factor(Ap, et, sym, prm0)
+    r = np.random.default_rng(1).standard_normal((p.n, 2))
+    np.testing.assert_allclose(Ap @ hodlr_mf.apply(fr0, et, sym, r), r, atol=1e-9)
+
+
+def test_kappa_estimate_matches_closed_form_spectrum():
+    """Q1 Poisson: lambda_min and lambda_max from the closed-form eigenvalues.  Lanczos
+    Ritz values approach the extreme eigenvalues from below: lambda_max(A^{-1}) =
+    1 / lambda_min converges fast (well separated at the bottom of the spectrum), the
+    top of the spectrum is clustered so lambda_max(A) only to about a percent; the
+    Gershgorin row sum bounds lambda_max from above."""
+    from oracle import condest
+    m = 24
+    p = q1_square(m)
+    h = 1.0 / m
+    c = np.cos(np.arange(1, m) * np.pi * h)
+    lam = (2.0 / 3.0) * (4 - c[:, None] - c[None, :] - 2 * c[:, None] * c[None, :])
+    A = p.scipy()
+    lu = spl.splu(A.tocsc())
+    inv_max = condest.lanczos_max(lu.solve, p.n, 40, seed=3)
+    assert abs(inv_max * lam.min() - 1.0) <= 1e-8
+    top = condest.lanczos_max(lambda v: A @ v, p.n, 60, seed=3)
+    assert 0.99 * lam.max() <= top <= lam.max() * (1 + 1e-12)
+    assert condest.gershgorin_max(A) >= lam.max()
+    k = condest.kappa_estimate(A, lu.solve, 60, seed=3)
+    kappa = lam.max() / lam.min()
+    assert 0.99 * kappa <= k <= kappa * (1 + 1e-8)

@@ -43,6 +43,8 @@ def test_noalloc_apply_matches_allocating_apply(precision):
         for r, ref in zip(rs, refs):  # two allocation-free calls in a row
             d_r = torch.from_numpy(np.ascontiguousarray(r.T)).cuda()
             d_z = torch.full_like(d_r, float("nan"))
+            # the call runs on the library's own stream: r must be on the device first
+            torch.cuda.synchronize()
             hm.hm_precond_apply_noalloc(s.sys, nrhs, d_r, d_z)
             torch.cuda.synchronize()
             z = d_z.cpu().numpy().T
