@@ -84,10 +84,15 @@ typedef struct hm_opts {
   int compressor;        /* enum hm_compressor (HM_COMP_RRF)                              */
   int bdlr_depth;        /* BDLR graph-distance depth d (1, the paper's usual setting)   */
   int wait_limit;        /* polls of a bounded device-side wait (the tensor-core GEMM's
-                            mbarrier waits on its MMAs) before the kernel gives up with
+                            mbarrier waits on its MMAs; the first poll never suspends
+                            the thread) before the kernel gives up with
                             HM_ERR_DEVICE_TIMEOUT; 0 = the default, 2^22.  A kernel that
                             gives up still waits (with the default limit) for the MMAs it
                             issued and frees its tensor memory before it returns.        */
+  int inject_wait_timeout; /* fault injection for tests (0 = off): 1 makes every tile of
+                            the tensor-core GEMM end with one more bounded wait, on a
+                            barrier nothing arrives on, so the factorization reports
+                            HM_ERR_DEVICE_TIMEOUT through the path a real timeout takes  */
 } hm_opts;
 
 typedef struct hm_solve_info {
@@ -109,7 +114,8 @@ typedef struct hm_factor_info {
 
 /* Fill *opts with defaults (device 0, mixed precision, nd_leaf 64, hodlr_leaf 64,
    n_c 64, samples 48, restart 30, dofs_per_node 1, compressor HM_COMP_RRF,
-   bdlr_depth 1, wait_limit 0).  Never fails for a non-null pointer.                  */
+   bdlr_depth 1, wait_limit 0, inject_wait_timeout 0).  Never fails for a non-null
+   pointer.                                                                           */
 int hm_default_opts(hm_opts* opts);
 
 /* Create a context on opts->device.  The context owns a CUDA stream (unless one is

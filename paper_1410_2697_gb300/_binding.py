@@ -44,7 +44,7 @@ class HmOpts(C.Structure):
                 ("hodlr_leaf", C.c_int), ("n_c", C.c_int), ("samples", C.c_int),
                 ("seed", C.c_uint64), ("restart", C.c_int), ("hbm_budget", C.c_size_t),
                 ("stream", C.c_void_p), ("dofs_per_node", C.c_int), ("compressor", C.c_int),
-                ("bdlr_depth", C.c_int), ("wait_limit", C.c_int)]
+                ("bdlr_depth", C.c_int), ("wait_limit", C.c_int), ("inject_wait_timeout", C.c_int)]
 
 
 class HmSolveInfo(C.Structure):

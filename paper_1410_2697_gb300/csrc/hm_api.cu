@@ -125,7 +125,8 @@ const char* prof_cat_name(int c) {
       "nd_order", "symbolic", "permute_csr", "scatter_A", "extend_add", "dense_potrf",
       "dense_trsm", "gemm_factor", "sketch", "householder_qr", "jacobi_svd", "leaf_solve",
       "core_lu_inverse", "spd_inverse", "apply_up", "apply_down", "gemm_apply", "spmv", "gmres_dots",
-      "gmres_gs_update", "gmres_small", "vector_ops", "memset", "dense_sweep", "bdlr"};
+      "gmres_gs_update", "gmres_small", "vector_ops", "memset", "dense_sweep", "bdlr", "hodlr_apply_up",
+      "hodlr_apply_down"};
   return (c >= 0 && c < PC_COUNT) ? names[c] : "?";
 }
 
@@ -247,6 +248,7 @@ int hm_default_opts(hm_opts* o) {
   o->compressor = HM_COMP_RRF;
   o->bdlr_depth = 1;
   o->wait_limit = 0;
+  o->inject_wait_timeout = 0;
   return HM_OK;
 }
 
@@ -263,10 +265,11 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   if (o.nd_leaf < 1 || o.hodlr_leaf < 2 || o.hodlr_leaf > 64 || o.n_c < 0 || o.n_c > 128 ||
       o.samples < 1 || o.samples > kmax || o.restart < 1 || o.restart > 200 || o.dofs_per_node < 1 ||
       o.dofs_per_node > 8 || (o.compressor != HM_COMP_RRF && o.compressor != HM_COMP_BDLR) ||
-      o.bdlr_depth < 1 || o.bdlr_depth > 8 || o.wait_limit < 0) {
+      o.bdlr_depth < 1 || o.bdlr_depth > 8 || o.wait_limit < 0 ||
+      (o.inject_wait_timeout != 0 && o.inject_wait_timeout != 1)) {
     set_last_error("option out of range: nd_leaf>=1, 2<=hodlr_leaf<=64, 0<=n_c<=128, "
                    "1<=samples<=" + std::to_string(kmax) + ", 1<=restart<=200, 1<=dofs_per_node<=8, "
-                   "compressor RRF or BDLR, 1<=bdlr_depth<=8, wait_limit>=0");
+                   "compressor RRF or BDLR, 1<=bdlr_depth<=8, wait_limit>=0, inject_wait_timeout 0 or 1");
     return HM_ERR_INVALID_ARG;
   }
   int ndev = 0;
@@ -313,7 +316,10 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
   if (st == HM_OK) st = dense_tc_setup(ctx->max_smem);
   if (st == HM_OK) st = gemm_async_setup(ctx->max_smem);
   if (st == HM_OK) st = solve_setup(ctx->max_smem);
+  if (st == HM_OK) st = hodlr_apply_setup(ctx->max_smem);
   if (st != HM_OK) {
+    cudaMemPoolDestroy(ctx->pool);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return st;
   }

@@ -179,8 +179,10 @@ void gemm_tiles_for(const GemmTask& t, int task_index, int bm, int bn, int nspli
 // FP32 data in memory.  A mbarrier wait that runs out (after wait_limit polls; <= 0: the
 // default) raises HM_ERR_DEVICE_TIMEOUT in err.
 constexpr int kTcBM = 128, kTcBN = 64;
+// inject_timeout != 0: every tile ends with one more bounded wait, on a barrier nothing
+// arrives on, which runs out (fault injection for the tests of the timeout path).
 void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
-                    unsigned* split_cnt, int* err, int wait_limit, cudaStream_t s);
+                    unsigned* split_cnt, int* err, int wait_limit, int inject_timeout, cudaStream_t s);
 int dense_tc_setup(int max_smem);
 
 int dense_fact_setup(int max_dyn_smem);

@@ -51,14 +51,25 @@ __device__ __forceinline__ uint32_t kmaj(int row, int kk, int rows) {
   return (uint32_t)((kk >> 3) * rows * 16 + (row >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
 }
 
+// Waits for the phase of parity `parity` of the mbarrier to complete, `limit` polls at
+// most: the first poll is mbarrier.test_wait (it never suspends the thread), the later
+// ones mbarrier.try_wait (which may suspend it for a while).  Returns false if the phase
+// did not complete within the limit.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
   for (int it = 0; it < limit; ++it) {
     uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
+    if (it == 0)
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(bar), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(bar), "r"(parity)
+          : "memory");
     if (ok) return true;
   }
   return false;
@@ -107,9 +118,10 @@ __device__ __forceinline__ void stage_slice(unsigned char* __restrict__ sl, cons
 __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ tasks,
                                                  const GemmTile* __restrict__ tiles, float* __restrict__ split_ws,
                                                  unsigned* __restrict__ split_cnt, int* __restrict__ err,
-                                                 int wait_limit) {
+                                                 int wait_limit, int inject_timeout) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar_never;  // fault injection: nothing ever arrives on it
   __shared__ uint32_t tmem_slot;
   __shared__ int s_ok, s_last, s_committed;
   const GemmTile tl = tiles[blockIdx.x];
@@ -121,6 +133,7 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar_never)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
     s_committed = 0;  // k slices whose MMAs have been committed
@@ -172,6 +185,9 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
     const int s = (nk - 1) & 1;
     if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((nk - 1) >> 1) & 1), wait_limit)) s_ok = 0;
   }
+  // fault injection: one more bounded wait, on a barrier that no MMA commit arrives on,
+  // so it runs out (right after the last commit, with MMAs possibly still in flight)
+  if (inject_timeout && tid == 0 && s_ok && !mbar_wait(smem_u32(&mbar_never), 0u, wait_limit)) s_ok = 0;
   __syncthreads();
   const bool ok = s_ok != 0;
   if (!ok && tid == 0) {
@@ -253,10 +269,10 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
 }
 
 void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
-                    unsigned* split_cnt, int* err, int wait_limit, cudaStream_t s) {
+                    unsigned* split_cnt, int* err, int wait_limit, int inject_timeout, cudaStream_t s) {
   if (ntiles <= 0) return;
   k_gemm_tc<<<ntiles, 256, kTcSmem, s>>>(tasks, tiles, split_ws, split_cnt, err,
-                                          wait_limit > 0 ? wait_limit : kWaitLimit);
+                                          wait_limit > 0 ? wait_limit : kWaitLimit, inject_timeout);
 }
 
 int dense_tc_setup(int max_smem) {

@@ -116,7 +116,8 @@ static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* bas
   ProfScope ps(sys->ctx, cat, b.tasks.work);
   if (b.tc && sizeof(T) == 4) {
     launch_gemm_tc(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, (float*)sys->plan.d_split_ws,
-                   sys->plan.d_split_cnt, sys->d_err, sys->ctx->opts.wait_limit, sys->ctx->stream);
+                   sys->plan.d_split_cnt, sys->d_err, sys->ctx->opts.wait_limit,
+                   sys->ctx->opts.inject_wait_timeout, sys->ctx->stream);
     return;
   }
   TuneScope ts(sys->ctx, TS_GEMM, b.sig);

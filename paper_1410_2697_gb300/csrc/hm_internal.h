@@ -96,7 +96,7 @@ struct Sig {
 };
 
 // Tunable launch sites and their variants (variant 0 is the built-in default).
-enum TuneSite { TS_GEMM = 1, TS_QR = 2, TS_DENSE_UP = 3, TS_DENSE_DOWN = 4 };
+enum TuneSite { TS_GEMM = 1, TS_QR = 2, TS_DENSE_UP = 3, TS_DENSE_DOWN = 4, TS_HODLR_APPLY = 5 };
 inline uint64_t tune_key(int site, uint64_t sig) { return sig ^ ((uint64_t)site * 0x9e3779b97f4a7c15ull); }
 
 // Host builder of the task buffer (one upload after planning).
@@ -192,7 +192,7 @@ enum ProfCat {
   PC_ND = 0, PC_SYMBOLIC, PC_PERMUTE_CSR, PC_SCATTER, PC_EXTEND_ADD, PC_POTRF, PC_TRSM,
   PC_GEMM_FACTOR, PC_SKETCH, PC_QR, PC_SVD, PC_CHOL_SOLVE, PC_CORE_LU, PC_INVERSE,
   PC_UP, PC_DOWN, PC_GEMM_APPLY, PC_SPMV, PC_DOTS, PC_GS_UPDATE, PC_GMRES_SMALL, PC_VECTOR,
-  PC_MEMSET, PC_SWEEP, PC_BDLR, PC_COUNT
+  PC_MEMSET, PC_SWEEP, PC_BDLR, PC_HODLR_UP, PC_HODLR_DOWN, PC_COUNT
 };
 const char* prof_cat_name(int c);
 
@@ -323,6 +323,28 @@ struct LevelFactorPlan {
   int n_dense = 0, n_hodlr = 0;
 };
 
+// One HODLR front in the fused per-level apply kernels (hm_hodlr_apply.cu).
+constexpr int kHaMaxL = 16;  // deepest HODLR tree the fused kernels take
+struct HApplyTask {
+  const void* X;    // np x xc (ld np): Vtilde = F_pp^{-1} V_f in the first kf columns
+  const void* Bo;   // np x xc (ld np): [V_f | B_0 | ... | B_{L-1}], level l's U on the
+                    // rows of each node's first child, V on the second's
+  const void* G;    // np x 2 (xc - kf) (ld np): G_l = Zhat_l C_l^{-1} per level
+  const void* W;    // nu x kf (ld nu): F_fp ~ W V_f^T
+  const void* F;    // the front (nhat x nhat, ld nhat): leaf inverses on the diagonal
+  int64_t fv_off;   // element offset of the front's vector block (nhat x nrhs)
+  int q, first, np, nu, nhat, L, kf, leaf_off;  // leaf_off: its 2^L + 1 leaf boundaries
+  int kl[kHaMaxL];  // sketch width (column capacity) per level
+  int col[kHaMaxL]; // first column of each level in X / Bo
+};
+// Per-launch sizes of the fused kernels' shared memory (elements, maxima over the
+// level's fronts).
+struct HaDims {
+  int rowsP, rowsU;  // pivot / update rows of one CTA
+  int kmax, kf;      // widest level, widest F_fp
+  int tstore;        // t of the nodes one CTA processes at once (RB columns)
+};
+
 // Solve-time plan for a given number of right-hand sides.
 struct UpItem {
   int q;
@@ -344,6 +366,15 @@ struct LevelSolvePlan {
   };
   std::vector<Height> heights;
   GemmBatch down1, down2;      // tf = W^T (-x_f) ; y += Vtilde tf
+  // fused kernels: one cluster of ha_C CTAs per (HODLR front, group of ha_RB
+  // right-hand sides), one launch per pass (ha_ok: the level fits them)
+  bool ha_ok = false;
+  int ha_C = 1, ha_RB = 1;
+  HaDims ha_dims{};
+  Span<HApplyTask> ha_tasks;
+  Span<int> ha_leaf;
+  uint64_t ha_sig = 0;         // autotuner key (fused kernels or the GEMM path)
+  Work ha_up_work, ha_down_work;
 };
 
 struct SolvePlan {
@@ -576,6 +607,14 @@ int apply_impl_eager(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 // As apply_impl, with z written row-major (element (i, r) at i nrhs + r).
 int apply_impl_rowmajor(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 int solve_setup(int max_smem);
+// The fused HODLR-front apply of one level (upward: down = false, input win; downward:
+// solution rows of the level's fronts into xv).
+// rb: right-hand sides per cluster (1, 2, 4, 8 or 16, at most lp.ha_RB).
+template <typename T>
+int launch_hodlr_apply(bool down, const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys,
+                       SolvePlan* sp, int nrhs, const T* win, T* xv, int rb);
+size_t hodlr_apply_smem(const HaDims& d, int RB, bool down, int es);
+int hodlr_apply_setup(int max_smem);
 int direct_impl(hm_sys_s* sys, int nrhs, const double* d_b, int refine, double* d_x, hm_solve_info* info);
 int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
                double* d_x, hm_solve_info* info);

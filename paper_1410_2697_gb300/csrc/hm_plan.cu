@@ -575,6 +575,109 @@ void release_solve_state(hm_sys_s* sys) {
   sys->gm.m = 0;
 }
 
+// The fused kernels of a level's HODLR fronts: one cluster of C CTAs per front (C a
+// power of two, at most 8, about 64 pivot rows per CTA, at most the number of leaves of
+// the shallowest front so that every CTA owns a node of depth log2 C), RB right-hand
+// sides per cluster (the widest group whose shared memory fits; the autotuner may take
+// a half or a quarter of it, for more clusters).
+static void plan_hodlr_apply(hm_sys_s* sys, SolvePlan* sp, LevelSolvePlan& lp, const std::vector<int>& hod,
+                             int nrhs, int es) {
+  Plan& P = sys->plan;
+  TaskBuf& tb = sp->tb;
+  lp.ha_ok = false;
+  if (hod.empty()) return;
+  int max_np = 0, min_L = 1 << 20;
+  for (int q : hod) {
+    const HFront& h = P.hf[P.fg[q].hodlr];
+    if (h.L > kHaMaxL || (int)h.leaf_lo.size() != (1 << h.L)) return;
+    max_np = std::max(max_np, h.np);
+    min_L = std::min(min_L, h.L);
+  }
+  int C = 1;
+  while (C < 8 && C * 64 < max_np && 2 * C <= (1 << min_L)) C *= 2;
+  int lc = 0;
+  while ((1 << lc) < C) ++lc;
+  std::vector<HApplyTask> tasks;
+  std::vector<int> leafb;
+  HaDims d{};
+  double fbytes_up = 0, fbytes_down = 0, vbytes_up = 0, vbytes_down = 0;
+  for (int q : hod) {
+    const FrontGeom& g = P.fg[q];
+    const HFront& h = P.hf[g.hodlr];
+    HApplyTask t{};
+    t.X = at(sys->d_x, h.bo_off, es);
+    t.Bo = at(sys->d_bo, h.bo_off, es);
+    t.G = at(sys->d_g, h.g_off, es);
+    t.W = at(sys->d_w, h.w_off, es);
+    t.F = at(sys->d_front, g.off, es);
+    t.fv_off = sp->fv_off[q];
+    t.q = q;
+    t.first = sys->h_first[q];
+    t.np = h.np;
+    t.nu = h.nu;
+    t.nhat = g.nhat;
+    t.L = h.L;
+    t.kf = h.kf;
+    t.leaf_off = (int)leafb.size();
+    for (int l = 0; l < h.L; ++l) {
+      t.kl[l] = h.kl[l];
+      t.col[l] = h.col[l];
+      d.kmax = std::max(d.kmax, h.kl[l]);
+    }
+    for (int lo : h.leaf_lo) leafb.push_back(lo);
+    leafb.push_back(h.np);
+    const int span = 1 << (h.L - lc);
+    for (int c = 0; c < C; ++c) {
+      const int j1 = (c + 1) * span;
+      const int p1 = j1 < (int)h.leaf_lo.size() ? h.leaf_lo[j1] : h.np;
+      d.rowsP = std::max(d.rowsP, p1 - h.leaf_lo[c * span]);
+    }
+    d.rowsU = std::max(d.rowsU, (h.nu + C - 1) / C);
+    d.kf = std::max(d.kf, h.kf);
+    tasks.push_back(t);
+    // algorithmic bytes: every factor entry the pass reads, once; the vectors per RHS
+    double leaves = 0, xc = 0;
+    for (size_t i = 0; i < h.leaf_lo.size(); ++i) leaves += (double)(h.leaf_hi[i] - h.leaf_lo[i]) * (h.leaf_hi[i] - h.leaf_lo[i]);
+    for (int l = 0; l < h.L; ++l) xc += h.kl[l];
+    fbytes_up += (double)es * ((double)h.np * h.kf + (double)h.nu * h.kf);
+    fbytes_down += (double)es * ((double)h.np * h.kf + (double)h.nu * h.kf + (double)h.np * 3.0 * xc + leaves);
+    double child = 0;
+    for (int c : sys->children(q)) child += (double)es * nrhs * P.fg[c].nu + 4.0 * P.fg[c].nu;
+    vbytes_up += (double)es * nrhs * ((double)h.np + g.nhat) + child;
+    vbytes_down += (double)es * nrhs * (2.0 * h.np + h.nu) + 4.0 * h.nu;
+  }
+  // widest right-hand-side group whose shared memory fits
+  int RB = nrhs >= 16 ? 16 : nrhs > 4 ? 8 : nrhs > 2 ? 4 : nrhs;
+  auto tstore = [&](int rb) {
+    int m = 0;
+    for (int q : hod) {
+      const HFront& h = P.hf[P.fg[q].hodlr];
+      for (int l = 0; l < h.L; ++l) {
+        const int nodes = l >= lc ? (1 << (l - lc)) : 1;
+        m = std::max(m, nodes * 2 * h.kl[l] * rb);
+      }
+    }
+    return m;
+  };
+  const size_t cap = (size_t)sys->ctx->max_smem;
+  for (; RB >= 1; RB /= 2) {
+    d.tstore = tstore(RB);
+    if (hodlr_apply_smem(d, RB, true, es) <= cap && hodlr_apply_smem(d, RB, false, es) <= cap) break;
+  }
+  if (RB < 1) return;
+  lp.ha_C = C;
+  lp.ha_RB = RB;
+  lp.ha_dims = d;
+  lp.ha_tasks = tb.add(tasks);
+  lp.ha_leaf = tb.add(leafb);
+  lp.ha_up_work = Work{0.0, fbytes_up + vbytes_up};
+  lp.ha_down_work = Work{0.0, fbytes_down + vbytes_down};
+  Sig sg;
+  sg << nrhs << (int64_t)hod.size() << C << RB << d.rowsP << d.rowsU << d.kmax << d.kf;
+  lp.ha_sig = sg.h;
+  lp.ha_ok = true;
+}
+
 int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   auto it = sys->solve_plans.find(nrhs);
   sys->ctx->last_nrhs = nrhs;
@@ -726,6 +829,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     }
     lp.down1 = tb.add_gemm(d1);
     lp.down2 = tb.add_gemm(d2);
+    plan_hodlr_apply(sys, sp.get(), lp, hod, nrhs, es);
   }
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));

@@ -282,14 +282,21 @@ __global__ void __launch_bounds__(NT) k_dense_down(const int* __restrict__ front
 static int rhs_block(int nrhs) { return nrhs >= 16 ? 16 : nrhs > 4 ? 8 : nrhs > 2 ? 4 : nrhs; }
 
 // 64 threads per front when every front of the level is small (more fronts in flight per
-// SM); 256 otherwise.  The autotuner's variant 1 takes the other width.
+// SM); 256 otherwise.  The autotuner's variants 1 and 3 take the other width, 2 and 3 a
+// quarter of the right-hand sides per block (four times the blocks, for levels with few
+// fronts; each block reads the front again).
 static uint64_t dense_sig(const LevelSolvePlan& lp, int nrhs) {
   Sig sg;
   sg << nrhs << lp.dense.count << lp.dense_max_nhat << lp.dense_max_np;
   return sg.h;
 }
 static bool narrow_level(const hm_ctx_s* ctx, int site, const LevelSolvePlan& lp, int nrhs) {
-  return (lp.dense_max_nhat <= 128) != (ctx->tune.variant(site, dense_sig(lp, nrhs)) == 1);
+  const int v = ctx->tune.variant(site, dense_sig(lp, nrhs));
+  return (lp.dense_max_nhat <= 128) != (v == 1 || v == 3);
+}
+static int dense_rhs_block(const hm_ctx_s* ctx, int site, const LevelSolvePlan& lp, int nrhs) {
+  const int rb = rhs_block(nrhs);
+  return ctx->tune.variant(site, dense_sig(lp, nrhs)) >= 2 ? std::max(1, rb / 4) : rb;
 }
 
 template <typename T, int RB, int NT>
@@ -337,7 +344,7 @@ static void dense_down_rb(const LevelSolvePlan& lp, const unsigned char* base, h
 template <typename T>
 static int up_rhs_block(const hm_ctx_s* ctx, const LevelSolvePlan& lp, int nrhs, int max_smem) {
   const int nt = narrow_level(ctx, TS_DENSE_UP, lp, nrhs) ? 64 : 256;
-  int rb = rhs_block(nrhs);
+  int rb = dense_rhs_block(ctx, TS_DENSE_UP, lp, nrhs);
   while (rb > 1 && sizeof(T) * (size_t)rb * (lp.dense_max_nhat + nt) > (size_t)max_smem) rb /= 2;
   return rb;
 }
@@ -363,7 +370,7 @@ static int dense_up(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_
 template <typename T>
 static void dense_down(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
                        int nrhs, T* xv, cudaStream_t s) {
-  switch (rhs_block(nrhs)) {
+  switch (dense_rhs_block(sys->ctx, TS_DENSE_DOWN, lp, nrhs)) {
     case 1: dense_down_rb<T, 1>(lp, base, sys, sp, nrhs, xv, s); break;
     case 2: dense_down_rb<T, 2>(lp, base, sys, sp, nrhs, xv, s); break;
     case 4: dense_down_rb<T, 4>(lp, base, sys, sp, nrhs, xv, s); break;
@@ -393,6 +400,18 @@ static dim3 vgrid(int nitems, int nrhs, int maxlen) {
               (unsigned)std::max(1, (maxlen + kVecChunk - 1) / kVecChunk));
 }
 
+// A level's HODLR fronts take the fused cluster kernels where they fit: variant 0 with
+// a quarter of the plan's widest right-hand-side group per cluster, 2 and 3 with an
+// eighth and a sixteenth (more clusters in flight, each reading the factor again, mostly
+// from L2); variant 1 is the batched-GEMM path.
+static bool fused_level(const hm_ctx_s* ctx, const LevelSolvePlan& lp) {
+  return lp.ha_ok && ctx->tune.variant(TS_HODLR_APPLY, lp.ha_sig) != 1;
+}
+static int fused_rb(const hm_ctx_s* ctx, const LevelSolvePlan& lp) {
+  const int v = ctx->tune.variant(TS_HODLR_APPLY, lp.ha_sig);
+  return std::max(1, lp.ha_RB >> (v == 2 ? 3 : v == 3 ? 4 : 2));
+}
+
 // The launches of one apply (input win, output in the plan's fixed buffer).
 template <typename T>
 static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) {
@@ -410,7 +429,12 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
       TuneScope ts(ctx, TS_DENSE_UP, dense_sig(lp, nrhs));
       HM_TRY(dense_up<T>(lp, base, sys, sp, nrhs, win, s));
     }
-    if (lp.n_hodlr) {
+    if (lp.n_hodlr && fused_level(ctx, lp)) {
+      ProfScope ps(ctx, PC_HODLR_UP, lp.ha_up_work);
+      TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);
+      HM_TRY(launch_hodlr_apply<T>(false, lp, base, sys, sp, nrhs, win, nullptr, fused_rb(ctx, lp)));
+    } else if (lp.n_hodlr) {
+      TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);
       {
         ProfScope ps(ctx, PC_VECTOR, lp.hup_work);
         k_vassemble<T><<<dim3((unsigned)lp.n_hodlr, (unsigned)nrhs), 256, 0, s>>>(
@@ -428,7 +452,12 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
       TuneScope ts(ctx, TS_DENSE_DOWN, dense_sig(lp, nrhs));
       dense_down<T>(lp, base, sys, sp, nrhs, xfix, s);
     }
-    if (lp.n_hodlr) {
+    if (lp.n_hodlr && fused_level(ctx, lp)) {
+      ProfScope ps(ctx, PC_HODLR_DOWN, lp.ha_down_work);
+      TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);  // one key for both passes: one choice
+      HM_TRY(launch_hodlr_apply<T>(true, lp, base, sys, sp, nrhs, nullptr, xfix, fused_rb(ctx, lp)));
+    } else if (lp.n_hodlr) {
+      TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);  // one key for both passes: one choice
       if (lp.hodlr_max_nu > 0) {
         ProfScope ps(ctx, PC_VECTOR, lp.hdown_work);
         k_vgather<T><<<vgrid(lp.n_hodlr, nrhs, lp.hodlr_max_nu), 256, 0, s>>>(

@@ -153,14 +153,16 @@ def test_iteration_cap_reports_no_convergence(precision):
 
 
 def test_tensor_core_wait_that_runs_out_reports_timeout():
-    """The BF16 mode's tensor-core GEMM waits on its MMAs through a bounded mbarrier
-    poll.  With a limit of one poll the wait gives up before the MMAs finish (no fault,
-    no hang: the kernel still drains the MMAs it issued, with the default limit, before
-    it frees its tensor memory): the factorization reports HM_ERR_DEVICE_TIMEOUT.  A new
-    context with the default limit on the same device then factors and solves."""
+    """The BF16 mode's tensor-core GEMM waits on its MMAs through bounded mbarrier polls.
+    The fault injection option adds one more wait per tile, on a barrier that nothing
+    arrives on, limited to 16 polls: it runs out right after the tile's last MMA commit
+    (no fault, no hang: the kernel then drains the MMAs it issued, with the default
+    limit, before it frees its tensor memory), and the factorization reports
+    HM_ERR_DEVICE_TIMEOUT.  A new context without the injection on the same device then
+    factors and solves."""
     from fixtures import hex_cube
     P = hex_cube(20, lognormal_coefficients(20 ** 3, 0.5, seed=97))
-    c = ctx(hm.HM_PREC_MIXED_BF16, wait_limit=1)
+    c = ctx(hm.HM_PREC_MIXED_BF16, wait_limit=16, inject_wait_timeout=1)
     s = hm.hm_analyze(c, P.n, P.rowptr, P.colidx, 3, P.coords)
     with pytest.raises(hm.HmError) as e:
         hm.hm_factor(s, P.values, 1e-4)
