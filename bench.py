@@ -54,11 +54,9 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "hex_lognormal_64^3", "p1_batch_256", "q1_poisson_64x64", "elasticity_hex_40^3",
                              "serving"])
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving: length of the arrival trace")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: length of the arrival trace")
     ap.add_argument("--serve-workers", type=int, default=4)
-    ap.add_argument("--serve-outstanding", type=int, default=64,
-                    help="serving: the client waits while this many requests are unanswered")
-    ap.add_argument("--serve-seq", type=int, default=6,
+    ap.add_argument("--serve-seq", type=int, default=24,
                     help="serving: requests of the trace replayed sequentially in FP64 (baseline)")
     ap.add_argument("--nrhs", type=int, default=None, help="default: the workload's")
     ap.add_argument("--m", type=int, default=1024, help="elements per side (1024 = the workload)")
@@ -70,6 +68,8 @@ def parse_args():
     ap.add_argument("--bdlr-depth", type=int, default=1, help="BDLR graph-distance depth")
     ap.add_argument("--sweep-tol", action="store_true",
                     help="accuracy sweep over the compression tolerance (Q1 lognormal, --m elements)")
+    ap.add_argument("--adaptive-rank", action="store_true",
+                    help="double the sketch width of front levels whose blocks reach it (hm_opts.adaptive_rank)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner pass of the warm-up (built-in launch variants)")
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -243,6 +243,16 @@ def kernel_roofline(e: dict, precision: str, peaks, clocks) -> dict:
     launches = max(e["launches"], 1)
     per_launch_ms = e["ms"] / launches
     hbm = (peaks or {}).get("hbm_gbs") or 6800.0
+    if e.get("name") == "gemm_tensor_core":
+        # tcgen05 GEMMs: BF16 operands (the BF16 sampling mode) against the BF16 peak; FP32
+        # products as 3xTF32 (three TF32 MMAs per product, TF32 at half the BF16 rate)
+        bf16 = (peaks or {}).get("bf16_tflops") or 1900.0
+        peak = bf16 if precision == "bf16" else bf16 * 0.5 / 3.0
+        achieved = (e["flops"] / launches) / (per_launch_ms * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "launches": e["launches"], "avg_launch_ms": per_launch_ms,
+                "peak_source": ("measured" if peaks else "fallback") + (
+                    " BF16" if precision == "bf16" else " BF16 x 0.5 (TF32 rate) / 3 (three MMAs per product)")}
     alu = alu_peak_tflops(precision, (clocks or {}).get("sm_max_mhz"))
     ridge = alu * 1e12 / (hbm * 1e9)
     if e["flops"] > 0 and e["flops"] >= ridge * e["bytes"]:
@@ -265,11 +275,11 @@ def roofline(prof: dict, precision: str, peaks, clocks) -> dict:
     for c, e in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
         if e["ms"] <= 0:
             continue
-        r = kernel_roofline(e, precision, peaks, clocks)
+        r = kernel_roofline(dict(e, name=c), precision, peaks, clocks)
         table[c] = {"bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"], "frac": r["frac"],
                     "share": e["ms"] / total, "launches": e["launches"]}
     cat = max(prof, key=lambda c: prof[c]["ms"])
-    rl = {"kernel": cat, **kernel_roofline(prof[cat], precision, peaks, clocks)}
+    rl = {"kernel": cat, **kernel_roofline(dict(prof[cat], name=cat), precision, peaks, clocks)}
     rl["traffic"] = ncu_traffic(cat)
     rl["share_of_profiled_time"] = prof[cat]["ms"] / total
     rl["kernels"] = table
@@ -360,6 +370,7 @@ def run_ours(args, rank, world, local):
         o.dofs_per_node = W.dofs
         o.compressor = hm.abi.HM_COMP_BDLR if args.compressor == "bdlr" else hm.abi.HM_COMP_RRF
         o.bdlr_depth = args.bdlr_depth
+        o.adaptive_rank = 1 if args.adaptive_rank else 0
         o.stream = stream.cuda_stream
         return hm.hm_create(o)
 
@@ -480,7 +491,7 @@ def run_ours(args, rank, world, local):
     value = whole_job_rate(nsolve, args.steps, world, total_max)
     fi, si = infos[-1]
     peaks = load_peaks()
-    rl = roofline(prof, "f64" if W.headline == "FP64" else "f32", peaks, clk)
+    rl = roofline(prof, {"FP64": "f64", "MIXED_BF16": "bf16"}.get(W.headline, "f32"), peaks, clk)
     kernels = sum(v["kernels"] for v in prof.values())  # per profiled pass of K steps
     per_sorted = sorted(per)
     p50 = statistics.median(per)
@@ -501,7 +512,9 @@ def run_ours(args, rank, world, local):
         "p50_ms": p50, "p99_ms": p99,
         "gmres_iters": si["iters"], "relres": relres,
         "factor": {"nfronts": fi["nfronts"], "n_hodlr": fi["n_hodlr"], "max_rank": fi["max_rank"],
-                   "rank_capped": fi["rank_capped"], "factor_bytes": fi["factor_bytes"]},
+                   "rank_capped": fi["rank_capped"], "factor_bytes": fi["factor_bytes"],
+                   "max_sketch_width": fi["max_width"], "refactorizations": fi["refactorizations"],
+                   "adaptive_rank": bool(args.adaptive_rank)},
         "fp64_plain": {"value": nsolve * k64 * world / (total64 * 1e-3), "ms_per_step": total64 / k64,
                        "steps": k64, "gmres_iters": infos64[-1][1]["iters"]},
         "roofline": rl,
@@ -657,14 +670,20 @@ def run_reference(args, rank, world):
 
 
 def run_serving(args):
-    """Serving stream: Poisson arrivals (mean 200 requests/s, seed 6) over 24 matrices --
-    8 each of the Q1 64^2, Q1 1024^2 (lognormal sigma 1) and hex 64^3 (lognormal sigma 0.5)
-    sizes with coefficient seeds 11-18, 21-28, 31-38 -- picked uniformly (seed 7), 1-64
-    right-hand sides each (seed 7), served by hm_server (factor on first miss, resident
-    after, 150 GB HBM budget, continuous batching per matrix).  The client submits at the
-    arrival times but holds back while `--serve-outstanding` requests are unanswered (host
-    memory for the answers).  Baseline: the first `--serve-seq` requests replayed one
+    """Serving stream: Poisson arrivals (mean 200 requests/s, seed 6) for `--serve-seconds`
+    (60 by default) over 24 matrices -- 8 each of the Q1 64^2, Q1 1024^2 (lognormal sigma 1)
+    and hex 64^3 (lognormal sigma 0.5) sizes with coefficient seeds 11-18, 21-28, 31-38 --
+    picked uniformly (seed 7), 1-64 right-hand sides each (seed 7), served by hm_server
+    (factor on first miss, resident after, 150 GB HBM budget, continuous batching: a
+    request joins the running GMRES session of its matrix at the next restart boundary).
+    Open loop: every request is submitted at its arrival time whatever is outstanding;
+    the answers of all requests for one matrix go to one reused host buffer (the client
+    checks each request's relative residual from its solve info, not its answer), which
+    keeps the client's host memory bounded.  Throughput = requests / (time to the last
+    answer).  Baseline: `--serve-seq` requests drawn from the trace (seed 8) replayed one
     after another through an FP64 server with one worker."""
+    import threading as th
+
     import numpy as np
 
     import paper_1410_2697_gb300 as hm
@@ -683,57 +702,70 @@ def run_serving(args):
     # one read-only block of right-hand sides per matrix; request k uses its first nrhs columns
     rhs = [np.asfortranarray(np.random.Generator(np.random.PCG64(100 + i)).uniform(-1, 1, (m.n, 64)))
            for i, m in enumerate(mats)]
+    outs = [np.zeros((m.n, 64), order="F") for m in mats]
 
     def serve(precision, nworkers, reqs, sequential):
         o = hm.hm_default_opts()
         o.precision = precision
         o.hbm_budget = 150 * (1 << 30)
+        o.adaptive_rank = 1 if args.adaptive_rank else 0
         srv = hm.hm_server_create(o, nworkers=nworkers, max_batch_rhs=64)
         ids = [hm.hm_server_add_matrix(srv, m, 1e-4) for m in mats]
-        pending, lat, worst, t0 = [], [], 0.0, time.perf_counter()
+        lat, worst, fails = [], [0.0], [0]
+        rids = []
+        done = th.Event()
 
-        def finish(item):
-            nonlocal worst
-            mi, x, rid = item
-            r = hm.hm_server_wait(srv, rid)
-            assert r["status"] == 0, r
-            lat.append(r["latency_ms"])
-            worst = max(worst, r["relres"])
+        def waiter():  # answers in submission order (a request's wait returns when it is done)
+            k = 0
+            while True:
+                while k >= len(rids):
+                    if done.is_set() and k >= len(rids):
+                        return
+                    time.sleep(0.0005)
+                r = hm.hm_server_wait(srv, rids[k])
+                if r["status"] != 0:
+                    fails[0] += 1
+                lat.append(r["latency_ms"])
+                worst[0] = max(worst[0], r["relres"])
+                k += 1
 
+        wt = th.Thread(target=waiter)
+        wt.start()
+        t0 = time.perf_counter()
         for (ta, mi, nr) in reqs:
             if not sequential:
                 while time.perf_counter() - t0 < ta:
                     time.sleep(0.0002)
-                while len(pending) >= args.serve_outstanding:
-                    finish(pending.pop(0))
-            x = np.zeros((mats[mi].n, nr), order="F")
-            pending.append((mi, x, hm.hm_server_submit(srv, ids[mi], rhs[mi][:, :nr], x)))
+            rids.append(hm.hm_server_submit(srv, ids[mi], rhs[mi][:, :nr], outs[mi][:, :nr]))
             if sequential:
-                finish(pending.pop(0))
-        while pending:
-            finish(pending.pop(0))
+                hm.hm_server_wait(srv, rids[-1])
+        done.set()
+        wt.join()
         elapsed = time.perf_counter() - t0
         st = hm.hm_server_get_stats(srv)
         hm.hm_server_destroy(srv)
-        return elapsed, st, lat, worst
+        return elapsed, st, lat, worst[0], fails[0]
 
-    el, st, lat, worst = serve(hm.HM_PREC_MIXED, args.serve_workers, trace, False)
+    el, st, lat, worst, fails = serve(hm.HM_PREC_MIXED, args.serve_workers, trace, False)
     k = min(args.serve_seq, len(trace))
-    el64, st64, lat64, _ = serve(hm.HM_PREC_FP64, 1, trace[:k], True)
+    pick = np.random.Generator(np.random.PCG64(8)).choice(len(trace), size=k, replace=False)
+    el64, st64, lat64, _, _ = serve(hm.HM_PREC_FP64, 1, [trace[i] for i in sorted(pick)], True)
     rhs_total = sum(nr for _, _, nr in trace)
     return {
         "metric": METRIC, "value": len(trace) / el, "unit": "requests/s", "n_gpus": 1, "steps": 1,
         "warmup": 0, "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 factor/apply + f64 GMRES", "data": "synthetic",
         "config": {"workload": "serving", "matrices": "8 x Q1 64^2, 8 x Q1 1024^2, 8 x hex 64^3",
-                   "arrivals": f"Poisson 200/s for {args.serve_seconds} s ({len(trace)} requests, "
+                   "arrivals": f"Poisson 200/s for {args.serve_seconds} s, open loop ({len(trace)} requests, "
                                f"{rhs_total} right-hand sides)", "rtol": RTOL, "tol": 1e-4,
                    "workers": args.serve_workers, "max_batch_rhs": 64, "hbm_budget_gb": 150,
-                   "client_outstanding_cap": args.serve_outstanding},
+                   "answers": "one reused host buffer per matrix; relres checked per request"},
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "rhs_per_s": rhs_total / el, "relres": worst,
-        "server": {k2: st[k2] for k2 in ("completed", "failed", "batches", "batched_rhs", "factorizations",
-                                          "evictions", "device_bytes")},
+        "failed_requests": fails,
+        "server": {k2: st[k2] for k2 in ("completed", "failed", "batches", "batched_rhs", "joined",
+                                          "factorizations", "evictions", "device_bytes")},
         "fp64_sequential": {"value": k / el64, "unit": "requests/s", "requests": k,
+                            "sample": "requests drawn from the trace (seed 8), replayed one after another",
                             "p50_ms": st64["p50_ms"], "p99_ms": st64["p99_ms"]},
     }
 

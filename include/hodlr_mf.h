@@ -72,7 +72,8 @@ typedef struct hm_opts {
   int hodlr_leaf;        /* HODLR leaves hold <= hodlr_leaf rows (64)                    */
   int n_c;               /* fronts whose pivot block has > n_c unknowns become HODLR
                             fronts; smaller ones stay dense (the paper's n_c)            */
-  int samples;           /* randomized range finder sketch width cap k (>= 1)            */
+  int samples;           /* randomized range finder sketch width cap k (1 .. 96; FP64:
+                            1 .. 64)                                                     */
   uint64_t seed;         /* seed of the Philox4x32-10 sketch                             */
   int restart;           /* GMRES restart length m (30)                                  */
   size_t hbm_budget;     /* bytes the context may allocate on the device; 0 = no limit  */
@@ -89,6 +90,13 @@ typedef struct hm_opts {
                             HM_ERR_DEVICE_TIMEOUT; 0 = the default, 2^22.  A kernel that
                             gives up still waits (with the default limit) for the MMAs it
                             issued and frees its tensor memory before it returns.        */
+  int adaptive_rank;     /* 1 (FP32 and BF16 modes; ignored in FP64): a compressed block
+                            whose rank reaches its sketch width was truncated by the
+                            width, not by tol: the factorization then doubles the sketch
+                            width of that front level (up to 96) and
+                            factors again, until no block is capped or no width can
+                            grow; the widths are remembered for later analyses of the
+                            same shape in this context (0 = off)                        */
   int inject_wait_timeout; /* fault injection for tests (0 = off): 1 makes every tile of
                             the tensor-core GEMM end with one more bounded wait, on a
                             barrier nothing arrives on, so the factorization reports
@@ -110,12 +118,14 @@ typedef struct hm_factor_info {
   int32_t rank_capped;   /* blocks whose rank reached their sketch width                 */
   double factor_bytes;   /* bytes of factor data read by one preconditioner apply        */
   double front_bytes;    /* bytes of dense front storage                                 */
+  int32_t refactorizations; /* extra factorizations the adaptive rank rule ran            */
+  int32_t max_width;     /* largest sketch width in use (per front level)                 */
 } hm_factor_info;
 
 /* Fill *opts with defaults (device 0, mixed precision, nd_leaf 64, hodlr_leaf 64,
    n_c 64, samples 48, restart 30, dofs_per_node 1, compressor HM_COMP_RRF,
-   bdlr_depth 1, wait_limit 0, inject_wait_timeout 0).  Never fails for a non-null
-   pointer.                                                                           */
+   bdlr_depth 1, wait_limit 0, adaptive_rank 0, inject_wait_timeout 0).  Never fails
+   for a non-null pointer.                                                            */
 int hm_default_opts(hm_opts* opts);
 
 /* Create a context on opts->device.  The context owns a CUDA stream (unless one is
@@ -220,20 +230,24 @@ int hm_direct_solve(hm_sys_t sys, int32_t nrhs, const double* b, int32_t refine,
  * another is more than 3% faster) in the CONTEXT, so later systems of the same shapes
  * analysed on it use the choices too; then refactors sys with them.  values may be host
  * or device memory.  *nsites (may be NULL) = number of sites timed.  The variants
- * compute the same quantities (GEMM variants bit-identically; the QR variants to
- * rounding).  Requires the launch profiler off (HM_ERR_STATE).  1 <= nrhs <= 64,
- * 1 <= reps <= 16.
+ * compute the same quantities (the SIMT GEMM variants bit-identically; the tensor-core
+ * GEMM, the QR and the apply variants to rounding).  Requires the launch profiler off
+ * (HM_ERR_STATE).  1 <= nrhs <= 64, 1 <= reps <= 16.
  */
 int hm_autotune(hm_sys_t sys, const double* values, double tol, int32_t nrhs, int32_t reps,
                 int32_t* nsites);
 
 /* Fix every tunable launch site of the context to one variant (0 = the built-in
    default; GEMM sites: 1 deeper k-slices, 2 cp.async staging, 3 FP32 128 x 128 tiles
-   where the batch has such products; QR sites: 1 global memory; dense apply levels:
-   1 the other thread count; a variant a site lacks acts as 0), or -1 to return to the
-   autotuner's choices.  For reproducing a configuration and for tests; hm_autotune
-   clears it.  Applies to launches issued afterwards (apply graphs captured earlier
-   keep their variants until the solve plan is rebuilt).                              */
+   where the batch has such products, 4 FP32 on the tensor cores (3xTF32, tcgen05) where
+   the batch has a product of at least 64 x 32 x 64; QR sites: 1 global memory; dense
+   apply levels: 1 the other thread count, 2 and 3 a quarter of the right-hand sides per
+   block (with the default / the other thread count); HODLR-front apply levels: 1 the
+   batched-GEMM path, 0 / 2 / 3 the fused cluster kernels with a quarter / an eighth / a
+   sixteenth of the widest right-hand-side group per cluster; a variant a site lacks acts
+   as 0), or -1 to return to the autotuner's choices.  For reproducing a configuration
+   and for tests; hm_autotune clears it.  Applies to launches issued afterwards (apply
+   graphs captured earlier keep their variants until the solve plan is rebuilt).      */
 int hm_tune_force(hm_ctx_t ctx, int32_t variant);
 
 /*
@@ -330,15 +344,20 @@ const char* hm_last_error(void);
  * Serving (many matrices, requests arriving over time).  A server owns nworkers worker
  * threads, each with its own context (stream, memory pool and hbm_budget / nworkers of
  * the budget in *opts; opts->stream is ignored).  Registered matrices (host copies of
- * the CSR, FP64 values and lattice coordinates) are bound to workers round robin and
- * analysed + factored on their first request; the factorization then stays resident
- * until evicted (least recently used first) to admit another matrix within the budget.
- * A free worker takes its oldest waiting request and joins every waiting request for
- * the same matrix, up to max_batch_rhs right-hand sides, into one hm_solve (continuous
- * batching), in column chunks that keep the GMRES workspace within a quarter of the
- * worker's budget; workers run concurrently, so different matrices overlap on the GPU.  Each
- * right-hand side is its own GMRES instance, so a request's answer equals (to rounding)
- * the answer it gets alone.  Latency = completion - submission, host clock.
+ * the CSR, FP64 values and lattice coordinates) are analysed + factored on their first
+ * request by the worker that takes it, and the factorization stays resident in that
+ * worker's context until evicted (least recently used first) to admit another matrix
+ * within the budget.  Requests wait in one queue; a free worker takes the oldest one
+ * whose matrix no other worker is serving (and that is resident on it or nowhere) and
+ * runs a GMRES session on the matrix: a fixed number of right-hand-side slots (twice the
+ * starting columns, at most max_batch_rhs, within a quarter of the worker's budget for
+ * the GMRES workspace), every waiting request for the matrix that fits put in; after
+ * every restart cycle the requests whose columns all converged leave with their answers
+ * and requests that arrived meanwhile take the free slots (continuous batching).  Each
+ * right-hand side is its own GMRES instance with its own restart boundaries, so a
+ * request's answer equals (to rounding) the answer it gets alone.  Workers run
+ * concurrently, so different matrices overlap on the GPU.  Latency = completion -
+ * submission, host clock.
  *
  *   hm_server_submit: b, x are host arrays (n x nrhs column-major) that must stay valid
  *   until hm_server_wait returns for the request; nrhs <= max_batch_rhs.
@@ -355,6 +374,7 @@ typedef struct hm_server_stats {
   int64_t evictions;             /* resident systems destroyed to admit others          */
   double p50_ms, p99_ms;         /* latency percentiles of the successful requests      */
   double device_bytes;           /* device memory held by the workers' contexts         */
+  int64_t joined;                /* requests that entered a session already running     */
 } hm_server_stats;
 
 int hm_server_create(const hm_opts* opts, int32_t nworkers, int32_t max_batch_rhs, hm_server_t* out);

@@ -49,6 +49,9 @@ class Params:
     samples: int = 64              # RRF sketch width k (capped by the block's size)
     seed: int = 0x5EED             # RRF sketch seed
     compress_ff: bool = False
+    level_samples: dict | None = None  # sketch width per front level (tree depth); default samples
+    adaptive: bool = False         # grow the width of a level whose blocks hit it (see factor)
+    max_samples: int = 96          # largest width the adaptive rule may reach (64 for FP64 parity)
 
 
 @dataclass
@@ -62,7 +65,9 @@ class Front:
     V: np.ndarray | None = None
 
 
-def _compressor(prm: Params, front: int, kind: int, graph=None, npv: int = 0):
+def _compressor(prm: Params, front: int, kind: int, graph=None, npv: int = 0, samples: int | None = None):
+    width = prm.samples if samples is None else samples
+
     def comp(B, level, index, lo=None, mid=None, hi=None):
         if prm.compressor == "svd":
             return hodlr.truncated_svd(B, prm.tol)
@@ -72,16 +77,64 @@ def _compressor(prm: Params, front: int, kind: int, graph=None, npv: int = 0):
             off = npv if kind == 2 else 0  # F_ff nodes sit after the pivot positions
             X = np.arange(off + lo, off + mid) if kind != 1 else np.arange(npv, npv + B.shape[0])
             Y = np.arange(off + mid, off + hi) if kind != 1 else np.arange(0, npv)
-            cap = min(prm.samples, B.shape[0], B.shape[1])
+            cap = min(width, B.shape[0], B.shape[1])
             I, J = bdlr.select(graph, X, Y, prm.bdlr_depth, cap)
             return bdlr.compress(B, I, J, prm.tol)
-        k = min(prm.samples, B.shape[0], B.shape[1])
+        k = min(width, B.shape[0], B.shape[1])
         Om = sketch(B.shape[1], k, block_id(front, kind, level, index), prm.seed)
         return hodlr.randomized_range_finder(B, prm.tol, Om)
     return comp
 
 
 def factor(Ap: sp.csr_matrix, et: ETree, sym: Symbolic, prm: Params, keep: bool = False):
+    """HODLR-MF factorization.  With ``prm.adaptive`` the tolerance rule of Section 2.2
+    decides the ranks: a block whose rank reached its sketch width was cut by the width,
+    not by tol, so the width of every front level (tree depth) holding such a block is
+    doubled (up to ``max_samples`` and the level's largest block dimension) and the
+    factorization is repeated, at most four times; the widths used are returned in
+    ``trace["widths"]`` when ``keep`` is set, and always in ``factor.last_widths``."""
+    widths = dict(prm.level_samples or {})
+    for _ in range(5):
+        fronts, trace = _factor_once(Ap, et, sym, prm, widths, keep)
+        if not prm.adaptive:
+            break
+        capped, room = _capped_levels(fronts, et, prm, widths)
+        grow = False
+        for lv in sorted(capped):
+            w = widths.get(lv, prm.samples)
+            if w < min(prm.max_samples, room[lv]):
+                widths[lv] = min(2 * w, prm.max_samples, room[lv])
+                grow = True
+        if not grow:
+            break
+    factor.last_widths = dict(widths)
+    if keep:
+        trace["widths"] = dict(widths)
+    return fronts, trace
+
+
+def _capped_levels(fronts, et: ETree, prm: Params, widths: dict):
+    """Front levels holding a block whose rank equals its sketch width while the block
+    is larger than that width; and, per level, the largest block dimension."""
+    capped, room = set(), {}
+    for p, fr in enumerate(fronts):
+        if fr.kind != "hodlr":
+            continue
+        lv = int(et.level[p])
+        w = widths.get(lv, prm.samples)
+        blocks = [(fr.W.shape[1], fr.W.shape[0], fr.V.shape[0])] if fr.W.shape[0] else []
+        for node in hodlr.iter_nodes(fr.H):
+            if node.children:
+                a, b = node.children
+                blocks.append((node.U.shape[1], a.hi - a.lo, b.hi - b.lo))
+        for r, m, n in blocks:
+            room[lv] = max(room.get(lv, 0), min(m, n))
+            if r >= min(w, m, n) and min(w, m, n) < min(m, n):
+                capped.add(lv)
+    return capped, room
+
+
+def _factor_once(Ap: sp.csr_matrix, et: ETree, sym: Symbolic, prm: Params, widths: dict, keep: bool):
     nf = et.nfronts
     fronts: list = [None] * nf
     updates: list = [None] * nf
@@ -102,12 +155,13 @@ def factor(Ap: sp.csr_matrix, et: ETree, sym: Symbolic, prm: Params, keep: bool 
             fronts[p] = Front(npv, "dense", cho=cho, Ffp=Ffp.copy())
         else:
             graph = bdlr.front_graph(Ap, front_indices(et, sym, p)) if prm.compressor == "bdlr" else None
-            H = hodlr.build(Fpp, prm.leaf, prm.tol, _compressor(prm, p, 0, graph, npv))
+            w = widths.get(int(et.level[p]), prm.samples)
+            H = hodlr.build(Fpp, prm.leaf, prm.tol, _compressor(prm, p, 0, graph, npv, w))
             hodlr.factor(H)
-            W, V = _compressor(prm, p, 1, graph, npv)(Ffp, 0, 0) if Ffp.shape[0] else \
+            W, V = _compressor(prm, p, 1, graph, npv, w)(Ffp, 0, 0) if Ffp.shape[0] else \
                 (np.zeros((0, 0)), np.zeros((npv, 0)))
             if prm.compress_ff and Fff.shape[0]:
-                Fff = hodlr.to_dense(hodlr.build(Fff, prm.leaf, prm.tol, _compressor(prm, p, 2, graph, npv)))
+                Fff = hodlr.to_dense(hodlr.build(Fff, prm.leaf, prm.tol, _compressor(prm, p, 2, graph, npv, w)))
             T = V.T @ hodlr.solve(H, V)
             updates[p] = Fff - W @ T @ W.T
             fronts[p] = Front(npv, "hodlr", H=H, W=W, V=V)

@@ -44,7 +44,8 @@ class HmOpts(C.Structure):
                 ("hodlr_leaf", C.c_int), ("n_c", C.c_int), ("samples", C.c_int),
                 ("seed", C.c_uint64), ("restart", C.c_int), ("hbm_budget", C.c_size_t),
                 ("stream", C.c_void_p), ("dofs_per_node", C.c_int), ("compressor", C.c_int),
-                ("bdlr_depth", C.c_int), ("wait_limit", C.c_int), ("inject_wait_timeout", C.c_int)]
+                ("bdlr_depth", C.c_int), ("wait_limit", C.c_int), ("adaptive_rank", C.c_int),
+                ("inject_wait_timeout", C.c_int)]
 
 
 class HmSolveInfo(C.Structure):
@@ -55,13 +56,14 @@ class HmSolveInfo(C.Structure):
 class HmFactorInfo(C.Structure):
     _fields_ = [("nfronts", C.c_int32), ("nlevels", C.c_int32), ("n_hodlr", C.c_int32),
                 ("max_rank", C.c_int32), ("rank_capped", C.c_int32), ("factor_bytes", C.c_double),
-                ("front_bytes", C.c_double)]
+                ("front_bytes", C.c_double), ("refactorizations", C.c_int32), ("max_width", C.c_int32)]
 
 
 class HmServerStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("batches", C.c_int64),
                 ("batched_rhs", C.c_int64), ("factorizations", C.c_int64), ("evictions", C.c_int64),
-                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("device_bytes", C.c_double)]
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("device_bytes", C.c_double),
+                ("joined", C.c_int64)]
 
 
 class HmProfEntry(C.Structure):

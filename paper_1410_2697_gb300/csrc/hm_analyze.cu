@@ -998,6 +998,18 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   }
   HM_TRY(check_device_error(sys, "analyze: relative maps"));
   host_mark("analyze: relative maps");
+  {
+    // shape signature of the analysis: sketch widths learned by the adaptive rank rule
+    // for the same shape (and precision) are reused
+    uint64_t h = 0x9E3779B97F4A7C15ull ^ (uint64_t)sys->n ^ ((uint64_t)sys->nf << 32) ^ (uint64_t)sys->precision;
+    auto mix = [&](uint64_t v) { h = (h ^ v) * 0x100000001B3ull; h ^= h >> 29; };
+    for (int q = 0; q < sys->nf; ++q)
+      mix(((uint64_t)(sys->h_first[q + 1] - sys->h_first[q]) << 40) ^ ((uint64_t)sys->h_nupd[q] << 8) ^
+          (uint64_t)sys->h_level[q]);
+    sys->shape_sig = h;
+    auto it = sys->ctx->level_widths.find(h);
+    sys->level_width = it != sys->ctx->level_widths.end() ? it->second : std::vector<int>();
+  }
   HM_TRY(build_plan(sys));
   host_mark("analyze: build_plan");
   HM_TRY(dev_alloc(sys, (void**)&sys->d_amap, sizeof(int64_t) * sys->nnz));

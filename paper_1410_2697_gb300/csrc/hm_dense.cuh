@@ -150,6 +150,9 @@ template <typename T>
 void launch_trsm(const TrsmTask* tasks, int ntasks, int maxn, cudaStream_t s);
 template <typename T>
 void launch_qr(const QrTask* tasks, int ntasks, int maxm, int64_t maxmk, int max_smem, cudaStream_t s);
+// Bytes the shared-memory panel QR needs beyond its panel and reflector block (its static
+// shared memory and a margin), es = element size.
+size_t qr_smem_overhead(int es);
 template <typename T>
 void launch_tsqr(const TsqrTask* tasks, int ntasks, const TsqrBlock* blocks, int nblocks, size_t smem_block,
                  size_t smem_stack, T* scratch, cudaStream_t s);
@@ -183,6 +186,10 @@ constexpr int kTcBM = 128, kTcBN = 64;
 // arrives on, which runs out (fault injection for the tests of the timeout path).
 void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
                     unsigned* split_cnt, int* err, int wait_limit, int inject_timeout, cudaStream_t s);
+// FP32 products at FP32 accuracy on the tensor cores (tcgen05 kind::tf32, every operand
+// split into a TF32 hi part and its remainder, three MMAs per step), same tiles.
+void launch_gemm_tf32x3(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
+                        unsigned* split_cnt, int* err, int wait_limit, cudaStream_t s);
 int dense_tc_setup(int max_smem);
 
 int dense_fact_setup(int max_dyn_smem);

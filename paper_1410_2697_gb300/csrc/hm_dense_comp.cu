@@ -714,6 +714,10 @@ constexpr size_t qr_smem_static() {
   return (512 + 256 / kQrNB * kQrNB * kQrNB + 16 * kQrNB * (kQrNB - 1) / 2 + kQrNB * kQrNB) * sizeof(T);
 }
 
+size_t qr_smem_overhead(int es) {
+  return (es == 8 ? qr_smem_static<double>() : qr_smem_static<float>()) + 1024;
+}
+
 template <typename T>
 void launch_qr(const QrTask* tasks, int ntasks, int maxm, int64_t maxmk, int max_smem, cudaStream_t s) {
   if (ntasks <= 0) return;
@@ -725,7 +729,11 @@ void launch_qr(const QrTask* tasks, int ntasks, int maxm, int64_t maxmk, int max
     return;
   }
   const size_t vs = (size_t)maxm * kQrNB * sizeof(T);
-  if (vs + 8192 <= (size_t)max_smem) {
+  static const size_t blocked_static = [] {  // the kernel's own static shared memory
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k_qr_blocked<T>) == cudaSuccess ? (size_t)a.sharedSizeBytes : (size_t)32768;
+  }();
+  if (vs + blocked_static + 1024 <= (size_t)max_smem) {
     k_qr_blocked<T><<<ntasks, 512, vs, s>>>(tasks);
     return;
   }

@@ -17,6 +17,14 @@
 // tile, but first waits, with the default limit, for the last MMA group it committed
 // (tcgen05.commit tracks every MMA issued before it), so the tensor memory is freed only
 // once no MMA can still write it.
+//
+// The same kernel in its second mode computes FP32 products at FP32 accuracy on the
+// tensor cores (kind::tf32): every operand x is split while it is staged into
+// hi = x rounded to TF32 (10 mantissa bits, round to nearest) and lo = x - hi (exact in
+// FP32), and each k slice runs three MMAs per 8-deep step, hi*hi + hi*lo + lo*hi, into
+// the same FP32 accumulator (the lo*lo term is below FP32 rounding).  32-deep slices of
+// FP32 take the same 128 bytes per row as the 64-deep BF16 slices, so the core-matrix
+// layout and descriptors are shared; the stage holds four buffers (A and B, hi and lo).
 #include <cuda_bf16.h>
 
 #include "hm_dense.cuh"
@@ -25,10 +33,17 @@ namespace hm {
 
 namespace {
 
-constexpr int TM = 128, TN = 64, TK = 64;                 // tile and k slice
-constexpr int kStageA = TM * TK * 2, kStageB = TN * TK * 2;  // bytes of one slice (BF16)
-constexpr int kTcSmem = 2 * (kStageA + kStageB);           // double-buffered
-constexpr int kWaitLimit = 1 << 22;                        // default mbarrier polls before giving up
+constexpr int TM = 128, TN = 64;                           // output tile
+constexpr int kSliceBytes = 128;                             // bytes of one row of a k slice
+constexpr int kStageA = TM * kSliceBytes, kStageB = TN * kSliceBytes;  // one operand copy
+constexpr int kTcSmem = 2 * (kStageA + kStageB);             // BF16: double-buffered A, B
+constexpr int kTf32Smem = 2 * 2 * (kStageA + kStageB);       // TF32x3: A, B in hi and lo, double-buffered
+constexpr int kWaitLimit = 1 << 22;                          // default mbarrier polls before giving up
+enum TcMode { kModeBf16 = 0, kModeTf32x3 = 1 };
+// k elements per slice (128 bytes per row) and per MMA instruction (32 bytes)
+template <int MODE> struct TcShape;
+template <> struct TcShape<kModeBf16> { static constexpr int TK = 64, KI = 16; };
+template <> struct TcShape<kModeTf32x3> { static constexpr int TK = 32, KI = 8; };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -41,14 +56,29 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
-// N >> 3 and M >> 4.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptors: FP32 accumulator (bits 4-5 = 1), A and B K-major, N >> 3 at
+// bit 17, M >> 4 at bit 24; operand types at bits 7-9 and 10-12: kind::f16 with BF16
+// (1), kind::tf32 with TF32 (2).
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                ((uint32_t)(TM >> 4) << 24);
 
-// byte offset of element (row, kk) of a K-major slice with `rows` rows
+// byte offset of element (row, kk) of a K-major slice with `rows` rows: core matrices of
+// 8 rows x 16 bytes (8 BF16 or 4 FP32 elements along k), K-adjacent ones 16 * rows bytes
+// apart, row-group adjacent ones 128 bytes apart
+template <int MODE>
 __device__ __forceinline__ uint32_t kmaj(int row, int kk, int rows) {
-  return (uint32_t)((kk >> 3) * rows * 16 + (row >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+  if (MODE == kModeBf16)
+    return (uint32_t)((kk >> 3) * rows * 16 + (row >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+  return (uint32_t)((kk >> 2) * rows * 16 + (row >> 3) * 128 + (row & 7) * 16 + (kk & 3) * 4);
+}
+
+// x rounded to TF32 (round to nearest, ties away from zero): low 13 bits of the result zero
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 // Waits for the phase of parity `parity` of the mbarrier to complete, `limit` polls at
@@ -76,45 +106,44 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
 }
 
 // Stages rows row0 .. row0+R-1 and k indices k0 .. k0+TK-1 of an operand (FP32 in
-// memory, zero outside rows < nrows and k < kend) as BF16 into a K-major slice of R rows.
+// memory, zero outside rows < nrows and k < kend) into a K-major slice of R rows: as BF16
+// (BF16 mode), or as its TF32 split, hi into sl and lo into sl_lo (TF32x3 mode).
 // rows_fast: element (row, k) sits at X[row + k ld] (consecutive threads take consecutive
 // rows), else at X[k + row ld] (consecutive threads take consecutive k).  A thread issues
 // all its loads before converting and storing, so they are in flight together.
-template <int R>
-__device__ __forceinline__ void stage_slice(unsigned char* __restrict__ sl, const float* __restrict__ X,
-                                            bool rows_fast, int ld, int row0, int nrows, int k0, int kend,
-                                            int tid) {
+template <int MODE, int R>
+__device__ __forceinline__ void stage_slice(unsigned char* __restrict__ sl, unsigned char* __restrict__ sl_lo,
+                                            const float* __restrict__ X, bool rows_fast, int ld, int row0,
+                                            int nrows, int k0, int kend, int tid) {
+  constexpr int TK = TcShape<MODE>::TK;
   constexpr int PER = R * TK / 256;
   float v[PER];
-  if (rows_fast) {
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = tid + 256 * q, r = e % R, c = e / R;
-      const int gr = row0 + r, gk = k0 + c;
-      v[q] = (gr < nrows && gk < kend) ? X[(size_t)gr + (size_t)gk * ld] : 0.f;
-    }
+  for (int q = 0; q < PER; ++q) {
+    const int e = tid + 256 * q;
+    const int r = rows_fast ? e % R : e / TK, c = rows_fast ? e / R : e % TK;
+    const int gr = row0 + r, gk = k0 + c;
+    v[q] = (gr < nrows && gk < kend) ? (rows_fast ? X[(size_t)gr + (size_t)gk * ld] : X[(size_t)gk + (size_t)gr * ld])
+                                     : 0.f;
+  }
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = tid + 256 * q, r = e % R, c = e / R;
-      *(__nv_bfloat16*)(sl + kmaj(r, c, R)) = __float2bfloat16(v[q]);
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = tid + 256 * q, c = e % TK, r = e / TK;
-      const int gr = row0 + r, gk = k0 + c;
-      v[q] = (gr < nrows && gk < kend) ? X[(size_t)gk + (size_t)gr * ld] : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = tid + 256 * q, c = e % TK, r = e / TK;
-      *(__nv_bfloat16*)(sl + kmaj(r, c, R)) = __float2bfloat16(v[q]);
+  for (int q = 0; q < PER; ++q) {
+    const int e = tid + 256 * q;
+    const int r = rows_fast ? e % R : e / TK, c = rows_fast ? e / R : e % TK;
+    const uint32_t off = kmaj<MODE>(r, c, R);
+    if (MODE == kModeBf16) {
+      *(__nv_bfloat16*)(sl + off) = __float2bfloat16(v[q]);
+    } else {
+      const float hi = tf32_hi(v[q]);
+      *(float*)(sl + off) = hi;
+      *(float*)(sl_lo + off) = v[q] - hi;
     }
   }
 }
 
 }  // namespace
 
+template <int MODE>
 __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ tasks,
                                                  const GemmTile* __restrict__ tiles, float* __restrict__ split_ws,
                                                  unsigned* __restrict__ split_cnt, int* __restrict__ err,
@@ -147,6 +176,8 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  constexpr int TK = TcShape<MODE>::TK, KI = TcShape<MODE>::KI;
+  constexpr int kStage = MODE == kModeBf16 ? kStageA + kStageB : 2 * (kStageA + kStageB);
   const int nk = (tl.k1 - tl.k0 + TK - 1) / TK;
   for (int kt = 0; kt < nk; ++kt) {
     const int s = kt & 1;
@@ -155,27 +186,39 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
       __syncthreads();
       if (!s_ok) break;
     }
-    unsigned char* sA = smem + s * (kStageA + kStageB);
+    unsigned char* sA = smem + s * kStage;
     unsigned char* sB = sA + kStageA;
+    unsigned char* sAlo = sB + kStageB;  // TF32x3 mode only
+    unsigned char* sBlo = sAlo + kStageA;
     const int kb = tl.k0 + kt * TK;
     // A slice: op(A)[m0 .., kb ..]; B slice as N x K (row n = column n of op(B))
-    stage_slice<TM>(sA, A, t.opA == 0, t.lda, m0, t.m, kb, tl.k1, tid);
-    stage_slice<TN>(sB, B, t.opB != 0, t.ldb, n0, t.n, kb, tl.k1, tid);
+    stage_slice<MODE, TM>(sA, sAlo, A, t.opA == 0, t.lda, m0, t.m, kb, tl.k1, tid);
+    stage_slice<MODE, TN>(sB, sBlo, B, t.opB != 0, t.ldb, n0, t.n, kb, tl.k1, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      // one MMA instruction per KI-deep step: 32 bytes = two core matrices along k
+      constexpr int nterm = MODE == kModeBf16 ? 1 : 3;  // hi*hi, hi*lo, lo*hi
 #pragma unroll
-      for (int j = 0; j < TK / 16; ++j) {
-        const uint64_t da = umma_desc(a0 + (uint32_t)(2 * j * TM * 16), TM * 16, 128);
-        const uint64_t db = umma_desc(b0 + (uint32_t)(2 * j * TN * 16), TN * 16, 128);
-        const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
-        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                     :: "r"(tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
-                     : "memory");
-      }
+      for (int j = 0; j < TK / KI; ++j)
+#pragma unroll
+        for (int term = 0; term < nterm; ++term) {
+          const uint32_t a0 = smem_u32(term == 2 ? sAlo : sA), b0 = smem_u32(term == 1 ? sBlo : sB);
+          const uint64_t da = umma_desc(a0 + (uint32_t)(2 * j * TM * 16), TM * 16, 128);
+          const uint64_t db = umma_desc(b0 + (uint32_t)(2 * j * TN * 16), TN * 16, 128);
+          const uint32_t acc = (kt > 0 || j > 0 || term > 0) ? 1u : 0u;
+          if (MODE == kModeBf16)
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                         :: "r"(tmem), "l"(da), "l"(db), "r"(kIdescBf16), "r"(acc)
+                         : "memory");
+          else
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                         :: "r"(tmem), "l"(da), "l"(db), "r"(kIdescTf32), "r"(acc)
+                         : "memory");
+        }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_u32(&mbar[s])) : "memory");
       s_committed = kt + 1;
@@ -271,13 +314,21 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmTask* __restrict__ ta
 void launch_gemm_tc(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
                     unsigned* split_cnt, int* err, int wait_limit, int inject_timeout, cudaStream_t s) {
   if (ntiles <= 0) return;
-  k_gemm_tc<<<ntiles, 256, kTcSmem, s>>>(tasks, tiles, split_ws, split_cnt, err,
-                                          wait_limit > 0 ? wait_limit : kWaitLimit, inject_timeout);
+  k_gemm_tc<kModeBf16><<<ntiles, 256, kTcSmem, s>>>(tasks, tiles, split_ws, split_cnt, err,
+                                                     wait_limit > 0 ? wait_limit : kWaitLimit, inject_timeout);
+}
+
+void launch_gemm_tf32x3(const GemmTask* tasks, const GemmTile* tiles, int ntiles, float* split_ws,
+                        unsigned* split_cnt, int* err, int wait_limit, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_gemm_tc<kModeTf32x3><<<ntiles, 256, kTf32Smem, s>>>(tasks, tiles, split_ws, split_cnt, err,
+                                                         wait_limit > 0 ? wait_limit : kWaitLimit, 0);
 }
 
 int dense_tc_setup(int max_smem) {
   (void)max_smem;
-  HM_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  HM_CUDA(cudaFuncSetAttribute(k_gemm_tc<kModeBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  HM_CUDA(cudaFuncSetAttribute(k_gemm_tc<kModeTf32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTf32Smem));
   return HM_OK;
 }
 

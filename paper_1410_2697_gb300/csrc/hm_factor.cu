@@ -93,6 +93,7 @@ static void debug_stage(hm_sys_s* sys, const char* stage, int level) {
   if (!on) return;
   cudaStream_t s = sys->ctx->stream;
   const Plan& P = sys->plan;
+  const cudaError_t le = cudaPeekAtLastError();  // a launch of this stage refused
   unsigned long long* d = nullptr;
   cudaMalloc(&d, 6 * sizeof(unsigned long long));
   cudaMemsetAsync(d, 0, 6 * sizeof(unsigned long long), s);
@@ -106,14 +107,16 @@ static void debug_stage(hm_sys_s* sys, const char* stage, int level) {
   cudaMemcpyAsync(e, sys->d_err, sizeof(e), cudaMemcpyDeviceToHost, s);
   cudaError_t ce = cudaStreamSynchronize(s);
   cudaFree(d);
-  fprintf(stderr, "[hm debug] level %d %-10s cuda=%s err=%d(%d,%d) nonfinite front=%llu comp=%llu bo=%llu x=%llu core=%llu tb=%llu\n",
-          level, stage, cudaGetErrorString(ce), e[0], e[1], e[2], h[0], h[1], h[2], h[3], h[4], h[5]);
+  fprintf(stderr, "[hm debug] level %d %-10s launch=%s cuda=%s err=%d(%d,%d) nonfinite front=%llu comp=%llu bo=%llu x=%llu core=%llu tb=%llu\n",
+          level, stage, cudaGetErrorString(le), cudaGetErrorString(ce), e[0], e[1], e[2], h[0], h[1], h[2], h[3], h[4], h[5]);
 }
 
 template <typename T>
 static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* base, int cat) {
   if (b.tiles.count == 0) return;
-  ProfScope ps(sys->ctx, cat, b.tasks.work);
+  const int vt = sys->ctx->tune.variant(TS_GEMM, b.sig);
+  const bool on_tc = sizeof(T) == 4 && (b.tc || (vt == 4 && b.tiles_tc.count > 0));
+  ProfScope ps(sys->ctx, on_tc ? PC_GEMM_TC : cat, b.tasks.work);  // tensor-core launches apart
   if (b.tc && sizeof(T) == 4) {
     launch_gemm_tc(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, (float*)sys->plan.d_split_ws,
                    sys->plan.d_split_cnt, sys->d_err, sys->ctx->opts.wait_limit,
@@ -122,12 +125,17 @@ static void run_gemm(hm_sys_s* sys, const GemmBatch& b, const unsigned char* bas
   }
   TuneScope ts(sys->ctx, TS_GEMM, b.sig);
   const int v = sys->ctx->tune.variant(TS_GEMM, b.sig);
+  if (v == 4 && b.tiles_tc.count > 0 && sizeof(T) == 4) {  // FP32 on the tensor cores (3xTF32)
+    launch_gemm_tf32x3(b.tasks.dev(base), b.tiles_tc.dev(base), b.tiles_tc.count, (float*)sys->plan.d_split_ws,
+                       sys->plan.d_split_cnt, sys->d_err, sys->ctx->opts.wait_limit, sys->ctx->stream);
+    return;
+  }
   if (v == 3 && b.tiles_big.count > 0 && sizeof(T) == 4) {  // FP32 large-tile kernel
     launch_gemm_big(b.tasks.dev(base), b.tiles_big.dev(base), b.tiles_big.count, (float*)sys->plan.d_split_ws,
                     sys->plan.d_split_cnt, sys->ctx->stream);
     return;
   }
-  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, v == 3 ? 0 : v,
+  launch_gemm<T>(b.tasks.dev(base), b.tiles.dev(base), b.tiles.count, b.bn, v >= 3 ? 0 : v,
                  (T*)sys->plan.d_split_ws, sys->plan.d_split_cnt, sys->ctx->stream);
 }
 

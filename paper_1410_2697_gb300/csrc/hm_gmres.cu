@@ -635,6 +635,126 @@ static void sqnorm(hm_sys_s* sys, const double* v, double* ss, int stride, int n
   launch_reduce_dots(G.part, G.nchunks, G.cptr, sys->nseg, ninst, 1, stride, ss, nullptr, s);
 }
 
+// One restart cycle of GMRES(m) over the instances with active[inst] = 1 (right
+// preconditioning, flexible form): V_0 = r / ||r||, then at most min(m, budget) Arnoldi
+// steps, each the preconditioner apply, the double-float Krylov product, CGS2 and a
+// Givens rotation, stopping early once every active instance's rotated residual
+// estimate is at or below rtol; then x += Z y and the true FP64 residual r = b - A x.
+// *its = the Arnoldi steps run.
+template <typename T>
+static int gm_cycle(hm_sys_s* sys, int nrhs, double rtol, int budget, const std::vector<int>& active, int* its) {
+  const int m = std::max(1, sys->ctx->opts.restart);
+  auto& G = sys->gm;
+  cudaStream_t s = sys->ctx->stream;
+  const int n = sys->n;
+  const int64_t nn = (int64_t)n * nrhs;
+  const int stride = m + 2;
+  const int nseg = sys->nseg, ninst = nrhs * nseg;
+  const dim3 vgrid((unsigned)G.nchunks, (unsigned)nrhs);
+  int* d_active = G.len + ninst;
+  double* rss = G.hv + 2 * (int64_t)ninst * stride + ninst;  // squared residual norms
+  T* Z = (T*)G.Z;
+  const int max_iters = budget;
+  int iters = 0;
+  HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s));
+  {
+    ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, (16.0 + sizeof(T)) * nn}, 2);
+    k_cycle_init<T><<<vgrid, 256, 0, s>>>(G.r, G.V, (T*)G.wT, n, nrhs, rss, d_active, G.crow, G.cseg, nseg);
+    k_cycle_g<<<(ninst + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, ninst);
+  }
+  int j = 0;
+  for (; j < m && iters < max_iters; ++j) {
+    T* Zj = Z + (int64_t)j * nrhs * n;
+    // G.wT holds V_j in the factor precision (written with V_j by k_cycle_init / k_scale)
+    HM_TRY(apply_impl_rowmajor(sys, nrhs, G.wT, Zj));  // Z_j row-major
+    {
+      ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs,
+                                           12.0 * sys->nnz + 8.0 * n + (8.0 + sizeof(T)) * nn});
+      if (sizeof(T) == 4)
+        k_spmv_df<<<dim3((n + 255) / 256, (nrhs + kSpmvDF - 1) / kSpmvDF), 256, 0, s>>>(
+            sys->d_prowptr, sys->d_pcol, sys->d_pvals2, n, nrhs, (const float*)Zj, G.w);
+      else
+        k_spmv_rm<T><<<dim3((n + 255) / 256, (nrhs + kSpmvRM - 1) / kSpmvRM), 256, 0, s>>>(
+            sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs, Zj, G.w);
+    }
+    // CGS2: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
+    double* h1 = G.hv;
+    double* h2 = G.hv + (int64_t)ninst * stride;
+    double* wss = G.hv + 2 * (int64_t)ninst * stride + 2 * ninst;  // ||w||^2 per instance
+    const int nvec = j + 1;
+    {
+      ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
+      launch_multidot(G.V, G.w, n, nrhs, nvec, stride, G.crow, G.part, G.nchunks, s);
+      launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h1, nullptr, s);
+    }
+    if (nvec <= kFusedGs) {
+      {
+        ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{4.0 * nvec * nn, 8.0 * (nvec + 2) * nn}, 2);
+        launch_gs_update_dots(G.V, G.w, n, nrhs, nvec, stride, h1, G.crow, G.cseg, nseg, 0, stride, G.part,
+                              G.nchunks, s);
+        launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h2, h1, s);  // h1 += h2
+      }
+      {
+        ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * (nvec + 1) * nn, 8.0 * (nvec + 2) * nn}, 2);
+        launch_gs_update_dots(G.V, G.w, n, nrhs, nvec, stride, h2, G.crow, G.cseg, nseg, 1, 1, G.part,
+                              G.nchunks, s);
+        launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, 1, 1, wss, nullptr, s);
+      }
+    } else {
+      {
+        ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
+        k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h1, G.crow, G.cseg, nseg);
+      }
+      {
+        ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
+        launch_multidot(G.V, G.w, n, nrhs, nvec, stride, G.crow, G.part, G.nchunks, s);
+        launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h2, h1, s);  // h1 += h2
+      }
+      {
+        ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
+        k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h2, G.crow, G.cseg, nseg);
+      }
+      sqnorm(sys, G.w, wss, 1, nrhs);
+    }
+    {
+      ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, (16.0 + sizeof(T)) * nn});
+      k_scale<T><<<vgrid, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, (T*)G.wT, n, nrhs, wss, 1,
+                                       G.crow, G.cseg, nseg);
+    }
+    {
+      ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
+      k_givens<<<(ninst + 63) / 64, 64, 0, s>>>(G.H, h1, stride, wss, 1, G.cs, G.sn, G.g, G.bnorm,
+                                                G.res, G.len, j, m, ninst, rtol);
+    }
+    ++iters;
+    HM_CUDA(cudaMemcpyAsync(G.h_res, G.res, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    host_mark("gmres: iteration");
+    bool all = true;
+    for (int r = 0; r < ninst; ++r)
+      if (active[r] && !(G.h_res[r] <= rtol)) all = false;
+    if (all) { ++j; break; }
+  }
+  const int jend = std::min(j, m);
+  {
+    ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
+    k_backsolve<<<(ninst + 63) / 64, 64, 0, s>>>(G.H, G.g, G.y, G.len, jend, m, ninst);
+  }
+  {
+    ProfScope ps(sys->ctx, PC_VECTOR, Work{2.0 * jend * nn, (16.0 + sizeof(T) * jend) * nn});
+    const int split = std::max(1, (6 * sys->ctx->num_sms + G.nchunks - 1) / G.nchunks);
+    k_update_x<T><<<dim3(G.nchunks, split), 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m, G.crow, G.cseg, nseg);
+  }
+  {
+    ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});
+    k_spmv<double><<<spmv_grid(n, nrhs), 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
+                                                   G.x, n, G.r, n, G.b, n);
+  }
+  sqnorm(sys, G.r, rss, 1, nrhs);
+  *its = iters;
+  return HM_OK;
+}
+
 template <typename T>
 static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
                    double* d_x, hm_solve_info* info) {
@@ -648,7 +768,6 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
   const int64_t nn = (int64_t)n * nrhs;
   const int stride = m + 2;
   const int nseg = sys->nseg, ninst = nrhs * nseg;  // instance = r * nseg + block
-  const dim3 vgrid((unsigned)G.nchunks, (unsigned)nrhs);
   {
     ProfScope ps(sys->ctx, PC_VECTOR, Work{0.0, 20.0 * nn});
     launch_permute_in(d_b, G.b, sys->d_perm, n, nrhs, s);
@@ -669,109 +788,15 @@ static int gmres_t(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int 
   std::vector<int> active(ninst);
   for (int r = 0; r < ninst; ++r) relres[r] = bnorm[r] > 0 ? 1.0 : 0.0;
   int iters = 0, cycles = 0;
-  int* d_active = G.len + ninst;
   double* rss = G.hv + 2 * (int64_t)ninst * stride + ninst;  // squared residual norms
   HM_CUDA(cudaMemcpyAsync(rss, bn2, sizeof(double) * ninst, cudaMemcpyDeviceToDevice, s));
   bool done = true;
   for (int r = 0; r < ninst; ++r) done = done && relres[r] <= rtol;
-  T* Z = (T*)G.Z;
   while (!done && iters < max_iters) {
     for (int r = 0; r < ninst; ++r) active[r] = relres[r] > rtol ? 1 : 0;
-    HM_CUDA(cudaMemcpyAsync(d_active, active.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s));
-    {
-      ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, (16.0 + sizeof(T)) * nn}, 2);
-      k_cycle_init<T><<<vgrid, 256, 0, s>>>(G.r, G.V, (T*)G.wT, n, nrhs, rss, d_active, G.crow, G.cseg, nseg);
-      k_cycle_g<<<(ninst + 63) / 64, 64, 0, s>>>(G.g, G.len, rss, d_active, m, ninst);
-    }
     int j = 0;
-    for (; j < m && iters < max_iters; ++j) {
-      T* Zj = Z + (int64_t)j * nrhs * n;
-      // G.wT holds V_j in the factor precision (written with V_j by k_cycle_init / k_scale)
-      HM_TRY(apply_impl_rowmajor(sys, nrhs, G.wT, Zj));  // Z_j row-major
-      {
-        ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs,
-                                             12.0 * sys->nnz + 8.0 * n + (8.0 + sizeof(T)) * nn});
-        if (sizeof(T) == 4)
-          k_spmv_df<<<dim3((n + 255) / 256, (nrhs + kSpmvDF - 1) / kSpmvDF), 256, 0, s>>>(
-              sys->d_prowptr, sys->d_pcol, sys->d_pvals2, n, nrhs, (const float*)Zj, G.w);
-        else
-          k_spmv_rm<T><<<dim3((n + 255) / 256, (nrhs + kSpmvRM - 1) / kSpmvRM), 256, 0, s>>>(
-              sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs, Zj, G.w);
-      }
-      // CGS2: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
-      double* h1 = G.hv;
-      double* h2 = G.hv + (int64_t)ninst * stride;
-      double* wss = G.hv + 2 * (int64_t)ninst * stride + 2 * ninst;  // ||w||^2 per instance
-      const int nvec = j + 1;
-      {
-        ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
-        launch_multidot(G.V, G.w, n, nrhs, nvec, stride, G.crow, G.part, G.nchunks, s);
-        launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h1, nullptr, s);
-      }
-      if (nvec <= kFusedGs) {
-        {
-          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{4.0 * nvec * nn, 8.0 * (nvec + 2) * nn}, 2);
-          launch_gs_update_dots(G.V, G.w, n, nrhs, nvec, stride, h1, G.crow, G.cseg, nseg, 0, stride, G.part,
-                                G.nchunks, s);
-          launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h2, h1, s);  // h1 += h2
-        }
-        {
-          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * (nvec + 1) * nn, 8.0 * (nvec + 2) * nn}, 2);
-          launch_gs_update_dots(G.V, G.w, n, nrhs, nvec, stride, h2, G.crow, G.cseg, nseg, 1, 1, G.part,
-                                G.nchunks, s);
-          launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, 1, 1, wss, nullptr, s);
-        }
-      } else {
-        {
-          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
-          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h1, G.crow, G.cseg, nseg);
-        }
-        {
-          ProfScope ps(sys->ctx, PC_DOTS, Work{2.0 * nvec * nn, 8.0 * (nvec + 1) * nn}, 2);
-          launch_multidot(G.V, G.w, n, nrhs, nvec, stride, G.crow, G.part, G.nchunks, s);
-          launch_reduce_dots(G.part, G.nchunks, G.cptr, nseg, ninst, nvec, stride, h2, h1, s);  // h1 += h2
-        }
-        {
-          ProfScope ps(sys->ctx, PC_GS_UPDATE, Work{2.0 * nvec * nn, 8.0 * (nvec + 2) * nn});
-          k_gs_update<<<vgrid, 256, 0, s>>>(G.V, G.w, n, nrhs, nvec, stride, h2, G.crow, G.cseg, nseg);
-        }
-        sqnorm(sys, G.w, wss, 1, nrhs);
-      }
-      {
-        ProfScope ps(sys->ctx, PC_VECTOR, Work{(double)nn, (16.0 + sizeof(T)) * nn});
-        k_scale<T><<<vgrid, 256, 0, s>>>(G.w, G.V + (int64_t)(j + 1) * nrhs * n, (T*)G.wT, n, nrhs, wss, 1,
-                                         G.crow, G.cseg, nseg);
-      }
-      {
-        ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
-        k_givens<<<(ninst + 63) / 64, 64, 0, s>>>(G.H, h1, stride, wss, 1, G.cs, G.sn, G.g, G.bnorm,
-                                                  G.res, G.len, j, m, ninst, rtol);
-      }
-      ++iters;
-      HM_CUDA(cudaMemcpyAsync(G.h_res, G.res, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
-      HM_CUDA(cudaStreamSynchronize(s));
-      host_mark("gmres: iteration");
-      bool all = true;
-      for (int r = 0; r < ninst; ++r)
-        if (active[r] && !(G.h_res[r] <= rtol)) all = false;
-      if (all) { ++j; break; }
-    }
-    const int jend = std::min(j, m);
-    {
-      ProfScope ps(sys->ctx, PC_GMRES_SMALL, Work{});
-      k_backsolve<<<(ninst + 63) / 64, 64, 0, s>>>(G.H, G.g, G.y, G.len, jend, m, ninst);
-    }
-    {
-      ProfScope ps(sys->ctx, PC_VECTOR, Work{2.0 * jend * nn, (16.0 + sizeof(T) * jend) * nn});
-      const int split = std::max(1, (6 * sys->ctx->num_sms + G.nchunks - 1) / G.nchunks);
-      k_update_x<T><<<dim3(G.nchunks, split), 256, 0, s>>>(G.x, Z, G.y, G.len, n, nrhs, m, G.crow, G.cseg, nseg);
-    }
-    {
-      ProfScope ps(sys->ctx, PC_SPMV, Work{2.0 * sys->nnz * nrhs, 12.0 * sys->nnz + 8.0 * n + 24.0 * nn});
-      k_spmv<double><<<spmv_grid(n, nrhs), 256, 0, s>>>(sys->d_prowptr, sys->d_pcol, sys->d_pvals, n, nrhs,
-                                                     G.x, n, G.r, n, G.b, n);
-    }
-    sqnorm(sys, G.r, rss, 1, nrhs);
+    HM_TRY(gm_cycle<T>(sys, nrhs, rtol, max_iters - iters, active, &j));
+    iters += j;
     std::vector<double> hr(ninst);
     HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
@@ -877,6 +902,133 @@ int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_
                hm_solve_info* info) {
   if (sys->precision == HM_PREC_FP64) return gmres_t<double>(sys, nrhs, d_b, rtol, max_iters, d_x, info);
   return gmres_t<float>(sys, nrhs, d_b, rtol, max_iters, d_x, info);
+}
+
+// ------------------------------------------------------------------------------------
+// Slot sessions.  Between cycles the columns are independent instances: a slot's b, x
+// and r are (re)set without touching the others, and the next cycle's V_0 = r / ||r|| is
+// formed per column, so a right-hand side that joins a running session is solved by the
+// same iteration as alone (GMRES runs each column on its own Krylov space).
+// ------------------------------------------------------------------------------------
+int gm_session_begin(hm_sys_s* sys, int nslots) {
+  if (sys->nseg != 1) {
+    set_last_error("solve sessions serve one mesh per system");
+    return HM_ERR_INVALID_ARG;
+  }
+  const int m = std::max(1, sys->ctx->opts.restart);
+  HM_TRY(ensure_workspace(sys, nslots, m));
+  auto& G = sys->gm;
+  cudaStream_t s = sys->ctx->stream;
+  const int64_t nn = (int64_t)sys->n * nslots;
+  HM_CUDA(cudaMemsetAsync(G.b, 0, sizeof(double) * nn, s));
+  HM_CUDA(cudaMemsetAsync(G.x, 0, sizeof(double) * nn, s));
+  HM_CUDA(cudaMemsetAsync(G.r, 0, sizeof(double) * nn, s));
+  G.on.assign(nslots, 0);
+  G.fresh.assign(nslots, 0);
+  G.rtol.assign(nslots, 1e-10);
+  G.bnorm_h.assign(nslots, 0.0);
+  G.relres.assign(nslots, 0.0);
+  G.iters.assign(nslots, 0);
+  G.cap.assign(nslots, 0);
+  return HM_OK;
+}
+
+int gm_session_put(hm_sys_s* sys, int slot, const double* b_host, double rtol, int max_iters) {
+  auto& G = sys->gm;
+  if (slot < 0 || slot >= (int)G.on.size() || G.on[slot]) return HM_ERR_INVALID_ARG;
+  cudaStream_t s = sys->ctx->stream;
+  const int n = sys->n;
+  double* stage = G.w + (int64_t)slot * n;  // the Arnoldi scratch is free between cycles
+  HM_CUDA(cudaMemcpyAsync(stage, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  launch_permute_in(stage, G.b + (int64_t)slot * n, sys->d_perm, n, 1, s);
+  HM_CUDA(cudaMemsetAsync(G.x + (int64_t)slot * n, 0, sizeof(double) * n, s));
+  HM_CUDA(cudaMemcpyAsync(G.r + (int64_t)slot * n, G.b + (int64_t)slot * n, sizeof(double) * n,
+                          cudaMemcpyDeviceToDevice, s));
+  G.on[slot] = 1;
+  G.fresh[slot] = 1;
+  G.rtol[slot] = rtol;
+  G.iters[slot] = 0;
+  G.cap[slot] = max_iters;
+  G.relres[slot] = 1.0;
+  HM_CUDA(cudaStreamSynchronize(s));  // the host array may go away after the call
+  return HM_OK;
+}
+
+template <typename T>
+static int session_cycle_t(hm_sys_s* sys, int* its) {
+  auto& G = sys->gm;
+  cudaStream_t s = sys->ctx->stream;
+  const int nslots = G.nrhs, m = G.m, stride = m + 2;
+  double* bn2 = G.hv + 2 * (int64_t)nslots * stride;
+  double* rss = bn2 + nslots;
+  *its = 0;
+  bool fresh = false;
+  for (int k = 0; k < nslots; ++k) fresh = fresh || G.fresh[k];
+  if (fresh) {  // ||b|| of the slots that joined; their squared residual is ||b||^2 (x = 0)
+    std::vector<double> hb(nslots), hr(nslots);
+    sqnorm(sys, G.b, bn2, 1, nslots);
+    HM_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * nslots, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * nslots, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < nslots; ++k)
+      if (G.fresh[k]) {
+        G.bnorm_h[k] = std::sqrt(hb[k]);
+        G.relres[k] = G.bnorm_h[k] > 0 ? 1.0 : 0.0;
+        hr[k] = hb[k];
+        G.fresh[k] = 0;
+      }
+    HM_CUDA(cudaMemcpyAsync(G.bnorm, G.bnorm_h.data(), sizeof(double) * nslots, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(rss, hr.data(), sizeof(double) * nslots, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<int> active(nslots, 0);
+  double rtol = 1.0;
+  int budget = 0;
+  bool any = false;
+  for (int k = 0; k < nslots; ++k)
+    if (G.on[k] && G.relres[k] > G.rtol[k] && G.iters[k] < G.cap[k]) {
+      active[k] = 1;
+      any = true;
+      rtol = std::min(rtol, G.rtol[k]);
+      budget = std::max(budget, G.cap[k] - G.iters[k]);
+    }
+  if (!any) return HM_OK;
+  HM_TRY(gm_cycle<T>(sys, nslots, rtol, budget, active, its));
+  std::vector<double> hr(nslots);
+  HM_CUDA(cudaMemcpyAsync(hr.data(), rss, sizeof(double) * nslots, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < nslots; ++k)
+    if (active[k]) {
+      G.iters[k] += *its;
+      G.relres[k] = G.bnorm_h[k] > 0 ? std::sqrt(hr[k]) / G.bnorm_h[k] : 0.0;
+    }
+  return check_device_error(sys, "solve session");
+}
+
+int gm_session_cycle(hm_sys_s* sys, int* its) {
+  if (sys->precision == HM_PREC_FP64) return session_cycle_t<double>(sys, its);
+  return session_cycle_t<float>(sys, its);
+}
+
+int gm_session_state(const hm_sys_s* sys, int slot, double* relres, int* iters) {
+  const auto& G = sys->gm;
+  if (relres) *relres = G.relres[slot];
+  if (iters) *iters = G.iters[slot];
+  if (G.relres[slot] <= G.rtol[slot]) return 1;
+  return G.iters[slot] >= G.cap[slot] ? -1 : 0;
+}
+
+int gm_session_take(hm_sys_s* sys, int slot, double* x_host) {
+  auto& G = sys->gm;
+  if (slot < 0 || slot >= (int)G.on.size() || !G.on[slot]) return HM_ERR_INVALID_ARG;
+  cudaStream_t s = sys->ctx->stream;
+  const int n = sys->n;
+  double* stage = G.w + (int64_t)slot * n;
+  launch_permute_out(G.x + (int64_t)slot * n, stage, sys->d_perm, n, 1, s);
+  HM_CUDA(cudaMemcpyAsync(x_host, stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  G.on[slot] = 0;
+  return HM_OK;
 }
 
 }  // namespace hm

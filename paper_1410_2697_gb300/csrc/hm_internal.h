@@ -77,6 +77,7 @@ struct GemmBatch {
   Span<GemmTask> tasks;
   Span<GemmTile> tiles;
   Span<GemmTile> tiles_big;  // 128 x 128 tiles for the FP32 large-tile variant (if eligible)
+  Span<GemmTile> tiles_tc;   // 128 x 64 tiles for the FP32 tensor-core (3xTF32) variant
   int bn = 64;       // tile width of the batch
   int tc = 0;        // 1: tensor-core BF16 kernel (128 x 64 tiles)
   uint64_t sig = 0;  // shape signature (autotuner key)
@@ -173,6 +174,25 @@ struct TaskBuf {
       split_ws = std::max(split_ws, bws);
       split_slots = std::max(split_slots, bslots);
     }
+    // FP32 batches holding a product of at least one 128 x 64 tile over 64 k also get the
+    // tiles of the tensor-core 3xTF32 kernel (an autotuner variant)
+    std::vector<GemmTile> tct;
+    bool sizable = false;
+    for (const auto& x : t) sizable = sizable || (x.m >= 64 && x.n >= 32 && x.k >= 64);
+    if (!tc && es == 4 && sizable) {
+      int ntc = 0;
+      for (const auto& x : t) ntc += gemm_tile_count(x, kTcBM, kTcBN);
+      int tslots = 0;
+      int64_t tws = 0;
+      for (size_t i = 0; i < t.size(); ++i) {
+        int nsplit = 1;
+        if (ntc < split_target && t[i].k >= 2 * kSplitMinK)
+          nsplit = std::min(std::min(split_target / std::max(ntc, 1), t[i].k / kSplitMinK), kSplitMax);
+        gemm_tiles_for(t[i], (int)i, kTcBM, kTcBN, nsplit, &tct, &tslots, &tws);
+      }
+      split_ws = std::max(split_ws, tws);
+      split_slots = std::max(split_slots, tslots);
+    }
     Sig sg;
     sg << b.bn << b.tc << (int64_t)t.size() << (int64_t)tiles.size();
     for (const auto& x : t) sg << x.m << x.n << x.k << (x.opA + 2 * x.opB + 4 * x.lower);
@@ -180,6 +200,7 @@ struct TaskBuf {
     b.tasks = add(t);
     b.tiles = add(tiles);
     b.tiles_big = add(big);
+    b.tiles_tc = add(tct);
     return b;
   }
 };
@@ -192,7 +213,7 @@ enum ProfCat {
   PC_ND = 0, PC_SYMBOLIC, PC_PERMUTE_CSR, PC_SCATTER, PC_EXTEND_ADD, PC_POTRF, PC_TRSM,
   PC_GEMM_FACTOR, PC_SKETCH, PC_QR, PC_SVD, PC_CHOL_SOLVE, PC_CORE_LU, PC_INVERSE,
   PC_UP, PC_DOWN, PC_GEMM_APPLY, PC_SPMV, PC_DOTS, PC_GS_UPDATE, PC_GMRES_SMALL, PC_VECTOR,
-  PC_MEMSET, PC_SWEEP, PC_BDLR, PC_HODLR_UP, PC_HODLR_DOWN, PC_COUNT
+  PC_MEMSET, PC_SWEEP, PC_BDLR, PC_HODLR_UP, PC_HODLR_DOWN, PC_GEMM_TC, PC_COUNT
 };
 const char* prof_cat_name(int c);
 
@@ -447,6 +468,9 @@ struct hm_ctx_s {
   cudaMemPool_t pool = nullptr;  // stream-ordered pool; freed memory is kept for reuse
   std::vector<void*> allocs;
   void* noalloc_scratch = nullptr;  // device address of the allocation-free apply's array
+  // adaptive rank: sketch width per front level learned for an analysis (key: its shape
+  // signature), so a later analysis of the same pattern starts from the grown widths
+  std::unordered_map<uint64_t, std::vector<int>> level_widths;
 };
 
 struct hm_sys_s {
@@ -519,6 +543,9 @@ struct hm_sys_s {
   std::map<int, std::unique_ptr<hm::SolvePlan>> solve_plans;
   int64_t plan_clock = 0;
   std::vector<void*> allocs;
+  std::vector<void*> plan_allocs;     // device memory of the plan (rebuilt when widths grow)
+  std::vector<int> level_width;       // sketch width per front level (empty: opts.samples)
+  uint64_t shape_sig = 0;             // analysis signature (key of ctx->level_widths)
   // GMRES workspace (grown on demand)
   struct Gm {
     int nrhs = 0, m = 0;
@@ -532,6 +559,11 @@ struct hm_sys_s {
     std::vector<void*> allocs;
     int nchunks = 0;                          // row chunks (never straddling a block)
     int *crow = nullptr, *cseg = nullptr, *cptr = nullptr;  // chunk rows, block, chunks per block
+    // slot session (serving): per column, occupied / tolerance / iterations / cap / ||b|| /
+    // last true relative residual; `fresh` marks columns whose norms must be computed
+    std::vector<char> on, fresh;
+    std::vector<double> rtol, bnorm_h, relres;
+    std::vector<int> iters, cap;
   } gm;
 };
 
@@ -592,6 +624,8 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
                  const int32_t* first_in, const int32_t* parent_in, int nblocks,
                  const int32_t* block_ptr);
 int build_plan(hm_sys_s* sys);
+// Frees the plan's device memory and builds it again (after the sketch widths changed).
+int rebuild_plan(hm_sys_s* sys);
 int factor_impl(hm_sys_s* sys, const double* d_values, double tol);
 // Apply plans are kept for at most this many right-hand-side counts per system.
 constexpr int kMaxSolvePlans = 4;
@@ -616,6 +650,17 @@ int launch_hodlr_apply(bool down, const LevelSolvePlan& lp, const unsigned char*
 size_t hodlr_apply_smem(const HaDims& d, int RB, bool down, int es);
 int hodlr_apply_setup(int max_smem);
 int direct_impl(hm_sys_s* sys, int nrhs, const double* d_b, int refine, double* d_x, hm_solve_info* info);
+// Slot sessions of GMRES for serving: nslots columns, each its own instance.  A right-hand
+// side enters a free slot between restart cycles (gm_session_put, host array in the
+// original numbering) and leaves when taken (gm_session_take, x to a host array); each
+// gm_session_cycle runs one restart cycle over the occupied, unconverged slots (one
+// system, no batch of meshes).
+int gm_session_begin(hm_sys_s* sys, int nslots);
+int gm_session_put(hm_sys_s* sys, int slot, const double* b_host, double rtol, int max_iters);
+int gm_session_cycle(hm_sys_s* sys, int* its);
+// state of a slot: 1 = converged, 0 = running, -1 = its iteration cap was reached
+int gm_session_state(const hm_sys_s* sys, int slot, double* relres, int* iters);
+int gm_session_take(hm_sys_s* sys, int slot, double* x_host);
 int gmres_impl(hm_sys_s* sys, int nrhs, const double* d_b, double rtol, int max_iters,
                double* d_x, hm_solve_info* info);
 // permutation helpers (new <-> original numbering), FP64 n x nrhs

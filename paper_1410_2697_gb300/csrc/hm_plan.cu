@@ -45,9 +45,11 @@ static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, 
   std::vector<TsqrBlock> blocks;
   std::vector<GemmTask> cmb;
   std::vector<int> plain_rel;  // plain tasks whose R and Q hold scratch offsets
-  const size_t budget = (size_t)std::max(0, max_smem - 2048);
+  // TSQR blocks and stacks must leave room for the kernels' own static shared memory
+  const size_t budget = (size_t)std::max(0, max_smem - 8192);
+  const size_t over = qr_smem_overhead(es);
   auto smem_fits = [&](int64_t m, int k) {
-    return ((size_t)((m * k + 15) / 16 * 16) + (size_t)8 * m) * es + (size_t)20 * 1024 <= (size_t)max_smem;
+    return ((size_t)((m * k + 15) / 16 * 16) + (size_t)8 * m) * es + over <= (size_t)max_smem;
   };
   auto scratch = [&](int64_t elems) { return (void*)(uintptr_t)(elems * es); };
   int64_t off = 0;
@@ -58,7 +60,7 @@ static QrBatch make_qr_batch(TaskBuf& tb, const std::vector<QrTask>& v, int es, 
       plain.push_back(t);
       continue;
     }
-    int mfit = (int)(((int64_t)max_smem - 20 * 1024) / es / (k + 8)) - 16;
+    int mfit = (int)(((int64_t)max_smem - (int64_t)over) / es / (k + 8)) - 16;
     while (mfit > k && !smem_fits(mfit, k)) --mfit;
     const int nbr = mfit > 0 ? (m + mfit - 1) / mfit : 0;
     const int mb = nbr > 0 ? (m + nbr - 1) / nbr : 0;
@@ -144,7 +146,7 @@ int build_plan(hm_sys_s* sys) {
   const hm_opts& o = sys->ctx->opts;
   const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
   const int nf = sys->nf;
-  const int S = o.samples;
+  const int S0 = o.samples;
   P.fg.assign(nf, FrontGeom());
   int maxlev = 0;
   for (int q = 0; q < nf; ++q) {
@@ -189,6 +191,7 @@ int build_plan(hm_sys_s* sys) {
       h.np = g.np;
       h.nu = g.nu;
       h.L = hodlr_depth(g.np, o.hodlr_leaf);
+      const int S = sys->level_width.empty() ? S0 : sys->level_width[g.level];  // sketch width cap
       h.kf = g.nu > 0 ? std::min(S, std::min(g.nu, g.np)) : 0;
       // node ranges level by level
       std::vector<std::pair<int, int>> ranges = {{0, g.np}};
@@ -264,7 +267,7 @@ int build_plan(hm_sys_s* sys) {
 
   // ---------------------------------------------------------------- allocations
   auto A = [&](void** p, int64_t elems, int size) -> int {
-    return dev_alloc(sys, p, (size_t)std::max<int64_t>(elems, 1) * size);
+    return dev_alloc_ctx(sys->ctx, &sys->plan_allocs, p, (size_t)std::max<int64_t>(elems, 1) * size);
   };
   HM_TRY(A(&sys->d_front, P.front_total, es));
   HM_TRY(A(&sys->d_bo, P.bo_total, es));
@@ -550,12 +553,12 @@ int build_plan(hm_sys_s* sys) {
     lp.schurF = tb.add_gemm(sF);
   }
   P.factor_bytes = fbytes;
-  HM_TRY(dev_alloc(sys, &sys->d_qrs, (size_t)std::max<int64_t>(P.qr_scratch, 1) * es));
+  HM_TRY(A(&sys->d_qrs, P.qr_scratch, es));
   tb.relocate(sys->d_qrs);  // row-block QR tasks address the scratch by offset until now
-  HM_TRY(dev_alloc(sys, &P.d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
-  HM_TRY(dev_alloc(sys, (void**)&P.d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));
+  HM_TRY(A(&P.d_split_ws, tb.split_ws, es));
+  HM_TRY(A((void**)&P.d_split_cnt, tb.split_slots, (int)sizeof(unsigned)));
   HM_CUDA(cudaMemsetAsync(P.d_split_cnt, 0, sizeof(unsigned) * std::max(tb.split_slots, 1), sys->ctx->stream));
-  HM_TRY(dev_alloc(sys, (void**)&P.d_tasks, std::max<size_t>(tb.host.size(), 16)));
+  HM_TRY(A((void**)&P.d_tasks, (int64_t)std::max<size_t>(tb.host.size(), 16), 1));
   HM_CUDA(cudaMemcpyAsync(P.d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));
   return HM_OK;
@@ -843,6 +846,18 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   sys->solve_plans[nrhs] = std::move(sp);
   host_mark("solve plan: built");
   return HM_OK;
+}
+
+}  // namespace hm
+
+namespace hm {
+
+int rebuild_plan(hm_sys_s* sys) {
+  HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
+  release_solve_state(sys);
+  dev_free_all(sys->ctx, &sys->plan_allocs);
+  sys->plan = Plan();
+  return build_plan(sys);
 }
 
 }  // namespace hm

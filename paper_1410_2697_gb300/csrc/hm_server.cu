@@ -1,22 +1,23 @@
 // hm_server.cu -- serving runtime: a request loop over many matrices that keeps their
-// factorizations resident on the device, batches the right-hand sides that wait for the
-// same matrix into one multi-RHS solve (continuous batching), admits work by an HBM
-// budget, and overlaps the work of different matrices on the device.
+// factorizations resident on the device, solves the right-hand sides of one matrix
+// together and lets new ones join a running solve (continuous batching), admits work by
+// an HBM budget, and overlaps the work of different matrices on the device.
 //
 // Design.  The server owns W worker threads, each with its own context (CUDA stream and
-// stream-ordered memory pool, budget = total budget / W).  A matrix is bound to one
-// worker when it is registered (round robin), so its system (analysis, factors, apply
-// plans, GMRES workspace) lives in that worker's context and every call on it comes
-// from that thread.  Workers run concurrently, so solves of matrices on different
-// workers overlap on the GPU.  A worker takes the oldest waiting request, joins every
-// other waiting request for the same matrix (in arrival order, up to max_batch_rhs
-// right-hand sides in all) and solves them in one hm_solve: each right-hand side is its
-// own GMRES instance, so a request's answer does not depend on its companions beyond
-// rounding.  The first request for a matrix analyses and factors it (a miss); the
-// system then stays resident until evicted.  Admission: when an allocation of the
-// worker's context would exceed its budget, the least recently used resident system of
-// that worker is destroyed and the step retried; a matrix that does not fit alone fails
-// its requests with HM_ERR_OUT_OF_MEMORY.
+// stream-ordered memory pool, budget = total budget / W).  Requests wait in one queue.
+// A free worker takes the oldest waiting request whose matrix no other worker is
+// serving; a matrix that is not resident is bound to the worker that takes it (analyse +
+// factor: a miss) and stays resident in that worker's context until evicted.  The worker
+// then runs a GMRES session over a fixed number of slots (right-hand-side columns, each
+// its own GMRES instance): every waiting request for the matrix that fits the free slots
+// is put in, and after each restart cycle the converged requests leave (their answers
+// are returned at once) and newly arrived requests for the matrix take the free slots.
+// A request therefore never waits for a running solve of its matrix to finish, and its
+// answer is the one it gets alone (each column has its own Krylov space and its own
+// restart boundaries).  Workers run concurrently, so solves of different matrices
+// overlap on the GPU.  Admission: when an allocation of the worker's context would
+// exceed its budget, the least recently used resident system of that worker is destroyed
+// and the step retried; a matrix that does not fit alone fails with HM_ERR_OUT_OF_MEMORY.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -33,7 +34,9 @@ namespace hm {
 using Clock = std::chrono::steady_clock;
 
 struct SrvMatrix {
-  int n = 0, dim = 0, worker = 0;
+  int n = 0, dim = 0;
+  int worker = -1;              // worker whose context holds the resident system (-1: none)
+  int serving = -1;             // worker running a session on it now (-1: none)
   double tol = 0;
   std::vector<int64_t> rowptr;
   std::vector<int32_t> colidx, coords;
@@ -59,9 +62,8 @@ struct SrvRequest {
 struct SrvWorker {
   hm_ctx_t ctx = nullptr;
   std::thread th;
-  std::deque<SrvRequest*> q;
   int64_t clock = 0;
-  SrvMatrix* last = nullptr;  // matrix of the previous batch
+  SrvMatrix* last = nullptr;  // matrix of the previous session
 };
 
 }  // namespace hm
@@ -71,11 +73,13 @@ struct hm_server_s {
   std::condition_variable cv_work, cv_done;
   bool stop = false;
   int max_batch_rhs = 64;
+  std::deque<hm::SrvRequest*> q;   // waiting requests, in arrival order
   std::vector<hm::SrvWorker> workers;
   std::vector<std::unique_ptr<hm::SrvMatrix>> matrices;  // stable addresses
   std::vector<std::unique_ptr<hm::SrvRequest>> requests;  // index = id
   std::vector<double> latency_ms;
   int64_t completed = 0, failed = 0, batches = 0, batched_rhs = 0, factorizations = 0, evictions = 0;
+  int64_t joined = 0;  // requests that entered a running session
 };
 
 namespace hm {
@@ -90,15 +94,19 @@ static bool evict_one(hm_server_s* S, int w, int keep) {
     std::lock_guard<std::mutex> lk(S->mu);
     for (int m = 0; m < (int)S->matrices.size(); ++m) {
       SrvMatrix* M = S->matrices[m].get();
-      if (M->worker != w || !M->sys || m == keep) continue;
+      if (M->worker != w || !M->sys || m == keep || M->serving >= 0) continue;
       if (!victim || M->last_use < victim->last_use) victim = M;
     }
     if (!victim) return false;
     S->evictions++;
   }
   hm_destroy(victim->sys);
-  victim->sys = nullptr;
-  victim->bytes = 0;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    victim->sys = nullptr;
+    victim->bytes = 0;
+    victim->worker = -1;
+  }
   if (S->workers[w].last == victim) S->workers[w].last = nullptr;
   return true;
 }
@@ -128,103 +136,189 @@ static int make_resident(hm_server_s* S, int w, int m, SrvMatrix& M) {
   }
 }
 
+// Completes request r (status st; x already written) under the server lock.
+static void finish(hm_server_s* S, SrvRequest* r, int st, const hm_solve_info& info, int batch_rhs) {
+  r->status = st;
+  r->info = info;
+  r->batch_rhs = batch_rhs;
+  r->t_done = Clock::now();
+  r->done = true;
+  if (st == HM_OK) {
+    S->completed++;
+    S->latency_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+  } else {
+    S->failed++;
+  }
+}
+
+// Moves the waiting requests for matrix m (arrival order) that fit `free_slots` from the
+// queue into `out`; the caller holds the lock.
+static void take_requests(hm_server_s* S, int m, int free_slots, std::vector<SrvRequest*>* out) {
+  for (auto it = S->q.begin(); it != S->q.end() && free_slots > 0;) {
+    SrvRequest* r = *it;
+    if (r->matrix == m && r->nrhs <= free_slots) {
+      out->push_back(r);
+      free_slots -= r->nrhs;
+      it = S->q.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// A GMRES session on matrix M: requests join at restart boundaries, leave when done.
+// Every request the session takes is appended to `owned`: the caller fails those still
+// open if the session returns an error.
+static int run_session(hm_server_s* S, int w, int m, SrvMatrix& M, std::vector<SrvRequest*>& owned) {
+  const std::vector<SrvRequest*> first = owned;
+  int rhs0 = 0;
+  for (SrvRequest* r : first) rhs0 += r->nrhs;
+  // slots: room for about as many joiners as the session starts with, within the GMRES
+  // workspace a quarter of the worker's budget allows ((2 restart + 6) FP64 vectors each)
+  int slots = 1;
+  while (slots < std::min(2 * rhs0, S->max_batch_rhs)) slots *= 2;
+  slots = std::min(slots, S->max_batch_rhs);
+  const hm_opts& o = S->workers[w].ctx->opts;
+  if (o.hbm_budget) {
+    const double per_col = (2.0 * o.restart + 6.0) * 8.0 * (double)M.n;
+    slots = std::max(rhs0 > 0 ? std::min(rhs0, S->max_batch_rhs) : 1,
+                     std::min(slots, (int)(0.25 * (double)o.hbm_budget / per_col)));
+  }
+  int st = gm_session_begin(M.sys, slots);
+  while (st == HM_ERR_OUT_OF_MEMORY && evict_one(S, w, m)) st = gm_session_begin(M.sys, slots);
+  if (st != HM_OK) return st;
+  struct Live { SrvRequest* r; int slot0; };
+  std::vector<Live> live;
+  std::vector<char> used(slots, 0);
+  const size_t n = (size_t)M.n;
+  auto put = [&](SrvRequest* r) -> int {
+    int s0 = -1;  // first run of r->nrhs free slots
+    for (int k = 0; k + r->nrhs <= slots && s0 < 0; ++k) {
+      bool ok = true;
+      for (int c = 0; c < r->nrhs; ++c) ok = ok && !used[k + c];
+      if (ok) s0 = k;
+    }
+    if (s0 < 0) return HM_ERR_CAPACITY;
+    for (int c = 0; c < r->nrhs; ++c) {
+      HM_TRY(gm_session_put(M.sys, s0 + c, r->b + n * c, r->rtol, 4000));
+      used[s0 + c] = 1;
+    }
+    live.push_back(Live{r, s0});
+    return HM_OK;
+  };
+  int total_rhs = 0;
+  for (SrvRequest* r : first) {
+    HM_TRY(put(r));
+    total_rhs += r->nrhs;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->batches++;
+    S->batched_rhs += total_rhs;
+  }
+  while (!live.empty()) {
+    int its = 0;
+    HM_TRY(gm_session_cycle(M.sys, &its));
+    // requests whose every column converged (or hit its cap) leave
+    std::vector<std::pair<SrvRequest*, std::pair<int, hm_solve_info>>> done;
+    for (size_t i = 0; i < live.size();) {
+      SrvRequest* r = live[i].r;
+      bool all = true, conv = true;
+      hm_solve_info info{};
+      info.converged = 1;
+      for (int c = 0; c < r->nrhs; ++c) {
+        double rr = 0;
+        int it = 0;
+        const int state = gm_session_state(M.sys, live[i].slot0 + c, &rr, &it);
+        all = all && state != 0;
+        conv = conv && state == 1;
+        info.iters = std::max(info.iters, it);
+        info.relres = std::max(info.relres, rr);
+      }
+      if (!all) { ++i; continue; }
+      info.converged = conv ? 1 : 0;
+      for (int c = 0; c < r->nrhs; ++c) {
+        HM_TRY(gm_session_take(M.sys, live[i].slot0 + c, r->x + n * c));
+        used[live[i].slot0 + c] = 0;
+      }
+      done.push_back({r, {conv ? HM_OK : HM_ERR_NO_CONVERGENCE, info}});
+      live.erase(live.begin() + (long)i);
+    }
+    std::vector<SrvRequest*> joiners;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto& d : done) finish(S, d.first, d.second.first, d.second.second, slots);
+      if (!done.empty()) S->cv_done.notify_all();
+      int free_slots = 0;
+      for (int k = 0; k < slots; ++k) free_slots += used[k] ? 0 : 1;
+      take_requests(S, m, free_slots, &joiners);
+      owned.insert(owned.end(), joiners.begin(), joiners.end());
+      S->joined += (int64_t)joiners.size();
+      int add = 0;
+      for (SrvRequest* r : joiners) add += r->nrhs;
+      S->batched_rhs += add;
+    }
+    for (SrvRequest* r : joiners) {
+      const int ps = put(r);
+      if (ps == HM_ERR_CAPACITY) {  // no contiguous run of free slots: back to the queue's head
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->batched_rhs -= r->nrhs;
+        S->joined -= 1;
+        owned.erase(std::find(owned.begin(), owned.end(), r));
+        S->q.push_front(r);
+        S->cv_work.notify_all();
+      } else if (ps != HM_OK) {
+        return ps;
+      }
+    }
+    M.last_use = ++S->workers[w].clock;
+  }
+  return HM_OK;
+}
+
 static void worker_loop(hm_server_s* S, int w) {
   SrvWorker& W = S->workers[w];
   cudaSetDevice(W.ctx->opts.device);
-  std::vector<double> B, X;
   for (;;) {
     std::vector<SrvRequest*> batch;
+    int m = -1;
+    SrvMatrix* Mp = nullptr;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] { return S->stop || !W.q.empty(); });
-      if (W.q.empty()) return;  // stopping and drained
-      // continuous batching: the oldest request and every later one for its matrix
-      const int m = W.q.front()->matrix;
-      int rhs = 0;
-      for (auto it = W.q.begin(); it != W.q.end();) {
-        SrvRequest* r = *it;
-        if (r->matrix == m && (batch.empty() || rhs + r->nrhs <= S->max_batch_rhs)) {
-          batch.push_back(r);
-          rhs += r->nrhs;
-          it = W.q.erase(it);
-        } else {
-          ++it;
+      // the oldest request whose matrix nobody serves and that is resident here or nowhere
+      auto pick = [&]() -> bool {
+        for (SrvRequest* r : S->q) {
+          SrvMatrix* M = S->matrices[r->matrix].get();
+          if (M->serving < 0 && (M->worker < 0 || M->worker == w)) {
+            m = r->matrix;
+            Mp = M;
+            return true;
+          }
         }
-      }
-    }
-    const int m = batch.front()->matrix;
-    SrvMatrix* Mp;
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      Mp = S->matrices[m].get();
+        return false;
+      };
+      S->cv_work.wait(lk, [&] { return S->stop || pick(); });
+      if (!Mp) return;  // stopping, and nothing this worker can take
+      Mp->serving = w;
+      Mp->worker = w;
+      take_requests(S, m, S->max_batch_rhs, &batch);
     }
     SrvMatrix& M = *Mp;
     // one system's transient solve state (apply plans, GMRES workspace) per worker
     if (W.last && W.last != Mp && W.last->sys) release_solve_state(W.last->sys);
     W.last = Mp;
     int st = make_resident(S, w, m, M);
-    int nrhs = 0;
-    double rtol = 1.0;
-    for (SrvRequest* r : batch) { nrhs += r->nrhs; rtol = std::min(rtol, r->rtol); }
-    hm_solve_info info{};
     if (st == HM_OK) {
       M.last_use = ++W.clock;
-      const size_t n = (size_t)M.n;
-      B.assign(n * nrhs, 0.0);
-      X.assign(n * nrhs, 0.0);
-      int c = 0;
-      for (SrvRequest* r : batch) {
-        std::copy(r->b, r->b + n * r->nrhs, B.begin() + n * c);
-        c += r->nrhs;
-      }
-      // The GMRES workspace grows with n x right-hand sides ((2 restart + 6) FP64 vectors
-      // per column); columns are solved in chunks that keep it within a quarter of the
-      // worker's budget, so large systems do not evict their neighbours for workspace.
-      const hm_opts& o = W.ctx->opts;
-      int chunk = nrhs;
-      if (o.hbm_budget) {
-        const double per_col = (2.0 * o.restart + 6.0) * 8.0 * (double)n;
-        chunk = std::max(1, std::min(nrhs, (int)(0.25 * (double)o.hbm_budget / per_col)));
-      }
-      info.converged = 1;
-      for (int c0 = 0; c0 < nrhs && (st == HM_OK || st == HM_ERR_NO_CONVERGENCE); c0 += chunk) {
-        const int nc = std::min(chunk, nrhs - c0);
-        hm_solve_info ci{};
-        int cs = hm_solve(M.sys, nc, B.data() + n * c0, rtol, 4000, X.data() + n * c0, &ci);
-        while (cs == HM_ERR_OUT_OF_MEMORY && evict_one(S, w, m))  // workspace: make room
-          cs = hm_solve(M.sys, nc, B.data() + n * c0, rtol, 4000, X.data() + n * c0, &ci);
-        if (st == HM_OK) st = cs;
-        info.iters = std::max(info.iters, ci.iters);
-        info.restarts = std::max(info.restarts, ci.restarts);
-        info.relres = std::max(info.relres, ci.relres);
-        info.converged = info.converged && ci.converged;
-      }
-      if (st == HM_OK || st == HM_ERR_NO_CONVERGENCE) {
-        c = 0;
-        for (SrvRequest* r : batch) {
-          std::copy(X.begin() + n * c, X.begin() + n * (c + r->nrhs), r->x);
-          c += r->nrhs;
-        }
-      }
+      st = run_session(S, w, m, M, batch);
     }
-    const Clock::time_point now = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
-    S->batches++;
-    S->batched_rhs += nrhs;
-    for (SrvRequest* r : batch) {
-      r->status = st;
-      r->info = info;
-      r->batch_rhs = nrhs;
-      r->t_done = now;
-      r->done = true;
-      if (st == HM_OK) {
-        S->completed++;
-        S->latency_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
-      } else {
-        S->failed++;
-      }
-    }
+    if (!M.sys) M.worker = -1;
+    M.serving = -1;
+    for (SrvRequest* r : batch)  // requests still open after a failure fail with it
+      if (!r->done) finish(S, r, st == HM_OK ? HM_ERR_CUDA : st, hm_solve_info{}, 0);
     S->cv_done.notify_all();
+    S->cv_work.notify_all();  // the matrix is free for other workers again
   }
 }
 
@@ -288,7 +382,6 @@ int hm_server_add_matrix(hm_server_t S, int32_t n, const int64_t* rowptr, const 
   M.values.assign(values, values + nnz);
   M.coords.assign(grid_coords, grid_coords + (size_t)n * dim);
   std::lock_guard<std::mutex> lk(S->mu);
-  M.worker = (int)(S->matrices.size() % S->workers.size());
   S->matrices.push_back(std::make_unique<SrvMatrix>(std::move(M)));
   *matrix_id = (int32_t)S->matrices.size() - 1;
   return HM_OK;
@@ -313,7 +406,7 @@ int hm_server_submit(hm_server_t S, int32_t matrix_id, int32_t nrhs, const doubl
   r->x = x;
   r->rtol = rtol;
   r->t_submit = Clock::now();
-  S->workers[S->matrices[matrix_id]->worker].q.push_back(r.get());
+  S->q.push_back(r.get());
   *request_id = r->id;
   S->requests.push_back(std::move(r));
   S->cv_work.notify_all();
@@ -350,6 +443,7 @@ int hm_server_get_stats(hm_server_t S, hm_server_stats* st) {
   size_t resident = 0;
   for (auto& W : S->workers) resident += W.ctx->allocated;
   st->device_bytes = (double)resident;
+  st->joined = S->joined;
   return HM_OK;
 }
 
@@ -364,7 +458,7 @@ int hm_server_destroy(hm_server_t S) {
     if (W.th.joinable()) W.th.join();
   // the worker threads are gone: free every resident system and context from here
   for (auto& M : S->matrices)
-    if (M->sys) {
+    if (M->sys && M->worker >= 0) {
       cudaSetDevice(S->workers[M->worker].ctx->opts.device);
       hm_destroy(M->sys);
     }

@@ -391,7 +391,7 @@ static void gemm_b(hm_ctx_s* ctx, const SolvePlan* sp, const GemmBatch& b) {
     return;
   }
   launch_gemm<T>(b.tasks.dev(sp->d_tasks), b.tiles.dev(sp->d_tasks), b.tiles.count, b.bn,
-                 v == 3 ? 0 : v, (T*)sp->d_split_ws,
+                 v >= 3 ? 0 : v, (T*)sp->d_split_ws,
                  sp->d_split_cnt, ctx->stream);
 }
 

@@ -91,7 +91,7 @@ def test_tol0_hodlr_preconditioner_is_exact(name):
     """FP64, HODLR fronts with every sampled direction kept and sketches as wide as the
     blocks: the preconditioner is A^{-1} up to rounding."""
     p = PROBLEMS[name]
-    s = make(p, hm.HM_PREC_FP64, nd_leaf=16, hodlr_leaf=8, n_c=8, samples=112)
+    s = make(p, hm.HM_PREC_FP64, nd_leaf=16, hodlr_leaf=8, n_c=8, samples=64)
     info = s.factor(p.values, 0.0)
     assert info["n_hodlr"] > 0
     r = rhs_uniform(p.n, 3, 7)
@@ -263,3 +263,93 @@ def test_graph_replayed_apply_is_bitwise_the_eager_apply(prec):
     for z in outs:
         assert np.array_equal(z, eager)
     s.close()
+
+
+def test_adaptive_width_is_ignored_in_fp64():
+    p = PROBLEMS["q1_33_lognormal"]
+    o = hm.hm_default_opts()
+    o.precision, o.nd_leaf, o.hodlr_leaf, o.n_c, o.samples, o.adaptive_rank = 0, 64, 8, 8, 4, 1
+    ctx = hm.hm_create(o)
+    s = hm.hm_analyze(ctx, p.n, p.rowptr, p.colidx, 2, p.coords)
+    info = hm.hm_factor(s, p.values, 1e-6)
+    assert info["refactorizations"] == 0 and info["max_width"] <= 4 and info["rank_capped"] > 0
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [1])
+def test_adaptive_width_growth_matches_oracle(prec):
+    """Adaptive rank (hm_opts.adaptive_rank, FP32): from a 4-column sketch the GPU doubles
+    the width of every front level holding a capped block and factors again, the oracle
+    applies the same rule; the widths reached (each block's column capacity) agree, no
+    block stays capped, every block matches the oracle's (same sketch) within the FP32
+    block bound and the solve converges."""
+    p = PROBLEMS["q1_33_lognormal"]
+    leaf, hl, nc, tol = 64, 8, 8, 1e-6
+    et = nd.nested_dissection(p.coords, leaf)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    prm = hodlr_mf.Params(tol=tol, n_c=nc, leaf=hl, compressor="rrf", samples=4, seed=0x5EED, adaptive=True,
+                          max_samples=64 if prec == 0 else 96)
+    fr, tr = hodlr_mf.factor(Ap, et, sym, prm, keep=True)
+    o = hm.hm_default_opts()
+    o.precision, o.nd_leaf, o.hodlr_leaf, o.n_c, o.samples, o.adaptive_rank = prec, leaf, hl, nc, 4, 1
+    ctx = hm.hm_create(o)
+    s = hm.hm_analyze(ctx, p.n, p.rowptr, p.colidx, 2, p.coords)
+    info = hm.hm_factor(s, p.values, tol)
+    assert info["refactorizations"] >= 1 and info["rank_capped"] == 0, info
+    assert info["max_width"] == max(tr["widths"].values())
+    nblocks = 0
+    for q in range(et.nfronts):
+        if fr[q].kind != "hodlr":
+            continue
+        w = tr["widths"].get(int(et.level[q]), 4)
+        for (lv, nd_), Bo in _oracle_blocks(fr[q]).items():
+            if Bo.size == 0:
+                continue
+            U, V, r = hm.hm_get_hodlr_block(s, q, lv, nd_)
+            assert U.shape[1] >= min(w, *Bo.shape)  # the level's width reached the GPU too
+            err = np.linalg.norm(U @ V.T - Bo, 2) / max(np.linalg.norm(Bo, 2), 1e-300)
+            # FP32: the factor's single-precision rounding (about 2e-5 of a block here)
+            assert err <= (1e-9 if prec == 0 else 5 * tol + 5e-5), (q, lv, nd_, err)
+            nblocks += 1
+    assert nblocks > 0
+    b = rhs_uniform(p.n, 1, 3)
+    x = np.zeros_like(b)
+    si = hm.hm_solve(s, 1, b, 1e-10, 500, x)
+    assert si["converged"] == 1
+    # a second analysis of the same shape in this context starts from the learned widths
+    s2 = hm.hm_analyze(ctx, p.n, p.rowptr, p.colidx, 2, p.coords)
+    info2 = hm.hm_factor(s2, p.values, tol)
+    assert info2["refactorizations"] == 0 and info2["rank_capped"] == 0
+    hm.hm_destroy(s2)
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(ctx)
+
+
+def test_tensor_core_3xtf32_gemms_match_simt():
+    """The FP32 tensor-core GEMM variant (tcgen05 kind::tf32 with every operand split into
+    a TF32 part and its remainder, three MMAs per step) keeps FP32 accuracy: forced on
+    every GEMM site of the factorization it gives the same Schur updates U_p as the SIMT
+    GEMMs to FP32 rounding (2e-5 of the largest entry over the tree), the same ranks up
+    to the truncation threshold, and the same GMRES iteration count within one."""
+    p = q1_square(96, lognormal_coefficients(96 * 96, 1.0, seed=8))
+    out = {}
+    for v in (0, 4):
+        s = make(p, hm.HM_PREC_MIXED, nd_leaf=64, hodlr_leaf=32, n_c=32, samples=48)
+        hm.hm_tune_force(s.ctx, v)
+        s.factor(p.values, 1e-4)
+        _, nf = hm.hm_get_sizes(s.sys)
+        nupd, _, _, _ = hm.hm_get_symbolic(s.sys)
+        ups = {q: hm.hm_get_update(s.sys, q, int(nupd[q])) for q in range(nf) if 0 < nupd[q]}
+        b = rhs_uniform(p.n, 2, 9)
+        x = np.zeros_like(b)
+        x, info = s.solve(b, rtol=1e-10, x=x)
+        assert info["converged"] == 1
+        out[v] = (ups, info["iters"], x)
+        s.close()
+    (u0, it0, x0), (u4, it4, x4) = out[0], out[4]
+    worst = max(np.abs(np.tril(u4[q]) - np.tril(u0[q])).max() / max(np.abs(u0[q]).max(), 1e-300) for q in u0)
+    assert worst <= 2e-5, worst
+    assert abs(it4 - it0) <= 1
+    assert np.linalg.norm(x4 - x0) / np.linalg.norm(x0) <= 1e-8

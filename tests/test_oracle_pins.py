@@ -523,3 +523,41 @@ def test_kappa_estimate_matches_closed_form_spectrum():
     k = condest.kappa_estimate(A, lu.solve, 60, seed=3)
     kappa = lam.max() / lam.min()
     assert 0.99 * kappa <= k <= kappa * (1 + 1e-8)
+
+
+def test_hodlr_mf_adaptive_width_meets_the_tolerance_rule():
+    """Adaptive rank (Section 2.2: the rank is set by the tolerance, not by the sketch):
+    with a 4-column sketch most blocks of this problem have more than 4 singular values
+    above tol sigma_1, so the fixed-width range finder truncates them far above tol;
+    doubling the width of every level that holds a capped block until none is capped
+    brings every block (checked against its SVD) to within 2 tol sigma_1, the range
+    finder's error with a one-column oversampling margin at worst."""
+    p = q1_square(48, lognormal_coefficients(48 * 48, 1.0, seed=5))
+    et, sym, Ap = _setup(p, 16)
+    tol = 1e-6
+    worst = {}
+    for adaptive in (False, True):
+        prm = hodlr_mf.Params(tol=tol, n_c=8, leaf=8, compressor="rrf", samples=4, adaptive=adaptive)
+        fr, tr = hodlr_mf.factor(Ap, et, sym, prm, keep=True)
+        w = 0.0
+        for q, f in enumerate(fr):
+            if f.kind != "hodlr":
+                continue
+            F, npv = tr["F"][q], f.npiv
+            width = tr["widths"].get(int(et.level[q]), 4)
+            blocks = [(F[npv:, :npv], f.W, f.V)] if f.W.shape[0] else []
+            for node in hodlr.iter_nodes(f.H):
+                if node.children:
+                    a, b = node.children
+                    blocks.append((F[a.lo:a.hi, b.lo:b.hi], node.U, node.V))
+            for B, U, V in blocks:
+                s = np.linalg.svd(B, compute_uv=False)
+                w = max(w, np.linalg.norm(B - U @ V.T, 2) / s[0])
+                if adaptive:  # no block is cut by its width any more
+                    assert U.shape[1] < min(width, *B.shape) or width >= min(B.shape), (q, U.shape, width)
+        worst[adaptive] = w
+        if adaptive:
+            assert max(tr["widths"].values()) > 4
+            assert all(v <= 96 for v in tr["widths"].values())
+    assert worst[False] > 1e3 * tol
+    assert worst[True] <= 2 * tol, worst
