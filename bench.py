@@ -56,6 +56,9 @@ def parse_args():
                              "serving"])
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: length of the arrival trace")
     ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-rate", type=float, default=200.0,
+                    help="serving: mean arrivals per second (200 = the workload; a lower rate measures "
+                         "latency below saturation)")
     ap.add_argument("--serve-seq", type=int, default=24,
                     help="serving: requests of the trace replayed sequentially in FP64 (baseline)")
     ap.add_argument("--nrhs", type=int, default=None, help="default: the workload's")
@@ -515,6 +518,11 @@ def run_ours(args, rank, world, local):
                    "rank_capped": fi["rank_capped"], "factor_bytes": fi["factor_bytes"],
                    "max_sketch_width": fi["max_width"], "refactorizations": fi["refactorizations"],
                    "adaptive_rank": bool(args.adaptive_rank)},
+        "memory_gb": {"stored_factor": fi["stored_bytes"] / 1e9, "device_after_factor": fi["device_bytes"] / 1e9,
+                      "front_arena": fi["front_bytes"] / 1e9,
+                      "conventional_L": fi["conventional_bytes"] / 1e9,
+                      "conventional_peak": fi["conventional_peak_bytes"] / 1e9,
+                      "note": "conventional multifrontal Cholesky on the same ordering, same precision"},
         "fp64_plain": {"value": nsolve * k64 * world / (total64 * 1e-3), "ms_per_step": total64 / k64,
                        "steps": k64, "gmres_iters": infos64[-1][1]["iters"]},
         "roofline": rl,
@@ -670,7 +678,7 @@ def run_reference(args, rank, world):
 
 
 def run_serving(args):
-    """Serving stream: Poisson arrivals (mean 200 requests/s, seed 6) for `--serve-seconds`
+    """Serving stream: Poisson arrivals (mean `--serve-rate`, 200 requests/s, seed 6) for `--serve-seconds`
     (60 by default) over 24 matrices -- 8 each of the Q1 64^2, Q1 1024^2 (lognormal sigma 1)
     and hex 64^3 (lognormal sigma 0.5) sizes with coefficient seeds 11-18, 21-28, 31-38 --
     picked uniformly (seed 7), 1-64 right-hand sides each (seed 7), served by hm_server
@@ -695,7 +703,7 @@ def run_serving(args):
     rng_p = np.random.Generator(np.random.PCG64(7))
     t, trace = 0.0, []
     while True:
-        t += rng_a.exponential(1.0 / 200.0)
+        t += rng_a.exponential(1.0 / args.serve_rate)
         if t > args.serve_seconds:
             break
         trace.append((t, int(rng_p.integers(0, len(mats))), int(rng_p.integers(1, 65))))
@@ -756,14 +764,15 @@ def run_serving(args):
         "warmup": 0, "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 factor/apply + f64 GMRES", "data": "synthetic",
         "config": {"workload": "serving", "matrices": "8 x Q1 64^2, 8 x Q1 1024^2, 8 x hex 64^3",
-                   "arrivals": f"Poisson 200/s for {args.serve_seconds} s, open loop ({len(trace)} requests, "
+                   "arrivals": f"Poisson {args.serve_rate:g}/s for {args.serve_seconds} s, open loop ({len(trace)} requests, "
                                f"{rhs_total} right-hand sides)", "rtol": RTOL, "tol": 1e-4,
                    "workers": args.serve_workers, "max_batch_rhs": 64, "hbm_budget_gb": 150,
                    "answers": "one reused host buffer per matrix; relres checked per request"},
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "rhs_per_s": rhs_total / el, "relres": worst,
         "failed_requests": fails,
         "server": {k2: st[k2] for k2 in ("completed", "failed", "batches", "batched_rhs", "joined",
-                                          "factorizations", "evictions", "device_bytes")},
+                                          "factorizations", "evictions", "oom_retries", "device_bytes")},
+        "saturated": len(trace) / el < 0.9 * args.serve_rate,
         "fp64_sequential": {"value": k / el64, "unit": "requests/s", "requests": k,
                             "sample": "requests drawn from the trace (seed 8), replayed one after another",
                             "p50_ms": st64["p50_ms"], "p99_ms": st64["p99_ms"]},
@@ -818,7 +827,8 @@ def run_tol_sweep(args):
         fms, sms, fi, si = rec[len(rec) // 2]
         points.append({"tol": tol, "analyze_factor_ms": fms, "solve_ms": sms, "gmres_iters": si["iters"],
                        "max_rank": fi["max_rank"], "rank_capped": fi["rank_capped"],
-                       "factor_bytes": fi["factor_bytes"], "relres": worst,
+                       "factor_bytes": fi["factor_bytes"], "stored_factor_gb": fi["stored_bytes"] / 1e9,
+                       "conventional_L_gb": fi["conventional_bytes"] / 1e9, "relres": worst,
                        "solves_per_s": nrhs / ((fms + sms) * 1e-3)})
     hm.hm_ctx_destroy(ctx)
     return {"sweep": "compression tolerance", "workload": f"q1_lognormal_{m}x{m}", "nrhs": nrhs,

@@ -101,6 +101,22 @@ typedef struct hm_opts {
                             the tensor-core GEMM end with one more bounded wait, on a
                             barrier nothing arrives on, so the factorization reports
                             HM_ERR_DEVICE_TIMEOUT through the path a real timeout takes  */
+  int compress_ff;       /* 1: a HODLR front's update block F_ff is first replaced by its
+                            own HODLR approximation F_ff^HODLR (Section 4.2.1: every
+                            off-diagonal block of F_ff's HODLR tree, leaf hodlr_leaf,
+                            compressed by the range finder at tol with the level's sketch
+                            width), so the update passed to the parent is
+                            F_ff^HODLR - W T W^T (Eq. update_HODLR).  The approximation is
+                            written back into the dense front (the extend-add stays dense).
+                            Range finder only (HM_ERR_INVALID_ARG with BDLR); 0 = off    */
+  int keep_fronts;       /* 0 (default): the dense front storage is reused across tree
+                            levels (two banks, one for even and one for odd depths: a level's
+                            fronts live until their parents have absorbed their updates), so
+                            the transient fronts take the two largest level sums instead of
+                            all levels; the factor the apply needs is packed out of the
+                            fronts level by level.  1: every front keeps its own storage after
+                            the factorization, for hm_get_update (which fails with
+                            HM_ERR_STATE otherwise)                                      */
 } hm_opts;
 
 typedef struct hm_solve_info {
@@ -120,11 +136,23 @@ typedef struct hm_factor_info {
   double front_bytes;    /* bytes of dense front storage                                 */
   int32_t refactorizations; /* extra factorizations the adaptive rank rule ran            */
   int32_t max_width;     /* largest sketch width in use (per front level)                 */
+  /* memory (bytes), the paper's comparison with the conventional method (Section 6):   */
+  double stored_bytes;   /* factor data the preconditioner keeps for the apply: dense fronts'
+                            F_pp^-1, K and K^T; HODLR fronts' bases U / V / Vf, Vtilde, G,
+                            W and leaf inverses                                            */
+  double conventional_bytes; /* the conventional multifrontal Cholesky factor L of the same
+                            ordering in the same precision: sum of np (np + 1) / 2 + np nu */
+  double conventional_peak_bytes; /* the conventional method's peak: L so far plus the live
+                            update matrices plus the current front (lower triangles),
+                            maximum over the fronts in elimination order                  */
+  double device_bytes;   /* device memory this system holds after the factorization
+                            (pattern, plan, fronts, factor, scratch)                      */
 } hm_factor_info;
 
 /* Fill *opts with defaults (device 0, mixed precision, nd_leaf 64, hodlr_leaf 64,
    n_c 64, samples 48, restart 30, dofs_per_node 1, compressor HM_COMP_RRF,
-   bdlr_depth 1, wait_limit 0, adaptive_rank 0, inject_wait_timeout 0).  Never fails
+   bdlr_depth 1, wait_limit 0, adaptive_rank 0, inject_wait_timeout 0, compress_ff 0,
+   keep_fronts 0).  Never fails
    for a non-null pointer.                                                            */
 int hm_default_opts(hm_opts* opts);
 
@@ -300,7 +328,8 @@ int hm_precond_apply_noalloc(hm_sys_t sys, int32_t nrhs, const double* r, double
 
 /* Inspection for tests: the dense Schur-complement update U_p = F_ff - F_fp F_pp^-1 F_pf
    of front p as computed by the last hm_factor (nupd[p]^2 entries, column-major, lower
-   triangle valid, FP64).  Host pointer.                                                */
+   triangle valid, FP64).  Host pointer.  With front storage reuse (keep_fronts 0) only
+   fronts of depth 0 and 1 keep their update; deeper ones give HM_ERR_STATE.            */
 int hm_get_update(hm_sys_t sys, int32_t front, double* U);
 
 /* Inspection: front kind (0 dense, 1 HODLR) and ranks of the last hm_factor.  ranks
@@ -347,7 +376,13 @@ const char* hm_last_error(void);
  * the CSR, FP64 values and lattice coordinates) are analysed + factored on their first
  * request by the worker that takes it, and the factorization stays resident in that
  * worker's context until evicted (least recently used first) to admit another matrix
- * within the budget.  Requests wait in one queue; a free worker takes the oldest one
+ * within the budget.  Admission is by estimate, before the work allocates: a matrix's
+ * estimate is its footprint when last resident (plus an eighth), else the largest bytes
+ * per nonzero seen for matrices of its dimension; a session's is its slots times
+ * (2 restart + 10) FP64 vectors (plus a quarter and 4 MiB); the worker evicts until its
+ * bytes plus the estimate fit.  A shortfall of the
+ * estimate is caught by the budget check of the allocation itself (one more eviction
+ * and a retry, counted in oom_retries).  Requests wait in one queue; a free worker takes the oldest one
  * whose matrix no other worker is serving (and that is resident on it or nowhere) and
  * runs a GMRES session on the matrix: a fixed number of right-hand-side slots (twice the
  * starting columns, at most max_batch_rhs, within a quarter of the worker's budget for
@@ -375,6 +410,8 @@ typedef struct hm_server_stats {
   double p50_ms, p99_ms;         /* latency percentiles of the successful requests      */
   double device_bytes;           /* device memory held by the workers' contexts         */
   int64_t joined;                /* requests that entered a session already running     */
+  int64_t oom_retries;           /* budget misses the admission estimate did not foresee
+                                    (the step was retried after one more eviction)      */
 } hm_server_stats;
 
 int hm_server_create(const hm_opts* opts, int32_t nworkers, int32_t max_batch_rhs, hm_server_t* out);

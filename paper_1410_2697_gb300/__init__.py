@@ -27,11 +27,15 @@ class Solver:
 
     def __init__(self, n, rowptr, colidx, grid_coords=None, dim=0, precision=HM_PREC_MIXED,
                  nd_leaf=64, hodlr_leaf=64, n_c=64, samples=48, restart=30, seed=0x5EED, device=0,
-                 stream=None, hbm_budget=0, perm=None, first=None, parent=None):
+                 stream=None, hbm_budget=0, perm=None, first=None, parent=None, **opts):
         o = hm_default_opts()
         o.device, o.precision, o.nd_leaf, o.hodlr_leaf = device, precision, nd_leaf, hodlr_leaf
         o.n_c, o.samples, o.restart, o.seed, o.hbm_budget = n_c, samples, restart, seed, hbm_budget
         o.stream = stream
+        for k, v in opts.items():  # any other hm_opts field by name
+            if k not in dict(type(o)._fields_):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
         self.ctx = hm_create(o)
         self.n = int(n)
         try:

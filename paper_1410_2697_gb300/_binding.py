@@ -45,7 +45,8 @@ class HmOpts(C.Structure):
                 ("seed", C.c_uint64), ("restart", C.c_int), ("hbm_budget", C.c_size_t),
                 ("stream", C.c_void_p), ("dofs_per_node", C.c_int), ("compressor", C.c_int),
                 ("bdlr_depth", C.c_int), ("wait_limit", C.c_int), ("adaptive_rank", C.c_int),
-                ("inject_wait_timeout", C.c_int)]
+                ("inject_wait_timeout", C.c_int),
+                ("compress_ff", C.c_int), ("keep_fronts", C.c_int)]
 
 
 class HmSolveInfo(C.Structure):
@@ -56,14 +57,16 @@ class HmSolveInfo(C.Structure):
 class HmFactorInfo(C.Structure):
     _fields_ = [("nfronts", C.c_int32), ("nlevels", C.c_int32), ("n_hodlr", C.c_int32),
                 ("max_rank", C.c_int32), ("rank_capped", C.c_int32), ("factor_bytes", C.c_double),
-                ("front_bytes", C.c_double), ("refactorizations", C.c_int32), ("max_width", C.c_int32)]
+                ("front_bytes", C.c_double), ("refactorizations", C.c_int32), ("max_width", C.c_int32),
+                ("stored_bytes", C.c_double), ("conventional_bytes", C.c_double),
+                ("conventional_peak_bytes", C.c_double), ("device_bytes", C.c_double)]
 
 
 class HmServerStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("batches", C.c_int64),
                 ("batched_rhs", C.c_int64), ("factorizations", C.c_int64), ("evictions", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("device_bytes", C.c_double),
-                ("joined", C.c_int64)]
+                ("joined", C.c_int64), ("oom_retries", C.c_int64)]
 
 
 class HmProfEntry(C.Structure):

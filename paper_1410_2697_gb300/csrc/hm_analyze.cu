@@ -657,6 +657,107 @@ void launch_amap(hm_sys_s* sys) {
 }
 
 // ------------------------------------------------------------------------------------
+// A's lower-triangle entries grouped by the tree depth of their front (a counting sort:
+// per block of entries a depth histogram, exclusive offsets depth-major, then placement),
+// so that the factorization scatters one level at a time into reused front storage.
+// The order within a depth is not fixed, but every entry has its own destination.
+// ------------------------------------------------------------------------------------
+__global__ void k_lev_count(const int64_t* __restrict__ amap, const int32_t* __restrict__ pcol,
+                            const int32_t* __restrict__ node_of, const int* __restrict__ flevel, int64_t nnz,
+                            int64_t chunk, int nlev, int64_t* __restrict__ counts) {
+  extern __shared__ int hist[];
+  for (int i = threadIdx.x; i < nlev; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const int64_t b0 = blockIdx.x * chunk, b1 = min(nnz, b0 + chunk);
+  for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x)
+    if (amap[k] >= 0) atomicAdd(&hist[flevel[node_of[pcol[k]]]], 1);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nlev; i += blockDim.x) counts[(int64_t)blockIdx.x * nlev + i] = hist[i];
+}
+
+// Block l: counts[b][l] becomes the number of depth-l entries of blocks before b (an
+// exclusive scan over b, 256 threads, each over a run of consecutive b); range[2 l + 1]
+// receives the depth's total.
+__global__ void __launch_bounds__(256) k_lev_scan(int64_t* __restrict__ counts, int nb, int nlev,
+                                                   int64_t* __restrict__ range) {
+  __shared__ int64_t part[256];
+  const int l = blockIdx.x, t = threadIdx.x;
+  const int run = (nb + 255) / 256, b0 = min(nb, t * run), b1 = min(nb, b0 + run);
+  int64_t s = 0;
+  for (int b = b0; b < b1; ++b) s += counts[(int64_t)b * nlev + l];
+  part[t] = s;
+  __syncthreads();
+  for (int d = 1; d < 256; d <<= 1) {  // inclusive scan of the runs' sums
+    const int64_t v = t >= d ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run0 = t ? part[t - 1] : 0;
+  for (int b = b0; b < b1; ++b) {
+    const int64_t c = counts[(int64_t)b * nlev + l];
+    counts[(int64_t)b * nlev + l] = run0;
+    run0 += c;
+  }
+  if (t == 255) range[2 * l + 1] = part[255];
+}
+
+// range[2 l], range[2 l + 1]: the positions of depth l (depths in order).
+__global__ void k_lev_ranges(int nlev, int64_t* __restrict__ range) {
+  if (threadIdx.x != 0) return;
+  int64_t s = 0;
+  for (int l = 0; l < nlev; ++l) {
+    const int64_t t = range[2 * l + 1];
+    range[2 * l] = s;
+    s += t;
+    range[2 * l + 1] = s;
+  }
+}
+
+__global__ void k_lev_place(const int64_t* __restrict__ amap, const int64_t* __restrict__ psrc,
+                            const int32_t* __restrict__ pcol, const int32_t* __restrict__ node_of,
+                            const int* __restrict__ flevel, int64_t nnz, int64_t chunk, int nlev,
+                            const int64_t* __restrict__ offs, const int64_t* __restrict__ range,
+                            int64_t* __restrict__ src, int64_t* __restrict__ dst) {
+  extern __shared__ int cur[];
+  for (int i = threadIdx.x; i < nlev; i += blockDim.x) cur[i] = 0;
+  __syncthreads();
+  const int64_t b0 = blockIdx.x * chunk, b1 = min(nnz, b0 + chunk);
+  for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+    const int64_t d = amap[k];
+    if (d < 0) continue;
+    const int l = flevel[node_of[pcol[k]]];
+    const int64_t pos = range[2 * l] + offs[(int64_t)blockIdx.x * nlev + l] + atomicAdd(&cur[l], 1);
+    src[pos] = psrc[k];
+    dst[pos] = d;
+  }
+}
+
+static int build_level_scatter(hm_sys_s* sys, const int64_t* d_amap, std::vector<void*>* tmp) {
+  cudaStream_t s = sys->ctx->stream;
+  const int nlev = sys->plan.nlevels;
+  const int64_t nnz = sys->nnz;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((nnz + 2047) / 2048, (int64_t)sys->ctx->num_sms * 8));
+  const int64_t chunk = (nnz + nb - 1) / nb;
+  int64_t* counts = nullptr;
+  HM_TRY(dev_alloc_ctx(sys->ctx, tmp, (void**)&counts, sizeof(int64_t) * (size_t)nb * nlev));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_lev_range, sizeof(int64_t) * 2 * nlev));
+  const size_t hs = sizeof(int) * (size_t)nlev;
+  if (hs > 48 * 1024) { set_last_error("elimination tree deeper than 12288 levels"); return HM_ERR_CAPACITY; }
+  k_lev_count<<<nb, 256, hs, s>>>(d_amap, sys->d_pcol, sys->d_node_of, sys->plan.d_flevel, nnz, chunk, nlev,
+                                  counts);
+  k_lev_scan<<<nlev, 256, 0, s>>>(counts, nb, nlev, sys->d_lev_range);
+  k_lev_ranges<<<1, 32, 0, s>>>(nlev, sys->d_lev_range);
+  // (nnz bounds the lower entries; the ranges stay on the device, so no host round trip)
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_scat_src, sizeof(int64_t) * std::max<int64_t>(nnz, 1)));
+  HM_TRY(dev_alloc(sys, (void**)&sys->d_scat_dst, sizeof(int64_t) * std::max<int64_t>(nnz, 1)));
+  k_lev_place<<<nb, 256, hs, s>>>(d_amap, sys->d_psrc, sys->d_pcol, sys->d_node_of, sys->plan.d_flevel, nnz, chunk,
+                                  nlev, counts, sys->d_lev_range, sys->d_scat_src, sys->d_scat_dst);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+// ------------------------------------------------------------------------------------
 // Host driver of the symbolic analysis.
 // ------------------------------------------------------------------------------------
 static int tmp_alloc(hm_sys_s* sys, std::vector<void*>* tmp, void** p, size_t bytes) {
@@ -1012,12 +1113,19 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
   }
   HM_TRY(build_plan(sys));
   host_mark("analyze: build_plan");
-  HM_TRY(dev_alloc(sys, (void**)&sys->d_amap, sizeof(int64_t) * sys->nnz));
+  // the assembly map is needed only to group the entries by depth
+  HM_TRY(tmp_alloc(sys, &tmp, (void**)&sys->d_amap, sizeof(int64_t) * sys->nnz));
   {
     ProfScope ps(sys->ctx, PC_SYMBOLIC, Work{0.0, 24.0 * sys->nnz});
     launch_amap(sys);
   }
-  return check_device_error(sys, "analyze: assembly map");
+  HM_TRY(check_device_error(sys, "analyze: assembly map"));
+  {
+    ProfScope ps(sys->ctx, PC_GROUP, Work{0.0, 48.0 * sys->nnz}, 4);
+    HM_TRY(build_level_scatter(sys, sys->d_amap, &tmp));
+  }
+  sys->d_amap = nullptr;  // freed with the analysis temporaries
+  return check_device_error(sys, "analyze: entries by depth");
 }
 
 }  // namespace hm

@@ -75,6 +75,18 @@ void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner) {
 
 int dev_alloc(hm_sys_s* sys, void** p, size_t bytes) { return dev_alloc_ctx(sys->ctx, &sys->allocs, p, bytes); }
 
+// Bytes of the allocations in `owner` (sizes from the context's side table).
+static double owned_bytes(const hm_ctx_s* ctx, const std::vector<void*>& owner) {
+  std::unordered_map<const void*, size_t> size;
+  for (size_t i = 0; i + 1 < ctx->allocs.size(); i += 2) size[ctx->allocs[i + 1]] = (size_t)(uintptr_t)ctx->allocs[i];
+  double b = 0;
+  for (const void* p : owner) {
+    auto it = size.find(p);
+    if (it != size.end()) b += (double)it->second;
+  }
+  return b;
+}
+
 int copy_in(hm_sys_s* sys, void* dst, const void* src, size_t bytes) {
   HM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, sys->ctx->stream));
   HM_CUDA(cudaStreamSynchronize(sys->ctx->stream));
@@ -126,7 +138,7 @@ const char* prof_cat_name(int c) {
       "dense_trsm", "gemm_factor", "sketch", "householder_qr", "jacobi_svd", "leaf_solve",
       "core_lu_inverse", "spd_inverse", "apply_up", "apply_down", "gemm_apply", "spmv", "gmres_dots",
       "gmres_gs_update", "gmres_small", "vector_ops", "memset", "dense_sweep", "bdlr", "hodlr_apply_up",
-      "hodlr_apply_down", "gemm_tensor_core"};
+      "hodlr_apply_down", "gemm_tensor_core", "pack_factor", "entries_by_depth"};
   return (c >= 0 && c < PC_COUNT) ? names[c] : "?";
 }
 
@@ -251,6 +263,8 @@ int hm_default_opts(hm_opts* o) {
   o->wait_limit = 0;
   o->adaptive_rank = 0;
   o->inject_wait_timeout = 0;
+  o->compress_ff = 0;
+  o->keep_fronts = 0;
   return HM_OK;
 }
 
@@ -271,11 +285,12 @@ int hm_create(hm_ctx_t* out, const hm_opts* opts) {
       o.dofs_per_node > 8 || (o.compressor != HM_COMP_RRF && o.compressor != HM_COMP_BDLR) ||
       o.bdlr_depth < 1 || o.bdlr_depth > 8 || o.wait_limit < 0 ||
       (o.inject_wait_timeout != 0 && o.inject_wait_timeout != 1) ||
-      (o.adaptive_rank != 0 && o.adaptive_rank != 1)) {
+      (o.adaptive_rank != 0 && o.adaptive_rank != 1) || (o.compress_ff != 0 && o.compress_ff != 1) ||
+      (o.compress_ff == 1 && o.compressor != HM_COMP_RRF) || (o.keep_fronts != 0 && o.keep_fronts != 1)) {
     set_last_error("option out of range: nd_leaf>=1, 2<=hodlr_leaf<=64, 0<=n_c<=128, "
                    "1<=samples<=" + std::to_string(kmax) + ", 1<=restart<=200, 1<=dofs_per_node<=8, "
                    "compressor RRF or BDLR, 1<=bdlr_depth<=8, wait_limit>=0, adaptive_rank and "
-                   "inject_wait_timeout 0 or 1");
+                   "inject_wait_timeout 0 or 1, compress_ff 0 or 1 (range finder only), keep_fronts 0 or 1");
     return HM_ERR_INVALID_ARG;
   }
   int ndev = 0;
@@ -535,7 +550,23 @@ int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* in
     info->max_rank = mx;
     info->rank_capped = capped;
     info->factor_bytes = P.factor_bytes;
-    info->front_bytes = (double)P.front_total * (sys->precision == HM_PREC_FP64 ? 8 : 4);
+    const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
+    info->front_bytes = (double)P.front_total * es;
+    info->stored_bytes = P.stored_bytes;
+    // the conventional method on the same tree: L, and in elimination order (children
+    // before parents) the peak of L so far + live updates + the current front
+    double L = 0, live = 0, peak = 0;
+    for (int q = 0; q < sys->nf; ++q) {
+      const double np = P.fg[q].np, nu = P.fg[q].nu, nh = P.fg[q].nhat;
+      peak = std::max(peak, L + live + nh * (nh + 1) / 2);
+      for (int c : sys->children(q)) live -= (double)P.fg[c].nu * (P.fg[c].nu + 1) / 2;
+      L += np * (np + 1) / 2 + np * nu;
+      live += nu * (nu + 1) / 2;
+    }
+    peak = std::max(peak, L);
+    info->conventional_bytes = L * es;
+    info->conventional_peak_bytes = peak * es;
+    info->device_bytes = owned_bytes(sys->ctx, sys->allocs) + owned_bytes(sys->ctx, sys->plan_allocs);
   }
   return HM_OK;
 }
@@ -660,6 +691,11 @@ int hm_get_update(hm_sys_t sys, int32_t front, double* U) {
   if (!sys->factored) return HM_ERR_STATE;
   cudaSetDevice(sys->ctx->opts.device);
   const FrontGeom& g = sys->plan.fg[front];
+  if (sys->plan.reuse && g.level > 1) {  // levels 0 and 1 are the last ones in their banks
+    set_last_error("hm_get_update: the front storage of depth " + std::to_string(g.level) +
+                   " was reused; create the context with keep_fronts = 1");
+    return HM_ERR_STATE;
+  }
   const int es = sys->precision == HM_PREC_FP64 ? 8 : 4;
   std::vector<unsigned char> buf((size_t)g.nhat * g.nhat * es + 8);
   HM_TRY(copy_in(sys, buf.data(), (char*)sys->d_front + g.off * es, (size_t)g.nhat * g.nhat * es));

@@ -112,11 +112,24 @@ struct OmegaTask {
 // Woodbury core C (n2 = 2k, ld n2): the GEMMs have written the two diagonal k x k
 // blocks; this sets the off-diagonal blocks to I, LU-factors C with partial pivoting and
 // writes the explicit inverse to Cinv (n2 x n2, ld n2).
+// A rows x cols block copied from src (ld lds) to dst (ld ldd).
+struct CopyTask {
+  const void* src;
+  void* dst;
+  int rows, cols, lds, ldd;
+};
+
 // A dense front (nhat x nhat, ld nhat, nhat <= 128) factored in one pass by np
-// Gauss-Jordan sweeps: F_pp^{-1}, K^T, K and U_p in place.
+// Gauss-Jordan sweeps into F_pp^{-1}, K^T, K and U_p.  The rows of the pivot block
+// [F_pp^{-1} | K^T] go to P (ld ldp, or np when ldp is 0), K (nu x np) to
+// P + packed_k_offset (ld nu), the lower triangle of U_p back into F (where the parent's
+// extend-add reads it).  A HODLR leaf (np = nhat) sends its inverse to the packed leaf
+// store this way.
 struct SweepTask {
   void* F;
+  void* P;
   int np, nhat, front, ld;  // ld: leading dimension of F (0: nhat)
+  int ldp, pad;
 };
 
 struct CoreLuTask {

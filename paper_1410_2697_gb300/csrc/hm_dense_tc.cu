@@ -45,9 +45,6 @@ template <int MODE> struct TcShape;
 template <> struct TcShape<kModeBf16> { static constexpr int TK = 64, KI = 16; };
 template <> struct TcShape<kModeTf32x3> { static constexpr int TK = 32, KI = 8; };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 // Shared-memory matrix descriptor: start address, leading (K-direction) and stride
 // (row-group direction) byte offsets, descriptor version 1, no swizzle.
@@ -81,29 +78,6 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(r);
 }
 
-// Waits for the phase of parity `parity` of the mbarrier to complete, `limit` polls at
-// most: the first poll is mbarrier.test_wait (it never suspends the thread), the later
-// ones mbarrier.try_wait (which may suspend it for a while).  Returns false if the phase
-// did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
-  for (int it = 0; it < limit; ++it) {
-    uint32_t ok;
-    if (it == 0)
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-          : "=r"(ok)
-          : "r"(bar), "r"(parity)
-          : "memory");
-    else
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-          : "=r"(ok)
-          : "r"(bar), "r"(parity)
-          : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
 
 // Stages rows row0 .. row0+R-1 and k indices k0 .. k0+TK-1 of an operand (FP32 in
 // memory, zero outside rows < nrows and k < kend) into a K-major slice of R rows: as BF16

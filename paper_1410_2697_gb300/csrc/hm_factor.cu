@@ -14,21 +14,43 @@
 
 namespace hm {
 
-// F[amap[k]] = A value of permuted entry k (lower triangle); also keeps the permuted
-// FP64 values for the GMRES residual.
-template <typename T>
-__global__ void k_scatter(const double* __restrict__ vals, const int64_t* __restrict__ psrc,
-                          const int64_t* __restrict__ amap, int64_t nnz, T* __restrict__ F,
-                          double* __restrict__ pvals, float2* __restrict__ pvals2) {
+// The permuted FP64 values of A for the GMRES residual, and the same split as FP32
+// hi + lo (48 of the 53 bits) for the double-float SpMV.
+__global__ void k_perm_values(const double* __restrict__ vals, const int64_t* __restrict__ psrc, int64_t nnz,
+                              double* __restrict__ pvals, float2* __restrict__ pvals2) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
        k += (int64_t)gridDim.x * blockDim.x) {
     const double v = vals[psrc[k]];
     pvals[k] = v;
-    // v = hi + lo with hi, lo FP32 (48 of the 53 bits), for the double-float SpMV
     const float hi = (float)v;
     pvals2[k] = make_float2(hi, (float)(v - (double)hi));
-    const int64_t d = amap[k];
-    if (d >= 0) F[d] = (T)v;
+  }
+}
+
+// F-bar of one tree level (Eq. fbar): A's lower-triangle entries whose front is at
+// depth l, at their positions in the front storage.
+template <typename T>
+__global__ void k_scatter_level(const double* __restrict__ vals, const int64_t* __restrict__ src,
+                                const int64_t* __restrict__ dst, const int64_t* __restrict__ range, int l,
+                                T* __restrict__ F) {
+  const int64_t m1 = range[2 * l + 1];
+  for (int64_t m = range[2 * l] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < m1;
+       m += (int64_t)gridDim.x * blockDim.x)
+    F[dst[m]] = (T)vals[src[m]];
+}
+
+// Packs the factor of a level out of the front storage (one task per block, a warp per
+// column, lanes along the rows).
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy2d(const CopyTask* __restrict__ tasks) {
+  const CopyTask t = tasks[blockIdx.x];
+  const T* src = (const T*)t.src;
+  T* dst = (T*)t.dst;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < t.cols; c += 8) {
+    const T* s = src + (int64_t)c * t.lds;
+    T* d = dst + (int64_t)c * t.ldd;
+    for (int r = lane; r < t.rows; r += 32) d[r] = s[r];
   }
 }
 
@@ -149,20 +171,28 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
   const int es = sizeof(T);
   HM_CUDA(cudaMemsetAsync(sys->d_err, 0, 4 * sizeof(int), s));
   {
-    ProfScope ps(ctx, PC_MEMSET, Work{0.0, (double)es * (P.front_total + P.bo_total + P.w_total)}, 0);
-    HM_CUDA(cudaMemsetAsync(F, 0, (size_t)P.front_total * sizeof(T), s));
+    ProfScope ps(ctx, PC_MEMSET, Work{0.0, (double)es * (P.bo_total + P.w_total)}, 0);
     if (P.bo_total) HM_CUDA(cudaMemsetAsync(sys->d_bo, 0, (size_t)P.bo_total * sizeof(T), s));
     if (P.w_total) HM_CUDA(cudaMemsetAsync(sys->d_w, 0, (size_t)P.w_total * sizeof(T), s));
   }
   {
     const int64_t nnz = sys->nnz;
-    ProfScope ps(ctx, PC_SCATTER, Work{0.0, nnz * 32.0 + 0.5 * nnz * es});
+    ProfScope ps(ctx, PC_SCATTER, Work{0.0, nnz * 32.0});
     const int grid = (int)std::min<int64_t>((nnz + 255) / 256, (int64_t)ctx->num_sms * 16);
-    k_scatter<T><<<std::max(grid, 1), 256, 0, s>>>(d_values, sys->d_psrc, sys->d_amap, nnz, F,
-                                                  sys->d_pvals, sys->d_pvals2);
+    k_perm_values<<<std::max(grid, 1), 256, 0, s>>>(d_values, sys->d_psrc, nnz, sys->d_pvals, sys->d_pvals2);
   }
   for (int l = P.nlevels - 1; l >= 0; --l) {
     const LevelFactorPlan& lp = P.levels[l];
+    {  // the level's fronts: zero, then A's entries (their children's level is still live)
+      const int64_t f0 = P.level_front_begin[l], f1 = P.level_front_end[l];
+      ProfScope ps(ctx, PC_SCATTER, Work{0.0, (double)es * (f1 - f0) + (16.0 + 8.0 + es) * P.level_entries[l]});
+      if (f1 > f0) HM_CUDA(cudaMemsetAsync(F + f0, 0, (size_t)(f1 - f0) * sizeof(T), s));
+      // the entry count of a level is known on the device only: a grid for about the
+      // nonzeros the level's fronts hold, read bounds from the device
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((P.level_entries[l] + 255) / 256,
+                                                                    (int64_t)ctx->num_sms * 16));
+      k_scatter_level<T><<<grid, 256, 0, s>>>(d_values, sys->d_scat_src, sys->d_scat_dst, sys->d_lev_range, l, F);
+    }
     for (size_t si = 0; si < lp.ea_parents.size(); ++si) {
       const auto& par = lp.ea_parents[si];
       if (par.count == 0 || lp.ea_max_nu[si] == 0) continue;
@@ -214,6 +244,7 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
       debug_stage<T>(sys, "svd", l);
       run_gemm<T>(sys, lp.formU, base, PC_GEMM_FACTOR);
       run_gemm<T>(sys, lp.formV, base, PC_GEMM_FACTOR);
+      run_gemm<T>(sys, lp.ffx, base, PC_GEMM_FACTOR);  // F_ff^HODLR written back (compress_ff)
       debug_stage<T>(sys, "formUV", l);
       {
         ProfScope ps(ctx, PC_INVERSE, lp.leaf_sweep.work);
@@ -238,6 +269,10 @@ static int factor_t(hm_sys_s* sys, const double* d_values, double tol) {
       run_gemm<T>(sys, lp.schurP, base, PC_GEMM_FACTOR);
       run_gemm<T>(sys, lp.schurF, base, PC_GEMM_FACTOR);
       debug_stage<T>(sys, "schur", l);
+    }
+    if (lp.pack.count) {  // the level's factor out of the fronts, for the apply
+      ProfScope ps(ctx, PC_PACK, lp.pack.work);
+      k_copy2d<T><<<lp.pack.count, 256, 0, s>>>(lp.pack.dev(base));
     }
   }
   HM_CUDA(cudaGetLastError());

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
     }
   }
   // leaves: y = K_leaf^{-1} b_p, one row per thread (the leaf's inverse, symmetric, is
-  // read by columns: consecutive threads read consecutive rows)
+  // read by columns: consecutive threads read consecutive rows; packed, ld np)
   const T* F = (const T*)tk.F;
   for (int i = threadIdx.x; i < nP; i += kHaThreads) {
     const int j = leaf_of(lb, c * span, (c + 1) * span, P0 + i);
@@ -316,20 +316,20 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
     T acc[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) acc[r] = T(0);
-    const T* K = F + (lo + ii) + (int64_t)lo * nh;
+    const T* K = F + (lo + ii);
     const T* b = Bp + (lo - P0) * RP;
     int jj = 0;
     for (; jj + 16 <= nl; jj += 16) {  // sixteen loads in flight per thread
       T m[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) m[u] = K[(int64_t)(jj + u) * nh];
+      for (int u = 0; u < 16; ++u) m[u] = K[(int64_t)(jj + u) * np];
 #pragma unroll
       for (int u = 0; u < 16; ++u)
 #pragma unroll
         for (int r = 0; r < RB; ++r) acc[r] = fma(m[u], b[(jj + u) * RP + r], acc[r]);
     }
     for (; jj < nl; ++jj) {
-      const T m = K[(int64_t)jj * nh];
+      const T m = K[(int64_t)jj * np];
 #pragma unroll
       for (int r = 0; r < RB; ++r) acc[r] = fma(m, b[jj * RP + r], acc[r]);
     }

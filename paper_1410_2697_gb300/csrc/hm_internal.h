@@ -50,6 +50,7 @@ inline Work work_of(const SvdTask& t, int es) {
   return Work{12.0 * t.k * t.k * t.k, es * 3.0 * t.k * t.k};  // ~ per-sweep cost x 2
 }
 inline Work work_of(const OmegaTask& t, int es) { return Work{0.0, (double)es * t.rows * t.cols}; }
+inline Work work_of(const CopyTask& t, int es) { return Work{0.0, 2.0 * es * t.rows * t.cols}; }
 inline Work work_of(const CoreLuTask& t, int es) {
   const double n2 = 2.0 * t.k;
   return Work{2.0 * n2 * n2 * n2 / 3.0 + 2.0 * n2 * n2 * n2, es * 3.0 * n2 * n2};
@@ -213,7 +214,7 @@ enum ProfCat {
   PC_ND = 0, PC_SYMBOLIC, PC_PERMUTE_CSR, PC_SCATTER, PC_EXTEND_ADD, PC_POTRF, PC_TRSM,
   PC_GEMM_FACTOR, PC_SKETCH, PC_QR, PC_SVD, PC_CHOL_SOLVE, PC_CORE_LU, PC_INVERSE,
   PC_UP, PC_DOWN, PC_GEMM_APPLY, PC_SPMV, PC_DOTS, PC_GS_UPDATE, PC_GMRES_SMALL, PC_VECTOR,
-  PC_MEMSET, PC_SWEEP, PC_BDLR, PC_HODLR_UP, PC_HODLR_DOWN, PC_GEMM_TC, PC_COUNT
+  PC_MEMSET, PC_SWEEP, PC_BDLR, PC_HODLR_UP, PC_HODLR_DOWN, PC_GEMM_TC, PC_PACK, PC_GROUP, PC_COUNT
 };
 const char* prof_cat_name(int c);
 
@@ -258,6 +259,7 @@ struct FrontGeom {
   int level = 0;
   int hodlr = -1;          // index into Plan::hf, -1 for a dense front
   int64_t off = 0;         // element offset of the dense front (nhat x nhat) in the arena
+  int64_t cf_off = -1;     // dense front: its packed factor (see Plan::dense_total)
 };
 
 struct HNodeGeom {
@@ -268,6 +270,7 @@ struct HNodeGeom {
   int rank_slot;
   int64_t om_off, y_off, z_off, r_off, uhs_off, vh_off;  // compression scratch
   int64_t tb_off;          // factor-time t then s buffers, 2 x (2 k_level x A_level)
+  int64_t u_off = 0, v_off = 0;  // F_ff nodes: the block's U (na x kb) and V (nb x kb)
 };
 
 struct HFront {
@@ -286,6 +289,9 @@ struct HFront {
   int64_t fom_off, fy_off, fz_off, fr_off, fuhs_off, fvh_off;
   std::vector<HNodeGeom> nodes;   // all internal nodes, level by level
   std::vector<int> leaf_lo, leaf_hi;
+  std::vector<HNodeGeom> ff_nodes;  // compress_ff: internal nodes of F_ff's HODLR tree
+  int64_t lv_off = 0;      // leaf inverses, packed: np x lmax (ld np), leaf [lo, hi) in rows
+  int lmax = 0;            // lo..hi and columns 0..hi-lo
 };
 
 // Panel QRs of one launch group: shared-memory TSQR where the panel fits, the
@@ -320,9 +326,11 @@ struct LevelFactorPlan {
   Span<CholInvTask> dinv;      // F_pp^{-1} and K = F_fp F_pp^{-1} of the dense fronts
   Span<SweepTask> sweep;       // dense fronts with nhat <= 128, factored in one pass
   int sweep_maxn = 0;
+  Span<CopyTask> pack;         // the level's factor out of the fronts (dense and leaf inverses)
   // HODLR fronts
   Span<OmegaTask> omega;
   GemmBatch sampY, sampZ, formU, formV;
+  GemmBatch ffx;               // compress_ff: F_ff's off-diagonal blocks <- V U^T
   QrBatch qrY, qrZ;
   Span<SvdTask> svd;
   int svd_maxk = 0;
@@ -352,7 +360,7 @@ struct HApplyTask {
                     // rows of each node's first child, V on the second's
   const void* G;    // np x 2 (xc - kf) (ld np): G_l = Zhat_l C_l^{-1} per level
   const void* W;    // nu x kf (ld nu): F_fp ~ W V_f^T
-  const void* F;    // the front (nhat x nhat, ld nhat): leaf inverses on the diagonal
+  const void* F;    // packed leaf inverses (np x lmax, ld np): leaf [lo, hi) in rows lo..hi
   int64_t fv_off;   // element offset of the front's vector block (nhat x nrhs)
   int q, first, np, nu, nhat, L, kf, leaf_off;  // leaf_off: its 2^L + 1 leaf boundaries
   int kl[kHaMaxL];  // sketch width (column capacity) per level
@@ -433,6 +441,7 @@ struct Plan {
   int64_t qr_scratch = 0;  // elements of the TSQR scratch arena (reused by every QR launch)
   int nrank = 0;
   std::vector<int64_t> level_front_begin, level_front_end;   // element ranges per level
+  std::vector<int64_t> level_entries;  // A's lower entries per level, estimated (grid sizes)
   std::vector<LevelFactorPlan> levels;
   TaskBuf tb;
   unsigned char* d_tasks = nullptr;
@@ -447,6 +456,16 @@ struct Plan {
   std::vector<int> h_nhat, h_np, h_hkind;
   int max_children = 0;
   double factor_bytes = 0;
+  double stored_bytes = 0;   // factor data the apply reads (see hm_factor_info)
+  // Packed factor, written level by level as the fronts are factored (the apply reads
+  // only these, so the front storage may be reused): per dense front [F_pp^-1 | K^T]
+  // (np x nhat, ld np) then K (nu x np, ld nu); per HODLR front its leaf inverses.
+  int64_t dense_total = 0, leaf_total = 0;
+  bool reuse = false;               // front storage shared by the levels of each parity
+  int64_t* d_cf_off = nullptr;      // per front: packed dense factor offset
+  int* d_flevel = nullptr;          // per front: tree depth
+  std::vector<int64_t> h_cf_off;
+  std::vector<int> h_flevel;
 };
 
 struct DevArena {
@@ -533,6 +552,13 @@ struct hm_sys_s {
   int* d_piv = nullptr;
   void* d_comp = nullptr;    // T
   void* d_qrs = nullptr;     // T, TSQR scratch
+  void* d_dfac = nullptr;    // T, packed dense-front factors
+  void* d_leafinv = nullptr; // T, packed HODLR leaf inverses
+  // A's lower-triangle entries grouped by the tree depth of their front: value index and
+  // element offset in the front storage; [lev_range[2 l], lev_range[2 l + 1]) per depth
+  int64_t* d_scat_src = nullptr;
+  int64_t* d_scat_dst = nullptr;
+  int64_t* d_lev_range = nullptr;
   void* d_tb = nullptr;      // T
   int* d_ranks = nullptr;
   double* d_pvals = nullptr; // permuted A values (FP64) for SpMV

@@ -162,8 +162,18 @@ int build_plan(hm_sys_s* sys) {
   for (int q = 0; q < nf; ++q) P.level_fronts[P.fg[q].level].push_back(q);
   P.level_front_begin.assign(P.nlevels, 0);
   P.level_front_end.assign(P.nlevels, 0);
+  // Front storage: with reuse, the levels of even depth share one bank and those of odd
+  // depth the other (a level is assembled while its children's level, of the other
+  // parity, still holds their updates; the level two below is packed and dead by then);
+  // otherwise every level has its own range, deepest first.
+  P.reuse = o.keep_fronts == 0;
+  std::vector<int64_t> lsum(P.nlevels, 0);
+  for (int q = 0; q < nf; ++q) lsum[P.fg[q].level] += (int64_t)P.fg[q].nhat * P.fg[q].nhat;
+  int64_t bank[2] = {0, 0};
+  for (int l = 0; l < P.nlevels; ++l) bank[l & 1] = std::max(bank[l & 1], lsum[l]);
   int64_t off = 0;
   for (int l = P.nlevels - 1; l >= 0; --l) {
+    if (P.reuse) off = (l & 1) ? bank[0] : 0;
     P.level_front_begin[l] = off;
     for (int q : P.level_fronts[l]) {
       P.fg[q].off = off;
@@ -171,7 +181,10 @@ int build_plan(hm_sys_s* sys) {
     }
     P.level_front_end[l] = off;
   }
-  P.front_total = off;
+  P.front_total = P.reuse ? bank[0] + bank[1] : off;
+  P.level_entries.assign(P.nlevels, 0);
+  const double per_col = ((double)sys->nnz + sys->n) / (2.0 * std::max(sys->n, 1));
+  for (int q = 0; q < nf; ++q) P.level_entries[P.fg[q].level] += (int64_t)(per_col * P.fg[q].np + 0.5);
   P.max_children = 0;
   for (int q = 0; q < nf; ++q) P.max_children = std::max(P.max_children, sys->children(q).size());
 
@@ -214,6 +227,26 @@ int build_plan(hm_sys_s* sys) {
         ranges.swap(next);
       }
       for (auto& r : ranges) { h.leaf_lo.push_back(r.first); h.leaf_hi.push_back(r.second); }
+      if (o.compress_ff && g.nu > 0) {  // F_ff's HODLR tree (leaf hodlr_leaf), the same width
+        std::vector<std::pair<int, int>> fr = {{0, g.nu}};
+        const int Lf = hodlr_depth(g.nu, o.hodlr_leaf);
+        for (int lv = 0; lv < Lf; ++lv) {
+          std::vector<std::pair<int, int>> next;
+          for (size_t j = 0; j < fr.size(); ++j) {
+            const int lo = fr[j].first, hi = fr[j].second, mid = lo + (hi - lo) / 2;
+            HNodeGeom nd;
+            nd.level = lv;
+            nd.index = (int)j;
+            nd.lo = lo; nd.mid = mid; nd.hi = hi;
+            nd.kb = std::min(S, std::min(mid - lo, hi - mid));
+            nd.core_off = nd.piv_off = nd.tb_off = 0;
+            h.ff_nodes.push_back(nd);
+            next.push_back({lo, mid});
+            next.push_back({mid, hi});
+          }
+          fr.swap(next);
+        }
+      }
       h.col.assign(h.L + 1, 0);
       h.col[0] = h.kf;
       for (int lv = 0; lv < h.L; ++lv) h.col[lv + 1] = h.col[lv] + h.kl[lv];
@@ -251,6 +284,18 @@ int build_plan(hm_sys_s* sys) {
         nd.vh_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
         nd.tb_off = P.tb_total; P.tb_total += (int64_t)2 * (2 * k) * h.col[nd.level];
       }
+      for (auto& nd : h.ff_nodes) {
+        const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid, kb = nd.kb;
+        nd.rank_slot = P.nrank++;
+        nd.om_off = P.comp_total; P.comp_total += (int64_t)nb * kb;
+        nd.y_off = P.comp_total; P.comp_total += (int64_t)na * kb;
+        nd.z_off = P.comp_total; P.comp_total += (int64_t)nb * kb;
+        nd.r_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
+        nd.uhs_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
+        nd.vh_off = P.comp_total; P.comp_total += (int64_t)kb * kb;
+        nd.u_off = P.comp_total; P.comp_total += (int64_t)na * kb;
+        nd.v_off = P.comp_total; P.comp_total += (int64_t)nb * kb;
+      }
       g.hodlr = (int)P.hf.size();
       P.hf.push_back(std::move(h));
     }
@@ -263,6 +308,22 @@ int build_plan(hm_sys_s* sys) {
       set_last_error("dense pivot block larger than 128 (lower n_c)");
       return HM_ERR_CAPACITY;
     }
+  }
+
+  // ---------------------------------------------------------------- packed factor
+  P.dense_total = P.leaf_total = 0;
+  for (int q = 0; q < nf; ++q) {
+    FrontGeom& g = P.fg[q];
+    if (g.hodlr < 0) {
+      g.cf_off = P.dense_total;
+      P.dense_total += packed_size(g.np, g.nhat, es);
+      continue;
+    }
+    HFront& h = P.hf[g.hodlr];
+    h.lmax = 0;
+    for (size_t li = 0; li < h.leaf_lo.size(); ++li) h.lmax = std::max(h.lmax, h.leaf_hi[li] - h.leaf_lo[li]);
+    h.lv_off = P.leaf_total;
+    P.leaf_total += (int64_t)h.np * h.lmax;
   }
 
   // ---------------------------------------------------------------- allocations
@@ -287,6 +348,10 @@ int build_plan(hm_sys_s* sys) {
   HM_TRY(A((void**)&P.d_nhat, nf, 4));
   HM_TRY(A((void**)&P.d_np, nf, 4));
   HM_TRY(A((void**)&P.d_hkind, nf, 4));
+  HM_TRY(A(&sys->d_dfac, P.dense_total, es));
+  HM_TRY(A(&sys->d_leafinv, P.leaf_total, es));
+  HM_TRY(A((void**)&P.d_cf_off, nf, 8));
+  HM_TRY(A((void**)&P.d_flevel, nf, 4));
   {
     // the host copies live as long as the plan, so the uploads need no synchronization
     auto& fo = P.h_front_off;
@@ -294,14 +359,20 @@ int build_plan(hm_sys_s* sys) {
     auto& npv = P.h_np;
     auto& hk = P.h_hkind;
     fo.resize(nf); nh.resize(nf); npv.resize(nf); hk.resize(nf);
+    P.h_cf_off.resize(nf);
+    P.h_flevel.resize(nf);
     for (int q = 0; q < nf; ++q) {
       fo[q] = P.fg[q].off; nh[q] = P.fg[q].nhat; npv[q] = P.fg[q].np; hk[q] = P.fg[q].hodlr;
+      P.h_cf_off[q] = P.fg[q].cf_off;
+      P.h_flevel[q] = P.fg[q].level;
     }
     cudaStream_t s = sys->ctx->stream;
     HM_CUDA(cudaMemcpyAsync(P.d_front_off, fo.data(), nf * 8, cudaMemcpyHostToDevice, s));
     HM_CUDA(cudaMemcpyAsync(P.d_nhat, nh.data(), nf * 4, cudaMemcpyHostToDevice, s));
     HM_CUDA(cudaMemcpyAsync(P.d_np, npv.data(), nf * 4, cudaMemcpyHostToDevice, s));
     HM_CUDA(cudaMemcpyAsync(P.d_hkind, hk.data(), nf * 4, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(P.d_cf_off, P.h_cf_off.data(), nf * 8, cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(P.d_flevel, P.h_flevel.data(), nf * 4, cudaMemcpyHostToDevice, s));
   }
 
   // ---------------------------------------------------------------- factor tasks
@@ -360,7 +431,7 @@ int build_plan(hm_sys_s* sys) {
       void* Fq = at(F, g.off, es);
       fbytes += es * ((double)g.np * g.np + 2.0 * g.nu * g.np);
       if (g.nhat <= kSweepMaxN) {
-        sweep.push_back(SweepTask{Fq, g.np, g.nhat, q, 0});
+        sweep.push_back(SweepTask{Fq, at(sys->d_dfac, g.cf_off, es), g.np, g.nhat, q, 0, 0, 0});
         lp.sweep_maxn = std::max(lp.sweep_maxn, g.nhat);
         continue;
       }
@@ -386,7 +457,7 @@ int build_plan(hm_sys_s* sys) {
     lp.sweep = tb.add(sweep);
     // HODLR fronts
     std::vector<OmegaTask> om;
-    std::vector<GemmTask> gy, gz, gu, gv;
+    std::vector<GemmTask> gy, gz, gu, gv, ffx;
     std::vector<QrTask> qy, qz;
     std::vector<SvdTask> sv;
     std::vector<SweepTask> lsw;
@@ -469,14 +540,40 @@ int build_plan(hm_sys_s* sys) {
                           at(F, fo + np + (int64_t)np * nh, es), nh, nu, nu, kf, -1.0, 1.0, 1));
         fbytes += es * 4.0 * (double)(np + nu) * kf;
       }
+      // compress_ff: F_ff's off-diagonal blocks (lower storage, nb x na at rows np + mid,
+      // columns np + lo) by the same range finder, then written back as V U^T, before
+      // the Schur update subtracts W T W^T
+      for (const auto& nd : h.ff_nodes) {
+        const int na = nd.mid - nd.lo, nb = nd.hi - nd.mid, kb = nd.kb;
+        const uint64_t blk = block_id(q, 2, nd.level, nd.index);
+        void* Kba = at(F, fo + np + nd.mid + (int64_t)(np + nd.lo) * nh, es);
+        om.push_back(OmegaTask{at(Cp, nd.om_off, es), blk, nb, kb, nb, 0});
+        gy.push_back(gemm(Kba, nh, 1, at(Cp, nd.om_off, es), nb, 0, at(Cp, nd.y_off, es), na, na, kb,
+                          nb, 1.0, 0.0));
+        qy.push_back(QrTask{at(Cp, nd.y_off, es), nullptr, na, kb, na, 0});
+        gz.push_back(gemm(Kba, nh, 0, at(Cp, nd.y_off, es), na, 0, at(Cp, nd.z_off, es), nb, nb, kb,
+                          na, 1.0, 0.0));
+        qz.push_back(QrTask{at(Cp, nd.z_off, es), at(Cp, nd.r_off, es), nb, kb, nb, 0});
+        sv.push_back(SvdTask{at(Cp, nd.r_off, es), at(Cp, nd.uhs_off, es), at(Cp, nd.vh_off, es),
+                             ranks + nd.rank_slot, kb, 0});
+        lp.svd_maxk = std::max(lp.svd_maxk, kb);
+        gu.push_back(gemm(at(Cp, nd.y_off, es), na, 0, at(Cp, nd.uhs_off, es), kb, 0, at(Cp, nd.u_off, es), na,
+                          na, kb, kb, 1.0, 0.0));
+        gv.push_back(gemm(at(Cp, nd.z_off, es), nb, 0, at(Cp, nd.vh_off, es), kb, 0, at(Cp, nd.v_off, es), nb,
+                          nb, kb, kb, 1.0, 0.0));
+        ffx.push_back(gemm(at(Cp, nd.v_off, es), nb, 0, at(Cp, nd.u_off, es), na, 1, Kba, nh, nb, na, kb, 1.0,
+                           0.0));
+      }
       for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
         const int lo = h.leaf_lo[li], n = h.leaf_hi[li] - lo;
         void* Lq = at(F, fo + lo + (int64_t)lo * nh, es);
-        lsw.push_back(SweepTask{Lq, n, n, q, nh});  // the leaf's inverse in one sweep kernel
+        // the leaf's inverse in one sweep kernel, into the packed leaf store
+        void* Lp = at(sys->d_leafinv, h.lv_off + lo, es);
+        lsw.push_back(SweepTask{Lq, Lp, n, n, q, nh, np, 0});
         lp.leaf_maxn = std::max(lp.leaf_maxn, n);
         // X (leaf rows) = K_leaf^{-1} Bo (leaf rows), once the explicit inverse is formed
         if (h.xc > 0)
-          lxg.push_back(gemm(Lq, nh, 0, at(Bo, h.bo_off + lo, es), np, 0, at(X, h.bo_off + lo, es), np, n, h.xc,
+          lxg.push_back(gemm(Lp, np, 0, at(Bo, h.bo_off + lo, es), np, 0, at(X, h.bo_off + lo, es), np, n, h.xc,
                              n, 1.0, 0.0));
         fbytes += es * (double)n * n;
       }
@@ -491,6 +588,7 @@ int build_plan(hm_sys_s* sys) {
     lp.svd = tb.add(sv);
     lp.formU = tb.add_gemm(gu);
     lp.formV = tb.add_gemm(gv);
+    lp.ffx = tb.add_gemm(ffx);
     lp.leaf_sweep = tb.add(lsw);
     lp.leaf_x = tb.add_gemm(lxg);
     // Woodbury levels, bottom-up (height 1 = parents of the leaves)
@@ -551,8 +649,37 @@ int build_plan(hm_sys_s* sys) {
     lp.schurT = tb.add_gemm(sT);
     lp.schurP = tb.add_gemm(sP);
     lp.schurF = tb.add_gemm(sF);
+    // pack the dense fronts factored in place (beyond the sweep kernel): [F_pp^-1 | K^T]
+    // (np x nhat) and K (nu x np).  The sweep kernel writes its fronts and the HODLR
+    // leaves' inverses to the packed stores itself.
+    std::vector<CopyTask> pk;
+    for (int q : fr) {
+      const FrontGeom& g = P.fg[q];
+      if (g.hodlr >= 0 || g.nhat <= kSweepMaxN) continue;
+      pk.push_back(CopyTask{at(F, g.off, es), at(sys->d_dfac, g.cf_off, es), g.np, g.nhat, g.nhat, g.np});
+      if (g.nu > 0)
+        pk.push_back(CopyTask{at(F, g.off + g.np, es),
+                              at(sys->d_dfac, g.cf_off + packed_k_offset(g.np, g.nhat, es), es), g.nu, g.np, g.nhat,
+                              g.nu});
+    }
+    lp.pack = tb.add(pk);
   }
   P.factor_bytes = fbytes;
+  P.stored_bytes = 0;
+  for (int q = 0; q < nf; ++q) {
+    const FrontGeom& g = P.fg[q];
+    if (g.hodlr < 0) {  // F_pp^{-1}, K and K^T
+      P.stored_bytes += es * ((double)g.np * g.np + 2.0 * g.np * g.nu);
+      continue;
+    }
+    const HFront& h = P.hf[g.hodlr];
+    double e = (double)h.np * h.xc + (double)h.np * h.kf + (double)h.np * 2 * (h.xc - h.kf) + (double)h.nu * h.kf;
+    for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
+      const double n = h.leaf_hi[li] - h.leaf_lo[li];
+      e += n * n;
+    }
+    P.stored_bytes += es * e;
+  }
   HM_TRY(A(&sys->d_qrs, P.qr_scratch, es));
   tb.relocate(sys->d_qrs);  // row-block QR tasks address the scratch by offset until now
   HM_TRY(A(&P.d_split_ws, tb.split_ws, es));
@@ -612,7 +739,7 @@ static void plan_hodlr_apply(hm_sys_s* sys, SolvePlan* sp, LevelSolvePlan& lp, c
     t.Bo = at(sys->d_bo, h.bo_off, es);
     t.G = at(sys->d_g, h.g_off, es);
     t.W = at(sys->d_w, h.w_off, es);
-    t.F = at(sys->d_front, g.off, es);
+    t.F = at(sys->d_leafinv, h.lv_off, es);
     t.fv_off = sp->fv_off[q];
     t.q = q;
     t.first = sys->h_first[q];
@@ -729,7 +856,6 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
                           sys->ctx->stream));
   void* XF = sp->d_xfix;
   const int n = sys->n;
-  void* F = sys->d_front;
   void* Bo = sys->d_bo;
   void* X = sys->d_x;
   void* W = sys->d_w;
@@ -781,7 +907,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
       const int64_t fvq = sp->fv_off[q], yq = sys->h_first[q];  // y = xfix rows of I_q
       for (size_t li = 0; li < h.leaf_lo.size(); ++li) {
         const int lo = h.leaf_lo[li], nl = h.leaf_hi[li] - lo;
-        dg.push_back(gemm(at(F, g.off + lo + (int64_t)lo * g.nhat, es), g.nhat, 0, at(FV, fvq + lo, es),
+        dg.push_back(gemm(at(sys->d_leafinv, h.lv_off + lo, es), h.np, 0, at(FV, fvq + lo, es),
                           g.nhat, 0, at(XF, yq + lo, es), n, nl, nrhs, nl, 1.0, 0.0));
       }
       if (h.kf > 0) {

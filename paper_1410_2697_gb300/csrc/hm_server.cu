@@ -15,9 +15,15 @@
 // A request therefore never waits for a running solve of its matrix to finish, and its
 // answer is the one it gets alone (each column has its own Krylov space and its own
 // restart boundaries).  Workers run concurrently, so solves of different matrices
-// overlap on the GPU.  Admission: when an allocation of the worker's context would
-// exceed its budget, the least recently used resident system of that worker is destroyed
-// and the step retried; a matrix that does not fit alone fails with HM_ERR_OUT_OF_MEMORY.
+// overlap on the GPU.  Admission by estimate: before a matrix is analysed and factored
+// (and before a session's GMRES workspace is allocated), the worker destroys its least
+// recently used idle resident systems until its context's bytes plus the estimate fit its
+// budget.  The estimate of a matrix is the footprint it had when last resident (plus an
+// eighth), else the largest bytes per nonzero seen so far for matrices of its dimension
+// (a fixed per-nonzero figure before any); a session's is its slots times the GMRES and
+// apply vectors per column (plus a quarter and 4 MiB).  Should the estimate fall short, the allocation that exceeds the budget fails
+// and the step is retried after one more eviction (counted as oom_retries); a matrix that
+// does not fit alone fails with HM_ERR_OUT_OF_MEMORY.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -43,6 +49,8 @@ struct SrvMatrix {
   std::vector<double> values;
   hm_sys_t sys = nullptr;       // resident system (worker-owned), or null
   size_t bytes = 0;             // device bytes while resident
+  size_t bytes_seen = 0;        // footprint when last resident (0: never)
+  int64_t nnz = 0;
   int64_t last_use = 0;         // worker-local use counter (LRU)
 };
 
@@ -80,6 +88,7 @@ struct hm_server_s {
   std::vector<double> latency_ms;
   int64_t completed = 0, failed = 0, batches = 0, batched_rhs = 0, factorizations = 0, evictions = 0;
   int64_t joined = 0;  // requests that entered a running session
+  int64_t oom_retries = 0;  // budget misses the estimate did not foresee
 };
 
 namespace hm {
@@ -111,10 +120,36 @@ static bool evict_one(hm_server_s* S, int w, int keep) {
   return true;
 }
 
-// Makes matrix m resident on worker w (analyze + factor), evicting on budget misses.
+// Estimated device bytes of matrix M when resident (see the header comment).
+static size_t estimate_bytes(hm_server_s* S, const SrvMatrix& M) {
+  if (M.bytes_seen) return M.bytes_seen + M.bytes_seen / 8;  // an eighth to spare
+  std::lock_guard<std::mutex> lk(S->mu);
+  double per_nnz = M.dim == 3 ? 1024.0 : 512.0;
+  bool seen = false;
+  for (const auto& o : S->matrices)
+    if (o->bytes_seen && o->dim == M.dim && o->nnz > 0) {
+      const double r = (double)o->bytes_seen / (double)o->nnz;
+      per_nnz = seen ? std::max(per_nnz, r) : r;
+      seen = true;
+    }
+  return (size_t)(per_nnz * (double)M.nnz);
+}
+
+// Evicts worker w's least recently used idle systems (not m) until `need` more bytes fit
+// its budget (or nothing is left to evict).
+static void admit(hm_server_s* S, int w, int m, size_t need) {
+  hm_ctx_t ctx = S->workers[w].ctx;
+  const size_t budget = ctx->opts.hbm_budget;
+  if (!budget) return;
+  while (ctx_bytes(ctx) + need > budget && evict_one(S, w, m)) {
+  }
+}
+
+// Makes matrix m resident on worker w (analyze + factor), admitted by its estimate.
 static int make_resident(hm_server_s* S, int w, int m, SrvMatrix& M) {
   if (M.sys) return HM_OK;
   hm_ctx_t ctx = S->workers[w].ctx;
+  admit(S, w, m, estimate_bytes(S, M));
   for (;;) {
     const size_t before = ctx_bytes(ctx);
     hm_sys_t sys = nullptr;
@@ -129,10 +164,13 @@ static int make_resident(hm_server_s* S, int w, int m, SrvMatrix& M) {
       M.sys = sys;
       M.bytes = ctx_bytes(ctx) - before;
       std::lock_guard<std::mutex> lk(S->mu);
+      M.bytes_seen = M.bytes;
       S->factorizations++;
       return HM_OK;
     }
     if (st != HM_ERR_OUT_OF_MEMORY || !evict_one(S, w, m)) return st;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->oom_retries++;
   }
 }
 
@@ -184,8 +222,17 @@ static int run_session(hm_server_s* S, int w, int m, SrvMatrix& M, std::vector<S
     slots = std::max(rhs0 > 0 ? std::min(rhs0, S->max_batch_rhs) : 1,
                      std::min(slots, (int)(0.25 * (double)o.hbm_budget / per_col)));
   }
+  // the session's GMRES workspace (V, Z and the work vectors of every slot) and its apply
+  // buffers, admitted by estimate (with a quarter and 4 MiB to spare) before allocation
+  admit(S, w, m, (size_t)(1.25 * ((2.0 * o.restart + 10.0) * 8.0 * (double)M.n * slots) + (4u << 20)));
   int st = gm_session_begin(M.sys, slots);
-  while (st == HM_ERR_OUT_OF_MEMORY && evict_one(S, w, m)) st = gm_session_begin(M.sys, slots);
+  while (st == HM_ERR_OUT_OF_MEMORY && evict_one(S, w, m)) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->oom_retries++;
+    }
+    st = gm_session_begin(M.sys, slots);
+  }
   if (st != HM_OK) return st;
   struct Live { SrvRequest* r; int slot0; };
   std::vector<Live> live;
@@ -286,12 +333,14 @@ static void worker_loop(hm_server_s* S, int w) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
       // the oldest request whose matrix nobody serves and that is resident here or nowhere
+      int first_nrhs = 0;
       auto pick = [&]() -> bool {
         for (SrvRequest* r : S->q) {
           SrvMatrix* M = S->matrices[r->matrix].get();
           if (M->serving < 0 && (M->worker < 0 || M->worker == w)) {
             m = r->matrix;
             Mp = M;
+            first_nrhs = r->nrhs;
             return true;
           }
         }
@@ -301,7 +350,15 @@ static void worker_loop(hm_server_s* S, int w) {
       if (!Mp) return;  // stopping, and nothing this worker can take
       Mp->serving = w;
       Mp->worker = w;
-      take_requests(S, m, S->max_batch_rhs, &batch);
+      // the session's starting columns: within a quarter of the worker's budget for the
+      // GMRES workspace (the oldest request always fits)
+      int cap = S->max_batch_rhs;
+      const hm_opts& o = W.ctx->opts;
+      if (o.hbm_budget) {
+        const double per_col = (2.0 * o.restart + 6.0) * 8.0 * (double)Mp->n;
+        cap = std::max(first_nrhs, std::min(cap, (int)(0.25 * (double)o.hbm_budget / per_col)));
+      }
+      take_requests(S, m, cap, &batch);
     }
     SrvMatrix& M = *Mp;
     // one system's transient solve state (apply plans, GMRES workspace) per worker
@@ -380,6 +437,7 @@ int hm_server_add_matrix(hm_server_t S, int32_t n, const int64_t* rowptr, const 
   }
   M.colidx.assign(colidx, colidx + nnz);
   M.values.assign(values, values + nnz);
+  M.nnz = nnz;
   M.coords.assign(grid_coords, grid_coords + (size_t)n * dim);
   std::lock_guard<std::mutex> lk(S->mu);
   S->matrices.push_back(std::make_unique<SrvMatrix>(std::move(M)));
@@ -444,6 +502,7 @@ int hm_server_get_stats(hm_server_t S, hm_server_stats* st) {
   for (auto& W : S->workers) resident += W.ctx->allocated;
   st->device_bytes = (double)resident;
   st->joined = S->joined;
+  st->oom_retries = S->oom_retries;
   return HM_OK;
 }
 

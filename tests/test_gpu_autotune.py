@@ -82,7 +82,7 @@ def test_every_forced_variant_solves(precision):
     b = rhs_uniform(P.n, 2, 14)
     A = P.scipy()
     xs = []
-    for v in (0, 1, 2, 3):
+    for v in (0, 1, 2, 3, 4):
         hm.hm_tune_force(ctx, v)
         s = hm.hm_analyze(ctx, P.n, P.rowptr, P.colidx, 2, P.coords)
         hm.hm_factor(s, P.values, 1e-4)
@@ -93,7 +93,7 @@ def test_every_forced_variant_solves(precision):
             assert np.linalg.norm(b[:, c] - A @ x[:, c]) / np.linalg.norm(b[:, c]) <= 1e-10, v
         xs.append(x)
         hm.hm_destroy(s)
-    for v in (1, 2, 3):
+    for v in (1, 2, 3, 4):
         assert np.linalg.norm(xs[v] - xs[0]) / np.linalg.norm(xs[0]) <= 1e-8, v
     with pytest.raises(hm.HmError):
         hm.hm_tune_force(ctx, 7)

@@ -24,9 +24,10 @@ except ImportError:  # the library is built on the GPU machine; a CPU-only machine s
 RTOL = 1e-10
 
 
-def bench_ctx(precision):
+def bench_ctx(precision, keep_fronts=0):
     o = hm.hm_default_opts()  # nd_leaf 64, hodlr_leaf 64, n_c 64, samples 48: bench.py's
     o.precision = precision
+    o.keep_fronts = keep_fronts  # 1: every front's update stays readable (hm_get_update)
     return hm.hm_create(o)
 
 
@@ -63,7 +64,7 @@ def test_q1024_ordering_and_symbolic_bit_exact(q1024):
 
 def test_q1024_sampled_leaf_updates_and_bench_solve(q1024):
     P, prm, et, sym = q1024
-    ctx = bench_ctx(hm.HM_PREC_MIXED)
+    ctx = bench_ctx(hm.HM_PREC_MIXED, keep_fronts=1)
     s = hm.hm_analyze(ctx, P.n, P.rowptr, P.colidx, 2, P.coords)
     hm.hm_factor(s, P.values, prm["tol"])
     # leaves: U = F_ff - F_fp F_pp^{-1} F_pf of the assembled front alone (FP32 factor)

@@ -36,9 +36,9 @@ def problems():
 PROBLEMS = problems()
 
 
-def make(p, precision, nd_leaf=64, hodlr_leaf=64, n_c=64, samples=48):
+def make(p, precision, nd_leaf=64, hodlr_leaf=64, n_c=64, samples=48, **opts):
     return hm.Solver(p.n, p.rowptr, p.colidx, grid_coords=p.coords, dim=p.dim, precision=precision,
-                     nd_leaf=nd_leaf, hodlr_leaf=hodlr_leaf, n_c=n_c, samples=samples)
+                     nd_leaf=nd_leaf, hodlr_leaf=hodlr_leaf, n_c=n_c, samples=samples, **opts)
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
@@ -73,7 +73,7 @@ def test_dense_fronts_match_conventional_mf(name, prec, tol):
     sym = symbolic.symbolic(p.rowptr, p.colidx, et)
     Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
     _, (F, U) = dense_mf.factor(Ap, et, sym, keep_fronts=True)
-    s = make(p, prec, nd_leaf=leaf, n_c=128)
+    s = make(p, prec, nd_leaf=leaf, n_c=128, keep_fronts=1)
     s.factor(p.values, 0.0)
     for q in range(et.nfronts):
         nu = len(sym.If[q])
@@ -116,7 +116,7 @@ def test_hodlr_updates_match_oracle_rrf(name):
     Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
     prm = hodlr_mf.Params(tol=tol, n_c=nc, leaf=hl, compressor="rrf", samples=k, seed=0x5EED)
     fr, trace = hodlr_mf.factor(Ap, et, sym, prm, keep=True)
-    s = make(p, hm.HM_PREC_FP64, nd_leaf=leaf, hodlr_leaf=hl, n_c=nc, samples=k)
+    s = make(p, hm.HM_PREC_FP64, nd_leaf=leaf, hodlr_leaf=hl, n_c=nc, samples=k, keep_fronts=1)
     s.factor(p.values, tol)
     oranks = hodlr_mf.ranks(fr)
     mismatched = 0
@@ -137,6 +137,142 @@ def test_hodlr_updates_match_oracle_rrf(name):
         assert err <= 1e-8, (q, err)
     assert mismatched <= max(1, len(oranks) // 100), mismatched
     s.close()
+
+
+@pytest.mark.parametrize("name", ["q1_64", "q1_33_lognormal", "hex_9"])
+def test_compressed_fff_updates_match_oracle(name):
+    """compress_ff (the paper's F_ff^HODLR, Section 4.2.1): F_ff's off-diagonal blocks
+    are replaced by their range-finder approximations (block kind 2 of the sketch) before
+    the update F_ff^HODLR - W T W^T is formed.  FP64 against the oracle's
+    ``compress_ff=True``: every update U_p agrees to 1e-8, except fronts where a
+    singular value sits at the threshold and the two ranks differ by one (<= 3% of the
+    fronts; there the difference is that singular value, <= 10 tol of the front); the
+    approximation is active (the updates differ from the uncompressed ones by more than
+    rounding on some front) and the preconditioned solve reaches x*."""
+    p = PROBLEMS[name]
+    leaf, hl, nc, k, tol = 16, 8, 8, 12, 1e-6
+    et = nd.nested_dissection(p.coords, leaf)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    Ap = dense_mf.permuted_matrix(p.rowptr, p.colidx, p.values, et)
+    prm = hodlr_mf.Params(tol=tol, n_c=nc, leaf=hl, compressor="rrf", samples=k, seed=0x5EED,
+                          compress_ff=True)
+    _, trace = hodlr_mf.factor(Ap, et, sym, prm, keep=True)
+    prm0 = hodlr_mf.Params(tol=tol, n_c=nc, leaf=hl, compressor="rrf", samples=k, seed=0x5EED)
+    _, trace0 = hodlr_mf.factor(Ap, et, sym, prm0, keep=True)
+    s = make(p, hm.HM_PREC_FP64, nd_leaf=leaf, hodlr_leaf=hl, n_c=nc, samples=k, compress_ff=1,
+             keep_fronts=1)
+    s.factor(p.values, tol)
+    off, changed, checked = [], 0, 0
+    for q in range(et.nfronts):
+        nu = len(sym.If[q])
+        if nu == 0:
+            continue
+        Ug = np.tril(hm.hm_get_update(s.sys, q, nu))
+        ref = np.tril(trace["U"][q])
+        scale = max(np.abs(ref).max(), 1e-300)
+        err = np.abs(Ug - ref).max() / scale
+        changed += np.abs(np.tril(trace0["U"][q]) - ref).max() / scale > 1e-10
+        checked += 1
+        if err > 1e-8:
+            off.append((q, err))
+            assert err <= 10 * tol, (q, err)
+    assert changed > 0
+    assert len(off) <= max(1, 3 * checked // 100), off
+    b = rhs_uniform(p.n, 1, 4)[:, 0]
+    x, info = s.solve(b, rtol=1e-10)
+    assert info["converged"] == 1
+    xs = dense_mf.direct_solve(p.rowptr, p.colidx, p.values, p.coords, b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["q1_64", "hex_9", "p1_37"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_memory_report_matches_symbolic(name, prec):
+    """The memory comparison of hm_factor_info (Section 6: factor storage against the
+    conventional multifrontal method) recomputed from the oracle's ordering and symbolic
+    structure: L of the conventional method = sum over fronts of np (np + 1) / 2 + np nu
+    entries; its peak (L so far + live updates + the current front, children before
+    parents) by a replay of the elimination; the front storage = sum of nhat^2 with one
+    range per front, the largest even-depth plus the largest odd-depth level sum of
+    nhat^2 with reuse."""
+    p = PROBLEMS[name]
+    es = 8 if prec == 0 else 4
+    et = nd.nested_dissection(p.coords, 16)
+    sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+    npv = np.diff(np.asarray(et.first)).astype(float)
+    nu = np.array([len(sym.If[q]) for q in range(et.nfronts)], dtype=float)
+    L = float(np.sum(npv * (npv + 1) / 2 + npv * nu))
+    Lsofar, live, peak = 0.0, 0.0, 0.0
+    for q in range(et.nfronts):
+        nh = npv[q] + nu[q]
+        peak = max(peak, Lsofar + live + nh * (nh + 1) / 2)
+        live -= sum(nu[c] * (nu[c] + 1) / 2 for c in sym.children[q])
+        Lsofar += npv[q] * (npv[q] + 1) / 2 + npv[q] * nu[q]
+        live += nu[q] * (nu[q] + 1) / 2
+    peak = max(peak, Lsofar)
+    lev = np.asarray(et.level)
+    per_level = np.array([np.sum((npv[lev == l] + nu[lev == l]) ** 2) for l in range(lev.max() + 1)])
+    banks = per_level[0::2].max() + (per_level[1::2].max() if len(per_level) > 1 else 0)
+    for keep, arena in ((1, float(np.sum((npv + nu) ** 2))), (0, float(banks))):
+        s = make(p, prec, nd_leaf=16, hodlr_leaf=8, n_c=8, samples=12, keep_fronts=keep)
+        info = s.factor(p.values, 1e-6)
+        assert info["conventional_bytes"] == pytest.approx(L * es, rel=1e-12)
+        assert info["conventional_peak_bytes"] == pytest.approx(peak * es, rel=1e-12)
+        # the front storage: one range per front, or two banks (even / odd depths)
+        assert info["front_bytes"] == pytest.approx(arena * es, rel=1e-12)
+        assert 0 < info["stored_bytes"] < info["device_bytes"]
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["q1_64", "hex_9", "p1_37"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_front_storage_reuse_changes_nothing(name, prec):
+    """Front storage shared by the tree levels of each parity (keep_fronts 0, the
+    default) against one range per front (keep_fronts 1): the preconditioner applies are
+    bit for bit the same, the storage is smaller, and only the updates of depth <= 1
+    stay readable."""
+    p = PROBLEMS[name]
+    r = rhs_uniform(p.n, 3, 9)
+    out, info = [], []
+    for keep in (0, 1):
+        s = make(p, prec, nd_leaf=16, hodlr_leaf=8, n_c=8, samples=12, keep_fronts=keep)
+        info.append(s.factor(p.values, 1e-6))
+        z = np.zeros_like(r)
+        s.precond(r, z, nrhs=3)
+        out.append(z)
+        if keep == 0:
+            et = nd.nested_dissection(p.coords, 16)  # the same tree (bit-exact ordering)
+            sym = symbolic.symbolic(p.rowptr, p.colidx, et)
+            deep = int(np.flatnonzero(np.asarray(et.level) >= 2)[0])
+            with pytest.raises(hm.HmError):
+                hm.hm_get_update(s.sys, deep, len(sym.If[deep]))
+        s.close()
+    assert np.array_equal(out[0], out[1])
+    assert info[0]["front_bytes"] < info[1]["front_bytes"]
+    assert info[0]["device_bytes"] < info[1]["device_bytes"]
+
+
+@pytest.mark.parametrize("name", ["q1_64", "hex_9", "p1_37"])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_bulk_staged_dense_down_matches_default(name, prec, nrhs):
+    """Variant 4 of the dense downward site (pivot rows staged in shared memory by bulk
+    copies in chunks, two buffers) against the default kernel: the same products summed
+    in another order, so equal to rounding (FP64 1e-12, FP32 1e-5 relative)."""
+    p = PROBLEMS[name]
+    r = rhs_uniform(p.n, nrhs, 21)
+    z = []
+    for v in (0, 4):
+        s = make(p, prec, nd_leaf=16, hodlr_leaf=8, n_c=8, samples=12)
+        hm.hm_tune_force(s.ctx, v)
+        s.factor(p.values, 1e-6)
+        zz = np.zeros_like(r)
+        s.precond(r, zz, nrhs=nrhs)
+        z.append(zz)
+        s.close()
+    err = np.abs(z[1] - z[0]).max() / np.abs(z[0]).max()
+    assert err <= (1e-12 if prec == 0 else 1e-5), err
 
 
 def _oracle_blocks(fr_q):
@@ -336,7 +472,7 @@ def test_tensor_core_3xtf32_gemms_match_simt():
     p = q1_square(96, lognormal_coefficients(96 * 96, 1.0, seed=8))
     out = {}
     for v in (0, 4):
-        s = make(p, hm.HM_PREC_MIXED, nd_leaf=64, hodlr_leaf=32, n_c=32, samples=48)
+        s = make(p, hm.HM_PREC_MIXED, nd_leaf=64, hodlr_leaf=32, n_c=32, samples=48, keep_fronts=1)
         hm.hm_tune_force(s.ctx, v)
         s.factor(p.values, 1e-4)
         _, nf = hm.hm_get_sizes(s.sys)
