@@ -132,7 +132,7 @@ __host__ __device__ __forceinline__ uint64_t block_id(int front, int kind, int l
 __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // Packed dense-front factor: [F_pp^-1 | K^T] (np x nhat, ld np) then K (nu x np, ld nu),
-// each part starting on a 16-byte boundary (bulk copies read whole 16-byte units).
+// each part starting on a 16-byte boundary (whole 16-byte units for vector or bulk copies).
 __host__ __device__ __forceinline__ int64_t packed_k_offset(int np, int nhat, int es) {
   const int64_t a = 16 / es;
   return ((int64_t)np * nhat + a - 1) / a * a;
@@ -171,15 +171,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
   return false;
 }
 
-// One bulk copy by the copy engine (not the threads): `bytes` (a multiple of 16; both
-// addresses 16-byte aligned) from global memory into this CTA's shared memory at `dst`;
-// the mbarrier `bar` expects the bytes (one arrival, by the calling thread).
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
 #endif
 
 // Opt a kernel into the largest dynamic shared memory the device allows per block

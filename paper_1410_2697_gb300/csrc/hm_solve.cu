@@ -281,116 +281,6 @@ __global__ void __launch_bounds__(NT) k_dense_down(const int* __restrict__ front
   }
 }
 
-// Downward pass of a dense front with the packed pivot rows staged by the bulk-copy
-// engine: [F_pp^-1 | K^T] (np x nhat, contiguous, ld np) is copied in column chunks of
-// `chunk_elems` elements into two shared-memory buffers ahead of the threads, so the
-// bytes in flight do not depend on the threads; each thread then forms one row of
-// x_p = [F_pp^-1 | K^T] [b_p; -x(I_p^f)] from shared memory (np <= NT).  Every wait on a
-// chunk is bounded (wait_limit polls): a chunk that does not arrive stops the block's
-// arithmetic, raises HM_ERR_DEVICE_TIMEOUT and the block waits (bounded) for the copies
-// it issued before it exits.
-constexpr int kBulkMaxCols = 128;  // columns of one chunk at most (the vector chunk's rows)
-constexpr int kBulkWaitLimit = 1 << 22;  // default polls of one chunk's mbarrier
-
-template <typename T, int RB, int NT>
-__global__ void __launch_bounds__(NT) k_dense_down_bulk(const int* __restrict__ fronts, int nrhs, int n,
-                                                        T* __restrict__ xv, const int32_t* __restrict__ first,
-                                                        const int* __restrict__ npiv, const int* __restrict__ nhat,
-                                                        const int64_t* __restrict__ cf_off,
-                                                        const int64_t* __restrict__ fvoff,
-                                                        const int64_t* __restrict__ ifoff,
-                                                        const int32_t* __restrict__ iflist, const T* __restrict__ D,
-                                                        const T* __restrict__ FV, int chunk_elems, int wait_limit,
-                                                        int* __restrict__ err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int s_ok;
-  T* Mb0 = reinterpret_cast<T*>(smem_raw);
-  T* X = Mb0 + 2 * (size_t)chunk_elems;  // kBulkMaxCols x RB
-  const int q = fronts[blockIdx.x];
-  const int r0 = blockIdx.y * RB, nr = min(RB, nrhs - r0);
-  const int np = npiv[q], nh = nhat[q], b0 = first[q];
-  const T* H = D + cf_off[q];
-  const T* fv = FV + fvoff[q];
-  const int32_t* If = iflist + ifoff[q];
-  constexpr int A = 16 / (int)sizeof(T);
-  const int ch = min(kBulkMaxCols, chunk_elems / np) / A * A;  // >= A: np <= chunk_elems / A
-  const int nch = (nh + ch - 1) / ch;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_ok = 1;
-  }
-  __syncthreads();
-  auto issue = [&](int k) {  // chunk k into buffer k & 1 (whole 16-byte units)
-    const int cols = min(ch, nh - k * ch);
-    const uint32_t bytes = (uint32_t)(((int64_t)np * cols * (int64_t)sizeof(T) + 15) / 16 * 16);
-    bulk_g2s(smem_u32(Mb0 + (size_t)(k & 1) * chunk_elems), H + (int64_t)k * ch * np, bytes, smem_u32(&bar[k & 1]));
-  };
-  int issued = 0;  // chunks issued so far (thread 0's count)
-  if (tid == 0) {
-    issue(0);
-    if (nch > 1) issue(1);
-    issued = min(nch, 2);
-  }
-  T acc[RB];
-#pragma unroll
-  for (int r = 0; r < RB; ++r) acc[r] = T(0);
-  for (int k = 0; k < nch; ++k) {
-    const int c0 = k * ch, cols = min(ch, nh - c0);
-    for (int e = tid; e < cols * RB; e += NT) {  // [b_p; -x(I_p^f)] rows c0 .. c0 + cols
-      const int i = c0 + e % cols, r = e / cols;
-      T v = T(0);
-      if (r < nr) v = i < np ? fv[i + (int64_t)(r0 + r) * nh] : -xv[If[i - np] + (int64_t)(r0 + r) * n];
-      X[(i - c0) * RB + r] = v;
-    }
-    if (s_ok && !mbar_wait(smem_u32(&bar[k & 1]), (uint32_t)((k >> 1) & 1), wait_limit)) s_ok = 0;
-    __syncthreads();
-    if (s_ok && tid < np) {
-      const T* M = Mb0 + (size_t)(k & 1) * chunk_elems + tid;
-      int c = 0;
-      for (; c + 4 <= cols; c += 4) {
-        T m[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) m[u] = M[(c + u) * np];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int r = 0; r < RB; ++r) acc[r] = fma(m[u], X[(c + u) * RB + r], acc[r]);
-      }
-      for (; c < cols; ++c) {
-        const T m = M[c * np];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) acc[r] = fma(m, X[c * RB + r], acc[r]);
-      }
-    }
-    __syncthreads();  // buffer k & 1 and X are free again
-    if (tid == 0 && k + 2 < nch && s_ok) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // our reads before the copy's writes
-      issue(k + 2);
-      issued = k + 3;
-    }
-  }
-  if (s_ok) {
-    if (tid < np) {
-#pragma unroll
-      for (int r = 0; r < RB; ++r)
-        if (r < nr) xv[b0 + tid + (int64_t)(r0 + r) * n] = acc[r];
-    }
-    return;
-  }
-  if (tid == 0) {  // a chunk did not arrive: report, then wait for the last copy into each buffer
-    raise_error(err, HM_ERR_DEVICE_TIMEOUT, q, 0);
-    for (int b = 0; b < 2 && b < issued; ++b) {
-      const int last = b + (issued - 1 - b) / 2 * 2;  // the last chunk issued into buffer b
-      (void)mbar_wait(smem_u32(&bar[b]), (uint32_t)((last >> 1) & 1), wait_limit);
-    }
-  }
-  __syncthreads();
-}
-
 static int rhs_block(int nrhs) { return nrhs >= 16 ? 16 : nrhs > 4 ? 8 : nrhs > 2 ? 4 : nrhs; }
 
 // 64 threads per front when every front of the level is small (more fronts in flight per
@@ -479,43 +369,9 @@ static int dense_up(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_
   return HM_OK;
 }
 
-// The bulk-staged downward kernel: 64 or 128 threads (one per pivot row), two buffers of
-// 8 KB, the vector chunk beside them.
-template <typename T, int RB>
-static void dense_down_bulk(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
-                            int nrhs, T* xv, cudaStream_t s) {
-  const Plan& P = sys->plan;
-  const int chunk = 8192 / (int)sizeof(T);
-  const size_t smem = sizeof(T) * ((size_t)2 * chunk + (size_t)kBulkMaxCols * RB);
-  const dim3 grid((unsigned)lp.dense.count, (unsigned)((nrhs + RB - 1) / RB));
-  const int wl = sys->ctx->opts.wait_limit > 0 ? sys->ctx->opts.wait_limit : kBulkWaitLimit;
-  if (lp.dense_max_np <= 64)
-    k_dense_down_bulk<T, RB, 64><<<grid, 64, smem, s>>>(lp.dense.dev(base), nrhs, sys->n, xv, sys->d_first, P.d_np,
-                                                       P.d_nhat, P.d_cf_off, sp->d_fvoff, sys->d_ifoff,
-                                                       sys->d_iflist, (const T*)sys->d_dfac, (const T*)sp->d_fv,
-                                                       chunk, wl, sys->d_err);
-  else
-    k_dense_down_bulk<T, RB, 128><<<grid, 128, smem, s>>>(lp.dense.dev(base), nrhs, sys->n, xv, sys->d_first,
-                                                         P.d_np, P.d_nhat, P.d_cf_off, sp->d_fvoff, sys->d_ifoff,
-                                                         sys->d_iflist, (const T*)sys->d_dfac, (const T*)sp->d_fv,
-                                                         chunk, wl, sys->d_err);
-}
-
-// Variant 4 of the downward site: the bulk-staged kernel (pivot blocks of at most 128
-// rows, which every dense front has: n_c <= 128).
 template <typename T>
 static void dense_down(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp,
                        int nrhs, T* xv, cudaStream_t s) {
-  if (sys->ctx->tune.variant(TS_DENSE_DOWN, dense_sig(lp, nrhs)) == 4 && lp.dense_max_np <= 128) {
-    switch (rhs_block(nrhs)) {
-      case 1: dense_down_bulk<T, 1>(lp, base, sys, sp, nrhs, xv, s); break;
-      case 2: dense_down_bulk<T, 2>(lp, base, sys, sp, nrhs, xv, s); break;
-      case 4: dense_down_bulk<T, 4>(lp, base, sys, sp, nrhs, xv, s); break;
-      case 8: dense_down_bulk<T, 8>(lp, base, sys, sp, nrhs, xv, s); break;
-      default: dense_down_bulk<T, 16>(lp, base, sys, sp, nrhs, xv, s); break;
-    }
-    return;
-  }
   switch (dense_rhs_block(sys->ctx, TS_DENSE_DOWN, lp, nrhs)) {
     case 1: dense_down_rb<T, 1>(lp, base, sys, sp, nrhs, xv, s); break;
     case 2: dense_down_rb<T, 2>(lp, base, sys, sp, nrhs, xv, s); break;

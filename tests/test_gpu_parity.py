@@ -253,28 +253,6 @@ def test_front_storage_reuse_changes_nothing(name, prec):
     assert info[0]["device_bytes"] < info[1]["device_bytes"]
 
 
-@pytest.mark.parametrize("name", ["q1_64", "hex_9", "p1_37"])
-@pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("nrhs", [1, 3, 16])
-def test_bulk_staged_dense_down_matches_default(name, prec, nrhs):
-    """Variant 4 of the dense downward site (pivot rows staged in shared memory by bulk
-    copies in chunks, two buffers) against the default kernel: the same products summed
-    in another order, so equal to rounding (FP64 1e-12, FP32 1e-5 relative)."""
-    p = PROBLEMS[name]
-    r = rhs_uniform(p.n, nrhs, 21)
-    z = []
-    for v in (0, 4):
-        s = make(p, prec, nd_leaf=16, hodlr_leaf=8, n_c=8, samples=12)
-        hm.hm_tune_force(s.ctx, v)
-        s.factor(p.values, 1e-6)
-        zz = np.zeros_like(r)
-        s.precond(r, zz, nrhs=nrhs)
-        z.append(zz)
-        s.close()
-    err = np.abs(z[1] - z[0]).max() / np.abs(z[0]).max()
-    assert err <= (1e-12 if prec == 0 else 1e-5), err
-
-
 def _oracle_blocks(fr_q):
     """(level, node) -> dense U V^T of the oracle's compressed blocks; -1 -> F_fp."""
     out = {(-1, 0): fr_q.W @ fr_q.V.T}
