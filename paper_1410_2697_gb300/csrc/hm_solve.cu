@@ -169,7 +169,7 @@ __device__ __forceinline__ void slice_reduce(T* __restrict__ red, int S, T (&acc
 // starts at D + cf_off[q]: [F_pp^-1 | K^T] (np x nhat, ld np), then K (nu x np, ld nu)
 // at packed_k_offset.
 template <typename T, int RB, int NT>
-__global__ void __launch_bounds__(NT) k_dense_up(const int* __restrict__ fronts, int nrhs, int n,
+__global__ void __launch_bounds__(NT, 1024 / NT) k_dense_up(const int* __restrict__ fronts, int nrhs, int n,
                                                  const T* __restrict__ win, const int32_t* __restrict__ first,
                                                  const int* __restrict__ npiv, const int* __restrict__ nhat,
                                                  const int64_t* __restrict__ cf_off,
@@ -186,9 +186,18 @@ __global__ void __launch_bounds__(NT) k_dense_up(const int* __restrict__ fronts,
   const int q = fronts[blockIdx.x];
   const int r0 = blockIdx.y * RB, nr = min(RB, nrhs - r0);
   const int np = npiv[q], nh = nhat[q], nu = nh - np, b0 = first[q];
-  for (int e = threadIdx.x; e < nh * RB; e += NT) {
-    const int i = e % nh, r = e / nh;
-    X[i * RB + r] = (i < np && r < nr) ? win[b0 + i + (int64_t)(r0 + r) * n] : T(0);
+  // one row per thread, its loads eight at a time in flight (as in the downward pass)
+  constexpr int VB = RB < 8 ? RB : 8;
+  for (int i = threadIdx.x; i < nh; i += NT) {
+    const T* src = win + b0 + i + (int64_t)r0 * n;
+#pragma unroll
+    for (int rb = 0; rb < RB; rb += VB) {
+      T v[VB];
+#pragma unroll
+      for (int r = 0; r < VB; ++r) v[r] = (i < np && rb + r < nr) ? src[(int64_t)(rb + r) * n] : T(0);
+#pragma unroll
+      for (int r = 0; r < VB; ++r) X[i * RB + rb + r] = v[r];
+    }
   }
   __syncthreads();
   for (int ci = child_ptr[q]; ci < child_ptr[q + 1]; ++ci) {
@@ -196,9 +205,17 @@ __global__ void __launch_bounds__(NT) k_dense_up(const int* __restrict__ fronts,
     const int npc = npiv[c], nhc = nhat[c], nuc = nhc - npc;
     const T* fc = FV + fvoff[c] + npc;
     const int32_t* rm = relmap + ifoff[c];
-    for (int e = threadIdx.x; e < nuc * nr; e += NT) {
-      const int t = e % nuc, r = e / nuc;
-      X[rm[t] * RB + r] += fc[t + (int64_t)(r0 + r) * nhc];
+    for (int t = threadIdx.x; t < nuc; t += NT) {  // the child's rows go to distinct rows here
+      const T* src = fc + t + (int64_t)r0 * nhc;
+      T* dst = X + rm[t] * RB;
+#pragma unroll
+      for (int rb = 0; rb < RB; rb += VB) {
+        T v[VB];
+#pragma unroll
+        for (int r = 0; r < VB; ++r) v[r] = rb + r < nr ? src[(int64_t)(rb + r) * nhc] : T(0);
+#pragma unroll
+        for (int r = 0; r < VB; ++r) dst[rb + r] += v[r];
+      }
     }
     __syncthreads();
   }
@@ -263,11 +280,23 @@ __global__ void __launch_bounds__(NT) k_dense_down(const int* __restrict__ front
     for (int kc0 = 0; kc0 < nh; kc0 += smem_rows) {
       const int kc1 = min(nh, kc0 + smem_rows), len = kc1 - kc0;
       __syncthreads();
-      for (int e = threadIdx.x; e < len * RB; e += NT) {
-        const int i = kc0 + e % len, r = e / len;
-        T v = T(0);
-        if (r < nr) v = i < np ? fv[i + (int64_t)(r0 + r) * nh] : -xv[If[i - np] + (int64_t)(r0 + r) * n];
-        X[(i - kc0) * RB + r] = v;
+      // one row of the right-hand block per thread: its loads are independent, so they
+      // go in flight eight at a time (the update rows gather x through I_p^f)
+      constexpr int VB = RB < 8 ? RB : 8;
+      for (int i = kc0 + threadIdx.x; i < kc1; i += NT) {
+        const bool piv = i < np;
+        const T* src = piv ? fv + i + (int64_t)r0 * nh : xv + If[i - np] + (int64_t)r0 * n;
+        const int64_t ld = piv ? nh : n;
+        const T sgn = piv ? T(1) : T(-1);
+        T* dst = X + (i - kc0) * RB;
+#pragma unroll
+        for (int rb = 0; rb < RB; rb += VB) {
+          T v[VB];
+#pragma unroll
+          for (int r = 0; r < VB; ++r) v[r] = rb + r < nr ? src[(int64_t)(rb + r) * ld] : T(0);
+#pragma unroll
+          for (int r = 0; r < VB; ++r) dst[rb + r] = sgn * v[r];
+        }
       }
       __syncthreads();
       if (active) rowblock_acc<T, RB>(H, np, j, kc0 + sl * len / S, kc0 + (sl + 1) * len / S, X, kc0, acc);
