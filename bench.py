@@ -845,7 +845,7 @@ def run_probe(args):
     from fixtures import lognormal_coefficients, q1_square, rhs_uniform, workload
     if args.probe == "hex_factor":
         P, _ = workload("hex_lognormal_64^3")
-        precision, nrhs = hm.HM_PREC_MIXED_BF16, 0
+        precision, nrhs = hm.HM_PREC_MIXED_BF16, 1
     else:
         m = args.m
         P = q1_square(m, lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=1))

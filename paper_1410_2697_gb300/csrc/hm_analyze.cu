@@ -1120,11 +1120,13 @@ int analyze_impl(hm_sys_s* sys, const int64_t* rowptr, const int32_t* colidx, in
     launch_amap(sys);
   }
   HM_TRY(check_device_error(sys, "analyze: assembly map"));
+  host_mark("analyze: assembly map");
   {
     ProfScope ps(sys->ctx, PC_GROUP, Work{0.0, 48.0 * sys->nnz}, 4);
     HM_TRY(build_level_scatter(sys, sys->d_amap, &tmp));
   }
   sys->d_amap = nullptr;  // freed with the analysis temporaries
+  host_mark("analyze: entries by depth");
   return check_device_error(sys, "analyze: entries by depth");
 }
 

@@ -567,6 +567,7 @@ int hm_factor(hm_sys_t sys, const double* values, double tol, hm_factor_info* in
     info->conventional_bytes = L * es;
     info->conventional_peak_bytes = peak * es;
     info->device_bytes = owned_bytes(sys->ctx, sys->allocs) + owned_bytes(sys->ctx, sys->plan_allocs);
+    host_mark("factor: info");
   }
   return HM_OK;
 }

@@ -729,12 +729,12 @@ __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict
   T* P = (T*)t.P;
   const int ldp = t.ldp > 0 ? t.ldp : np, nu = nh - np;
   T* PK = P + packed_k_offset(np, nh, (int)sizeof(T));
-  for (int c = warp; c < nh; c += 8) {
-    for (int r = lane; r < np; r += 32) P[r + (size_t)c * ldp] = S[r + c * ls];
-    if (c < np) {
-      for (int r = np + lane; r < nh; r += 32) PK[(r - np) + (size_t)c * nu] = S[r + c * ls];
-    } else {
-      for (int r = c + lane; r < nh; r += 32) F[r + (size_t)c * ldf] = S[r + c * ls];
+  for (int c = warp; c < nh; c += 8) {  // one pass over the column, each entry to its store
+    for (int r = lane; r < nh; r += 32) {
+      const T v = S[r + c * ls];
+      if (r < np) P[r + (size_t)c * ldp] = v;
+      else if (c < np) PK[(r - np) + (size_t)c * nu] = v;
+      else if (r >= c) F[r + (size_t)c * ldf] = v;  // U_p: the lower triangle only
     }
   }
 }

@@ -301,6 +301,7 @@ int build_plan(hm_sys_s* sys) {
     }
   }
 
+  host_mark("build_plan: geometry");
   // ---------------------------------------------------------------- capacity checks
   for (int q = 0; q < nf; ++q) {
     const FrontGeom& g = P.fg[q];
@@ -375,6 +376,7 @@ int build_plan(hm_sys_s* sys) {
     HM_CUDA(cudaMemcpyAsync(P.d_flevel, P.h_flevel.data(), nf * 4, cudaMemcpyHostToDevice, s));
   }
 
+  host_mark("build_plan: allocations");
   // ---------------------------------------------------------------- factor tasks
   void* F = sys->d_front;
   void* Bo = sys->d_bo;
@@ -680,6 +682,7 @@ int build_plan(hm_sys_s* sys) {
     }
     P.stored_bytes += es * e;
   }
+  host_mark("build_plan: tasks");
   HM_TRY(A(&sys->d_qrs, P.qr_scratch, es));
   tb.relocate(sys->d_qrs);  // row-block QR tasks address the scratch by offset until now
   HM_TRY(A(&P.d_split_ws, tb.split_ws, es));
@@ -960,6 +963,7 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
     lp.down2 = tb.add_gemm(d2);
     plan_hodlr_apply(sys, sp.get(), lp, hod, nrhs, es);
   }
+  host_mark("solve plan: tasks");
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, &sp->d_split_ws, (size_t)std::max<int64_t>(tb.split_ws, 1) * es));
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_split_cnt, sizeof(unsigned) * std::max(tb.split_slots, 1)));
   HM_CUDA(cudaMemsetAsync(sp->d_split_cnt, 0, sizeof(unsigned) * std::max(tb.split_slots, 1),
