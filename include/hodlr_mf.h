@@ -377,8 +377,8 @@ const char* hm_last_error(void);
  * request by the worker that takes it, and the factorization stays resident in that
  * worker's context until evicted (least recently used first) to admit another matrix
  * within the budget.  Admission is by estimate, before the work allocates: a matrix's
- * estimate is its footprint when last resident (plus an eighth), else the largest bytes
- * per nonzero seen for matrices of its dimension; a session's is its slots times
+ * estimate is its footprint when last resident (plus an eighth), else the bytes per
+ * nonzero of the largest matrix of its dimension seen so far; a session's is its slots times
  * (2 restart + 10) FP64 vectors (plus a quarter and 4 MiB); the worker evicts until its
  * bytes plus the estimate fit.  A shortfall of the
  * estimate is caught by the budget check of the allocation itself (one more eviction

@@ -650,6 +650,20 @@ void launch_chol_inverse(const CholInvTask* tasks, int ntasks, int maxn, cudaStr
 // in registers; a sweep costs every thread TT^2 FMAs and 2 TT shared-memory reads of the
 // published pivot row and column, with one barrier per sweep (double-buffered).
 // =====================================================================================
+// (a0, a1) += m (r0, r1) by one packed FP32 instruction (fma.rn.f32x2: the two lanes
+// are the same round-to-nearest FMAs as two fma.rn.f32).
+__device__ __forceinline__ void fma_pair_f32(float& a0, float& a1, float m, float r0, float r1) {
+  asm("{\n.reg .b64 acc, mm, rr;\n"
+      "mov.b64 acc, {%0, %1};\n"
+      "mov.b64 mm, {%2, %2};\n"
+      "mov.b64 rr, {%3, %4};\n"
+      "fma.rn.f32x2 acc, mm, rr, acc;\n"
+      "mov.b64 {%0, %1}, acc;\n}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(m), "f"(r0), "f"(r1));
+}
+__device__ __forceinline__ void fma_pair_f32(double&, double&, double, double, double) {}
+
 template <typename T, int TT>
 __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict__ tasks, int* err) {
   extern __shared__ unsigned char smem_raw[];
@@ -701,10 +715,17 @@ __global__ void __launch_bounds__(256) k_front_sweep(const SweepTask* __restrict
       for (int i = 0; i < TT; ++i) ci[i] = colk[buf][ty + 16 * i] * inv;
 #pragma unroll
       for (int j = 0; j < TT; ++j) rk[j] = rowk[buf][tx + 16 * j];
+      if constexpr (sizeof(T) == 4) {  // two FMAs per instruction (packed FP32 pairs)
 #pragma unroll
-      for (int i = 0; i < TT; ++i)
+        for (int i = 0; i < TT; ++i)
 #pragma unroll
-        for (int j = 0; j < TT; ++j) a[i][j] = fma(-ci[i], rk[j], a[i][j]);
+          for (int j = 0; j < TT; j += 2) fma_pair_f32(a[i][j], a[i][j + 1], -ci[i], rk[j], rk[j + 1]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < TT; ++i)
+#pragma unroll
+          for (int j = 0; j < TT; ++j) a[i][j] = fma(-ci[i], rk[j], a[i][j]);
+      }
       // row k and column k (the generic update left them at zero)
       if (tx == kr) {
 #pragma unroll

@@ -76,7 +76,22 @@ __global__ void __launch_bounds__(256) k_extend_add(const int* __restrict__ pare
   T* Fp = F + front_off[q];
   const int32_t* rm = relmap + ifoff[c];
   const int64_t cc = (int64_t)rm[col] * ldp;
-  for (int r = col + lane; r < nuc; r += 32) Fp[rm[r] + cc] += Fc[r];
+  // four rows per lane at a time: their map entries, then the values and destinations
+  for (int r0 = col + lane; r0 < nuc; r0 += 128) {
+    int d[4];
+    T v[4], o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = min(r0 + 32 * u, nuc - 1);
+      d[u] = rm[r];
+      v[u] = Fc[r];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o[u] = Fp[d[u] + cc];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r0 + 32 * u < nuc) Fp[d[u] + cc] = o[u] + v[u];
+  }
 }
 
 template <typename T>

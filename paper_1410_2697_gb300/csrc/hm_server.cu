@@ -19,7 +19,7 @@
 // (and before a session's GMRES workspace is allocated), the worker destroys its least
 // recently used idle resident systems until its context's bytes plus the estimate fit its
 // budget.  The estimate of a matrix is the footprint it had when last resident (plus an
-// eighth), else the largest bytes per nonzero seen so far for matrices of its dimension
+// eighth), else the bytes per nonzero of the largest matrix of its dimension seen so far
 // (a fixed per-nonzero figure before any); a session's is its slots times the GMRES and
 // apply vectors per column (plus a quarter and 4 MiB).  Should the estimate fall short, the allocation that exceeds the budget fails
 // and the step is retried after one more eviction (counted as oom_retries); a matrix that
@@ -124,13 +124,14 @@ static bool evict_one(hm_server_s* S, int w, int keep) {
 static size_t estimate_bytes(hm_server_s* S, const SrvMatrix& M) {
   if (M.bytes_seen) return M.bytes_seen + M.bytes_seen / 8;  // an eighth to spare
   std::lock_guard<std::mutex> lk(S->mu);
+  // the bytes per nonzero of the largest matrix of the same dimension seen so far (small
+  // systems carry fixed costs that would overstate a large one)
   double per_nnz = M.dim == 3 ? 1024.0 : 512.0;
-  bool seen = false;
+  int64_t best = 0;
   for (const auto& o : S->matrices)
-    if (o->bytes_seen && o->dim == M.dim && o->nnz > 0) {
-      const double r = (double)o->bytes_seen / (double)o->nnz;
-      per_nnz = seen ? std::max(per_nnz, r) : r;
-      seen = true;
+    if (o->bytes_seen && o->dim == M.dim && o->nnz > best) {
+      per_nnz = (double)o->bytes_seen / (double)o->nnz;
+      best = o->nnz;
     }
   return (size_t)(per_nnz * (double)M.nnz);
 }
