@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
     const int* __restrict__ npiv, const int* __restrict__ nhat, const int64_t* __restrict__ fvoff,
     const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child_list,
     const int64_t* __restrict__ ifoff, const int32_t* __restrict__ relmap, const int* __restrict__ leafb,
-    T* __restrict__ FV, HaDims dm) {
+    const int4* __restrict__ ea, T* __restrict__ FV, HaDims dm) {
   constexpr int RP = RB + 1;
   extern __shared__ __align__(16) unsigned char ha_smem[];
   T* sm = reinterpret_cast<T*>(ha_smem);
@@ -172,14 +172,15 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
   // the children's update parts through the relative maps, one child after another; a
   // relative map is increasing, so the entries that land on this CTA's rows are two
   // contiguous ranges of it
-  for (int ci = child_ptr[tk.q]; ci < child_ptr[tk.q + 1]; ++ci) {
+  const int cp0 = child_ptr[tk.q], nch = child_ptr[tk.q + 1] - cp0;
+  for (int ci = cp0; ci < cp0 + nch; ++ci) {
     __syncthreads();
     const int ch = child_list[ci];
-    const int npc = npiv[ch], nhc = nhat[ch], nuc = nhc - npc;
+    const int npc = npiv[ch], nhc = nhat[ch];
     const T* fc = FV + fvoff[ch] + npc;
     const int32_t* rm = relmap + ifoff[ch];
-    const int ta = lower_bound_i32(rm, nuc, P0), tb = lower_bound_i32(rm, nuc, P1);
-    const int tc = lower_bound_i32(rm, nuc, np + U0), td = lower_bound_i32(rm, nuc, np + U1);
+    const int4 rg = ea[tk.ea_off + c * nch + (ci - cp0)];  // formed once per plan
+    const int ta = rg.x, tb = rg.y, tc = rg.z, td = rg.w;
     const int na = tb - ta, nb = td - tc;
     const int tot = (na + nb) * nr;
     for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * kHaThreads) {  // eight entries per thread in flight
@@ -419,9 +420,43 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
   if (C > 1) cluster.sync();  // no CTA leaves while a peer reads its partials
 }
 
+// The relative map of a child is increasing, so the entries that land on CTA c's pivot
+// rows [P0, P1) and update rows np + [U0, U1) are two contiguous ranges of it: found by
+// binary search once per plan (one thread per (task, CTA, child)), not in every apply.
+__global__ void k_hodlr_child_ranges(const HApplyTask* __restrict__ tasks, int C,
+                                     const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child_list,
+                                     const int* __restrict__ npiv, const int* __restrict__ nhat,
+                                     const int64_t* __restrict__ ifoff, const int32_t* __restrict__ relmap,
+                                     const int* __restrict__ leafb, int4* __restrict__ ea) {
+  const HApplyTask& tk = tasks[blockIdx.x];
+  const int cp0 = child_ptr[tk.q], nch = child_ptr[tk.q + 1] - cp0;
+  const int lc = ilog2i(C);
+  const int* lb = leafb + tk.leaf_off;
+  const int span = 1 << (tk.L - lc);
+  for (int e = threadIdx.x; e < C * nch; e += blockDim.x) {
+    const int c = e / nch, ci = e - c * nch;
+    const int P0 = lb[c * span], P1 = lb[(c + 1) * span];
+    const int U0 = (int)((int64_t)tk.nu * c / C), U1 = (int)((int64_t)tk.nu * (c + 1) / C);
+    const int ch = child_list[cp0 + ci];
+    const int nuc = nhat[ch] - npiv[ch];
+    const int32_t* rm = relmap + ifoff[ch];
+    ea[tk.ea_off + e] = make_int4(lower_bound_i32(rm, nuc, P0), lower_bound_i32(rm, nuc, P1),
+                                  lower_bound_i32(rm, nuc, tk.np + U0), lower_bound_i32(rm, nuc, tk.np + U1));
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------
+int hodlr_child_ranges(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp) {
+  if (!lp.ha_ok || lp.ha_tasks.count == 0) return HM_OK;
+  const Plan& P = sys->plan;
+  k_hodlr_child_ranges<<<lp.ha_tasks.count, 64, 0, sys->ctx->stream>>>(
+      lp.ha_tasks.dev(base), lp.ha_C, sys->d_child_ptr, sys->d_child_list, P.d_np, P.d_nhat, sys->d_ifoff,
+      sys->d_relmap, lp.ha_leaf.dev(base), sp->d_ea);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
 size_t hodlr_apply_smem(const HaDims& d, int RB, bool down, int es) {
   return (size_t)ha_layout(d, RB, down).total * es;
 }
@@ -450,7 +485,7 @@ static cudaError_t launch_rb(bool down, const LevelSolvePlan& lp, const unsigned
     return cudaLaunchKernelEx(&cfg, k_hodlr_up<T, RB>, tasks, C, nrhs, sys->n, win, (const int*)P.d_np,
                               (const int*)P.d_nhat, (const int64_t*)sp->d_fvoff, (const int32_t*)sys->d_child_ptr,
                               (const int32_t*)sys->d_child_list, (const int64_t*)sys->d_ifoff,
-                              (const int32_t*)sys->d_relmap, leafb, (T*)sp->d_fv, dm);
+                              (const int32_t*)sys->d_relmap, leafb, (const int4*)sp->d_ea, (T*)sp->d_fv, dm);
   return cudaLaunchKernelEx(&cfg, k_hodlr_down<T, RB>, tasks, C, nrhs, sys->n, xv, (const int64_t*)sys->d_ifoff,
                             (const int32_t*)sys->d_iflist, leafb, (const T*)sp->d_fv, dm);
 }

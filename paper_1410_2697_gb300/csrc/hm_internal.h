@@ -363,6 +363,7 @@ struct HApplyTask {
   const void* F;    // packed leaf inverses (np x lmax, ld np): leaf [lo, hi) in rows lo..hi
   int64_t fv_off;   // element offset of the front's vector block (nhat x nrhs)
   int q, first, np, nu, nhat, L, kf, leaf_off;  // leaf_off: its 2^L + 1 leaf boundaries
+  int ea_off;       // its entries of the child-range table (C x children of them)
   int kl[kHaMaxL];  // sketch width (column capacity) per level
   int col[kHaMaxL]; // first column of each level in X / Bo
 };
@@ -420,6 +421,8 @@ struct SolvePlan {
   void* d_sb = nullptr;         // T
   void* d_xfix = nullptr;       // T, n x nrhs: the solution (task tables point into it)
   int64_t* d_fvoff = nullptr;
+  int4* d_ea = nullptr;         // per (fused HODLR task, CTA, child): the child's relative-map
+  int64_t ea_total = 0;         // ranges landing on the CTA's pivot and update rows
   // captured apply (graph of the launches for input graph_in) and the last input seen
   std::vector<void*> allocs;    // device memory of this plan (freed when it is dropped)
   int64_t last_use = 0;
@@ -675,6 +678,7 @@ int launch_hodlr_apply(bool down, const LevelSolvePlan& lp, const unsigned char*
                        SolvePlan* sp, int nrhs, const T* win, T* xv, int rb);
 size_t hodlr_apply_smem(const HaDims& d, int RB, bool down, int es);
 int hodlr_apply_setup(int max_smem);
+int hodlr_child_ranges(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp);
 int direct_impl(hm_sys_s* sys, int nrhs, const double* d_b, int refine, double* d_x, hm_solve_info* info);
 // Slot sessions of GMRES for serving: nslots columns, each its own instance.  A right-hand
 // side enters a free slot between restart cycles (gm_session_put, host array in the

@@ -752,6 +752,8 @@ static void plan_hodlr_apply(hm_sys_s* sys, SolvePlan* sp, LevelSolvePlan& lp, c
     t.L = h.L;
     t.kf = h.kf;
     t.leaf_off = (int)leafb.size();
+    t.ea_off = (int)sp->ea_total;
+    sp->ea_total += (int64_t)C * sys->children(q).size();
     for (int l = 0; l < h.L; ++l) {
       t.kl[l] = h.kl[l];
       t.col[l] = h.col[l];
@@ -971,6 +973,8 @@ int get_solve_plan(hm_sys_s* sys, int nrhs, SolvePlan** out) {
   HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_tasks, std::max<size_t>(tb.host.size(), 16)));
   HM_CUDA(cudaMemcpyAsync(sp->d_tasks, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice,
                           sys->ctx->stream));
+  HM_TRY(dev_alloc_ctx(sys->ctx, &sp->allocs, (void**)&sp->d_ea, sizeof(int4) * std::max<int64_t>(sp->ea_total, 1)));
+  for (const auto& lp : sp->levels) HM_TRY(hodlr_child_ranges(lp, sp->d_tasks, sys, sp.get()));
   sp->last_use = ++sys->plan_clock;
   *out = sp.get();
   sys->solve_plans[nrhs] = std::move(sp);

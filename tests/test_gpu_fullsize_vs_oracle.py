@@ -61,6 +61,8 @@ def oracle():
     jobs = {
         "hex_blocks": pool.apply_async(oracle_jobs.hodlr_blocks, ("hex_lognormal_64^3", 1, TOL, 48),
                                        {"m": HEX_BLOCKS_M}),
+        "hex_blocks64": pool.apply_async(oracle_jobs.hodlr_blocks, ("hex_lognormal_64^3", 1, TOL, 64),
+                                         {"m": HEX_BLOCKS_M}),
         "hex": pool.apply_async(oracle_jobs.direct_with_kappa, ("hex_lognormal_64^3", 1)),
         "q1024": pool.apply_async(oracle_jobs.direct_with_kappa, ("q1_lognormal_1024x1024", 16)),
         "q1024_blocks": pool.apply_async(oracle_jobs.hodlr_blocks, ("q1_lognormal_1024x1024", 2, TOL, 48)),
@@ -74,10 +76,11 @@ def oracle():
     pool.join()
 
 
-def bench_ctx(precision, dofs_per_node=1):
+def bench_ctx(precision, dofs_per_node=1, samples=48):
     o = hm.hm_default_opts()  # nd_leaf 64, hodlr_leaf 64, n_c 64, samples 48: bench.py's
     o.precision = precision
     o.dofs_per_node = dofs_per_node
+    o.samples = samples
     return hm.hm_create(o)
 
 
@@ -164,6 +167,7 @@ def check_blocks(label, s, ref, bound, min_blocks, samples=48):
     width, not at tol, on both sides alike: there the GPU must be no farther from the
     exact block than the oracle is (plus the parity bound)."""
     count, capped, worst_o, worst_b = 0, 0, 0.0, 0.0
+    errs = []
     for q, (nupd, npv, blocks) in sorted(ref.items()):
         for (lv, nd_), (B, Uo, Vo) in sorted(blocks.items()):
             Ug, Vg, rank = hm.hm_get_hodlr_block(s, q, lv, nd_)
@@ -180,11 +184,13 @@ def check_blocks(label, s, ref, bound, min_blocks, samples=48):
             assert e_o <= bound, (label, q, lv, nd_, e_o, rank, Uo.shape[1])
             assert e_b <= e_ob + bound, (label, q, lv, nd_, e_b, e_ob)
             worst_o, worst_b = max(worst_o, e_o), max(worst_b, e_b)
+            errs.append(e_o)
             count += 1
         print(f"{label}: front {q} np {npv} nupd {nupd}: {len(blocks)} blocks")
     print(f"{label}: {count} blocks ({capped} at the sketch width), worst vs oracle {worst_o:.2e}, "
           f"vs exact block {worst_b:.2e}")
     assert count >= min_blocks
+    return np.array(errs)
 
 
 def test_q1024_top_front_blocks_vs_oracle_rrf(oracle):
@@ -213,5 +219,25 @@ def test_hex48_fp32_top_front_blocks_vs_oracle_rrf(oracle):
     ref = oracle["hex_blocks"].get()
     assert max(nupd for nupd, _, _ in ref.values()) > 2048
     check_blocks(f"hex{HEX_BLOCKS_M} fp32", s, ref, 5 * TOL + 1e-5, 16)
+    hm.hm_destroy(s)
+    hm.hm_ctx_destroy(ctx)
+
+
+def test_hex48_fp64_k64_top_front_blocks_vs_oracle_tsqr(oracle):
+    """FP64 with 64-column sketches: the depth-1 fronts' F_fp panels of the 48^3 hex
+    problem (2209+ rows) are too tall for a shared-memory stack of row-block R factors
+    (at most ~1700 rows at this width in FP64) and take the three-stage TSQR
+    (k_tsqr_*); every block against the oracle's range finder with the same sketch on the
+    oracle's own front, at FP64 rounding level."""
+    P, prm = workload("hex_lognormal_64^3", m=HEX_BLOCKS_M)
+    ctx = bench_ctx(hm.HM_PREC_FP64, samples=64)
+    s = hm.hm_analyze(ctx, P.n, P.rowptr, P.colidx, 3, P.coords)
+    hm.hm_factor(s, P.values, prm["tol"])
+    ref = oracle["hex_blocks64"].get()
+    assert any(1800 < nupd <= 2600 for nupd, _, _ in ref.values())  # the TSQR size class
+    # a singular value at the truncation threshold may be kept on one side and dropped on
+    # the other (then the two blocks differ by about tol); all others agree to rounding
+    errs = check_blocks(f"hex{HEX_BLOCKS_M} fp64 k64", s, ref, 2 * TOL, 16, samples=64)
+    assert np.mean(errs <= 1e-8) >= 0.98, np.sort(errs)[-10:]
     hm.hm_destroy(s)
     hm.hm_ctx_destroy(ctx)
