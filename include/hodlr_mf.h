@@ -371,24 +371,29 @@ const char* hm_last_error(void);
 
 /*
  * Serving (many matrices, requests arriving over time).  A server owns nworkers worker
- * threads, each with its own context (stream, memory pool and hbm_budget / nworkers of
- * the budget in *opts; opts->stream is ignored).  Registered matrices (host copies of
- * the CSR, FP64 values and lattice coordinates) are analysed + factored on their first
- * request by the worker that takes it, and the factorization stays resident in that
- * worker's context until evicted (least recently used first) to admit another matrix
- * within the budget.  Admission is by estimate, before the work allocates: a matrix's
- * estimate is its footprint when last resident (plus an eighth), else the bytes per
- * nonzero of the largest matrix of its dimension seen so far; a session's is its slots times
- * (2 restart + 10) FP64 vectors (plus a quarter and 4 MiB); the worker evicts until its
- * bytes plus the estimate fit.  A shortfall of the
- * estimate is caught by the budget check of the allocation itself (one more eviction
- * and a retry, counted in oom_retries).  Requests wait in one queue; a free worker takes the oldest one
- * whose matrix no other worker is serving (and that is resident on it or nowhere) and
- * runs a GMRES session on the matrix: a fixed number of right-hand-side slots (twice the
- * starting columns, at most max_batch_rhs, within a quarter of the worker's budget for
- * the GMRES workspace), every waiting request for the matrix that fits put in; after
- * every restart cycle the requests whose columns all converged leave with their answers
- * and requests that arrived meanwhile take the free slots (continuous batching).  Each
+ * threads, each with its own context (stream; opts->stream is ignored); the contexts
+ * share one stream-ordered memory pool and the one budget opts->hbm_budget, so a single
+ * matrix may use all of it.  Registered matrices (host copies of the CSR, FP64 values
+ * and lattice coordinates) are analysed + factored on their first request by the worker
+ * that takes it, and the factorization stays resident until evicted (least recently used
+ * first, among the systems no worker holds, whichever worker holds them) to admit other
+ * work within the budget.  Admission is by estimate, before the work allocates: a
+ * matrix's estimate is its footprint when last resident (plus an eighth), else the bytes
+ * per nonzero of the largest matrix of its dimension seen so far; a session's is its
+ * slots times (2 restart + 10) FP64 vectors (plus a quarter and 4 MiB); the worker evicts
+ * until the bytes held plus the estimate fit.  A shortfall of the estimate is caught by
+ * the budget check of the allocation itself (one more eviction and a retry, counted in
+ * oom_retries); with nothing left to evict while other workers run sessions, the worker
+ * waits for one of them to end (memory_waits; meanwhile sessions take no new requests),
+ * and the request fails with HM_ERR_OUT_OF_MEMORY only when it does not fit with no other
+ * session running.  Requests wait in one queue; a free worker takes the oldest one whose
+ * matrix no worker holds (one resident on another, idle worker is left to that worker;
+ * one resident on a busy worker moves to the taker's context, counted in moved) and runs
+ * a GMRES session on the matrix: a fixed number of right-hand-side slots (twice the
+ * starting columns, at most max_batch_rhs, within a quarter of budget / nworkers for the
+ * GMRES workspace), every waiting request for the matrix that fits put in; after every
+ * restart cycle the requests whose columns all converged leave with their answers and
+ * requests that arrived meanwhile take the free slots (continuous batching).  Each
  * right-hand side is its own GMRES instance with its own restart boundaries, so a
  * request's answer equals (to rounding) the answer it gets alone.  Workers run
  * concurrently, so different matrices overlap on the GPU.  Latency = completion -
@@ -411,7 +416,10 @@ typedef struct hm_server_stats {
   double device_bytes;           /* device memory held by the workers' contexts         */
   int64_t joined;                /* requests that entered a session already running     */
   int64_t oom_retries;           /* budget misses the admission estimate did not foresee
-                                    (the step was retried after one more eviction)      */
+                                    (the step was retried after one more eviction, or
+                                    after another worker's session ended)               */
+  int64_t moved;                 /* resident systems moved to another worker's context  */
+  int64_t memory_waits;          /* waits for another worker's session to end, for room */
 } hm_server_stats;
 
 int hm_server_create(const hm_opts* opts, int32_t nworkers, int32_t max_batch_rhs, hm_server_t* out);

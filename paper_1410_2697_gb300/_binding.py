@@ -66,7 +66,8 @@ class HmServerStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("batches", C.c_int64),
                 ("batched_rhs", C.c_int64), ("factorizations", C.c_int64), ("evictions", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("device_bytes", C.c_double),
-                ("joined", C.c_int64), ("oom_retries", C.c_int64)]
+                ("joined", C.c_int64), ("oom_retries", C.c_int64),
+                ("moved", C.c_int64), ("memory_waits", C.c_int64)]
 
 
 class HmProfEntry(C.Structure):

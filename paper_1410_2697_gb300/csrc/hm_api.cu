@@ -36,9 +36,20 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+std::unique_lock<std::mutex> alloc_lock(const hm_ctx_s* ctx) {
+  return ctx->shared ? std::unique_lock<std::mutex>(ctx->shared->mu) : std::unique_lock<std::mutex>();
+}
+
 int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t bytes) {
   *p = nullptr;
   bytes = std::max<size_t>(bytes, 16);
+  auto lk = alloc_lock(ctx);
+  SharedBudget* sb = ctx->shared;
+  if (sb && sb->limit && sb->used + bytes > sb->limit) {
+    set_last_error("shared HBM budget exceeded: " + std::to_string(sb->used + bytes) + " > " +
+                   std::to_string(sb->limit));
+    return HM_ERR_OUT_OF_MEMORY;
+  }
   if (ctx->opts.hbm_budget && ctx->allocated + bytes > ctx->opts.hbm_budget) {
     set_last_error("HBM budget exceeded: " + std::to_string(ctx->allocated + bytes) + " > " +
                    std::to_string(ctx->opts.hbm_budget));
@@ -52,6 +63,7 @@ int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t byt
     return HM_ERR_OUT_OF_MEMORY;
   }
   ctx->allocated += bytes;
+  if (sb) sb->used += bytes;
   owner->push_back(*p);
   // remember the size for the budget through a side table
   ctx->allocs.push_back((void*)(uintptr_t)bytes);
@@ -60,10 +72,13 @@ int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t byt
 }
 
 void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner) {
+  auto lk = alloc_lock(ctx);
   for (void* p : *owner) {
     for (size_t i = 0; i + 1 < ctx->allocs.size(); i += 2) {
       if (ctx->allocs[i + 1] == p) {
-        ctx->allocated -= (size_t)(uintptr_t)ctx->allocs[i];
+        const size_t b = (size_t)(uintptr_t)ctx->allocs[i];
+        ctx->allocated -= b;
+        if (ctx->shared) ctx->shared->used -= b;
         ctx->allocs.erase(ctx->allocs.begin() + i, ctx->allocs.begin() + i + 2);
         break;
       }
@@ -73,10 +88,41 @@ void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner) {
   owner->clear();
 }
 
+// Moves an idle system to another context that shares its memory pool and budget: the
+// system's transient solve state (apply plans, GMRES workspace) is freed, its stream is
+// drained, and the records of its allocations move to `to`, whose stream then runs its
+// work and, later, its frees.  The caller guarantees that no thread uses the system.
+int move_sys(hm_sys_s* sys, hm_ctx_s* to) {
+  hm_ctx_s* from = sys->ctx;
+  if (from == to) return HM_OK;
+  if (!from->shared || from->shared != to->shared || from->pool != to->pool) {
+    set_last_error("move_sys: the contexts do not share a memory pool and budget");
+    return HM_ERR_INVALID_ARG;
+  }
+  release_solve_state(sys);
+  HM_CUDA(cudaStreamSynchronize(from->stream));
+  auto lk = alloc_lock(from);
+  for (const std::vector<void*>* owner : {&sys->allocs, &sys->plan_allocs})
+    for (void* p : *owner)
+      for (size_t i = 0; i + 1 < from->allocs.size(); i += 2) {
+        if (from->allocs[i + 1] != p) continue;
+        const size_t b = (size_t)(uintptr_t)from->allocs[i];
+        from->allocated -= b;
+        from->allocs.erase(from->allocs.begin() + i, from->allocs.begin() + i + 2);
+        to->allocated += b;
+        to->allocs.push_back((void*)(uintptr_t)b);
+        to->allocs.push_back(p);
+        break;
+      }
+  sys->ctx = to;
+  return HM_OK;
+}
+
 int dev_alloc(hm_sys_s* sys, void** p, size_t bytes) { return dev_alloc_ctx(sys->ctx, &sys->allocs, p, bytes); }
 
 // Bytes of the allocations in `owner` (sizes from the context's side table).
 static double owned_bytes(const hm_ctx_s* ctx, const std::vector<void*>& owner) {
+  auto lk = alloc_lock(ctx);
   std::unordered_map<const void*, size_t> size;
   for (size_t i = 0; i + 1 < ctx->allocs.size(); i += 2) size[ctx->allocs[i + 1]] = (size_t)(uintptr_t)ctx->allocs[i];
   double b = 0;
@@ -85,6 +131,13 @@ static double owned_bytes(const hm_ctx_s* ctx, const std::vector<void*>& owner) 
     if (it != size.end()) b += (double)it->second;
   }
   return b;
+}
+
+size_t sys_bytes(const hm_sys_s* sys) {
+  double b = owned_bytes(sys->ctx, sys->allocs) + owned_bytes(sys->ctx, sys->plan_allocs) +
+             owned_bytes(sys->ctx, sys->gm.allocs);
+  for (const auto& kv : sys->solve_plans) b += owned_bytes(sys->ctx, kv.second->allocs);
+  return (size_t)b;
 }
 
 int copy_in(hm_sys_s* sys, void* dst, const void* src, size_t bytes) {
@@ -355,7 +408,7 @@ int hm_ctx_destroy(hm_ctx_t ctx) {
   for (auto& r : ctx->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto& e : ctx->prof.pool) cudaEventDestroy(e);
   for (auto& e : ctx->tune.pool) cudaEventDestroy(e);
-  if (ctx->pool) {
+  if (ctx->pool && ctx->own_pool) {
     cudaStreamSynchronize(ctx->stream);
     cudaMemPoolDestroy(ctx->pool);
   }

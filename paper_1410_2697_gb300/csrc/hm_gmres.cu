@@ -986,7 +986,7 @@ static int session_cycle_t(hm_sys_s* sys, int* its) {
   int budget = 0;
   bool any = false;
   for (int k = 0; k < nslots; ++k)
-    if (G.on[k] && G.relres[k] > G.rtol[k] && G.iters[k] < G.cap[k]) {
+    if (G.on[k] && !(G.relres[k] <= G.rtol[k]) && G.iters[k] < G.cap[k]) {  // NaN: runs to its cap
       active[k] = 1;
       any = true;
       rtol = std::min(rtol, G.rtol[k]);

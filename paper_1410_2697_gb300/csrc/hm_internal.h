@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -475,6 +476,15 @@ struct DevArena {
   std::vector<void*> ptrs;
 };
 
+// A device-memory budget shared by several contexts (the serving workers, which also
+// share one memory pool): every allocation and free of a context that points here, and
+// every read or move of its allocation records, holds `mu`.
+struct SharedBudget {
+  std::mutex mu;
+  size_t limit = 0;  // bytes the contexts may hold together; 0 = no limit
+  size_t used = 0;   // bytes they hold now
+};
+
 }  // namespace hm
 
 struct hm_ctx_s {
@@ -488,7 +498,9 @@ struct hm_ctx_s {
   int last_nrhs = 0;             // right-hand-side count of the most recent apply plan
   hm::Tuner tune;
   cudaMemPool_t pool = nullptr;  // stream-ordered pool; freed memory is kept for reuse
-  std::vector<void*> allocs;
+  bool own_pool = true;          // false: the pool belongs to another context
+  hm::SharedBudget* shared = nullptr;  // budget shared with other contexts, or null
+  std::vector<void*> allocs;     // (bytes, pointer) pairs of the live allocations
   void* noalloc_scratch = nullptr;  // device address of the allocation-free apply's array
   // adaptive rank: sketch width per front level learned for an analysis (key: its shape
   // signature), so a later analysis of the same pattern starts from the grown widths
@@ -644,6 +656,9 @@ struct TuneScope {
 int dev_alloc(hm_sys_s* sys, void** p, size_t bytes);
 int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t bytes);
 void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner);
+std::unique_lock<std::mutex> alloc_lock(const hm_ctx_s* ctx);
+int move_sys(hm_sys_s* sys, hm_ctx_s* to);
+size_t sys_bytes(const hm_sys_s* sys);  // device bytes a system holds (all its owners)
 int check_device_error(hm_sys_s* sys, const char* where);
 bool is_device_ptr(const void* p);
 int copy_in(hm_sys_s* sys, void* dst, const void* src, size_t bytes);

@@ -3,27 +3,34 @@
 // together and lets new ones join a running solve (continuous batching), admits work by
 // an HBM budget, and overlaps the work of different matrices on the device.
 //
-// Design.  The server owns W worker threads, each with its own context (CUDA stream and
-// stream-ordered memory pool, budget = total budget / W).  Requests wait in one queue.
-// A free worker takes the oldest waiting request whose matrix no other worker is
-// serving; a matrix that is not resident is bound to the worker that takes it (analyse +
-// factor: a miss) and stays resident in that worker's context until evicted.  The worker
-// then runs a GMRES session over a fixed number of slots (right-hand-side columns, each
-// its own GMRES instance): every waiting request for the matrix that fits the free slots
-// is put in, and after each restart cycle the converged requests leave (their answers
-// are returned at once) and newly arrived requests for the matrix take the free slots.
-// A request therefore never waits for a running solve of its matrix to finish, and its
-// answer is the one it gets alone (each column has its own Krylov space and its own
-// restart boundaries).  Workers run concurrently, so solves of different matrices
-// overlap on the GPU.  Admission by estimate: before a matrix is analysed and factored
-// (and before a session's GMRES workspace is allocated), the worker destroys its least
-// recently used idle resident systems until its context's bytes plus the estimate fit its
-// budget.  The estimate of a matrix is the footprint it had when last resident (plus an
-// eighth), else the bytes per nonzero of the largest matrix of its dimension seen so far
-// (a fixed per-nonzero figure before any); a session's is its slots times the GMRES and
-// apply vectors per column (plus a quarter and 4 MiB).  Should the estimate fall short, the allocation that exceeds the budget fails
-// and the step is retried after one more eviction (counted as oom_retries); a matrix that
-// does not fit alone fails with HM_ERR_OUT_OF_MEMORY.
+// Design.  The server owns W worker threads, each with its own context (CUDA stream);
+// the contexts share one stream-ordered memory pool and one HBM budget, so memory one
+// worker frees is the next one's to use, and a matrix may take the whole budget.
+// Requests wait in one queue.  A free worker takes the oldest waiting request whose
+// matrix no worker holds (a matrix resident on another worker that is idle is left to
+// that worker, which keeps the matrix's solve state).  A matrix that is not resident is
+// analysed and factored by the worker that takes it (a miss); one that is resident on
+// another worker moves to the taker's context (its solve state is dropped, its
+// factorization stays where it is in the pool).  The worker then runs a GMRES session
+// over a fixed number of slots (right-hand-side columns, each its own GMRES instance):
+// every waiting request for the matrix that fits the free slots is put in, and after
+// each restart cycle the converged requests leave (their answers are returned at once)
+// and newly arrived requests for the matrix take the free slots.  A request therefore
+// never waits for a running solve of its matrix to finish, and its answer is the one it
+// gets alone (each column has its own Krylov space and its own restart boundaries).
+// Workers run concurrently, so solves of different matrices overlap on the GPU.
+// Admission by estimate: before a matrix is analysed and factored (and before a
+// session's GMRES workspace is allocated), the worker destroys the least recently used
+// resident systems that no worker holds (of any worker) until the bytes held plus the
+// estimate fit the budget.  The estimate of a matrix is the footprint it had when last
+// resident (plus an eighth), else the bytes per nonzero of the largest matrix of its
+// dimension seen so far (a fixed per-nonzero figure before any); a session's is its
+// slots times the GMRES and apply vectors per column (plus a quarter and 4 MiB).  Should
+// the estimate fall short, the allocation that exceeds the budget fails and the step is
+// retried after one more eviction (counted as oom_retries).  With nothing left to evict
+// while other workers run sessions, the worker waits for one of them to end (meanwhile
+// running sessions take no new requests, so they end); a matrix that does not fit with
+// every other session gone fails with HM_ERR_OUT_OF_MEMORY.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -42,7 +49,7 @@ using Clock = std::chrono::steady_clock;
 struct SrvMatrix {
   int n = 0, dim = 0;
   int worker = -1;              // worker whose context holds the resident system (-1: none)
-  int serving = -1;             // worker running a session on it now (-1: none)
+  int serving = -1;             // worker holding it now: session, move, eviction or release
   double tol = 0;
   std::vector<int64_t> rowptr;
   std::vector<int32_t> colidx, coords;
@@ -51,7 +58,7 @@ struct SrvMatrix {
   size_t bytes = 0;             // device bytes while resident
   size_t bytes_seen = 0;        // footprint when last resident (0: never)
   int64_t nnz = 0;
-  int64_t last_use = 0;         // worker-local use counter (LRU)
+  int64_t last_use = 0;         // server-wide use counter (LRU)
 };
 
 struct SrvRequest {
@@ -70,8 +77,8 @@ struct SrvRequest {
 struct SrvWorker {
   hm_ctx_t ctx = nullptr;
   std::thread th;
-  int64_t clock = 0;
-  SrvMatrix* last = nullptr;  // matrix of the previous session
+  bool busy = false;          // between taking a request and the end of its session
+  SrvMatrix* last = nullptr;  // matrix whose solve state this worker keeps (its last session)
 };
 
 }  // namespace hm
@@ -89,34 +96,61 @@ struct hm_server_s {
   int64_t completed = 0, failed = 0, batches = 0, batched_rhs = 0, factorizations = 0, evictions = 0;
   int64_t joined = 0;  // requests that entered a running session
   int64_t oom_retries = 0;  // budget misses the estimate did not foresee
+  int64_t moved = 0;        // resident systems moved to another worker's context
+  int64_t memory_waits = 0; // waits for another worker's session to end, for memory
+  int64_t clock = 0;        // use counter (LRU)
+  int in_session = 0;       // workers inside a GMRES session
+  int mem_waiters = 0;      // workers waiting for memory (sessions take no joiners then)
+  int64_t sessions_ended = 0;
+  hm::SharedBudget budget;  // shared by the workers' contexts (one memory pool)
 };
 
 namespace hm {
 
-static size_t ctx_bytes(hm_ctx_t ctx) { return ctx->allocated; }
+// Device bytes the workers hold together.
+static size_t held_bytes(hm_server_s* S) {
+  std::lock_guard<std::mutex> lk(S->budget.mu);
+  return S->budget.used;
+}
 
-// Destroys the least recently used resident system of worker w (not `keep`); false if
-// there is none.  Only worker w creates or destroys its systems.
+// Destroys the least recently used resident system that no worker holds (any worker's;
+// not matrix `keep`); false if there is none.  The caller (worker w) holds no lock.
 static bool evict_one(hm_server_s* S, int w, int keep) {
   SrvMatrix* victim = nullptr;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     for (int m = 0; m < (int)S->matrices.size(); ++m) {
       SrvMatrix* M = S->matrices[m].get();
-      if (M->worker != w || !M->sys || m == keep || M->serving >= 0) continue;
+      if (M->serving >= 0 || !M->sys || m == keep) continue;
       if (!victim || M->last_use < victim->last_use) victim = M;
     }
     if (!victim) return false;
+    victim->serving = w;  // held while it is destroyed
+    if (S->workers[victim->worker].last == victim) S->workers[victim->worker].last = nullptr;
     S->evictions++;
   }
-  hm_destroy(victim->sys);
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    victim->sys = nullptr;
-    victim->bytes = 0;
-    victim->worker = -1;
-  }
-  if (S->workers[w].last == victim) S->workers[w].last = nullptr;
+  hm_destroy(victim->sys);  // drains the owner's stream, frees into the shared pool
+  std::lock_guard<std::mutex> lk(S->mu);
+  victim->sys = nullptr;
+  victim->bytes = 0;
+  victim->worker = -1;
+  victim->serving = -1;
+  S->cv_work.notify_all();  // requests for it may be taken again
+  return true;
+}
+
+// After an allocation failed with nothing left to evict: waits until a session of
+// another worker ends and returns true, or returns false at once when no other worker
+// is in a session (then the work does not fit the budget).  While a worker waits,
+// running sessions take no new requests, so they end.
+static bool wait_for_memory(hm_server_s* S) {
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->in_session == 0) return false;
+  const int64_t ended = S->sessions_ended;
+  S->mem_waiters++;
+  S->memory_waits++;
+  S->cv_done.wait(lk, [&] { return S->sessions_ended != ended; });
+  S->mem_waiters--;
   return true;
 }
 
@@ -136,13 +170,25 @@ static size_t estimate_bytes(hm_server_s* S, const SrvMatrix& M) {
   return (size_t)(per_nnz * (double)M.nnz);
 }
 
-// Evicts worker w's least recently used idle systems (not m) until `need` more bytes fit
-// its budget (or nothing is left to evict).
+// Evicts least recently used idle systems (not m) until `need` more bytes fit the
+// budget (or nothing is left to evict).
 static void admit(hm_server_s* S, int w, int m, size_t need) {
-  hm_ctx_t ctx = S->workers[w].ctx;
-  const size_t budget = ctx->opts.hbm_budget;
+  const size_t budget = S->budget.limit;
   if (!budget) return;
-  while (ctx_bytes(ctx) + need > budget && evict_one(S, w, m)) {
+  while (held_bytes(S) + need > budget && evict_one(S, w, m)) {
+  }
+}
+
+// Retries `step` (an allocating step of worker w for matrix m) after one more eviction,
+// or after another worker's session ended, while it fails for lack of memory.
+template <class F>
+static int with_memory(hm_server_s* S, int w, int m, F step) {
+  for (;;) {
+    const int st = step();
+    if (st != HM_ERR_OUT_OF_MEMORY) return st;
+    if (!evict_one(S, w, m) && !wait_for_memory(S)) return st;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->oom_retries++;
   }
 }
 
@@ -151,28 +197,24 @@ static int make_resident(hm_server_s* S, int w, int m, SrvMatrix& M) {
   if (M.sys) return HM_OK;
   hm_ctx_t ctx = S->workers[w].ctx;
   admit(S, w, m, estimate_bytes(S, M));
-  for (;;) {
-    const size_t before = ctx_bytes(ctx);
+  return with_memory(S, w, m, [&]() -> int {
     hm_sys_t sys = nullptr;
+    hm_factor_info fi;
     int st = hm_analyze(ctx, M.n, M.rowptr.data(), M.colidx.data(), M.dim, M.coords.data(), nullptr, 0,
                         nullptr, nullptr, &sys);
     if (st == HM_OK) {
-      hm_factor_info fi;
       st = hm_factor(sys, M.values.data(), M.tol, &fi);
       if (st != HM_OK) hm_destroy(sys);
     }
-    if (st == HM_OK) {
-      M.sys = sys;
-      M.bytes = ctx_bytes(ctx) - before;
-      std::lock_guard<std::mutex> lk(S->mu);
-      M.bytes_seen = M.bytes;
-      S->factorizations++;
-      return HM_OK;
-    }
-    if (st != HM_ERR_OUT_OF_MEMORY || !evict_one(S, w, m)) return st;
+    if (st != HM_OK) return st;
+    const size_t bytes = sys_bytes(sys);
     std::lock_guard<std::mutex> lk(S->mu);
-    S->oom_retries++;
-  }
+    M.sys = sys;
+    M.bytes = bytes;
+    M.bytes_seen = M.bytes;
+    S->factorizations++;
+    return HM_OK;
+  });
 }
 
 // Completes request r (status st; x already written) under the server lock.
@@ -207,34 +249,34 @@ static void take_requests(hm_server_s* S, int m, int free_slots, std::vector<Srv
 
 // A GMRES session on matrix M: requests join at restart boundaries, leave when done.
 // Every request the session takes is appended to `owned`: the caller fails those still
-// open if the session returns an error.
-static int run_session(hm_server_s* S, int w, int m, SrvMatrix& M, std::vector<SrvRequest*>& owned) {
+// open if the session returns an error.  `entered` is set once the session counts in
+// in_session; the caller ends it there after releasing the matrix.
+static int run_session(hm_server_s* S, int w, int m, SrvMatrix& M, std::vector<SrvRequest*>& owned,
+                       bool* entered) {
   const std::vector<SrvRequest*> first = owned;
   int rhs0 = 0;
   for (SrvRequest* r : first) rhs0 += r->nrhs;
   // slots: room for about as many joiners as the session starts with, within the GMRES
-  // workspace a quarter of the worker's budget allows ((2 restart + 6) FP64 vectors each)
+  // workspace a quarter of a worker's share of the budget allows ((2 restart + 6) FP64
+  // vectors each)
   int slots = 1;
   while (slots < std::min(2 * rhs0, S->max_batch_rhs)) slots *= 2;
   slots = std::min(slots, S->max_batch_rhs);
   const hm_opts& o = S->workers[w].ctx->opts;
-  if (o.hbm_budget) {
+  if (S->budget.limit) {
     const double per_col = (2.0 * o.restart + 6.0) * 8.0 * (double)M.n;
     slots = std::max(rhs0 > 0 ? std::min(rhs0, S->max_batch_rhs) : 1,
-                     std::min(slots, (int)(0.25 * (double)o.hbm_budget / per_col)));
+                     std::min(slots, (int)(0.25 * (double)S->budget.limit / S->workers.size() / per_col)));
   }
   // the session's GMRES workspace (V, Z and the work vectors of every slot) and its apply
   // buffers, admitted by estimate (with a quarter and 4 MiB to spare) before allocation
   admit(S, w, m, (size_t)(1.25 * ((2.0 * o.restart + 10.0) * 8.0 * (double)M.n * slots) + (4u << 20)));
-  int st = gm_session_begin(M.sys, slots);
-  while (st == HM_ERR_OUT_OF_MEMORY && evict_one(S, w, m)) {
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      S->oom_retries++;
-    }
-    st = gm_session_begin(M.sys, slots);
+  HM_TRY(with_memory(S, w, m, [&] { return gm_session_begin(M.sys, slots); }));
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->in_session++;  // until the worker releases the matrix (workers short of memory wait)
+    *entered = true;
   }
-  if (st != HM_OK) return st;
   struct Live { SrvRequest* r; int slot0; };
   std::vector<Live> live;
   std::vector<char> used(slots, 0);
@@ -299,7 +341,7 @@ static int run_session(hm_server_s* S, int w, int m, SrvMatrix& M, std::vector<S
       if (!done.empty()) S->cv_done.notify_all();
       int free_slots = 0;
       for (int k = 0; k < slots; ++k) free_slots += used[k] ? 0 : 1;
-      take_requests(S, m, free_slots, &joiners);
+      if (S->mem_waiters == 0) take_requests(S, m, free_slots, &joiners);  // else: end soon
       owned.insert(owned.end(), joiners.begin(), joiners.end());
       S->joined += (int64_t)joiners.size();
       int add = 0;
@@ -319,7 +361,8 @@ static int run_session(hm_server_s* S, int w, int m, SrvMatrix& M, std::vector<S
         return ps;
       }
     }
-    M.last_use = ++S->workers[w].clock;
+    std::lock_guard<std::mutex> lk(S->mu);
+    M.last_use = ++S->clock;
   }
   return HM_OK;
 }
@@ -329,50 +372,93 @@ static void worker_loop(hm_server_s* S, int w) {
   cudaSetDevice(W.ctx->opts.device);
   for (;;) {
     std::vector<SrvRequest*> batch;
-    int m = -1;
+    int m = -1, from = -1;
     SrvMatrix* Mp = nullptr;
+    SrvMatrix* rel = nullptr;  // previous matrix whose solve state is released here
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      // the oldest request whose matrix nobody serves and that is resident here or nowhere
+      // the oldest request whose matrix no worker holds, unless it is resident on another
+      // worker that is idle (that worker takes it and keeps its solve state)
       int first_nrhs = 0;
       auto pick = [&]() -> bool {
         for (SrvRequest* r : S->q) {
           SrvMatrix* M = S->matrices[r->matrix].get();
-          if (M->serving < 0 && (M->worker < 0 || M->worker == w)) {
-            m = r->matrix;
-            Mp = M;
-            first_nrhs = r->nrhs;
-            return true;
-          }
+          if (M->serving >= 0) continue;
+          if (M->worker >= 0 && M->worker != w && !S->workers[M->worker].busy) continue;
+          m = r->matrix;
+          Mp = M;
+          first_nrhs = r->nrhs;
+          return true;
         }
         return false;
       };
       S->cv_work.wait(lk, [&] { return S->stop || pick(); });
       if (!Mp) return;  // stopping, and nothing this worker can take
       Mp->serving = w;
-      Mp->worker = w;
-      // the session's starting columns: within a quarter of the worker's budget for the
-      // GMRES workspace (the oldest request always fits)
+      W.busy = true;
+      S->cv_work.notify_all();  // requests left to this worker while it was idle are free now
+      from = Mp->sys ? Mp->worker : -1;
+      if (from >= 0 && from != w && S->workers[from].last == Mp) S->workers[from].last = nullptr;
+      if (W.last && W.last != Mp) {
+        // one system's transient solve state (apply plans, GMRES workspace) per worker;
+        // a previous matrix held by another worker is that worker's to release
+        if (W.last->sys && W.last->serving < 0 && W.last->worker == w) {
+          rel = W.last;
+          rel->serving = w;
+        }
+        W.last = nullptr;
+      }
+      // the session's starting columns: within a quarter of a worker's share of the
+      // budget for the GMRES workspace (the oldest request always fits)
       int cap = S->max_batch_rhs;
       const hm_opts& o = W.ctx->opts;
-      if (o.hbm_budget) {
+      if (S->budget.limit) {
         const double per_col = (2.0 * o.restart + 6.0) * 8.0 * (double)Mp->n;
-        cap = std::max(first_nrhs, std::min(cap, (int)(0.25 * (double)o.hbm_budget / per_col)));
+        cap = std::max(first_nrhs,
+                       std::min(cap, (int)(0.25 * (double)S->budget.limit / S->workers.size() / per_col)));
       }
       take_requests(S, m, cap, &batch);
     }
+    if (rel) {
+      release_solve_state(rel->sys);
+      std::lock_guard<std::mutex> lk(S->mu);
+      rel->serving = -1;
+      S->cv_work.notify_all();
+    }
     SrvMatrix& M = *Mp;
-    // one system's transient solve state (apply plans, GMRES workspace) per worker
-    if (W.last && W.last != Mp && W.last->sys) release_solve_state(W.last->sys);
-    W.last = Mp;
-    int st = make_resident(S, w, m, M);
+    int st = HM_OK;
+    bool entered = false;
+    if (from >= 0 && from != w) {  // resident on another worker: move it here
+      st = move_sys(M.sys, W.ctx);
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (st == HM_OK) {
+        M.worker = w;
+        S->moved++;
+      }
+    }
     if (st == HM_OK) {
-      M.last_use = ++W.clock;
-      st = run_session(S, w, m, M, batch);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (!M.sys) M.worker = w;
+      }
+      st = make_resident(S, w, m, M);
+    }
+    if (st == HM_OK) {
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        M.last_use = ++S->clock;
+      }
+      st = run_session(S, w, m, M, batch, &entered);
     }
     std::lock_guard<std::mutex> lk(S->mu);
     if (!M.sys) M.worker = -1;
+    if (M.sys && M.worker == w) W.last = Mp;
     M.serving = -1;
+    W.busy = false;
+    if (entered) {  // the matrix is evictable now: workers waiting for memory retry
+      S->in_session--;
+      S->sessions_ended++;
+    }
     for (SrvRequest* r : batch)  // requests still open after a failure fail with it
       if (!r->done) finish(S, r, st == HM_OK ? HM_ERR_CUDA : st, hm_solve_info{}, 0);
     S->cv_done.notify_all();
@@ -402,16 +488,24 @@ int hm_server_create(const hm_opts* opts, int32_t nworkers, int32_t max_batch_rh
   hm_opts o;
   if (opts) o = *opts; else hm_default_opts(&o);
   o.stream = nullptr;  // every worker owns its stream
-  if (o.hbm_budget) o.hbm_budget /= (size_t)nworkers;
   hm_server_s* S = new hm_server_s();
+  S->budget.limit = o.hbm_budget;  // one budget for all workers
+  o.hbm_budget = 0;
   S->max_batch_rhs = max_batch_rhs;
   S->workers.resize(nworkers);
   for (int w = 0; w < nworkers; ++w) {
     const int st = hm_create(&S->workers[w].ctx, &o);
     if (st != HM_OK) {
-      for (int v = 0; v < w; ++v) hm_ctx_destroy(S->workers[v].ctx);
+      for (int v = w - 1; v >= 0; --v) hm_ctx_destroy(S->workers[v].ctx);
       delete S;
       return st;
+    }
+    hm_ctx_s* ctx = S->workers[w].ctx;
+    ctx->shared = &S->budget;
+    if (w > 0) {  // the memory pool of worker 0 serves every worker
+      cudaMemPoolDestroy(ctx->pool);
+      ctx->pool = S->workers[0].ctx->pool;
+      ctx->own_pool = false;
     }
   }
   for (int w = 0; w < nworkers; ++w) S->workers[w].th = std::thread(worker_loop, S, w);
@@ -499,11 +593,11 @@ int hm_server_get_stats(hm_server_t S, hm_server_stats* st) {
   st->evictions = S->evictions;
   st->p50_ms = percentile(S->latency_ms, 0.50);
   st->p99_ms = percentile(S->latency_ms, 0.99);
-  size_t resident = 0;
-  for (auto& W : S->workers) resident += W.ctx->allocated;
-  st->device_bytes = (double)resident;
+  st->device_bytes = (double)held_bytes(S);
   st->joined = S->joined;
   st->oom_retries = S->oom_retries;
+  st->moved = S->moved;
+  st->memory_waits = S->memory_waits;
   return HM_OK;
 }
 
@@ -522,7 +616,7 @@ int hm_server_destroy(hm_server_t S) {
       cudaSetDevice(S->workers[M->worker].ctx->opts.device);
       hm_destroy(M->sys);
     }
-  for (auto& W : S->workers) hm_ctx_destroy(W.ctx);
+  for (int w = (int)S->workers.size() - 1; w >= 0; --w) hm_ctx_destroy(S->workers[w].ctx);  // pool owner last
   delete S;
   return HM_OK;
 }

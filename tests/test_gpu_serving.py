@@ -171,3 +171,95 @@ def test_request_joins_a_running_solve_and_matches_its_alone_result():
         assert np.linalg.norm(b_x - xa) / np.linalg.norm(xa) <= 1e-8
     finally:
         hm.hm_server_destroy(srv)
+
+
+def _footprint(p, nrhs=2):
+    """Device bytes one worker holds after serving one request of matrix p."""
+    probe = hm.hm_server_create(opts(), nworkers=1, max_batch_rhs=8)
+    try:
+        mid = hm.hm_server_add_matrix(probe, p, TOL)
+        b = np.asfortranarray(rhs_uniform(p.n, nrhs, 1))
+        x = np.zeros_like(b, order="F")
+        assert hm.hm_server_wait(probe, hm.hm_server_submit(probe, mid, b, x))["status"] == hm.abi.HM_OK
+        return hm.hm_server_get_stats(probe)["device_bytes"]
+    finally:
+        hm.hm_server_destroy(probe)
+
+
+def test_one_matrix_may_use_most_of_the_shared_budget():
+    """The workers share one budget and one memory pool: with 2 workers and a budget of
+    1.3 times one matrix's footprint, the matrix is served (a split of budget / workers
+    would refuse it), and the bytes held stay within the budget."""
+    p = matrices()[1]
+    one = _footprint(p)
+    budget = int(1.3 * one)
+    srv = hm.hm_server_create(opts(budget), nworkers=2, max_batch_rhs=8)
+    try:
+        mid = hm.hm_server_add_matrix(srv, p, TOL)
+        for k in range(3):
+            b = np.asfortranarray(rhs_uniform(p.n, 2, 20 + k))
+            x = np.zeros_like(b, order="F")
+            r = hm.hm_server_wait(srv, hm.hm_server_submit(srv, mid, b, x))
+            assert r["status"] == hm.abi.HM_OK
+            assert np.linalg.norm(b - p.scipy() @ x) / np.linalg.norm(b) <= 1e-9
+        st = hm.hm_server_get_stats(srv)
+        assert st["failed"] == 0 and st["factorizations"] == 1
+        assert st["device_bytes"] <= budget
+    finally:
+        hm.hm_server_destroy(srv)
+
+
+def test_resident_matrix_moves_to_a_free_worker():
+    """A matrix resident on a busy worker is served by the free one: its factorization
+    moves to the free worker's context (shared pool) instead of being factored again or
+    waiting.  Two long requests (relative tolerance 0: every column runs to the 4000
+    iteration cap and ends HM_ERR_NO_CONVERGENCE) keep the workers busy in a known order:
+    worker X takes A, worker Y factors B and then takes C; once A ends, X is free while
+    Y still runs C, and the next request for B moves B to X.  B's answer equals its
+    answer alone within 1e-8."""
+    import time
+    pa = q1_square(150, lognormal_coefficients(150 * 150, 1.0, seed=21))
+    pc = q1_square(170, lognormal_coefficients(170 * 170, 1.0, seed=22))
+    pb = matrices()[1]
+    loose = 3e-1  # poor preconditioners for the long requests
+    o = opts()
+    o.restart = 10
+    srv = hm.hm_server_create(o, nworkers=2, max_batch_rhs=8)
+    try:
+        ia = hm.hm_server_add_matrix(srv, pa, loose)
+        ib = hm.hm_server_add_matrix(srv, pb, TOL)
+        ic = hm.hm_server_add_matrix(srv, pc, loose)
+
+        def submit(mid, p, seed, rtol=1e-10, nrhs=1):
+            b = np.asfortranarray(rhs_uniform(p.n, nrhs, seed))
+            x = np.zeros_like(b, order="F")
+            return b, x, hm.hm_server_submit(srv, mid, b, x, rtol=rtol)
+
+        def wait_batches(k):
+            t0 = time.time()
+            while hm.hm_server_get_stats(srv)["batches"] < k and time.time() - t0 < 30:
+                time.sleep(0.0005)
+            assert hm.hm_server_get_stats(srv)["batches"] >= k
+
+        _, _, ra = submit(ia, pa, 1, rtol=0.0)          # X: A, runs to the cap
+        wait_batches(1)
+        b1, x1, rb1 = submit(ib, pb, 2)                 # Y: factor B, solve
+        assert hm.hm_server_wait(srv, rb1)["status"] == hm.abi.HM_OK
+        _, _, rc = submit(ic, pc, 3, rtol=0.0, nrhs=2)  # Y: C, runs to the cap (longer)
+        wait_batches(3)
+        res_a = hm.hm_server_wait(srv, ra)
+        assert res_a["status"] == hm.abi.HM_ERR_NO_CONVERGENCE and res_a["iters"] >= 4000
+        b2, x2, rb2 = submit(ib, pb, 4)                 # X is free, B lives on busy Y
+        res_b = hm.hm_server_wait(srv, rb2)
+        st = hm.hm_server_get_stats(srv)
+        res_c = hm.hm_server_wait(srv, rc)
+        assert res_b["status"] == hm.abi.HM_OK
+        assert res_c["status"] == hm.abi.HM_ERR_NO_CONVERGENCE
+        assert st["moved"] >= 1 and st["factorizations"] == 3, st
+        A = pb.scipy()
+        for b, x in ((b1, x1), (b2, x2)):
+            assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-10
+        xa = solve_alone(pb, b2)
+        assert np.linalg.norm(x2 - xa) / np.linalg.norm(xa) <= 1e-8
+    finally:
+        hm.hm_server_destroy(srv)
