@@ -719,7 +719,7 @@ def run_serving(args):
         o.adaptive_rank = 1 if args.adaptive_rank else 0
         srv = hm.hm_server_create(o, nworkers=nworkers, max_batch_rhs=64)
         ids = [hm.hm_server_add_matrix(srv, m, 1e-4) for m in mats]
-        lat, worst, fails = [], [0.0], [0]
+        lat, worst, fails, statuses = [], [0.0], [0], {}
         rids = []
         done = th.Event()
 
@@ -733,6 +733,7 @@ def run_serving(args):
                 r = hm.hm_server_wait(srv, rids[k])
                 if r["status"] != 0:
                     fails[0] += 1
+                    statuses[r["status"]] = statuses.get(r["status"], 0) + 1
                 lat.append(r["latency_ms"])
                 worst[0] = max(worst[0], r["relres"])
                 k += 1
@@ -752,9 +753,9 @@ def run_serving(args):
         elapsed = time.perf_counter() - t0
         st = hm.hm_server_get_stats(srv)
         hm.hm_server_destroy(srv)
-        return elapsed, st, lat, worst[0], fails[0]
+        return elapsed, st, lat, worst[0], (fails[0], statuses)
 
-    el, st, lat, worst, fails = serve(hm.HM_PREC_MIXED, args.serve_workers, trace, False)
+    el, st, lat, worst, (fails, fail_status) = serve(hm.HM_PREC_MIXED, args.serve_workers, trace, False)
     k = min(args.serve_seq, len(trace))
     pick = np.random.Generator(np.random.PCG64(8)).choice(len(trace), size=k, replace=False)
     el64, st64, lat64, _, _ = serve(hm.HM_PREC_FP64, 1, [trace[i] for i in sorted(pick)], True)
@@ -770,8 +771,10 @@ def run_serving(args):
                    "answers": "one reused host buffer per matrix; relres checked per request"},
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "rhs_per_s": rhs_total / el, "relres": worst,
         "failed_requests": fails,
+        "failed_status": {hm.hm_status_str(k): v for k, v in fail_status.items()},
         "server": {k2: st[k2] for k2 in ("completed", "failed", "batches", "batched_rhs", "joined",
-                                          "factorizations", "evictions", "oom_retries", "device_bytes")},
+                                          "factorizations", "evictions", "oom_retries", "moved", "memory_waits",
+                                          "device_bytes")},
         "saturated": len(trace) / el < 0.9 * args.serve_rate,
         "fp64_sequential": {"value": k / el64, "unit": "requests/s", "requests": k,
                             "sample": "requests drawn from the trace (seed 8), replayed one after another",

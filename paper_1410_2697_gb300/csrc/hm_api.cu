@@ -89,21 +89,23 @@ void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner) {
 }
 
 // Moves an idle system to another context that shares its memory pool and budget: the
-// system's transient solve state (apply plans, GMRES workspace) is freed, its stream is
-// drained, and the records of its allocations move to `to`, whose stream then runs its
-// work and, later, its frees.  The caller guarantees that no thread uses the system.
-int move_sys(hm_sys_s* sys, hm_ctx_s* to) {
+// records of all its allocations (factor, plan, apply plans, GMRES workspace) move to
+// `to`, whose stream runs the system's later work and frees.  `ready` (may be null) is
+// an event recorded on the old context's stream after the system's last work there; it
+// is waited for on the host, and nothing is enqueued on the old stream (its owner may
+// be capturing a graph on it).  The caller guarantees that no other thread uses the
+// system.
+int move_sys(hm_sys_s* sys, hm_ctx_s* to, cudaEvent_t ready) {
   hm_ctx_s* from = sys->ctx;
   if (from == to) return HM_OK;
   if (!from->shared || from->shared != to->shared || from->pool != to->pool) {
     set_last_error("move_sys: the contexts do not share a memory pool and budget");
     return HM_ERR_INVALID_ARG;
   }
-  release_solve_state(sys);
-  HM_CUDA(cudaStreamSynchronize(from->stream));
+  if (ready) HM_CUDA(cudaEventSynchronize(ready));
   auto lk = alloc_lock(from);
-  for (const std::vector<void*>* owner : {&sys->allocs, &sys->plan_allocs})
-    for (void* p : *owner)
+  auto move = [&](const std::vector<void*>& owner) {
+    for (void* p : owner)
       for (size_t i = 0; i + 1 < from->allocs.size(); i += 2) {
         if (from->allocs[i + 1] != p) continue;
         const size_t b = (size_t)(uintptr_t)from->allocs[i];
@@ -114,6 +116,11 @@ int move_sys(hm_sys_s* sys, hm_ctx_s* to) {
         to->allocs.push_back(p);
         break;
       }
+  };
+  move(sys->allocs);
+  move(sys->plan_allocs);
+  move(sys->gm.allocs);
+  for (const auto& kv : sys->solve_plans) move(kv.second->allocs);
   sys->ctx = to;
   return HM_OK;
 }

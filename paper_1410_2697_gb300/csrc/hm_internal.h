@@ -657,7 +657,7 @@ int dev_alloc(hm_sys_s* sys, void** p, size_t bytes);
 int dev_alloc_ctx(hm_ctx_s* ctx, std::vector<void*>* owner, void** p, size_t bytes);
 void dev_free_all(hm_ctx_s* ctx, std::vector<void*>* owner);
 std::unique_lock<std::mutex> alloc_lock(const hm_ctx_s* ctx);
-int move_sys(hm_sys_s* sys, hm_ctx_s* to);
+int move_sys(hm_sys_s* sys, hm_ctx_s* to, cudaEvent_t ready);
 size_t sys_bytes(const hm_sys_s* sys);  // device bytes a system holds (all its owners)
 int check_device_error(hm_sys_s* sys, const char* where);
 bool is_device_ptr(const void* p);

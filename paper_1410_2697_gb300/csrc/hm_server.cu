@@ -59,6 +59,7 @@ struct SrvMatrix {
   size_t bytes_seen = 0;        // footprint when last resident (0: never)
   int64_t nnz = 0;
   int64_t last_use = 0;         // server-wide use counter (LRU)
+  cudaEvent_t ready = nullptr;  // recorded on the holder's stream when it lets go of the system
 };
 
 struct SrvRequest {
@@ -129,7 +130,9 @@ static bool evict_one(hm_server_s* S, int w, int keep) {
     if (S->workers[victim->worker].last == victim) S->workers[victim->worker].last = nullptr;
     S->evictions++;
   }
-  hm_destroy(victim->sys);  // drains the owner's stream, frees into the shared pool
+  // the system moves to this worker first: its frees then run on this worker's own
+  // stream (another worker's stream may be capturing a graph)
+  if (move_sys(victim->sys, S->workers[w].ctx, victim->ready) == HM_OK) hm_destroy(victim->sys);
   std::lock_guard<std::mutex> lk(S->mu);
   victim->sys = nullptr;
   victim->bytes = 0;
@@ -429,7 +432,7 @@ static void worker_loop(hm_server_s* S, int w) {
     int st = HM_OK;
     bool entered = false;
     if (from >= 0 && from != w) {  // resident on another worker: move it here
-      st = move_sys(M.sys, W.ctx);
+      st = move_sys(M.sys, W.ctx, M.ready);
       std::lock_guard<std::mutex> lk(S->mu);
       if (st == HM_OK) {
         M.worker = w;
@@ -449,6 +452,10 @@ static void worker_loop(hm_server_s* S, int w) {
         M.last_use = ++S->clock;
       }
       st = run_session(S, w, m, M, batch, &entered);
+    }
+    if (M.sys) {  // marks the end of the system's work on this stream for a later mover
+      if (!M.ready) cudaEventCreateWithFlags(&M.ready, cudaEventDisableTiming);
+      if (M.ready) cudaEventRecord(M.ready, W.ctx->stream);
     }
     std::lock_guard<std::mutex> lk(S->mu);
     if (!M.sys) M.worker = -1;
@@ -611,11 +618,13 @@ int hm_server_destroy(hm_server_t S) {
   for (auto& W : S->workers)
     if (W.th.joinable()) W.th.join();
   // the worker threads are gone: free every resident system and context from here
-  for (auto& M : S->matrices)
+  for (auto& M : S->matrices) {
     if (M->sys && M->worker >= 0) {
       cudaSetDevice(S->workers[M->worker].ctx->opts.device);
       hm_destroy(M->sys);
     }
+    if (M->ready) cudaEventDestroy(M->ready);
+  }
   for (int w = (int)S->workers.size() - 1; w >= 0; --w) hm_ctx_destroy(S->workers[w].ctx);  // pool owner last
   delete S;
   return HM_OK;

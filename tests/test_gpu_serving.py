@@ -241,11 +241,13 @@ def test_resident_matrix_moves_to_a_free_worker():
                 time.sleep(0.0005)
             assert hm.hm_server_get_stats(srv)["batches"] >= k
 
-        _, _, ra = submit(ia, pa, 1, rtol=0.0)          # X: A, runs to the cap
+        # every b and x stays referenced until its request has been waited for: the
+        # server reads b and writes x from its worker threads
+        ba, xa_, ra = submit(ia, pa, 1, rtol=0.0)       # X: A, runs to the cap
         wait_batches(1)
         b1, x1, rb1 = submit(ib, pb, 2)                 # Y: factor B, solve
         assert hm.hm_server_wait(srv, rb1)["status"] == hm.abi.HM_OK
-        _, _, rc = submit(ic, pc, 3, rtol=0.0, nrhs=2)  # Y: C, runs to the cap (longer)
+        bc, xc, rc = submit(ic, pc, 3, rtol=0.0, nrhs=2)  # Y: C, runs to the cap (longer)
         wait_batches(3)
         res_a = hm.hm_server_wait(srv, ra)
         assert res_a["status"] == hm.abi.HM_ERR_NO_CONVERGENCE and res_a["iters"] >= 4000
