@@ -33,7 +33,7 @@ namespace hm {
 
 namespace {
 
-constexpr int kHaThreads = 256, kHaWarps = kHaThreads / 32;
+constexpr int kHaThreads = 256;  // threads per CTA (an autotuner variant takes 512)
 
 __device__ __forceinline__ int ilog2i(int v) { return 31 - __clz(v); }
 
@@ -85,11 +85,11 @@ __device__ __forceinline__ void warp_col_dot(const T* __restrict__ M, int cnt, c
 // Y[i * RP + r] += sign * sum_{c < ncols} M[i + c ld] * Tsrc(i)[c * RB + r] for the rows i
 // of [0, rows) (one row per thread; M's rows start at the CTA's first row; Tsrc(i) is
 // the coefficient block of row i's node).
-template <typename T, int RB, typename TSrc>
+template <typename T, int RB, int NT, typename TSrc>
 __device__ __forceinline__ void rows_update(const T* __restrict__ M, int64_t ld, int rows, int ncols, TSrc tsrc,
                                             T* __restrict__ Y, T sign) {
   constexpr int RP = RB + 1, U = 16;  // sixteen loads of M in flight per thread
-  for (int i = threadIdx.x; i < rows; i += kHaThreads) {
+  for (int i = threadIdx.x; i < rows; i += NT) {
     const T* __restrict__ Tsrc = tsrc(i);
     T acc[RB];
 #pragma unroll
@@ -139,8 +139,8 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, in
 // ------------------------------------------------------------------------------------
 // Upward pass of the HODLR fronts of one level.
 // ------------------------------------------------------------------------------------
-template <typename T, int RB>
-__global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
+template <typename T, int RB, int NT>
+__global__ void __launch_bounds__(NT) k_hodlr_up(
     const HApplyTask* __restrict__ tasks, int C, int nrhs, int n, const T* __restrict__ win,
     const int* __restrict__ npiv, const int* __restrict__ nhat, const int64_t* __restrict__ fvoff,
     const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child_list,
@@ -164,11 +164,11 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
   const int U0 = (int)((int64_t)tk.nu * c / C), U1 = (int)((int64_t)tk.nu * (c + 1) / C), nU = U1 - U0;
   const int np = tk.np, nh = tk.nhat;
   // [r(I_q); 0] on this CTA's rows
-  for (int e = threadIdx.x; e < nP * RB; e += kHaThreads) {
+  for (int e = threadIdx.x; e < nP * RB; e += NT) {
     const int i = e % nP, r = e / nP;
     Bp[i * RP + r] = r < nr ? win[tk.first + P0 + i + (int64_t)(r0 + r) * n] : T(0);
   }
-  for (int e = threadIdx.x; e < nU * RP; e += kHaThreads) Fs[e] = T(0);
+  for (int e = threadIdx.x; e < nU * RP; e += NT) Fs[e] = T(0);
   // the children's update parts through the relative maps, one child after another; a
   // relative map is increasing, so the entries that land on this CTA's rows are two
   // contiguous ranges of it
@@ -183,19 +183,19 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
     const int ta = rg.x, tb = rg.y, tc = rg.z, td = rg.w;
     const int na = tb - ta, nb = td - tc;
     const int tot = (na + nb) * nr;
-    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * kHaThreads) {  // eight entries per thread in flight
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * NT) {  // eight entries per thread in flight
       int d[8], t[8];
       T v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = min(e0 + u * kHaThreads, tot - 1), r = e / (na + nb), j = e - r * (na + nb);
+        const int e = min(e0 + u * NT, tot - 1), r = e / (na + nb), j = e - r * (na + nb);
         t[u] = j < na ? ta + j : tc + (j - na);
         d[u] = rm[t[u]];
         v[u] = fc[t[u] + (int64_t)(r0 + r) * nhc];
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * kHaThreads;
+        const int e = e0 + u * NT;
         if (e >= tot) continue;
         const int r = e / (na + nb), j = e - r * (na + nb);
         if (j < na) Bp[(d[u] - P0) * RP + r] += v[u];
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
   if (tk.kf > 0) {
     // partial tf = Vtilde(rows)^T b_p(rows), one column of Vtilde per warp
     const T* Vt = (const T*)tk.X + P0;
-    for (int col = threadIdx.x >> 5; col < tk.kf; col += kHaWarps) {
+    for (int col = threadIdx.x >> 5; col < tk.kf; col += (NT / 32)) {
       T acc[RB];
       warp_col_dot<T, RB>(Vt + (int64_t)col * np, nP, Bp, 0, acc);
       if ((threadIdx.x & 31) == 0) {
@@ -217,22 +217,22 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
       }
     }
     if (C > 1) cluster.sync(); else __syncthreads();
-    for (int e = threadIdx.x; e < tk.kf * RB; e += kHaThreads) {
+    for (int e = threadIdx.x; e < tk.kf * RB; e += NT) {
       T s = T(0);
       for (int cc = 0; cc < C; ++cc) s += cluster.map_shared_rank(Part, cc)[e];
       tf[e] = s;
     }
     __syncthreads();
     // b_f -= W(rows) tf
-    rows_update<T, RB>((const T*)tk.W + U0, tk.nu, nU, tk.kf, [&](int) { return (const T*)tf; }, Fs, T(-1));
+    rows_update<T, RB, NT>((const T*)tk.W + U0, tk.nu, nU, tk.kf, [&](int) { return (const T*)tf; }, Fs, T(-1));
     __syncthreads();
   }
   T* fv = FV + tk.fv_off;
-  for (int e = threadIdx.x; e < nP * nr; e += kHaThreads) {
+  for (int e = threadIdx.x; e < nP * nr; e += NT) {
     const int i = e % nP, r = e / nP;
     fv[P0 + i + (int64_t)(r0 + r) * nh] = Bp[i * RP + r];
   }
-  for (int e = threadIdx.x; e < nU * nr; e += kHaThreads) {
+  for (int e = threadIdx.x; e < nU * nr; e += NT) {
     const int i = e % nU, r = e / nU;
     fv[np + U0 + i + (int64_t)(r0 + r) * nh] = Fs[i * RP + r];
   }
@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_up(
 // ------------------------------------------------------------------------------------
 // Downward pass of the HODLR fronts of one level.
 // ------------------------------------------------------------------------------------
-template <typename T, int RB>
-__global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
+template <typename T, int RB, int NT>
+__global__ void __launch_bounds__(NT) k_hodlr_down(
     const HApplyTask* __restrict__ tasks, int C, int nrhs, int n, T* __restrict__ xv,
     const int64_t* __restrict__ ifoff, const int32_t* __restrict__ iflist, const int* __restrict__ leafb,
     const T* __restrict__ FV, HaDims dm) {
@@ -270,28 +270,28 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // b_p (left by the upward pass) and -x(I_q^f) on this CTA's rows
   const T* fv = FV + tk.fv_off;
-  for (int e = threadIdx.x; e < nP * RB; e += kHaThreads) {
+  for (int e = threadIdx.x; e < nP * RB; e += NT) {
     const int i = e % nP, r = e / nP;
     Bp[i * RP + r] = r < nr ? fv[P0 + i + (int64_t)(r0 + r) * nh] : T(0);
   }
   // -x(I_q^f): eight indices per thread loaded, then the eight values
   const int32_t* If = iflist + ifoff[tk.q];
-  for (int e0 = threadIdx.x; e0 < nU * RB; e0 += 8 * kHaThreads) {
+  for (int e0 = threadIdx.x; e0 < nU * RB; e0 += 8 * NT) {
     int g[8];
     T v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = min(e0 + u * kHaThreads, nU * RB - 1), i = e % nU;
+      const int e = min(e0 + u * NT, nU * RB - 1), i = e % nU;
       g[u] = If[U0 + i];
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = min(e0 + u * kHaThreads, nU * RB - 1), r = e / nU;
+      const int e = min(e0 + u * NT, nU * RB - 1), r = e / nU;
       v[u] = r < nr ? -xv[g[u] + (int64_t)(r0 + r) * n] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * kHaThreads;
+      const int e = e0 + u * NT;
       if (e < nU * RB) Xf[(e % nU) * RP + e / nU] = v[u];
     }
   }
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
   // this CTA's partial of tf = W^T (-x_f)
   if (tk.kf > 0) {
     const T* Wr = (const T*)tk.W + U0;
-    for (int col = warp; col < tk.kf; col += kHaWarps) {
+    for (int col = warp; col < tk.kf; col += (NT / 32)) {
       T acc[RB];
       warp_col_dot<T, RB>(Wr + (int64_t)col * tk.nu, nU, Xf, 0, acc);
       if (lane == 0) {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
   // leaves: y = K_leaf^{-1} b_p, one row per thread (the leaf's inverse, symmetric, is
   // read by columns: consecutive threads read consecutive rows; packed, ld np)
   const T* F = (const T*)tk.F;
-  for (int i = threadIdx.x; i < nP; i += kHaThreads) {
+  for (int i = threadIdx.x; i < nP; i += NT) {
     const int j = leaf_of(lb, c * span, (c + 1) * span, P0 + i);
     const int lo = lb[j], nl = lb[j + 1] - lo, ii = P0 + i - lo;
     T acc[RB];
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
     if (l >= lc) {
       // nodes inside this CTA: t = [U^T y_a; V^T y_b] for each, then y -= G t
       const int nn = 1 << (l - lc), n0 = c << (l - lc);
-      for (int it = warp; it < nn * 2 * k; it += kHaWarps) {
+      for (int it = warp; it < nn * 2 * k; it += (NT / 32)) {
         const int ni = it / (2 * k), cc = it - ni * 2 * k;
         const int nd = n0 + ni;
         const int lo = lb[nd * nspan], mid = lb[nd * nspan + nspan / 2], hi = lb[(nd + 1) * nspan];
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
       }
       __syncthreads();
       const int sh = L - l;
-      rows_update<T, RB>(Gl + P0, np, nP, 2 * k,
+      rows_update<T, RB, NT>(Gl + P0, np, nP, 2 * k,
                          [&](int i) {
                            const int ni = (leaf_of(lb, c * span, (c + 1) * span, P0 + i) >> sh) - n0;
                            return (const T*)(Ts + ni * 2 * k * RB);
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
       // the node spans 2^(lc - l) CTAs; this CTA's rows lie on one side of its split
       const int g = lc - l, nd = c >> g;
       T* pb = Part + buf * dm.kmax * RB;
-      for (int col = warp; col < k; col += kHaWarps) {
+      for (int col = warp; col < k; col += (NT / 32)) {
         T acc[RB];
         warp_col_dot<T, RB>(Bo + P0 + (int64_t)col * np, nP, Ys, 0, acc);
         if (lane == 0) {
@@ -384,14 +384,14 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
       }
       cluster.sync();
       const int cfirst = nd << g, half = 1 << (g - 1);
-      for (int e = threadIdx.x; e < 2 * k * RB; e += kHaThreads) {
+      for (int e = threadIdx.x; e < 2 * k * RB; e += NT) {
         const int cc = e / RB, r = e - cc * RB, sd = cc < k ? 0 : 1, col = cc - sd * k;
         T s = T(0);
         for (int p = 0; p < half; ++p) s += cluster.map_shared_rank(pb, cfirst + sd * half + p)[col * RB + r];
         Ts[e] = s;
       }
       if (!tf_ready && tk.kf > 0) {
-        for (int e = threadIdx.x; e < tk.kf * RB; e += kHaThreads) {
+        for (int e = threadIdx.x; e < tk.kf * RB; e += NT) {
           T s = T(0);
           for (int cc = 0; cc < C; ++cc) s += cluster.map_shared_rank(Part2, cc)[e];
           tf2[e] = s;
@@ -399,21 +399,21 @@ __global__ void __launch_bounds__(kHaThreads) k_hodlr_down(
       }
       tf_ready = true;
       __syncthreads();
-      rows_update<T, RB>(Gl + P0, np, nP, 2 * k, [&](int) { return (const T*)Ts; }, Ys, T(-1));
+      rows_update<T, RB, NT>(Gl + P0, np, nP, 2 * k, [&](int) { return (const T*)Ts; }, Ys, T(-1));
       __syncthreads();
       buf ^= 1;
     }
   }
   if (tk.kf > 0) {
     if (!tf_ready) {  // one CTA per front (or no level spans several): the partial is the sum
-      for (int e = threadIdx.x; e < tk.kf * RB; e += kHaThreads) tf2[e] = Part2[e];
+      for (int e = threadIdx.x; e < tk.kf * RB; e += NT) tf2[e] = Part2[e];
       __syncthreads();
     }
     // x_p = y + Vtilde tf,  tf = W^T (-x_f)
-    rows_update<T, RB>((const T*)tk.X + P0, np, nP, tk.kf, [&](int) { return (const T*)tf2; }, Ys, T(1));
+    rows_update<T, RB, NT>((const T*)tk.X + P0, np, nP, tk.kf, [&](int) { return (const T*)tf2; }, Ys, T(1));
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < nP * nr; e += kHaThreads) {
+  for (int e = threadIdx.x; e < nP * nr; e += NT) {
     const int i = e % nP, r = e / nP;
     xv[tk.first + P0 + i + (int64_t)(r0 + r) * n] = Ys[i * RP + r];
   }
@@ -461,7 +461,7 @@ size_t hodlr_apply_smem(const HaDims& d, int RB, bool down, int es) {
   return (size_t)ha_layout(d, RB, down).total * es;
 }
 
-template <typename T, int RB>
+template <typename T, int RB, int NT>
 static cudaError_t launch_rb(bool down, const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys,
                              SolvePlan* sp, int nrhs, const T* win, T* xv, cudaStream_t s) {
   const Plan& P = sys->plan;
@@ -469,7 +469,7 @@ static cudaError_t launch_rb(bool down, const LevelSolvePlan& lp, const unsigned
   const int C = lp.ha_C;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(lp.ha_tasks.count * C), (unsigned)((nrhs + RB - 1) / RB), 1);
-  cfg.blockDim = dim3(kHaThreads, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
   cfg.dynamicSmemBytes = hodlr_apply_smem(dm, RB, down, (int)sizeof(T));
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -482,47 +482,60 @@ static cudaError_t launch_rb(bool down, const LevelSolvePlan& lp, const unsigned
   const HApplyTask* tasks = lp.ha_tasks.dev(base);
   const int* leafb = lp.ha_leaf.dev(base);
   if (!down)
-    return cudaLaunchKernelEx(&cfg, k_hodlr_up<T, RB>, tasks, C, nrhs, sys->n, win, (const int*)P.d_np,
+    return cudaLaunchKernelEx(&cfg, k_hodlr_up<T, RB, NT>, tasks, C, nrhs, sys->n, win, (const int*)P.d_np,
                               (const int*)P.d_nhat, (const int64_t*)sp->d_fvoff, (const int32_t*)sys->d_child_ptr,
                               (const int32_t*)sys->d_child_list, (const int64_t*)sys->d_ifoff,
                               (const int32_t*)sys->d_relmap, leafb, (const int4*)sp->d_ea, (T*)sp->d_fv, dm);
-  return cudaLaunchKernelEx(&cfg, k_hodlr_down<T, RB>, tasks, C, nrhs, sys->n, xv, (const int64_t*)sys->d_ifoff,
+  return cudaLaunchKernelEx(&cfg, k_hodlr_down<T, RB, NT>, tasks, C, nrhs, sys->n, xv, (const int64_t*)sys->d_ifoff,
                             (const int32_t*)sys->d_iflist, leafb, (const T*)sp->d_fv, dm);
 }
 
+// nt: threads per CTA, 256, or 512 (for groups of at most four right-hand sides: more
+// loads in flight on the few clusters of the top levels)
 template <typename T>
 int launch_hodlr_apply(bool down, const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys,
-                       SolvePlan* sp, int nrhs, const T* win, T* xv, int rb) {
+                       SolvePlan* sp, int nrhs, const T* win, T* xv, int rb, int nt) {
   cudaStream_t s = sys->ctx->stream;
   cudaError_t e;
-  switch (rb) {
-    case 1: e = launch_rb<T, 1>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
-    case 2: e = launch_rb<T, 2>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
-    case 4: e = launch_rb<T, 4>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
-    case 8: e = launch_rb<T, 8>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
-    default: e = launch_rb<T, 16>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+  if (nt == 512 && rb <= 4) {
+    switch (rb) {
+      case 1: e = launch_rb<T, 1, 512>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+      case 2: e = launch_rb<T, 2, 512>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+      default: e = launch_rb<T, 4, 512>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+    }
+  } else {
+    switch (rb) {
+      case 1: e = launch_rb<T, 1, kHaThreads>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+      case 2: e = launch_rb<T, 2, kHaThreads>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+      case 4: e = launch_rb<T, 4, kHaThreads>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+      case 8: e = launch_rb<T, 8, kHaThreads>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+      default: e = launch_rb<T, 16, kHaThreads>(down, lp, base, sys, sp, nrhs, win, xv, s); break;
+    }
   }
   HM_CUDA(e);
   return HM_OK;
 }
 template int launch_hodlr_apply<float>(bool, const LevelSolvePlan&, const unsigned char*, hm_sys_s*, SolvePlan*,
-                                       int, const float*, float*, int);
+                                       int, const float*, float*, int, int);
 template int launch_hodlr_apply<double>(bool, const LevelSolvePlan&, const unsigned char*, hm_sys_s*, SolvePlan*,
-                                        int, const double*, double*, int);
+                                        int, const double*, double*, int, int);
 
-template <typename T, int RB>
+template <typename T, int RB, int NT>
 static int setup_rb(int max_smem) {
-  HM_CUDA(allow_max_dyn_smem(k_hodlr_up<T, RB>, max_smem));
-  HM_CUDA(allow_max_dyn_smem(k_hodlr_down<T, RB>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_hodlr_up<T, RB, NT>, max_smem));
+  HM_CUDA(allow_max_dyn_smem(k_hodlr_down<T, RB, NT>, max_smem));
   return HM_OK;
 }
 template <typename T>
 static int setup_t(int max_smem) {
-  HM_TRY((setup_rb<T, 1>(max_smem)));
-  HM_TRY((setup_rb<T, 2>(max_smem)));
-  HM_TRY((setup_rb<T, 4>(max_smem)));
-  HM_TRY((setup_rb<T, 8>(max_smem)));
-  HM_TRY((setup_rb<T, 16>(max_smem)));
+  HM_TRY((setup_rb<T, 1, kHaThreads>(max_smem)));
+  HM_TRY((setup_rb<T, 2, kHaThreads>(max_smem)));
+  HM_TRY((setup_rb<T, 4, kHaThreads>(max_smem)));
+  HM_TRY((setup_rb<T, 8, kHaThreads>(max_smem)));
+  HM_TRY((setup_rb<T, 16, kHaThreads>(max_smem)));
+  HM_TRY((setup_rb<T, 1, 512>(max_smem)));
+  HM_TRY((setup_rb<T, 2, 512>(max_smem)));
+  HM_TRY((setup_rb<T, 4, 512>(max_smem)));
   return HM_OK;
 }
 int hodlr_apply_setup(int max_smem) {

@@ -687,10 +687,11 @@ int apply_impl_rowmajor(hm_sys_s* sys, int nrhs, const void* rT, void* zT);
 int solve_setup(int max_smem);
 // The fused HODLR-front apply of one level (upward: down = false, input win; downward:
 // solution rows of the level's fronts into xv).
-// rb: right-hand sides per cluster (1, 2, 4, 8 or 16, at most lp.ha_RB).
+// rb: right-hand sides per cluster (1, 2, 4, 8 or 16, at most lp.ha_RB); nt: threads per
+// CTA (256, or 512 for rb <= 4).
 template <typename T>
 int launch_hodlr_apply(bool down, const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys,
-                       SolvePlan* sp, int nrhs, const T* win, T* xv, int rb);
+                       SolvePlan* sp, int nrhs, const T* win, T* xv, int rb, int nt);
 size_t hodlr_apply_smem(const HaDims& d, int RB, bool down, int es);
 int hodlr_apply_setup(int max_smem);
 int hodlr_child_ranges(const LevelSolvePlan& lp, const unsigned char* base, hm_sys_s* sys, SolvePlan* sp);

@@ -434,13 +434,18 @@ static dim3 vgrid(int nitems, int nrhs, int maxlen) {
 // A level's HODLR fronts take the fused cluster kernels where they fit: variant 0 with
 // a quarter of the plan's widest right-hand-side group per cluster, 2 and 3 with an
 // eighth and a sixteenth (more clusters in flight, each reading the factor again, mostly
-// from L2); variant 1 is the batched-GEMM path.
+// from L2), 4 as 0 with 512 threads per CTA instead of 256 (twice the loads in flight
+// on the few clusters of the top levels; groups of up to four right-hand sides);
+// variant 1 is the batched-GEMM path.
 static bool fused_level(const hm_ctx_s* ctx, const LevelSolvePlan& lp) {
   return lp.ha_ok && ctx->tune.variant(TS_HODLR_APPLY, lp.ha_sig) != 1;
 }
 static int fused_rb(const hm_ctx_s* ctx, const LevelSolvePlan& lp) {
   const int v = ctx->tune.variant(TS_HODLR_APPLY, lp.ha_sig);
   return std::max(1, lp.ha_RB >> (v == 2 ? 3 : v == 3 ? 4 : 2));
+}
+static int fused_nt(const hm_ctx_s* ctx, const LevelSolvePlan& lp) {
+  return ctx->tune.variant(TS_HODLR_APPLY, lp.ha_sig) == 4 ? 512 : 256;
 }
 
 // The launches of one apply (input win, output in the plan's fixed buffer).
@@ -463,7 +468,8 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
     if (lp.n_hodlr && fused_level(ctx, lp)) {
       ProfScope ps(ctx, PC_HODLR_UP, lp.ha_up_work);
       TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);
-      HM_TRY(launch_hodlr_apply<T>(false, lp, base, sys, sp, nrhs, win, nullptr, fused_rb(ctx, lp)));
+      HM_TRY(launch_hodlr_apply<T>(false, lp, base, sys, sp, nrhs, win, nullptr, fused_rb(ctx, lp),
+                                    fused_nt(ctx, lp)));
     } else if (lp.n_hodlr) {
       TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);
       {
@@ -486,7 +492,8 @@ static int apply_launches(hm_sys_s* sys, SolvePlan* sp, int nrhs, const T* win) 
     if (lp.n_hodlr && fused_level(ctx, lp)) {
       ProfScope ps(ctx, PC_HODLR_DOWN, lp.ha_down_work);
       TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);  // one key for both passes: one choice
-      HM_TRY(launch_hodlr_apply<T>(true, lp, base, sys, sp, nrhs, nullptr, xfix, fused_rb(ctx, lp)));
+      HM_TRY(launch_hodlr_apply<T>(true, lp, base, sys, sp, nrhs, nullptr, xfix, fused_rb(ctx, lp),
+                                    fused_nt(ctx, lp)));
     } else if (lp.n_hodlr) {
       TuneScope ts(ctx, TS_HODLR_APPLY, lp.ha_sig);  // one key for both passes: one choice
       if (lp.hodlr_max_nu > 0) {

@@ -98,3 +98,31 @@ def test_every_forced_variant_solves(precision):
     with pytest.raises(hm.HmError):
         hm.hm_tune_force(ctx, 7)
     hm.hm_ctx_destroy(ctx)
+
+
+def test_hodlr_apply_variants_agree():
+    """The HODLR fronts' cluster apply with 512 threads per CTA (variant 4) computes every
+    row and every column sum in the same order as with 256 (variant 0): on two identical
+    factorizations (both under variant 0) the applies agree to FP32 rounding."""
+    m = 160
+    P = q1_square(m, lognormal_coefficients(m * m, sigma=1.0, mu=0.0, seed=17))
+    o = hm.hm_default_opts()
+    o.precision = hm.HM_PREC_MIXED
+    o.n_c = 32
+    o.hodlr_leaf = 32
+    ctx = hm.hm_create(o)
+    r = rhs_uniform(P.n, 3, 18)
+    zs = []
+    for v in (0, 4):
+        hm.hm_tune_force(ctx, 0)
+        s = hm.hm_analyze(ctx, P.n, P.rowptr, P.colidx, 2, P.coords)
+        info = hm.hm_factor(s, P.values, 1e-4)
+        assert info["n_hodlr"] > 0
+        hm.hm_tune_force(ctx, v)  # the apply plan and its launches are made after this
+        z = np.zeros_like(r)
+        hm.hm_precond_apply(s, 3, r, z)
+        zs.append(z)
+        hm.hm_destroy(s)
+    hm.hm_tune_force(ctx, -1)
+    assert np.linalg.norm(zs[1] - zs[0]) / np.linalg.norm(zs[0]) <= 1e-6
+    hm.hm_ctx_destroy(ctx)
