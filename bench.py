@@ -92,6 +92,9 @@ def parse_args():
                     help="profiling driver for ncu: run analyze + factor (+ one apply) of the "
                          "workload twice, the second factor / apply inside NVTX ranges "
                          "'factor1' / 'apply1'; prints nothing else")
+    ap.add_argument("--probe-apply-variant", type=int, default=-1,
+                    help="probe: launch variant forced on the apply's tunable sites (the "
+                         "factorization keeps the defaults); -1 = the defaults")
     return ap.parse_args()
 
 
@@ -871,12 +874,14 @@ def run_probe(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         if nrhs:
+            hm.hm_tune_force(ctx, args.probe_apply_variant)
             hm.hm_precond_apply(s, nrhs, b, z)
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_push(f"apply{it}")
             hm.hm_precond_apply(s, nrhs, b, z)
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_pop()
+            hm.hm_tune_force(ctx, -1)
         hm.hm_destroy(s)
     hm.hm_ctx_destroy(ctx)
 
