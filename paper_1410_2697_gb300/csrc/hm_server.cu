@@ -131,8 +131,16 @@ static bool evict_one(hm_server_s* S, int w, int keep) {
     S->evictions++;
   }
   // the system moves to this worker first: its frees then run on this worker's own
-  // stream (another worker's stream may be capturing a graph)
-  if (move_sys(victim->sys, S->workers[w].ctx, victim->ready) == HM_OK) hm_destroy(victim->sys);
+  // stream (another worker's stream may be capturing a graph); a system that cannot move
+  // stays resident where it is
+  if (move_sys(victim->sys, S->workers[w].ctx, victim->ready) != HM_OK) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    victim->serving = -1;
+    S->evictions--;
+    S->cv_work.notify_all();
+    return false;
+  }
+  hm_destroy(victim->sys);
   std::lock_guard<std::mutex> lk(S->mu);
   victim->sys = nullptr;
   victim->bytes = 0;
