@@ -28,3 +28,13 @@ def test_reference_arm_json_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert d["relres_max"] <= 1e-10
+
+
+def test_l2_note_states_the_working_set_against_l2():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    big = bench.l2_note(121e6, 615e6, 525e6, 129e6)  # the 1024^2 step: CSR, factor, fronts
+    assert big.startswith("inputs larger than L2") and "1261 MB" in big and "129 MB" in big
+    small = bench.l2_note(0.4e6, 3e6, 4e6, 129e6)   # the 64^2 step fits in L2
+    assert small.startswith("working set 7 MB, within the 129 MB L2")
